@@ -1,0 +1,20 @@
+"""Seeded synthetic two-sided markets.
+
+This package only draws random inputs: factor matrices, popularity biases and
+capacities. It holds none of the IPFP arithmetic, so both the CPU oracle
+(``oracle/``) and the CUDA path (``paper_2411_19214_gb300``) can be fed from it
+without sharing any of the method's code.
+"""
+
+from .markets import (  # noqa: F401
+    Market,
+    make_market,
+    round_to_bf16,
+    bf16_bits,
+    dense_job_market,
+    fused_market,
+    plain_dense_market,
+    paper_shaped_market,
+    batched_market_sizes,
+    serving_request_sizes,
+)

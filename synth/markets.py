@@ -1,0 +1,197 @@
+"""Seeded generators for synthetic matching markets.
+
+Every workload of the benchmark and of the tests comes from here. A market is
+the input of the matrix-factorisation IPFP: factor matrices F, K (candidates,
+N x d) and G, L (employers, M x d), optional additive popularity biases per
+user, capacities n (N) and m (M), and the entropy scale sigma (= beta).
+
+Values are drawn with numpy's PCG64 generator from a fixed seed, in float32,
+then rounded (round-to-nearest-even) to the element type the device computes
+in. The arrays stored in a :class:`Market` are exactly the values the device
+sees, so a float64 computation on them measures the kernel and not the
+quantisation.
+
+Recipes (shapes and distributions follow the paper's Sec. 4.2 benchmark,
+factors U[0, 1/sqrt(D)] with equal capacities, and the larger job-market
+shapes of the benchmark configurations):
+
+* ``plain_dense_market``: N = M = 1000, d = 16, factors N(0, 1/d), n = m = 1,
+  sigma = 1.
+* ``dense_job_market``: N = 20000 candidates, M = 10000 jobs, d = 32, factors
+  N(0, 1/d), a LogNormal(0, 1) popularity bias on jobs, n = 1, job capacities
+  uniform on {1..5}, sigma = 0.5, float32.
+* ``fused_market``: N = M = 1e6, d = 64, bf16 factors N(0, 1/d), LogNormal(0, 1)
+  popularity biases on both sides (float32), n = m = 1, sigma = 0.5.
+* ``paper_shaped_market``: N = M, D = 50, factors U[0, 1/sqrt(D)],
+  n = m = 1 (C = N), sigma = 1.
+"""
+
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+
+
+def round_to_bf16(x: np.ndarray) -> np.ndarray:
+    """Round float32 values to the nearest bfloat16 (ties to even).
+
+    Returns float32 values that are exactly representable in bfloat16.
+    """
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    bits = a.view(np.uint32).astype(np.uint64)
+    bias = ((bits >> np.uint64(16)) & np.uint64(1)) + np.uint64(0x7FFF)
+    out = ((bits + bias) & np.uint64(0xFFFF0000)).astype(np.uint32)
+    return out.view(np.float32).reshape(a.shape)
+
+
+def bf16_bits(x: np.ndarray) -> np.ndarray:
+    """The bfloat16 bit patterns (uint16) of float32 values that are already
+    bfloat16-representable (output of :func:`round_to_bf16`)."""
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    bits = a.view(np.uint32)
+    if np.any(bits & np.uint32(0xFFFF)):
+        raise ValueError("values are not bfloat16-representable; call round_to_bf16 first")
+    return (bits >> np.uint32(16)).astype(np.uint16).reshape(a.shape)
+
+
+@dataclasses.dataclass
+class Market:
+    """One synthetic market, values as the device sees them."""
+
+    F: np.ndarray  # (N, d) float32
+    K: np.ndarray  # (N, d) float32
+    G: np.ndarray  # (M, d) float32
+    L: np.ndarray  # (M, d) float32
+    bias_x: Optional[np.ndarray]  # (N,) float32 or None
+    bias_y: Optional[np.ndarray]  # (M,) float32 or None
+    n: np.ndarray  # (N,) float64 capacities of side X
+    m: np.ndarray  # (M,) float64 capacities of side Y
+    sigma: float
+    dtype: str  # "bf16" or "fp32": element type of F, K, G, L on the device
+    seed: int
+    recipe: str
+
+    @property
+    def N(self) -> int:
+        return int(self.F.shape[0])
+
+    @property
+    def M(self) -> int:
+        return int(self.G.shape[0])
+
+    @property
+    def d(self) -> int:
+        return int(self.F.shape[1])
+
+    def f64(self) -> dict:
+        """float64 copies of every array (what the oracle consumes)."""
+        out = {k: getattr(self, k).astype(np.float64) for k in ("F", "K", "G", "L", "n", "m")}
+        out["bias_x"] = None if self.bias_x is None else self.bias_x.astype(np.float64)
+        out["bias_y"] = None if self.bias_y is None else self.bias_y.astype(np.float64)
+        out["sigma"] = float(self.sigma)
+        return out
+
+    def swapped(self) -> "Market":
+        """The same market with the two sides exchanged (X <-> Y)."""
+        return dataclasses.replace(
+            self, F=self.G, K=self.L, G=self.F, L=self.K,
+            bias_x=self.bias_y, bias_y=self.bias_x, n=self.m, m=self.n,
+            recipe=self.recipe + "/swapped")
+
+
+def _capacities(rng: np.random.Generator, size: int, kind: str) -> np.ndarray:
+    if kind == "unit":
+        return np.ones(size, dtype=np.float64)
+    if kind == "uniform1to5":
+        return rng.integers(1, 6, size=size).astype(np.float64)
+    if kind == "uniform1to3":
+        return rng.integers(1, 4, size=size).astype(np.float64)
+    if kind == "uniform_real":
+        return rng.uniform(0.5, 2.0, size=size)
+    raise ValueError(f"unknown capacity kind {kind!r}")
+
+
+def _factors(rng: np.random.Generator, rows: int, d: int, dist: str) -> np.ndarray:
+    if dist == "normal":
+        return rng.standard_normal((rows, d), dtype=np.float32) * np.float32(1.0 / math.sqrt(d))
+    if dist == "uniform":
+        return rng.random((rows, d), dtype=np.float32) * np.float32(1.0 / math.sqrt(d))
+    raise ValueError(f"unknown factor distribution {dist!r}")
+
+
+def make_market(N: int, M: int, d: int, *, sigma: float, seed: int,
+                dist: str = "normal", bias_x: bool = False, bias_y: bool = False,
+                n_kind: str = "unit", m_kind: str = "unit", dtype: str = "bf16",
+                factor_scale: float = 1.0, recipe: str = "custom") -> Market:
+    """Draw one market. Draw order (fixed): F, K, G, L, bias_x, bias_y, n, m."""
+    if dtype not in ("bf16", "fp32"):
+        raise ValueError("dtype must be 'bf16' or 'fp32'")
+    rng = np.random.default_rng(seed)
+    mats = []
+    for rows in (N, N, M, M):
+        a = _factors(rng, rows, d, dist)
+        if factor_scale != 1.0:
+            a = a * np.float32(factor_scale)
+        mats.append(round_to_bf16(a) if dtype == "bf16" else a.astype(np.float32))
+    F, K, G, L = mats
+    bx = rng.lognormal(0.0, 1.0, size=N).astype(np.float32) if bias_x else None
+    by = rng.lognormal(0.0, 1.0, size=M).astype(np.float32) if bias_y else None
+    n = _capacities(rng, N, n_kind)
+    m = _capacities(rng, M, m_kind)
+    return Market(F, K, G, L, bx, by, n, m, float(sigma), dtype, seed, recipe)
+
+
+def plain_dense_market(N: int = 1000, M: int = 1000, d: int = 16, seed: int = 1000,
+                       dtype: str = "fp32") -> Market:
+    """Balanced plain market: factors N(0, 1/d), unit capacities, sigma = 1."""
+    return make_market(N, M, d, sigma=1.0, seed=seed, dtype=dtype,
+                       recipe=f"plain N={N} M={M} d={d}")
+
+
+def dense_job_market(N: int = 20000, M: int = 10000, d: int = 32, seed: int = 1001,
+                     dtype: str = "fp32") -> Market:
+    """Job market for the materialised-kernel path: lognormal job popularity,
+    job capacities uniform on {1..5}, sigma = 0.5."""
+    return make_market(N, M, d, sigma=0.5, seed=seed, bias_y=True, m_kind="uniform1to5",
+                       dtype=dtype, recipe=f"job N={N} M={M} d={d}")
+
+
+def fused_market(N: int = 1_000_000, M: int = 1_000_000, d: int = 64, seed: int = 1002,
+                 dtype: str = "bf16") -> Market:
+    """Large balanced market for the on-the-fly path: bf16 factors N(0, 1/d),
+    lognormal popularity biases on both sides, unit capacities, sigma = 0.5."""
+    return make_market(N, M, d, sigma=0.5, seed=seed, bias_x=True, bias_y=True,
+                       dtype=dtype, recipe=f"fused N={N} M={M} d={d}")
+
+
+def paper_shaped_market(N: int, D: int = 50, seed: int = 1005, dtype: str = "bf16") -> Market:
+    """Sec. 4.2 shape: N = M, factors U[0, 1/sqrt(D)], n = m = C/N with C = N, beta = 1."""
+    return make_market(N, N, D, sigma=1.0, seed=seed, dist="uniform", dtype=dtype,
+                       recipe=f"paper N={N} D={D}")
+
+
+def batched_market_sizes(count: int = 512, lo: int = 100, hi: int = 50_000,
+                         seed: int = 1003) -> list:
+    """(N, M, capacity kind) of many independent markets; sizes log-uniform."""
+    rng = np.random.default_rng(seed)
+    ln = rng.uniform(math.log(lo), math.log(hi), size=(count, 2))
+    sizes = np.rint(np.exp(ln)).astype(np.int64)
+    kinds = ["unit" if i % 2 == 0 else "uniform1to3" for i in range(count)]
+    return [(int(a), int(b), k) for (a, b), k in zip(sizes, kinds)]
+
+
+def serving_request_sizes(count: int, rate: float = 200.0, lo: int = 1000, hi: int = 200_000,
+                          seed: int = 1004) -> list:
+    """Poisson arrival times and log-uniform sizes of a stream of solve requests."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=count)
+    t = np.cumsum(gaps)
+    ln = rng.uniform(math.log(lo), math.log(hi), size=(count, 2))
+    sizes = np.rint(np.exp(ln)).astype(np.int64)
+    d = rng.choice([32, 64], size=count)
+    resolve = rng.random(count) < 0.3
+    return [dict(t=float(ti), N=int(a), M=int(b), d=int(di), resolve=bool(r))
+            for ti, (a, b), di, r in zip(t, sizes, d, resolve)]

@@ -1,0 +1,440 @@
+"""Pins of the float64 oracle against what the paper and the mathematics fix.
+
+None of these tests uses the CUDA path. Each pin is chosen so that a plausible
+mistake in the oracle (a dropped 1/2, beta instead of 2 beta, a transposed
+operand, a wrong sign, Jacobi instead of Gauss-Seidel order) fails at least one
+of them; ``test_planted_mistakes_are_caught`` checks that for a list of such
+mistakes planted into the oracle.
+"""
+
+import json
+import os
+
+import mpmath as mp
+import numpy as np
+import pytest
+
+import oracle
+from oracle import ipfp as O
+from synth import make_market
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")
+
+
+def _random_market(rng, N, M, d=3, bias=True, cap=True):
+    F, K = rng.normal(0, 0.7, (N, d)), rng.normal(0, 0.7, (N, d))
+    G, L = rng.normal(0, 0.7, (M, d)), rng.normal(0, 0.7, (M, d))
+    bx = rng.lognormal(0, 0.5, N) if bias else None
+    by = rng.lognormal(0, 0.5, M) if bias else None
+    n = rng.uniform(0.5, 2.0, N) if cap else np.ones(N)
+    m = rng.uniform(0.5, 3.0, M) if cap else np.ones(M)
+    return F, K, G, L, bx, by, n, m
+
+
+def _solve(Phi, n, m, beta, tol=1e-13, max_sweeps=200000):
+    r = oracle.ipfp_batch(Phi, n, m, beta, max_sweeps=max_sweeps, tol=tol)
+    assert r["res_inf"] <= tol * 10, r["res_inf"]
+    return r
+
+
+# ---------------------------------------------------------------------------
+# Closed forms
+# ---------------------------------------------------------------------------
+
+def _golden():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("case", _golden()["one_by_one"], ids=lambda c: f"phi{c['phi']}")
+def test_closed_form_1x1(case):
+    """Eq. stable_condition + Eq. IPFP with one user per side: mu solves
+    (a^2-1) mu^2 - a^2 (n+m) mu + a^2 n m = 0, a = exp(phi/(2 beta))."""
+    Phi = np.array([[case["phi"]]])
+    n, m = np.array([case["n"]]), np.array([case["m"]])
+    r = _solve(Phi, n, m, case["beta"], tol=1e-14)
+    logA = oracle.log_kernel(Phi, case["beta"])
+    mu = float(np.exp(oracle.log_mu(logA, r["log_u"], r["log_v"]))[0, 0])
+    exact = float(mp.mpf(case["mu"]))
+    assert abs(mu - exact) <= 1e-12 * exact
+    # the unmatched masses close the two constraints of Eq. primary optimization
+    assert abs(np.exp(2 * r["log_u"][0]) + mu - case["n"]) <= 1e-12 * case["n"]
+    assert abs(np.exp(2 * r["log_v"][0]) + mu - case["m"]) <= 1e-12 * case["m"]
+
+
+def test_closed_form_fixture_matches_formula():
+    """The stored 1x1 values are the root of the quadratic (recomputed here)."""
+    mp.mp.dps = 40
+    for c in _golden()["one_by_one"]:
+        a2 = mp.e ** (mp.mpf(str(c["phi"])) / mp.mpf(str(c["beta"])))
+        n, m, mu = mp.mpf(str(c["n"])), mp.mpf(str(c["m"])), mp.mpf(c["mu"])
+        val = (a2 - 1) * mu ** 2 - a2 * (n + m) * mu + a2 * n * m
+        assert abs(val) <= mp.mpf("1e-25") * a2 * n * m
+
+
+@pytest.mark.parametrize("case", _golden()["symmetric_two_by_two"], ids=lambda c: f"a{c['alpha']}")
+def test_closed_form_symmetric_2x2(case):
+    """Symmetric 2x2 market, unit capacities: u = v = 1/sqrt(1 + e^{alpha/2b} + e^{gamma/2b})."""
+    a, g = case["alpha"], case["gamma"]
+    Phi = np.array([[a, g], [g, a]])
+    r = _solve(Phi, np.ones(2), np.ones(2), case["beta"], tol=1e-14)
+    w = float(mp.mpf(case["w"]))
+    np.testing.assert_allclose(np.exp(r["log_u"]), [w, w], rtol=1e-12)
+    np.testing.assert_allclose(np.exp(r["log_v"]), [w, w], rtol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Independent solvers of the same fixed point
+# ---------------------------------------------------------------------------
+
+def _newton_dual(Phi, n, m, beta, iters=100):
+    """Maximise the concave dual G(a, b) = sum n a + sum m b - 1/2 sum e^{2a}
+    - 1/2 sum e^{2b} - sum_xy A_xy e^{a_x + b_y}, whose gradient is exactly the
+    system Eq. IPFP with u = e^a, v = e^b. Newton with backtracking."""
+    A = np.exp(Phi / (2 * beta))
+    N, M = A.shape
+
+    def value(z):
+        a, b = z[:N], z[N:]
+        return (n @ a + m @ b - 0.5 * np.sum(np.exp(2 * a)) - 0.5 * np.sum(np.exp(2 * b))
+                - np.sum(A * np.exp(a[:, None] + b[None, :])))
+
+    z = np.full(N + M, -1.0)
+    for _ in range(iters):
+        a, b = z[:N], z[N:]
+        mu = A * np.exp(a[:, None] + b[None, :])
+        grad = np.concatenate([n - np.exp(2 * a) - mu.sum(1), m - np.exp(2 * b) - mu.sum(0)])
+        if np.max(np.abs(grad)) < 1e-15:
+            break
+        H = np.zeros((N + M, N + M))
+        H[:N, :N] = -np.diag(2 * np.exp(2 * a) + mu.sum(1))
+        H[N:, N:] = -np.diag(2 * np.exp(2 * b) + mu.sum(0))
+        H[:N, N:] = -mu
+        H[N:, :N] = -mu.T
+        step = np.linalg.solve(H, -grad)
+        t, g0 = 1.0, value(z)
+        while value(z + t * step) < g0 - 1e-14 and t > 1e-8:
+            t *= 0.5
+        z = z + t * step
+    return z[:N], z[N:]
+
+
+@pytest.mark.parametrize("shape", [(3, 4), (5, 2), (6, 6)])
+def test_newton_on_concave_dual(shape):
+    rng = np.random.default_rng(7)
+    F, K, G, L, bx, by, n, m = _random_market(rng, *shape)
+    beta = 0.8
+    Phi = oracle.phi_dense(F, K, G, L, bx, by)
+    r = _solve(Phi, n, m, beta)
+    a, b = _newton_dual(Phi, n, m, beta)
+    np.testing.assert_allclose(r["log_u"], a, atol=1e-11)
+    np.testing.assert_allclose(r["log_v"], b, atol=1e-11)
+
+
+def test_fixed_point_maximises_primal_welfare():
+    """Eq. primary optimization: the IPFP equilibrium is the maximiser of
+    W = sum mu phi + beta E(mu). W is strictly concave inside the feasible set,
+    so a stationary point is the maximum. Check stationarity by central finite
+    differences and the maximum against random feasible perturbations. This pins
+    the 2 beta of A = exp(Phi / (2 beta)) independently of the iteration."""
+    rng = np.random.default_rng(11)
+    F, K, G, L, bx, by, n, m = _random_market(rng, 3, 4)
+    beta = 0.6
+    Phi = oracle.phi_dense(F, K, G, L, bx, by)
+    r = _solve(Phi, n, m, beta)
+    mu = np.exp(oracle.log_mu(oracle.log_kernel(Phi, beta), r["log_u"], r["log_v"]))
+    w0 = oracle.welfare(Phi, mu, n, m, beta)
+    h = 1e-6
+    for i in range(mu.shape[0]):
+        for j in range(mu.shape[1]):
+            e = np.zeros_like(mu); e[i, j] = h
+            g = (oracle.welfare(Phi, mu + e, n, m, beta) - oracle.welfare(Phi, mu - e, n, m, beta)) / (2 * h)
+            assert abs(g) < 1e-6
+    for _ in range(200):
+        d = rng.normal(size=mu.shape) * 1e-3 * mu
+        assert oracle.welfare(Phi, mu + d, n, m, beta) < w0
+
+
+# ---------------------------------------------------------------------------
+# The update and the literal algorithm
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("s", [1e-300, 1e-12, 1e-3, 0.5, 1.0, 7.0, 1e4, 1e8, 1e150, 1e300])
+@pytest.mark.parametrize("n", [1e-6, 1.0, 5.0])
+def test_scaling_update_against_high_precision(s, n):
+    """Eq. iteration: u = sqrt(n + s^2) - s, the printed form evaluated in high precision."""
+    # enough digits that the printed difference itself does not cancel
+    mp.mp.dps = 60 + int(2 * abs(np.log10(s)) + abs(np.log10(n)))
+    S, Nm = mp.mpf(s), mp.mpf(n)
+    exact = mp.sqrt(Nm + S * S) - S
+    got = oracle.scaling_update(np.log(s), n)  # log u
+    assert abs(got - float(mp.log(exact))) <= 1e-13 * max(1.0, abs(got))
+
+
+def test_printed_update_cancels_where_stable_form_does_not():
+    """The printed difference loses every digit once s^2 >> n (reason for the
+    stable form); the two agree where it does not cancel."""
+    s, n = 1e8, 1.0
+    assert np.sqrt(n + s * s) - s == 0.0
+    assert np.exp(oracle.scaling_update(np.log(s), n)) == pytest.approx(0.5e-8, rel=1e-12)
+    for s in (0.1, 1.0, 3.0):
+        assert np.exp(oracle.scaling_update(np.log(s), n)) == pytest.approx(np.sqrt(n + s * s) - s, rel=1e-13)
+
+
+def test_literal_algorithm_1_matches_log_form():
+    """Alg. 1 as printed (linear domain) and the log-domain oracle give the same
+    iterates on a well-conditioned market, sweep by sweep."""
+    rng = np.random.default_rng(3)
+    F, K, G, L, _, _, n, m = _random_market(rng, 7, 5, bias=False)
+    beta = 1.0
+    P, Q = F @ G.T, K @ L.T
+    for iters in (1, 2, 5, 40):
+        u, v, mu = oracle.ipfp_batch_literal(P, Q, n, m, beta, iters)
+        r = oracle.ipfp_batch(P + Q, n, m, beta, max_sweeps=iters)
+        np.testing.assert_allclose(np.log(u), r["log_u"], rtol=0, atol=1e-13)
+        np.testing.assert_allclose(np.log(v), r["log_v"], rtol=0, atol=1e-13)
+        lm = oracle.log_mu(oracle.log_kernel(P + Q, beta), r["log_u"], r["log_v"])
+        np.testing.assert_allclose(np.log(mu), lm, atol=1e-12)
+
+
+def test_gauss_seidel_order():
+    """Eq. iteration: the v step uses the u of the same sweep. One sweep from
+    u = v = 1 is checked against values written out by hand for a 1x2 market."""
+    Phi = np.array([[0.4, -0.6]])
+    beta, n, m = 0.5, np.array([1.0]), np.array([2.0, 1.0])
+    A = np.exp(Phi / (2 * beta))[0]
+    s = 0.5 * (A[0] + A[1])
+    u = np.sqrt(n[0] + s * s) - s
+    v = [np.sqrt(m[j] + (0.5 * A[j] * u) ** 2) - 0.5 * A[j] * u for j in range(2)]
+    r = oracle.ipfp_batch(Phi, n, m, beta, max_sweeps=1)
+    assert np.exp(r["log_u"][0]) == pytest.approx(u, rel=1e-14)
+    np.testing.assert_allclose(np.exp(r["log_v"]), v, rtol=1e-14)
+
+
+# ---------------------------------------------------------------------------
+# Invariants at the fixed point
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def solved():
+    rng = np.random.default_rng(5)
+    F, K, G, L, bx, by, n, m = _random_market(rng, 30, 40, d=4)
+    beta = 0.7
+    Phi = oracle.phi_dense(F, K, G, L, bx, by)
+    r = _solve(Phi, n, m, beta)
+    return dict(F=F, K=K, G=G, L=L, bx=bx, by=by, n=n, m=m, beta=beta, Phi=Phi, r=r)
+
+
+def test_marginals_at_fixed_point(solved):
+    """Constraints of Eq. primary optimization with mu_x0 = u^2, mu_0y = v^2."""
+    s = solved
+    logA = oracle.log_kernel(s["Phi"], s["beta"])
+    mu = np.exp(oracle.log_mu(logA, s["r"]["log_u"], s["r"]["log_v"]))
+    np.testing.assert_allclose(mu.sum(1) + np.exp(2 * s["r"]["log_u"]), s["n"], rtol=1e-12)
+    np.testing.assert_allclose(mu.sum(0) + np.exp(2 * s["r"]["log_v"]), s["m"], rtol=1e-12)
+    assert oracle.col_residual(logA, s["m"], s["r"]["log_u"], s["r"]["log_v"])[0] < 1e-12
+
+
+def test_total_mass_identity(solved):
+    s = solved
+    logA = oracle.log_kernel(s["Phi"], s["beta"])
+    mu = np.exp(oracle.log_mu(logA, s["r"]["log_u"], s["r"]["log_v"]))
+    cx, cy = oracle.match_count(s["n"], s["r"]["log_u"], s["m"], s["r"]["log_v"])
+    assert cx == pytest.approx(mu.sum(), rel=1e-12)
+    assert cy == pytest.approx(mu.sum(), rel=1e-12)
+
+
+def test_permutation_equivariance(solved):
+    s = solved
+    rng = np.random.default_rng(9)
+    px, py = rng.permutation(30), rng.permutation(40)
+    Phi = oracle.phi_dense(s["F"][px], s["K"][px], s["G"][py], s["L"][py], s["bx"][px], s["by"][py])
+    r = _solve(Phi, s["n"][px], s["m"][py], s["beta"])
+    np.testing.assert_allclose(r["log_u"], s["r"]["log_u"][px], atol=1e-11)
+    np.testing.assert_allclose(r["log_v"], s["r"]["log_v"][py], atol=1e-11)
+
+
+def test_side_swap(solved):
+    """Exchanging the roles of X and Y (F<->G, K<->L, n<->m) exchanges u and v."""
+    s = solved
+    Phi_t = oracle.phi_dense(s["G"], s["L"], s["F"], s["K"], s["by"], s["bx"])
+    np.testing.assert_allclose(Phi_t, s["Phi"].T, atol=1e-13)
+    r = _solve(Phi_t, s["m"], s["n"], s["beta"])
+    np.testing.assert_allclose(r["log_u"], s["r"]["log_v"], atol=1e-11)
+    np.testing.assert_allclose(r["log_v"], s["r"]["log_u"], atol=1e-11)
+
+
+def test_mass_scaling(solved):
+    """n, m -> c n, c m gives u, v -> sqrt(c) u, sqrt(c) v and mu -> c mu."""
+    s = solved
+    c = 3.7
+    r = _solve(s["Phi"], c * s["n"], c * s["m"], s["beta"])
+    np.testing.assert_allclose(r["log_u"], s["r"]["log_u"] + 0.5 * np.log(c), atol=1e-11)
+    np.testing.assert_allclose(r["log_v"], s["r"]["log_v"] + 0.5 * np.log(c), atol=1e-11)
+
+
+def test_constant_shift_is_not_neutral(solved):
+    """Adding a constant to phi raises every match gain: the total matched mass
+    must grow (the unmatched option is not shifted)."""
+    s = solved
+    r = _solve(s["Phi"] + 1.0, s["n"], s["m"], s["beta"])
+    assert oracle.match_count(s["n"], r["log_u"]) > oracle.match_count(s["n"], s["r"]["log_u"]) + 1e-5
+    assert np.min(s["r"]["log_u"] - r["log_u"]) > 0.1  # every unmatched mass shrinks
+
+
+# ---------------------------------------------------------------------------
+# Mini-batch == batch (Sec. 3.3: the mini-batch update needs no approximation)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("bx_rows,by_rows", [(1, 1), (3, 7), (7, 40), (31, 2)])
+def test_minibatch_iterates_equal_batch(bx_rows, by_rows):
+    rng = np.random.default_rng(13)
+    F, K, G, L, bx, by, n, m = _random_market(rng, 31, 40, d=4)
+    beta = 0.9
+    Phi = oracle.phi_dense(F, K, G, L, bx, by)
+    for sweeps in (1, 3, 10):
+        rb = oracle.ipfp_batch(Phi, n, m, beta, max_sweeps=sweeps)
+        rm = oracle.ipfp_minibatch(F, K, G, L, n, m, beta, sweeps, bx_rows, by_rows, bx, by)
+        np.testing.assert_allclose(rm["log_u"], rb["log_u"], atol=1e-12)
+        np.testing.assert_allclose(rm["log_v"], rb["log_v"], atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Stable factors (Psi, Xi)
+# ---------------------------------------------------------------------------
+
+def test_stable_factors_corrected_reading(solved):
+    """log mu = <psi_x, xi_y>/(2 beta) holds with 2 beta log u, 2 beta log v;
+    the printed beta log u, beta log v is off (the garble the reading fixes)."""
+    s = solved
+    Psi, Xi = oracle.stable_factors(s["F"], s["K"], s["G"], s["L"], s["beta"],
+                                    s["r"]["log_u"], s["r"]["log_v"], s["bx"], s["by"])
+    assert Psi.shape == (30, 2 * 4 + 2) and Xi.shape == (40, 2 * 4 + 2)
+    lm = oracle.log_mu(oracle.log_kernel(s["Phi"], s["beta"]), s["r"]["log_u"], s["r"]["log_v"])
+    np.testing.assert_allclose(Psi @ Xi.T / (2 * s["beta"]), lm, atol=1e-12)
+    printed_psi = Psi.copy(); printed_xi = Xi.copy()
+    printed_psi[:, -2] = s["beta"] * s["r"]["log_u"] + s["bx"]
+    printed_xi[:, -1] = s["beta"] * s["r"]["log_v"] + s["by"]
+    assert np.max(np.abs(printed_psi @ printed_xi.T / (2 * s["beta"]) - lm)) > 0.1
+
+
+# ---------------------------------------------------------------------------
+# Ranked lists, residual, sampled certification
+# ---------------------------------------------------------------------------
+
+def test_topk_against_brute_force():
+    rng = np.random.default_rng(17)
+    logA = np.round(rng.normal(size=(9, 13)), 1)  # rounded: many exact ties
+    lu, lv = np.zeros(9), np.round(rng.normal(size=13), 1) * 0
+    for side in (0, 1):
+        idx, vals = oracle.topk_partners(logA, lu, lv, 5, side)
+        sc = logA if side == 0 else logA.T
+        for i in range(sc.shape[0]):
+            brute = sorted(range(sc.shape[1]), key=lambda j: (-sc[i, j], j))[:5]
+            assert list(idx[i]) == brute
+            np.testing.assert_array_equal(vals[i], sc[i, brute])
+
+
+def test_row_residual_direct():
+    rng = np.random.default_rng(19)
+    F, K, G, L, bx, by, n, m = _random_market(rng, 6, 8)
+    beta = 1.1
+    Phi = oracle.phi_dense(F, K, G, L, bx, by)
+    lu, lv = rng.normal(size=6) - 1, rng.normal(size=8) - 1
+    A = np.exp(Phi / (2 * beta))
+    u, v = np.exp(lu), np.exp(lv)
+    r_direct = u * u + u * (A @ v) - n
+    r_inf, r_l1, r = oracle.row_residual(oracle.log_kernel(Phi, beta), n, lu, lv)
+    np.testing.assert_allclose(r, r_direct, rtol=1e-12)
+    assert r_inf == pytest.approx(np.max(np.abs(r_direct) / n), rel=1e-12)
+    assert r_l1 == pytest.approx(np.sum(np.abs(r_direct)) / np.sum(n), rel=1e-12)
+
+
+def test_sampled_row_update_equals_dense_half_sweep():
+    mk = make_market(50, 333, 8, sigma=0.5, seed=23, bias_x=True, bias_y=True, dtype="bf16")
+    f = mk.f64()
+    Phi = oracle.phi_dense(f["F"], f["K"], f["G"], f["L"], f["bias_x"], f["bias_y"])
+    logA = oracle.log_kernel(Phi, f["sigma"])
+    lv = np.random.default_rng(1).normal(size=333)
+    full = oracle.half_sweep_x(logA, lv, f["n"])
+    rows = np.array([0, 7, 19, 49])
+    _, lu = oracle.sampled_row_update(f["F"], f["K"], f["G"], f["L"], f["sigma"], f["n"], lv, rows,
+                                      f["bias_x"], f["bias_y"], col_chunk=50)
+    np.testing.assert_allclose(lu, full[rows], atol=1e-13)
+    # the Y side through the same function with the sides exchanged
+    lu_all = full
+    fully = oracle.half_sweep_y(logA, lu_all, f["m"])
+    cols = np.array([3, 100, 332])
+    _, lvs = oracle.sampled_row_update(f["G"], f["L"], f["F"], f["K"], f["sigma"], f["m"], lu_all, cols,
+                                       f["bias_y"], f["bias_x"], col_chunk=17)
+    np.testing.assert_allclose(lvs, fully[cols], atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# The pins catch plausible mistakes
+# ---------------------------------------------------------------------------
+
+def _pins_pass():
+    """Run a compact set of the pins above; True if all hold."""
+    try:
+        g = _golden()
+        for c in g["one_by_one"][:3]:
+            test_closed_form_1x1(c)
+        for c in g["symmetric_two_by_two"]:
+            test_closed_form_symmetric_2x2(c)
+        test_fixed_point_maximises_primal_welfare()
+        test_gauss_seidel_order()
+        test_literal_algorithm_1_matches_log_form()
+        test_row_residual_direct()
+        test_newton_on_concave_dual((6, 6))
+    except (AssertionError, ValueError, FloatingPointError):
+        return False
+    return True
+
+
+MISTAKES = {
+    "drop the 1/2 in s = A v / 2": ("LOG_HALF", 0.0),
+    "beta instead of 2 beta": ("log_kernel", lambda Phi, beta: np.asarray(Phi, float) / float(beta)),
+    "wrong sign in the update": ("scaling_update",
+                                 lambda log_s, mass: 0.5 * np.log(mass) + O.asinh_exp(log_s - 0.5 * np.log(mass))),
+    "transposed kernel in the u step": ("half_sweep_x",
+                                        lambda logA, lv, n: O.scaling_update(
+                                            O.LOG_HALF + O._logsumexp(logA.T + lv[None, :], axis=1), n)),
+    "Jacobi order (v from the old u)": None,
+    "residual without the u^2 term": ("row_residual", None),
+}
+
+
+def test_planted_mistakes_are_caught(monkeypatch):
+    assert _pins_pass()
+    for name, patch in MISTAKES.items():
+        with monkeypatch.context() as mpatch:
+            if name.startswith("Jacobi"):
+                orig_batch = O.ipfp_batch
+
+                def jacobi(Phi, n, m, beta, max_sweeps, tol=None, log_u=None, log_v=None):
+                    logA = O.log_kernel(Phi, beta)
+                    lu = np.zeros(logA.shape[0]) if log_u is None else log_u
+                    lv = np.zeros(logA.shape[1]) if log_v is None else log_v
+                    for _ in range(int(max_sweeps)):
+                        if tol is not None and O.row_residual(logA, n, lu, lv)[0] <= tol:
+                            break
+                        lu, lv = O.half_sweep_x(logA, lv, n), O.half_sweep_y(logA, lu, m)
+                    r = orig_batch(Phi, n, m, beta, 0, None, lu, lv)
+                    return r
+                mpatch.setattr(O, "ipfp_batch", jacobi)
+                mpatch.setattr(oracle, "ipfp_batch", jacobi)
+            elif name.startswith("residual"):
+                def bad_res(logA, n, log_u, log_v):
+                    lse = O._logsumexp(logA + log_v[None, :], axis=1)
+                    r = np.exp(log_u + lse) - n
+                    return float(np.max(np.abs(r) / n)), float(np.sum(np.abs(r)) / np.sum(n)), r
+                mpatch.setattr(O, "row_residual", bad_res)
+                mpatch.setattr(oracle, "row_residual", bad_res)
+            else:
+                attr, val = patch
+                mpatch.setattr(O, attr, val)
+                if hasattr(oracle, attr):
+                    mpatch.setattr(oracle, attr, val)
+            assert not _pins_pass(), f"planted mistake not caught: {name}"
+    assert _pins_pass()
