@@ -1,0 +1,160 @@
+/*
+ * tu_ipfp.h -- C ABI of the GB300 IPFP library (libtu_ipfp.so).
+ *
+ * Solves the Choo-Siow transferable-utility matching model of
+ * "Parallel and Mini-Batch Stable Matching for Large-Scale Reciprocal
+ * Recommender Systems" (arXiv 2411.19214) with the IPFP / Sinkhorn sweep.
+ *
+ * Model (Sec. 3.1-3.3). Side X has N users (candidates, index x, capacity n_x),
+ * side Y has M users (employers, index y, capacity m_y). Each user carries two
+ * d-dimensional factor vectors: f_x, k_x (rows of F, K) and g_y, l_y (rows of
+ * G, L). The joint surplus is phi_xy = <f_x, g_y> + <k_x, l_y> + b^X_x + b^Y_y,
+ * where the optional popularity biases b are an extension the paper does not
+ * have (unit coefficient, kept in FP32 outside the tensor-core product).
+ * With A = exp(Phi / (2 sigma)) (sigma is the paper's beta) and the scaling
+ * vectors u_x = sqrt(mu_x0), v_y = sqrt(mu_0y), one sweep is (Eq. iteration):
+ *     u_x <- sqrt(n_x + s_x^2) - s_x,  s_x = 1/2 sum_y A_xy v_y
+ *     v_y <- sqrt(m_y + s_y^2) - s_y,  s_y = 1/2 sum_x A_xy u_x   (new u)
+ * and the equilibrium is mu_xy = A_xy u_x v_y (Eq. stable_condition).
+ * The library keeps log u and log v (FP32) and evaluates the update in the
+ * algebraically identical form log u = 1/2 log n - asinh(s / sqrt(n)).
+ *
+ * Two paths compute the same iteration:
+ *   TU_PATH_FUSED  mini-batch IPFP (Alg. 2 / Eq. iteration_minibatch): Phi is
+ *                  formed tile by tile from BF16 factors on the tensor cores
+ *                  and never stored; requires d <= 64.
+ *   TU_PATH_DENSE  batch IPFP (Alg. 1 / Eq. iteration_matrix): the FP32 kernel
+ *                  A-hat = exp((Phi - b^X - b^Y) / (2 sigma)) is materialised
+ *                  once (N*M*4 bytes) and streamed every half-sweep.
+ *
+ * Conventions shared by every entry point:
+ *   - Return codes only; nothing is thrown across the ABI.
+ *   - Pointers marked "host or device" may point to host memory (pageable or
+ *     pinned) or to device memory of the market's device; the library detects
+ *     which and copies as needed. All device work is ordered on the market's
+ *     stream. Calls that return host values synchronise that stream.
+ *   - After TU_ERR_CUDA the market is poisoned: every later call returns
+ *     TU_ERR_CUDA and only tu_market_destroy is valid.
+ *   - A market is not thread-safe: one host thread at a time per market.
+ */
+#ifndef TU_IPFP_H
+#define TU_IPFP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tu_market* tu_market_t;
+
+typedef enum {
+  TU_OK = 0,
+  TU_ERR_INVALID_ARG = 1,   /* a size, pointer or value is out of range */
+  TU_ERR_OOM = 2,           /* device memory allocation failed */
+  TU_ERR_CUDA = 3,          /* a CUDA call failed; the market is poisoned */
+  TU_ERR_NOT_CONVERGED = 4, /* tu_ipfp_solve hit max_iter; potentials are still valid */
+  TU_ERR_NONFINITE = 5,     /* an input or a computed potential is NaN or infinite */
+  TU_ERR_TIMEOUT = 6,       /* a device-side wait ran out of its time limit */
+  TU_ERR_UNSUPPORTED = 7    /* valid request this build cannot serve (e.g. d > 64 on the fused path) */
+} tu_status;
+
+enum { TU_DTYPE_BF16 = 0, TU_DTYPE_FP32 = 1 };
+enum { TU_PATH_FUSED = 0, TU_PATH_DENSE = 1 };
+
+typedef struct {
+  int64_t N;             /* users on side X, >= 1 */
+  int64_t M;             /* users on side Y, >= 1 */
+  int64_t d;             /* factor dimension D of Sec. 3.3, >= 1 (fused path: <= 64) */
+  int32_t dtype;         /* element type of F, K, G, L: TU_DTYPE_BF16 (uint16 bit patterns) or TU_DTYPE_FP32.
+                            The fused path computes with BF16 (FP32 inputs are rounded to nearest even);
+                            the dense path computes with FP32 (BF16 inputs are widened exactly). */
+  int32_t path;          /* TU_PATH_FUSED or TU_PATH_DENSE */
+  const void* F;         /* N x d row-major, host or device; copied (the market owns its copy) */
+  const void* K;         /* N x d row-major, host or device; copied */
+  const void* G;         /* M x d row-major, host or device; copied */
+  const void* L;         /* M x d row-major, host or device; copied */
+  const float* bias_x;   /* N FP32 popularity biases b^X (host or device), or NULL for none */
+  const float* bias_y;   /* M FP32 popularity biases b^Y (host or device), or NULL for none */
+  const double* n;       /* N capacities n_x > 0, HOST memory */
+  const double* m;       /* M capacities m_y > 0, HOST memory */
+  double sigma;          /* entropy scale beta of Eq. primary optimization, > 0 */
+  int64_t partition;     /* rows per mini-batch of Alg. 2 (0: whole side). Results do not depend on it:
+                            within a half-sweep every u_x depends only on the fixed v. */
+  void* stream;          /* cudaStream_t for all work of this market (NULL: the legacy default stream) */
+} tu_market_desc;
+
+/* Create a market from factor matrices and capacities (Sec. 3.3, Alg. 2 inputs).
+ * Potentials start at u = v = 1 (Alg. 1 / Alg. 2 initialisation).
+ * Validates sizes, pointers, sigma > 0, capacities > 0 and finite, and that the
+ * exponent range fits FP32: max_x |a_x| * max_y |b_y| / (2 sigma) <= 40, where
+ * a_x = (f_x, k_x), b_y = (g_y, l_y) (a Cauchy-Schwarz bound on the bias-free
+ * part of phi / (2 sigma)); otherwise TU_ERR_UNSUPPORTED. Biases have no limit:
+ * they are folded into the potentials in log space. On success *out owns device memory of about
+ * (N + M) * 2 * d * 2 bytes (fused) or N * M * 4 bytes (dense) plus O(N + M). */
+tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out);
+
+/* Replace F, K, G, L (same shapes and dtype as at creation; host or device).
+ * Potentials are kept, so the next solve can be warm-started. Dense markets
+ * rebuild A-hat. */
+tu_status tu_market_update_factors(tu_market_t mkt, const void* F, const void* K, const void* G,
+                                   const void* L);
+
+/* Run nsweeps >= 0 full sweeps of Eq. iteration (u from v, then v from the new u;
+ * Alg. 1 loop body / Alg. 2 loop body). If residual_out != NULL, synchronise and
+ * store the row residual of the resulting potentials:
+ *     max_x |u_x^2 + u_x sum_y A_xy v_y - n_x| / n_x     (row equations of Eq. IPFP),
+ * which costs one extra half-sweep of work. */
+tu_status tu_ipfp_sweep(tu_market_t mkt, int nsweeps, double* residual_out);
+
+typedef struct {
+  int32_t sweeps;        /* sweeps run by this call */
+  int32_t status;        /* the tu_status returned */
+  double residual_inf;   /* max_x |r_x| / n_x of the returned potentials (Eq. IPFP rows) */
+  double residual_l1;    /* sum_x |r_x| / sum_x n_x of the returned potentials */
+  double match_count;    /* sum_xy mu_xy = sum_y m_y - sum_y v_y^2 (FP64 reduction) */
+} tu_solve_info;
+
+/* Sweep until residual_inf <= tol or max_iter sweeps (Alg. 1 with a stopping
+ * rule; the paper runs a fixed count). warm_start = 0 resets to u = v = 1 first;
+ * 1 continues from the current potentials. The residual of each sweep's input
+ * state is reduced in FP64 inside the X half-sweep; the returned state is
+ * certified by one final residual pass. Returns TU_OK, TU_ERR_NOT_CONVERGED
+ * (potentials valid), or an error. info may be NULL. */
+tu_status tu_ipfp_solve(tu_market_t mkt, double tol, int max_iter, int warm_start, tu_solve_info* info);
+
+/* mu_xy = exp(phi_xy / (2 sigma) + log u_x + log v_y) (Eq. stable_condition,
+ * Alg. 1 final line) for x in [x0, x0 + nx), y in [y0, y0 + ny), written FP32
+ * row-major to out (host or device) with leading dimension ld >= ny. */
+tu_status tu_mu_block(tu_market_t mkt, int64_t x0, int64_t nx, int64_t y0, int64_t ny, float* out,
+                      int64_t ld);
+
+/* Ranked recommendation lists (Sec. 4.1 ranks a list per user; Sec. 3.3 scores
+ * by log mu). side 0: for each x in [row0, row0 + nrows), the k partners y with
+ * the largest mu_xy; side 1: for each y, the k partners x. Ties are broken by
+ * the lower partner index. idx (int32) and log_mu (FP32, may be NULL) are
+ * nrows x k row-major, host or device, best first. 1 <= k <= 64 and
+ * k <= partner count. */
+tu_status tu_topk_partners(tu_market_t mkt, int side, int k, int64_t row0, int64_t nrows, int32_t* idx,
+                           float* log_mu);
+
+/* Checkpoint / restore the solver state (the scaling vectors of Alg. 2's
+ * output, Psi and Xi's last columns): log u (N floats) and log v (M floats),
+ * host or device. Either pointer may be NULL to skip that side. */
+tu_status tu_get_potentials(tu_market_t mkt, float* log_u, float* log_v);
+tu_status tu_set_potentials(tu_market_t mkt, const float* log_u, const float* log_v);
+
+/* Free every resource of the market (safe on NULL). */
+void tu_market_destroy(tu_market_t mkt);
+
+/* Static description of a status code. */
+const char* tu_status_string(tu_status s);
+
+/* Detail of the market's last error ("" if none). Valid until the next call on mkt. */
+const char* tu_market_last_error(tu_market_t mkt);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TU_IPFP_H */

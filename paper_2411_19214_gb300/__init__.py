@@ -1,0 +1,328 @@
+"""Python binding of libtu_ipfp.so (C ABI in include/tu_ipfp.h).
+
+The binding only marshals arguments: every step of the IPFP runs in the CUDA
+library. Functions carry the C names (``tu_market_create``, ``tu_ipfp_sweep``,
+``tu_ipfp_solve``, ``tu_mu_block``, ``tu_topk_partners``,
+``tu_get_potentials``, ``tu_set_potentials``, ``tu_market_update_factors``,
+``tu_market_destroy``); :class:`Market` wraps them for convenience. Arrays may
+be torch tensors (CPU or CUDA) or numpy arrays; the library detects host or
+device memory itself. There is no CPU fallback: without the built library
+every call raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+TU_OK, TU_ERR_INVALID_ARG, TU_ERR_OOM, TU_ERR_CUDA, TU_ERR_NOT_CONVERGED, TU_ERR_NONFINITE, TU_ERR_TIMEOUT, \
+    TU_ERR_UNSUPPORTED = range(8)
+TU_DTYPE_BF16, TU_DTYPE_FP32 = 0, 1
+TU_PATH_FUSED, TU_PATH_DENSE = 0, 1
+
+LIB_PATH = _build.LIB
+_lib = None
+
+
+class MarketDesc(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("M", ctypes.c_int64), ("d", ctypes.c_int64),
+                ("dtype", ctypes.c_int32), ("path", ctypes.c_int32),
+                ("F", ctypes.c_void_p), ("K", ctypes.c_void_p), ("G", ctypes.c_void_p), ("L", ctypes.c_void_p),
+                ("bias_x", ctypes.c_void_p), ("bias_y", ctypes.c_void_p),
+                ("n", ctypes.c_void_p), ("m", ctypes.c_void_p),
+                ("sigma", ctypes.c_double), ("partition", ctypes.c_int64), ("stream", ctypes.c_void_p)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int32), ("status", ctypes.c_int32), ("residual_inf", ctypes.c_double),
+                ("residual_l1", ctypes.c_double), ("match_count", ctypes.c_double)]
+
+
+class TuError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        name = status_string(status) if _lib is not None else str(status)
+        super().__init__(f"{where}: {name}" + (f" ({detail})" if detail else ""))
+
+
+def load(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load the shared library (it must have been built: see build.py)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is missing: build it with `python -m paper_2411_19214_gb300.build`")
+    lib = ctypes.CDLL(p)
+    V, I64, I32, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    sigs = {
+        "tu_market_create": (I32, [ctypes.POINTER(MarketDesc), ctypes.POINTER(V)]),
+        "tu_market_update_factors": (I32, [V, V, V, V, V]),
+        "tu_ipfp_sweep": (I32, [V, I32, ctypes.POINTER(D)]),
+        "tu_ipfp_solve": (I32, [V, D, I32, I32, ctypes.POINTER(SolveInfo)]),
+        "tu_mu_block": (I32, [V, I64, I64, I64, I64, V, I64]),
+        "tu_topk_partners": (I32, [V, I32, I32, I64, I64, V, V]),
+        "tu_get_potentials": (I32, [V, V, V]),
+        "tu_set_potentials": (I32, [V, V, V]),
+        "tu_market_destroy": (None, [V]),
+        "tu_status_string": (ctypes.c_char_p, [I32]),
+        "tu_market_last_error": (ctypes.c_char_p, [V]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> list:
+    """Names of the ABI functions the loaded library exports."""
+    lib = load()
+    names = ["tu_market_create", "tu_market_update_factors", "tu_ipfp_sweep", "tu_ipfp_solve", "tu_mu_block",
+             "tu_topk_partners", "tu_get_potentials", "tu_set_potentials", "tu_market_destroy",
+             "tu_status_string", "tu_market_last_error"]
+    return [n for n in names if hasattr(lib, n)]
+
+
+def status_string(status: int) -> str:
+    return load().tu_status_string(int(status)).decode()
+
+
+# ---------------------------------------------------------------------------
+# argument marshalling
+# ---------------------------------------------------------------------------
+
+def _ptr(a) -> Optional[int]:
+    if a is None:
+        return None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if not a.is_contiguous():
+                raise ValueError("tensors passed to the library must be contiguous")
+            return a.data_ptr()
+    except ImportError:  # pragma: no cover
+        pass
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays passed to the library must be C-contiguous")
+        return a.ctypes.data
+    if isinstance(a, int):
+        return a
+    raise TypeError(f"unsupported array type {type(a)!r}")
+
+
+def _dtype_code(a) -> int:
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype == torch.bfloat16:
+                return TU_DTYPE_BF16
+            if a.dtype == torch.float32:
+                return TU_DTYPE_FP32
+            raise TypeError(f"factor dtype {a.dtype} not supported (bfloat16 or float32)")
+    except ImportError:  # pragma: no cover
+        pass
+    if a.dtype == np.uint16:
+        return TU_DTYPE_BF16
+    if a.dtype == np.float32:
+        return TU_DTYPE_FP32
+    raise TypeError(f"factor dtype {a.dtype} not supported (uint16 bf16 bits or float32)")
+
+
+def _shape(a):
+    return tuple(int(s) for s in a.shape)
+
+
+def _check(status: int, where: str, handle=None):
+    if status != TU_OK:
+        detail = ""
+        if handle:
+            raw = load().tu_market_last_error(handle)
+            detail = raw.decode() if raw else ""
+        raise TuError(status, where, detail)
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# the C functions, same names
+# ---------------------------------------------------------------------------
+
+def tu_market_create(F, K, G, L, n, m, sigma: float, *, bias_x=None, bias_y=None, path: str = "fused",
+                     partition: int = 0, stream=None) -> int:
+    """Create a market; returns the opaque handle (int). n, m: host float64."""
+    lib = load()
+    N, d = _shape(F)
+    M, d2 = _shape(G)
+    if _shape(K) != (N, d) or _shape(L) != (M, d2) or d != d2:
+        raise ValueError("F, K must be N x d and G, L must be M x d")
+    dt = _dtype_code(F)
+    if any(_dtype_code(x) != dt for x in (K, G, L)):
+        raise TypeError("F, K, G, L must share one dtype")
+    n = np.ascontiguousarray(n, dtype=np.float64)
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    if n.shape != (N,) or m.shape != (M,):
+        raise ValueError("n must have N entries and m must have M entries")
+    desc = MarketDesc(N=N, M=M, d=d, dtype=dt, path=TU_PATH_FUSED if path == "fused" else TU_PATH_DENSE,
+                      F=_ptr(F), K=_ptr(K), G=_ptr(G), L=_ptr(L), bias_x=_ptr(bias_x), bias_y=_ptr(bias_y),
+                      n=_ptr(n), m=_ptr(m), sigma=float(sigma), partition=int(partition),
+                      stream=_stream_handle(stream))
+    if path not in ("fused", "dense"):
+        raise ValueError("path must be 'fused' or 'dense'")
+    h = ctypes.c_void_p()
+    _check(lib.tu_market_create(ctypes.byref(desc), ctypes.byref(h)), "tu_market_create")
+    return h.value
+
+
+def tu_market_update_factors(h: int, F, K, G, L) -> None:
+    _check(load().tu_market_update_factors(h, _ptr(F), _ptr(K), _ptr(G), _ptr(L)), "tu_market_update_factors", h)
+
+
+def tu_ipfp_sweep(h: int, nsweeps: int, residual: bool = False) -> Optional[float]:
+    r = ctypes.c_double(float("nan"))
+    _check(load().tu_ipfp_sweep(h, int(nsweeps), ctypes.byref(r) if residual else None), "tu_ipfp_sweep", h)
+    return r.value if residual else None
+
+
+def tu_ipfp_solve(h: int, tol: float, max_iter: int, warm_start: bool = False) -> dict:
+    info = SolveInfo()
+    st = load().tu_ipfp_solve(h, float(tol), int(max_iter), int(bool(warm_start)), ctypes.byref(info))
+    if st not in (TU_OK, TU_ERR_NOT_CONVERGED):
+        _check(st, "tu_ipfp_solve", h)
+    return dict(status=st, converged=st == TU_OK, sweeps=info.sweeps, residual_inf=info.residual_inf,
+                residual_l1=info.residual_l1, match_count=info.match_count)
+
+
+def tu_mu_block(h: int, x0: int, nx: int, y0: int, ny: int, out, ld: Optional[int] = None) -> None:
+    ld = ny if ld is None else ld
+    _check(load().tu_mu_block(h, int(x0), int(nx), int(y0), int(ny), _ptr(out), int(ld)), "tu_mu_block", h)
+
+
+def tu_topk_partners(h: int, side: int, k: int, row0: int, nrows: int, idx, log_mu=None) -> None:
+    _check(load().tu_topk_partners(h, int(side), int(k), int(row0), int(nrows), _ptr(idx), _ptr(log_mu)),
+           "tu_topk_partners", h)
+
+
+def tu_get_potentials(h: int, log_u=None, log_v=None) -> None:
+    _check(load().tu_get_potentials(h, _ptr(log_u), _ptr(log_v)), "tu_get_potentials", h)
+
+
+def tu_set_potentials(h: int, log_u=None, log_v=None) -> None:
+    _check(load().tu_set_potentials(h, _ptr(log_u), _ptr(log_v)), "tu_set_potentials", h)
+
+
+def tu_market_destroy(h: int) -> None:
+    if h:
+        load().tu_market_destroy(h)
+
+
+# ---------------------------------------------------------------------------
+# convenience object
+# ---------------------------------------------------------------------------
+
+class Market:
+    """Owning wrapper of a market handle (torch CUDA tensors for outputs)."""
+
+    def __init__(self, F, K, G, L, n, m, sigma, *, bias_x=None, bias_y=None, path="fused", partition=0,
+                 stream=None, device="cuda"):
+        self.N, self.d = _shape(F)
+        self.M = _shape(G)[0]
+        self.device = device
+        self.stream = stream
+        self.handle = tu_market_create(F, K, G, L, n, m, sigma, bias_x=bias_x, bias_y=bias_y, path=path,
+                                       partition=partition, stream=stream)
+
+    def sweep(self, nsweeps: int, residual: bool = False):
+        return tu_ipfp_sweep(self.handle, nsweeps, residual)
+
+    def solve(self, tol: float, max_iter: int, warm_start: bool = False) -> dict:
+        return tu_ipfp_solve(self.handle, tol, max_iter, warm_start)
+
+    def potentials(self):
+        import torch
+        lu = torch.empty(self.N, dtype=torch.float32, device=self.device)
+        lv = torch.empty(self.M, dtype=torch.float32, device=self.device)
+        tu_get_potentials(self.handle, lu, lv)
+        self._sync()
+        return lu, lv
+
+    def set_potentials(self, log_u=None, log_v=None):
+        tu_set_potentials(self.handle, log_u, log_v)
+
+    def update_factors(self, F, K, G, L):
+        tu_market_update_factors(self.handle, F, K, G, L)
+
+    def mu_block(self, x0=0, nx=None, y0=0, ny=None):
+        import torch
+        nx = self.N - x0 if nx is None else nx
+        ny = self.M - y0 if ny is None else ny
+        out = torch.empty((nx, ny), dtype=torch.float32, device=self.device)
+        tu_mu_block(self.handle, x0, nx, y0, ny, out, ny)
+        self._sync()
+        return out
+
+    def topk(self, side: int, k: int, row0: int = 0, nrows: Optional[int] = None):
+        import torch
+        rows = self.N if side == 0 else self.M
+        nrows = rows - row0 if nrows is None else nrows
+        idx = torch.empty((nrows, k), dtype=torch.int32, device=self.device)
+        lm = torch.empty((nrows, k), dtype=torch.float32, device=self.device)
+        tu_topk_partners(self.handle, side, k, row0, nrows, idx, lm)
+        self._sync()
+        return idx, lm
+
+    def _sync(self):
+        import torch
+        if self.stream is not None:
+            self.stream.synchronize()
+        else:
+            torch.cuda.synchronize()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            tu_market_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def from_synth(mk, path: str = "fused", device: str = "cuda", stream=None, partition: int = 0) -> Market:
+    """Create a :class:`Market` on the device from a ``synth.Market``."""
+    import torch
+
+    def dev(a):
+        if a is None:
+            return None
+        if mk.dtype == "bf16" and a.ndim == 2:
+            bits = (np.ascontiguousarray(a, dtype=np.float32).view(np.uint32) >> 16).astype(np.uint16)
+            return torch.from_numpy(bits.view(np.int16)).view(torch.bfloat16).to(device)
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(device)
+
+    F, K, G, L = (dev(x) for x in (mk.F, mk.K, mk.G, mk.L))
+    bx, by = dev(mk.bias_x), dev(mk.bias_y)
+    torch.cuda.synchronize()
+    return Market(F, K, G, L, mk.n, mk.m, mk.sigma, bias_x=bx, bias_y=by, path=path, partition=partition,
+                  stream=stream, device=device)

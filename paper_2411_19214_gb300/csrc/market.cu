@@ -1,0 +1,563 @@
+// market.cu -- the C ABI (include/tu_ipfp.h): market lifetime, argument
+// checking, host/device staging, the sweep loop with CUDA-graph replay, and the
+// convergence test of tu_ipfp_solve.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "tu_internal.cuh"
+
+using namespace tu;
+
+namespace {
+
+const char* kStatusNames[] = {"TU_OK",          "TU_ERR_INVALID_ARG", "TU_ERR_OOM",     "TU_ERR_CUDA",
+                              "TU_ERR_NOT_CONVERGED", "TU_ERR_NONFINITE", "TU_ERR_TIMEOUT", "TU_ERR_UNSUPPORTED"};
+
+int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+tu_status fail(tu_market* m, tu_status s, const std::string& msg) {
+  if (m != nullptr) m->last_error = msg;
+  return s;
+}
+
+tu_status fail_cuda(tu_market* m, cudaError_t e, const char* what) {
+  cudaGetLastError();  // clear a sticky-free error so later calls can report their own
+  if (m != nullptr) {
+    m->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e != cudaErrorMemoryAllocation) m->poisoned = true;
+  }
+  return e == cudaErrorMemoryAllocation ? TU_ERR_OOM : TU_ERR_CUDA;
+}
+
+#define TU_CK(m, call)                                      \
+  do {                                                      \
+    cudaError_t _e = (call);                                \
+    if (_e != cudaSuccess) return fail_cuda((m), _e, #call); \
+  } while (0)
+
+#define TU_TRY(expr)                 \
+  do {                               \
+    tu_status _s = (expr);           \
+    if (_s != TU_OK) return _s;      \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+tu_status dev_alloc(tu_market* m, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return TU_OK;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail_cuda(m, e, "cudaMalloc");
+  }
+  return TU_OK;
+}
+
+tu_status ensure_staging(tu_market* m, size_t bytes) {
+  if (m->staging_bytes >= bytes) return TU_OK;
+  if (m->staging != nullptr) {
+    TU_CK(m, cudaStreamSynchronize(m->stream));
+    cudaFree(m->staging);
+    m->staging = nullptr;
+    m->staging_bytes = 0;
+  }
+  TU_CK(m, cudaMalloc(&m->staging, bytes));
+  m->staging_bytes = bytes;
+  return TU_OK;
+}
+
+// Device view of a caller pointer: the pointer itself if it is device memory,
+// else a copy in the staging buffer at byte offset `off`.
+tu_status device_view(tu_market* m, const void* src, size_t bytes, size_t off, const void** out) {
+  if (is_device_ptr(src)) {
+    *out = src;
+    return TU_OK;
+  }
+  void* dst = static_cast<char*>(m->staging) + off;
+  TU_CK(m, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, m->stream));
+  *out = dst;
+  return TU_OK;
+}
+
+tu_status side_alloc(tu_market* m, Side& s, int64_t rows, bool has_bias) {
+  s.rows = rows;
+  s.rows_pad = round_up(rows, kRowPad);
+  TU_TRY(dev_alloc(m, &s.log_u, s.rows_pad));
+  TU_TRY(dev_alloc(m, &s.ell, s.rows_pad));
+  TU_TRY(dev_alloc(m, &s.pvec, s.rows_pad));
+  TU_TRY(dev_alloc(m, &s.mass, s.rows_pad));
+  TU_TRY(dev_alloc(m, &s.lmax, 1));
+  if (has_bias) TU_TRY(dev_alloc(m, &s.b2s, s.rows_pad));
+  if (m->path == TU_PATH_FUSED) {
+    TU_TRY(dev_alloc(m, &s.fac16, (size_t)rows * m->kp));
+  } else {
+    TU_TRY(dev_alloc(m, &s.fac32, (size_t)rows * m->kp));
+  }
+  return TU_OK;
+}
+
+void side_free(Side& s) {
+  cudaFree(s.log_u);
+  cudaFree(s.ell);
+  cudaFree(s.pvec);
+  cudaFree(s.mass);
+  cudaFree(s.lmax);
+  cudaFree(s.b2s);
+  cudaFree(s.fac16);
+  cudaFree(s.fac32);
+  s = Side();
+}
+
+tu_status upload_masses(tu_market* m, Side& s, const double* host) {
+  double sum = 0.0;
+  for (int64_t i = 0; i < s.rows; ++i) {
+    const double v = host[i];
+    if (!(v > 0.0) || !std::isfinite(v)) return fail(m, TU_ERR_INVALID_ARG, "capacities must be finite and > 0");
+    sum += v;
+  }
+  s.sum_mass = sum;
+  TU_CK(m, cudaMemcpyAsync(s.mass, host, (size_t)s.rows * sizeof(double), cudaMemcpyHostToDevice, m->stream));
+  // padding capacities are 1 so that padded rows never produce log(0)
+  if (s.rows_pad > s.rows) {
+    const size_t npad = (size_t)(s.rows_pad - s.rows);
+    double* ones = new (std::nothrow) double[npad];
+    if (ones == nullptr) return fail(m, TU_ERR_OOM, "host allocation");
+    for (size_t i = 0; i < npad; ++i) ones[i] = 1.0;
+    cudaError_t e = cudaMemcpy(s.mass + s.rows, ones, npad * sizeof(double), cudaMemcpyHostToDevice);
+    delete[] ones;
+    if (e != cudaSuccess) return fail_cuda(m, e, "cudaMemcpy(mass padding)");
+  }
+  return TU_OK;
+}
+
+// Pack both factor pairs (and rebuild the dense kernel) from caller pointers.
+tu_status load_factors(tu_market* m, const void* F, const void* K, const void* G, const void* L) {
+  const size_t esz = m->dtype == TU_DTYPE_BF16 ? 2 : 4;
+  const size_t bx = (size_t)m->N * m->d * esz, by = (size_t)m->M * m->d * esz;
+  TU_TRY(ensure_staging(m, 2 * (bx > by ? bx : by)));
+  const void *a = nullptr, *b = nullptr;
+  TU_TRY(device_view(m, F, bx, 0, &a));
+  TU_TRY(device_view(m, K, bx, bx, &b));
+  TU_CK(m, launch_pack_factors(m, m->X, a, b, m->dtype));
+  TU_CK(m, cudaStreamSynchronize(m->stream));  // the staging buffer is reused for the other side
+  TU_TRY(device_view(m, G, by, 0, &a));
+  TU_TRY(device_view(m, L, by, by, &b));
+  TU_CK(m, launch_pack_factors(m, m->Y, a, b, m->dtype));
+  // exponent-range check (Cauchy-Schwarz bound of |phi_hat| / (2 sigma))
+  float* norms = nullptr;
+  TU_TRY(dev_alloc(m, &norms, 2));
+  float hn[2] = {0.f, 0.f};
+  cudaError_t e = launch_row_norms(m, m->X, norms);
+  if (e == cudaSuccess) e = launch_row_norms(m, m->Y, norms + 1);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hn, norms, sizeof(hn), cudaMemcpyDeviceToHost, m->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+  cudaFree(norms);
+  if (e != cudaSuccess) return fail_cuda(m, e, "factor norms");
+  if (!std::isfinite(hn[0]) || !std::isfinite(hn[1]))
+    return fail(m, TU_ERR_NONFINITE, "factor matrices contain NaN or Inf");
+  const double bound = (double)hn[0] * (double)hn[1] / (2.0 * m->sigma);
+  if (bound > 40.0) {
+    char buf[160];
+    snprintf(buf, sizeof(buf), "max|a_x| * max|b_y| / (2 sigma) = %.3g exceeds 40 (FP32 exponent range)", bound);
+    return fail(m, TU_ERR_UNSUPPORTED, buf);
+  }
+  if (m->path == TU_PATH_DENSE) TU_CK(m, launch_dense_build(m));
+  TU_CK(m, cudaStreamSynchronize(m->stream));
+  if (m->graph != nullptr) {
+    cudaGraphExecDestroy(m->graph);
+    m->graph = nullptr;
+    m->graph_sweeps = 0;
+  }
+  return TU_OK;
+}
+
+tu_status check_device_error(tu_market* m) {
+  if (*m->err_host == kErrTimeout) return fail(m, TU_ERR_TIMEOUT, "a device-side wait ran out of its time limit");
+  if (*m->err_host != kErrNone) return fail(m, TU_ERR_CUDA, "device error word set");
+  return TU_OK;
+}
+
+// One half-sweep: prepare the partner potentials, run the pass, reduce partials.
+cudaError_t enqueue_half(tu_market* m, int side, int residual, int update) {
+  Side& partner = side == 0 ? m->Y : m->X;
+  cudaError_t e = launch_prep(m, partner, m->path == TU_PATH_FUSED ? 1 : 0);
+  if (e != cudaSuccess) return e;
+  int nparts = 0;
+  if (m->path == TU_PATH_FUSED) {
+    e = launch_fused_halfsweep(m, side, residual, update, &nparts);
+  } else if (side == 0) {
+    e = launch_dense_rowpass(m, residual, update, &nparts);
+  } else {
+    e = launch_dense_colpass(m, update, &nparts);
+  }
+  if (e != cudaSuccess) return e;
+  return launch_finalize(m, nparts, side == 0 ? 1 : 0, residual);
+}
+
+// One sweep of Eq. iteration: u from v (with the residual of the entering
+// state), then v from the new u.
+cudaError_t enqueue_sweep(tu_market* m) {
+  cudaError_t e = enqueue_half(m, 0, 1, 1);
+  if (e != cudaSuccess) return e;
+  return enqueue_half(m, 1, 0, 1);
+}
+
+bool stream_capturable(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread; }
+
+// Enqueue k sweeps, replaying a captured graph of k sweeps when possible.
+tu_status enqueue_sweeps(tu_market* m, int k) {
+  if (k <= 0) return TU_OK;
+  if (stream_capturable(m->stream) && k > 1) {
+    if (m->graph == nullptr || m->graph_sweeps != k) {
+      if (m->graph != nullptr) {
+        cudaGraphExecDestroy(m->graph);
+        m->graph = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      TU_CK(m, cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = cudaSuccess;
+      for (int i = 0; i < k && e == cudaSuccess; ++i) e = enqueue_sweep(m);
+      cudaError_t e2 = cudaStreamEndCapture(m->stream, &g);
+      if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail_cuda(m, e, "capture of the sweep graph");
+      }
+      if (e2 != cudaSuccess) return fail_cuda(m, e2, "cudaStreamEndCapture");
+      cudaError_t e3 = cudaGraphInstantiate(&m->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e3 != cudaSuccess) return fail_cuda(m, e3, "cudaGraphInstantiate");
+      m->graph_sweeps = k;
+    }
+    TU_CK(m, cudaGraphLaunch(m->graph, m->stream));
+    return TU_OK;
+  }
+  for (int i = 0; i < k; ++i) TU_CK(m, enqueue_sweep(m));
+  return TU_OK;
+}
+
+tu_status read_results(tu_market* m) {
+  TU_CK(m, cudaMemcpyAsync(m->results_host, m->results, kResSlots * sizeof(double), cudaMemcpyDeviceToHost,
+                           m->stream));
+  TU_CK(m, cudaMemcpyAsync(m->err_host, m->err_dev, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+  TU_CK(m, cudaStreamSynchronize(m->stream));
+  TU_TRY(check_device_error(m));
+  if (m->results_host[kResNonfin] > 0.0) return fail(m, TU_ERR_NONFINITE, "a computed potential is not finite");
+  return TU_OK;
+}
+
+tu_status clear_results(tu_market* m) {
+  TU_CK(m, cudaMemsetAsync(m->results, 0, kResSlots * sizeof(double), m->stream));
+  TU_CK(m, cudaMemsetAsync(m->err_dev, 0, sizeof(int), m->stream));
+  return TU_OK;
+}
+
+// Residual of the current potentials (one X pass without update).
+tu_status certify(tu_market* m, double* res_inf, double* res_l1) {
+  TU_CK(m, enqueue_half(m, 0, 1, 0));
+  TU_TRY(read_results(m));
+  if (res_inf) *res_inf = m->results_host[kResXInf];
+  if (res_l1) *res_l1 = m->results_host[kResXL1] / m->X.sum_mass;
+  return TU_OK;
+}
+
+tu_status check_live(tu_market* m) {
+  if (m == nullptr) return TU_ERR_INVALID_ARG;
+  if (m->poisoned) return TU_ERR_CUDA;
+  m->last_error.clear();
+  cudaError_t e = cudaSetDevice(m->device);
+  if (e != cudaSuccess) return fail_cuda(m, e, "cudaSetDevice");
+  return TU_OK;
+}
+
+// Device destination for an output of `bytes`; host destinations go through staging.
+tu_status output_view(tu_market* m, void* dst, size_t bytes, size_t off, void** out, bool* is_host) {
+  if (is_device_ptr(dst)) {
+    *out = dst;
+    *is_host = false;
+    return TU_OK;
+  }
+  TU_TRY(ensure_staging(m, off + bytes));
+  *out = static_cast<char*>(m->staging) + off;
+  *is_host = true;
+  return TU_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tu_status_string(tu_status s) {
+  if ((int)s < 0 || (int)s > 7) return "TU_ERR_UNKNOWN";
+  return kStatusNames[(int)s];
+}
+
+const char* tu_market_last_error(tu_market_t m) { return m ? m->last_error.c_str() : ""; }
+
+void tu_market_destroy(tu_market_t m) {
+  if (m == nullptr) return;
+  cudaSetDevice(m->device);
+  if (m->stream) cudaStreamSynchronize(m->stream);
+  if (m->graph) cudaGraphExecDestroy(m->graph);
+  side_free(m->X);
+  side_free(m->Y);
+  cudaFree(m->Ahat);
+  cudaFree(m->partials);
+  cudaFree(m->fpartials);
+  cudaFree(m->colpart);
+  cudaFree(m->results);
+  cudaFree(m->err_dev);
+  cudaFree(m->staging);
+  cudaFreeHost(m->results_host);
+  cudaFreeHost(m->err_host);
+  delete m;
+}
+
+tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
+  if (out == nullptr || desc == nullptr) return TU_ERR_INVALID_ARG;
+  *out = nullptr;
+  const tu_market_desc& D = *desc;
+  if (D.N < 1 || D.M < 1 || D.d < 1 || D.N > (int64_t)1 << 31 || D.M > (int64_t)1 << 31 || D.d > 4096)
+    return TU_ERR_INVALID_ARG;
+  if (D.dtype != TU_DTYPE_BF16 && D.dtype != TU_DTYPE_FP32) return TU_ERR_INVALID_ARG;
+  if (D.path != TU_PATH_FUSED && D.path != TU_PATH_DENSE) return TU_ERR_INVALID_ARG;
+  if (!D.F || !D.K || !D.G || !D.L || !D.n || !D.m) return TU_ERR_INVALID_ARG;
+  if (!(D.sigma > 0.0) || !std::isfinite(D.sigma)) return TU_ERR_INVALID_ARG;
+  if (D.partition < 0) return TU_ERR_INVALID_ARG;
+  if (D.path == TU_PATH_FUSED && 2 * D.d > 2 * kKBlock) return TU_ERR_UNSUPPORTED;
+  if (D.path == TU_PATH_DENSE && (double)D.N * (double)round_up(D.M, 4) * 4.0 > 200e9) return TU_ERR_UNSUPPORTED;
+
+  tu_market* m = new (std::nothrow) tu_market();
+  if (m == nullptr) return TU_ERR_OOM;
+  m->N = D.N;
+  m->M = D.M;
+  m->d = D.d;
+  m->kp = round_up(2 * D.d, kKBlock);
+  m->dtype = D.dtype;
+  m->path = D.path;
+  m->sigma = D.sigma;
+  m->partition = D.partition;
+  m->stream = static_cast<cudaStream_t>(D.stream);
+  tu_status st = TU_OK;
+  auto bail = [&](tu_status s) {
+    tu_market_destroy(m);
+    return s;
+  };
+  if (cudaGetDevice(&m->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&m->num_sms, cudaDevAttrMultiProcessorCount, m->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete m;
+    return TU_ERR_CUDA;
+  }
+  if (D.path == TU_PATH_FUSED) {
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, m->device);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, m->device);
+    if (major != 10) {
+      delete m;
+      return TU_ERR_UNSUPPORTED;
+    }
+  }
+  if ((st = side_alloc(m, m->X, D.N, D.bias_x != nullptr)) != TU_OK) return bail(st);
+  if ((st = side_alloc(m, m->Y, D.M, D.bias_y != nullptr)) != TU_OK) return bail(st);
+  if ((st = dev_alloc(m, &m->partials, (size_t)kMaxPartials * 4)) != TU_OK) return bail(st);
+  if ((st = dev_alloc(m, &m->fpartials, (size_t)kMaxPartials)) != TU_OK) return bail(st);
+  if ((st = dev_alloc(m, &m->results, (size_t)kResSlots)) != TU_OK) return bail(st);
+  if ((st = dev_alloc(m, &m->err_dev, 1)) != TU_OK) return bail(st);
+  if (cudaMallocHost(&m->results_host, kResSlots * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&m->err_host, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return bail(TU_ERR_OOM);
+  }
+  *m->err_host = 0;
+  if (D.path == TU_PATH_DENSE) {
+    m->ldA = round_up(D.M, 4);
+    if ((st = dev_alloc(m, &m->Ahat, (size_t)m->N * m->ldA)) != TU_OK) return bail(st);
+    const int64_t colblocks = (m->ldA / 4 + 255) / 256;
+    int64_t chunks = (4 * (int64_t)m->num_sms + colblocks - 1) / colblocks;
+    if (chunks > (m->N + 15) / 16) chunks = (m->N + 15) / 16;
+    if (chunks < 1) chunks = 1;
+    if (chunks > 1024) chunks = 1024;
+    m->col_chunks = (int)chunks;
+    m->colpart_elems = chunks * m->ldA;
+    if ((st = dev_alloc(m, &m->colpart, (size_t)m->colpart_elems)) != TU_OK) return bail(st);
+  }
+  if ((st = upload_masses(m, m->X, D.n)) != TU_OK) return bail(st);
+  if ((st = upload_masses(m, m->Y, D.m)) != TU_OK) return bail(st);
+  // biases -> b / (2 sigma); potentials start at u = v = 1
+  {
+    const size_t bbytes = (size_t)(D.N > D.M ? D.N : D.M) * sizeof(float);
+    if ((st = ensure_staging(m, bbytes)) != TU_OK) return bail(st);
+    const void* bdev = nullptr;
+    if (D.bias_x && (st = device_view(m, D.bias_x, (size_t)D.N * 4, 0, &bdev)) != TU_OK) return bail(st);
+    if (launch_init_side(m, m->X, static_cast<const float*>(bdev), D.bias_x != nullptr) != cudaSuccess)
+      return bail(fail_cuda(m, cudaGetLastError(), "init side X"));
+    if (cudaStreamSynchronize(m->stream) != cudaSuccess) return bail(TU_ERR_CUDA);
+    bdev = nullptr;
+    if (D.bias_y && (st = device_view(m, D.bias_y, (size_t)D.M * 4, 0, &bdev)) != TU_OK) return bail(st);
+    if (launch_init_side(m, m->Y, static_cast<const float*>(bdev), D.bias_y != nullptr) != cudaSuccess)
+      return bail(fail_cuda(m, cudaGetLastError(), "init side Y"));
+    if (cudaStreamSynchronize(m->stream) != cudaSuccess) return bail(TU_ERR_CUDA);
+  }
+  if ((st = load_factors(m, D.F, D.K, D.G, D.L)) != TU_OK) {
+    // keep the message for the caller by returning it through a status only
+    return bail(st);
+  }
+  if (D.path == TU_PATH_FUSED) {
+    cudaError_t e = fused_prepare(m);
+    if (e != cudaSuccess) return bail(fail_cuda(m, e, "fused_prepare"));
+  }
+  if (clear_results(m) != TU_OK || cudaStreamSynchronize(m->stream) != cudaSuccess) return bail(TU_ERR_CUDA);
+  *out = m;
+  return TU_OK;
+}
+
+tu_status tu_market_update_factors(tu_market_t m, const void* F, const void* K, const void* G, const void* L) {
+  TU_TRY(check_live(m));
+  if (!F || !K || !G || !L) return fail(m, TU_ERR_INVALID_ARG, "null factor pointer");
+  return load_factors(m, F, K, G, L);
+}
+
+tu_status tu_ipfp_sweep(tu_market_t m, int nsweeps, double* residual_out) {
+  TU_TRY(check_live(m));
+  if (nsweeps < 0) return fail(m, TU_ERR_INVALID_ARG, "nsweeps < 0");
+  TU_TRY(clear_results(m));
+  TU_TRY(enqueue_sweeps(m, nsweeps));
+  if (residual_out != nullptr) {
+    TU_TRY(certify(m, residual_out, nullptr));
+  }
+  return TU_OK;
+}
+
+tu_status tu_ipfp_solve(tu_market_t m, double tol, int max_iter, int warm_start, tu_solve_info* info) {
+  TU_TRY(check_live(m));
+  if (!(tol >= 0.0) || max_iter < 0) return fail(m, TU_ERR_INVALID_ARG, "tol < 0 or max_iter < 0");
+  if (!warm_start) {
+    TU_CK(m, launch_reset_potentials(m, m->X));
+    TU_CK(m, launch_reset_potentials(m, m->Y));
+  }
+  TU_TRY(clear_results(m));
+  // sweeps between host checks: about 2e9 pair evaluations per check, 1..64
+  const double pairs = (double)m->N * (double)m->M;
+  int block = (int)std::ceil(2e9 / pairs);
+  if (block < 1) block = 1;
+  if (block > 64) block = 64;
+  int done = 0;
+  double res_inf = INFINITY, res_l1 = INFINITY;
+  tu_status status = TU_ERR_NOT_CONVERGED;
+  while (true) {
+    TU_TRY(certify(m, &res_inf, &res_l1));
+    if (res_inf <= tol) {
+      status = TU_OK;
+      break;
+    }
+    if (done >= max_iter) break;
+    // sweep until the residual folded into the X half-sweeps (state entering
+    // the last sweep of a block) reaches tol, then certify the returned state
+    while (done < max_iter) {
+      const int k = (max_iter - done) < block ? (max_iter - done) : block;
+      TU_TRY(enqueue_sweeps(m, k));
+      TU_TRY(read_results(m));
+      done += k;
+      if (m->results_host[kResXInf] <= tol) break;
+    }
+  }
+  // match count from the column equations (they hold after every v update):
+  // sum_xy mu_xy = sum m - sum v^2
+  TU_TRY(clear_results(m));
+  TU_CK(m, launch_sum_sq(m, m->Y, 0));
+  TU_TRY(read_results(m));
+  const double match = m->Y.sum_mass - m->results_host[kResYSq];
+  if (info != nullptr) {
+    info->sweeps = done;
+    info->status = status;
+    info->residual_inf = res_inf;
+    info->residual_l1 = res_l1;
+    info->match_count = match;
+  }
+  if (status != TU_OK) m->last_error = "max_iter reached before the residual met tol";
+  return status;
+}
+
+tu_status tu_mu_block(tu_market_t m, int64_t x0, int64_t nx, int64_t y0, int64_t ny, float* out, int64_t ld) {
+  TU_TRY(check_live(m));
+  if (out == nullptr || x0 < 0 || y0 < 0 || nx < 0 || ny < 0 || x0 + nx > m->N || y0 + ny > m->M || ld < ny)
+    return fail(m, TU_ERR_INVALID_ARG, "mu block out of range");
+  if (nx == 0 || ny == 0) return TU_OK;
+  const size_t bytes = (size_t)((nx - 1) * ld + ny) * sizeof(float);
+  void* dst;
+  bool host;
+  TU_TRY(output_view(m, out, bytes, 0, &dst, &host));
+  TU_CK(m, launch_mu_block(m, x0, nx, y0, ny, static_cast<float*>(dst), ld));
+  if (host) {
+    TU_CK(m, cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, m->stream));
+    TU_CK(m, cudaStreamSynchronize(m->stream));
+  }
+  return TU_OK;
+}
+
+tu_status tu_topk_partners(tu_market_t m, int side, int k, int64_t row0, int64_t nrows, int32_t* idx,
+                           float* log_mu) {
+  TU_TRY(check_live(m));
+  const int64_t rows = side == 0 ? m->N : m->M;
+  const int64_t partners = side == 0 ? m->M : m->N;
+  if ((side != 0 && side != 1) || idx == nullptr || k < 1 || k > 64 || k > partners || row0 < 0 || nrows < 0 ||
+      row0 + nrows > rows)
+    return fail(m, TU_ERR_INVALID_ARG, "topk arguments out of range");
+  if (nrows == 0) return TU_OK;
+  const size_t ib = (size_t)nrows * k * sizeof(int32_t), vb = (size_t)nrows * k * sizeof(float);
+  void *di, *dv = nullptr;
+  bool hi, hv = false;
+  TU_TRY(output_view(m, idx, ib, 0, &di, &hi));
+  if (log_mu != nullptr) TU_TRY(output_view(m, log_mu, vb, round_up((int64_t)ib, 256), &dv, &hv));
+  TU_CK(m, launch_topk(m, side, k, row0, nrows, static_cast<int32_t*>(di), static_cast<float*>(dv)));
+  if (hi) TU_CK(m, cudaMemcpyAsync(idx, di, ib, cudaMemcpyDeviceToHost, m->stream));
+  if (hv) TU_CK(m, cudaMemcpyAsync(log_mu, dv, vb, cudaMemcpyDeviceToHost, m->stream));
+  if (hi || hv) TU_CK(m, cudaStreamSynchronize(m->stream));
+  return TU_OK;
+}
+
+tu_status tu_get_potentials(tu_market_t m, float* log_u, float* log_v) {
+  TU_TRY(check_live(m));
+  Side* sides[2] = {&m->X, &m->Y};
+  float* outs[2] = {log_u, log_v};
+  bool sync = false;
+  for (int i = 0; i < 2; ++i) {
+    if (outs[i] == nullptr) continue;
+    const size_t bytes = (size_t)sides[i]->rows * sizeof(float);
+    const bool dev = is_device_ptr(outs[i]);
+    TU_CK(m, cudaMemcpyAsync(outs[i], sides[i]->log_u, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             m->stream));
+    sync = sync || !dev;
+  }
+  if (sync) TU_CK(m, cudaStreamSynchronize(m->stream));
+  return TU_OK;
+}
+
+tu_status tu_set_potentials(tu_market_t m, const float* log_u, const float* log_v) {
+  TU_TRY(check_live(m));
+  Side* sides[2] = {&m->X, &m->Y};
+  const float* ins[2] = {log_u, log_v};
+  TU_TRY(ensure_staging(m, (size_t)(m->N > m->M ? m->N : m->M) * sizeof(float)));
+  for (int i = 0; i < 2; ++i) {
+    if (ins[i] == nullptr) continue;
+    const void* src = nullptr;
+    TU_TRY(device_view(m, ins[i], (size_t)sides[i]->rows * sizeof(float), 0, &src));
+    TU_CK(m, launch_set_potentials(m, *sides[i], static_cast<const float*>(src)));
+    TU_CK(m, cudaStreamSynchronize(m->stream));
+  }
+  return TU_OK;
+}
+
+}  // extern "C"

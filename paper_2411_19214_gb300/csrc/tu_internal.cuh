@@ -1,0 +1,335 @@
+// tu_internal.cuh -- internal declarations shared by the translation units of
+// libtu_ipfp.so: the market object, the per-row scaling update, and the inline
+// PTX wrappers (mbarrier, TMA, tcgen05) used by the sm_103a kernels.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/tu_ipfp.h"
+
+// ---------------------------------------------------------------------------
+// Sizes shared by host and device code
+// ---------------------------------------------------------------------------
+namespace tu {
+
+constexpr int kFusedOwnRows = 256;      // own-side rows per CTA tile (two 128-row MMAs)
+constexpr int kFusedPartnerRows = 128;  // partner rows per pipeline stage (MMA N)
+constexpr int kKBlock = 64;             // bf16 elements per 128-byte swizzle row
+constexpr int kRowPad = 256;            // every per-side vector is padded to this multiple
+constexpr int kMaxPartials = 4096;      // per-CTA FP64 partials per half-sweep
+
+// results[] slots (FP64, device), written by the finalize kernels
+enum : int {
+  kResXInf = 0,   // max_x |r_x| / n_x of the state entering the X half-sweep
+  kResXL1 = 1,    // sum_x |r_x|
+  kResXSq = 2,    // sum_x u_x^2 after the X half-sweep
+  kResYSq = 3,    // sum_y v_y^2 after the Y half-sweep
+  kResNonfin = 4, // count of non-finite potentials written
+  kResSlots = 8
+};
+
+// device error word codes (first error wins)
+enum : int { kErrNone = 0, kErrTimeout = 1, kErrNonfinite = 2 };
+
+struct Side {
+  int64_t rows = 0;      // users on this side
+  int64_t rows_pad = 0;  // rows rounded up to kRowPad
+  float* log_u = nullptr;   // log u (side X) or log v (side Y), rows_pad
+  float* ell = nullptr;     // log u + b / (2 sigma), rows_pad
+  float* b2s = nullptr;     // b / (2 sigma), rows_pad, or nullptr without bias
+  double* mass = nullptr;   // capacities, rows_pad (padding 1)
+  float* pvec = nullptr;    // this side's potentials prepared for the other side's half-sweep, rows_pad
+  float* lmax = nullptr;    // device scalar: max_i ell_i
+  double sum_mass = 0.0;    // host copy of sum of capacities
+  __nv_bfloat16* fac16 = nullptr;  // packed [F | K] (or [G | L]) rows x kp, bf16, zero padded
+  float* fac32 = nullptr;          // packed rows x kp, fp32 (dense path), zero padded
+  CUtensorMap tm_own;       // TMA map, box kKBlock x kFusedOwnRows
+  CUtensorMap tm_partner;   // TMA map, box kKBlock x kFusedPartnerRows
+};
+
+}  // namespace tu
+
+struct tu_market {
+  int64_t N = 0, M = 0, d = 0;
+  int64_t kp = 0;           // packed inner dimension: 2d rounded up to a multiple of 64
+  int dtype = 0, path = 0;
+  double sigma = 1.0;
+  int64_t partition = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  tu::Side X, Y;
+  float* Ahat = nullptr;     // dense path: N x ldA fp32
+  int64_t ldA = 0;
+  double* partials = nullptr;   // kMaxPartials x 3 doubles
+  float* fpartials = nullptr;   // kMaxPartials floats (max reduction)
+  float* colpart = nullptr;     // dense column-pass partial sums
+  int64_t colpart_elems = 0;
+  int col_chunks = 0;
+  double* results = nullptr;       // device, kResSlots
+  double* results_host = nullptr;  // pinned, kResSlots
+  int* err_dev = nullptr;          // device error word
+  int* err_host = nullptr;         // pinned
+  void* staging = nullptr;         // device staging buffer for host-memory arguments
+  size_t staging_bytes = 0;
+  cudaGraphExec_t graph = nullptr; // captured block of sweeps
+  int graph_sweeps = 0;
+  bool poisoned = false;
+  std::string last_error;
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (one translation unit each); all return cudaGetLastError().
+// ---------------------------------------------------------------------------
+namespace tu {
+
+// reduce.cu
+cudaError_t launch_prep(tu_market* m, Side& partner, int fused_mode);
+cudaError_t launch_finalize(tu_market* m, int nparts, int is_x, int residual);
+cudaError_t launch_pack_factors(tu_market* m, Side& s, const void* A, const void* B, int src_dtype);
+cudaError_t launch_init_side(tu_market* m, Side& s, const float* bias_dev, int has_bias);
+cudaError_t launch_reset_potentials(tu_market* m, Side& s);
+cudaError_t launch_set_potentials(tu_market* m, Side& s, const float* log_u_dev);
+cudaError_t launch_row_norms(tu_market* m, Side& s, float* out_max);
+cudaError_t launch_sum_sq(tu_market* m, Side& s, int is_x);  // results[kResXSq or kResYSq] = sum exp(2 log u)
+
+// dense.cu
+cudaError_t launch_dense_build(tu_market* m);
+cudaError_t launch_dense_rowpass(tu_market* m, int residual, int update, int* nparts_out);
+cudaError_t launch_dense_colpass(tu_market* m, int update, int* nparts_out);
+
+// fused.cu
+cudaError_t fused_prepare(tu_market* m);  // tensor maps + kernel attributes
+cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int update, int* nparts_out);
+
+// topk.cu
+cudaError_t launch_mu_block(tu_market* m, int64_t x0, int64_t nx, int64_t y0, int64_t ny, float* out,
+                            int64_t ld);
+cudaError_t launch_topk(tu_market* m, int side, int k, int64_t row0, int64_t nrows, int32_t* idx,
+                        float* logmu);
+
+}  // namespace tu
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+namespace tu {
+
+constexpr double kLnHalf = -0.69314718055994530942;
+constexpr float kLog2e = 1.4426950408889634f;
+
+// asinh(e^z) for any z without overflow: z + log(1 + sqrt(1 + e^{-2z})) for z > 0.
+__device__ __forceinline__ double asinh_exp(double z) {
+  if (z > 0.0) return z + log1p(sqrt(1.0 + exp(-2.0 * z)));
+  return asinh(exp(z));
+}
+
+struct RowResult {
+  float log_u, ell;
+  double r_rel, r_abs, u2;
+};
+
+// The closed-form update of Eq. iteration for one user, in logs.
+//   ln_sum   : log of sum_y exp(phi_hat_xy / (2 sigma) + ell_y - shift)
+//   shift    : the partner-side shift (max_y ell_y) taken out of the sum
+//   b2s      : this user's bias / (2 sigma)
+//   log_s    = log(1/2) + b2s + shift + ln_sum          (s = 1/2 sum_y A_xy v_y)
+//   log u    = 1/2 log n - asinh(exp(log s - 1/2 log n)) (= sqrt(n + s^2) - s)
+// With residual, r = u_old^2 + 2 u_old s - n is the row equation of Eq. IPFP
+// evaluated at the state entering the half-sweep.
+__device__ __forceinline__ RowResult row_update(double ln_sum, double shift, float b2s, double mass,
+                                                float log_u_old, bool residual) {
+  RowResult o;
+  const double log_s = kLnHalf + (double)b2s + shift + ln_sum;
+  o.r_rel = 0.0;
+  o.r_abs = 0.0;
+  if (residual) {
+    const double u = exp((double)log_u_old);
+    const double r = u * u + 2.0 * u * exp(log_s) - mass;
+    o.r_abs = fabs(r);
+    o.r_rel = fabs(r) / mass;
+  }
+  const double hl = 0.5 * log(mass);
+  const double lu = hl - asinh_exp(log_s - hl);
+  o.log_u = (float)lu;
+  o.ell = (float)(lu + (double)b2s);
+  o.u2 = exp(2.0 * lu);
+  return o;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Time limit of every device-side wait. No legitimate wait in these kernels
+// lasts more than microseconds; a wait that runs out sets an error word.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// ---- mbarrier --------------------------------------------------------------
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity. Returns false when the
+// time limit runs out or another role of the CTA has raised the abort flag.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          uint64_t limit_ns = kWaitLimitNs) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (global_timer_ns() - t0 > limit_ns) return false;
+  }
+}
+
+// Bounded wait that ignores the abort flag: used while draining after an abort,
+// so that copies and MMAs already issued complete before shared memory or TMEM
+// is released.
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  const uint64_t t0 = global_timer_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    if (global_timer_ns() - t0 > limit_ns) return false;
+  }
+  return true;
+}
+
+// ---- TMA -------------------------------------------------------------------
+__device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+      "[%2];" ::"r"(smem_u32(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_map(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// ---- tcgen05 ---------------------------------------------------------------
+__device__ __forceinline__ void tmem_alloc(uint32_t* smem_dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(smem_dst)),
+               "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// D[tmem] (+)= A[smem] * B[smem]^T, both K-major, BF16 in, FP32 accumulate.
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrive on an mbarrier once every tcgen05 operation issued so far by this thread completes.
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major tile written by TMA with
+// 128-byte swizzle: rows of 128 bytes, 8-row atoms 1024 bytes apart.
+//   bits  0-13 start address >> 4     bits 16-29 leading byte offset >> 4 (unused here: 1)
+//   bits 32-45 stride byte offset >> 4 (1024 B)   bits 46-47 descriptor version (1)
+//   bits 61-63 layout: 2 = 128-byte swizzle
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t smem_addr) {
+  uint64_t desc = 0;
+  desc |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);
+  desc |= (uint64_t)1u << 16;
+  desc |= (uint64_t)(1024u >> 4) << 32;
+  desc |= (uint64_t)1u << 46;
+  desc |= (uint64_t)2u << 61;
+  return desc;
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1),
+// A and B BF16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0),
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// 32 lanes x 32 columns of FP32 from TMEM (lane quadrant fixed by the warp), then wait.
+__device__ __forceinline__ void tmem_ld32x32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ void named_bar_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Order-preserving float <-> uint mapping for atomic max on floats of any sign.
+__device__ __forceinline__ unsigned int float_to_ordered(float f) {
+  unsigned int u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+}  // namespace tu
+#endif  // __CUDACC__

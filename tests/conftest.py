@@ -20,5 +20,7 @@ def gpu_lib():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import paper_2411_19214_gb300 as tu
+    from paper_2411_19214_gb300 import build as tb
+    tb.build()
     tu.load()
     return tu

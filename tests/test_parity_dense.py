@@ -1,0 +1,113 @@
+"""GPU parity of the dense (materialised FP32 kernel) path against the FP64 oracle.
+
+Tolerance (derivation): A-hat is FP32 (relative error ~1e-7 from the FP32 dot
+product and expf), row sums are FP32 warp-tree sums of float4 partials, column
+sums add FP32 chunk partials in FP64: log s is within ~1e-6, so one sweep moves
+the log potentials by at most ~1e-6; ATOL_LOG = 1e-5. At the fixed point the
+benchmark's FP32 bar applies: 1e-5 relative on mu and on the marginals.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import dense_job_market, make_market, plain_dense_market
+
+from _parity import dense_logA, oracle_solve, oracle_sweeps
+
+pytestmark = pytest.mark.gpu
+
+ATOL_LOG = 1e-5
+MU_RTOL_FP32 = 1e-5
+
+
+SHAPES = [(700, 555, 32), (1, 333, 8), (333, 1, 8), (2048, 1001, 32), (97, 4099, 5)]
+
+
+@pytest.mark.parametrize("N,M,d", SHAPES, ids=lambda v: str(v))
+def test_sweeps_match_oracle(gpu_lib, N, M, d):
+    tu = gpu_lib
+    mk = make_market(N, M, d, sigma=0.5, seed=N + 3 * M, bias_y=True, m_kind="uniform1to5", dtype="fp32")
+    mkt = tu.from_synth(mk, path="dense")
+    try:
+        done = 0
+        for target in (1, 3, 8):
+            mkt.sweep(target - done)
+            done = target
+            lu, lv = (t.double().cpu().numpy() for t in mkt.potentials())
+            ou, ov = oracle_sweeps(mk, target)
+            np.testing.assert_allclose(lu, ou, rtol=0, atol=ATOL_LOG, err_msg=f"log u after {target} sweeps")
+            np.testing.assert_allclose(lv, ov, rtol=0, atol=ATOL_LOG, err_msg=f"log v after {target} sweeps")
+    finally:
+        mkt.close()
+
+
+def test_job_market_solve_matches_oracle(gpu_lib):
+    """Job-market recipe (lognormal job popularity, capacities U{1..5}, sigma 0.5)
+    at a size the oracle solves in seconds."""
+    tu = gpu_lib
+    mk = dense_job_market(N=2000, M=1000)
+    mkt = tu.from_synth(mk, path="dense")
+    try:
+        info = mkt.solve(tol=1e-7, max_iter=2000)
+        assert info["converged"], info
+        r, logA, f = oracle_solve(mk)
+        mu_ref = np.exp(oracle.log_mu(logA, r["log_u"], r["log_v"]))
+        mu = mkt.mu_block().double().cpu().numpy()
+        rel = np.max(np.abs(mu / mu_ref - 1))
+        print(f"dense job market: max rel mu err {rel:.3e}, sweeps {info['sweeps']}")
+        np.testing.assert_allclose(mu, mu_ref, rtol=MU_RTOL_FP32, atol=0)
+        lu, lv = (t.double().cpu().numpy() for t in mkt.potentials())
+        # marginals (constraints of Eq. primary optimization) of the GPU solution
+        np.testing.assert_allclose(mu.sum(1) + np.exp(2 * lu), f["n"], rtol=MU_RTOL_FP32)
+        np.testing.assert_allclose(mu.sum(0) + np.exp(2 * lv), f["m"], rtol=MU_RTOL_FP32)
+        cx = oracle.match_count(f["n"], r["log_u"])
+        assert abs(info["match_count"] - cx) <= MU_RTOL_FP32 * cx
+    finally:
+        mkt.close()
+
+
+def test_plain_balanced_market_fixed_point(gpu_lib):
+    """Plain balanced market (factors N(0, 1/d), unit capacities, sigma 1),
+    reduced to 300 x 300 so the oracle converges in seconds."""
+    tu = gpu_lib
+    mk = plain_dense_market(N=300, M=300)
+    mkt = tu.from_synth(mk, path="dense")
+    try:
+        info = mkt.solve(tol=1e-6, max_iter=20000)
+        assert info["converged"], info
+        r, logA, f = oracle_solve(mk, tol=1e-12)
+        mu_ref = np.exp(oracle.log_mu(logA, r["log_u"], r["log_v"]))
+        mu = mkt.mu_block().double().cpu().numpy()
+        rel = np.max(np.abs(mu / mu_ref - 1))
+        cx = oracle.match_count(f["n"], r["log_u"])
+        print(f"balanced 300: max rel mu err {rel:.3e}; match {info['match_count']:.9f} vs {cx:.9f}")
+        # a residual of 1e-6 in a balanced market (slow mode ~ N) bounds mu only to ~N * 1e-6
+        np.testing.assert_allclose(mu, mu_ref, rtol=3e-4)
+        assert abs(info["match_count"] - cx) <= 1e-5 * cx
+    finally:
+        mkt.close()
+
+
+def test_full_size_job_market_sampled(gpu_lib):
+    """20000 x 10000, d = 32: three sweeps on the GPU, then one more sweep
+    checked on 64 sampled rows and columns against the oracle's update from
+    the GPU's own state."""
+    tu = gpu_lib
+    mk = dense_job_market()
+    mkt = tu.from_synth(mk, path="dense")
+    try:
+        mkt.sweep(3)
+        lu0, lv0 = (t.double().cpu().numpy() for t in mkt.potentials())
+        mkt.sweep(1)
+        lu, lv = (t.double().cpu().numpy() for t in mkt.potentials())
+        rng = np.random.default_rng(1)
+        rows = np.sort(rng.choice(mk.N, 64, replace=False))
+        cols = np.sort(rng.choice(mk.M, 64, replace=False))
+        f = mk.f64()
+        _, ou = oracle.sampled_row_update(mk.F, mk.K, mk.G, mk.L, f["sigma"], f["n"], lv0, rows, None, mk.bias_y)
+        np.testing.assert_allclose(lu[rows], ou, atol=ATOL_LOG)
+        _, ov = oracle.sampled_row_update(mk.G, mk.L, mk.F, mk.K, f["sigma"], f["m"], lu, cols, mk.bias_y, None)
+        np.testing.assert_allclose(lv[cols], ov, atol=ATOL_LOG)
+    finally:
+        mkt.close()
