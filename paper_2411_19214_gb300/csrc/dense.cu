@@ -113,11 +113,11 @@ __device__ void block_write_partials(PartialAcc a, double* __restrict__ partials
 
 __global__ void __launch_bounds__(kThreads) k_dense_rowpass(
     const float* __restrict__ Ahat, int64_t ldA, int64_t N, const float* __restrict__ w,
-    const float* __restrict__ lmax_partner, const float* __restrict__ b2s, const double* __restrict__ mass,
-    float* __restrict__ log_u, float* __restrict__ ell, double* __restrict__ partials, int residual,
+    const double* __restrict__ lmax_partner, const float* __restrict__ b2s, const double* __restrict__ mass,
+    double* __restrict__ log_u, double* __restrict__ ell, double* __restrict__ partials, int residual,
     int update) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const double shift = (double)*lmax_partner;
+  const double shift = *lmax_partner;
   const int64_t n4 = ldA / 4;
   const float4* w4 = reinterpret_cast<const float4*>(w);
   PartialAcc acc;
@@ -197,10 +197,10 @@ __global__ void __launch_bounds__(kThreads) k_dense_colpart(const float* __restr
 }
 
 __global__ void __launch_bounds__(kThreads) k_dense_colfinal(
-    const float* __restrict__ colpart, int chunks, int64_t ldA, int64_t M, const float* __restrict__ lmax_partner,
-    const float* __restrict__ b2s, const double* __restrict__ mass, float* __restrict__ log_v,
-    float* __restrict__ ell, double* __restrict__ partials, int update) {
-  const double shift = (double)*lmax_partner;
+    const float* __restrict__ colpart, int chunks, int64_t ldA, int64_t M, const double* __restrict__ lmax_partner,
+    const float* __restrict__ b2s, const double* __restrict__ mass, double* __restrict__ log_v,
+    double* __restrict__ ell, double* __restrict__ partials, int update) {
+  const double shift = *lmax_partner;
   PartialAcc acc;
   for (int64_t y = (int64_t)blockIdx.x * kThreads + threadIdx.x; y < M; y += (int64_t)gridDim.x * kThreads) {
     double s = 0.0;

@@ -46,11 +46,11 @@ struct FusedParams {
   int num_partner_tiles;   // ceil(partner rows / 128)
   float c;                 // log2(e) / (2 sigma)
   const float* g;          // partner prepared potentials, >= num_partner_tiles * 128, -inf padded
-  const float* lmax;       // partner shift (natural log)
+  const double* lmax;      // partner shift (natural log)
   const float* b2s;        // own bias / (2 sigma), or nullptr
   const double* mass;      // own capacities
-  float* log_u;            // own potentials (in: old, out: new)
-  float* ell;              // own ell (out)
+  double* log_u;           // own potentials (in: old, out: new), FP64 state
+  double* ell;             // own ell (out), FP64 state
   double* partials;        // [gridDim.x][4]
   int* err;                // device error word
   int residual;
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;   // TMEM lane quadrant this warp may access
     const int h = ew >> 2;    // own sub-tile: rows [h*128, h*128+128)
     const float c = p.c;
-    const double shift = (double)__ldg(p.lmax);
+    const double shift = __ldg(p.lmax);
     int buf = 0;
     uint32_t tphase = 0;
     bool ok = true;

@@ -314,7 +314,7 @@ void tu_market_destroy(tu_market_t m) {
   side_free(m->Y);
   cudaFree(m->Ahat);
   cudaFree(m->partials);
-  cudaFree(m->fpartials);
+  cudaFree(m->mpartials);
   cudaFree(m->colpart);
   cudaFree(m->results);
   cudaFree(m->err_dev);
@@ -372,7 +372,7 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
   if ((st = side_alloc(m, m->X, D.N, D.bias_x != nullptr)) != TU_OK) return bail(st);
   if ((st = side_alloc(m, m->Y, D.M, D.bias_y != nullptr)) != TU_OK) return bail(st);
   if ((st = dev_alloc(m, &m->partials, (size_t)kMaxPartials * 4)) != TU_OK) return bail(st);
-  if ((st = dev_alloc(m, &m->fpartials, (size_t)kMaxPartials)) != TU_OK) return bail(st);
+  if ((st = dev_alloc(m, &m->mpartials, (size_t)kMaxPartials)) != TU_OK) return bail(st);
   if ((st = dev_alloc(m, &m->results, (size_t)kResSlots)) != TU_OK) return bail(st);
   if ((st = dev_alloc(m, &m->err_dev, 1)) != TU_OK) return bail(st);
   if (cudaMallocHost(&m->results_host, kResSlots * sizeof(double)) != cudaSuccess ||
@@ -501,7 +501,9 @@ tu_status tu_mu_block(tu_market_t m, int64_t x0, int64_t nx, int64_t y0, int64_t
   TU_TRY(output_view(m, out, bytes, 0, &dst, &host));
   TU_CK(m, launch_mu_block(m, x0, nx, y0, ny, static_cast<float*>(dst), ld));
   if (host) {
-    TU_CK(m, cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, m->stream));
+    // pitched copy: the caller's columns [ny, ld) of each row are left untouched
+    TU_CK(m, cudaMemcpy2DAsync(out, (size_t)ld * sizeof(float), dst, (size_t)ld * sizeof(float),
+                               (size_t)ny * sizeof(float), (size_t)nx, cudaMemcpyDeviceToHost, m->stream));
     TU_CK(m, cudaStreamSynchronize(m->stream));
   }
   return TU_OK;
@@ -532,16 +534,18 @@ tu_status tu_get_potentials(tu_market_t m, float* log_u, float* log_v) {
   TU_TRY(check_live(m));
   Side* sides[2] = {&m->X, &m->Y};
   float* outs[2] = {log_u, log_v};
-  bool sync = false;
   for (int i = 0; i < 2; ++i) {
     if (outs[i] == nullptr) continue;
     const size_t bytes = (size_t)sides[i]->rows * sizeof(float);
-    const bool dev = is_device_ptr(outs[i]);
-    TU_CK(m, cudaMemcpyAsync(outs[i], sides[i]->log_u, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                             m->stream));
-    sync = sync || !dev;
+    void* dst;
+    bool host;
+    TU_TRY(output_view(m, outs[i], bytes, 0, &dst, &host));
+    TU_CK(m, launch_get_potentials(m, *sides[i], static_cast<float*>(dst)));
+    if (host) {
+      TU_CK(m, cudaMemcpyAsync(outs[i], dst, bytes, cudaMemcpyDeviceToHost, m->stream));
+      TU_CK(m, cudaStreamSynchronize(m->stream));
+    }
   }
-  if (sync) TU_CK(m, cudaStreamSynchronize(m->stream));
   return TU_OK;
 }
 

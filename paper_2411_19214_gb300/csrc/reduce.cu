@@ -42,26 +42,32 @@ __global__ void k_pack_factors(const void* __restrict__ A, const void* __restric
 }
 
 __global__ void k_init_side(const float* __restrict__ bias, int has_bias, float inv2s, int64_t rows,
-                            int64_t rows_pad, float* __restrict__ b2s, float* __restrict__ log_u,
-                            float* __restrict__ ell) {
+                            int64_t rows_pad, float* __restrict__ b2s, double* __restrict__ log_u,
+                            double* __restrict__ ell) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows_pad;
        i += (int64_t)gridDim.x * blockDim.x) {
     float b = 0.0f;
     if (has_bias && i < rows) b = (float)((double)bias[i] * (double)inv2s);
     if (b2s != nullptr) b2s[i] = b;
-    log_u[i] = 0.0f;  // u = 1 (Alg. 1 / Alg. 2 initialisation)
-    ell[i] = (i < rows) ? b : 0.0f;
+    log_u[i] = 0.0;  // u = 1 (Alg. 1 / Alg. 2 initialisation)
+    ell[i] = (i < rows) ? (double)b : 0.0;
   }
 }
 
 __global__ void k_set_potentials(const float* __restrict__ src, const float* __restrict__ b2s, int64_t rows,
-                                 float* __restrict__ log_u, float* __restrict__ ell) {
+                                 double* __restrict__ log_u, double* __restrict__ ell) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const float lu = (src != nullptr) ? src[i] : 0.0f;
+    const double lu = (src != nullptr) ? (double)src[i] : 0.0;
     log_u[i] = lu;
-    ell[i] = (b2s != nullptr) ? (float)((double)lu + (double)b2s[i]) : lu;
+    ell[i] = (b2s != nullptr) ? lu + (double)b2s[i] : lu;
   }
+}
+
+__global__ void k_get_potentials(const double* __restrict__ log_u, int64_t rows, float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (float)log_u[i];
 }
 
 __global__ void k_row_norm_max(const float* __restrict__ f32, const __nv_bfloat16* __restrict__ f16,
@@ -89,50 +95,51 @@ __global__ void k_row_norm_max(const float* __restrict__ f32, const __nv_bfloat1
 }
 
 // Partner preparation, phase 1: per-block maximum of ell.
-__global__ void k_prep_max(const float* __restrict__ ell, int64_t rows, float* __restrict__ fpartials) {
-  __shared__ float red[kThreads / 32];
-  float mx = -INFINITY;
+__global__ void k_prep_max(const double* __restrict__ ell, int64_t rows, double* __restrict__ mpartials) {
+  __shared__ double red[kThreads / 32];
+  double mx = -INFINITY;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
        i += (int64_t)gridDim.x * blockDim.x)
-    mx = fmaxf(mx, ell[i]);
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    mx = fmax(mx, ell[i]);
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
-    float b = -INFINITY;
-    for (int w = 0; w < kThreads / 32; ++w) b = fmaxf(b, red[w]);
-    fpartials[blockIdx.x] = b;
+    double b = -INFINITY;
+    for (int w = 0; w < kThreads / 32; ++w) b = fmax(b, red[w]);
+    mpartials[blockIdx.x] = b;
   }
 }
 
 // Partner preparation, phase 2: shift = max ell; write the vector the
 // half-sweep consumes. fused_mode 1: (ell - shift) * log2(e), padding -inf
 // (exp2 of it is 0); fused_mode 0: exp(ell - shift), padding 0.
-__global__ void k_prep_write(const float* __restrict__ ell, int64_t rows, int64_t rows_pad,
-                             const float* __restrict__ fpartials, int nparts, int fused_mode,
-                             float* __restrict__ out, float* __restrict__ lmax) {
-  __shared__ float red[kThreads / 32];
-  __shared__ float shift_s;
-  float mx = -INFINITY;
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) mx = fmaxf(mx, fpartials[i]);
-  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+__global__ void k_prep_write(const double* __restrict__ ell, int64_t rows, int64_t rows_pad,
+                             const double* __restrict__ mpartials, int nparts, int fused_mode,
+                             float* __restrict__ out, double* __restrict__ lmax) {
+  __shared__ double red[kThreads / 32];
+  __shared__ double shift_s;
+  double mx = -INFINITY;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) mx = fmax(mx, mpartials[i]);
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = mx;
   __syncthreads();
   if (threadIdx.x == 0) {
-    float b = -INFINITY;
-    for (int w = 0; w < kThreads / 32; ++w) b = fmaxf(b, red[w]);
-    if (!(b > -INFINITY && b < INFINITY)) b = 0.0f;  // non-finite potentials are reported elsewhere
+    double b = -INFINITY;
+    for (int w = 0; w < kThreads / 32; ++w) b = fmax(b, red[w]);
+    if (!(b > -INFINITY && b < INFINITY)) b = 0.0;  // non-finite potentials are reported elsewhere
     shift_s = b;
     if (blockIdx.x == 0) *lmax = b;
   }
   __syncthreads();
-  const float shift = shift_s;
+  const double shift = shift_s;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows_pad;
        i += (int64_t)gridDim.x * blockDim.x) {
     float v;
     if (i < rows) {
-      const float z = ell[i] - shift;
-      v = fused_mode ? z * kLog2e : expf(z);
+      // the FP64 state is rounded once, to the FP32 vector the half-sweep streams
+      const double z = ell[i] - shift;
+      v = fused_mode ? (float)(z * 1.4426950408889634) : (float)exp(z);
     } else {
       v = fused_mode ? -INFINITY : 0.0f;
     }
@@ -180,12 +187,12 @@ __global__ void k_finalize(const double* __restrict__ partials, int nparts, int 
 }
 
 // sum_i exp(2 log u_i) in FP64 as per-block partials in the common format.
-__global__ void k_sum_sq(const float* __restrict__ log_u, int64_t rows, double* __restrict__ partials) {
+__global__ void k_sum_sq(const double* __restrict__ log_u, int64_t rows, double* __restrict__ partials) {
   __shared__ double red[kThreads / 32];
   double s = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
        i += (int64_t)gridDim.x * blockDim.x)
-    s += exp(2.0 * (double)log_u[i]);
+    s += exp(2.0 * log_u[i]);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = s;
   __syncthreads();
@@ -228,6 +235,12 @@ cudaError_t launch_reset_potentials(tu_market* m, Side& s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_get_potentials(tu_market* m, Side& s, float* out_dev) {
+  const int g = grid_for(s.rows, m->num_sms);
+  k_get_potentials<<<g, kThreads, 0, m->stream>>>(s.log_u, s.rows, out_dev);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_set_potentials(tu_market* m, Side& s, const float* log_u_dev) {
   const int g = grid_for(s.rows, m->num_sms);
   k_set_potentials<<<g, kThreads, 0, m->stream>>>(log_u_dev, s.b2s, s.rows, s.log_u, s.ell);
@@ -247,9 +260,9 @@ cudaError_t launch_row_norms(tu_market* m, Side& s, float* out_max) {
 cudaError_t launch_prep(tu_market* m, Side& partner, int fused_mode) {
   int g1 = grid_for(partner.rows, m->num_sms, 4);
   if (g1 > kMaxPartials) g1 = kMaxPartials;
-  k_prep_max<<<g1, kThreads, 0, m->stream>>>(partner.ell, partner.rows, m->fpartials);
+  k_prep_max<<<g1, kThreads, 0, m->stream>>>(partner.ell, partner.rows, m->mpartials);
   const int g2 = grid_for(partner.rows_pad, m->num_sms, 4);
-  k_prep_write<<<g2, kThreads, 0, m->stream>>>(partner.ell, partner.rows, partner.rows_pad, m->fpartials, g1,
+  k_prep_write<<<g2, kThreads, 0, m->stream>>>(partner.ell, partner.rows, partner.rows_pad, m->mpartials, g1,
                                                 fused_mode, partner.pvec, partner.lmax);
   return cudaGetLastError();
 }

@@ -50,20 +50,20 @@ struct ScoreSrc {
   }
 };
 
-__global__ void k_mu_block(ScoreSrc src, const float* __restrict__ ell_x, const float* __restrict__ ell_y, int64_t x0,
+__global__ void k_mu_block(ScoreSrc src, const double* __restrict__ ell_x, const double* __restrict__ ell_y, int64_t x0,
                            int64_t nx, int64_t y0, int64_t ny, float* __restrict__ out, int64_t ld) {
   const int64_t y = y0 + (int64_t)blockIdx.x * 32 + threadIdx.x;
   const int64_t x = x0 + (int64_t)blockIdx.y * 8 + threadIdx.y;
   if (x >= x0 + nx || y >= y0 + ny) return;
-  const double lm = (double)src.phi2s(x, y) + (double)ell_x[x] + (double)ell_y[y];
+  const double lm = (double)src.phi2s(x, y) + ell_x[x] + ell_y[y];
   out[(x - x0) * ld + (y - y0)] = (float)exp(lm);
 }
 
 // One warp per own row: each lane keeps a sorted top-k of the partners it
 // visits (increasing index, so equal scores keep the lower index first), then
 // the 32 lists are merged by k rounds of a warp-wide argmax.
-__global__ void __launch_bounds__(256) k_topk(ScoreSrc src, const float* __restrict__ ell_own,
-                                              const float* __restrict__ ell_par, int64_t partners, int k,
+__global__ void __launch_bounds__(256) k_topk(ScoreSrc src, const double* __restrict__ ell_own,
+                                              const double* __restrict__ ell_par, int64_t partners, int k,
                                               int64_t row0, int64_t nrows, int32_t* __restrict__ idx,
                                               float* __restrict__ logmu) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) k_topk(ScoreSrc src, const float* __restr
   int si[kMaxK];
   int cnt = 0;
   for (int64_t c = lane; c < partners; c += 32) {
-    const float s = src.phi2s(row, c) + ell_par[c];
+    const float s = (float)((double)src.phi2s(row, c) + ell_par[c]);
     if (cnt == k && !(s > sv[k - 1])) continue;
     int pos = (cnt < k) ? cnt : k - 1;
     while (pos > 0 && s > sv[pos - 1]) {
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256) k_topk(ScoreSrc src, const float* __restr
     si[pos] = (int)c;
     if (cnt < k) ++cnt;
   }
-  const float base = ell_own[row];
+  const double base = ell_own[row];
   int head = 0;
   for (int out_i = 0; out_i < k; ++out_i) {
     float bs = (head < cnt) ? sv[head] : -INFINITY;
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(256) k_topk(ScoreSrc src, const float* __restr
     if (lane == bl) ++head;
     if (lane == 0) {
       idx[r * k + out_i] = bi;
-      if (logmu != nullptr) logmu[r * k + out_i] = bs + base;
+      if (logmu != nullptr) logmu[r * k + out_i] = (float)((double)bs + base);
     }
   }
 }

@@ -39,12 +39,12 @@ enum : int { kErrNone = 0, kErrTimeout = 1, kErrNonfinite = 2 };
 struct Side {
   int64_t rows = 0;      // users on this side
   int64_t rows_pad = 0;  // rows rounded up to kRowPad
-  float* log_u = nullptr;   // log u (side X) or log v (side Y), rows_pad
-  float* ell = nullptr;     // log u + b / (2 sigma), rows_pad
+  double* log_u = nullptr;  // log u (side X) or log v (side Y), rows_pad (FP64 state)
+  double* ell = nullptr;    // log u + b / (2 sigma), rows_pad (FP64 state)
   float* b2s = nullptr;     // b / (2 sigma), rows_pad, or nullptr without bias
   double* mass = nullptr;   // capacities, rows_pad (padding 1)
   float* pvec = nullptr;    // this side's potentials prepared for the other side's half-sweep, rows_pad
-  float* lmax = nullptr;    // device scalar: max_i ell_i
+  double* lmax = nullptr;   // device scalar: max_i ell_i
   double sum_mass = 0.0;    // host copy of sum of capacities
   __nv_bfloat16* fac16 = nullptr;  // packed [F | K] (or [G | L]) rows x kp, bf16, zero padded
   float* fac32 = nullptr;          // packed rows x kp, fp32 (dense path), zero padded
@@ -67,7 +67,7 @@ struct tu_market {
   float* Ahat = nullptr;     // dense path: N x ldA fp32
   int64_t ldA = 0;
   double* partials = nullptr;   // kMaxPartials x 3 doubles
-  float* fpartials = nullptr;   // kMaxPartials floats (max reduction)
+  double* mpartials = nullptr;  // kMaxPartials doubles (max reduction)
   float* colpart = nullptr;     // dense column-pass partial sums
   int64_t colpart_elems = 0;
   int col_chunks = 0;
@@ -95,6 +95,7 @@ cudaError_t launch_pack_factors(tu_market* m, Side& s, const void* A, const void
 cudaError_t launch_init_side(tu_market* m, Side& s, const float* bias_dev, int has_bias);
 cudaError_t launch_reset_potentials(tu_market* m, Side& s);
 cudaError_t launch_set_potentials(tu_market* m, Side& s, const float* log_u_dev);
+cudaError_t launch_get_potentials(tu_market* m, Side& s, float* out_dev);  // FP64 state -> FP32
 cudaError_t launch_row_norms(tu_market* m, Side& s, float* out_max);
 cudaError_t launch_sum_sq(tu_market* m, Side& s, int is_x);  // results[kResXSq or kResYSq] = sum exp(2 log u)
 
@@ -131,7 +132,7 @@ __device__ __forceinline__ double asinh_exp(double z) {
 }
 
 struct RowResult {
-  float log_u, ell;
+  double log_u, ell;
   double r_rel, r_abs, u2;
 };
 
@@ -144,21 +145,21 @@ struct RowResult {
 // With residual, r = u_old^2 + 2 u_old s - n is the row equation of Eq. IPFP
 // evaluated at the state entering the half-sweep.
 __device__ __forceinline__ RowResult row_update(double ln_sum, double shift, float b2s, double mass,
-                                                float log_u_old, bool residual) {
+                                                double log_u_old, bool residual) {
   RowResult o;
   const double log_s = kLnHalf + (double)b2s + shift + ln_sum;
   o.r_rel = 0.0;
   o.r_abs = 0.0;
   if (residual) {
-    const double u = exp((double)log_u_old);
+    const double u = exp(log_u_old);
     const double r = u * u + 2.0 * u * exp(log_s) - mass;
     o.r_abs = fabs(r);
     o.r_rel = fabs(r) / mass;
   }
   const double hl = 0.5 * log(mass);
   const double lu = hl - asinh_exp(log_s - hl);
-  o.log_u = (float)lu;
-  o.ell = (float)(lu + (double)b2s);
+  o.log_u = lu;
+  o.ell = lu + (double)b2s;
   o.u2 = exp(2.0 * lu);
   return o;
 }

@@ -17,7 +17,10 @@ from _parity import dense_logA
 
 pytestmark = pytest.mark.gpu
 
-EPS = {"fused": 2e-5, "dense": 2e-6}
+# log mu is returned in FP32: at |log mu| ~ 16 one FP32 spacing is 1.9e-6 and the
+# score is the sum of three rounded terms, so the dense path is held to 1e-5;
+# the fused path adds the BF16-product / FP32-accumulation error of phi (2e-5).
+EPS = {"fused": 2e-5, "dense": 1e-5}
 
 
 def _market(path, N=517, M=1333, d=32, seed=21):
