@@ -1,0 +1,456 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the IPFP sweep (one JSON line on rank 0).
+
+Default workload: the fused mini-batch IPFP (Alg. 2) on a 1e6 x 1e6 market,
+d = 64, bf16 factors N(0, 1/d), LogNormal(0, 1) popularity biases on both
+sides, unit capacities, sigma = 0.5, partitions of 65536 users. One step is
+one full sweep of Eq. iteration: both half-sweeps (partner preparation,
+tcgen05 half-sweep, FP64 partial reduction), with the residual of the entering
+state folded into the X half-sweep.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload fused|dense]
+
+N > 1 (under torchrun): every rank solves its own market of the same shape
+(independent markets, weak scaling, no collective on the data path).
+--impl reference times the float64 CPU oracle on the host cores on a bounded
+sample of the same workload (rank 0 only).
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "IPFP sweeps/s and Gpair-evals/s at 1M×1M d=64 vs plain FP32; p50/p99 solve latency"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+
+def make_workload(name: str, rank: int, shape=None):
+    from synth import dense_job_market, fused_market
+    kw = {} if shape is None else {"N": shape[0], "M": shape[1]}
+    if name == "fused":
+        mk = fused_market(seed=1002 + 97 * rank, **kw)
+        cfg = {"workload": "fused mini-batch IPFP (Alg. 2): N=M=1,000,000 users, d=64 per factor (MMA K=128), "
+                           "bf16 factors N(0,1/d), lognormal(0,1) popularity bias on both sides, n=m=1, "
+                           "sigma=0.5, partitions of 65,536",
+               "N": mk.N, "M": mk.M, "d": mk.d, "sigma": mk.sigma, "partition": 65536, "path": "fused",
+               "l2": "inputs larger than L2: each half-sweep streams the 256 MB partner factor matrix "
+                     "(L2 is 129 MB); no flush between steps"}
+        if shape is not None:
+            cfg["workload"] = f"fused mini-batch IPFP (Alg. 2), reduced shape N={mk.N}, M={mk.M}, same recipe"
+        return mk, cfg, 65536
+    if name == "dense":
+        mk = dense_job_market(seed=1001 + 97 * rank, **kw)
+        cfg = {"workload": "dense batch IPFP (Alg. 1) over a materialised FP32 kernel: N=20,000 candidates x "
+                           "M=10,000 jobs, d=32, factors N(0,1/d), lognormal(0,1) job popularity bias, n=1, "
+                           "m~U{1..5}, sigma=0.5",
+               "N": mk.N, "M": mk.M, "d": mk.d, "sigma": mk.sigma, "path": "dense",
+               "l2": "inputs larger than L2: each half-sweep streams the 800 MB kernel matrix "
+                     "(L2 is 129 MB); no flush between steps"}
+        if shape is not None:
+            cfg["workload"] = f"dense batch IPFP (Alg. 1), reduced shape N={mk.N}, M={mk.M}, same recipe"
+        return mk, cfg, 0
+    raise ValueError(name)
+
+
+def load_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    return dict(FALLBACK_PEAKS)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu_index), "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_median": statistics.median(power), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on the host cores (bounded sample)
+# ---------------------------------------------------------------------------
+
+def _oracle_worker(args):
+    path, rows, sigma = args
+    import numpy as np
+
+    import oracle
+    F = np.load(os.path.join(path, "F.npy"), mmap_mode="r")
+    K = np.load(os.path.join(path, "K.npy"), mmap_mode="r")
+    G = np.load(os.path.join(path, "G.npy"), mmap_mode="r")
+    L = np.load(os.path.join(path, "L.npy"), mmap_mode="r")
+    bx = np.load(os.path.join(path, "bx.npy"))
+    by = np.load(os.path.join(path, "by.npy"))
+    n = np.load(os.path.join(path, "n.npy"))
+    lv = np.zeros(G.shape[0])
+    t0 = time.perf_counter()
+    oracle.sampled_row_update(F, K, G, L, sigma, n, lv, rows, bx, by)
+    return time.perf_counter() - t0
+
+
+class OraclePool:
+    """The float64 oracle's X half-sweep over sampled rows, on every host core
+    (one single-threaded process per core, spawned), against all partners."""
+
+    def __init__(self, mk):
+        import numpy as np
+        self.dir = tempfile.mkdtemp(prefix="oracle_")
+        for name, a in (("F", mk.F), ("K", mk.K), ("G", mk.G), ("L", mk.L), ("n", mk.n), ("m", mk.m)):
+            np.save(os.path.join(self.dir, f"{name}.npy"), a)
+        np.save(os.path.join(self.dir, "bx.npy"),
+                mk.bias_x if mk.bias_x is not None else np.zeros(mk.N, np.float32))
+        np.save(os.path.join(self.dir, "by.npy"),
+                mk.bias_y if mk.bias_y is not None else np.zeros(mk.M, np.float32))
+        self.N, self.M, self.sigma = mk.N, mk.M, mk.sigma
+        self.cores = os.cpu_count() or 1
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[var] = "1"
+        self.pool = mp.get_context("spawn").Pool(self.cores)
+        self.rng = np.random.default_rng(12345)
+
+    def run(self, rows_per_core: int) -> float:
+        """Wall seconds for cores x rows_per_core sampled rows."""
+        import numpy as np
+        tasks = []
+        for _ in range(self.cores):
+            rows = np.sort(self.rng.choice(self.N, rows_per_core, replace=False))
+            tasks.append((self.dir, rows, self.sigma))
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_worker, tasks)
+        return time.perf_counter() - t0
+
+    def calibrate(self, budget_s: float) -> int:
+        """rows per core so that one run takes about budget_s."""
+        self.run(2)  # warm the workers (imports, page cache)
+        t = self.run(4)
+        per_row = max(t / 4.0, 1e-4)
+        return max(4, int(budget_s / per_row))
+
+    def close(self):
+        import shutil
+        self.pool.close()
+        self.pool.join()
+        shutil.rmtree(self.dir, ignore_errors=True)
+
+
+def cpu_baseline(mk, budget_s: float = 15.0) -> dict:
+    pool = OraclePool(mk)
+    try:
+        rpc = pool.calibrate(budget_s)
+        t = pool.run(rpc)
+        rows = rpc * pool.cores
+        pairs = rows * mk.M
+        pair_rate = pairs / t
+        sweeps = pair_rate / (2.0 * mk.N * mk.M)
+        return {"value": sweeps, "unit": "sweeps/s", "cores": pool.cores, "kind": "oracle",
+                "gpair_evals_per_s": pair_rate / 1e9, "seconds": t,
+                "sample": f"float64 oracle X half-sweep (Eq. iteration_minibatch) of {rows} sampled users "
+                          f"against all {mk.M} partners ({pairs:.3g} pair evaluations, one process per core), "
+                          f"extrapolated to 2*N*M pair evaluations per sweep"}
+    finally:
+        pool.close()
+
+
+def run_reference(args):
+    """--impl reference: the oracle as it stands, rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    mk, cfg, _ = make_workload(args.workload, 0, args.shape)
+    pool = OraclePool(mk)
+    try:
+        rpc = pool.calibrate(8.0)
+        for _ in range(args.warmup):
+            pool.run(max(1, rpc // 4))
+        times = [pool.run(rpc) for _ in range(args.steps)]
+    finally:
+        pool.close()
+    rows = rpc * pool.cores
+    per_step_pairs = rows * mk.M
+    total_t = sum(times)
+    pair_rate = per_step_pairs * args.steps / total_t
+    value = pair_rate / (2.0 * mk.N * mk.M)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "sweeps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "gpair_evals_per_s": pair_rate / 1e9,
+            "cpu_baseline": {"value": value, "unit": "sweeps/s", "cores": pool.cores, "kind": "oracle",
+                             "sample": f"each step: float64 oracle X half-sweep of {rows} sampled users against "
+                                       f"all {mk.M} partners, one process per host core; sweeps/s extrapolated "
+                                       f"to 2*N*M pair evaluations per sweep"},
+            "e2e": {"value": value, "unit": "sweeps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def to_device_factors(mk, device, pinned=False):
+    import numpy as np
+    import torch
+
+    def conv(a):
+        if mk.dtype == "bf16":
+            bits = (np.ascontiguousarray(a, np.float32).view(np.uint32) >> 16).astype(np.uint16)
+            t = torch.from_numpy(bits.view(np.int16)).view(torch.bfloat16)
+        else:
+            t = torch.from_numpy(np.ascontiguousarray(a, np.float32))
+        if pinned:
+            return t.pin_memory()
+        return t.to(device)
+    return [conv(a) for a in (mk.F, mk.K, mk.G, mk.L)]
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2411_19214_gb300 as tu
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={world}")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    tu.load()
+    mk, cfg, partition = make_workload(args.workload, rank, args.shape)
+    # the CPU baseline pool is spawned before the first CUDA work of this process
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(mk, budget_s=args.cpu_budget)
+
+    stream = torch.cuda.Stream()
+    dev = torch.device("cuda", local)
+    Fd, Kd, Gd, Ld = to_device_factors(mk, dev)
+    bx = None if mk.bias_x is None else torch.from_numpy(mk.bias_x).to(dev)
+    by = None if mk.bias_y is None else torch.from_numpy(mk.bias_y).to(dev)
+    torch.cuda.synchronize()
+    h = tu.tu_market_create(Fd, Kd, Gd, Ld, mk.n, mk.m, mk.sigma, bias_x=bx, bias_y=by,
+                            path=cfg["path"], partition=partition, stream=stream)
+    try:
+        tu.tu_profile_enable(h, True)
+        for _ in range(args.warmup):
+            tu.tu_ipfp_sweep(h, 1)
+        torch.cuda.synchronize()
+        tu.tu_profile_read(h)  # discard warm-up passes
+
+        gpu_index = local
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            try:
+                gpu_index = int(vis.split(",")[local])
+            except ValueError:
+                gpu_index = local
+        clocks = ClockSampler(gpu_index)
+        barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        time.sleep(0.3)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            tu.tu_ipfp_sweep(h, 1)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clk = clocks.stop()
+        ms = ev0.elapsed_time(ev1)
+        pass_ms, passes = tu.tu_profile_read(h)
+        tu.tu_profile_enable(h, False)
+        if world > 1:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        residual = tu.tu_ipfp_sweep(h, 0, residual=True)
+
+        # end to end through the C ABI with host buffers: H2D of the step's
+        # factors from pinned memory, one sweep, D2H of the potentials
+        Fh, Kh, Gh, Lh = to_device_factors(mk, dev, pinned=True)
+        hu = torch.empty(mk.N, dtype=torch.float32).pin_memory()
+        hv = torch.empty(mk.M, dtype=torch.float32).pin_memory()
+        e2e_steps = max(1, min(args.steps, 5))
+        tu.tu_market_update_factors(h, Fh, Kh, Gh, Lh)
+        tu.tu_ipfp_sweep(h, 1)
+        tu.tu_get_potentials(h, hu, hv)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            tu.tu_market_update_factors(h, Fh, Kh, Gh, Lh)
+            tu.tu_ipfp_sweep(h, 1)
+            tu.tu_get_potentials(h, hu, hv)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        elem = 2 if mk.dtype == "bf16" else 4
+        h2d = 2 * (mk.N + mk.M) * mk.d * elem  # F, K (N x d) and G, L (M x d)
+        d2h = (mk.N + mk.M) * 4
+    finally:
+        tu.tu_market_destroy(h)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    peaks = load_peaks()
+    sweeps_per_s = world * args.steps / (ms / 1e3)
+    pairs_per_sweep = 2.0 * mk.N * mk.M
+    avg_pass_s = pass_ms / max(passes, 1) / 1e3
+    if cfg["path"] == "fused":
+        kp = 2 * mk.d
+        flops = 2.0 * mk.N * mk.M * kp  # one half-sweep: Phi tile products over all pairs
+        achieved = flops / avg_pass_s / 1e12
+        peak = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": "k_fused_halfsweep (tcgen05 BF16 MMA + ex2 row reduction)",
+                    "per_launch": f"{flops:.4g} flop (2*N*M*2d) in {avg_pass_s * 1e3:.2f} ms average over "
+                                  f"{passes} launches",
+                    "peak_source": f"{peaks.get('source')} bf16_tflops_sustained"}
+        exps = mk.N * mk.M
+        sm_mhz = clk.get("sm_mhz") or 1900.0
+        mufu_peak = 152 * 32 * sm_mhz * 1e6 / 1e12  # T ex2/s at the sampled clock, 32 ex2/clk/SM
+        roofline_exp = {"bound": "alu", "achieved": exps / avg_pass_s / 1e12, "peak": mufu_peak,
+                        "unit": "Tex2/s", "frac": exps / avg_pass_s / 1e12 / mufu_peak,
+                        "peak_source": "152 SMs x 32 ex2/clk/SM x sampled median SM clock"}
+    else:
+        ldA = (mk.M + 3) // 4 * 4
+        bytes_ = mk.N * ldA * 4.0
+        achieved = bytes_ / avg_pass_s / 1e9
+        peak = peaks.get("hbm_gbs")
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": None, "kernel": "dense row/column pass (A-hat stream)",
+                    "per_launch": f"{bytes_:.4g} B (N*ldA*4) in {avg_pass_s * 1e3:.3f} ms average over "
+                                  f"{passes} launches",
+                    "peak_source": f"{peaks.get('source')} hbm_gbs"}
+        roofline_exp = None
+    line = {"metric": METRIC, "value": sweeps_per_s, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": mk.dtype, "data": "synthetic", "config": cfg,
+            "gpair_evals_per_s": sweeps_per_s * pairs_per_sweep / 1e9,
+            "residual_inf_after": residual, "sweeps_run": args.warmup + args.steps,
+            "roofline": roofline,
+            "clocks": clk,
+            "gpu_launches": (8 if cfg["path"] == "fused" else 9) * args.steps,
+            "e2e": {"value": world * e2e_steps / e2e_s, "unit": "sweeps/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h,
+                    "path": "tu_market_update_factors(pinned host F,K,G,L) + tu_ipfp_sweep(1) + "
+                            "tu_get_potentials(pinned host)"}}
+    if roofline_exp is not None:
+        line["roofline_exp"] = roofline_exp
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["fused", "dense"], default="fused")
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shape", default=None,
+                    help="N,M override of the workload's sizes (same recipe; for small profiling cases)")
+    args = ap.parse_args()
+    if args.shape:
+        args.shape = tuple(int(v) for v in args.shape.split(","))
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

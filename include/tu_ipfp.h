@@ -144,6 +144,16 @@ tu_status tu_topk_partners(tu_market_t mkt, int side, int k, int64_t row0, int64
 tu_status tu_get_potentials(tu_market_t mkt, float* log_u, float* log_v);
 tu_status tu_set_potentials(tu_market_t mkt, const float* log_u, const float* log_v);
 
+/* Kernel timing for benchmarks (no counterpart in the paper). While enabled,
+ * every half-sweep pass records a CUDA event pair on the market's stream
+ * around its main kernel (fused: the tcgen05 half-sweep; dense: the row pass,
+ * or the two column-pass kernels), and sweeps are launched directly instead of
+ * through a captured graph. tu_profile_read synchronises the stream, returns
+ * the summed elapsed milliseconds and the number of timed passes since the
+ * last read (either pointer may be NULL), and starts a new count. */
+tu_status tu_profile_enable(tu_market_t mkt, int enable);
+tu_status tu_profile_read(tu_market_t mkt, double* pass_ms, int64_t* passes);
+
 /* Free every resource of the market (safe on NULL). */
 void tu_market_destroy(tu_market_t mkt);
 

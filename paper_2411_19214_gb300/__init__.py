@@ -69,6 +69,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tu_topk_partners": (I32, [V, I32, I32, I64, I64, V, V]),
         "tu_get_potentials": (I32, [V, V, V]),
         "tu_set_potentials": (I32, [V, V, V]),
+        "tu_profile_enable": (I32, [V, I32]),
+        "tu_profile_read": (I32, [V, ctypes.POINTER(D), ctypes.POINTER(I64)]),
         "tu_market_destroy": (None, [V]),
         "tu_status_string": (ctypes.c_char_p, [I32]),
         "tu_market_last_error": (ctypes.c_char_p, [V]),
@@ -85,8 +87,8 @@ def exported_symbols() -> list:
     """Names of the ABI functions the loaded library exports."""
     lib = load()
     names = ["tu_market_create", "tu_market_update_factors", "tu_ipfp_sweep", "tu_ipfp_solve", "tu_mu_block",
-             "tu_topk_partners", "tu_get_potentials", "tu_set_potentials", "tu_market_destroy",
-             "tu_status_string", "tu_market_last_error"]
+             "tu_topk_partners", "tu_get_potentials", "tu_set_potentials", "tu_profile_enable",
+             "tu_profile_read", "tu_market_destroy", "tu_status_string", "tu_market_last_error"]
     return [n for n in names if hasattr(lib, n)]
 
 
@@ -222,6 +224,18 @@ def tu_get_potentials(h: int, log_u=None, log_v=None) -> None:
 
 def tu_set_potentials(h: int, log_u=None, log_v=None) -> None:
     _check(load().tu_set_potentials(h, _ptr(log_u), _ptr(log_v)), "tu_set_potentials", h)
+
+
+def tu_profile_enable(h: int, enable: bool = True) -> None:
+    _check(load().tu_profile_enable(h, int(bool(enable))), "tu_profile_enable", h)
+
+
+def tu_profile_read(h: int):
+    """(summed milliseconds, number of timed passes) since the last read."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    _check(load().tu_profile_read(h, ctypes.byref(ms), ctypes.byref(n)), "tu_profile_read", h)
+    return ms.value, n.value
 
 
 def tu_market_destroy(h: int) -> None:

@@ -189,11 +189,34 @@ tu_status check_device_error(tu_market* m) {
   return TU_OK;
 }
 
+// Event pair around the main pass of a half-sweep (profiling only).
+cudaError_t profile_mark(tu_market* m, bool start) {
+  if (!m->profiling) return cudaSuccess;
+  if (start) {
+    if (m->ev_used == m->ev_pool.size()) {
+      cudaEvent_t a, b;
+      cudaError_t e = cudaEventCreate(&a);
+      if (e != cudaSuccess) return e;
+      e = cudaEventCreate(&b);
+      if (e != cudaSuccess) {
+        cudaEventDestroy(a);
+        return e;
+      }
+      m->ev_pool.push_back({a, b});
+    }
+    return cudaEventRecord(m->ev_pool[m->ev_used].first, m->stream);
+  }
+  cudaError_t e = cudaEventRecord(m->ev_pool[m->ev_used].second, m->stream);
+  ++m->ev_used;
+  return e;
+}
+
 // One half-sweep: prepare the partner potentials, run the pass, reduce partials.
 cudaError_t enqueue_half(tu_market* m, int side, int residual, int update) {
   Side& partner = side == 0 ? m->Y : m->X;
   cudaError_t e = launch_prep(m, partner, m->path == TU_PATH_FUSED ? 1 : 0);
   if (e != cudaSuccess) return e;
+  if ((e = profile_mark(m, true)) != cudaSuccess) return e;
   int nparts = 0;
   if (m->path == TU_PATH_FUSED) {
     e = launch_fused_halfsweep(m, side, residual, update, &nparts);
@@ -203,6 +226,7 @@ cudaError_t enqueue_half(tu_market* m, int side, int residual, int update) {
     e = launch_dense_colpass(m, update, &nparts);
   }
   if (e != cudaSuccess) return e;
+  if ((e = profile_mark(m, false)) != cudaSuccess) return e;
   return launch_finalize(m, nparts, side == 0 ? 1 : 0, residual);
 }
 
@@ -219,7 +243,7 @@ bool stream_capturable(cudaStream_t s) { return s != nullptr && s != cudaStreamL
 // Enqueue k sweeps, replaying a captured graph of k sweeps when possible.
 tu_status enqueue_sweeps(tu_market* m, int k) {
   if (k <= 0) return TU_OK;
-  if (stream_capturable(m->stream) && k > 1) {
+  if (stream_capturable(m->stream) && k > 1 && !m->profiling) {
     if (m->graph == nullptr || m->graph_sweeps != k) {
       if (m->graph != nullptr) {
         cudaGraphExecDestroy(m->graph);
@@ -305,10 +329,35 @@ const char* tu_status_string(tu_status s) {
 
 const char* tu_market_last_error(tu_market_t m) { return m ? m->last_error.c_str() : ""; }
 
+tu_status tu_profile_enable(tu_market_t m, int enable) {
+  TU_TRY(check_live(m));
+  m->profiling = enable != 0;
+  return TU_OK;
+}
+
+tu_status tu_profile_read(tu_market_t m, double* pass_ms, int64_t* passes) {
+  TU_TRY(check_live(m));
+  TU_CK(m, cudaStreamSynchronize(m->stream));
+  double total = 0.0;
+  for (size_t i = 0; i < m->ev_used; ++i) {
+    float ms = 0.0f;
+    TU_CK(m, cudaEventElapsedTime(&ms, m->ev_pool[i].first, m->ev_pool[i].second));
+    total += ms;
+  }
+  if (pass_ms) *pass_ms = total;
+  if (passes) *passes = (int64_t)m->ev_used;
+  m->ev_used = 0;
+  return TU_OK;
+}
+
 void tu_market_destroy(tu_market_t m) {
   if (m == nullptr) return;
   cudaSetDevice(m->device);
   if (m->stream) cudaStreamSynchronize(m->stream);
+  for (auto& pr : m->ev_pool) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
   if (m->graph) cudaGraphExecDestroy(m->graph);
   side_free(m->X);
   side_free(m->Y);

@@ -9,6 +9,8 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "../../include/tu_ipfp.h"
 
@@ -81,6 +83,10 @@ struct tu_market {
   int graph_sweeps = 0;
   bool poisoned = false;
   std::string last_error;
+  // benchmark timing (tu_profile_enable / tu_profile_read)
+  bool profiling = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
+  size_t ev_used = 0;
 };
 
 // ---------------------------------------------------------------------------
