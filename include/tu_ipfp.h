@@ -154,6 +154,43 @@ tu_status tu_set_potentials(tu_market_t mkt, const float* log_u, const float* lo
 tu_status tu_profile_enable(tu_market_t mkt, int enable);
 tu_status tu_profile_read(tu_market_t mkt, double* pass_ms, int64_t* passes);
 
+/* One fused X half-sweep on caller buffers that allocates no device memory.
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * call cudaMalloc, such as a serving process whose device memory is fully
+ * budgeted by an admission controller or held by another allocator (a
+ * framework's caching allocator), or a latency-critical loop where cudaMalloc /
+ * cudaFree would synchronise the device. It computes what the u step of a
+ * market sweep computes (Eq. iteration_minibatch, first line): for every own
+ * user r,
+ *     log u_r <- 1/2 log n_r - asinh(s_r / sqrt(n_r)),
+ *     s_r = 1/2 sum_c exp((<a_r, b_c> + b^own_r + b^par_c) / (2 sigma)) v_c.
+ * All pointers are DEVICE memory of the current device:
+ *   own_packed      rows x kp BF16 row-major: [f_r | k_r | zeros], kp = 64 or 128 (>= 2d), 16-byte aligned
+ *   partner_packed  cols x kp BF16 row-major: [g_c | l_c | zeros], 16-byte aligned
+ *   own_bias        rows FP32 biases b^own, or NULL
+ *   own_mass        rows FP64 capacities n_r > 0
+ *   own_log_u_in    rows FP32: the log u entering the half-sweep (used only for the residual)
+ *   partner_bias    cols FP32 biases b^par, or NULL
+ *   partner_log_v   cols FP32 log v of the partners
+ *   own_log_u_out   rows FP32: the new log u (may not alias own_log_u_in)
+ * residual_out (host, may be NULL): if given, the call synchronises the stream
+ * and stores max_r |u_r^2 + 2 u_r s_r - n_r| / n_r of the entering state (row
+ * equations of Eq. IPFP); otherwise the call only enqueues work on `stream`.
+ * Limits: 1 <= rows <= 65536 and 1 <= cols <= 1048576 (TU_ERR_UNSUPPORTED
+ * beyond them, and for kp other than 64 or 128); the exponent-range condition
+ * of tu_market_create applies and is not checked here.
+ * Scratch: one file-scope __device__ array of 5,644,576 bytes that every GPU
+ * loading the library holds until the process exits; its device address is
+ * resolved on the first call on each device (with that device current), so
+ * make that first call before any stream capture. Every call shares the array
+ * and it keeps the last call's contents: calls that overlap on the GPU (two
+ * streams, two host threads) race and must be serialised by the caller. */
+tu_status tu_fused_halfsweep_noalloc(int64_t rows, int64_t cols, int64_t kp, const void* own_packed,
+                                     const void* partner_packed, const float* own_bias, const double* own_mass,
+                                     const float* own_log_u_in, const float* partner_bias,
+                                     const float* partner_log_v, double sigma, float* own_log_u_out,
+                                     double* residual_out, void* stream);
+
 /* Free every resource of the market (safe on NULL). */
 void tu_market_destroy(tu_market_t mkt);
 

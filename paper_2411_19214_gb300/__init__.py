@@ -69,6 +69,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tu_topk_partners": (I32, [V, I32, I32, I64, I64, V, V]),
         "tu_get_potentials": (I32, [V, V, V]),
         "tu_set_potentials": (I32, [V, V, V]),
+        "tu_fused_halfsweep_noalloc": (I32, [I64, I64, I64, V, V, V, V, V, V, V, D, V, ctypes.POINTER(D), V]),
         "tu_profile_enable": (I32, [V, I32]),
         "tu_profile_read": (I32, [V, ctypes.POINTER(D), ctypes.POINTER(I64)]),
         "tu_market_destroy": (None, [V]),
@@ -224,6 +225,22 @@ def tu_get_potentials(h: int, log_u=None, log_v=None) -> None:
 
 def tu_set_potentials(h: int, log_u=None, log_v=None) -> None:
     _check(load().tu_set_potentials(h, _ptr(log_u), _ptr(log_v)), "tu_set_potentials", h)
+
+
+def tu_fused_halfsweep_noalloc(rows: int, cols: int, kp: int, own_packed, partner_packed, own_bias, own_mass,
+                               own_log_u_in, partner_bias, partner_log_v, sigma: float, own_log_u_out,
+                               residual: bool = False, stream=None) -> Optional[float]:
+    """One fused X half-sweep on caller device buffers, without any device
+    allocation (for callers whose device memory is fully budgeted or held by
+    another allocator). Returns the residual of the entering state when
+    ``residual`` is set (the call then synchronises the stream)."""
+    r = ctypes.c_double(float("nan"))
+    st = load().tu_fused_halfsweep_noalloc(int(rows), int(cols), int(kp), _ptr(own_packed), _ptr(partner_packed),
+                                           _ptr(own_bias), _ptr(own_mass), _ptr(own_log_u_in), _ptr(partner_bias),
+                                           _ptr(partner_log_v), float(sigma), _ptr(own_log_u_out),
+                                           ctypes.byref(r) if residual else None, _stream_handle(stream))
+    _check(st, "tu_fused_halfsweep_noalloc")
+    return r.value if residual else None
 
 
 def tu_profile_enable(h: int, enable: bool = True) -> None:

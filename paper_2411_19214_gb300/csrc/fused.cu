@@ -405,4 +405,46 @@ cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int upd
   return cudaGetLastError();
 }
 
+// Same kernel on caller-described buffers (no market object): used by the
+// allocation-free entry point. Tensor maps are built on the host stack.
+cudaError_t launch_fused_halfsweep_raw(const FusedRaw& r, cudaStream_t stream, int num_sms, int* nparts_out) {
+  CUtensorMap own_map, partner_map;
+  cudaError_t e;
+  if ((e = make_map(&own_map, r.own16, r.rows, r.kp, kFusedOwnRows)) != cudaSuccess) return e;
+  if ((e = make_map(&partner_map, r.par16, r.cols, r.kp, kFusedPartnerRows)) != cudaSuccess) return e;
+  FusedParams p;
+  p.rows = r.rows;
+  p.num_own_tiles = (int)((r.rows + kFusedOwnRows - 1) / kFusedOwnRows);
+  p.num_partner_tiles = (int)((r.cols + kFusedPartnerRows - 1) / kFusedPartnerRows);
+  p.c = (float)(1.4426950408889634 / (2.0 * r.sigma));
+  p.g = r.g;
+  p.lmax = r.lmax;
+  p.b2s = r.b2s;
+  p.mass = r.mass;
+  p.log_u = r.log_u;
+  p.ell = r.ell;
+  p.partials = r.partials;
+  p.err = r.err;
+  p.residual = r.residual;
+  p.update = 1;
+  int grid = p.num_own_tiles < num_sms ? p.num_own_tiles : num_sms;
+  if (grid > kMaxPartials) grid = kMaxPartials;
+  const int kb = (int)(r.kp / kKBlock);
+  if (kb == 1) {
+    if ((e = cudaFuncSetAttribute(k_fused_halfsweep<1, kStagesKB1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem_bytes<1>(kStagesKB1))) != cudaSuccess)
+      return e;
+    k_fused_halfsweep<1, kStagesKB1><<<grid, kThreads, smem_bytes<1>(kStagesKB1), stream>>>(own_map, partner_map, p);
+  } else if (kb == 2) {
+    if ((e = cudaFuncSetAttribute(k_fused_halfsweep<2, kStagesKB2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  smem_bytes<2>(kStagesKB2))) != cudaSuccess)
+      return e;
+    k_fused_halfsweep<2, kStagesKB2><<<grid, kThreads, smem_bytes<2>(kStagesKB2), stream>>>(own_map, partner_map, p);
+  } else {
+    return cudaErrorNotSupported;
+  }
+  *nparts_out = grid;
+  return cudaGetLastError();
+}
+
 }  // namespace tu

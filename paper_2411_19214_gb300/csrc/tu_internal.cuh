@@ -114,6 +114,26 @@ cudaError_t launch_dense_colpass(tu_market* m, int update, int* nparts_out);
 cudaError_t fused_prepare(tu_market* m);  // tensor maps + kernel attributes
 cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int update, int* nparts_out);
 
+// The fused half-sweep on caller-described device buffers (no market object).
+struct FusedRaw {
+  const __nv_bfloat16* own16;  // rows x kp packed own factors
+  int64_t rows;
+  const __nv_bfloat16* par16;  // cols x kp packed partner factors
+  int64_t cols;
+  int64_t kp;                  // 64 or 128
+  double sigma;
+  const float* g;              // prepared partner vector, >= ceil(cols / 128) * 128, -inf padded
+  const double* lmax;          // partner shift
+  const float* b2s;            // own bias / (2 sigma) or nullptr
+  const double* mass;          // own capacities
+  double* log_u;               // own log u (in: old, out: new)
+  double* ell;                 // own ell (out)
+  double* partials;            // >= min(ceil(rows / 256), num_sms) x 4
+  int* err;
+  int residual;
+};
+cudaError_t launch_fused_halfsweep_raw(const FusedRaw& r, cudaStream_t stream, int num_sms, int* nparts_out);
+
 // topk.cu
 cudaError_t launch_mu_block(tu_market* m, int64_t x0, int64_t nx, int64_t y0, int64_t ny, float* out,
                             int64_t ld);
