@@ -13,16 +13,20 @@
 // flash-attention collapses to one shift per half-sweep.
 //
 // CTA layout (320 threads, one CTA per SM, persistent over own tiles):
-//   warp 0     : TMA producer (one elected thread): the own tile [F|K]_j
-//                (256 rows x kp) once per own tile, then partner tiles
-//                (128 rows x kp) through a STAGES-deep shared-memory ring.
+//   warp 0     : producer (one elected thread): TMA loads of the own tile
+//                [F|K]_j (256 rows x kp) once per own tile and of partner tiles
+//                (128 rows x kp) through a STAGES-deep shared-memory ring, plus
+//                a bulk copy of each partner tile's 128 g values into an
+//                8-slot ring that the epilogue reads with broadcast loads.
 //   warp 1     : MMA issuer (one thread): two tcgen05.mma M=128 N=128 chains
 //                (own rows 0-127 and 128-255) per partner tile into one of two
 //                TMEM accumulator buffers (2 x 256 columns = all 512).
 //   warps 2-9  : epilogue: warp w reads TMEM lanes 32*(w%4).. of own sub-tile
 //                (w-2)/4, i.e. one own row per thread, so the row reduction
-//                stays inside the thread (no shuffles): FFMA + ex2 + FADD per
-//                pair, per-tile partials added into a compensated sum.
+//                stays inside the thread (no shuffles). TMEM loads run one
+//                32-column chunk ahead of the arithmetic; per pair of columns
+//                one packed FMA (f32x2), two ex2.approx and one packed add;
+//                per-tile partials go into a compensated (Kahan) sum.
 // Every wait is bounded (kWaitLimitNs); a wait that runs out raises the
 // abort flag and the error word, the roles drain, TMEM is freed, and the
 // kernel returns.
@@ -38,6 +42,8 @@ constexpr int kThreads = 320;
 constexpr int kEpiWarps = 8;
 constexpr int kOwnBytesPerKB = kFusedOwnRows * 128;          // 32 KB per 64-wide k block
 constexpr int kPartnerBytesPerKB = kFusedPartnerRows * 128;  // 16 KB per 64-wide k block
+constexpr int kGSlots = 8;                                   // g ring depth
+constexpr int kGBytes = kFusedPartnerRows * 4;               // one partner tile of g (512 B)
 constexpr uint32_t kTmemCols = 512;
 
 struct FusedParams {
@@ -57,14 +63,82 @@ struct FusedParams {
   int update;
 };
 
+// shared memory: [A: KB x 32 KB][B: STAGES x KB x 16 KB][g ring: 8 x 512 B][barriers, flags, reduction]
 template <int KB>
 constexpr int smem_bytes(int stages) {
-  return 1024 /*alignment slack*/ + KB * kOwnBytesPerKB + stages * KB * kPartnerBytesPerKB + 512;
+  return 1024 /*alignment slack*/ + KB * kOwnBytesPerKB + stages * KB * kPartnerBytesPerKB + kGSlots * kGBytes +
+         1024;
 }
 
 __device__ __forceinline__ void raise_error(int* err, volatile int* abort_flag, int code) {
   atomicCAS(err, kErrNone, code);
   *abort_flag = 1;
+}
+
+// 1D bulk copy global -> shared, completion counted on an mbarrier (16-byte aligned, size % 16 == 0).
+__device__ __forceinline__ void bulk_load(void* smem_dst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(gsrc)), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Issue a 32-lane x 32-column FP32 TMEM load without waiting for it.
+__device__ __forceinline__ void tmem_ld_issue(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+}
+
+// Wait for the outstanding TMEM loads; the registers are passed through so
+// that no use of them can be scheduled before the wait.
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
+}
+
+// acc(2 lanes) += (ex2(phi0 * c + g0), ex2(phi1 * c + g1)) with packed FP32x2 FMA and add.
+__device__ __forceinline__ void pair_step(uint64_t& acc, uint32_t phi0, uint32_t phi1, float g0, float g1,
+                                          uint64_t cc) {
+  asm("{\n\t.reg .b64 a, gg, t, e;\n\t.reg .f32 t0, t1, e0, e1;\n\t"
+      "mov.b64 a, {%1, %2};\n\t"
+      "mov.b64 gg, {%3, %4};\n\t"
+      "fma.rn.f32x2 t, a, %5, gg;\n\t"
+      "mov.b64 {t0, t1}, t;\n\t"
+      "ex2.approx.ftz.f32 e0, t0;\n\t"
+      "ex2.approx.ftz.f32 e1, t1;\n\t"
+      "mov.b64 e, {e0, e1};\n\t"
+      "add.rn.f32x2 %0, %0, e;\n\t}"
+      : "+l"(acc)
+      : "r"(phi0), "r"(phi1), "f"(g0), "f"(g1), "l"(cc));
+}
+
+__device__ __forceinline__ float unpack_sum(uint64_t a) {
+  return __uint_as_float((uint32_t)a) + __uint_as_float((uint32_t)(a >> 32));
+}
+
+// Sum over one 32-column chunk: 16 packed pairs into four packed accumulators.
+__device__ __forceinline__ void chunk_sum(const uint32_t (&v)[32], const float4* gs4, uint64_t cc, uint64_t (&acc)[4]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float4 gg = gs4[i];
+    pair_step(acc[(2 * i) & 3], v[4 * i + 0], v[4 * i + 1], gg.x, gg.y, cc);
+    pair_step(acc[(2 * i + 1) & 3], v[4 * i + 2], v[4 * i + 3], gg.z, gg.w, cc);
+  }
 }
 
 template <int KB, int STAGES>
@@ -76,10 +150,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* smem = smem_raw + (((raw_u32 + 1023u) & ~1023u) - raw_u32);
   uint8_t* sA = smem;
   uint8_t* sB = smem + KB * kOwnBytesPerKB;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + STAGES * KB * kPartnerBytesPerKB);
+  float* sG = reinterpret_cast<float*>(sB + STAGES * KB * kPartnerBytesPerKB);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(sG) + kGSlots * kGBytes);
   uint64_t* full = bars;
   uint64_t* empty = bars + STAGES;
-  uint64_t* a_full = bars + 2 * STAGES;
+  uint64_t* gfull = bars + 2 * STAGES;
+  uint64_t* gempty = gfull + kGSlots;
+  uint64_t* a_full = gempty + kGSlots;
   uint64_t* a_empty = a_full + 1;
   uint64_t* tfull = a_full + 2;   // [2]
   uint64_t* tempty = a_full + 4;  // [2]
@@ -94,6 +171,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < kGSlots; ++s) {
+      mbar_init(&gfull[s], 1);
+      mbar_init(&gempty[s], kEpiWarps);
     }
     mbar_init(a_full, 1);
     mbar_init(a_empty, 1);
@@ -119,10 +200,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0, a_phase = 0;
-      uint32_t armed[STAGES];
+      int stage = 0, gs = 0;
+      uint32_t phase = 0, gphase = 0, a_phase = 0;
+      uint32_t armed[STAGES], garmed[kGSlots];
       for (int s = 0; s < STAGES; ++s) armed[s] = 0;
+      for (int s = 0; s < kGSlots; ++s) garmed[s] = 0;
       uint32_t a_armed = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < p.num_own_tiles && ok; t += gridDim.x) {
@@ -149,6 +231,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             stage = 0;
             phase ^= 1u;
           }
+          if (!mbar_wait(&gempty[gs], gphase ^ 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          mbar_arrive_expect_tx(&gfull[gs], kGBytes);
+          bulk_load(sG + gs * kFusedPartnerRows, p.g + (int64_t)j * kFusedPartnerRows, kGBytes, &gfull[gs]);
+          ++garmed[gs];
+          if (++gs == kGSlots) {
+            gs = 0;
+            gphase ^= 1u;
+          }
         }
       }
       if (!ok) {
@@ -156,6 +249,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         // let the copies already issued land before the CTA's shared memory goes away
         for (int s = 0; s < STAGES; ++s)
           if (armed[s]) mbar_wait_drain(&full[s], (armed[s] - 1u) & 1u, 10000000ull);
+        for (int s = 0; s < kGSlots; ++s)
+          if (garmed[s]) mbar_wait_drain(&gfull[s], (garmed[s] - 1u) & 1u, 10000000ull);
         if (a_armed) mbar_wait_drain(a_full, (a_armed - 1u) & 1u, 10000000ull);
       }
     }
@@ -215,53 +310,62 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int ew = warp - 2;
     const int q = warp & 3;   // TMEM lane quadrant this warp may access
     const int h = ew >> 2;    // own sub-tile: rows [h*128, h*128+128)
-    const float c = p.c;
+    uint64_t cc;
+    {
+      const uint32_t cb = __float_as_uint(p.c);
+      cc = ((uint64_t)cb << 32) | cb;
+    }
     const double shift = __ldg(p.lmax);
-    int buf = 0;
-    uint32_t tphase = 0;
+    int buf = 0, gs = 0;
+    uint32_t tphase = 0, gphase = 0;
     bool ok = true;
     double r_max = 0.0, r_sum = 0.0, sq = 0.0, nf = 0.0;
+    uint32_t va[32], vb[32];
     for (int t = blockIdx.x; t < p.num_own_tiles && ok; t += gridDim.x) {
       float sum = 0.0f, comp = 0.0f;
       for (int j = 0; j < p.num_partner_tiles; ++j) {
-        const float* gt = p.g + (int64_t)j * kFusedPartnerRows;
         // every lane waits; the outcome is made warp-uniform so that the
         // .sync.aligned TMEM loads below never run with a partial warp
-        if (!__all_sync(0xffffffffu, mbar_wait(&tfull[buf], tphase, abort_flag))) {
+        const bool got = mbar_wait(&tfull[buf], tphase, abort_flag) && mbar_wait(&gfull[gs], gphase, abort_flag);
+        if (!__all_sync(0xffffffffu, got)) {
           ok = false;
           break;
         }
         tc_fence_after();
         const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256 + h * 128);
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll
-        for (int chunk = 0; chunk < 4; ++chunk) {
-          float v[32];
-          tmem_ld32x32(taddr + chunk * 32, v);
-          if (chunk == 3) {
-            // this warp's part of the accumulator buffer has been read: hand it back to the MMA warp
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[buf]);
-          }
-          const float4* g4 = reinterpret_cast<const float4*>(gt + chunk * 32);
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const float4 gg = __ldg(g4 + i);
-            a0 += ex2_approx(fmaf(v[4 * i + 0], c, gg.x));
-            a1 += ex2_approx(fmaf(v[4 * i + 1], c, gg.y));
-            a2 += ex2_approx(fmaf(v[4 * i + 2], c, gg.z));
-            a3 += ex2_approx(fmaf(v[4 * i + 3], c, gg.w));
-          }
-        }
+        const float4* gs4 = reinterpret_cast<const float4*>(sG + gs * kFusedPartnerRows);
+        uint64_t acc[4] = {0ull, 0ull, 0ull, 0ull};
+        tmem_ld_issue(taddr, va);
+        tmem_ld_wait(va);
+        tmem_ld_issue(taddr + 32, vb);
+        chunk_sum(va, gs4, cc, acc);
+        tmem_ld_wait(vb);
+        tmem_ld_issue(taddr + 64, va);
+        chunk_sum(vb, gs4 + 8, cc, acc);
+        tmem_ld_wait(va);
+        tmem_ld_issue(taddr + 96, vb);
+        chunk_sum(va, gs4 + 16, cc, acc);
+        tmem_ld_wait(vb);
+        // this warp's part of the accumulator buffer has been read: hand it back to the MMA warp
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
+        chunk_sum(vb, gs4 + 24, cc, acc);
+        // the g slot has been read by this warp
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&gempty[gs]);
         // compensated (Kahan) accumulation of the per-tile partial sums
-        const float tile = (a0 + a1) + (a2 + a3);
+        const float tile = (unpack_sum(acc[0]) + unpack_sum(acc[1])) + (unpack_sum(acc[2]) + unpack_sum(acc[3]));
         const float y = tile - comp;
         const float tsum = sum + y;
         comp = (tsum - sum) - y;
         sum = tsum;
         buf ^= 1;
         if (buf == 0) tphase ^= 1u;
+        if (++gs == kGSlots) {
+          gs = 0;
+          gphase ^= 1u;
+        }
       }
       if (!ok) break;
       const int64_t row = (int64_t)t * kFusedOwnRows + h * 128 + q * 32 + lane;
@@ -354,6 +458,31 @@ cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, 
 constexpr int kStagesKB1 = 6;
 constexpr int kStagesKB2 = 4;
 
+template <int KB, int STAGES>
+cudaError_t launch_kernel(const CUtensorMap& own, const CUtensorMap& partner, const FusedParams& p, int grid,
+                          cudaStream_t stream) {
+  static_assert(smem_bytes<KB>(STAGES) <= 232448, "shared memory budget");
+  k_fused_halfsweep<KB, STAGES><<<grid, kThreads, smem_bytes<KB>(STAGES), stream>>>(own, partner, p);
+  return cudaGetLastError();
+}
+
+// Dynamic shared memory opt-in of every instantiation, on the current device.
+cudaError_t set_kernel_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_fused_halfsweep<1, kStagesKB1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem_bytes<1>(kStagesKB1));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_fused_halfsweep<2, kStagesKB2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem_bytes<2>(kStagesKB2));
+}
+
+cudaError_t launch_any(int64_t kp, const CUtensorMap& own, const CUtensorMap& partner, const FusedParams& p,
+                       int grid, cudaStream_t stream) {
+  const int kb = (int)(kp / kKBlock);
+  if (kb == 1) return launch_kernel<1, kStagesKB1>(own, partner, p, grid, stream);
+  if (kb == 2) return launch_kernel<2, kStagesKB2>(own, partner, p, grid, stream);
+  return cudaErrorNotSupported;
+}
+
 }  // namespace
 
 cudaError_t fused_prepare(tu_market* m) {
@@ -362,13 +491,7 @@ cudaError_t fused_prepare(tu_market* m) {
   if ((e = make_map(&m->X.tm_partner, m->X.fac16, m->X.rows, m->kp, kFusedPartnerRows)) != cudaSuccess) return e;
   if ((e = make_map(&m->Y.tm_own, m->Y.fac16, m->Y.rows, m->kp, kFusedOwnRows)) != cudaSuccess) return e;
   if ((e = make_map(&m->Y.tm_partner, m->Y.fac16, m->Y.rows, m->kp, kFusedPartnerRows)) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(k_fused_halfsweep<1, kStagesKB1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem_bytes<1>(kStagesKB1))) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(k_fused_halfsweep<2, kStagesKB2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                smem_bytes<2>(kStagesKB2))) != cudaSuccess)
-    return e;
-  return cudaSuccess;
+  return set_kernel_attributes();
 }
 
 cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int update, int* nparts_out) {
@@ -391,18 +514,8 @@ cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int upd
   p.update = update;
   int grid = p.num_own_tiles < m->num_sms ? p.num_own_tiles : m->num_sms;
   if (grid > kMaxPartials) grid = kMaxPartials;
-  const int kb = (int)(m->kp / kKBlock);
-  if (kb == 1) {
-    k_fused_halfsweep<1, kStagesKB1><<<grid, kThreads, smem_bytes<1>(kStagesKB1), m->stream>>>(
-        own.tm_own, partner.tm_partner, p);
-  } else if (kb == 2) {
-    k_fused_halfsweep<2, kStagesKB2><<<grid, kThreads, smem_bytes<2>(kStagesKB2), m->stream>>>(
-        own.tm_own, partner.tm_partner, p);
-  } else {
-    return cudaErrorNotSupported;
-  }
   *nparts_out = grid;
-  return cudaGetLastError();
+  return launch_any(m->kp, own.tm_own, partner.tm_partner, p, grid, m->stream);
 }
 
 // Same kernel on caller-described buffers (no market object): used by the
@@ -412,6 +525,7 @@ cudaError_t launch_fused_halfsweep_raw(const FusedRaw& r, cudaStream_t stream, i
   cudaError_t e;
   if ((e = make_map(&own_map, r.own16, r.rows, r.kp, kFusedOwnRows)) != cudaSuccess) return e;
   if ((e = make_map(&partner_map, r.par16, r.cols, r.kp, kFusedPartnerRows)) != cudaSuccess) return e;
+  if ((e = set_kernel_attributes()) != cudaSuccess) return e;
   FusedParams p;
   p.rows = r.rows;
   p.num_own_tiles = (int)((r.rows + kFusedOwnRows - 1) / kFusedOwnRows);
@@ -429,22 +543,8 @@ cudaError_t launch_fused_halfsweep_raw(const FusedRaw& r, cudaStream_t stream, i
   p.update = 1;
   int grid = p.num_own_tiles < num_sms ? p.num_own_tiles : num_sms;
   if (grid > kMaxPartials) grid = kMaxPartials;
-  const int kb = (int)(r.kp / kKBlock);
-  if (kb == 1) {
-    if ((e = cudaFuncSetAttribute(k_fused_halfsweep<1, kStagesKB1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  smem_bytes<1>(kStagesKB1))) != cudaSuccess)
-      return e;
-    k_fused_halfsweep<1, kStagesKB1><<<grid, kThreads, smem_bytes<1>(kStagesKB1), stream>>>(own_map, partner_map, p);
-  } else if (kb == 2) {
-    if ((e = cudaFuncSetAttribute(k_fused_halfsweep<2, kStagesKB2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  smem_bytes<2>(kStagesKB2))) != cudaSuccess)
-      return e;
-    k_fused_halfsweep<2, kStagesKB2><<<grid, kThreads, smem_bytes<2>(kStagesKB2), stream>>>(own_map, partner_map, p);
-  } else {
-    return cudaErrorNotSupported;
-  }
   *nparts_out = grid;
-  return cudaGetLastError();
+  return launch_any(r.kp, own_map, partner_map, p, grid, stream);
 }
 
 }  // namespace tu
