@@ -25,7 +25,8 @@
  *                  and never stored; requires d <= 64.
  *   TU_PATH_DENSE  batch IPFP (Alg. 1 / Eq. iteration_matrix): the FP32 kernel
  *                  A-hat = exp((Phi - b^X - b^Y) / (2 sigma)) is materialised
- *                  once (N*M*4 bytes) and streamed every half-sweep.
+ *                  once, with its transpose (2*N*M*4 bytes), and one of the
+ *                  two is streamed every half-sweep.
  *
  * Conventions shared by every entry point:
  *   - Return codes only; nothing is thrown across the ABI.
@@ -91,7 +92,7 @@ typedef struct {
  * a_x = (f_x, k_x), b_y = (g_y, l_y) (a Cauchy-Schwarz bound on the bias-free
  * part of phi / (2 sigma)); otherwise TU_ERR_UNSUPPORTED. Biases have no limit:
  * they are folded into the potentials in log space. On success *out owns device memory of about
- * (N + M) * 2 * d * 2 bytes (fused) or N * M * 4 bytes (dense) plus O(N + M). */
+ * (N + M) * 2 * d * 2 bytes (fused) or 2 * N * M * 4 bytes (dense) plus O(N + M). */
 tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out);
 
 /* Replace F, K, G, L (same shapes and dtype as at creation; host or device).

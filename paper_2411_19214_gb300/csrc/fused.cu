@@ -38,8 +38,8 @@ namespace tu {
 
 namespace {
 
-constexpr int kThreads = 320;
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;
+constexpr int kThreads = 64 + kEpiWarps * 32;  // producer warp, MMA warp, epilogue warps
 constexpr int kOwnBytesPerKB = kFusedOwnRows * 128;          // 32 KB per 64-wide k block
 constexpr int kPartnerBytesPerKB = kFusedPartnerRows * 128;  // 16 KB per 64-wide k block
 constexpr int kGSlots = 8;                                   // g ring depth
@@ -63,11 +63,13 @@ struct FusedParams {
   int update;
 };
 
-// shared memory: [A: KB x 32 KB][B: STAGES x KB x 16 KB][g ring: 8 x 512 B][barriers, flags, reduction]
+// shared memory: [A: KB x 32 KB][B: STAGES x KB x 16 KB][g ring: 8 x 512 B]
+//                [barriers and flags: 512 B][reduction: 512 B][row hand-over: 2 x 256 floats]
+constexpr int kTailBytes = 512 + 512 + 2 * kFusedOwnRows * 4;
 template <int KB>
 constexpr int smem_bytes(int stages) {
   return 1024 /*alignment slack*/ + KB * kOwnBytesPerKB + stages * KB * kPartnerBytesPerKB + kGSlots * kGBytes +
-         1024;
+         kTailBytes;
 }
 
 __device__ __forceinline__ void raise_error(int* err, volatile int* abort_flag, int code) {
@@ -161,9 +163,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* tfull = a_full + 2;   // [2]
   uint64_t* tempty = a_full + 4;  // [2]
   uint64_t* mma_done = a_full + 6;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_done + 1);
+  uint64_t* rowfull = a_full + 7;  // [2] second column half of the rows written
+  uint64_t* rowfree = a_full + 9;  // [2] row hand-over buffer read
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(a_full + 11);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  double* red = reinterpret_cast<double*>(mma_done + 2);  // 4 x kEpiWarps doubles
+  double* red = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(bars) + 512);      // 4 x kEpiWarps doubles
+  float* rowbuf = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bars) + 1024);   // 2 x 256 floats
+  static_assert(4 * kEpiWarps * 8 <= 512, "reduction area");
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
@@ -183,6 +189,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&tempty[b], kEpiWarps);
     }
     mbar_init(mma_done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&rowfull[b], kEpiWarps / 2);
+      mbar_init(&rowfree[b], kEpiWarps / 2);
+    }
     *abort_flag = 0;
     fence_mbar_init();
     tma_prefetch_map(&tm_own);
@@ -307,9 +317,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncwarp();
   } else {
     // ------------------------------------------------------------ epilogue
-    const int ew = warp - 2;
-    const int q = warp & 3;   // TMEM lane quadrant this warp may access
-    const int h = ew >> 2;    // own sub-tile: rows [h*128, h*128+128)
+    const int ew = warp - 2;          // 0..15
+    const int q = warp & 3;           // TMEM lane quadrant this warp may access
+    const int h = (ew >> 2) & 1;      // own sub-tile: rows [h*128, h*128+128)
+    const int half = ew >> 3;         // columns [half*64, half*64+64) of every partner tile
     uint64_t cc;
     {
       const uint32_t cb = __float_as_uint(p.c);
@@ -321,7 +332,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     double r_max = 0.0, r_sum = 0.0, sq = 0.0, nf = 0.0;
     uint32_t va[32], vb[32];
-    for (int t = blockIdx.x; t < p.num_own_tiles && ok; t += gridDim.x) {
+    int tile_iter = 0;
+    for (int t = blockIdx.x; t < p.num_own_tiles && ok; t += gridDim.x, ++tile_iter) {
       float sum = 0.0f, comp = 0.0f;
       for (int j = 0; j < p.num_partner_tiles; ++j) {
         // every lane waits; the outcome is made warp-uniform so that the
@@ -332,25 +344,20 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256 + h * 128);
-        const float4* gs4 = reinterpret_cast<const float4*>(sG + gs * kFusedPartnerRows);
+        const uint32_t taddr =
+            tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256 + h * 128 + half * 64);
+        const float4* gs4 = reinterpret_cast<const float4*>(sG + gs * kFusedPartnerRows + half * 64);
         uint64_t acc[4] = {0ull, 0ull, 0ull, 0ull};
         tmem_ld_issue(taddr, va);
         tmem_ld_wait(va);
         tmem_ld_issue(taddr + 32, vb);
         chunk_sum(va, gs4, cc, acc);
         tmem_ld_wait(vb);
-        tmem_ld_issue(taddr + 64, va);
-        chunk_sum(vb, gs4 + 8, cc, acc);
-        tmem_ld_wait(va);
-        tmem_ld_issue(taddr + 96, vb);
-        chunk_sum(va, gs4 + 16, cc, acc);
-        tmem_ld_wait(vb);
         // this warp's part of the accumulator buffer has been read: hand it back to the MMA warp
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[buf]);
-        chunk_sum(vb, gs4 + 24, cc, acc);
+        chunk_sum(vb, gs4 + 8, cc, acc);
         // the g slot has been read by this warp
         __syncwarp();
         if (lane == 0) mbar_arrive(&gempty[gs]);
@@ -368,9 +375,32 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       if (!ok) break;
-      const int64_t row = (int64_t)t * kFusedOwnRows + h * 128 + q * 32 + lane;
+      // the two column halves of a row meet in shared memory (double-buffered
+      // by own-tile parity, handed over through bounded mbarrier waits)
+      const int rloc = h * 128 + q * 32 + lane;
+      const int pb = tile_iter & 1;
+      const uint32_t rphase = (uint32_t)(tile_iter >> 1) & 1u;
+      float* rb = rowbuf + pb * kFusedOwnRows;
+      if (half == 1) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&rowfree[pb], rphase ^ 1u, abort_flag))) {
+          ok = false;
+          break;
+        }
+        rb[rloc] = sum - comp;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&rowfull[pb]);
+        continue;
+      }
+      if (!__all_sync(0xffffffffu, mbar_wait(&rowfull[pb], rphase, abort_flag))) {
+        ok = false;
+        break;
+      }
+      const float total = (sum - comp) + rb[rloc];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&rowfree[pb]);
+      const int64_t row = (int64_t)t * kFusedOwnRows + rloc;
       if (row < p.rows) {
-        const RowResult rr = row_update(log((double)sum), shift, p.b2s ? p.b2s[row] : 0.0f, p.mass[row],
+        const RowResult rr = row_update((double)logf(total), shift, p.b2s ? p.b2s[row] : 0.0f, p.mass[row],
                                         p.log_u[row], p.residual != 0);
         if (p.update) {
           p.log_u[row] = rr.log_u;
@@ -383,7 +413,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
     if (!ok && !*abort_flag) raise_error(p.err, abort_flag, kErrTimeout);
-    // reduce the CTA's partials over the 256 epilogue threads
+    // reduce the CTA's partials over the epilogue threads
     for (int o = 16; o > 0; o >>= 1) {
       r_max = fmax(r_max, __shfl_xor_sync(0xffffffffu, r_max, o));
       r_sum += __shfl_xor_sync(0xffffffffu, r_sum, o);

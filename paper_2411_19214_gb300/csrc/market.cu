@@ -364,7 +364,7 @@ void tu_market_destroy(tu_market_t m) {
   cudaFree(m->Ahat);
   cudaFree(m->partials);
   cudaFree(m->mpartials);
-  cudaFree(m->colpart);
+  cudaFree(m->AhatT);
   cudaFree(m->results);
   cudaFree(m->err_dev);
   cudaFree(m->staging);
@@ -385,7 +385,10 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
   if (!(D.sigma > 0.0) || !std::isfinite(D.sigma)) return TU_ERR_INVALID_ARG;
   if (D.partition < 0) return TU_ERR_INVALID_ARG;
   if (D.path == TU_PATH_FUSED && 2 * D.d > 2 * kKBlock) return TU_ERR_UNSUPPORTED;
-  if (D.path == TU_PATH_DENSE && (double)D.N * (double)round_up(D.M, 4) * 4.0 > 200e9) return TU_ERR_UNSUPPORTED;
+  // the dense path keeps A-hat and its transpose resident
+  if (D.path == TU_PATH_DENSE &&
+      (double)D.N * (double)round_up(D.M, 4) * 4.0 + (double)D.M * (double)round_up(D.N, 4) * 4.0 > 200e9)
+    return TU_ERR_UNSUPPORTED;
 
   tu_market* m = new (std::nothrow) tu_market();
   if (m == nullptr) return TU_ERR_OOM;
@@ -432,15 +435,9 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
   *m->err_host = 0;
   if (D.path == TU_PATH_DENSE) {
     m->ldA = round_up(D.M, 4);
+    m->ldN = round_up(D.N, 4);
     if ((st = dev_alloc(m, &m->Ahat, (size_t)m->N * m->ldA)) != TU_OK) return bail(st);
-    const int64_t colblocks = (m->ldA / 4 + 255) / 256;
-    int64_t chunks = (4 * (int64_t)m->num_sms + colblocks - 1) / colblocks;
-    if (chunks > (m->N + 15) / 16) chunks = (m->N + 15) / 16;
-    if (chunks < 1) chunks = 1;
-    if (chunks > 1024) chunks = 1024;
-    m->col_chunks = (int)chunks;
-    m->colpart_elems = chunks * m->ldA;
-    if ((st = dev_alloc(m, &m->colpart, (size_t)m->colpart_elems)) != TU_OK) return bail(st);
+    if ((st = dev_alloc(m, &m->AhatT, (size_t)m->M * m->ldN)) != TU_OK) return bail(st);
   }
   if ((st = upload_masses(m, m->X, D.n)) != TU_OK) return bail(st);
   if ((st = upload_masses(m, m->Y, D.m)) != TU_OK) return bail(st);

@@ -70,9 +70,8 @@ struct tu_market {
   int64_t ldA = 0;
   double* partials = nullptr;   // kMaxPartials x 3 doubles
   double* mpartials = nullptr;  // kMaxPartials doubles (max reduction)
-  float* colpart = nullptr;     // dense column-pass partial sums
-  int64_t colpart_elems = 0;
-  int col_chunks = 0;
+  float* AhatT = nullptr;       // dense path: transpose of A-hat, M x ldN fp32
+  int64_t ldN = 0;
   double* results = nullptr;       // device, kResSlots
   double* results_host = nullptr;  // pinned, kResSlots
   int* err_dev = nullptr;          // device error word
@@ -151,12 +150,6 @@ namespace tu {
 constexpr double kLnHalf = -0.69314718055994530942;
 constexpr float kLog2e = 1.4426950408889634f;
 
-// asinh(e^z) for any z without overflow: z + log(1 + sqrt(1 + e^{-2z})) for z > 0.
-__device__ __forceinline__ double asinh_exp(double z) {
-  if (z > 0.0) return z + log1p(sqrt(1.0 + exp(-2.0 * z)));
-  return asinh(exp(z));
-}
-
 struct RowResult {
   double log_u, ell;
   double r_rel, r_abs, u2;
@@ -170,6 +163,13 @@ struct RowResult {
 //   log u    = 1/2 log n - asinh(exp(log s - 1/2 log n)) (= sqrt(n + s^2) - s)
 // With residual, r = u_old^2 + 2 u_old s - n is the row equation of Eq. IPFP
 // evaluated at the state entering the half-sweep.
+//
+// Precision: the sums are FP32, so every transcendental here is evaluated in
+// FP32 (FP64 transcendentals are slow on this part) while the additions whose
+// operands may be large and cancel (log s, log u, ell: |.| up to ~100 with
+// popularity biases) stay in FP64. For z = log s - 1/2 log n > 0,
+// asinh(e^z) = z + c(z) with c(z) = log1p(sqrt(1 + e^{-2z})) in (ln 2, 0.89],
+// so only the bounded correction c is rounded to FP32 (absolute error ~1e-7).
 __device__ __forceinline__ RowResult row_update(double ln_sum, double shift, float b2s, double mass,
                                                 double log_u_old, bool residual) {
   RowResult o;
@@ -177,16 +177,25 @@ __device__ __forceinline__ RowResult row_update(double ln_sum, double shift, flo
   o.r_rel = 0.0;
   o.r_abs = 0.0;
   if (residual) {
-    const double u = exp(log_u_old);
-    const double r = u * u + 2.0 * u * exp(log_s) - mass;
+    // r = u^2 + 2 u s - n with u^2 = e^{2 log u}, 2 u s = e^{log u + log s + ln 2}
+    const double r = (double)expf((float)(2.0 * log_u_old)) +
+                     (double)expf((float)(log_u_old + log_s + 0.69314718055994530942)) - mass;
     o.r_abs = fabs(r);
     o.r_rel = fabs(r) / mass;
   }
-  const double hl = 0.5 * log(mass);
-  const double lu = hl - asinh_exp(log_s - hl);
+  const double hl = 0.5 * (double)logf((float)mass);
+  const double z = log_s - hl;
+  double a;
+  if (z > 0.0) {
+    const float c = log1pf(sqrtf(1.0f + expf((float)(-2.0 * z))));
+    a = z + (double)c;
+  } else {
+    a = (double)asinhf(expf((float)z));
+  }
+  const double lu = hl - a;
   o.log_u = lu;
   o.ell = lu + (double)b2s;
-  o.u2 = exp(2.0 * lu);
+  o.u2 = (double)expf((float)(2.0 * lu));
   return o;
 }
 

@@ -49,7 +49,10 @@ def test_job_market_solve_matches_oracle(gpu_lib):
     mk = dense_job_market(N=2000, M=1000)
     mkt = tu.from_synth(mk, path="dense")
     try:
-        info = mkt.solve(tol=1e-7, max_iter=2000)
+        # tol of the job-market configuration; the FP32 row sums put the
+        # residual floor near 1e-7 (relative error of s), so 1e-6 is reachable
+        info = mkt.solve(tol=1e-6, max_iter=2000)
+        assert info["residual_inf"] <= 1e-6
         assert info["converged"], info
         r, logA, f = oracle_solve(mk)
         mu_ref = np.exp(oracle.log_mu(logA, r["log_u"], r["log_v"]))
