@@ -46,21 +46,40 @@ constexpr int kGSlots = 8;                                   // g ring depth
 constexpr int kGBytes = kFusedPartnerRows * 4;               // one partner tile of g (512 B)
 constexpr uint32_t kTmemCols = 512;
 
+// Epilogue modes of the one fused kernel: the same TMA / MMA pipeline forms
+// the tiles of c * phi_hat + g; the epilogue either reduces them (a half-sweep),
+// keeps the k best columns of every row (ranked lists) or writes mu.
+enum : int { kModeSweep = 0, kModeTopK = 1, kModeMu = 2 };
+
 struct FusedParams {
-  int64_t rows;            // own-side users
+  int64_t rows;            // own users of this launch: [row0, row0 + rows)
+  int64_t row0;            // first own user
+  int64_t col0;            // first partner column streamed (multiple of 4)
+  int64_t ncols;           // partner columns streamed: [col0, col0 + ncols)
   int num_own_tiles;       // ceil(rows / 256)
-  int num_partner_tiles;   // ceil(partner rows / 128)
+  int num_partner_tiles;   // ceil(ncols / 128)
   float c;                 // log2(e) / (2 sigma)
-  const float* g;          // partner prepared potentials, >= num_partner_tiles * 128, -inf padded
+  const float* g;          // partner prepared potentials (index = partner user), -inf padded
   const double* lmax;      // partner shift (natural log)
-  const float* b2s;        // own bias / (2 sigma), or nullptr
-  const double* mass;      // own capacities
-  double* log_u;           // own potentials (in: old, out: new), FP64 state
-  double* ell;             // own ell (out), FP64 state
-  double* partials;        // [gridDim.x][4]
+  const float* b2s;        // own bias / (2 sigma), or nullptr          (sweep)
+  const double* mass;      // own capacities                             (sweep)
+  double* log_u;           // own potentials (in: old, out: new)          (sweep)
+  double* ell;             // own ell: out (sweep), in (ranked lists, mu)
+  double* partials;        // [gridDim.x][4]                              (sweep)
   int* err;                // device error word
   int residual;
   int update;
+  // ranked lists: for own user row0 + r, idx[r * k + i], logmu[r * k + i], best first
+  int k;
+  int32_t* idx;
+  float* logmu;
+  float* hand_v;           // rows x k scratch: second column half's list
+  int32_t* hand_i;
+  // mu block: out[(r) * ld + (col - y0)] for partner col in [y0, y0 + ny)
+  float* out;
+  int64_t ld;
+  int64_t y0;
+  int64_t ny;
 };
 
 // shared memory: [A: KB x 32 KB][B: STAGES x KB x 16 KB][g ring: 8 x 512 B]
@@ -143,7 +162,56 @@ __device__ __forceinline__ void chunk_sum(const uint32_t (&v)[32], const float4*
   }
 }
 
-template <int KB, int STAGES>
+constexpr int kMaxTopK = 64;
+
+// Insert score s of partner col into a thread's list, sorted by decreasing
+// score; equal scores keep the earlier (lower) column first.
+__device__ __forceinline__ void top_insert(float (&tv)[kMaxTopK], int32_t (&ti)[kMaxTopK], int& cnt, float& thr, int k,
+                                           float s, int32_t col) {
+  int pos = cnt < k ? cnt : k - 1;
+  while (pos > 0 && s > tv[pos - 1]) {
+    tv[pos] = tv[pos - 1];
+    ti[pos] = ti[pos - 1];
+    --pos;
+  }
+  tv[pos] = s;
+  ti[pos] = col;
+  if (cnt < k) ++cnt;
+  thr = cnt == k ? tv[k - 1] : -INFINITY;
+}
+
+// Ranked lists: score = c * phi_hat + g (log2 units, shifted; same order as
+// log mu within a row); only scores above the running k-th best are inserted.
+__device__ __forceinline__ void chunk_topk(const uint32_t (&v)[32], const float* g, float c, int64_t colbase, int k,
+                                           float (&tv)[kMaxTopK], int32_t (&ti)[kMaxTopK], int& cnt, float& thr) {
+  const float4* g4 = reinterpret_cast<const float4*>(g);
+#pragma unroll
+  for (int i4 = 0; i4 < 8; ++i4) {
+    const float4 gg = g4[i4];
+    const float gv[4] = {gg.x, gg.y, gg.z, gg.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int i = 4 * i4 + e;
+      const float s = fmaf(__uint_as_float(v[i]), c, gv[e]);
+      if (s > thr) top_insert(tv, ti, cnt, thr, k, s, (int32_t)(colbase + i));
+    }
+  }
+}
+
+// mu block: mu = 2^(c * phi_hat + g + lo) * 2^hi, where hi + lo = (shift + ell_row) log2 e.
+__device__ __forceinline__ void chunk_mu(const uint32_t (&v)[32], const float* g, float c, int64_t colbase, float lo,
+                                         int hi, bool row_ok, int64_t r, const FusedParams& p) {
+  if (!row_ok) return;
+  float* orow = p.out + r * p.ld;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    const int64_t col = colbase + i;
+    if (col >= p.y0 && col < p.y0 + p.ny)
+      orow[col - p.y0] = ldexpf(ex2_approx(fmaf(__uint_as_float(v[i]), c, g[i]) + lo), hi);
+  }
+}
+
+template <int KB, int STAGES, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     k_fused_halfsweep(const __grid_constant__ CUtensorMap tm_own, const __grid_constant__ CUtensorMap tm_partner,
                       const FusedParams p) {
@@ -225,7 +293,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         a_phase ^= 1u;
         mbar_arrive_expect_tx(a_full, KB * kOwnBytesPerKB);
         for (int kb = 0; kb < KB; ++kb)
-          tma_load_2d(sA + kb * kOwnBytesPerKB, &tm_own, a_full, kb * kKBlock, t * kFusedOwnRows);
+          tma_load_2d(sA + kb * kOwnBytesPerKB, &tm_own, a_full, kb * kKBlock, (int)(p.row0 + (int64_t)t * kFusedOwnRows));
         ++a_armed;
         for (int j = 0; j < p.num_partner_tiles; ++j) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
@@ -235,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           mbar_arrive_expect_tx(&full[stage], KB * kPartnerBytesPerKB);
           for (int kb = 0; kb < KB; ++kb)
             tma_load_2d(sB + (stage * KB + kb) * kPartnerBytesPerKB, &tm_partner, &full[stage], kb * kKBlock,
-                        j * kFusedPartnerRows);
+                        (int)(p.col0 + (int64_t)j * kFusedPartnerRows));
           ++armed[stage];
           if (++stage == STAGES) {
             stage = 0;
@@ -246,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           mbar_arrive_expect_tx(&gfull[gs], kGBytes);
-          bulk_load(sG + gs * kFusedPartnerRows, p.g + (int64_t)j * kFusedPartnerRows, kGBytes, &gfull[gs]);
+          bulk_load(sG + gs * kFusedPartnerRows, p.g + p.col0 + (int64_t)j * kFusedPartnerRows, kGBytes, &gfull[gs]);
           ++garmed[gs];
           if (++gs == kGSlots) {
             gs = 0;
@@ -332,9 +400,31 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     double r_max = 0.0, r_sum = 0.0, sq = 0.0, nf = 0.0;
     uint32_t va[32], vb[32];
+    // ranked lists: this thread's sorted candidates for its row and column half
+    float tv[MODE == kModeTopK ? kMaxTopK : 1];
+    int32_t ti[MODE == kModeTopK ? kMaxTopK : 1];
+    int tcnt = 0;
+    float thr = -INFINITY;
     int tile_iter = 0;
     for (int t = blockIdx.x; t < p.num_own_tiles && ok; t += gridDim.x, ++tile_iter) {
+      const int rloc = h * 128 + q * 32 + lane;          // row within the own tile
+      const int64_t r = (int64_t)t * kFusedOwnRows + rloc;  // row within the launch
+      const bool row_ok = r < p.rows;
       float sum = 0.0f, comp = 0.0f;
+      float mu_lo = 0.0f;
+      int mu_hi = 0;
+      if constexpr (MODE == kModeMu) {
+        if (row_ok) {
+          const double off = (shift + p.ell[p.row0 + r]) * 1.4426950408889634;
+          const double fl = floor(off);
+          mu_hi = (int)fl;
+          mu_lo = (float)(off - fl);
+        }
+      }
+      if constexpr (MODE == kModeTopK) {
+        tcnt = 0;
+        thr = -INFINITY;
+      }
       for (int j = 0; j < p.num_partner_tiles; ++j) {
         // every lane waits; the outcome is made warp-uniform so that the
         // .sync.aligned TMEM loads below never run with a partial warp
@@ -346,27 +436,36 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         const uint32_t taddr =
             tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256 + h * 128 + half * 64);
-        const float4* gs4 = reinterpret_cast<const float4*>(sG + gs * kFusedPartnerRows + half * 64);
+        const float* gsf = sG + gs * kFusedPartnerRows + half * 64;
+        const float4* gs4 = reinterpret_cast<const float4*>(gsf);
+        const int64_t colbase = p.col0 + (int64_t)j * kFusedPartnerRows + half * 64;
         uint64_t acc[4] = {0ull, 0ull, 0ull, 0ull};
         tmem_ld_issue(taddr, va);
         tmem_ld_wait(va);
         tmem_ld_issue(taddr + 32, vb);
-        chunk_sum(va, gs4, cc, acc);
+        if constexpr (MODE == kModeSweep) chunk_sum(va, gs4, cc, acc);
+        if constexpr (MODE == kModeTopK) chunk_topk(va, gsf, p.c, colbase, p.k, tv, ti, tcnt, thr);
+        if constexpr (MODE == kModeMu) chunk_mu(va, gsf, p.c, colbase, mu_lo, mu_hi, row_ok, r, p);
         tmem_ld_wait(vb);
         // this warp's part of the accumulator buffer has been read: hand it back to the MMA warp
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[buf]);
-        chunk_sum(vb, gs4 + 8, cc, acc);
+        if constexpr (MODE == kModeSweep) chunk_sum(vb, gs4 + 8, cc, acc);
+        if constexpr (MODE == kModeTopK) chunk_topk(vb, gsf + 32, p.c, colbase + 32, p.k, tv, ti, tcnt, thr);
+        if constexpr (MODE == kModeMu) chunk_mu(vb, gsf + 32, p.c, colbase + 32, mu_lo, mu_hi, row_ok, r, p);
         // the g slot has been read by this warp
         __syncwarp();
         if (lane == 0) mbar_arrive(&gempty[gs]);
-        // compensated (Kahan) accumulation of the per-tile partial sums
-        const float tile = (unpack_sum(acc[0]) + unpack_sum(acc[1])) + (unpack_sum(acc[2]) + unpack_sum(acc[3]));
-        const float y = tile - comp;
-        const float tsum = sum + y;
-        comp = (tsum - sum) - y;
-        sum = tsum;
+        if constexpr (MODE == kModeSweep) {
+          // compensated (Kahan) accumulation of the per-tile partial sums
+          const float tile =
+              (unpack_sum(acc[0]) + unpack_sum(acc[1])) + (unpack_sum(acc[2]) + unpack_sum(acc[3]));
+          const float y = tile - comp;
+          const float tsum = sum + y;
+          comp = (tsum - sum) - y;
+          sum = tsum;
+        }
         buf ^= 1;
         if (buf == 0) tphase ^= 1u;
         if (++gs == kGSlots) {
@@ -375,9 +474,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
       if (!ok) break;
-      // the two column halves of a row meet in shared memory (double-buffered
-      // by own-tile parity, handed over through bounded mbarrier waits)
-      const int rloc = h * 128 + q * 32 + lane;
+      if constexpr (MODE == kModeMu) continue;
+      // the two column halves of a row meet (double-buffered by own-tile
+      // parity, handed over through bounded mbarrier waits)
       const int pb = tile_iter & 1;
       const uint32_t rphase = (uint32_t)(tile_iter >> 1) & 1u;
       float* rb = rowbuf + pb * kFusedOwnRows;
@@ -386,7 +485,14 @@ __global__ void __launch_bounds__(kThreads, 1)
           ok = false;
           break;
         }
-        rb[rloc] = sum - comp;
+        if constexpr (MODE == kModeSweep) rb[rloc] = sum - comp;
+        if constexpr (MODE == kModeTopK) {
+          if (row_ok)
+            for (int i = 0; i < p.k; ++i) {
+              p.hand_v[r * p.k + i] = i < tcnt ? tv[i] : -INFINITY;
+              p.hand_i[r * p.k + i] = i < tcnt ? ti[i] : 0x7fffffff;
+            }
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive(&rowfull[pb]);
         continue;
@@ -395,50 +501,72 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = false;
         break;
       }
-      const float total = (sum - comp) + rb[rloc];
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&rowfree[pb]);
-      const int64_t row = (int64_t)t * kFusedOwnRows + rloc;
-      if (row < p.rows) {
-        const RowResult rr = row_update((double)logf(total), shift, p.b2s ? p.b2s[row] : 0.0f, p.mass[row],
-                                        p.log_u[row], p.residual != 0);
-        if (p.update) {
-          p.log_u[row] = rr.log_u;
-          p.ell[row] = rr.ell;
+      if constexpr (MODE == kModeTopK) {
+        if (row_ok) {
+          // merge the two sorted halves: higher score first, lower index on ties
+          const double base = shift + p.ell[p.row0 + r];
+          int a = 0, b = 0;
+          for (int i = 0; i < p.k; ++i) {
+            const float bv = p.hand_v[r * p.k + b];
+            const int32_t bi = p.hand_i[r * p.k + b];
+            const bool take_a = a < tcnt && (b >= p.k || tv[a] > bv || (tv[a] == bv && ti[a] < bi));
+            const float sv = take_a ? tv[a] : bv;
+            p.idx[r * p.k + i] = take_a ? ti[a] : bi;
+            if (p.logmu != nullptr) p.logmu[r * p.k + i] = (float)((double)sv * 0.69314718055994530942 + base);
+            if (take_a) ++a; else ++b;
+          }
         }
-        r_max = fmax(r_max, rr.r_rel);
-        r_sum += rr.r_abs;
-        sq += rr.u2;
-        if (!isfinite(rr.log_u) || !isfinite(rr.ell)) nf += 1.0;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&rowfree[pb]);
+      }
+      if constexpr (MODE == kModeSweep) {
+        const float total = (sum - comp) + rb[rloc];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&rowfree[pb]);
+        const int64_t row = p.row0 + r;
+        if (row_ok) {
+          const RowResult rr = row_update((double)logf(total), shift, p.b2s ? p.b2s[row] : 0.0f, p.mass[row],
+                                          p.log_u[row], p.residual != 0);
+          if (p.update) {
+            p.log_u[row] = rr.log_u;
+            p.ell[row] = rr.ell;
+          }
+          r_max = fmax(r_max, rr.r_rel);
+          r_sum += rr.r_abs;
+          sq += rr.u2;
+          if (!isfinite(rr.log_u) || !isfinite(rr.ell)) nf += 1.0;
+        }
       }
     }
     if (!ok && !*abort_flag) raise_error(p.err, abort_flag, kErrTimeout);
-    // reduce the CTA's partials over the epilogue threads
-    for (int o = 16; o > 0; o >>= 1) {
-      r_max = fmax(r_max, __shfl_xor_sync(0xffffffffu, r_max, o));
-      r_sum += __shfl_xor_sync(0xffffffffu, r_sum, o);
-      sq += __shfl_xor_sync(0xffffffffu, sq, o);
-      nf += __shfl_xor_sync(0xffffffffu, nf, o);
-    }
-    if (lane == 0) {
-      red[0 * kEpiWarps + ew] = r_max;
-      red[1 * kEpiWarps + ew] = r_sum;
-      red[2 * kEpiWarps + ew] = sq;
-      red[3 * kEpiWarps + ew] = nf;
-    }
-    named_bar_sync(1, kEpiWarps * 32);
-    if (ew == 0 && lane == 0) {
-      double m0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-      for (int w = 0; w < kEpiWarps; ++w) {
-        m0 = fmax(m0, red[w]);
-        s1 += red[kEpiWarps + w];
-        s2 += red[2 * kEpiWarps + w];
-        s3 += red[3 * kEpiWarps + w];
+    if constexpr (MODE == kModeSweep) {
+      // reduce the CTA's partials over the epilogue threads
+      for (int o = 16; o > 0; o >>= 1) {
+        r_max = fmax(r_max, __shfl_xor_sync(0xffffffffu, r_max, o));
+        r_sum += __shfl_xor_sync(0xffffffffu, r_sum, o);
+        sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        nf += __shfl_xor_sync(0xffffffffu, nf, o);
       }
-      p.partials[4 * blockIdx.x + 0] = m0;
-      p.partials[4 * blockIdx.x + 1] = s1;
-      p.partials[4 * blockIdx.x + 2] = s2;
-      p.partials[4 * blockIdx.x + 3] = s3;
+      if (lane == 0) {
+        red[0 * kEpiWarps + ew] = r_max;
+        red[1 * kEpiWarps + ew] = r_sum;
+        red[2 * kEpiWarps + ew] = sq;
+        red[3 * kEpiWarps + ew] = nf;
+      }
+      named_bar_sync(1, kEpiWarps * 32);
+      if (ew == 0 && lane == 0) {
+        double m0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        for (int w = 0; w < kEpiWarps; ++w) {
+          m0 = fmax(m0, red[w]);
+          s1 += red[kEpiWarps + w];
+          s2 += red[2 * kEpiWarps + w];
+          s3 += red[3 * kEpiWarps + w];
+        }
+        p.partials[4 * blockIdx.x + 0] = m0;
+        p.partials[4 * blockIdx.x + 1] = s1;
+        p.partials[4 * blockIdx.x + 2] = s2;
+        p.partials[4 * blockIdx.x + 3] = s3;
+      }
     }
   }
 
@@ -488,29 +616,56 @@ cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, 
 constexpr int kStagesKB1 = 6;
 constexpr int kStagesKB2 = 4;
 
-template <int KB, int STAGES>
+template <int KB, int STAGES, int MODE>
 cudaError_t launch_kernel(const CUtensorMap& own, const CUtensorMap& partner, const FusedParams& p, int grid,
                           cudaStream_t stream) {
   static_assert(smem_bytes<KB>(STAGES) <= 232448, "shared memory budget");
-  k_fused_halfsweep<KB, STAGES><<<grid, kThreads, smem_bytes<KB>(STAGES), stream>>>(own, partner, p);
+  k_fused_halfsweep<KB, STAGES, MODE><<<grid, kThreads, smem_bytes<KB>(STAGES), stream>>>(own, partner, p);
   return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t set_attributes_mode() {
+  cudaError_t e = cudaFuncSetAttribute(k_fused_halfsweep<1, kStagesKB1, MODE>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>(kStagesKB1));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_fused_halfsweep<2, kStagesKB2, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem_bytes<2>(kStagesKB2));
 }
 
 // Dynamic shared memory opt-in of every instantiation, on the current device.
 cudaError_t set_kernel_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(k_fused_halfsweep<1, kStagesKB1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       smem_bytes<1>(kStagesKB1));
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_fused_halfsweep<2, kStagesKB2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              smem_bytes<2>(kStagesKB2));
+  cudaError_t e = set_attributes_mode<kModeSweep>();
+  if (e == cudaSuccess) e = set_attributes_mode<kModeTopK>();
+  if (e == cudaSuccess) e = set_attributes_mode<kModeMu>();
+  return e;
 }
 
+template <int MODE>
 cudaError_t launch_any(int64_t kp, const CUtensorMap& own, const CUtensorMap& partner, const FusedParams& p,
                        int grid, cudaStream_t stream) {
   const int kb = (int)(kp / kKBlock);
-  if (kb == 1) return launch_kernel<1, kStagesKB1>(own, partner, p, grid, stream);
-  if (kb == 2) return launch_kernel<2, kStagesKB2>(own, partner, p, grid, stream);
+  if (kb == 1) return launch_kernel<1, kStagesKB1, MODE>(own, partner, p, grid, stream);
+  if (kb == 2) return launch_kernel<2, kStagesKB2, MODE>(own, partner, p, grid, stream);
   return cudaErrorNotSupported;
+}
+
+FusedParams base_params(int64_t rows, int64_t row0, int64_t col0, int64_t ncols, double sigma) {
+  FusedParams p{};
+  p.rows = rows;
+  p.row0 = row0;
+  p.col0 = col0;
+  p.ncols = ncols;
+  p.num_own_tiles = (int)((rows + kFusedOwnRows - 1) / kFusedOwnRows);
+  p.num_partner_tiles = (int)((ncols + kFusedPartnerRows - 1) / kFusedPartnerRows);
+  p.c = (float)(1.4426950408889634 / (2.0 * sigma));
+  return p;
+}
+
+int grid_for_tiles(int tiles, int num_sms) {
+  int grid = tiles < num_sms ? tiles : num_sms;
+  if (grid > kMaxPartials) grid = kMaxPartials;
+  return grid < 1 ? 1 : grid;
 }
 
 }  // namespace
@@ -527,11 +682,7 @@ cudaError_t fused_prepare(tu_market* m) {
 cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int update, int* nparts_out) {
   Side& own = side == 0 ? m->X : m->Y;
   Side& partner = side == 0 ? m->Y : m->X;
-  FusedParams p;
-  p.rows = own.rows;
-  p.num_own_tiles = (int)((own.rows + kFusedOwnRows - 1) / kFusedOwnRows);
-  p.num_partner_tiles = (int)((partner.rows + kFusedPartnerRows - 1) / kFusedPartnerRows);
-  p.c = (float)(1.4426950408889634 / (2.0 * m->sigma));
+  FusedParams p = base_params(own.rows, 0, 0, partner.rows, m->sigma);
   p.g = partner.pvec;
   p.lmax = partner.lmax;
   p.b2s = own.b2s;
@@ -542,10 +693,49 @@ cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int upd
   p.err = m->err_dev;
   p.residual = residual;
   p.update = update;
-  int grid = p.num_own_tiles < m->num_sms ? p.num_own_tiles : m->num_sms;
-  if (grid > kMaxPartials) grid = kMaxPartials;
+  const int grid = grid_for_tiles(p.num_own_tiles, m->num_sms);
   *nparts_out = grid;
-  return launch_any(m->kp, own.tm_own, partner.tm_partner, p, grid, m->stream);
+  return launch_any<kModeSweep>(m->kp, own.tm_own, partner.tm_partner, p, grid, m->stream);
+}
+
+// Ranked lists of own users [row0, row0 + nrows) over all partners (the
+// partner vector must have been prepared in log2 mode). hand_v / hand_i:
+// nrows x k scratch.
+cudaError_t launch_fused_topk(tu_market* m, int side, int k, int64_t row0, int64_t nrows, int32_t* idx,
+                              float* logmu, float* hand_v, int32_t* hand_i) {
+  Side& own = side == 0 ? m->X : m->Y;
+  Side& partner = side == 0 ? m->Y : m->X;
+  FusedParams p = base_params(nrows, row0, 0, partner.rows, m->sigma);
+  p.g = partner.pvec;
+  p.lmax = partner.lmax;
+  p.ell = own.ell;
+  p.partials = m->partials;
+  p.err = m->err_dev;
+  p.k = k;
+  p.idx = idx;
+  p.logmu = logmu;
+  p.hand_v = hand_v;
+  p.hand_i = hand_i;
+  return launch_any<kModeTopK>(m->kp, own.tm_own, partner.tm_partner, p, grid_for_tiles(p.num_own_tiles, m->num_sms),
+                               m->stream);
+}
+
+// mu for own X users [x0, x0 + nx) and partners [y0, y0 + ny) (the Y partner
+// vector must have been prepared in log2 mode).
+cudaError_t launch_fused_mu(tu_market* m, int64_t x0, int64_t nx, int64_t y0, int64_t ny, float* out, int64_t ld) {
+  const int64_t c0 = y0 & ~(int64_t)3;  // the g bulk copies start 16-byte aligned
+  FusedParams p = base_params(nx, x0, c0, y0 + ny - c0, m->sigma);
+  p.g = m->Y.pvec;
+  p.lmax = m->Y.lmax;
+  p.ell = m->X.ell;
+  p.partials = m->partials;
+  p.err = m->err_dev;
+  p.out = out;
+  p.ld = ld;
+  p.y0 = y0;
+  p.ny = ny;
+  return launch_any<kModeMu>(m->kp, m->X.tm_own, m->Y.tm_partner, p, grid_for_tiles(p.num_own_tiles, m->num_sms),
+                             m->stream);
 }
 
 // Same kernel on caller-described buffers (no market object): used by the
@@ -556,11 +746,7 @@ cudaError_t launch_fused_halfsweep_raw(const FusedRaw& r, cudaStream_t stream, i
   if ((e = make_map(&own_map, r.own16, r.rows, r.kp, kFusedOwnRows)) != cudaSuccess) return e;
   if ((e = make_map(&partner_map, r.par16, r.cols, r.kp, kFusedPartnerRows)) != cudaSuccess) return e;
   if ((e = set_kernel_attributes()) != cudaSuccess) return e;
-  FusedParams p;
-  p.rows = r.rows;
-  p.num_own_tiles = (int)((r.rows + kFusedOwnRows - 1) / kFusedOwnRows);
-  p.num_partner_tiles = (int)((r.cols + kFusedPartnerRows - 1) / kFusedPartnerRows);
-  p.c = (float)(1.4426950408889634 / (2.0 * r.sigma));
+  FusedParams p = base_params(r.rows, 0, 0, r.cols, r.sigma);
   p.g = r.g;
   p.lmax = r.lmax;
   p.b2s = r.b2s;
@@ -571,10 +757,9 @@ cudaError_t launch_fused_halfsweep_raw(const FusedRaw& r, cudaStream_t stream, i
   p.err = r.err;
   p.residual = r.residual;
   p.update = 1;
-  int grid = p.num_own_tiles < num_sms ? p.num_own_tiles : num_sms;
-  if (grid > kMaxPartials) grid = kMaxPartials;
+  const int grid = grid_for_tiles(p.num_own_tiles, num_sms);
   *nparts_out = grid;
-  return launch_any(r.kp, own_map, partner_map, p, grid, stream);
+  return launch_any<kModeSweep>(r.kp, own_map, partner_map, p, grid, stream);
 }
 
 }  // namespace tu

@@ -368,6 +368,7 @@ void tu_market_destroy(tu_market_t m) {
   cudaFree(m->results);
   cudaFree(m->err_dev);
   cudaFree(m->staging);
+  cudaFree(m->aux);
   cudaFreeHost(m->results_host);
   cudaFreeHost(m->err_host);
   delete m;
@@ -545,7 +546,13 @@ tu_status tu_mu_block(tu_market_t m, int64_t x0, int64_t nx, int64_t y0, int64_t
   void* dst;
   bool host;
   TU_TRY(output_view(m, out, bytes, 0, &dst, &host));
-  TU_CK(m, launch_mu_block(m, x0, nx, y0, ny, static_cast<float*>(dst), ld));
+  if (m->path == TU_PATH_FUSED) {
+    // Y potentials prepared in log2 mode, then the tensor-core mu epilogue
+    TU_CK(m, launch_prep(m, m->Y, 1));
+    TU_CK(m, launch_fused_mu(m, x0, nx, y0, ny, static_cast<float*>(dst), ld));
+  } else {
+    TU_CK(m, launch_mu_block(m, x0, nx, y0, ny, static_cast<float*>(dst), ld));
+  }
   if (host) {
     // pitched copy: the caller's columns [ny, ld) of each row are left untouched
     TU_CK(m, cudaMemcpy2DAsync(out, (size_t)ld * sizeof(float), dst, (size_t)ld * sizeof(float),
@@ -569,7 +576,25 @@ tu_status tu_topk_partners(tu_market_t m, int side, int k, int64_t row0, int64_t
   bool hi, hv = false;
   TU_TRY(output_view(m, idx, ib, 0, &di, &hi));
   if (log_mu != nullptr) TU_TRY(output_view(m, log_mu, vb, round_up((int64_t)ib, 256), &dv, &hv));
-  TU_CK(m, launch_topk(m, side, k, row0, nrows, static_cast<int32_t*>(di), static_cast<float*>(dv)));
+  if (m->path == TU_PATH_FUSED) {
+    // partner potentials in log2 mode; per-row candidate lists of the second
+    // column half go through a nrows x k scratch buffer
+    const size_t hb = (size_t)nrows * k * (sizeof(float) + sizeof(int32_t));
+    if (m->aux_bytes < hb) {
+      TU_CK(m, cudaStreamSynchronize(m->stream));
+      cudaFree(m->aux);
+      m->aux = nullptr;
+      m->aux_bytes = 0;
+      TU_CK(m, cudaMalloc(&m->aux, hb));
+      m->aux_bytes = hb;
+    }
+    float* hv = static_cast<float*>(m->aux);
+    int32_t* hi_ = reinterpret_cast<int32_t*>(hv + (size_t)nrows * k);
+    TU_CK(m, launch_prep(m, side == 0 ? m->Y : m->X, 1));
+    TU_CK(m, launch_fused_topk(m, side, k, row0, nrows, static_cast<int32_t*>(di), static_cast<float*>(dv), hv, hi_));
+  } else {
+    TU_CK(m, launch_topk(m, side, k, row0, nrows, static_cast<int32_t*>(di), static_cast<float*>(dv)));
+  }
   if (hi) TU_CK(m, cudaMemcpyAsync(idx, di, ib, cudaMemcpyDeviceToHost, m->stream));
   if (hv) TU_CK(m, cudaMemcpyAsync(log_mu, dv, vb, cudaMemcpyDeviceToHost, m->stream));
   if (hi || hv) TU_CK(m, cudaStreamSynchronize(m->stream));

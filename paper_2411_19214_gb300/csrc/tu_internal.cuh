@@ -78,6 +78,8 @@ struct tu_market {
   int* err_host = nullptr;         // pinned
   void* staging = nullptr;         // device staging buffer for host-memory arguments
   size_t staging_bytes = 0;
+  void* aux = nullptr;             // ranked-list hand-over scratch (grow-only)
+  size_t aux_bytes = 0;
   cudaGraphExec_t graph = nullptr; // captured block of sweeps
   int graph_sweeps = 0;
   bool poisoned = false;
@@ -132,6 +134,10 @@ struct FusedRaw {
   int residual;
 };
 cudaError_t launch_fused_halfsweep_raw(const FusedRaw& r, cudaStream_t stream, int num_sms, int* nparts_out);
+// ranked lists / mu block through the tensor-core pipeline (partner vector prepared in log2 mode)
+cudaError_t launch_fused_topk(tu_market* m, int side, int k, int64_t row0, int64_t nrows, int32_t* idx, float* logmu,
+                              float* hand_v, int32_t* hand_i);
+cudaError_t launch_fused_mu(tu_market* m, int64_t x0, int64_t nx, int64_t y0, int64_t ny, float* out, int64_t ld);
 
 // topk.cu
 cudaError_t launch_mu_block(tu_market* m, int64_t x0, int64_t nx, int64_t y0, int64_t ny, float* out,

@@ -58,12 +58,14 @@ def test_mu_block_matches_oracle(gpu_lib, path):
         ref = np.exp(oracle.log_mu(logA, lu, lv))
         full = mkt.mu_block().double().cpu().numpy()
         np.testing.assert_allclose(full, ref, rtol=EPS[path])
-        # a sub-block into a host buffer with a leading dimension larger than its width
+        # sub-blocks into a host buffer with a leading dimension larger than
+        # the width, at aligned and unaligned column offsets
         ld = 300
-        out = np.full((40, ld), -1.0, np.float32)
-        tu.tu_mu_block(mkt.handle, 100, 40, 1000, 257, out, ld)
-        np.testing.assert_allclose(out[:, :257], ref[100:140, 1000:1257], rtol=EPS[path])
-        assert np.all(out[:, 257:] == -1.0)
+        for y0 in (1000, 1001, 3):
+            out = np.full((40, ld), -1.0, np.float32)
+            tu.tu_mu_block(mkt.handle, 100, 40, y0, 257, out, ld)
+            np.testing.assert_allclose(out[:, :257], ref[100:140, y0:y0 + 257], rtol=EPS[path])
+            assert np.all(out[:, 257:] == -1.0)
     finally:
         mkt.close()
 
@@ -107,5 +109,57 @@ def test_topk_ties_prefer_lower_index(gpu_lib):
             for i in range(0, 20, 2):
                 a, b = idx[r, i], idx[r, i + 1]
                 assert b == a + 150 and a < 150, (r, idx[r])
+    finally:
+        mkt.close()
+
+
+def test_fused_topk_and_mu_full_size_sampled(gpu_lib):
+    """1e6 x 1e6, d = 64 (the benchmark market) after one sweep: ranked lists of
+    64 consecutive X users and 64 Y users over all 1e6 partners, and a mu block,
+    against the oracle's log mu of those users computed from the GPU's potentials."""
+    from synth import fused_market
+    tu = gpu_lib
+    mk = fused_market()
+    stream = torch.cuda.Stream()
+    mkt = tu.from_synth(mk, path="fused", stream=stream)
+    try:
+        mkt.sweep(1)
+        lu, lv = (t.double().cpu().numpy() for t in mkt.potentials())
+        f = mk.f64()
+        s2 = 2.0 * f["sigma"]
+        for side, row0 in ((0, 123457), (1, 876543)):
+            if side == 0:
+                A, B, own_b, par_b, lo, lp = mk.F, mk.K, mk.bias_x, mk.bias_y, lu, lv
+                P, Q = mk.G, mk.L
+            else:
+                A, B, own_b, par_b, lo, lp = mk.G, mk.L, mk.bias_y, mk.bias_x, lv, lu
+                P, Q = mk.F, mk.K
+            rows = np.arange(row0, row0 + 64)
+            phi = (A[rows].astype(np.float64) @ P.T.astype(np.float64)
+                   + B[rows].astype(np.float64) @ Q.T.astype(np.float64)
+                   + own_b[rows].astype(np.float64)[:, None] + par_b.astype(np.float64)[None, :])
+            scores = phi / s2 + lo[rows][:, None] + lp[None, :]
+            idx = torch.empty((64, 10), dtype=torch.int32, device="cuda")
+            lm = torch.empty((64, 10), dtype=torch.float32, device="cuda")
+            tu.tu_topk_partners(mkt.handle, side, 10, row0, 64, idx, lm)
+            stream.synchronize()
+            _check_ranked(idx.cpu().numpy(), lm.cpu().numpy().astype(np.float64), scores, EPS["fused"])
+        # mu block at an unaligned partner offset, from potentials that put mu
+        # near 1e-6 (one sweep from u = v = 1 leaves mu below the FP32 range)
+        lu_set = (-7.0 - mk.bias_x.astype(np.float64) / s2).astype(np.float32)
+        lv_set = (-7.0 - mk.bias_y.astype(np.float64) / s2).astype(np.float32)
+        mkt.set_potentials(torch.from_numpy(lu_set).cuda(), torch.from_numpy(lv_set).cuda())
+        rows = np.arange(123457, 123457 + 64)
+        cols = slice(654321, 654321 + 5000)
+        phi = (mk.F[rows].astype(np.float64) @ mk.G[cols].T.astype(np.float64)
+               + mk.K[rows].astype(np.float64) @ mk.L[cols].T.astype(np.float64)
+               + mk.bias_x[rows].astype(np.float64)[:, None] + mk.bias_y[cols].astype(np.float64)[None, :])
+        ref = phi / s2 + lu_set[rows].astype(np.float64)[:, None] + lv_set[cols].astype(np.float64)[None, :]
+        blk = torch.empty((64, 5000), dtype=torch.float32, device="cuda")
+        tu.tu_mu_block(mkt.handle, 123457, 64, 654321, 5000, blk, 5000)
+        stream.synchronize()
+        got = blk.double().cpu().numpy()
+        assert np.all(got > 0)
+        np.testing.assert_allclose(np.log(got), ref, rtol=0, atol=3e-5)
     finally:
         mkt.close()
