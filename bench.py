@@ -273,6 +273,66 @@ def to_device_factors(mk, device, pinned=False):
     return [conv(a) for a in (mk.F, mk.K, mk.G, mk.L)]
 
 
+def plain_fp32_sweep(mk, dev, stream, rows_per_part: int = 8192, parts: int = 2) -> dict:
+    """The comparison the method is measured against: Alg. 2 done literally in
+    FP32 on the same GPU (cuBLAS SGEMM with TF32 disabled for F_j G^T + K_j L^T,
+    the B x M block materialised in HBM, logsumexp, the closed-form update),
+    timed on `parts` partitions of `rows_per_part` users after one warm-up
+    partition and extrapolated to a full sweep (both half-sweeps cost the same
+    for N = M)."""
+    import math as _m
+
+    import numpy as np
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        with torch.cuda.stream(stream):
+            f32 = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dev)  # noqa: E731
+            F, K, G, L = f32(mk.F), f32(mk.K), f32(mk.G), f32(mk.L)
+            bx = f32(mk.bias_x) if mk.bias_x is not None else torch.zeros(mk.N, device=dev)
+            by = f32(mk.bias_y) if mk.bias_y is not None else torch.zeros(mk.M, device=dev)
+            n = torch.from_numpy(mk.n.astype(np.float32)).to(dev)
+            lv = torch.zeros(mk.M, device=dev)
+            inv2s = 1.0 / (2.0 * mk.sigma)
+
+            def partition(j0):
+                j1 = min(mk.N, j0 + rows_per_part)
+                logits = F[j0:j1] @ G.T
+                logits.addmm_(K[j0:j1], L.T)
+                logits += bx[j0:j1, None]
+                logits += by[None, :]
+                logits *= inv2s
+                logits += lv[None, :]
+                log_s = torch.logsumexp(logits, dim=1) + _m.log(0.5)
+                del logits
+                hl = 0.5 * torch.log(n[j0:j1])
+                z = log_s - hl
+                a = torch.where(z > 0, z + torch.log1p(torch.sqrt(1 + torch.exp(-2 * z))), torch.asinh(torch.exp(z)))
+                return hl - a
+
+            partition(0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for p in range(parts):
+                partition((p + 1) * rows_per_part)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            del F, K, G, L
+        per_row_ms = ms / (parts * rows_per_part)
+        sweep_ms = per_row_ms * (mk.N + mk.M)
+        return {"ms_per_sweep": sweep_ms, "sweeps_per_s": 1e3 / sweep_ms,
+                "sample": f"{parts} partitions of {rows_per_part} users of the X half-sweep (Alg. 2 in FP32, cuBLAS "
+                          f"SGEMM without TF32, logits materialised, logsumexp) timed with CUDA events, "
+                          f"extrapolated to N + M users per sweep"}
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+        torch.cuda.empty_cache()
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -350,6 +410,21 @@ def run_ours(args):
             ms = float(t.item())
         residual = tu.tu_ipfp_sweep(h, 0, residual=True)
 
+        # output stage: ranked top-10 lists for every X user (one pass over N x M)
+        topk_ms = None
+        if cfg["path"] == "fused" and not args.no_extras:
+            idx = torch.empty((mk.N, 10), dtype=torch.int32, device=dev)
+            lmv = torch.empty((mk.N, 10), dtype=torch.float32, device=dev)
+            tu.tu_topk_partners(h, 0, 10, 0, min(mk.N, 4096), idx, lmv)  # warm
+            torch.cuda.synchronize()
+            t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t0e.record(stream)
+            tu.tu_topk_partners(h, 0, 10, 0, mk.N, idx, lmv)
+            t1e.record(stream)
+            torch.cuda.synchronize()
+            topk_ms = t0e.elapsed_time(t1e)
+            del idx, lmv
+
         # end to end through the C ABI with host buffers: H2D of the step's
         # factors from pinned memory, one sweep, D2H of the potentials
         Fh, Kh, Gh, Lh = to_device_factors(mk, dev, pinned=True)
@@ -377,6 +452,11 @@ def run_ours(args):
         d2h = (mk.N + mk.M) * 4
     finally:
         tu.tu_market_destroy(h)
+
+    # the plain FP32 blocked IPFP on the same GPU (comparison only)
+    plain = None
+    if cfg["path"] == "fused" and not args.no_extras and rank == 0:
+        plain = plain_fp32_sweep(mk, dev, stream)
 
     if rank != 0:
         if world > 1:
@@ -431,6 +511,12 @@ def run_ours(args):
                             "tu_get_potentials(pinned host)"}}
     if roofline_exp is not None:
         line["roofline_exp"] = roofline_exp
+    if plain is not None:
+        plain["speedup_of_value"] = sweeps_per_s / world / plain["sweeps_per_s"]
+        line["plain_fp32"] = plain
+    if topk_ms is not None:
+        line["topk_all_users"] = {"ms": topk_ms, "k": 10, "users": mk.N,
+                                  "what": "tu_topk_partners(side X, k=10) for every X user over all partners"}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
@@ -447,6 +533,8 @@ def main():
     ap.add_argument("--workload", choices=["fused", "dense"], default="fused")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the plain-FP32 comparison and the ranked-list timing")
     ap.add_argument("--shape", default=None,
                     help="N,M override of the workload's sizes (same recipe; for small profiling cases)")
     args = ap.parse_args()
