@@ -165,10 +165,12 @@ __device__ __forceinline__ void chunk_sum(const uint32_t (&v)[32], const float4*
 constexpr int kMaxTopK = 64;
 
 // Insert score s of partner col into a thread's list, sorted by decreasing
-// score; equal scores keep the earlier (lower) column first.
-__device__ __forceinline__ void top_insert(float (&tv)[kMaxTopK], int32_t (&ti)[kMaxTopK], int& cnt, float& thr, int k,
-                                           float s, int32_t col) {
-  int pos = cnt < k ? cnt : k - 1;
+// score; equal scores keep the earlier (lower) column first. Returns the new
+// threshold (the k-th best score, -inf while the list is not full). Kept out
+// of line: it runs rarely, and one copy keeps the hot loop small.
+__device__ __noinline__ float top_insert(float* tv, int32_t* ti, int* cnt, int k, float s, int32_t col) {
+  int c = *cnt;
+  int pos = c < k ? c : k - 1;
   while (pos > 0 && s > tv[pos - 1]) {
     tv[pos] = tv[pos - 1];
     ti[pos] = ti[pos - 1];
@@ -176,25 +178,31 @@ __device__ __forceinline__ void top_insert(float (&tv)[kMaxTopK], int32_t (&ti)[
   }
   tv[pos] = s;
   ti[pos] = col;
-  if (cnt < k) ++cnt;
-  thr = cnt == k ? tv[k - 1] : -INFINITY;
+  if (c < k) *cnt = ++c;
+  return c == k ? tv[k - 1] : -INFINITY;
 }
 
 // Ranked lists: score = c * phi_hat + g (log2 units, shifted; same order as
-// log mu within a row); only scores above the running k-th best are inserted.
+// log mu within a row). The chunk's maximum is compared with the running k-th
+// best first, so most chunks cost one FFMA and one max per column.
 __device__ __forceinline__ void chunk_topk(const uint32_t (&v)[32], const float* g, float c, int64_t colbase, int k,
-                                           float (&tv)[kMaxTopK], int32_t (&ti)[kMaxTopK], int& cnt, float& thr) {
+                                           float* tv, int32_t* ti, int* cnt, float& thr) {
   const float4* g4 = reinterpret_cast<const float4*>(g);
+  float s[32];
+  float mx = -INFINITY;
 #pragma unroll
   for (int i4 = 0; i4 < 8; ++i4) {
     const float4 gg = g4[i4];
-    const float gv[4] = {gg.x, gg.y, gg.z, gg.w};
+    s[4 * i4 + 0] = fmaf(__uint_as_float(v[4 * i4 + 0]), c, gg.x);
+    s[4 * i4 + 1] = fmaf(__uint_as_float(v[4 * i4 + 1]), c, gg.y);
+    s[4 * i4 + 2] = fmaf(__uint_as_float(v[4 * i4 + 2]), c, gg.z);
+    s[4 * i4 + 3] = fmaf(__uint_as_float(v[4 * i4 + 3]), c, gg.w);
+    mx = fmaxf(mx, fmaxf(fmaxf(s[4 * i4 + 0], s[4 * i4 + 1]), fmaxf(s[4 * i4 + 2], s[4 * i4 + 3])));
+  }
+  if (mx > thr) {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int i = 4 * i4 + e;
-      const float s = fmaf(__uint_as_float(v[i]), c, gv[e]);
-      if (s > thr) top_insert(tv, ti, cnt, thr, k, s, (int32_t)(colbase + i));
-    }
+    for (int e = 0; e < 32; ++e)
+      if (s[e] > thr) thr = top_insert(tv, ti, cnt, k, s[e], (int32_t)(colbase + e));
   }
 }
 
@@ -444,7 +452,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tmem_ld_wait(va);
         tmem_ld_issue(taddr + 32, vb);
         if constexpr (MODE == kModeSweep) chunk_sum(va, gs4, cc, acc);
-        if constexpr (MODE == kModeTopK) chunk_topk(va, gsf, p.c, colbase, p.k, tv, ti, tcnt, thr);
+        if constexpr (MODE == kModeTopK) chunk_topk(va, gsf, p.c, colbase, p.k, tv, ti, &tcnt, thr);
         if constexpr (MODE == kModeMu) chunk_mu(va, gsf, p.c, colbase, mu_lo, mu_hi, row_ok, r, p);
         tmem_ld_wait(vb);
         // this warp's part of the accumulator buffer has been read: hand it back to the MMA warp
@@ -452,7 +460,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[buf]);
         if constexpr (MODE == kModeSweep) chunk_sum(vb, gs4 + 8, cc, acc);
-        if constexpr (MODE == kModeTopK) chunk_topk(vb, gsf + 32, p.c, colbase + 32, p.k, tv, ti, tcnt, thr);
+        if constexpr (MODE == kModeTopK) chunk_topk(vb, gsf + 32, p.c, colbase + 32, p.k, tv, ti, &tcnt, thr);
         if constexpr (MODE == kModeMu) chunk_mu(vb, gsf + 32, p.c, colbase + 32, mu_lo, mu_hi, row_ok, r, p);
         // the g slot has been read by this warp
         __syncwarp();
