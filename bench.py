@@ -333,6 +333,34 @@ def plain_fp32_sweep(mk, dev, stream, rows_per_part: int = 8192, parts: int = 2)
         torch.cuda.empty_cache()
 
 
+def serving_block(rates, count_per_rate, budget_gb: float = 64.0) -> dict:
+    """Serving: Poisson streams of solve requests (sizes log-uniform in
+    [1000, 200000] per side, d in {32, 64}, bf16, 30 % warm-started re-solves of
+    perturbed factors) replayed in real time through the continuous-batching
+    server; latency from arrival to the top-10 reply."""
+    from paper_2411_19214_gb300 import serve
+    from synth import serving_workload
+    out = {}
+    for rate, count in zip(rates, count_per_rate):
+        work = serving_workload(count, rate=rate, seed=1004)
+        reqs = [serve.SolveRequest(rid=w["rid"], arrival=w["t"], F=w["F"], K=w["K"], G=w["G"], L=w["L"], n=w["n"],
+                                   m=w["m"], sigma=w["sigma"], key=w["key"]) for w in work]
+        srv = serve.Server(hbm_budget_bytes=int(budget_gb * (1 << 30)), tol=1e-6, max_sweeps=200,
+                           sweeps_per_step=8, k=10)
+        t0 = time.perf_counter()
+        res = srv.run(reqs, realtime=True)
+        wall = time.perf_counter() - t0
+        srv.close()
+        lat = serve.percentiles([r.latency for r in res])
+        out[f"{rate:g}/s"] = {"requests": len(res), "p50_ms": 1e3 * lat["p50"], "p99_ms": 1e3 * lat["p99"],
+                              "mean_ms": 1e3 * lat["mean"], "served_per_s": len(res) / wall,
+                              "offered_per_s": rate, "window_s": reqs[-1].arrival,
+                              "not_converged_at_200_sweeps": sum(not r.converged for r in res),
+                              "warm_resolves": sum(r.warm for r in res), "peak_active": srv.stats["peak_active"],
+                              "overloaded": len(res) / wall < 0.95 * rate}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -455,8 +483,10 @@ def run_ours(args):
 
     # the plain FP32 blocked IPFP on the same GPU (comparison only)
     plain = None
+    serving = None
     if cfg["path"] == "fused" and not args.no_extras and rank == 0:
         plain = plain_fp32_sweep(mk, dev, stream)
+        serving = serving_block((20.0, 200.0), (60, 200))
 
     if rank != 0:
         if world > 1:
@@ -514,6 +544,8 @@ def run_ours(args):
     if plain is not None:
         plain["speedup_of_value"] = sweeps_per_s / world / plain["sweeps_per_s"]
         line["plain_fp32"] = plain
+    if serving is not None:
+        line["serving"] = serving
     if topk_ms is not None:
         line["topk_all_users"] = {"ms": topk_ms, "k": 10, "users": mk.N,
                                   "what": "tu_topk_partners(side X, k=10) for every X user over all partners"}

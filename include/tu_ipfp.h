@@ -145,6 +145,21 @@ tu_status tu_topk_partners(tu_market_t mkt, int side, int k, int64_t row0, int64
 tu_status tu_get_potentials(tu_market_t mkt, float* log_u, float* log_v);
 tu_status tu_set_potentials(tu_market_t mkt, const float* log_u, const float* log_v);
 
+/* Non-blocking progress query for serving loops that keep many markets busy
+ * from one host thread (no counterpart in the paper). tu_ipfp_sweep without
+ * residual_out only enqueues work; this call checks, without waiting, whether
+ * that work has finished. *idle = 1 when every sweep enqueued so far is done;
+ * then *residual = max_x |r_x| / n_x of the state that entered the last sweep
+ * (row equations of Eq. IPFP, reduced in FP64 inside that sweep's X
+ * half-sweep), *match_count = sum m - sum v^2 after it, and *sweeps = sweeps
+ * completed since creation. While busy (*idle = 0) the other outputs are not
+ * written. Any output pointer may be NULL. */
+tu_status tu_market_query(tu_market_t mkt, int* idle, double* residual, double* match_count, int64_t* sweeps);
+
+/* Device memory a market of this shape holds (bytes), for admission control:
+ * the packed factors, the per-user state and the dense matrices if any. */
+int64_t tu_market_footprint(int64_t N, int64_t M, int64_t d, int path);
+
 /* Kernel timing for benchmarks (no counterpart in the paper). While enabled,
  * every half-sweep pass records a CUDA event pair on the market's stream
  * around its main kernel (fused: the tcgen05 half-sweep; dense: the row pass,

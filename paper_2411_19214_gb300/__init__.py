@@ -70,6 +70,9 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tu_get_potentials": (I32, [V, V, V]),
         "tu_set_potentials": (I32, [V, V, V]),
         "tu_fused_halfsweep_noalloc": (I32, [I64, I64, I64, V, V, V, V, V, V, V, D, V, ctypes.POINTER(D), V]),
+        "tu_market_query": (I32, [V, ctypes.POINTER(I32), ctypes.POINTER(D), ctypes.POINTER(D),
+                                  ctypes.POINTER(I64)]),
+        "tu_market_footprint": (I64, [I64, I64, I64, I32]),
         "tu_profile_enable": (I32, [V, I32]),
         "tu_profile_read": (I32, [V, ctypes.POINTER(D), ctypes.POINTER(I64)]),
         "tu_market_destroy": (None, [V]),
@@ -241,6 +244,25 @@ def tu_fused_halfsweep_noalloc(rows: int, cols: int, kp: int, own_packed, partne
                                            ctypes.byref(r) if residual else None, _stream_handle(stream))
     _check(st, "tu_fused_halfsweep_noalloc")
     return r.value if residual else None
+
+
+def tu_market_query(h: int):
+    """Non-blocking: (idle, residual of the state entering the last sweep,
+    match count, sweeps completed); the last three are None while busy."""
+    idle = ctypes.c_int(0)
+    res = ctypes.c_double(float("nan"))
+    match = ctypes.c_double(float("nan"))
+    sweeps = ctypes.c_int64(0)
+    _check(load().tu_market_query(h, ctypes.byref(idle), ctypes.byref(res), ctypes.byref(match),
+                                  ctypes.byref(sweeps)), "tu_market_query", h)
+    if not idle.value:
+        return False, None, None, None
+    return True, res.value, match.value, sweeps.value
+
+
+def tu_market_footprint(N: int, M: int, d: int, path: str = "fused") -> int:
+    """Device bytes a market of this shape holds (admission control)."""
+    return int(load().tu_market_footprint(int(N), int(M), int(d), TU_PATH_FUSED if path == "fused" else TU_PATH_DENSE))
 
 
 def tu_profile_enable(h: int, enable: bool = True) -> None:

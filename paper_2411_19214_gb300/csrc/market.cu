@@ -369,6 +369,8 @@ void tu_market_destroy(tu_market_t m) {
   cudaFree(m->err_dev);
   cudaFree(m->staging);
   cudaFree(m->aux);
+  if (m->done_ev) cudaEventDestroy(m->done_ev);
+  cudaFreeHost(m->query_host);
   cudaFreeHost(m->results_host);
   cudaFreeHost(m->err_host);
   delete m;
@@ -429,6 +431,7 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
   if ((st = dev_alloc(m, &m->results, (size_t)kResSlots)) != TU_OK) return bail(st);
   if ((st = dev_alloc(m, &m->err_dev, 1)) != TU_OK) return bail(st);
   if (cudaMallocHost(&m->results_host, kResSlots * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&m->query_host, (kResSlots + 1) * sizeof(double)) != cudaSuccess ||
       cudaMallocHost(&m->err_host, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     return bail(TU_ERR_OOM);
@@ -481,10 +484,56 @@ tu_status tu_ipfp_sweep(tu_market_t m, int nsweeps, double* residual_out) {
   if (nsweeps < 0) return fail(m, TU_ERR_INVALID_ARG, "nsweeps < 0");
   TU_TRY(clear_results(m));
   TU_TRY(enqueue_sweeps(m, nsweeps));
+  m->sweeps_enqueued += nsweeps;
   if (residual_out != nullptr) {
     TU_TRY(certify(m, residual_out, nullptr));
+  } else if (nsweeps > 0) {
+    // snapshot of the FP64 results for tu_market_query, then the completion event
+    TU_CK(m, cudaMemcpyAsync(m->query_host, m->results, kResSlots * sizeof(double), cudaMemcpyDeviceToHost,
+                             m->stream));
+    TU_CK(m, cudaMemcpyAsync(m->query_host + kResSlots, m->err_dev, sizeof(int), cudaMemcpyDeviceToHost,
+                             m->stream));
+    if (m->done_ev == nullptr) TU_CK(m, cudaEventCreateWithFlags(&m->done_ev, cudaEventDisableTiming));
+    TU_CK(m, cudaEventRecord(m->done_ev, m->stream));
+    m->query_sweeps = m->sweeps_enqueued;
   }
   return TU_OK;
+}
+
+tu_status tu_market_query(tu_market_t m, int* idle, double* residual, double* match_count, int64_t* sweeps) {
+  TU_TRY(check_live(m));
+  if (m->done_ev != nullptr) {
+    const cudaError_t e = cudaEventQuery(m->done_ev);
+    if (e == cudaErrorNotReady) {
+      if (idle) *idle = 0;
+      return TU_OK;
+    }
+    if (e != cudaSuccess) return fail_cuda(m, e, "cudaEventQuery");
+    int err_word = 0;
+    memcpy(&err_word, m->query_host + kResSlots, sizeof(int));
+    if (err_word == kErrTimeout) return fail(m, TU_ERR_TIMEOUT, "a device-side wait ran out of its time limit");
+    if (m->query_host[kResNonfin] > 0.0) return fail(m, TU_ERR_NONFINITE, "a computed potential is not finite");
+  }
+  if (idle) *idle = 1;
+  if (residual) *residual = m->done_ev ? m->query_host[kResXInf] : INFINITY;
+  if (match_count) *match_count = m->done_ev ? m->Y.sum_mass - m->query_host[kResYSq] : 0.0;
+  if (sweeps) *sweeps = m->query_sweeps;
+  return TU_OK;
+}
+
+int64_t tu_market_footprint(int64_t N, int64_t M, int64_t d, int path) {
+  if (N < 1 || M < 1 || d < 1) return 0;
+  const int64_t kp = round_up(2 * d, kKBlock);
+  const int64_t np = round_up(N, kRowPad), mp = round_up(M, kRowPad);
+  int64_t bytes = (np + mp) * (8 + 8 + 4 + 8 + 4) + (int64_t)kMaxPartials * 5 * 8 + 4096;
+  // staging for host factor uploads (two matrices of the larger side)
+  bytes += 2 * (N > M ? N : M) * d * 4;
+  if (path == TU_PATH_FUSED) {
+    bytes += (N + M) * kp * 2;
+  } else {
+    bytes += (N + M) * kp * 4 + N * round_up(M, 4) * 4 + M * round_up(N, 4) * 4;
+  }
+  return bytes;
 }
 
 tu_status tu_ipfp_solve(tu_market_t m, double tol, int max_iter, int warm_start, tu_solve_info* info) {
@@ -515,6 +564,7 @@ tu_status tu_ipfp_solve(tu_market_t m, double tol, int max_iter, int warm_start,
     while (done < max_iter) {
       const int k = (max_iter - done) < block ? (max_iter - done) : block;
       TU_TRY(enqueue_sweeps(m, k));
+      m->sweeps_enqueued += k;
       TU_TRY(read_results(m));
       done += k;
       if (m->results_host[kResXInf] <= tol) break;

@@ -85,6 +85,11 @@ struct tu_market {
   bool poisoned = false;
   std::string last_error;
   // benchmark timing (tu_profile_enable / tu_profile_read)
+  // serving: completion of the last asynchronous tu_ipfp_sweep (tu_market_query)
+  cudaEvent_t done_ev = nullptr;
+  double* query_host = nullptr;  // pinned: kResSlots doubles + the error word
+  int64_t sweeps_enqueued = 0;
+  int64_t query_sweeps = 0;
   bool profiling = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
   size_t ev_used = 0;

@@ -17,4 +17,5 @@ from .markets import (  # noqa: F401
     paper_shaped_market,
     batched_market_sizes,
     serving_request_sizes,
+    serving_workload,
 )

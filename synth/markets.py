@@ -183,6 +183,40 @@ def batched_market_sizes(count: int = 512, lo: int = 100, hi: int = 50_000,
     return [(int(a), int(b), k) for (a, b), k in zip(sizes, kinds)]
 
 
+def serving_workload(count: int, rate: float = 200.0, lo: int = 1000, hi: int = 200_000, resolve_frac: float = 0.3,
+                     perturb_std: float = 0.01, sigma: float = 1.0, seed: int = 1004, dims=(32, 64)) -> list:
+    """A Poisson stream of solve requests: arrival times (rate per second),
+    per-side sizes log-uniform in [lo, hi], d drawn from `dims`, bf16 factors
+    N(0, 1/d) sliced from a seeded pool, capacities uniform on {1..3}, and a
+    fraction of re-solves that repeat an earlier request's market with its
+    factors perturbed by N(0, perturb_std^2) (same key, so a server can warm
+    start). Returns a list of dicts with rid, t, key, F, K, G, L, n, m, sigma."""
+    rng = np.random.default_rng(seed)
+    pools = {}
+    for d in dims:
+        prng = np.random.default_rng(seed + 17 * d)
+        pools[d] = [round_to_bf16(_factors(prng, hi, d, "normal")) for _ in range(4)]
+    t = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    out = []
+    for i in range(count):
+        if out and rng.random() < resolve_frac:
+            base = out[int(rng.integers(0, len(out)))]
+            d = base["F"].shape[1]
+            mats = [round_to_bf16(a + rng.normal(0.0, perturb_std, size=a.shape).astype(np.float32))
+                    for a in (base["F"], base["K"], base["G"], base["L"])]
+            out.append(dict(rid=i, t=float(t[i]), key=base["key"], F=mats[0], K=mats[1], G=mats[2], L=mats[3],
+                            n=base["n"], m=base["m"], sigma=sigma, resolve=True))
+            continue
+        N, M = (int(v) for v in np.rint(np.exp(rng.uniform(math.log(lo), math.log(hi), size=2))))
+        d = int(rng.choice(dims))
+        ox, oy = int(rng.integers(0, hi - N + 1)), int(rng.integers(0, hi - M + 1))
+        F, K, G, L = pools[d]
+        out.append(dict(rid=i, t=float(t[i]), key=f"market{i}", F=F[ox:ox + N], K=K[ox:ox + N],
+                        G=G[oy:oy + M], L=L[oy:oy + M], n=_capacities(rng, N, "uniform1to3"),
+                        m=_capacities(rng, M, "uniform1to3"), sigma=sigma, resolve=False))
+    return out
+
+
 def serving_request_sizes(count: int, rate: float = 200.0, lo: int = 1000, hi: int = 200_000,
                           seed: int = 1004) -> list:
     """Poisson arrival times and log-uniform sizes of a stream of solve requests."""

@@ -1,0 +1,82 @@
+"""The continuous-batching serving loop (GPU).
+
+* every result is the same alone and in the mix (markets overlap on the device
+  on separate streams; each market's arithmetic is deterministic);
+* a re-solve warm-started from the resident potentials needs fewer sweeps and
+  reaches the same fixed point as a cold solve;
+* admission never exceeds the HBM budget, and every request completes.
+"""
+
+import numpy as np
+import pytest
+
+from synth import make_market, round_to_bf16
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(serve, specs, seed=0):
+    reqs = []
+    for i, (N, M, d) in enumerate(specs):
+        mk = make_market(N, M, d, sigma=0.8, seed=seed + i, bias_x=True, bias_y=True, n_kind="uniform1to3",
+                         m_kind="uniform1to3", dtype="bf16")
+        reqs.append(serve.SolveRequest(rid=i, arrival=0.0, F=mk.F, K=mk.K, G=mk.G, L=mk.L, n=mk.n, m=mk.m,
+                                       sigma=mk.sigma, bias_x=mk.bias_x, bias_y=mk.bias_y))
+    return reqs
+
+
+SPECS = [(300, 700, 16), (2000, 900, 64), (1500, 3100, 32), (800, 1700, 64), (4096, 1000, 24), (513, 257, 8)]
+
+
+def test_same_result_alone_and_in_mix(gpu_lib):
+    from paper_2411_19214_gb300 import serve
+    mix = serve.Server(hbm_budget_bytes=8 << 30, tol=1e-6, max_sweeps=400, k=10, keep_potentials=True)
+    together = mix.run(_requests(serve, SPECS), realtime=False)
+    assert mix.stats["peak_active"] > 1  # they really overlapped
+    for i, spec in enumerate(SPECS):
+        solo = serve.Server(hbm_budget_bytes=8 << 30, tol=1e-6, max_sweeps=400, k=10, keep_potentials=True)
+        alone = solo.run([_requests(serve, SPECS)[i]], realtime=False)[0]
+        a, b = together[i], alone
+        assert a.sweeps == b.sweeps and a.converged and b.converged
+        np.testing.assert_allclose(a.log_u, b.log_u, rtol=0, atol=1e-6)
+        np.testing.assert_allclose(a.log_v, b.log_v, rtol=0, atol=1e-6)
+        np.testing.assert_array_equal(a.topk_idx, b.topk_idx)
+        assert a.match_count == pytest.approx(b.match_count, rel=1e-9)
+
+
+def test_warm_resolve(gpu_lib):
+    from paper_2411_19214_gb300 import serve
+    mk = make_market(3000, 4500, 32, sigma=0.8, seed=41, bias_x=True, bias_y=True, n_kind="uniform1to3",
+                     m_kind="uniform1to3", dtype="bf16")
+    rng = np.random.default_rng(2)
+    pert = [round_to_bf16(a + rng.normal(0, 0.01, a.shape).astype(np.float32)) for a in (mk.F, mk.K, mk.G, mk.L)]
+    r0 = serve.SolveRequest(rid=0, arrival=0.0, F=mk.F, K=mk.K, G=mk.G, L=mk.L, n=mk.n, m=mk.m, sigma=mk.sigma,
+                            bias_x=mk.bias_x, bias_y=mk.bias_y, key="A")
+    r1 = serve.SolveRequest(rid=1, arrival=0.0, F=pert[0], K=pert[1], G=pert[2], L=pert[3], n=mk.n, m=mk.m,
+                            sigma=mk.sigma, bias_x=mk.bias_x, bias_y=mk.bias_y, key="A")
+    srv = serve.Server(hbm_budget_bytes=8 << 30, tol=1e-6, max_sweeps=2000, keep_potentials=True, max_active=1)
+    res = srv.run([r0, r1], realtime=False)
+    assert res[1].warm and srv.stats["warm"] == 1
+    cold = serve.Server(hbm_budget_bytes=8 << 30, tol=1e-6, max_sweeps=2000, keep_potentials=True)
+    rc = cold.run([serve.SolveRequest(rid=1, arrival=0.0, F=pert[0], K=pert[1], G=pert[2], L=pert[3], n=mk.n,
+                                      m=mk.m, sigma=mk.sigma, bias_x=mk.bias_x, bias_y=mk.bias_y)],
+                  realtime=False)[0]
+    assert res[1].converged and rc.converged
+    assert res[1].sweeps < rc.sweeps
+    np.testing.assert_allclose(res[1].log_u, rc.log_u, atol=2e-5)
+    np.testing.assert_allclose(res[1].log_v, rc.log_v, atol=2e-5)
+    srv.close()
+
+
+def test_admission_respects_budget(gpu_lib):
+    from paper_2411_19214_gb300 import serve, tu_market_footprint
+    specs = [(20000, 15000, 64)] * 3 + [(500, 900, 16)] * 3
+    reqs = _requests(serve, specs, seed=7)
+    for r in reqs:
+        r.key = f"k{r.rid}"  # keep them resident: forces eviction
+    budget = tu_market_footprint(20000, 15000, 64) + tu_market_footprint(500, 900, 16) * 2 + (1 << 20)
+    srv = serve.Server(hbm_budget_bytes=budget, tol=1e-6, max_sweeps=300)
+    res = srv.run(reqs, realtime=False)
+    assert len(res) == 6 and srv.stats["peak_bytes"] <= budget
+    assert srv.stats["evicted"] >= 2
+    srv.close()
