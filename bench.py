@@ -357,7 +357,8 @@ def serving_block(rates, count_per_rate, budget_gb: float = 64.0) -> dict:
                               "offered_per_s": rate, "window_s": reqs[-1].arrival,
                               "not_converged_at_200_sweeps": sum(not r.converged for r in res),
                               "warm_resolves": sum(r.warm for r in res), "peak_active": srv.stats["peak_active"],
-                              "overloaded": len(res) / wall < 0.95 * rate}
+                              "drain_s": wall - reqs[-1].arrival,
+                              "overloaded": len(res) / wall < 0.9 * rate}
     return out
 
 

@@ -145,6 +145,20 @@ tu_status tu_topk_partners(tu_market_t mkt, int side, int k, int64_t row0, int64
 tu_status tu_get_potentials(tu_market_t mkt, float* log_u, float* log_v);
 tu_status tu_set_potentials(tu_market_t mkt, const float* log_u, const float* log_v);
 
+/* Over-relaxation of the log-domain update, an acceleration the paper does not
+ * have (its Sec. 5 names acceleration as future work): log u <- log u +
+ * omega * (update - log u), and the same for v. A fixed point of the relaxed
+ * sweep is a fixed point of Eq. iteration, so the solution is unchanged.
+ *   omega = 1 (default)  Alg. 1 exactly;
+ *   1 < omega < 2        tu_ipfp_sweep applies it from the next sweep on;
+ *                        tu_ipfp_solve applies it once the residual is below 0.1;
+ *   omega = 0            automatic: tu_ipfp_solve runs plain sweeps until the
+ *                        per-sweep decay q of the residual has settled, then uses
+ *                        omega = 2 / (1 + sqrt(1 - q)) (successive over-relaxation);
+ * in both relaxed modes tu_ipfp_solve halves omega - 1 whenever the residual
+ * grows tenfold over the best seen. Other values: TU_ERR_INVALID_ARG. */
+tu_status tu_market_set_relaxation(tu_market_t mkt, double omega);
+
 /* Non-blocking progress query for serving loops that keep many markets busy
  * from one host thread (no counterpart in the paper). tu_ipfp_sweep without
  * residual_out only enqueues work; this call checks, without waiting, whether

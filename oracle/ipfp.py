@@ -140,13 +140,17 @@ def col_residual(logA, m, log_u, log_v):
 # Batch IPFP (Alg. 1)
 # ---------------------------------------------------------------------------
 
-def ipfp_batch(Phi, n, m, beta, max_sweeps, tol=None, log_u=None, log_v=None):
+def ipfp_batch(Phi, n, m, beta, max_sweeps, tol=None, log_u=None, log_v=None, omega=1.0):
     """Batch IPFP, Alg. 1 / Eq. iteration_matrix, in logs.
 
     Starts from u = v = 1 (Alg. 1 initialisation) unless a warm start
     (log_u, log_v) is given. Each sweep updates u from v, then v from the new u.
     If ``tol`` is given, the row residual of the current state is evaluated
     before every sweep and the loop stops as soon as res_inf <= tol.
+
+    omega != 1 (an extension, not in the paper) over-relaxes each update in
+    the log domain, log u <- log u + omega * (update - log u), and likewise for
+    v; a fixed point of the relaxed sweep is a fixed point of Eq. iteration.
 
     Returns a dict: log_u, log_v, sweeps (number of sweeps run), res_inf,
     res_l1 (of the returned state) and trace (res_inf before each sweep when
@@ -164,8 +168,12 @@ def ipfp_batch(Phi, n, m, beta, max_sweeps, tol=None, log_u=None, log_v=None):
             trace.append(r_inf)
             if r_inf <= tol:
                 break
-        lu = half_sweep_x(logA, lv, n)
-        lv = half_sweep_y(logA, lu, m)
+        if omega == 1.0:
+            lu = half_sweep_x(logA, lv, n)
+            lv = half_sweep_y(logA, lu, m)
+        else:
+            lu = lu + omega * (half_sweep_x(logA, lv, n) - lu)
+            lv = lv + omega * (half_sweep_y(logA, lu, m) - lv)
         sweeps += 1
     r_inf, r_l1, _ = row_residual(logA, n, lu, lv)
     return dict(log_u=lu, log_v=lv, sweeps=sweeps, res_inf=r_inf, res_l1=r_l1, trace=trace)

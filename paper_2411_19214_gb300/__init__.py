@@ -70,6 +70,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tu_get_potentials": (I32, [V, V, V]),
         "tu_set_potentials": (I32, [V, V, V]),
         "tu_fused_halfsweep_noalloc": (I32, [I64, I64, I64, V, V, V, V, V, V, V, D, V, ctypes.POINTER(D), V]),
+        "tu_market_set_relaxation": (I32, [V, D]),
         "tu_market_query": (I32, [V, ctypes.POINTER(I32), ctypes.POINTER(D), ctypes.POINTER(D),
                                   ctypes.POINTER(I64)]),
         "tu_market_footprint": (I64, [I64, I64, I64, I32]),
@@ -246,6 +247,11 @@ def tu_fused_halfsweep_noalloc(rows: int, cols: int, kp: int, own_packed, partne
     return r.value if residual else None
 
 
+def tu_market_set_relaxation(h: int, omega: float) -> None:
+    """omega = 1: plain IPFP; 1 < omega < 2: fixed over-relaxation; 0: automatic in solve."""
+    _check(load().tu_market_set_relaxation(h, float(omega)), "tu_market_set_relaxation", h)
+
+
 def tu_market_query(h: int):
     """Non-blocking: (idle, residual of the state entering the last sweep,
     match count, sweeps completed); the last three are None while busy."""
@@ -303,6 +309,9 @@ class Market:
 
     def solve(self, tol: float, max_iter: int, warm_start: bool = False) -> dict:
         return tu_ipfp_solve(self.handle, tol, max_iter, warm_start)
+
+    def set_relaxation(self, omega: float) -> None:
+        tu_market_set_relaxation(self.handle, omega)
 
     def potentials(self):
         import torch

@@ -134,9 +134,10 @@ __global__ void __launch_bounds__(kThreads) k_dense_rowpass(
     const float* __restrict__ A, int64_t ld, int64_t rows, const float* __restrict__ w,
     const double* __restrict__ lmax_partner, const float* __restrict__ b2s, const double* __restrict__ mass,
     double* __restrict__ log_u, double* __restrict__ ell, double* __restrict__ partials, int residual,
-    int update) {
+    int update, const double* __restrict__ omega_p) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const double shift = *lmax_partner;
+  const double omega = omega_p ? *omega_p : 1.0;
   const int64_t n4 = ld / 4;
   const float4* w4 = reinterpret_cast<const float4*>(w);
   PartialAcc acc;
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(kThreads) k_dense_rowpass(
   auto flush = [&]() {
     if (parked_row >= 0) {
       const RowResult rr = row_update((double)logf(parked), shift, b2s ? b2s[parked_row] : 0.0f, mass[parked_row],
-                                      log_u[parked_row], residual != 0);
+                                      log_u[parked_row], residual != 0, update ? omega : 1.0);
       if (update) {
         log_u[parked_row] = rr.log_u;
         ell[parked_row] = rr.ell;
@@ -217,7 +218,8 @@ cudaError_t launch_dense_build(tu_market* m) {
 cudaError_t launch_dense_rowpass(tu_market* m, int residual, int update, int* nparts_out) {
   const int g = rowpass_grid(m, m->N);
   k_dense_rowpass<<<g, kThreads, 0, m->stream>>>(m->Ahat, m->ldA, m->N, m->Y.pvec, m->Y.lmax, m->X.b2s, m->X.mass,
-                                                 m->X.log_u, m->X.ell, m->partials, residual, update);
+                                                 m->X.log_u, m->X.ell, m->partials, residual, update,
+                                                 m->omega_dev);
   *nparts_out = g;
   return cudaGetLastError();
 }
@@ -225,7 +227,7 @@ cudaError_t launch_dense_rowpass(tu_market* m, int residual, int update, int* np
 cudaError_t launch_dense_colpass(tu_market* m, int update, int* nparts_out) {
   const int g = rowpass_grid(m, m->M);
   k_dense_rowpass<<<g, kThreads, 0, m->stream>>>(m->AhatT, m->ldN, m->M, m->X.pvec, m->X.lmax, m->Y.b2s, m->Y.mass,
-                                                 m->Y.log_u, m->Y.ell, m->partials, 0, update);
+                                                 m->Y.log_u, m->Y.ell, m->partials, 0, update, m->omega_dev);
   *nparts_out = g;
   return cudaGetLastError();
 }

@@ -69,6 +69,7 @@ struct FusedParams {
   int* err;                // device error word
   int residual;
   int update;
+  const double* omega;     // over-relaxation factor (device scalar) or nullptr for 1  (sweep)
   // ranked lists: for own user row0 + r, idx[r * k + i], logmu[r * k + i], best first
   int k;
   int32_t* idx;
@@ -403,6 +404,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       cc = ((uint64_t)cb << 32) | cb;
     }
     const double shift = __ldg(p.lmax);
+    const double omega = (p.omega != nullptr && p.update) ? *p.omega : 1.0;
     int buf = 0, gs = 0;
     uint32_t tphase = 0, gphase = 0;
     bool ok = true;
@@ -534,7 +536,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t row = p.row0 + r;
         if (row_ok) {
           const RowResult rr = row_update((double)logf(total), shift, p.b2s ? p.b2s[row] : 0.0f, p.mass[row],
-                                          p.log_u[row], p.residual != 0);
+                                          p.log_u[row], p.residual != 0, omega);
           if (p.update) {
             p.log_u[row] = rr.log_u;
             p.ell[row] = rr.ell;
@@ -701,6 +703,7 @@ cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int upd
   p.err = m->err_dev;
   p.residual = residual;
   p.update = update;
+  p.omega = m->omega_dev;
   const int grid = grid_for_tiles(p.num_own_tiles, m->num_sms);
   *nparts_out = grid;
   return launch_any<kModeSweep>(m->kp, own.tm_own, partner.tm_partner, p, grid, m->stream);

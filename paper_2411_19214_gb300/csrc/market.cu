@@ -296,6 +296,17 @@ tu_status certify(tu_market* m, double* res_inf, double* res_l1) {
   return TU_OK;
 }
 
+constexpr int kRelaxProbe = 10;  // sweeps between convergence-rate estimates
+
+// The over-relaxation factor every later pass reads (device scalar, so
+// captured graphs stay valid).
+tu_status set_omega(tu_market* m, double omega) {
+  TU_CK(m, cudaStreamSynchronize(m->stream));  // the pinned staging word may still be in use
+  *m->omega_host = omega;
+  TU_CK(m, cudaMemcpyAsync(m->omega_dev, m->omega_host, sizeof(double), cudaMemcpyHostToDevice, m->stream));
+  return TU_OK;
+}
+
 tu_status check_live(tu_market* m) {
   if (m == nullptr) return TU_ERR_INVALID_ARG;
   if (m->poisoned) return TU_ERR_CUDA;
@@ -370,6 +381,8 @@ void tu_market_destroy(tu_market_t m) {
   cudaFree(m->staging);
   cudaFree(m->aux);
   if (m->done_ev) cudaEventDestroy(m->done_ev);
+  cudaFree(m->omega_dev);
+  cudaFreeHost(m->omega_host);
   cudaFreeHost(m->query_host);
   cudaFreeHost(m->results_host);
   cudaFreeHost(m->err_host);
@@ -432,10 +445,15 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
   if ((st = dev_alloc(m, &m->err_dev, 1)) != TU_OK) return bail(st);
   if (cudaMallocHost(&m->results_host, kResSlots * sizeof(double)) != cudaSuccess ||
       cudaMallocHost(&m->query_host, (kResSlots + 1) * sizeof(double)) != cudaSuccess ||
+      cudaMallocHost(&m->omega_host, sizeof(double)) != cudaSuccess ||
       cudaMallocHost(&m->err_host, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();
     return bail(TU_ERR_OOM);
   }
+  if ((st = dev_alloc(m, &m->omega_dev, 1)) != TU_OK) return bail(st);
+  *m->omega_host = 1.0;
+  if (cudaMemcpy(m->omega_dev, m->omega_host, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(TU_ERR_CUDA);
   *m->err_host = 0;
   if (D.path == TU_PATH_DENSE) {
     m->ldA = round_up(D.M, 4);
@@ -500,6 +518,14 @@ tu_status tu_ipfp_sweep(tu_market_t m, int nsweeps, double* residual_out) {
   return TU_OK;
 }
 
+tu_status tu_market_set_relaxation(tu_market_t m, double omega) {
+  TU_TRY(check_live(m));
+  if (!(omega == 0.0 || (omega >= 1.0 && omega < 2.0)))
+    return fail(m, TU_ERR_INVALID_ARG, "omega must be 0 (automatic) or in [1, 2)");
+  m->omega_cfg = omega;
+  return set_omega(m, omega > 1.0 ? omega : 1.0);
+}
+
 tu_status tu_market_query(tu_market_t m, int* idle, double* residual, double* match_count, int64_t* sweeps) {
   TU_TRY(check_live(m));
   if (m->done_ev != nullptr) {
@@ -552,6 +578,17 @@ tu_status tu_ipfp_solve(tu_market_t m, double tol, int max_iter, int warm_start,
   int done = 0;
   double res_inf = INFINITY, res_l1 = INFINITY;
   tu_status status = TU_ERR_NOT_CONVERGED;
+  // over-relaxation: plain sweeps until the residual is below 0.1 and (in
+  // automatic mode) the per-sweep decay q of the plain iteration has settled,
+  // then omega = 2 / (1 + sqrt(1 - q)) (successive over-relaxation), tapered
+  // towards 1 as the residual approaches tol; halve the excess over 1 whenever
+  // the residual grows tenfold over the best seen
+  const bool relax = m->omega_cfg != 1.0;
+  if (relax && block > 16) block = 16;  // finer control of omega
+  double omega = 1.0, omega_target = 1.0, best = INFINITY, q_prev = -1.0;
+  int last_est = 0;
+  std::vector<std::pair<int, double>> hist;
+  if (relax) TU_TRY(set_omega(m, 1.0));
   while (true) {
     TU_TRY(certify(m, &res_inf, &res_l1));
     if (res_inf <= tol) {
@@ -567,9 +604,50 @@ tu_status tu_ipfp_solve(tu_market_t m, double tol, int max_iter, int warm_start,
       m->sweeps_enqueued += k;
       TU_TRY(read_results(m));
       done += k;
-      if (m->results_host[kResXInf] <= tol) break;
+      const double r = m->results_host[kResXInf];
+      if (r <= tol) break;
+      if (!relax) continue;
+      best = r < best ? r : best;
+      if (omega_target > 1.0) {
+        // the relaxed sweep amplifies the FP32 rounding of the row sums by about
+        // omega / (2 - omega), so omega tapers to 1 as the residual nears tol
+        if (r > 10.0 * best) {
+          omega_target = 1.0 + 0.5 * (omega_target - 1.0);
+          if (omega_target < 1.01) omega_target = 1.0;
+          best = r;
+        }
+        double w = std::log10(r / tol);
+        w = w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
+        const double next = 1.0 + (omega_target - 1.0) * w;
+        if (std::fabs(next - omega) > 1e-3) {
+          omega = next;
+          TU_TRY(set_omega(m, omega));
+        }
+        continue;
+      }
+      if (omega == 1.0) {
+        hist.push_back({done, r});
+        if (r < 0.1 && done - last_est >= kRelaxProbe) {
+          const std::pair<int, double>* base = nullptr;
+          for (const auto& h : hist)
+            if (h.first <= done - kRelaxProbe) base = &h;
+          if (base != nullptr && base->second > 0.0 && r > 0.0) {
+            const double q = std::pow(r / base->second, 1.0 / (double)(done - base->first));
+            last_est = done;
+            if (q > 0.0 && q < 1.0) {
+              const bool settled = q_prev > 0.0 && std::fabs(q - q_prev) < 0.05 * (1.0 - q);
+              if (m->omega_cfg > 1.0 || settled) {
+                omega_target =
+                    m->omega_cfg > 1.0 ? m->omega_cfg : std::fmin(1.98, 2.0 / (1.0 + std::sqrt(1.0 - q)));
+              }
+              q_prev = q;
+            }
+          }
+        }
+      }
     }
   }
+  if (relax) TU_TRY(set_omega(m, m->omega_cfg > 1.0 ? m->omega_cfg : 1.0));
   // match count from the column equations (they hold after every v update):
   // sum_xy mu_xy = sum m - sum v^2
   TU_TRY(clear_results(m));

@@ -85,6 +85,10 @@ struct tu_market {
   bool poisoned = false;
   std::string last_error;
   // benchmark timing (tu_profile_enable / tu_profile_read)
+  // over-relaxation: device scalar read by every pass (graphs stay valid when it changes)
+  double* omega_dev = nullptr;
+  double* omega_host = nullptr;  // pinned staging for updates of omega_dev
+  double omega_cfg = 1.0;        // 1: plain IPFP; (1, 2): fixed; 0: automatic in tu_ipfp_solve
   // serving: completion of the last asynchronous tu_ipfp_sweep (tu_market_query)
   cudaEvent_t done_ev = nullptr;
   double* query_host = nullptr;  // pinned: kResSlots doubles + the error word
@@ -181,8 +185,11 @@ struct RowResult {
 // popularity biases) stay in FP64. For z = log s - 1/2 log n > 0,
 // asinh(e^z) = z + c(z) with c(z) = log1p(sqrt(1 + e^{-2z})) in (ln 2, 0.89],
 // so only the bounded correction c is rounded to FP32 (absolute error ~1e-7).
+//
+// omega != 1 over-relaxes the update in the log domain:
+// log u <- log u_old + omega * (update - log u_old) (same fixed point).
 __device__ __forceinline__ RowResult row_update(double ln_sum, double shift, float b2s, double mass,
-                                                double log_u_old, bool residual) {
+                                                double log_u_old, bool residual, double omega = 1.0) {
   RowResult o;
   const double log_s = kLnHalf + (double)b2s + shift + ln_sum;
   o.r_rel = 0.0;
@@ -203,7 +210,8 @@ __device__ __forceinline__ RowResult row_update(double ln_sum, double shift, flo
   } else {
     a = (double)asinhf(expf((float)z));
   }
-  const double lu = hl - a;
+  const double lu_upd = hl - a;
+  const double lu = omega == 1.0 ? lu_upd : log_u_old + omega * (lu_upd - log_u_old);
   o.log_u = lu;
   o.ell = lu + (double)b2s;
   o.u2 = (double)expf((float)(2.0 * lu));

@@ -438,3 +438,49 @@ def test_planted_mistakes_are_caught(monkeypatch):
                     mpatch.setattr(oracle, attr, val)
             assert not _pins_pass(), f"planted mistake not caught: {name}"
     assert _pins_pass()
+
+
+# ---------------------------------------------------------------------------
+# Over-relaxed iteration (an extension): same fixed point, fewer sweeps
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("omega", [1.3, 1.6, 1.8])
+def test_relaxed_iteration_reaches_the_dual_fixed_point(omega):
+    rng = np.random.default_rng(29)
+    F, K, G, L, bx, by, n, m = _random_market(rng, 6, 6)
+    beta = 0.8
+    Phi = oracle.phi_dense(F, K, G, L, bx, by)
+    r = oracle.ipfp_batch(Phi, n, m, beta, max_sweeps=100000, tol=1e-13, omega=omega)
+    assert r["res_inf"] <= 1e-12
+    a, b = _newton_dual(Phi, n, m, beta)
+    np.testing.assert_allclose(r["log_u"], a, atol=1e-11)
+    np.testing.assert_allclose(r["log_v"], b, atol=1e-11)
+
+
+def test_relaxed_iteration_one_sweep_by_hand():
+    """One relaxed sweep = plain update u', then log u + omega (log u' - log u),
+    and the v update uses the relaxed u."""
+    Phi = np.array([[0.4, -0.6], [1.0, 0.2]])
+    beta, n, m, om = 0.5, np.array([1.0, 2.0]), np.array([2.0, 1.0]), 1.7
+    lu0, lv0 = np.array([-0.3, 0.1]), np.array([0.2, -0.5])
+    logA = oracle.log_kernel(Phi, beta)
+    A = np.exp(logA)
+    s = 0.5 * A @ np.exp(lv0)
+    lu_plain = np.log(np.sqrt(n + s * s) - s)
+    lu = lu0 + om * (lu_plain - lu0)
+    s = 0.5 * A.T @ np.exp(lu)
+    lv_plain = np.log(np.sqrt(m + s * s) - s)
+    lv = lv0 + om * (lv_plain - lv0)
+    r = oracle.ipfp_batch(Phi, n, m, beta, max_sweeps=1, log_u=lu0, log_v=lv0, omega=om)
+    np.testing.assert_allclose(r["log_u"], lu, atol=1e-14)
+    np.testing.assert_allclose(r["log_v"], lv, atol=1e-14)
+
+
+def test_relaxation_cuts_sweeps_on_a_balanced_market():
+    mk = make_market(100, 100, 16, sigma=1.0, seed=100, dtype="fp32")
+    f = mk.f64()
+    Phi = oracle.phi_dense(f["F"], f["K"], f["G"], f["L"])
+    plain = oracle.ipfp_batch(Phi, f["n"], f["m"], 1.0, max_sweeps=20000, tol=1e-8)
+    fast = oracle.ipfp_batch(Phi, f["n"], f["m"], 1.0, max_sweeps=20000, tol=1e-8, omega=1.6)
+    assert fast["sweeps"] * 2 < plain["sweeps"]
+    np.testing.assert_allclose(fast["log_u"], plain["log_u"], atol=1e-6)
