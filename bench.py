@@ -362,6 +362,37 @@ def serving_block(rates, count_per_rate, budget_gb: float = 64.0) -> dict:
     return out
 
 
+def run_paper_shapes(args):
+    """Sec. 4.2 of the paper: average time per IPFP iteration of the mini-batch
+    method for N = M in {1e2, ..., 1e6}, D = 50, factors U[0, 1/sqrt(D)],
+    n = m = 1, beta = 1 (the paper averages over I = 100 iterations). Here:
+    `--steps` sweeps per size (graph replay), after `--warmup` sweeps."""
+    import torch
+
+    import paper_2411_19214_gb300 as tu
+    from synth import paper_shaped_market
+    tu.load()
+    stream = torch.cuda.Stream()
+    for N in (100, 1_000, 10_000, 100_000, 1_000_000):
+        mk = paper_shaped_market(N)
+        mkt = tu.from_synth(mk, path="fused", stream=stream)
+        try:
+            mkt.sweep(args.warmup)
+            mkt.sweep(args.steps)  # graph capture
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            mkt.sweep(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+        finally:
+            mkt.close()
+        print(json.dumps({"workload": "paper-shaped mini-batch IPFP (Sec. 4.2)", "N": N, "M": N, "D": 50,
+                          "ms_per_sweep": ms, "sweeps": args.steps, "gpair_evals_per_s": 2.0 * N * N / ms / 1e6,
+                          "dtype": "bf16"}), flush=True)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -563,7 +594,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["fused", "dense"], default="fused")
+    ap.add_argument("--workload", choices=["fused", "dense", "paper"], default="fused",
+                    help="paper: the Sec. 4.2 shapes (N = M = 1e2..1e6, D = 50, U[0, 1/sqrt(D)], beta = 1), "
+                         "time per sweep, one JSON line per size")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -575,6 +608,9 @@ def main():
         args.shape = tuple(int(v) for v in args.shape.split(","))
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if args.workload == "paper" and args.impl == "ours":
+        run_paper_shapes(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
