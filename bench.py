@@ -9,7 +9,7 @@ tcgen05 half-sweep, FP64 partial reduction), with the residual of the entering
 state folded into the X half-sweep.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload fused|dense]
+                  [--workload fused|dense|paper|batched]
 
 N > 1 (under torchrun): every rank solves its own market of the same shape
 (independent markets, weak scaling, no collective on the data path).
@@ -393,6 +393,128 @@ def run_paper_shapes(args):
                           "dtype": "bf16"}), flush=True)
 
 
+def run_batched(args):
+    """Many independent markets in one persistent launch per half-sweep: 512
+    markets, per-side sizes log-uniform in [100, 50,000], d = 32 bf16 factors
+    N(0, 1/d), unit or uniform{1..3} capacities, sigma = 1. Reports (a) the
+    aggregate pair-evaluation rate of K batched sweeps against the same K
+    sweeps of the markets one after another (each replaying its own graph),
+    (b) the solve of every market to tol 1e-6 (automatic over-relaxation,
+    markets leave the launch when certified) with the tail of slow,
+    near-balanced markets, (c) the roofline of the batched tensor-core kernel."""
+    import numpy as np
+    import torch
+
+    import paper_2411_19214_gb300 as tu
+    from synth import batched_markets
+    tu.load()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    mks = batched_markets()
+    mkts = [tu.from_synth(mk, stream=stream) for mk in mks]
+    pairs = np.array([float(mk.N) * mk.M for mk in mks])
+    pair_evals = 2.0 * pairs.sum()
+    batch = tu.Batch(mkts, stream=stream)
+    gpu_index = 0
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        try:
+            gpu_index = int(vis.split(",")[0])
+        except ValueError:
+            pass
+    try:
+        for _ in range(args.warmup):
+            batch.sweep(1)
+        batch.sweep(args.steps)  # captures the graph the timed block replays
+        torch.cuda.synchronize()
+        clocks = ClockSampler(gpu_index)
+        clocks.start()
+        time.sleep(0.3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.sweep(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        batch.profile(True)
+        batch.sweep(args.steps)
+        pass_ms, passes = batch.profile_read()
+        batch.profile(False)
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        seq_ms = solve_s = None
+        st, infos = None, []
+        if not args.no_extras:
+            # the same sweeps, one market after another (each its own graph)
+            for mkt in mkts:
+                mkt.sweep(args.steps)
+            torch.cuda.synchronize()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            for mkt in mkts:
+                mkt.sweep(args.steps)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            seq_ms = s0.elapsed_time(s1)
+            # solve every market to tol 1e-6 from u = v = 1
+            for mkt in mkts:
+                mkt.set_relaxation(0.0)
+            batch.close()
+            batch = tu.Batch(mkts, stream=stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, infos = batch.solve(tol=1e-6, max_iter=args.max_iter)
+            solve_s = time.perf_counter() - t0
+    finally:
+        batch.close()
+        for mkt in mkts:
+            mkt.close()
+    peaks = load_peaks()
+    avg_pass_s = pass_ms / max(passes, 1) / 1e3
+    flops = 2.0 * pairs.sum() * 64  # one half-sweep: 2 * N * M * (2d padded to 64) per market
+    peak = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+    sm_mhz = clk.get("sm_mhz") or 1900.0
+    mufu_peak = 152 * 32 * sm_mhz * 1e6 / 1e12
+    rate = pair_evals * args.steps / (ms / 1e3)
+    line = {"metric": "aggregate Gpair-evals/s of 512 independent markets in one persistent launch per half-sweep",
+            "value": rate / 1e9, "unit": "Gpair-evals/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "batched: 512 markets, N and M log-uniform in [100, 50000], d=32 bf16 N(0,1/d), "
+                                   "unit (even) or uniform{1..3} (odd) capacities, sigma=1",
+                       "markets": len(mks), "pair_evals_per_sweep": pair_evals,
+                       "l2": "inputs larger than L2 (about 1 GB of packed factors); no flush"},
+            "roofline": {"bound": "tensor", "achieved": flops / avg_pass_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / avg_pass_s / 1e12 / peak, "traffic": None,
+                         "kernel": "k_fused_halfsweep batched (tcgen05 BF16 MMA, K=64, + ex2 row reduction)",
+                         "per_launch": f"{flops:.4g} flop in {avg_pass_s * 1e3:.3f} ms average over {passes} launches",
+                         "peak_source": f"{peaks.get('source')} bf16_tflops_sustained"},
+            "roofline_exp": {"bound": "alu", "achieved": pairs.sum() / avg_pass_s / 1e12, "peak": mufu_peak,
+                             "unit": "Tex2/s", "frac": pairs.sum() / avg_pass_s / 1e12 / mufu_peak,
+                             "peak_source": "152 SMs x 32 ex2/clk/SM x sampled median SM clock"},
+            "clocks": clk, "gpu_launches": 6 * args.steps,
+            "timing": "value: K batched sweeps replayed as one CUDA graph, CUDA events on the batch stream"}
+    if seq_ms is not None:
+        line["sequential"] = {"ms_per_sweep": seq_ms / args.steps,
+                              "gpair_evals_per_s": pair_evals * args.steps / (seq_ms / 1e3) / 1e9,
+                              "speedup_of_batched": seq_ms / ms,
+                              "what": "the same sweeps, one market after another on one stream (graph per market)"}
+    if infos:
+        sweeps = np.array([i["sweeps"] for i in infos])
+        conv = np.array([i["converged"] for i in infos])
+        balance = np.array([abs(math.log(mk.N / mk.M)) for mk in mks])
+        line.update({
+            "solve": {"tol": 1e-6, "max_iter": args.max_iter, "relaxation": "automatic", "status": int(st),
+                      "wall_s": solve_s, "converged": int(conv.sum()), "not_converged": int((~conv).sum()),
+                      "sweeps_p50": float(np.percentile(sweeps, 50)), "sweeps_p90": float(np.percentile(sweeps, 90)),
+                      "sweeps_p99": float(np.percentile(sweeps, 99)), "sweeps_max": int(sweeps.max()),
+                      "near_balanced": int((balance < 0.1).sum()),
+                      "near_balanced_sweeps_median": float(np.median(sweeps[balance < 0.1]))
+                      if (balance < 0.1).any() else None,
+                      "slowest": [{"N": mks[i].N, "M": mks[i].M, "sweeps": int(sweeps[i]),
+                                   "converged": bool(conv[i])} for i in np.argsort(-sweeps)[:5]]}})
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -594,9 +716,11 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["fused", "dense", "paper"], default="fused",
+    ap.add_argument("--workload", choices=["fused", "dense", "paper", "batched"], default="fused",
                     help="paper: the Sec. 4.2 shapes (N = M = 1e2..1e6, D = 50, U[0, 1/sqrt(D)], beta = 1), "
-                         "time per sweep, one JSON line per size")
+                         "time per sweep, one JSON line per size; batched: 512 independent markets in one "
+                         "persistent launch per half-sweep")
+    ap.add_argument("--max-iter", type=int, default=20000, help="sweep cap of the batched solve")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -610,6 +734,9 @@ def main():
         raise SystemExit("--warmup must be >= 3")
     if args.workload == "paper" and args.impl == "ours":
         run_paper_shapes(args)
+        return
+    if args.workload == "batched" and args.impl == "ours":
+        run_batched(args)
         return
     if args.impl == "reference":
         run_reference(args)

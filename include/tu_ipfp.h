@@ -221,6 +221,60 @@ tu_status tu_fused_halfsweep_noalloc(int64_t rows, int64_t cols, int64_t kp, con
                                      const float* partner_log_v, double sigma, float* own_log_u_out,
                                      double* residual_out, void* stream);
 
+/* ---- Many independent markets in one launch per half-sweep ----------------
+ * The paper solves one market at a time; a batch sweeps many independent
+ * markets together. Each market's arithmetic is exactly that of its own
+ * tu_ipfp_sweep (Eq. iteration_minibatch, fused path): after k batched sweeps
+ * its potentials are bit-identical to k sweeps of the market alone. Per
+ * half-sweep the batch runs one preparation kernel, one persistent tensor-core
+ * kernel over the (market, 256-user own tile) items of every active market,
+ * scheduled longest-first over the SMs, and one reduction kernel. */
+typedef struct tu_batch* tu_batch_t;
+
+/* Group `count` markets (1 <= count <= 65536), all created with TU_PATH_FUSED
+ * on the current device with the same packed width (2d rounded up to 64 or
+ * 128). The batch references the markets (their buffers, tensor maps, sigma
+ * and relaxation setting at creation); destroy the batch before any of them.
+ * Batch work is ordered on `stream` (a cudaStream_t, or NULL for the legacy
+ * default stream); every batch call first waits for work already enqueued on
+ * the members' own streams, and the caller orders later member calls after
+ * the batch's (every call below except tu_batch_sweep without residuals
+ * returns with `stream` synchronised). Errors: TU_ERR_INVALID_ARG (count,
+ * NULL, a dense-path, poisoned or repeated market, mixed widths or devices),
+ * TU_ERR_OOM, TU_ERR_CUDA. */
+tu_status tu_batch_create(const tu_market_t* markets, int count, void* stream, tu_batch_t* out);
+
+/* nsweeps >= 0 sweeps of Eq. iteration on every market of the batch (each
+ * with its fixed relaxation factor if one was set, else plain). residual_out:
+ * NULL (enqueue only), or host memory for `count` doubles that receives each
+ * market's max_x |r_x| / n_x of the returned state (one extra X pass without
+ * update, as tu_ipfp_sweep's residual_out). TU_ERR_NONFINITE if a computed
+ * potential of any market is not finite. */
+tu_status tu_batch_sweep(tu_batch_t b, int nsweeps, double* residual_out);
+
+/* Solve every market to max_x |r_x| / n_x <= tol, as tu_ipfp_solve does for
+ * one (warm_start = 0 resets u = v = 1 first). Markets leave the launch as
+ * soon as their residual is certified at or below tol, so the remaining ones
+ * share the GPU; automatic relaxation (tu_market_set_relaxation(m, 0)) runs
+ * per market. infos: host memory for `count` entries (may be NULL), filled
+ * per market (sweeps it received, its status, residuals, match count).
+ * Returns TU_OK if every market converged, TU_ERR_NONFINITE if any market
+ * produced a non-finite potential, else TU_ERR_NOT_CONVERGED when some market
+ * reached max_iter sweeps; potentials of every market stay valid. */
+tu_status tu_batch_solve(tu_batch_t b, double tol, int max_iter, int warm_start, tu_solve_info* infos);
+
+/* Kernel timing of the batched half-sweep kernel, as tu_profile_enable /
+ * tu_profile_read for a market (events around each batched tensor-core
+ * launch; no graph replay while enabled). */
+tu_status tu_batch_profile_enable(tu_batch_t b, int enable);
+tu_status tu_batch_profile_read(tu_batch_t b, double* pass_ms, int64_t* passes);
+
+/* Free the batch (not its markets; safe on NULL). */
+void tu_batch_destroy(tu_batch_t b);
+
+/* Detail of the batch's last error ("" if none). */
+const char* tu_batch_last_error(tu_batch_t b);
+
 /* Free every resource of the market (safe on NULL). */
 void tu_market_destroy(tu_market_t mkt);
 

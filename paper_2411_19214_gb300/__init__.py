@@ -79,6 +79,13 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tu_market_destroy": (None, [V]),
         "tu_status_string": (ctypes.c_char_p, [I32]),
         "tu_market_last_error": (ctypes.c_char_p, [V]),
+        "tu_batch_create": (I32, [ctypes.POINTER(V), I32, V, ctypes.POINTER(V)]),
+        "tu_batch_sweep": (I32, [V, I32, V]),
+        "tu_batch_solve": (I32, [V, D, I32, I32, ctypes.POINTER(SolveInfo)]),
+        "tu_batch_profile_enable": (I32, [V, I32]),
+        "tu_batch_profile_read": (I32, [V, ctypes.POINTER(D), ctypes.POINTER(I64)]),
+        "tu_batch_destroy": (None, [V]),
+        "tu_batch_last_error": (ctypes.c_char_p, [V]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -93,7 +100,9 @@ def exported_symbols() -> list:
     lib = load()
     names = ["tu_market_create", "tu_market_update_factors", "tu_ipfp_sweep", "tu_ipfp_solve", "tu_mu_block",
              "tu_topk_partners", "tu_get_potentials", "tu_set_potentials", "tu_profile_enable",
-             "tu_profile_read", "tu_market_destroy", "tu_status_string", "tu_market_last_error"]
+             "tu_profile_read", "tu_market_destroy", "tu_status_string", "tu_market_last_error",
+             "tu_batch_create", "tu_batch_sweep", "tu_batch_solve", "tu_batch_profile_enable",
+             "tu_batch_profile_read", "tu_batch_destroy", "tu_batch_last_error"]
     return [n for n in names if hasattr(lib, n)]
 
 
@@ -147,11 +156,12 @@ def _shape(a):
     return tuple(int(s) for s in a.shape)
 
 
-def _check(status: int, where: str, handle=None):
+def _check(status: int, where: str, handle=None, batch=False):
     if status != TU_OK:
         detail = ""
         if handle:
-            raw = load().tu_market_last_error(handle)
+            lib = load()
+            raw = lib.tu_batch_last_error(handle) if batch else lib.tu_market_last_error(handle)
             detail = raw.decode() if raw else ""
         raise TuError(status, where, detail)
 
@@ -288,6 +298,52 @@ def tu_market_destroy(h: int) -> None:
         load().tu_market_destroy(h)
 
 
+def tu_batch_create(handles, stream=None) -> int:
+    """Group market handles (fused path, same packed width) into one batch."""
+    arr = (ctypes.c_void_p * len(handles))(*[ctypes.c_void_p(h) for h in handles])
+    out = ctypes.c_void_p()
+    _check(load().tu_batch_create(arr, len(handles), _stream_handle(stream), ctypes.byref(out)), "tu_batch_create")
+    return out.value
+
+
+def tu_batch_sweep(h: int, nsweeps: int, count: int, residual: bool = False):
+    """nsweeps sweeps of every market; with residual, a float64 array of count
+    per-market residuals of the returned state."""
+    r = np.full(count, np.nan, dtype=np.float64) if residual else None
+    st = load().tu_batch_sweep(h, int(nsweeps), r.ctypes.data if residual else None)
+    _check(st, "tu_batch_sweep", h, batch=True)
+    return r
+
+
+def tu_batch_solve(h: int, tol: float, max_iter: int, count: int, warm_start: bool = False):
+    """(overall status, list of per-market dicts as tu_ipfp_solve returns)."""
+    infos = (SolveInfo * count)()
+    st = load().tu_batch_solve(h, float(tol), int(max_iter), int(bool(warm_start)), infos)
+    if st not in (TU_OK, TU_ERR_NOT_CONVERGED, TU_ERR_NONFINITE):
+        _check(st, "tu_batch_solve", h, batch=True)
+    out = [dict(status=i.status, converged=i.status == TU_OK, sweeps=i.sweeps, residual_inf=i.residual_inf,
+                residual_l1=i.residual_l1, match_count=i.match_count) for i in infos]
+    return st, out
+
+
+def tu_batch_profile_enable(h: int, enable: bool = True) -> None:
+    _check(load().tu_batch_profile_enable(h, int(bool(enable))), "tu_batch_profile_enable", h, batch=True)
+
+
+def tu_batch_profile_read(h: int):
+    """(summed milliseconds of the batched tensor-core passes, number of passes) since the last read."""
+    ms = ctypes.c_double(0.0)
+    n = ctypes.c_int64(0)
+    _check(load().tu_batch_profile_read(h, ctypes.byref(ms), ctypes.byref(n)), "tu_batch_profile_read", h,
+           batch=True)
+    return ms.value, n.value
+
+
+def tu_batch_destroy(h: int) -> None:
+    if h:
+        load().tu_batch_destroy(h)
+
+
 # ---------------------------------------------------------------------------
 # convenience object
 # ---------------------------------------------------------------------------
@@ -356,6 +412,45 @@ class Market:
     def close(self):
         if getattr(self, "handle", None):
             tu_market_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Owning wrapper of a batch handle over :class:`Market` objects (the
+    markets must outlive the batch; it keeps references to them)."""
+
+    def __init__(self, markets, stream=None):
+        self.markets = list(markets)
+        self.stream = stream
+        self.handle = tu_batch_create([mk.handle for mk in self.markets], stream=stream)
+
+    def sweep(self, nsweeps: int, residual: bool = False):
+        return tu_batch_sweep(self.handle, nsweeps, len(self.markets), residual)
+
+    def solve(self, tol: float, max_iter: int, warm_start: bool = False):
+        return tu_batch_solve(self.handle, tol, max_iter, len(self.markets), warm_start)
+
+    def profile(self, enable: bool = True) -> None:
+        tu_batch_profile_enable(self.handle, enable)
+
+    def profile_read(self):
+        return tu_batch_profile_read(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            tu_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

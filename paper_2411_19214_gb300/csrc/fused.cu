@@ -12,26 +12,33 @@
 // no per-pair running maximum is needed: the running-max rescale of
 // flash-attention collapses to one shift per half-sweep.
 //
-// CTA layout (320 threads, one CTA per SM, persistent over own tiles):
+// CTA layout (576 threads, one CTA per SM, persistent over own tiles):
 //   warp 0     : producer (one elected thread): TMA loads of the own tile
-//                [F|K]_j (256 rows x kp) once per own tile and of partner tiles
-//                (128 rows x kp) through a STAGES-deep shared-memory ring, plus
-//                a bulk copy of each partner tile's 128 g values into an
-//                8-slot ring that the epilogue reads with broadcast loads.
+//                [F|K]_j (256 rows x kp) once per own tile (double-buffered
+//                when kp = 64) and of partner tiles (128 rows x kp) through a
+//                STAGES-deep shared-memory ring, plus a bulk copy of each
+//                partner tile's 128 g values into an 8-slot ring that the
+//                epilogue reads with broadcast loads.
 //   warp 1     : MMA issuer (one thread): two tcgen05.mma M=128 N=128 chains
 //                (own rows 0-127 and 128-255) per partner tile into one of two
 //                TMEM accumulator buffers (2 x 256 columns = all 512).
-//   warps 2-9  : epilogue: warp w reads TMEM lanes 32*(w%4).. of own sub-tile
-//                (w-2)/4, i.e. one own row per thread, so the row reduction
-//                stays inside the thread (no shuffles). TMEM loads run one
-//                32-column chunk ahead of the arithmetic; per pair of columns
-//                one packed FMA (f32x2), two ex2.approx and one packed add;
-//                per-tile partials go into a compensated (Kahan) sum.
+//   warps 2-17 : epilogue: epilogue warp e reads TMEM lane quadrant (e+2)%4
+//                of own sub-tile (e/4)%2 and column half e/8 of every partner
+//                tile, i.e. one own row and 64 columns per thread, so the row
+//                reduction stays inside the thread; the two column halves of
+//                a row meet through shared memory at the end of the own tile.
+//                TMEM loads run one 32-column chunk ahead of the arithmetic;
+//                per pair of columns one packed FMA (f32x2), two ex2.approx
+//                and one packed add; per-tile partials go into a compensated
+//                (Kahan) sum.
+// In a batched launch the own tiles of a CTA come from a list of
+// (market, own tile) items of many independent markets.
 // Every wait is bounded (kWaitLimitNs); a wait that runs out raises the
 // abort flag and the error word, the roles drain, TMEM is freed, and the
 // kernel returns.
 #include "tu_internal.cuh"
 
+#include <cstring>
 #include <mutex>
 
 namespace tu {
@@ -70,6 +77,10 @@ struct FusedParams {
   int residual;
   int update;
   const double* omega;     // over-relaxation factor (device scalar) or nullptr for 1  (sweep)
+  // batched launches: per-market descriptors and this launch's item lists
+  const BatchDesc* bdesc;
+  const int2* items;
+  const int* cta_start;
   // ranked lists: for own user row0 + r, idx[r * k + i], logmu[r * k + i], best first
   int k;
   int32_t* idx;
@@ -83,13 +94,19 @@ struct FusedParams {
   int64_t ny;
 };
 
-// shared memory: [A: KB x 32 KB][B: STAGES x KB x 16 KB][g ring: 8 x 512 B]
+// Own-tile buffers: with a 64-wide inner dimension the next own tile is loaded
+// while the current one is still in use (short items of batched launches);
+// with 128 there is room for one only.
+template <int KB>
+constexpr int kABufs = KB == 1 ? 2 : 1;
+
+// shared memory: [A: ABUFS x KB x 32 KB][B: STAGES x KB x 16 KB][g ring: 8 x 512 B]
 //                [barriers and flags: 512 B][reduction: 512 B][row hand-over: 2 x 256 floats]
 constexpr int kTailBytes = 512 + 512 + 2 * kFusedOwnRows * 4;
 template <int KB>
 constexpr int smem_bytes(int stages) {
-  return 1024 /*alignment slack*/ + KB * kOwnBytesPerKB + stages * KB * kPartnerBytesPerKB + kGSlots * kGBytes +
-         kTailBytes;
+  return 1024 /*alignment slack*/ + kABufs<KB> * KB * kOwnBytesPerKB + stages * KB * kPartnerBytesPerKB +
+         kGSlots * kGBytes + kTailBytes;
 }
 
 __device__ __forceinline__ void raise_error(int* err, volatile int* abort_flag, int code) {
@@ -220,33 +237,69 @@ __device__ __forceinline__ void chunk_mu(const uint32_t (&v)[32], const float* g
   }
 }
 
-template <int KB, int STAGES, int MODE>
+// The items of a batched launch are (market, own tile) pairs.
+struct ItemRef {
+  const BatchDesc* d;
+  int t;
+};
+__device__ __forceinline__ ItemRef batch_item(const FusedParams& p, int it) {
+  const int2 v = p.items[it];
+  return {p.bdesc + v.x, v.y};
+}
+
+// This CTA's items: own tiles blockIdx.x, blockIdx.x + gridDim.x, ... of one
+// market, or a contiguous range of the batched item list (all roles walk the
+// same sequence).
+template <bool BATCH>
+__device__ __forceinline__ int item_begin(const FusedParams& p) {
+  if constexpr (BATCH) return p.cta_start[blockIdx.x];
+  return blockIdx.x;
+}
+template <bool BATCH>
+__device__ __forceinline__ int item_end(const FusedParams& p) {
+  if constexpr (BATCH) return p.cta_start[blockIdx.x + 1];
+  return p.num_own_tiles;
+}
+template <bool BATCH>
+__device__ __forceinline__ int item_step() {
+  if constexpr (BATCH) return 1;
+  return gridDim.x;
+}
+
+// BATCH: the CTA's own tiles come from the launch's item list and may belong
+// to different markets (tensor maps, vectors and sizes from BatchDesc); the
+// residual partials are then written per own tile and epilogue warp instead
+// of per CTA.
+template <int KB, int STAGES, int MODE, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 1)
     k_fused_halfsweep(const __grid_constant__ CUtensorMap tm_own, const __grid_constant__ CUtensorMap tm_partner,
                       const FusedParams p) {
+  static_assert(!BATCH || MODE == kModeSweep, "batched launches run half-sweeps only");
+  constexpr int ABUF = kABufs<KB>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_u32 = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + (((raw_u32 + 1023u) & ~1023u) - raw_u32);
   uint8_t* sA = smem;
-  uint8_t* sB = smem + KB * kOwnBytesPerKB;
+  uint8_t* sB = smem + ABUF * KB * kOwnBytesPerKB;
   float* sG = reinterpret_cast<float*>(sB + STAGES * KB * kPartnerBytesPerKB);
   uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(sG) + kGSlots * kGBytes);
   uint64_t* full = bars;
   uint64_t* empty = bars + STAGES;
   uint64_t* gfull = bars + 2 * STAGES;
   uint64_t* gempty = gfull + kGSlots;
-  uint64_t* a_full = gempty + kGSlots;
-  uint64_t* a_empty = a_full + 1;
-  uint64_t* tfull = a_full + 2;   // [2]
-  uint64_t* tempty = a_full + 4;  // [2]
-  uint64_t* mma_done = a_full + 6;
-  uint64_t* rowfull = a_full + 7;  // [2] second column half of the rows written
-  uint64_t* rowfree = a_full + 9;  // [2] row hand-over buffer read
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(a_full + 11);
+  uint64_t* a_full = gempty + kGSlots;  // [2]
+  uint64_t* a_empty = a_full + 2;       // [2]
+  uint64_t* tfull = a_full + 4;         // [2]
+  uint64_t* tempty = a_full + 6;        // [2]
+  uint64_t* mma_done = a_full + 8;
+  uint64_t* rowfull = a_full + 9;   // [2] second column half of the rows written
+  uint64_t* rowfree = a_full + 11;  // [2] row hand-over buffer read
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(a_full + 13);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   double* red = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(bars) + 512);      // 4 x kEpiWarps doubles
   float* rowbuf = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bars) + 1024);   // 2 x 256 floats
   static_assert(4 * kEpiWarps * 8 <= 512, "reduction area");
+  static_assert((2 * STAGES + 2 * kGSlots + 13) * 8 + 8 <= 512, "barrier area");
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 
@@ -259,8 +312,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&gfull[s], 1);
       mbar_init(&gempty[s], kEpiWarps);
     }
-    mbar_init(a_full, 1);
-    mbar_init(a_empty, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&a_full[b], 1);
+      mbar_init(&a_empty[b], 1);
+    }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], kEpiWarps);
@@ -272,8 +327,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     *abort_flag = 0;
     fence_mbar_init();
-    tma_prefetch_map(&tm_own);
-    tma_prefetch_map(&tm_partner);
+    if constexpr (!BATCH) {
+      tma_prefetch_map(&tm_own);
+      tma_prefetch_map(&tm_partner);
+    }
   }
   if (warp == 0) {
     tmem_alloc(tmem_slot, kTmemCols);
@@ -287,31 +344,51 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      int stage = 0, gs = 0;
+      int stage = 0, gs = 0, ab = 0;
       uint32_t phase = 0, gphase = 0, a_phase = 0;
-      uint32_t armed[STAGES], garmed[kGSlots];
+      uint32_t armed[STAGES], garmed[kGSlots], a_armed[2] = {0u, 0u};
       for (int s = 0; s < STAGES; ++s) armed[s] = 0;
       for (int s = 0; s < kGSlots; ++s) garmed[s] = 0;
-      uint32_t a_armed = 0;
+      const BatchDesc* prev = nullptr;
       bool ok = true;
-      for (int t = blockIdx.x; t < p.num_own_tiles && ok; t += gridDim.x) {
-        if (!mbar_wait(a_empty, a_phase ^ 1u, abort_flag)) {
+      for (int it = item_begin<BATCH>(p); it < item_end<BATCH>(p) && ok; it += item_step<BATCH>()) {
+        const BatchDesc* bd = nullptr;
+        int t = it;
+        if constexpr (BATCH) {
+          const ItemRef w = batch_item(p, it);
+          bd = w.d;
+          t = w.t;
+          if (bd != prev) {
+            tensormap_acquire(&bd->tm_own);
+            tensormap_acquire(&bd->tm_partner);
+            prev = bd;
+          }
+        }
+        const CUtensorMap* map_own = BATCH ? &bd->tm_own : &tm_own;
+        const CUtensorMap* map_partner = BATCH ? &bd->tm_partner : &tm_partner;
+        const float* gsrc = BATCH ? bd->g : p.g + p.col0;
+        const int npt = BATCH ? bd->num_partner_tiles : p.num_partner_tiles;
+        const int64_t arow = BATCH ? (int64_t)t * kFusedOwnRows : p.row0 + (int64_t)t * kFusedOwnRows;
+        if (!mbar_wait(&a_empty[ab], a_phase ^ 1u, abort_flag)) {
           ok = false;
           break;
         }
-        a_phase ^= 1u;
-        mbar_arrive_expect_tx(a_full, KB * kOwnBytesPerKB);
+        mbar_arrive_expect_tx(&a_full[ab], KB * kOwnBytesPerKB);
         for (int kb = 0; kb < KB; ++kb)
-          tma_load_2d(sA + kb * kOwnBytesPerKB, &tm_own, a_full, kb * kKBlock, (int)(p.row0 + (int64_t)t * kFusedOwnRows));
-        ++a_armed;
-        for (int j = 0; j < p.num_partner_tiles; ++j) {
+          tma_load_2d(sA + (ab * KB + kb) * kOwnBytesPerKB, map_own, &a_full[ab], kb * kKBlock, (int)arow);
+        ++a_armed[ab];
+        if (++ab == ABUF) {
+          ab = 0;
+          a_phase ^= 1u;
+        }
+        for (int j = 0; j < npt; ++j) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
             ok = false;
             break;
           }
           mbar_arrive_expect_tx(&full[stage], KB * kPartnerBytesPerKB);
           for (int kb = 0; kb < KB; ++kb)
-            tma_load_2d(sB + (stage * KB + kb) * kPartnerBytesPerKB, &tm_partner, &full[stage], kb * kKBlock,
+            tma_load_2d(sB + (stage * KB + kb) * kPartnerBytesPerKB, map_partner, &full[stage], kb * kKBlock,
                         (int)(p.col0 + (int64_t)j * kFusedPartnerRows));
           ++armed[stage];
           if (++stage == STAGES) {
@@ -323,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           mbar_arrive_expect_tx(&gfull[gs], kGBytes);
-          bulk_load(sG + gs * kFusedPartnerRows, p.g + p.col0 + (int64_t)j * kFusedPartnerRows, kGBytes, &gfull[gs]);
+          bulk_load(sG + gs * kFusedPartnerRows, gsrc + (int64_t)j * kFusedPartnerRows, kGBytes, &gfull[gs]);
           ++garmed[gs];
           if (++gs == kGSlots) {
             gs = 0;
@@ -338,7 +415,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (armed[s]) mbar_wait_drain(&full[s], (armed[s] - 1u) & 1u, 10000000ull);
         for (int s = 0; s < kGSlots; ++s)
           if (garmed[s]) mbar_wait_drain(&gfull[s], (garmed[s] - 1u) & 1u, 10000000ull);
-        if (a_armed) mbar_wait_drain(a_full, (a_armed - 1u) & 1u, 10000000ull);
+        for (int b = 0; b < ABUF; ++b)
+          if (a_armed[b]) mbar_wait_drain(&a_full[b], (a_armed[b] - 1u) & 1u, 10000000ull);
       }
     }
     __syncwarp();
@@ -346,18 +424,28 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16_f32(128, kFusedPartnerRows);
-      int stage = 0, buf = 0;
+      int stage = 0, buf = 0, ab = 0;
       uint32_t phase = 0, tphase = 0, a_phase = 0;
       bool ok = true;
-      const uint32_t a0 = smem_u32(sA);
-      for (int t = blockIdx.x; t < p.num_own_tiles && ok; t += gridDim.x) {
-        if (!mbar_wait(a_full, a_phase, abort_flag)) {
+      for (int it = item_begin<BATCH>(p); it < item_end<BATCH>(p) && ok; it += item_step<BATCH>()) {
+        int npt;
+        if constexpr (BATCH) {
+          npt = batch_item(p, it).d->num_partner_tiles;
+        } else {
+          npt = p.num_partner_tiles;
+        }
+        if (!mbar_wait(&a_full[ab], a_phase, abort_flag)) {
           ok = false;
           break;
         }
-        a_phase ^= 1u;
         tc_fence_after();
-        for (int j = 0; j < p.num_partner_tiles; ++j) {
+        const uint32_t a0 = smem_u32(sA + ab * KB * kOwnBytesPerKB);
+        uint64_t* a_release = &a_empty[ab];
+        if (++ab == ABUF) {
+          ab = 0;
+          a_phase ^= 1u;
+        }
+        for (int j = 0; j < npt; ++j) {
           if (!mbar_wait(&full[stage], phase, abort_flag) || !mbar_wait(&tempty[buf], tphase ^ 1u, abort_flag)) {
             ok = false;
             break;
@@ -377,7 +465,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           umma_commit(&empty[stage]);
           umma_commit(&tfull[buf]);
-          if (j == p.num_partner_tiles - 1) umma_commit(a_empty);
+          if (j == npt - 1) umma_commit(a_release);
           if (++stage == STAGES) {
             stage = 0;
             phase ^= 1u;
@@ -403,8 +491,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t cb = __float_as_uint(p.c);
       cc = ((uint64_t)cb << 32) | cb;
     }
-    const double shift = __ldg(p.lmax);
-    const double omega = (p.omega != nullptr && p.update) ? *p.omega : 1.0;
+    // single market: the shift and omega of the launch (batched: per item)
+    const double shift0 = BATCH ? 0.0 : __ldg(p.lmax);
+    const double omega0 = (!BATCH && p.omega != nullptr && p.update) ? *p.omega : 1.0;
     int buf = 0, gs = 0;
     uint32_t tphase = 0, gphase = 0;
     bool ok = true;
@@ -416,10 +505,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     int tcnt = 0;
     float thr = -INFINITY;
     int tile_iter = 0;
-    for (int t = blockIdx.x; t < p.num_own_tiles && ok; t += gridDim.x, ++tile_iter) {
+    for (int it = item_begin<BATCH>(p); it < item_end<BATCH>(p) && ok; it += item_step<BATCH>(), ++tile_iter) {
+      const BatchDesc* bd = nullptr;
+      int t = it;
+      if constexpr (BATCH) {
+        const ItemRef w = batch_item(p, it);
+        bd = w.d;
+        t = w.t;
+        const uint32_t cb = __float_as_uint(bd->c);
+        cc = ((uint64_t)cb << 32) | cb;
+      }
+      const double shift = BATCH ? *bd->lmax : shift0;
+      const int npt = BATCH ? bd->num_partner_tiles : p.num_partner_tiles;
       const int rloc = h * 128 + q * 32 + lane;          // row within the own tile
       const int64_t r = (int64_t)t * kFusedOwnRows + rloc;  // row within the launch
-      const bool row_ok = r < p.rows;
+      const bool row_ok = r < (BATCH ? bd->rows : p.rows);
       float sum = 0.0f, comp = 0.0f;
       float mu_lo = 0.0f;
       int mu_hi = 0;
@@ -435,7 +535,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tcnt = 0;
         thr = -INFINITY;
       }
-      for (int j = 0; j < p.num_partner_tiles; ++j) {
+      for (int j = 0; j < npt; ++j) {
         // every lane waits; the outcome is made warp-uniform so that the
         // .sync.aligned TMEM loads below never run with a partial warp
         const bool got = mbar_wait(&tfull[buf], tphase, abort_flag) && mbar_wait(&gfull[gs], gphase, abort_flag);
@@ -535,21 +635,43 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(&rowfree[pb]);
         const int64_t row = p.row0 + r;
         if (row_ok) {
-          const RowResult rr = row_update((double)logf(total), shift, p.b2s ? p.b2s[row] : 0.0f, p.mass[row],
-                                          p.log_u[row], p.residual != 0, omega);
+          const float* b2s = BATCH ? bd->b2s : p.b2s;
+          double* log_u = BATCH ? bd->log_u : p.log_u;
+          double* ell = BATCH ? bd->ell : p.ell;
+          const double omega = BATCH ? ((bd->omega != nullptr && p.update) ? *bd->omega : 1.0) : omega0;
+          const RowResult rr = row_update((double)logf(total), shift, b2s ? b2s[row] : 0.0f,
+                                          (BATCH ? bd->mass : p.mass)[row], log_u[row], p.residual != 0, omega);
           if (p.update) {
-            p.log_u[row] = rr.log_u;
-            p.ell[row] = rr.ell;
+            log_u[row] = rr.log_u;
+            ell[row] = rr.ell;
           }
           r_max = fmax(r_max, rr.r_rel);
           r_sum += rr.r_abs;
           sq += rr.u2;
           if (!isfinite(rr.log_u) || !isfinite(rr.ell)) nf += 1.0;
         }
+        if constexpr (BATCH) {
+          // partials of this own tile and warp (warps ew = 0..7 own the row
+          // updates); the batched finalize sums them per market in a fixed order
+          for (int o = 16; o > 0; o >>= 1) {
+            r_max = fmax(r_max, __shfl_xor_sync(0xffffffffu, r_max, o));
+            r_sum += __shfl_xor_sync(0xffffffffu, r_sum, o);
+            sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            nf += __shfl_xor_sync(0xffffffffu, nf, o);
+          }
+          if (lane == 0) {
+            double* dst = p.partials + ((int64_t)(bd->slot0 + t) * kBatchSlotWarps + ew) * 4;
+            dst[0] = r_max;
+            dst[1] = r_sum;
+            dst[2] = sq;
+            dst[3] = nf;
+          }
+          r_max = r_sum = sq = nf = 0.0;
+        }
       }
     }
     if (!ok && !*abort_flag) raise_error(p.err, abort_flag, kErrTimeout);
-    if constexpr (MODE == kModeSweep) {
+    if constexpr (MODE == kModeSweep && !BATCH) {
       // reduce the CTA's partials over the epilogue threads
       for (int o = 16; o > 0; o >>= 1) {
         r_max = fmax(r_max, __shfl_xor_sync(0xffffffffu, r_max, o));
@@ -626,37 +748,38 @@ cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, 
 constexpr int kStagesKB1 = 6;
 constexpr int kStagesKB2 = 4;
 
-template <int KB, int STAGES, int MODE>
+template <int KB, int STAGES, int MODE, bool BATCH>
 cudaError_t launch_kernel(const CUtensorMap& own, const CUtensorMap& partner, const FusedParams& p, int grid,
                           cudaStream_t stream) {
   static_assert(smem_bytes<KB>(STAGES) <= 232448, "shared memory budget");
-  k_fused_halfsweep<KB, STAGES, MODE><<<grid, kThreads, smem_bytes<KB>(STAGES), stream>>>(own, partner, p);
+  k_fused_halfsweep<KB, STAGES, MODE, BATCH><<<grid, kThreads, smem_bytes<KB>(STAGES), stream>>>(own, partner, p);
   return cudaGetLastError();
 }
 
-template <int MODE>
+template <int MODE, bool BATCH>
 cudaError_t set_attributes_mode() {
-  cudaError_t e = cudaFuncSetAttribute(k_fused_halfsweep<1, kStagesKB1, MODE>,
+  cudaError_t e = cudaFuncSetAttribute(k_fused_halfsweep<1, kStagesKB1, MODE, BATCH>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>(kStagesKB1));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_fused_halfsweep<2, kStagesKB2, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              smem_bytes<2>(kStagesKB2));
+  return cudaFuncSetAttribute(k_fused_halfsweep<2, kStagesKB2, MODE, BATCH>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<2>(kStagesKB2));
 }
 
 // Dynamic shared memory opt-in of every instantiation, on the current device.
 cudaError_t set_kernel_attributes() {
-  cudaError_t e = set_attributes_mode<kModeSweep>();
-  if (e == cudaSuccess) e = set_attributes_mode<kModeTopK>();
-  if (e == cudaSuccess) e = set_attributes_mode<kModeMu>();
+  cudaError_t e = set_attributes_mode<kModeSweep, false>();
+  if (e == cudaSuccess) e = set_attributes_mode<kModeTopK, false>();
+  if (e == cudaSuccess) e = set_attributes_mode<kModeMu, false>();
+  if (e == cudaSuccess) e = set_attributes_mode<kModeSweep, true>();
   return e;
 }
 
-template <int MODE>
+template <int MODE, bool BATCH = false>
 cudaError_t launch_any(int64_t kp, const CUtensorMap& own, const CUtensorMap& partner, const FusedParams& p,
                        int grid, cudaStream_t stream) {
   const int kb = (int)(kp / kKBlock);
-  if (kb == 1) return launch_kernel<1, kStagesKB1, MODE>(own, partner, p, grid, stream);
-  if (kb == 2) return launch_kernel<2, kStagesKB2, MODE>(own, partner, p, grid, stream);
+  if (kb == 1) return launch_kernel<1, kStagesKB1, MODE, BATCH>(own, partner, p, grid, stream);
+  if (kb == 2) return launch_kernel<2, kStagesKB2, MODE, BATCH>(own, partner, p, grid, stream);
   return cudaErrorNotSupported;
 }
 
@@ -771,6 +894,25 @@ cudaError_t launch_fused_halfsweep_raw(const FusedRaw& r, cudaStream_t stream, i
   const int grid = grid_for_tiles(p.num_own_tiles, num_sms);
   *nparts_out = grid;
   return launch_any<kModeSweep>(r.kp, own_map, partner_map, p, grid, stream);
+}
+
+// One half-sweep over the items of many markets (batched launch). The
+// per-market tensor maps live in the descriptors, so the kernel's map
+// parameters are unused.
+cudaError_t launch_fused_batch(const BatchLaunch& b, cudaStream_t stream) {
+  static_assert(kEpiWarps / 2 == kBatchSlotWarps, "per-tile partial slots");
+  // (the shared-memory opt-in was made when the member markets were prepared)
+  FusedParams p{};
+  p.bdesc = b.desc;
+  p.items = b.items;
+  p.cta_start = b.cta_start;
+  p.partials = b.partials;
+  p.err = b.err;
+  p.residual = b.residual;
+  p.update = b.update;
+  CUtensorMap unused;
+  memset(&unused, 0, sizeof(unused));
+  return launch_any<kModeSweep, true>(b.kp, unused, unused, p, b.grid, stream);
 }
 
 }  // namespace tu

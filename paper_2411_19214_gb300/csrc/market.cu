@@ -296,8 +296,6 @@ tu_status certify(tu_market* m, double* res_inf, double* res_l1) {
   return TU_OK;
 }
 
-constexpr int kRelaxProbe = 10;  // sweeps between convergence-rate estimates
-
 // The over-relaxation factor every later pass reads (device scalar, so
 // captured graphs stay valid).
 tu_status set_omega(tu_market* m, double omega) {
@@ -330,6 +328,40 @@ tu_status output_view(tu_market* m, void* dst, size_t bytes, size_t off, void** 
 }
 
 }  // namespace
+
+double tu::RelaxControl::observe(int done, double r, double tol) {
+  best = r < best ? r : best;
+  if (target > 1.0) {
+    if (r > 10.0 * best) {
+      target = 1.0 + 0.5 * (target - 1.0);
+      if (target < 1.01) target = 1.0;
+      best = r;
+    }
+    double w = std::log10(r / tol);
+    w = w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
+    const double next = 1.0 + (target - 1.0) * w;
+    if (std::fabs(next - omega) > 1e-3) omega = next;
+    return omega;
+  }
+  if (omega == 1.0) {
+    hist.push_back({done, r});
+    if (r < 0.1 && done - last_est >= kProbe) {
+      const std::pair<int, double>* base = nullptr;
+      for (const auto& h : hist)
+        if (h.first <= done - kProbe) base = &h;
+      if (base != nullptr && base->second > 0.0 && r > 0.0) {
+        const double q = std::pow(r / base->second, 1.0 / (double)(done - base->first));
+        last_est = done;
+        if (q > 0.0 && q < 1.0) {
+          const bool settled = q_prev > 0.0 && std::fabs(q - q_prev) < 0.05 * (1.0 - q);
+          if (cfg > 1.0 || settled) target = cfg > 1.0 ? cfg : std::fmin(1.98, 2.0 / (1.0 + std::sqrt(1.0 - q)));
+          q_prev = q;
+        }
+      }
+    }
+  }
+  return omega;
+}
 
 extern "C" {
 
@@ -578,16 +610,11 @@ tu_status tu_ipfp_solve(tu_market_t m, double tol, int max_iter, int warm_start,
   int done = 0;
   double res_inf = INFINITY, res_l1 = INFINITY;
   tu_status status = TU_ERR_NOT_CONVERGED;
-  // over-relaxation: plain sweeps until the residual is below 0.1 and (in
-  // automatic mode) the per-sweep decay q of the plain iteration has settled,
-  // then omega = 2 / (1 + sqrt(1 - q)) (successive over-relaxation), tapered
-  // towards 1 as the residual approaches tol; halve the excess over 1 whenever
-  // the residual grows tenfold over the best seen
-  const bool relax = m->omega_cfg != 1.0;
+  // over-relaxation (RelaxControl): omega is re-chosen after every block
+  RelaxControl ctl(m->omega_cfg);
+  const bool relax = ctl.enabled();
   if (relax && block > 16) block = 16;  // finer control of omega
-  double omega = 1.0, omega_target = 1.0, best = INFINITY, q_prev = -1.0;
-  int last_est = 0;
-  std::vector<std::pair<int, double>> hist;
+  double omega = 1.0;
   if (relax) TU_TRY(set_omega(m, 1.0));
   while (true) {
     TU_TRY(certify(m, &res_inf, &res_l1));
@@ -607,43 +634,10 @@ tu_status tu_ipfp_solve(tu_market_t m, double tol, int max_iter, int warm_start,
       const double r = m->results_host[kResXInf];
       if (r <= tol) break;
       if (!relax) continue;
-      best = r < best ? r : best;
-      if (omega_target > 1.0) {
-        // the relaxed sweep amplifies the FP32 rounding of the row sums by about
-        // omega / (2 - omega), so omega tapers to 1 as the residual nears tol
-        if (r > 10.0 * best) {
-          omega_target = 1.0 + 0.5 * (omega_target - 1.0);
-          if (omega_target < 1.01) omega_target = 1.0;
-          best = r;
-        }
-        double w = std::log10(r / tol);
-        w = w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
-        const double next = 1.0 + (omega_target - 1.0) * w;
-        if (std::fabs(next - omega) > 1e-3) {
-          omega = next;
-          TU_TRY(set_omega(m, omega));
-        }
-        continue;
-      }
-      if (omega == 1.0) {
-        hist.push_back({done, r});
-        if (r < 0.1 && done - last_est >= kRelaxProbe) {
-          const std::pair<int, double>* base = nullptr;
-          for (const auto& h : hist)
-            if (h.first <= done - kRelaxProbe) base = &h;
-          if (base != nullptr && base->second > 0.0 && r > 0.0) {
-            const double q = std::pow(r / base->second, 1.0 / (double)(done - base->first));
-            last_est = done;
-            if (q > 0.0 && q < 1.0) {
-              const bool settled = q_prev > 0.0 && std::fabs(q - q_prev) < 0.05 * (1.0 - q);
-              if (m->omega_cfg > 1.0 || settled) {
-                omega_target =
-                    m->omega_cfg > 1.0 ? m->omega_cfg : std::fmin(1.98, 2.0 / (1.0 + std::sqrt(1.0 - q)));
-              }
-              q_prev = q;
-            }
-          }
-        }
+      const double next = ctl.observe(done, r, tol);
+      if (next != omega) {
+        omega = next;
+        TU_TRY(set_omega(m, omega));
       }
     }
   }

@@ -143,6 +143,49 @@ struct FusedRaw {
   int residual;
 };
 cudaError_t launch_fused_halfsweep_raw(const FusedRaw& r, cudaStream_t stream, int num_sms, int* nparts_out);
+
+// One market of a batched launch, for the half-sweep that updates its "own"
+// side against its "partner" side (device copy; the tensor maps keep their
+// 128-byte alignment, so an array of these is a valid TMA operand array).
+// Two per market: X against Y and Y against X.
+struct BatchDesc {
+  CUtensorMap tm_own;          // own packed factors, box kKBlock x kFusedOwnRows
+  CUtensorMap tm_partner;      // partner packed factors, box kKBlock x kFusedPartnerRows
+  const float* b2s;            // own bias / (2 sigma) or nullptr
+  const double* mass;          // own capacities
+  double* log_u;               // own potentials (in: old, out: new)
+  double* ell;                 // own ell (out)
+  const double* partner_ell;   // partner ell (read by the preparation kernel)
+  float* g;                    // partner prepared vector (written by the preparation kernel)
+  double* lmax;                // partner shift (written by the preparation kernel)
+  const double* omega;         // over-relaxation factor of this market (device scalar)
+  int64_t rows;                // own users
+  int64_t partner_rows;        // partner users
+  int64_t partner_rows_pad;    // partner vector length (multiple of kRowPad)
+  int num_own_tiles;           // ceil(rows / kFusedOwnRows)
+  int num_partner_tiles;       // ceil(partner_rows / kFusedPartnerRows)
+  int slot0;                   // first own-tile slot of this market in the partials array
+  float c;                     // log2(e) / (2 sigma)
+};
+
+// Epilogue warps that write per-tile partials in a batched launch (the warps
+// that own the row updates); each own tile has kBatchSlotWarps x 4 doubles.
+constexpr int kBatchSlotWarps = 8;
+
+// A batched half-sweep: the CTA b processes items[cta_start[b] .. cta_start[b + 1])
+// in order, an item being (market, own tile).
+struct BatchLaunch {
+  const BatchDesc* desc;   // device, indexed by market
+  const int2* items;       // device
+  const int* cta_start;    // device, grid + 1 entries
+  double* partials;        // device, [slot][kBatchSlotWarps][4]
+  int* err;
+  int grid;
+  int64_t kp;              // 64 or 128, the same for every market
+  int residual;
+  int update;
+};
+cudaError_t launch_fused_batch(const BatchLaunch& b, cudaStream_t stream);
 // ranked lists / mu block through the tensor-core pipeline (partner vector prepared in log2 mode)
 cudaError_t launch_fused_topk(tu_market* m, int side, int k, int64_t row0, int64_t nrows, int32_t* idx, float* logmu,
                               float* hand_v, int32_t* hand_i);
@@ -153,6 +196,28 @@ cudaError_t launch_mu_block(tu_market* m, int64_t x0, int64_t nx, int64_t y0, in
                             int64_t ld);
 cudaError_t launch_topk(tu_market* m, int side, int k, int64_t row0, int64_t nrows, int32_t* idx,
                         float* logmu);
+
+// Over-relaxation controller of the solve loops (host side, one per market).
+// Plain sweeps until the residual is below 0.1 and (in automatic mode) the
+// per-sweep decay q of the plain iteration has settled, then
+// omega = 2 / (1 + sqrt(1 - q)) (successive over-relaxation), tapered towards
+// 1 as the residual approaches tol: the relaxed sweep amplifies the FP32
+// rounding of the row sums by about omega / (2 - omega). The excess over 1 is
+// halved whenever the residual grows tenfold over the best seen.
+struct RelaxControl {
+  static constexpr int kProbe = 10;  // sweeps between convergence-rate estimates
+  double cfg = 1.0;                  // 1: plain; (1, 2): fixed; 0: automatic
+  double omega = 1.0, target = 1.0, best = 1.0 / 0.0, q_prev = -1.0;
+  int last_est = 0;
+  std::vector<std::pair<int, double>> hist;
+
+  explicit RelaxControl(double c = 1.0) : cfg(c) {}
+  bool enabled() const { return cfg != 1.0; }
+
+  // r: residual of the state entering the last sweep of a block that ended
+  // after `done` sweeps (r > tol). Returns the omega of the next block.
+  double observe(int done, double r, double tol);
+};
 
 }  // namespace tu
 
@@ -292,6 +357,11 @@ __device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* m
 }
 __device__ __forceinline__ void tma_prefetch_map(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+// Order earlier writes of a tensor map held in global memory before its use by TMA.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+               : "memory");
 }
 
 // ---- tcgen05 ---------------------------------------------------------------

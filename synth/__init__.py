@@ -16,6 +16,7 @@ from .markets import (  # noqa: F401
     plain_dense_market,
     paper_shaped_market,
     batched_market_sizes,
+    batched_markets,
     serving_request_sizes,
     serving_workload,
 )

@@ -183,6 +183,29 @@ def batched_market_sizes(count: int = 512, lo: int = 100, hi: int = 50_000,
     return [(int(a), int(b), k) for (a, b), k in zip(sizes, kinds)]
 
 
+def batched_markets(count: int = 512, lo: int = 100, hi: int = 50_000, d: int = 32, sigma: float = 1.0,
+                    seed: int = 1003) -> list:
+    """The independent markets of the batched workload: per-side sizes from
+    batched_market_sizes (log-uniform in [lo, hi]); bf16 factors N(0, 1/d)
+    sliced at seeded offsets from one seeded pool per matrix (so 512 markets
+    are drawn in a second); capacities unit on both sides for even-indexed
+    markets and uniform on {1..3} per user for odd ones; no biases."""
+    sizes = batched_market_sizes(count, lo, hi, seed)
+    rng = np.random.default_rng(seed + 1)
+    pools = [round_to_bf16(_factors(rng, hi, d, "normal")) for _ in range(4)]
+    out = []
+    for i, (N, M, kind) in enumerate(sizes):
+        mats = []
+        for pool, rows in zip(pools, (N, N, M, M)):
+            off = int(rng.integers(0, hi - rows + 1))
+            mats.append(np.ascontiguousarray(pool[off:off + rows]))
+        n = _capacities(rng, N, kind)
+        m = _capacities(rng, M, kind)
+        out.append(Market(mats[0], mats[1], mats[2], mats[3], None, None, n, m, float(sigma), "bf16",
+                          seed * 100000 + i, f"batched #{i} N={N} M={M} d={d} {kind}"))
+    return out
+
+
 def serving_workload(count: int, rate: float = 200.0, lo: int = 1000, hi: int = 200_000, resolve_frac: float = 0.3,
                      perturb_std: float = 0.01, sigma: float = 1.0, seed: int = 1004, dims=(32, 64)) -> list:
     """A Poisson stream of solve requests: arrival times (rate per second),
