@@ -80,6 +80,37 @@ def load_peaks() -> dict:
     return dict(FALLBACK_PEAKS)
 
 
+KERNEL_SOURCES = {
+    "fused": ["paper_2411_19214_gb300/csrc/fused.cu", "paper_2411_19214_gb300/csrc/tu_internal.cuh"],
+    "dense": ["paper_2411_19214_gb300/csrc/dense.cu", "paper_2411_19214_gb300/csrc/tu_internal.cuh"],
+}
+
+
+def source_hash(kind: str) -> str:
+    """sha256 over the source files of a kernel family (ties a traffic capture to the code it measured)."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES[kind]:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(entry: str):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+    a kernel from profiles/traffic.json, or None when there is no capture or
+    the kernel's sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        table = json.load(f)
+    e = table.get(entry)
+    if not e or e.get("sha256") != source_hash(e["sources"]):
+        return None
+    return float(e["bytes_per_launch"])
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -484,7 +515,8 @@ def run_batched(args):
                        "markets": len(mks), "pair_evals_per_sweep": pair_evals,
                        "l2": "inputs larger than L2 (about 1 GB of packed factors); no flush"},
             "roofline": {"bound": "tensor", "achieved": flops / avg_pass_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                         "frac": flops / avg_pass_s / 1e12 / peak, "traffic": None,
+                         "frac": flops / avg_pass_s / 1e12 / peak,
+                         "traffic": measured_traffic("fused batched 512 markets d32"),
                          "kernel": "k_fused_halfsweep batched (tcgen05 BF16 MMA, K=64, + ex2 row reduction)",
                          "per_launch": f"{flops:.4g} flop in {avg_pass_s * 1e3:.3f} ms average over {passes} launches",
                          "peak_source": f"{peaks.get('source')} bf16_tflops_sustained"},
@@ -656,7 +688,8 @@ def run_ours(args):
         achieved = flops / avg_pass_s / 1e12
         peak = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
+                    "frac": achieved / peak,
+                    "traffic": measured_traffic("fused 1Mx1M d64") if args.shape is None else None,
                     "kernel": "k_fused_halfsweep (tcgen05 BF16 MMA + ex2 row reduction)",
                     "per_launch": f"{flops:.4g} flop (2*N*M*2d) in {avg_pass_s * 1e3:.2f} ms average over "
                                   f"{passes} launches",
@@ -673,7 +706,8 @@ def run_ours(args):
         achieved = bytes_ / avg_pass_s / 1e9
         peak = peaks.get("hbm_gbs")
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": None, "kernel": "dense row/column pass (A-hat stream)",
+                    "traffic": measured_traffic("dense rowpass 20000x10000") if args.shape is None else None,
+                    "kernel": "dense row/column pass (A-hat stream)",
                     "per_launch": f"{bytes_:.4g} B (N*ldA*4) in {avg_pass_s * 1e3:.3f} ms average over "
                                   f"{passes} launches",
                     "peak_source": f"{peaks.get('source')} hbm_gbs"}

@@ -136,8 +136,6 @@ __global__ void __launch_bounds__(kThreads) k_dense_rowpass(
     double* __restrict__ log_u, double* __restrict__ ell, double* __restrict__ partials, int residual,
     int update, const double* __restrict__ omega_p) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const double shift = *lmax_partner;
-  const double omega = omega_p ? *omega_p : 1.0;
   const int64_t n4 = ld / 4;
   const float4* w4 = reinterpret_cast<const float4*>(w);
   PartialAcc acc;
@@ -148,8 +146,11 @@ __global__ void __launch_bounds__(kThreads) k_dense_rowpass(
   int count = 0;
   auto flush = [&]() {
     if (parked_row >= 0) {
+      // scalars read here rather than kept live across the streaming loop
+      const double shift = __ldg(lmax_partner);
+      const double omega = (update && omega_p != nullptr) ? __ldg(omega_p) : 1.0;
       const RowResult rr = row_update((double)logf(parked), shift, b2s ? b2s[parked_row] : 0.0f, mass[parked_row],
-                                      log_u[parked_row], residual != 0, update ? omega : 1.0);
+                                      log_u[parked_row], residual != 0, omega);
       if (update) {
         log_u[parked_row] = rr.log_u;
         ell[parked_row] = rr.ell;
