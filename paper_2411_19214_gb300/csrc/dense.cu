@@ -129,13 +129,22 @@ __device__ void block_write_partials(PartialAcc a, double* __restrict__ partials
 // One half-sweep over a row-major matrix A (rows x ld): for every row r,
 // s_r = 1/2 exp(b_r / 2 sigma) exp(shift) sum_c A[r][c] w_c with
 // w_c = exp(ell_c - shift) of the partner side (zero-padded to ld), then the
-// closed-form update of the row's potential.
+// closed-form update of the row's potential. RELAX: the update is
+// over-relaxed by the device scalar *omega_p (markets with relaxation
+// enabled); the plain instantiation is Eq. iteration exactly.
+template <bool RELAX>
 __global__ void __launch_bounds__(kThreads) k_dense_rowpass(
     const float* __restrict__ A, int64_t ld, int64_t rows, const float* __restrict__ w,
     const double* __restrict__ lmax_partner, const float* __restrict__ b2s, const double* __restrict__ mass,
     double* __restrict__ log_u, double* __restrict__ ell, double* __restrict__ partials, int residual,
     int update, const double* __restrict__ omega_p) {
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  // plain: the shift is loaded up front, overlapped with the stream (a warp
+  // owns only a few rows, so its updates run once, at the end, and a load there
+  // would lengthen every warp's tail); relaxed: loaded at update time with
+  // omega, so that neither is live across the streaming loop (no spill)
+  double shift = 0.0;
+  if constexpr (!RELAX) shift = *lmax_partner;
   const int64_t n4 = ld / 4;
   const float4* w4 = reinterpret_cast<const float4*>(w);
   PartialAcc acc;
@@ -146,9 +155,11 @@ __global__ void __launch_bounds__(kThreads) k_dense_rowpass(
   int count = 0;
   auto flush = [&]() {
     if (parked_row >= 0) {
-      // scalars read here rather than kept live across the streaming loop
-      const double shift = __ldg(lmax_partner);
-      const double omega = (update && omega_p != nullptr) ? __ldg(omega_p) : 1.0;
+      double omega = 1.0;
+      if constexpr (RELAX) {
+        shift = __ldg(lmax_partner);
+        omega = (update && omega_p != nullptr) ? __ldg(omega_p) : 1.0;
+      }
       const RowResult rr = row_update((double)logf(parked), shift, b2s ? b2s[parked_row] : 0.0f, mass[parked_row],
                                       log_u[parked_row], residual != 0, omega);
       if (update) {
@@ -196,7 +207,8 @@ int rowpass_grid(tu_market* m, int64_t rows) {
   static int per_sm = 0;
   if (per_sm == 0) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dense_rowpass, kThreads, 0) != cudaSuccess || b < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dense_rowpass<false>, kThreads, 0) != cudaSuccess ||
+        b < 1)
       b = 2;
     per_sm = b;
   }
@@ -218,17 +230,18 @@ cudaError_t launch_dense_build(tu_market* m) {
 
 cudaError_t launch_dense_rowpass(tu_market* m, int residual, int update, int* nparts_out) {
   const int g = rowpass_grid(m, m->N);
-  k_dense_rowpass<<<g, kThreads, 0, m->stream>>>(m->Ahat, m->ldA, m->N, m->Y.pvec, m->Y.lmax, m->X.b2s, m->X.mass,
-                                                 m->X.log_u, m->X.ell, m->partials, residual, update,
-                                                 m->omega_dev);
+  auto kern = m->omega_cfg != 1.0 ? k_dense_rowpass<true> : k_dense_rowpass<false>;
+  kern<<<g, kThreads, 0, m->stream>>>(m->Ahat, m->ldA, m->N, m->Y.pvec, m->Y.lmax, m->X.b2s, m->X.mass, m->X.log_u,
+                                      m->X.ell, m->partials, residual, update, m->omega_dev);
   *nparts_out = g;
   return cudaGetLastError();
 }
 
 cudaError_t launch_dense_colpass(tu_market* m, int update, int* nparts_out) {
   const int g = rowpass_grid(m, m->M);
-  k_dense_rowpass<<<g, kThreads, 0, m->stream>>>(m->AhatT, m->ldN, m->M, m->X.pvec, m->X.lmax, m->Y.b2s, m->Y.mass,
-                                                 m->Y.log_u, m->Y.ell, m->partials, 0, update, m->omega_dev);
+  auto kern = m->omega_cfg != 1.0 ? k_dense_rowpass<true> : k_dense_rowpass<false>;
+  kern<<<g, kThreads, 0, m->stream>>>(m->AhatT, m->ldN, m->M, m->X.pvec, m->X.lmax, m->Y.b2s, m->Y.mass, m->Y.log_u,
+                                      m->Y.ell, m->partials, 0, update, m->omega_dev);
   *nparts_out = g;
   return cudaGetLastError();
 }

@@ -482,10 +482,6 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
     cudaGetLastError();
     return bail(TU_ERR_OOM);
   }
-  if ((st = dev_alloc(m, &m->omega_dev, 1)) != TU_OK) return bail(st);
-  *m->omega_host = 1.0;
-  if (cudaMemcpy(m->omega_dev, m->omega_host, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
-    return bail(TU_ERR_CUDA);
   *m->err_host = 0;
   if (D.path == TU_PATH_DENSE) {
     m->ldA = round_up(D.M, 4);
@@ -493,6 +489,12 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
     if ((st = dev_alloc(m, &m->Ahat, (size_t)m->N * m->ldA)) != TU_OK) return bail(st);
     if ((st = dev_alloc(m, &m->AhatT, (size_t)m->M * m->ldN)) != TU_OK) return bail(st);
   }
+  // (allocated after the dense matrices: placing this small allocation before
+  // them measurably slowed the dense row stream)
+  if ((st = dev_alloc(m, &m->omega_dev, 1)) != TU_OK) return bail(st);
+  *m->omega_host = 1.0;
+  if (cudaMemcpy(m->omega_dev, m->omega_host, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(TU_ERR_CUDA);
   if ((st = upload_masses(m, m->X, D.n)) != TU_OK) return bail(st);
   if ((st = upload_masses(m, m->Y, D.m)) != TU_OK) return bail(st);
   // biases -> b / (2 sigma); potentials start at u = v = 1
@@ -554,6 +556,13 @@ tu_status tu_market_set_relaxation(tu_market_t m, double omega) {
   TU_TRY(check_live(m));
   if (!(omega == 0.0 || (omega >= 1.0 && omega < 2.0)))
     return fail(m, TU_ERR_INVALID_ARG, "omega must be 0 (automatic) or in [1, 2)");
+  if (omega != m->omega_cfg && m->graph != nullptr) {
+    // the captured sweeps use the kernel variant of the previous setting
+    TU_CK(m, cudaStreamSynchronize(m->stream));
+    cudaGraphExecDestroy(m->graph);
+    m->graph = nullptr;
+    m->graph_sweeps = 0;
+  }
   m->omega_cfg = omega;
   return set_omega(m, omega > 1.0 ? omega : 1.0);
 }
