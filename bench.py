@@ -42,9 +42,22 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # workloads
 # ---------------------------------------------------------------------------
 
-def make_workload(name: str, rank: int, shape=None):
+def make_workload(name: str, rank: int, shape=None, fp8: bool = False):
     from synth import dense_job_market, fused_market
     kw = {} if shape is None else {"N": shape[0], "M": shape[1]}
+    if name == "fused" and fp8:
+        # the same market with unrounded FP32 factors, quantized to e4m3 by the library
+        mk = fused_market(seed=1002 + 97 * rank, dtype="fp32", **kw)
+        cfg = {"workload": "fused mini-batch IPFP (Alg. 2) with FP8 e4m3 factors (one power-of-two scale per "
+                           "side, tcgen05 kind::f8f6f4): N=M=1,000,000 users, d=64 per factor, factors N(0,1/d), "
+                           "lognormal(0,1) popularity bias on both sides, n=m=1, sigma=0.5",
+               "N": mk.N, "M": mk.M, "d": mk.d, "sigma": mk.sigma, "partition": 65536, "path": "fused",
+               "factors": "e4m3",
+               "l2": "inputs larger than L2: each half-sweep streams the 128 MB partner factor matrix "
+                     "(L2 is 129 MB); no flush between steps"}
+        if shape is not None:
+            cfg["workload"] = f"fused FP8 IPFP, reduced shape N={mk.N}, M={mk.M}, same recipe"
+        return mk, cfg, 65536
     if name == "fused":
         mk = fused_market(seed=1002 + 97 * rank, **kw)
         cfg = {"workload": "fused mini-batch IPFP (Alg. 2): N=M=1,000,000 users, d=64 per factor (MMA K=128), "
@@ -568,7 +581,7 @@ def run_ours(args):
             dist.barrier()
 
     tu.load()
-    mk, cfg, partition = make_workload(args.workload, rank, args.shape)
+    mk, cfg, partition = make_workload(args.workload, rank, args.shape, fp8=args.fp8)
     # the CPU baseline pool is spawned before the first CUDA work of this process
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -581,7 +594,7 @@ def run_ours(args):
     by = None if mk.bias_y is None else torch.from_numpy(mk.bias_y).to(dev)
     torch.cuda.synchronize()
     h = tu.tu_market_create(Fd, Kd, Gd, Ld, mk.n, mk.m, mk.sigma, bias_x=bx, bias_y=by,
-                            path=cfg["path"], partition=partition, stream=stream)
+                            path=cfg["path"], partition=partition, stream=stream, fp8=args.fp8)
     try:
         # warm-up: W single sweeps, then one untimed block of K sweeps that
         # captures the CUDA graph the timed block replays
@@ -670,7 +683,7 @@ def run_ours(args):
     # the plain FP32 blocked IPFP on the same GPU (comparison only)
     plain = None
     serving = None
-    if cfg["path"] == "fused" and not args.no_extras and rank == 0:
+    if cfg["path"] == "fused" and not args.no_extras and rank == 0 and not args.fp8:
         plain = plain_fp32_sweep(mk, dev, stream)
         serving = serving_block((20.0, 200.0), (60, 200))
 
@@ -687,13 +700,19 @@ def run_ours(args):
         flops = 2.0 * mk.N * mk.M * kp  # one half-sweep: Phi tile products over all pairs
         achieved = flops / avg_pass_s / 1e12
         peak = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
+        peak_source = f"{peaks.get('source')} bf16_tflops_sustained"
+        if args.fp8:
+            peak *= 2.0  # e4m3 dense rate = 2 x bf16 (nominal 4.5 / 2.25 PFLOP/s)
+            peak_source += " x 2 (nominal fp8/bf16 ratio)"
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak,
-                    "traffic": measured_traffic("fused 1Mx1M d64") if args.shape is None else None,
-                    "kernel": "k_fused_halfsweep (tcgen05 BF16 MMA + ex2 row reduction)",
+                    "traffic": measured_traffic("fused 1Mx1M d64") if args.shape is None and not args.fp8
+                    else None,
+                    "kernel": "k_fused_halfsweep (tcgen05 %s MMA + ex2 row reduction)" % ("e4m3" if args.fp8
+                                                                                         else "BF16"),
                     "per_launch": f"{flops:.4g} flop (2*N*M*2d) in {avg_pass_s * 1e3:.2f} ms average over "
                                   f"{passes} launches",
-                    "peak_source": f"{peaks.get('source')} bf16_tflops_sustained"}
+                    "peak_source": peak_source}
         exps = mk.N * mk.M
         sm_mhz = clk.get("sm_mhz") or 1900.0
         mufu_peak = 152 * 32 * sm_mhz * 1e6 / 1e12  # T ex2/s at the sampled clock, 32 ex2/clk/SM
@@ -714,7 +733,7 @@ def run_ours(args):
         roofline_exp = None
     line = {"metric": METRIC, "value": sweeps_per_s, "unit": "sweeps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": mk.dtype, "data": "synthetic", "config": cfg,
+            "vs_baseline": None, "dtype": "e4m3" if args.fp8 else mk.dtype, "data": "synthetic", "config": cfg,
             "gpair_evals_per_s": sweeps_per_s * pairs_per_sweep / 1e9,
             "residual_inf_after": residual, "sweeps_run": args.warmup + args.steps,
             "roofline": roofline,
@@ -755,6 +774,8 @@ def main():
                          "time per sweep, one JSON line per size; batched: 512 independent markets in one "
                          "persistent launch per half-sweep")
     ap.add_argument("--max-iter", type=int, default=20000, help="sweep cap of the batched solve")
+    ap.add_argument("--fp8", action="store_true",
+                    help="fused workload with e4m3 factors (the library quantizes the FP32 factors)")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",

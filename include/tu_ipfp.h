@@ -16,7 +16,7 @@
  *     u_x <- sqrt(n_x + s_x^2) - s_x,  s_x = 1/2 sum_y A_xy v_y
  *     v_y <- sqrt(m_y + s_y^2) - s_y,  s_y = 1/2 sum_x A_xy u_x   (new u)
  * and the equilibrium is mu_xy = A_xy u_x v_y (Eq. stable_condition).
- * The library keeps log u and log v (FP32) and evaluates the update in the
+ * The library keeps log u and log v (FP64) and evaluates the update in the
  * algebraically identical form log u = 1/2 log n - asinh(s / sqrt(n)).
  *
  * Two paths compute the same iteration:
@@ -60,7 +60,7 @@ typedef enum {
   TU_ERR_UNSUPPORTED = 7    /* valid request this build cannot serve (e.g. d > 64 on the fused path) */
 } tu_status;
 
-enum { TU_DTYPE_BF16 = 0, TU_DTYPE_FP32 = 1 };
+enum { TU_DTYPE_BF16 = 0, TU_DTYPE_FP32 = 1, TU_DTYPE_FP8E4M3 = 2 };
 enum { TU_PATH_FUSED = 0, TU_PATH_DENSE = 1 };
 
 typedef struct {
@@ -69,7 +69,14 @@ typedef struct {
   int64_t d;             /* factor dimension D of Sec. 3.3, >= 1 (fused path: <= 64) */
   int32_t dtype;         /* element type of F, K, G, L: TU_DTYPE_BF16 (uint16 bit patterns) or TU_DTYPE_FP32.
                             The fused path computes with BF16 (FP32 inputs are rounded to nearest even);
-                            the dense path computes with FP32 (BF16 inputs are widened exactly). */
+                            the dense path computes with FP32 (BF16 inputs are widened exactly).
+                            TU_DTYPE_FP8E4M3 (fused path only, 2d <= 128): F, K, G, L are FP32 and
+                            the market computes with e4m3 factors (OCP FP8: 4 exponent bits, bias 7,
+                            3 mantissa bits, largest finite 448) on the FP8 tensor cores: each side's
+                            [F | K] (resp. [G | L]) is scaled by 2^-k, k the smallest integer with
+                            max |entry| <= 448 * 2^k, and rounded to nearest even (saturating); the
+                            product is scaled back by 2^(k_X + k_Y) in FP32. This is a lower-precision
+                            model of phi (about 3 % per entry), not the BF16 one. */
   int32_t path;          /* TU_PATH_FUSED or TU_PATH_DENSE */
   const void* F;         /* N x d row-major, host or device; copied (the market owns its copy) */
   const void* K;         /* N x d row-major, host or device; copied */

@@ -22,7 +22,7 @@ from . import build as _build
 
 TU_OK, TU_ERR_INVALID_ARG, TU_ERR_OOM, TU_ERR_CUDA, TU_ERR_NOT_CONVERGED, TU_ERR_NONFINITE, TU_ERR_TIMEOUT, \
     TU_ERR_UNSUPPORTED = range(8)
-TU_DTYPE_BF16, TU_DTYPE_FP32 = 0, 1
+TU_DTYPE_BF16, TU_DTYPE_FP32, TU_DTYPE_FP8E4M3 = 0, 1, 2
 TU_PATH_FUSED, TU_PATH_DENSE = 0, 1
 
 LIB_PATH = _build.LIB
@@ -179,8 +179,10 @@ def _stream_handle(stream) -> Optional[int]:
 # ---------------------------------------------------------------------------
 
 def tu_market_create(F, K, G, L, n, m, sigma: float, *, bias_x=None, bias_y=None, path: str = "fused",
-                     partition: int = 0, stream=None) -> int:
-    """Create a market; returns the opaque handle (int). n, m: host float64."""
+                     partition: int = 0, stream=None, fp8: bool = False) -> int:
+    """Create a market; returns the opaque handle (int). n, m: host float64.
+    fp8: compute with e4m3 factors (F, K, G, L must be float32; the library
+    quantizes them with one power-of-two scale per side)."""
     lib = load()
     N, d = _shape(F)
     M, d2 = _shape(G)
@@ -189,6 +191,10 @@ def tu_market_create(F, K, G, L, n, m, sigma: float, *, bias_x=None, bias_y=None
     dt = _dtype_code(F)
     if any(_dtype_code(x) != dt for x in (K, G, L)):
         raise TypeError("F, K, G, L must share one dtype")
+    if fp8:
+        if dt != TU_DTYPE_FP32:
+            raise TypeError("fp8 markets take float32 factors")
+        dt = TU_DTYPE_FP8E4M3
     n = np.ascontiguousarray(n, dtype=np.float64)
     m = np.ascontiguousarray(m, dtype=np.float64)
     if n.shape != (N,) or m.shape != (M,):
@@ -352,13 +358,13 @@ class Market:
     """Owning wrapper of a market handle (torch CUDA tensors for outputs)."""
 
     def __init__(self, F, K, G, L, n, m, sigma, *, bias_x=None, bias_y=None, path="fused", partition=0,
-                 stream=None, device="cuda"):
+                 stream=None, device="cuda", fp8=False):
         self.N, self.d = _shape(F)
         self.M = _shape(G)[0]
         self.device = device
         self.stream = stream
         self.handle = tu_market_create(F, K, G, L, n, m, sigma, bias_x=bias_x, bias_y=bias_y, path=path,
-                                       partition=partition, stream=stream)
+                                       partition=partition, stream=stream, fp8=fp8)
 
     def sweep(self, nsweeps: int, residual: bool = False):
         return tu_ipfp_sweep(self.handle, nsweeps, residual)
@@ -466,14 +472,16 @@ class Batch:
         self.close()
 
 
-def from_synth(mk, path: str = "fused", device: str = "cuda", stream=None, partition: int = 0) -> Market:
-    """Create a :class:`Market` on the device from a ``synth.Market``."""
+def from_synth(mk, path: str = "fused", device: str = "cuda", stream=None, partition: int = 0,
+               fp8: bool = False) -> Market:
+    """Create a :class:`Market` on the device from a ``synth.Market`` (fp8: its
+    float32 factors, quantized by the library to e4m3)."""
     import torch
 
     def dev(a):
         if a is None:
             return None
-        if mk.dtype == "bf16" and a.ndim == 2:
+        if mk.dtype == "bf16" and a.ndim == 2 and not fp8:
             bits = (np.ascontiguousarray(a, dtype=np.float32).view(np.uint32) >> 16).astype(np.uint16)
             return torch.from_numpy(bits.view(np.int16)).view(torch.bfloat16).to(device)
         return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(device)
@@ -482,4 +490,4 @@ def from_synth(mk, path: str = "fused", device: str = "cuda", stream=None, parti
     bx, by = dev(mk.bias_x), dev(mk.bias_y)
     torch.cuda.synchronize()
     return Market(F, K, G, L, mk.n, mk.m, mk.sigma, bias_x=bx, bias_y=by, path=path, partition=partition,
-                  stream=stream, device=device)
+                  stream=stream, device=device, fp8=fp8)

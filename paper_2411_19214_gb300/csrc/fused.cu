@@ -270,11 +270,14 @@ __device__ __forceinline__ int item_step() {
 // to different markets (tensor maps, vectors and sizes from BatchDesc); the
 // residual partials are then written per own tile and epilogue warp instead
 // of per CTA.
-template <int KB, int STAGES, int MODE, bool BATCH>
+// F8: e4m3 factors, 128 per 128-byte row (KB = 1), tcgen05.mma kind::f8f6f4;
+// the per-side power-of-two scales are folded into p.c.
+template <int KB, int STAGES, int MODE, bool BATCH, bool F8>
 __global__ void __launch_bounds__(kThreads, 1)
     k_fused_halfsweep(const __grid_constant__ CUtensorMap tm_own, const __grid_constant__ CUtensorMap tm_partner,
                       const FusedParams p) {
   static_assert(!BATCH || MODE == kModeSweep, "batched launches run half-sweeps only");
+  static_assert(!F8 || KB == 1, "e4m3 rows are one 128-byte block");
   constexpr int ABUF = kABufs<KB>;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_u32 = smem_u32(smem_raw);
@@ -423,7 +426,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16_f32(128, kFusedPartnerRows);
+      constexpr uint32_t idesc = F8 ? idesc_e4m3_f32(128, kFusedPartnerRows) : idesc_bf16_f32(128, kFusedPartnerRows);
       int stage = 0, buf = 0, ab = 0;
       uint32_t phase = 0, tphase = 0, a_phase = 0;
       bool ok = true;
@@ -460,7 +463,11 @@ __global__ void __launch_bounds__(kThreads, 1)
               const int kb = k >> 2, kk = k & 3;
               const uint64_t adesc = sdesc_sw128(a0 + kb * kOwnBytesPerKB + h * 128 * 128 + kk * 32);
               const uint64_t bdesc = sdesc_sw128(b0 + kb * kPartnerBytesPerKB + kk * 32);
-              umma_bf16(d_tmem, adesc, bdesc, idesc, k > 0 ? 1u : 0u);
+              if constexpr (F8) {
+                umma_e4m3(d_tmem, adesc, bdesc, idesc, k > 0 ? 1u : 0u);
+              } else {
+                umma_bf16(d_tmem, adesc, bdesc, idesc, k > 0 ? 1u : 0u);
+              }
             }
           }
           umma_commit(&empty[stage]);
@@ -732,36 +739,44 @@ EncodeTiledFn get_encode_fn() {
   return fn;
 }
 
-cudaError_t make_map(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int64_t kp, int box_rows) {
+// Tensor map over packed rows x kp factors (bf16, or e4m3 bytes when fp8);
+// the box is one 128-byte swizzle row wide.
+cudaError_t make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t kp, int box_rows, bool fp8 = false) {
   EncodeTiledFn enc = get_encode_fn();
   if (enc == nullptr) return cudaErrorNotSupported;
+  const size_t esz = fp8 ? 1 : sizeof(__nv_bfloat16);
   const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)kp * sizeof(__nv_bfloat16)};
-  const cuuint32_t box[2] = {(cuuint32_t)kKBlock, (cuuint32_t)box_rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)kp * esz};
+  const cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides,
-                         box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  const CUresult r = enc(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                         const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 constexpr int kStagesKB1 = 6;
 constexpr int kStagesKB2 = 4;
 
-template <int KB, int STAGES, int MODE, bool BATCH>
+template <int KB, int STAGES, int MODE, bool BATCH, bool F8 = false>
 cudaError_t launch_kernel(const CUtensorMap& own, const CUtensorMap& partner, const FusedParams& p, int grid,
                           cudaStream_t stream) {
   static_assert(smem_bytes<KB>(STAGES) <= 232448, "shared memory budget");
-  k_fused_halfsweep<KB, STAGES, MODE, BATCH><<<grid, kThreads, smem_bytes<KB>(STAGES), stream>>>(own, partner, p);
+  k_fused_halfsweep<KB, STAGES, MODE, BATCH, F8><<<grid, kThreads, smem_bytes<KB>(STAGES), stream>>>(own, partner,
+                                                                                                     p);
   return cudaGetLastError();
 }
 
 template <int MODE, bool BATCH>
 cudaError_t set_attributes_mode() {
-  cudaError_t e = cudaFuncSetAttribute(k_fused_halfsweep<1, kStagesKB1, MODE, BATCH>,
+  cudaError_t e = cudaFuncSetAttribute(k_fused_halfsweep<1, kStagesKB1, MODE, BATCH, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>(kStagesKB1));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_fused_halfsweep<2, kStagesKB2, MODE, BATCH>,
+  e = cudaFuncSetAttribute(k_fused_halfsweep<1, kStagesKB1, MODE, BATCH, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>(kStagesKB1));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_fused_halfsweep<2, kStagesKB2, MODE, BATCH, false>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<2>(kStagesKB2));
 }
 
@@ -774,16 +789,21 @@ cudaError_t set_kernel_attributes() {
   return e;
 }
 
+// kp: packed width in elements (bf16: 64 or 128; e4m3: 128, one 128-byte block).
 template <int MODE, bool BATCH = false>
-cudaError_t launch_any(int64_t kp, const CUtensorMap& own, const CUtensorMap& partner, const FusedParams& p,
-                       int grid, cudaStream_t stream) {
+cudaError_t launch_any(int64_t kp, bool fp8, const CUtensorMap& own, const CUtensorMap& partner,
+                       const FusedParams& p, int grid, cudaStream_t stream) {
+  if (fp8) {
+    if (kp != 128) return cudaErrorNotSupported;
+    return launch_kernel<1, kStagesKB1, MODE, BATCH, true>(own, partner, p, grid, stream);
+  }
   const int kb = (int)(kp / kKBlock);
   if (kb == 1) return launch_kernel<1, kStagesKB1, MODE, BATCH>(own, partner, p, grid, stream);
   if (kb == 2) return launch_kernel<2, kStagesKB2, MODE, BATCH>(own, partner, p, grid, stream);
   return cudaErrorNotSupported;
 }
 
-FusedParams base_params(int64_t rows, int64_t row0, int64_t col0, int64_t ncols, double sigma) {
+FusedParams base_params(int64_t rows, int64_t row0, int64_t col0, int64_t ncols, float c) {
   FusedParams p{};
   p.rows = rows;
   p.row0 = row0;
@@ -791,7 +811,7 @@ FusedParams base_params(int64_t rows, int64_t row0, int64_t col0, int64_t ncols,
   p.ncols = ncols;
   p.num_own_tiles = (int)((rows + kFusedOwnRows - 1) / kFusedOwnRows);
   p.num_partner_tiles = (int)((ncols + kFusedPartnerRows - 1) / kFusedPartnerRows);
-  p.c = (float)(1.4426950408889634 / (2.0 * sigma));
+  p.c = c;
   return p;
 }
 
@@ -804,18 +824,21 @@ int grid_for_tiles(int tiles, int num_sms) {
 }  // namespace
 
 cudaError_t fused_prepare(tu_market* m) {
+  const bool f8 = m->dtype == TU_DTYPE_FP8E4M3;
+  const void* x = f8 ? (const void*)m->X.fac8 : (const void*)m->X.fac16;
+  const void* y = f8 ? (const void*)m->Y.fac8 : (const void*)m->Y.fac16;
   cudaError_t e;
-  if ((e = make_map(&m->X.tm_own, m->X.fac16, m->X.rows, m->kp, kFusedOwnRows)) != cudaSuccess) return e;
-  if ((e = make_map(&m->X.tm_partner, m->X.fac16, m->X.rows, m->kp, kFusedPartnerRows)) != cudaSuccess) return e;
-  if ((e = make_map(&m->Y.tm_own, m->Y.fac16, m->Y.rows, m->kp, kFusedOwnRows)) != cudaSuccess) return e;
-  if ((e = make_map(&m->Y.tm_partner, m->Y.fac16, m->Y.rows, m->kp, kFusedPartnerRows)) != cudaSuccess) return e;
+  if ((e = make_map(&m->X.tm_own, x, m->X.rows, m->kp, kFusedOwnRows, f8)) != cudaSuccess) return e;
+  if ((e = make_map(&m->X.tm_partner, x, m->X.rows, m->kp, kFusedPartnerRows, f8)) != cudaSuccess) return e;
+  if ((e = make_map(&m->Y.tm_own, y, m->Y.rows, m->kp, kFusedOwnRows, f8)) != cudaSuccess) return e;
+  if ((e = make_map(&m->Y.tm_partner, y, m->Y.rows, m->kp, kFusedPartnerRows, f8)) != cudaSuccess) return e;
   return set_kernel_attributes();
 }
 
 cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int update, int* nparts_out) {
   Side& own = side == 0 ? m->X : m->Y;
   Side& partner = side == 0 ? m->Y : m->X;
-  FusedParams p = base_params(own.rows, 0, 0, partner.rows, m->sigma);
+  FusedParams p = base_params(own.rows, 0, 0, partner.rows, m->cmul);
   p.g = partner.pvec;
   p.lmax = partner.lmax;
   p.b2s = own.b2s;
@@ -829,7 +852,8 @@ cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int upd
   p.omega = m->omega_dev;
   const int grid = grid_for_tiles(p.num_own_tiles, m->num_sms);
   *nparts_out = grid;
-  return launch_any<kModeSweep>(m->kp, own.tm_own, partner.tm_partner, p, grid, m->stream);
+  return launch_any<kModeSweep>(m->kp, m->dtype == TU_DTYPE_FP8E4M3, own.tm_own, partner.tm_partner, p, grid,
+                                m->stream);
 }
 
 // Ranked lists of own users [row0, row0 + nrows) over all partners (the
@@ -839,7 +863,7 @@ cudaError_t launch_fused_topk(tu_market* m, int side, int k, int64_t row0, int64
                               float* logmu, float* hand_v, int32_t* hand_i) {
   Side& own = side == 0 ? m->X : m->Y;
   Side& partner = side == 0 ? m->Y : m->X;
-  FusedParams p = base_params(nrows, row0, 0, partner.rows, m->sigma);
+  FusedParams p = base_params(nrows, row0, 0, partner.rows, m->cmul);
   p.g = partner.pvec;
   p.lmax = partner.lmax;
   p.ell = own.ell;
@@ -850,15 +874,15 @@ cudaError_t launch_fused_topk(tu_market* m, int side, int k, int64_t row0, int64
   p.logmu = logmu;
   p.hand_v = hand_v;
   p.hand_i = hand_i;
-  return launch_any<kModeTopK>(m->kp, own.tm_own, partner.tm_partner, p, grid_for_tiles(p.num_own_tiles, m->num_sms),
-                               m->stream);
+  return launch_any<kModeTopK>(m->kp, m->dtype == TU_DTYPE_FP8E4M3, own.tm_own, partner.tm_partner, p,
+                               grid_for_tiles(p.num_own_tiles, m->num_sms), m->stream);
 }
 
 // mu for own X users [x0, x0 + nx) and partners [y0, y0 + ny) (the Y partner
 // vector must have been prepared in log2 mode).
 cudaError_t launch_fused_mu(tu_market* m, int64_t x0, int64_t nx, int64_t y0, int64_t ny, float* out, int64_t ld) {
   const int64_t c0 = y0 & ~(int64_t)3;  // the g bulk copies start 16-byte aligned
-  FusedParams p = base_params(nx, x0, c0, y0 + ny - c0, m->sigma);
+  FusedParams p = base_params(nx, x0, c0, y0 + ny - c0, m->cmul);
   p.g = m->Y.pvec;
   p.lmax = m->Y.lmax;
   p.ell = m->X.ell;
@@ -868,8 +892,8 @@ cudaError_t launch_fused_mu(tu_market* m, int64_t x0, int64_t nx, int64_t y0, in
   p.ld = ld;
   p.y0 = y0;
   p.ny = ny;
-  return launch_any<kModeMu>(m->kp, m->X.tm_own, m->Y.tm_partner, p, grid_for_tiles(p.num_own_tiles, m->num_sms),
-                             m->stream);
+  return launch_any<kModeMu>(m->kp, m->dtype == TU_DTYPE_FP8E4M3, m->X.tm_own, m->Y.tm_partner, p,
+                             grid_for_tiles(p.num_own_tiles, m->num_sms), m->stream);
 }
 
 // Same kernel on caller-described buffers (no market object): used by the
@@ -880,7 +904,7 @@ cudaError_t launch_fused_halfsweep_raw(const FusedRaw& r, cudaStream_t stream, i
   if ((e = make_map(&own_map, r.own16, r.rows, r.kp, kFusedOwnRows)) != cudaSuccess) return e;
   if ((e = make_map(&partner_map, r.par16, r.cols, r.kp, kFusedPartnerRows)) != cudaSuccess) return e;
   if ((e = set_kernel_attributes()) != cudaSuccess) return e;
-  FusedParams p = base_params(r.rows, 0, 0, r.cols, r.sigma);
+  FusedParams p = base_params(r.rows, 0, 0, r.cols, (float)(1.4426950408889634 / (2.0 * r.sigma)));
   p.g = r.g;
   p.lmax = r.lmax;
   p.b2s = r.b2s;
@@ -893,7 +917,7 @@ cudaError_t launch_fused_halfsweep_raw(const FusedRaw& r, cudaStream_t stream, i
   p.update = 1;
   const int grid = grid_for_tiles(p.num_own_tiles, num_sms);
   *nparts_out = grid;
-  return launch_any<kModeSweep>(r.kp, own_map, partner_map, p, grid, stream);
+  return launch_any<kModeSweep>(r.kp, false, own_map, partner_map, p, grid, stream);
 }
 
 // One half-sweep over the items of many markets (batched launch). The
@@ -912,7 +936,7 @@ cudaError_t launch_fused_batch(const BatchLaunch& b, cudaStream_t stream) {
   p.update = b.update;
   CUtensorMap unused;
   memset(&unused, 0, sizeof(unused));
-  return launch_any<kModeSweep, true>(b.kp, unused, unused, p, b.grid, stream);
+  return launch_any<kModeSweep, true>(b.kp, b.fp8 != 0, unused, unused, p, b.grid, stream);
 }
 
 }  // namespace tu

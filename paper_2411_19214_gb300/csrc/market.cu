@@ -100,7 +100,9 @@ tu_status side_alloc(tu_market* m, Side& s, int64_t rows, bool has_bias) {
   TU_TRY(dev_alloc(m, &s.mass, s.rows_pad));
   TU_TRY(dev_alloc(m, &s.lmax, 1));
   if (has_bias) TU_TRY(dev_alloc(m, &s.b2s, s.rows_pad));
-  if (m->path == TU_PATH_FUSED) {
+  if (m->path == TU_PATH_FUSED && m->dtype == TU_DTYPE_FP8E4M3) {
+    TU_TRY(dev_alloc(m, &s.fac8, (size_t)rows * 128));
+  } else if (m->path == TU_PATH_FUSED) {
     TU_TRY(dev_alloc(m, &s.fac16, (size_t)rows * m->kp));
   } else {
     TU_TRY(dev_alloc(m, &s.fac32, (size_t)rows * m->kp));
@@ -116,6 +118,7 @@ void side_free(Side& s) {
   cudaFree(s.lmax);
   cudaFree(s.b2s);
   cudaFree(s.fac16);
+  cudaFree(s.fac8);
   cudaFree(s.fac32);
   s = Side();
 }
@@ -142,19 +145,56 @@ tu_status upload_masses(tu_market* m, Side& s, const double* host) {
   return TU_OK;
 }
 
+// FP8: smallest integer k with maxabs <= 448 * 2^k (exact comparisons with
+// powers of two; 0 for an all-zero side).
+int fp8_side_exponent(float maxabs) {
+  if (!(maxabs > 0.0f)) return 0;
+  int e = 0;
+  std::frexp((double)maxabs / 448.0, &e);
+  int k = e;
+  while (std::ldexp(448.0, k - 1) >= (double)maxabs) --k;
+  while (std::ldexp(448.0, k) < (double)maxabs) ++k;
+  return k;
+}
+
+// FP8: quantize one side's FP32 factor pair (device pointers) into s.fac8.
+tu_status pack_side_fp8(tu_market* m, Side& s, const void* a, const void* b, float* scratch) {
+  float mx = 0.0f;
+  TU_CK(m, launch_max_abs(m, static_cast<const float*>(a), static_cast<const float*>(b), s.rows * m->d, scratch));
+  TU_CK(m, cudaMemcpyAsync(&mx, scratch, sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+  TU_CK(m, cudaStreamSynchronize(m->stream));
+  if (!std::isfinite(mx)) return fail(m, TU_ERR_NONFINITE, "factor matrices contain NaN or Inf");
+  s.fp8_exp = fp8_side_exponent(mx);
+  TU_CK(m, launch_pack_fp8(m, s, static_cast<const float*>(a), static_cast<const float*>(b), s.fp8_exp));
+  return TU_OK;
+}
+
 // Pack both factor pairs (and rebuild the dense kernel) from caller pointers.
 tu_status load_factors(tu_market* m, const void* F, const void* K, const void* G, const void* L) {
+  const bool fp8 = m->dtype == TU_DTYPE_FP8E4M3;
   const size_t esz = m->dtype == TU_DTYPE_BF16 ? 2 : 4;
   const size_t bx = (size_t)m->N * m->d * esz, by = (size_t)m->M * m->d * esz;
   TU_TRY(ensure_staging(m, 2 * (bx > by ? bx : by)));
+  float* fscratch = nullptr;
+  if (fp8) TU_TRY(dev_alloc(m, &fscratch, 1));
+  auto pack = [&](Side& s, const void* a, const void* b) -> tu_status {
+    if (fp8) return pack_side_fp8(m, s, a, b, fscratch);
+    TU_CK(m, launch_pack_factors(m, s, a, b, m->dtype));
+    return TU_OK;
+  };
   const void *a = nullptr, *b = nullptr;
-  TU_TRY(device_view(m, F, bx, 0, &a));
-  TU_TRY(device_view(m, K, bx, bx, &b));
-  TU_CK(m, launch_pack_factors(m, m->X, a, b, m->dtype));
-  TU_CK(m, cudaStreamSynchronize(m->stream));  // the staging buffer is reused for the other side
-  TU_TRY(device_view(m, G, by, 0, &a));
-  TU_TRY(device_view(m, L, by, by, &b));
-  TU_CK(m, launch_pack_factors(m, m->Y, a, b, m->dtype));
+  tu_status st = device_view(m, F, bx, 0, &a);
+  if (st == TU_OK) st = device_view(m, K, bx, bx, &b);
+  if (st == TU_OK) st = pack(m->X, a, b);
+  if (st == TU_OK && cudaStreamSynchronize(m->stream) != cudaSuccess)  // the staging buffer is reused
+    st = fail_cuda(m, cudaGetLastError(), "cudaStreamSynchronize");
+  if (st == TU_OK) st = device_view(m, G, by, 0, &a);
+  if (st == TU_OK) st = device_view(m, L, by, by, &b);
+  if (st == TU_OK) st = pack(m->Y, a, b);
+  cudaFree(fscratch);
+  if (st != TU_OK) return st;
+  // the multiplier of <a_x, b_y> in the exponent (log2 units)
+  m->cmul = (float)std::ldexp(1.4426950408889634 / (2.0 * m->sigma), fp8 ? m->X.fp8_exp + m->Y.fp8_exp : 0);
   // exponent-range check (Cauchy-Schwarz bound of |phi_hat| / (2 sigma))
   float* norms = nullptr;
   TU_TRY(dev_alloc(m, &norms, 2));
@@ -167,7 +207,7 @@ tu_status load_factors(tu_market* m, const void* F, const void* K, const void* G
   if (e != cudaSuccess) return fail_cuda(m, e, "factor norms");
   if (!std::isfinite(hn[0]) || !std::isfinite(hn[1]))
     return fail(m, TU_ERR_NONFINITE, "factor matrices contain NaN or Inf");
-  const double bound = (double)hn[0] * (double)hn[1] / (2.0 * m->sigma);
+  const double bound = (double)hn[0] * (double)hn[1] / (2.0 * m->sigma);  // FP8: norms of the quantized rows
   if (bound > 40.0) {
     char buf[160];
     snprintf(buf, sizeof(buf), "max|a_x| * max|b_y| / (2 sigma) = %.3g exceeds 40 (FP32 exponent range)", bound);
@@ -427,12 +467,13 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
   const tu_market_desc& D = *desc;
   if (D.N < 1 || D.M < 1 || D.d < 1 || D.N > (int64_t)1 << 31 || D.M > (int64_t)1 << 31 || D.d > 4096)
     return TU_ERR_INVALID_ARG;
-  if (D.dtype != TU_DTYPE_BF16 && D.dtype != TU_DTYPE_FP32) return TU_ERR_INVALID_ARG;
+  if (D.dtype != TU_DTYPE_BF16 && D.dtype != TU_DTYPE_FP32 && D.dtype != TU_DTYPE_FP8E4M3) return TU_ERR_INVALID_ARG;
   if (D.path != TU_PATH_FUSED && D.path != TU_PATH_DENSE) return TU_ERR_INVALID_ARG;
   if (!D.F || !D.K || !D.G || !D.L || !D.n || !D.m) return TU_ERR_INVALID_ARG;
   if (!(D.sigma > 0.0) || !std::isfinite(D.sigma)) return TU_ERR_INVALID_ARG;
   if (D.partition < 0) return TU_ERR_INVALID_ARG;
   if (D.path == TU_PATH_FUSED && 2 * D.d > 2 * kKBlock) return TU_ERR_UNSUPPORTED;
+  if (D.dtype == TU_DTYPE_FP8E4M3 && D.path != TU_PATH_FUSED) return TU_ERR_UNSUPPORTED;
   // the dense path keeps A-hat and its transpose resident
   if (D.path == TU_PATH_DENSE &&
       (double)D.N * (double)round_up(D.M, 4) * 4.0 + (double)D.M * (double)round_up(D.N, 4) * 4.0 > 200e9)
@@ -443,7 +484,7 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
   m->N = D.N;
   m->M = D.M;
   m->d = D.d;
-  m->kp = round_up(2 * D.d, kKBlock);
+  m->kp = D.dtype == TU_DTYPE_FP8E4M3 ? 128 : round_up(2 * D.d, kKBlock);
   m->dtype = D.dtype;
   m->path = D.path;
   m->sigma = D.sigma;

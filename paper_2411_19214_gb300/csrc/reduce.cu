@@ -3,6 +3,8 @@
 // half-sweep, and the FP64 reductions that close it.
 #include "tu_internal.cuh"
 
+#include <cuda_fp8.h>
+
 namespace tu {
 
 namespace {
@@ -41,6 +43,42 @@ __global__ void k_pack_factors(const void* __restrict__ A, const void* __restric
   }
 }
 
+// Largest |entry| of two FP32 arrays of `count` entries each (non-negative
+// floats order like their bit patterns, so an unsigned atomicMax is exact).
+__global__ void k_max_abs(const float* __restrict__ A, const float* __restrict__ B, int64_t count,
+                          unsigned int* __restrict__ out) {
+  __shared__ float red[kThreads / 32];
+  float best = 0.0f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    best = fmaxf(best, fmaxf(fabsf(A[i]), fabsf(B[i])));
+  for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float b = 0.0f;
+    for (int w = 0; w < kThreads / 32; ++w) b = fmaxf(b, red[w]);
+    atomicMax(out, __float_as_uint(b));
+  }
+}
+
+// FP8 packing: row r of the output is [A_r | B_r | 0] * 2^-k rounded to the
+// nearest e4m3 value (ties to even), saturating at +-448; 128 bytes per row.
+__global__ void k_pack_fp8(const float* __restrict__ A, const float* __restrict__ B, int64_t rows, int64_t d,
+                           float scale, uint8_t* __restrict__ out) {
+  const int64_t total = rows * 128;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / 128;
+    const int64_t k = i - r * 128;
+    float v = 0.0f;
+    if (k < d) {
+      v = A[r * d + k];
+    } else if (k < 2 * d) {
+      v = B[r * d + (k - d)];
+    }
+    out[i] = (uint8_t)__nv_cvt_float_to_fp8(v * scale, __NV_SATFINITE, __NV_E4M3);
+  }
+}
+
 __global__ void k_init_side(const float* __restrict__ bias, int has_bias, float inv2s, int64_t rows,
                             int64_t rows_pad, float* __restrict__ b2s, double* __restrict__ log_u,
                             double* __restrict__ ell) {
@@ -71,7 +109,8 @@ __global__ void k_get_potentials(const double* __restrict__ log_u, int64_t rows,
 }
 
 __global__ void k_row_norm_max(const float* __restrict__ f32, const __nv_bfloat16* __restrict__ f16,
-                               int64_t rows, int64_t kp, unsigned int* __restrict__ out) {
+                               const uint8_t* __restrict__ f8, float f8scale, int64_t rows, int64_t kp,
+                               unsigned int* __restrict__ out) {
   __shared__ float red[kThreads / 32];
   float best = 0.0f;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -79,7 +118,13 @@ __global__ void k_row_norm_max(const float* __restrict__ f32, const __nv_bfloat1
        r += (int64_t)gridDim.x * (kThreads / 32)) {
     float s = 0.0f;
     for (int64_t k = lane; k < kp; k += 32) {
-      const float v = f32 ? f32[r * kp + k] : __bfloat162float(f16[r * kp + k]);
+      float v;
+      if (f8 != nullptr) {
+        const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)f8[r * kp + k], __NV_E4M3);
+        v = __half2float(__half(h)) * f8scale;
+      } else {
+        v = f32 ? f32[r * kp + k] : __bfloat162float(f16[r * kp + k]);
+      }
       s = fmaf(v, v, s);
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -252,8 +297,22 @@ cudaError_t launch_row_norms(tu_market* m, Side& s, float* out_max) {
   if (e != cudaSuccess) return e;
   int64_t blocks = (s.rows + (kThreads / 32) - 1) / (kThreads / 32);
   if (blocks > (int64_t)m->num_sms * 8) blocks = (int64_t)m->num_sms * 8;
-  k_row_norm_max<<<(int)blocks, kThreads, 0, m->stream>>>(s.fac32, s.fac16, s.rows, m->kp,
-                                                          reinterpret_cast<unsigned int*>(out_max));
+  k_row_norm_max<<<(int)blocks, kThreads, 0, m->stream>>>(s.fac32, s.fac16, s.fac8, ldexpf(1.0f, s.fp8_exp), s.rows,
+                                                          m->kp, reinterpret_cast<unsigned int*>(out_max));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_max_abs(tu_market* m, const float* A, const float* B, int64_t count, float* out_max) {
+  cudaError_t e = cudaMemsetAsync(out_max, 0, sizeof(float), m->stream);
+  if (e != cudaSuccess) return e;
+  k_max_abs<<<grid_for(count, m->num_sms, 8), kThreads, 0, m->stream>>>(A, B, count,
+                                                                       reinterpret_cast<unsigned int*>(out_max));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_fp8(tu_market* m, Side& s, const float* A, const float* B, int k) {
+  const int g = grid_for(s.rows * 128, m->num_sms, 16);
+  k_pack_fp8<<<g, kThreads, 0, m->stream>>>(A, B, s.rows, m->d, ldexpf(1.0f, -k), s.fac8);
   return cudaGetLastError();
 }
 

@@ -49,6 +49,8 @@ struct Side {
   double* lmax = nullptr;   // device scalar: max_i ell_i
   double sum_mass = 0.0;    // host copy of sum of capacities
   __nv_bfloat16* fac16 = nullptr;  // packed [F | K] (or [G | L]) rows x kp, bf16, zero padded
+  uint8_t* fac8 = nullptr;         // FP8 markets: packed rows x 128 e4m3 of [F | K] * 2^-fp8_exp
+  int fp8_exp = 0;                 // FP8 markets: this side's power-of-two scale k
   float* fac32 = nullptr;          // packed rows x kp, fp32 (dense path), zero padded
   CUtensorMap tm_own;       // TMA map, box kKBlock x kFusedOwnRows
   CUtensorMap tm_partner;   // TMA map, box kKBlock x kFusedPartnerRows
@@ -58,7 +60,8 @@ struct Side {
 
 struct tu_market {
   int64_t N = 0, M = 0, d = 0;
-  int64_t kp = 0;           // packed inner dimension: 2d rounded up to a multiple of 64
+  int64_t kp = 0;           // packed inner dimension: 2d rounded up to a multiple of 64 (FP8: 128)
+  float cmul = 0.0f;        // fused path: log2(e) / (2 sigma), times 2^(k_X + k_Y) for FP8 markets
   int dtype = 0, path = 0;
   double sigma = 1.0;
   int64_t partition = 0;
@@ -113,6 +116,10 @@ cudaError_t launch_reset_potentials(tu_market* m, Side& s);
 cudaError_t launch_set_potentials(tu_market* m, Side& s, const float* log_u_dev);
 cudaError_t launch_get_potentials(tu_market* m, Side& s, float* out_dev);  // FP64 state -> FP32
 cudaError_t launch_row_norms(tu_market* m, Side& s, float* out_max);
+// FP8 markets: max |entry| of the FP32 factor pair (A, B: rows x d each) into *out_max
+cudaError_t launch_max_abs(tu_market* m, const float* A, const float* B, int64_t count, float* out_max);
+// FP8 markets: pack [A | B | 0] * 2^-k into s.fac8 (rows x 128 e4m3, round to nearest even, saturating)
+cudaError_t launch_pack_fp8(tu_market* m, Side& s, const float* A, const float* B, int k);
 cudaError_t launch_sum_sq(tu_market* m, Side& s, int is_x);  // results[kResXSq or kResYSq] = sum exp(2 log u)
 
 // dense.cu
@@ -182,6 +189,7 @@ struct BatchLaunch {
   int* err;
   int grid;
   int64_t kp;              // 64 or 128, the same for every market
+  int fp8;                 // e4m3 factors (kp = 128 bytes per row), the same for every market
   int residual;
   int update;
 };
@@ -392,6 +400,16 @@ __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint6
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// D[tmem] (+)= A[smem] * B[smem]^T, both K-major, e4m3 in (32 per 32-byte K step), FP32 accumulate.
+__device__ __forceinline__ void umma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 // Arrive on an mbarrier once every tcgen05 operation issued so far by this thread completes.
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -419,6 +437,11 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t smem_addr) {
 // N >> 3 in bits 17-22, M >> 4 in bits 24-28.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+// Instruction descriptor of tcgen05.mma kind::f8f6f4: D FP32 (bits 4-5 = 1),
+// A and B e4m3 (format 0 in bits 7-9 and 10-12), both K-major, N >> 3, M >> 4.
+__host__ __device__ constexpr uint32_t idesc_e4m3_f32(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // 32 lanes x 32 columns of FP32 from TMEM (lane quadrant fixed by the warp), then wait.

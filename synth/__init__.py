@@ -10,6 +10,9 @@ from .markets import (  # noqa: F401
     Market,
     make_market,
     round_to_bf16,
+    round_to_e4m3,
+    fp8_side_exponent,
+    fp8_quantized,
     bf16_bits,
     dense_job_market,
     fused_market,

@@ -122,6 +122,48 @@ def _factors(rng: np.random.Generator, rows: int, d: int, dist: str) -> np.ndarr
     raise ValueError(f"unknown factor distribution {dist!r}")
 
 
+E4M3_MAX = 448.0
+
+
+def round_to_e4m3(x) -> np.ndarray:
+    """Nearest OCP FP8 E4M3 value (4 exponent bits with bias 7, 3 mantissa
+    bits, subnormal quantum 2^-9, no infinities, largest finite 448), ties to
+    even, saturating at +-448. Returns float64 (every e4m3 value is exact)."""
+    x = np.asarray(x, np.float64)
+    a = np.abs(x)
+    _, ex = np.frexp(a)              # a = m * 2^ex with m in [0.5, 1)
+    e = np.maximum(ex - 1, -6)       # binade; below 2^-6 the quantum stays 2^-9
+    q = np.ldexp(1.0, e - 3)
+    r = np.minimum(np.round(a / q) * q, E4M3_MAX)
+    return np.copysign(r, x)
+
+
+def fp8_side_exponent(A, B) -> int:
+    """Smallest integer k with max |entry| of A and B <= 448 * 2^k (0 if both are zero)."""
+    mx = float(max(np.max(np.abs(A)), np.max(np.abs(B))))
+    if not mx > 0.0:
+        return 0
+    k = math.frexp(mx / E4M3_MAX)[1]
+    while math.ldexp(E4M3_MAX, k - 1) >= mx:
+        k -= 1
+    while math.ldexp(E4M3_MAX, k) < mx:
+        k += 1
+    return k
+
+
+def fp8_quantized(mk: "Market"):
+    """The factors an FP8 market computes with: each side's [F | K] (resp.
+    [G | L]) scaled by 2^-k (fp8_side_exponent of that side), rounded to e4m3
+    and scaled back; exact in float32. Returns (market, (k_X, k_Y))."""
+    kx = fp8_side_exponent(mk.F, mk.K)
+    ky = fp8_side_exponent(mk.G, mk.L)
+
+    def q(a, k):
+        return (round_to_e4m3(np.asarray(a, np.float64) * 2.0 ** -k) * 2.0 ** k).astype(np.float32)
+
+    return dataclasses.replace(mk, F=q(mk.F, kx), K=q(mk.K, kx), G=q(mk.G, ky), L=q(mk.L, ky), dtype="fp8"), (kx, ky)
+
+
 def make_market(N: int, M: int, d: int, *, sigma: float, seed: int,
                 dist: str = "normal", bias_x: bool = False, bias_y: bool = False,
                 n_kind: str = "unit", m_kind: str = "unit", dtype: str = "bf16",
