@@ -146,6 +146,26 @@ tu_status tu_mu_block(tu_market_t mkt, int64_t x0, int64_t nx, int64_t y0, int64
 tu_status tu_topk_partners(tu_market_t mkt, int side, int k, int64_t row0, int64_t nrows, int32_t* idx,
                            float* log_mu);
 
+/* Sweep until the recommendation lists stop changing (the early-stopping
+ * criterion the paper proposes for practical use, Sec. 4.2 discussion: stop
+ * when the rankings of candidates and employers stay stable for a number of
+ * epochs). Every `check_every` sweeps the k best partners by log mu (the
+ * ranked lists of tu_topk_partners) of the first min(sample, N) X users and
+ * the first min(sample, M) Y users are recomputed, with the next partner's
+ * score. A check passes when every list position whose log mu is more than
+ * score_eps above the next entry's and below the previous entry's holds the
+ * same partner as at the previous check (near-ties are not compared: at the
+ * fixed point their order flips with the last bits of the potentials). The
+ * call returns TU_OK after `patience` consecutive passing checks and
+ * TU_ERR_NOT_CONVERGED after max_iter sweeps. warm_start and the relaxation
+ * setting apply as in tu_ipfp_solve. info (may be NULL): sweeps run, status,
+ * the certified residual of the returned state (rankings settle long before
+ * the marginals) and the match count. Requires 1 <= k <= 63, k <= min(N, M),
+ * sample >= 1, check_every >= 1, patience >= 1, score_eps >= 0, max_iter >= 0
+ * (else TU_ERR_INVALID_ARG). */
+tu_status tu_ipfp_solve_ranking(tu_market_t mkt, int k, int64_t sample, int check_every, int patience,
+                                double score_eps, int max_iter, int warm_start, tu_solve_info* info);
+
 /* Checkpoint / restore the solver state (the scaling vectors of Alg. 2's
  * output, Psi and Xi's last columns): log u (N floats) and log v (M floats),
  * host or device. Either pointer may be NULL to skip that side. */

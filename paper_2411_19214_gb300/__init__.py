@@ -65,6 +65,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tu_market_update_factors": (I32, [V, V, V, V, V]),
         "tu_ipfp_sweep": (I32, [V, I32, ctypes.POINTER(D)]),
         "tu_ipfp_solve": (I32, [V, D, I32, I32, ctypes.POINTER(SolveInfo)]),
+        "tu_ipfp_solve_ranking": (I32, [V, I32, I64, I32, I32, D, I32, I32, ctypes.POINTER(SolveInfo)]),
         "tu_mu_block": (I32, [V, I64, I64, I64, I64, V, I64]),
         "tu_topk_partners": (I32, [V, I32, I32, I64, I64, V, V]),
         "tu_get_potentials": (I32, [V, V, V]),
@@ -98,7 +99,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
 def exported_symbols() -> list:
     """Names of the ABI functions the loaded library exports."""
     lib = load()
-    names = ["tu_market_create", "tu_market_update_factors", "tu_ipfp_sweep", "tu_ipfp_solve", "tu_mu_block",
+    names = ["tu_market_create", "tu_market_update_factors", "tu_ipfp_sweep", "tu_ipfp_solve",
+             "tu_ipfp_solve_ranking", "tu_mu_block",
              "tu_topk_partners", "tu_get_potentials", "tu_set_potentials", "tu_profile_enable",
              "tu_profile_read", "tu_market_destroy", "tu_status_string", "tu_market_last_error",
              "tu_batch_create", "tu_batch_sweep", "tu_batch_solve", "tu_batch_profile_enable",
@@ -225,6 +227,20 @@ def tu_ipfp_solve(h: int, tol: float, max_iter: int, warm_start: bool = False) -
     st = load().tu_ipfp_solve(h, float(tol), int(max_iter), int(bool(warm_start)), ctypes.byref(info))
     if st not in (TU_OK, TU_ERR_NOT_CONVERGED):
         _check(st, "tu_ipfp_solve", h)
+    return dict(status=st, converged=st == TU_OK, sweeps=info.sweeps, residual_inf=info.residual_inf,
+                residual_l1=info.residual_l1, match_count=info.match_count)
+
+
+def tu_ipfp_solve_ranking(h: int, k: int, sample: int, check_every: int, patience: int, max_iter: int,
+                          warm_start: bool = False, score_eps: float = 1e-4) -> dict:
+    """Sweep until the top-k lists of the sampled users of both sides are unchanged
+    (positions separated by more than score_eps in log mu) at `patience`
+    consecutive checks, `check_every` sweeps apart."""
+    info = SolveInfo()
+    st = load().tu_ipfp_solve_ranking(h, int(k), int(sample), int(check_every), int(patience), float(score_eps),
+                                      int(max_iter), int(bool(warm_start)), ctypes.byref(info))
+    if st not in (TU_OK, TU_ERR_NOT_CONVERGED):
+        _check(st, "tu_ipfp_solve_ranking", h)
     return dict(status=st, converged=st == TU_OK, sweeps=info.sweeps, residual_inf=info.residual_inf,
                 residual_l1=info.residual_l1, match_count=info.match_count)
 
@@ -371,6 +387,10 @@ class Market:
 
     def solve(self, tol: float, max_iter: int, warm_start: bool = False) -> dict:
         return tu_ipfp_solve(self.handle, tol, max_iter, warm_start)
+
+    def solve_ranking(self, k: int = 10, sample: int = 4096, check_every: int = 5, patience: int = 3,
+                      max_iter: int = 10000, warm_start: bool = False, score_eps: float = 1e-4) -> dict:
+        return tu_ipfp_solve_ranking(self.handle, k, sample, check_every, patience, max_iter, warm_start, score_eps)
 
     def set_relaxation(self, omega: float) -> None:
         tu_market_set_relaxation(self.handle, omega)

@@ -709,6 +709,111 @@ tu_status tu_ipfp_solve(tu_market_t m, double tol, int max_iter, int warm_start,
   return status;
 }
 
+tu_status tu_ipfp_solve_ranking(tu_market_t m, int k, int64_t sample, int check_every, int patience,
+                                double score_eps, int max_iter, int warm_start, tu_solve_info* info) {
+  TU_TRY(check_live(m));
+  if (k < 1 || k > 63 || k > m->N || k > m->M || sample < 1 || check_every < 1 || patience < 1 ||
+      !(score_eps >= 0.0) || max_iter < 0)
+    return fail(m, TU_ERR_INVALID_ARG, "ranking-stability arguments out of range");
+  if (!warm_start) {
+    TU_CK(m, launch_reset_potentials(m, m->X));
+    TU_CK(m, launch_reset_potentials(m, m->Y));
+  }
+  TU_TRY(clear_results(m));
+  // per side: the users checked and the list length (k + 1 when there is a next partner)
+  const int64_t rows[2] = {sample < m->N ? sample : m->N, sample < m->M ? sample : m->M};
+  const int kq[2] = {k + 1 <= m->M ? k + 1 : k, k + 1 <= m->N ? k + 1 : k};
+  const size_t n0 = (size_t)rows[0] * kq[0], n1 = (size_t)rows[1] * kq[1], nidx = n0 + n1;
+  const size_t hand = (size_t)(rows[0] > rows[1] ? rows[0] : rows[1]) * 64;
+  // device: indices of both sides, their log mu, then (fused) the hand-over scratch
+  int32_t* buf = nullptr;
+  TU_TRY(dev_alloc(m, &buf, 2 * nidx + 2 * hand));
+  int32_t* d_idx = buf;
+  float* d_lmu = reinterpret_cast<float*>(buf + nidx);
+  std::vector<int32_t> cur(nidx), prev(nidx);
+  std::vector<float> score(nidx);
+  auto rank_lists = [&]() -> tu_status {
+    for (int side = 0; side < 2; ++side) {
+      const size_t off = side == 0 ? 0 : n0;
+      cudaError_t e = launch_prep(m, side == 0 ? m->Y : m->X, m->path == TU_PATH_FUSED ? 1 : 0);
+      if (e == cudaSuccess) {
+        if (m->path == TU_PATH_FUSED) {
+          float* hv = reinterpret_cast<float*>(buf + 2 * nidx);
+          e = launch_fused_topk(m, side, kq[side], 0, rows[side], d_idx + off, d_lmu + off, hv,
+                                buf + 2 * nidx + hand);
+        } else {
+          e = launch_topk(m, side, kq[side], 0, rows[side], d_idx + off, d_lmu + off);
+        }
+      }
+      if (e != cudaSuccess) return fail_cuda(m, e, "ranked lists");
+    }
+    TU_CK(m, cudaMemcpyAsync(cur.data(), d_idx, nidx * sizeof(int32_t), cudaMemcpyDeviceToHost, m->stream));
+    TU_CK(m, cudaMemcpyAsync(score.data(), d_lmu, nidx * sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+    TU_CK(m, cudaStreamSynchronize(m->stream));
+    return TU_OK;
+  };
+  // positions separated from both neighbours by more than score_eps must hold the same partner
+  auto same_rankings = [&]() -> bool {
+    for (int side = 0; side < 2; ++side) {
+      const size_t off = side == 0 ? 0 : n0;
+      for (int64_t r = 0; r < rows[side]; ++r) {
+        const size_t b = off + (size_t)r * kq[side];
+        for (int j = 0; j < k; ++j) {
+          const double above = j == 0 ? INFINITY : (double)score[b + j - 1] - score[b + j];
+          const double below = j + 1 < kq[side] ? (double)score[b + j] - score[b + j + 1] : INFINITY;
+          if (above > score_eps && below > score_eps && cur[b + j] != prev[b + j]) return false;
+        }
+      }
+    }
+    return true;
+  };
+  RelaxControl ctl(m->omega_cfg);
+  double omega = 1.0;
+  tu_status st = TU_OK;
+  if (ctl.enabled()) st = set_omega(m, 1.0);
+  int done = 0, stable = 0;
+  bool have_prev = false;
+  tu_status status = TU_ERR_NOT_CONVERGED;
+  while (st == TU_OK && done < max_iter) {
+    const int ks = (max_iter - done) < check_every ? (max_iter - done) : check_every;
+    st = enqueue_sweeps(m, ks);
+    if (st == TU_OK) st = read_results(m);
+    if (st != TU_OK) break;
+    m->sweeps_enqueued += ks;
+    done += ks;
+    if (ctl.enabled()) {
+      const double next = ctl.observe(done, m->results_host[kResXInf], 0.0);
+      if (next != omega && (st = set_omega(m, next)) != TU_OK) break;
+      omega = next;
+    }
+    if ((st = rank_lists()) != TU_OK) break;
+    stable = (have_prev && same_rankings()) ? stable + 1 : 0;
+    prev.swap(cur);
+    have_prev = true;
+    if (stable >= patience) {
+      status = TU_OK;
+      break;
+    }
+  }
+  cudaFree(buf);
+  if (st != TU_OK) return st;
+  if (ctl.enabled()) TU_TRY(set_omega(m, m->omega_cfg > 1.0 ? m->omega_cfg : 1.0));
+  double res_inf = INFINITY, res_l1 = INFINITY;
+  TU_TRY(certify(m, &res_inf, &res_l1));
+  TU_TRY(clear_results(m));
+  TU_CK(m, launch_sum_sq(m, m->Y, 0));
+  TU_TRY(read_results(m));
+  if (info != nullptr) {
+    info->sweeps = done;
+    info->status = status;
+    info->residual_inf = res_inf;
+    info->residual_l1 = res_l1;
+    info->match_count = m->Y.sum_mass - m->results_host[kResYSq];
+  }
+  if (status != TU_OK) m->last_error = "max_iter reached before the rankings were stable";
+  return status;
+}
+
 tu_status tu_mu_block(tu_market_t m, int64_t x0, int64_t nx, int64_t y0, int64_t ny, float* out, int64_t ld) {
   TU_TRY(check_live(m));
   if (out == nullptr || x0 < 0 || y0 < 0 || nx < 0 || ny < 0 || x0 + nx > m->N || y0 + ny > m->M || ld < ny)
