@@ -186,6 +186,26 @@ tu_status tu_set_potentials(tu_market_t mkt, const float* log_u, const float* lo
  * grows tenfold over the best seen. Other values: TU_ERR_INVALID_ARG. */
 tu_status tu_market_set_relaxation(tu_market_t mkt, double omega);
 
+/* Blocks of k > 1 sweeps replay a captured CUDA graph on the market's stream
+ * (enable = 1, the default), or are launched kernel by kernel (0). Capturing
+ * is not safe while another host thread uses the library: a capture in
+ * progress makes some of that thread's calls (host copies, allocation) fail
+ * and invalidates the capture, so callers that drive markets from several
+ * threads turn graphs off. No counterpart in the paper. */
+tu_status tu_market_use_graphs(tu_market_t mkt, int enable);
+
+/* Automatic over-relaxation for asynchronous sweeps (no counterpart in the
+ * paper). For a market whose relaxation setting is 0 (automatic), feed the
+ * residual of the last completed tu_ipfp_sweep block (the value
+ * tu_market_query reports) into the controller tu_ipfp_solve uses, and set the
+ * factor the next sweeps apply: plain sweeps until the decay rate has settled,
+ * then successive over-relaxation tapered towards 1 in the last decade above
+ * tol. Non-blocking: does nothing while the last block is still running, for
+ * other settings, or when the block was already fed. The controller restarts
+ * when the factors, potentials or setting change and after tu_ipfp_solve.
+ * tol < 0: TU_ERR_INVALID_ARG. */
+tu_status tu_market_relax_update(tu_market_t mkt, double tol);
+
 /* Non-blocking progress query for serving loops that keep many markets busy
  * from one host thread (no counterpart in the paper). tu_ipfp_sweep without
  * residual_out only enqueues work; this call checks, without waiting, whether

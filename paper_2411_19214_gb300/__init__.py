@@ -72,6 +72,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tu_set_potentials": (I32, [V, V, V]),
         "tu_fused_halfsweep_noalloc": (I32, [I64, I64, I64, V, V, V, V, V, V, V, D, V, ctypes.POINTER(D), V]),
         "tu_market_set_relaxation": (I32, [V, D]),
+        "tu_market_relax_update": (I32, [V, D]),
+        "tu_market_use_graphs": (I32, [V, I32]),
         "tu_market_query": (I32, [V, ctypes.POINTER(I32), ctypes.POINTER(D), ctypes.POINTER(D),
                                   ctypes.POINTER(I64)]),
         "tu_market_footprint": (I64, [I64, I64, I64, I32]),
@@ -282,6 +284,16 @@ def tu_fused_halfsweep_noalloc(rows: int, cols: int, kp: int, own_packed, partne
 def tu_market_set_relaxation(h: int, omega: float) -> None:
     """omega = 1: plain IPFP; 1 < omega < 2: fixed over-relaxation; 0: automatic in solve."""
     _check(load().tu_market_set_relaxation(h, float(omega)), "tu_market_set_relaxation", h)
+
+
+def tu_market_use_graphs(h: int, enable: bool) -> None:
+    """Replay captured CUDA graphs for blocks of sweeps (default), or launch directly (multi-threaded callers)."""
+    _check(load().tu_market_use_graphs(h, int(bool(enable))), "tu_market_use_graphs", h)
+
+
+def tu_market_relax_update(h: int, tol: float) -> None:
+    """Automatic relaxation of asynchronous sweeps: feed the last completed block's residual (non-blocking)."""
+    _check(load().tu_market_relax_update(h, float(tol)), "tu_market_relax_update", h)
 
 
 def tu_market_query(h: int):

@@ -283,7 +283,7 @@ bool stream_capturable(cudaStream_t s) { return s != nullptr && s != cudaStreamL
 // Enqueue k sweeps, replaying a captured graph of k sweeps when possible.
 tu_status enqueue_sweeps(tu_market* m, int k) {
   if (k <= 0) return TU_OK;
-  if (stream_capturable(m->stream) && k > 1 && !m->profiling) {
+  if (m->use_graphs && stream_capturable(m->stream) && k > 1 && !m->profiling) {
     if (m->graph == nullptr || m->graph_sweeps != k) {
       if (m->graph != nullptr) {
         cudaGraphExecDestroy(m->graph);
@@ -342,6 +342,16 @@ tu_status set_omega(tu_market* m, double omega) {
   TU_CK(m, cudaStreamSynchronize(m->stream));  // the pinned staging word may still be in use
   *m->omega_host = omega;
   TU_CK(m, cudaMemcpyAsync(m->omega_dev, m->omega_host, sizeof(double), cudaMemcpyHostToDevice, m->stream));
+  return TU_OK;
+}
+
+// Restart the controller of asynchronous sweeps (new factors, potentials or
+// setting): plain sweeps again until the decay rate has been re-estimated.
+tu_status relax_reset(tu_market* m) {
+  m->relax = RelaxControl(m->omega_cfg);
+  m->relax_base = m->sweeps_enqueued;
+  m->relax_seen = -1;
+  if (m->omega_cfg == 0.0 && *m->omega_host != 1.0) TU_TRY(set_omega(m, 1.0));
   return TU_OK;
 }
 
@@ -569,7 +579,8 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
 tu_status tu_market_update_factors(tu_market_t m, const void* F, const void* K, const void* G, const void* L) {
   TU_TRY(check_live(m));
   if (!F || !K || !G || !L) return fail(m, TU_ERR_INVALID_ARG, "null factor pointer");
-  return load_factors(m, F, K, G, L);
+  TU_TRY(load_factors(m, F, K, G, L));
+  return relax_reset(m);
 }
 
 tu_status tu_ipfp_sweep(tu_market_t m, int nsweeps, double* residual_out) {
@@ -597,15 +608,43 @@ tu_status tu_market_set_relaxation(tu_market_t m, double omega) {
   TU_TRY(check_live(m));
   if (!(omega == 0.0 || (omega >= 1.0 && omega < 2.0)))
     return fail(m, TU_ERR_INVALID_ARG, "omega must be 0 (automatic) or in [1, 2)");
-  if (omega != m->omega_cfg && m->graph != nullptr) {
-    // the captured sweeps use the kernel variant of the previous setting
+  if (m->path == TU_PATH_DENSE && (omega != 1.0) != (m->omega_cfg != 1.0) && m->graph != nullptr) {
+    // the captured dense sweeps use the row-pass variant of the previous setting
     TU_CK(m, cudaStreamSynchronize(m->stream));
     cudaGraphExecDestroy(m->graph);
     m->graph = nullptr;
     m->graph_sweeps = 0;
   }
   m->omega_cfg = omega;
-  return set_omega(m, omega > 1.0 ? omega : 1.0);
+  TU_TRY(set_omega(m, omega > 1.0 ? omega : 1.0));
+  return relax_reset(m);
+}
+
+tu_status tu_market_use_graphs(tu_market_t m, int enable) {
+  TU_TRY(check_live(m));
+  m->use_graphs = enable != 0;
+  if (!m->use_graphs && m->graph != nullptr) {
+    TU_CK(m, cudaStreamSynchronize(m->stream));
+    cudaGraphExecDestroy(m->graph);
+    m->graph = nullptr;
+    m->graph_sweeps = 0;
+  }
+  return TU_OK;
+}
+
+tu_status tu_market_relax_update(tu_market_t m, double tol) {
+  TU_TRY(check_live(m));
+  if (!(tol >= 0.0)) return fail(m, TU_ERR_INVALID_ARG, "tol < 0");
+  if (m->omega_cfg != 0.0 || m->done_ev == nullptr || m->query_sweeps == m->relax_seen) return TU_OK;
+  const cudaError_t e = cudaEventQuery(m->done_ev);
+  if (e == cudaErrorNotReady) return TU_OK;  // the last block is still running
+  if (e != cudaSuccess) return fail_cuda(m, e, "cudaEventQuery");
+  m->relax_seen = m->query_sweeps;
+  const double r = m->query_host[kResXInf];
+  if (!(r > tol) || !std::isfinite(r)) return TU_OK;
+  const double next = m->relax.observe((int)(m->query_sweeps - m->relax_base), r, tol);
+  if (next != *m->omega_host) TU_TRY(set_omega(m, next));
+  return TU_OK;
 }
 
 tu_status tu_market_query(tu_market_t m, int* idle, double* residual, double* match_count, int64_t* sweeps) {
@@ -705,6 +744,7 @@ tu_status tu_ipfp_solve(tu_market_t m, double tol, int max_iter, int warm_start,
     info->residual_l1 = res_l1;
     info->match_count = match;
   }
+  TU_TRY(relax_reset(m));  // the asynchronous controller restarts after a solve
   if (status != TU_OK) m->last_error = "max_iter reached before the residual met tol";
   return status;
 }
@@ -909,7 +949,7 @@ tu_status tu_set_potentials(tu_market_t m, const float* log_u, const float* log_
     TU_CK(m, launch_set_potentials(m, *sides[i], static_cast<const float*>(src)));
     TU_CK(m, cudaStreamSynchronize(m->stream));
   }
-  return TU_OK;
+  return relax_reset(m);
 }
 
 }  // extern "C"

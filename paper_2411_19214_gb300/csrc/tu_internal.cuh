@@ -56,6 +56,28 @@ struct Side {
   CUtensorMap tm_partner;   // TMA map, box kKBlock x kFusedPartnerRows
 };
 
+// Over-relaxation controller of the solve loops (host side, one per market).
+// Plain sweeps until the residual is below 0.1 and (in automatic mode) the
+// per-sweep decay q of the plain iteration has settled, then
+// omega = 2 / (1 + sqrt(1 - q)) (successive over-relaxation), tapered towards
+// 1 as the residual approaches tol: the relaxed sweep amplifies the FP32
+// rounding of the row sums by about omega / (2 - omega). The excess over 1 is
+// halved whenever the residual grows tenfold over the best seen.
+struct RelaxControl {
+  static constexpr int kProbe = 10;  // sweeps between convergence-rate estimates
+  double cfg = 1.0;                  // 1: plain; (1, 2): fixed; 0: automatic
+  double omega = 1.0, target = 1.0, best = 1.0 / 0.0, q_prev = -1.0;
+  int last_est = 0;
+  std::vector<std::pair<int, double>> hist;
+
+  explicit RelaxControl(double c = 1.0) : cfg(c) {}
+  bool enabled() const { return cfg != 1.0; }
+
+  // r: residual of the state entering the last sweep of a block that ended
+  // after `done` sweeps (r > tol). Returns the omega of the next block.
+  double observe(int done, double r, double tol);
+};
+
 }  // namespace tu
 
 struct tu_market {
@@ -85,6 +107,7 @@ struct tu_market {
   size_t aux_bytes = 0;
   cudaGraphExec_t graph = nullptr; // captured block of sweeps
   int graph_sweeps = 0;
+  bool use_graphs = true;          // tu_market_use_graphs
   bool poisoned = false;
   std::string last_error;
   // benchmark timing (tu_profile_enable / tu_profile_read)
@@ -97,6 +120,10 @@ struct tu_market {
   double* query_host = nullptr;  // pinned: kResSlots doubles + the error word
   int64_t sweeps_enqueued = 0;
   int64_t query_sweeps = 0;
+  // automatic relaxation of asynchronous sweeps (tu_market_relax_update)
+  tu::RelaxControl relax;
+  int64_t relax_base = 0;   // sweeps_enqueued when the controller was last reset
+  int64_t relax_seen = -1;  // query_sweeps last fed to the controller
   bool profiling = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pool;
   size_t ev_used = 0;
@@ -205,27 +232,7 @@ cudaError_t launch_mu_block(tu_market* m, int64_t x0, int64_t nx, int64_t y0, in
 cudaError_t launch_topk(tu_market* m, int side, int k, int64_t row0, int64_t nrows, int32_t* idx,
                         float* logmu);
 
-// Over-relaxation controller of the solve loops (host side, one per market).
-// Plain sweeps until the residual is below 0.1 and (in automatic mode) the
-// per-sweep decay q of the plain iteration has settled, then
-// omega = 2 / (1 + sqrt(1 - q)) (successive over-relaxation), tapered towards
-// 1 as the residual approaches tol: the relaxed sweep amplifies the FP32
-// rounding of the row sums by about omega / (2 - omega). The excess over 1 is
-// halved whenever the residual grows tenfold over the best seen.
-struct RelaxControl {
-  static constexpr int kProbe = 10;  // sweeps between convergence-rate estimates
-  double cfg = 1.0;                  // 1: plain; (1, 2): fixed; 0: automatic
-  double omega = 1.0, target = 1.0, best = 1.0 / 0.0, q_prev = -1.0;
-  int last_est = 0;
-  std::vector<std::pair<int, double>> hist;
 
-  explicit RelaxControl(double c = 1.0) : cfg(c) {}
-  bool enabled() const { return cfg != 1.0; }
-
-  // r: residual of the state entering the last sweep of a block that ended
-  // after `done` sweeps (r > tol). Returns the omega of the next block.
-  double observe(int done, double r, double tol);
-};
 
 }  // namespace tu
 

@@ -73,3 +73,46 @@ def test_invalid_omega_rejected(gpu_lib):
                 mkt.set_relaxation(bad)
     finally:
         mkt.close()
+
+
+def test_asynchronous_automatic_omega(gpu_lib):
+    """Serving-style loop: blocks of sweeps enqueued with tu_ipfp_sweep, the
+    residual read back with tu_market_query, and the automatic controller fed
+    between blocks (tu_market_relax_update). Same fixed point, fewer sweeps
+    than plain blocks; a relaxation update while a block runs is a no-op."""
+    tu = gpu_lib
+    mk = plain_dense_market(N=400, M=400, dtype="bf16")
+
+    def run(relax):
+        mkt = tu.from_synth(mk, path="fused")
+        if relax:
+            mkt.set_relaxation(0.0)
+        done = 0
+        while done < 40000:
+            tu.tu_ipfp_sweep(mkt.handle, 8)
+            done += 8
+            while True:
+                idle, res, _, sweeps = tu.tu_market_query(mkt.handle)
+                if idle:
+                    break
+                tu.tu_market_relax_update(mkt.handle, 1e-6)  # busy: must not change anything
+            assert sweeps == done
+            if res <= 1e-6:
+                break
+            if relax:
+                tu.tu_market_relax_update(mkt.handle, 1e-6)
+        return mkt, done, res
+
+    plain, n_plain, r_plain = run(False)
+    fast, n_fast, r_fast = run(True)
+    try:
+        assert r_plain <= 1e-6 and r_fast <= 1e-6
+        assert n_fast * 2 < n_plain, (n_fast, n_plain)
+        r, logA, f = oracle_solve(mk, tol=1e-12)
+        mu_ref = np.exp(oracle.log_mu(logA, r["log_u"], r["log_v"]))
+        np.testing.assert_allclose(fast.mu_block().double().cpu().numpy(), mu_ref, rtol=1e-3)
+        with pytest.raises(tu.TuError):
+            tu.tu_market_relax_update(fast.handle, -1.0)
+    finally:
+        plain.close()
+        fast.close()
