@@ -322,6 +322,18 @@ void tu_batch_destroy(tu_batch_t b);
 /* Detail of the batch's last error ("" if none). */
 const char* tu_batch_last_error(tu_batch_t b);
 
+/* Failure-path diagnostic (no counterpart in the paper). Every wait of the
+ * library's kernels is bounded: a wait that runs out sets a device error word,
+ * the kernel drains and returns, and the call that launched it reports
+ * TU_ERR_TIMEOUT. This entry point runs that bounded wait in a one-CTA kernel
+ * on an mbarrier that nothing signals, with a limit of limit_seconds (0 < limit
+ * <= 5, else TU_ERR_INVALID_ARG), on the legacy default stream of the current
+ * device. Expected result: TU_ERR_TIMEOUT, with the measured wait in
+ * *waited_seconds (may be NULL); TU_OK would mean the wait ended without a
+ * signal; TU_ERR_CUDA / TU_ERR_OOM report a CUDA failure. The device stays
+ * usable. */
+tu_status tu_selftest_wait_timeout(double limit_seconds, double* waited_seconds);
+
 /* Free every resource of the market (safe on NULL). */
 void tu_market_destroy(tu_market_t mkt);
 

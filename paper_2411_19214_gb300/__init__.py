@@ -74,6 +74,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tu_market_set_relaxation": (I32, [V, D]),
         "tu_market_relax_update": (I32, [V, D]),
         "tu_market_use_graphs": (I32, [V, I32]),
+        "tu_selftest_wait_timeout": (I32, [D, ctypes.POINTER(D)]),
         "tu_market_query": (I32, [V, ctypes.POINTER(I32), ctypes.POINTER(D), ctypes.POINTER(D),
                                   ctypes.POINTER(I64)]),
         "tu_market_footprint": (I64, [I64, I64, I64, I32]),
@@ -284,6 +285,13 @@ def tu_fused_halfsweep_noalloc(rows: int, cols: int, kp: int, own_packed, partne
 def tu_market_set_relaxation(h: int, omega: float) -> None:
     """omega = 1: plain IPFP; 1 < omega < 2: fixed over-relaxation; 0: automatic in solve."""
     _check(load().tu_market_set_relaxation(h, float(omega)), "tu_market_set_relaxation", h)
+
+
+def tu_selftest_wait_timeout(limit_seconds: float):
+    """(status, seconds waited) of the bounded device wait on a barrier nothing signals; expect TU_ERR_TIMEOUT."""
+    w = ctypes.c_double(float("nan"))
+    st = load().tu_selftest_wait_timeout(float(limit_seconds), ctypes.byref(w))
+    return st, w.value
 
 
 def tu_market_use_graphs(h: int, enable: bool) -> None:

@@ -20,7 +20,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libtu_ipfp.so")
-SOURCES = ["market.cu", "reduce.cu", "dense.cu", "fused.cu", "topk.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["market.cu", "reduce.cu", "dense.cu", "fused.cu", "topk.cu", "noalloc.cu", "batch.cu", "selftest.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr", f"-I{os.path.join(ROOT, 'include')}"]
