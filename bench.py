@@ -519,6 +519,19 @@ def run_batched(args):
     sm_mhz = clk.get("sm_mhz") or 1900.0
     mufu_peak = 152 * 32 * sm_mhz * 1e6 / 1e12
     rate = pair_evals * args.steps / (ms / 1e3)
+    traffic = measured_traffic("fused batched 512 markets d32")
+    rl_tensor = {"bound": "tensor", "achieved": flops / avg_pass_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                 "frac": flops / avg_pass_s / 1e12 / peak, "traffic": traffic,
+                 "kernel": "k_fused_halfsweep batched (tcgen05 BF16 MMA, K=64, + ex2 row reduction)",
+                 "per_launch": f"{flops:.4g} flop in {avg_pass_s * 1e3:.3f} ms average over {passes} launches",
+                 "peak_source": f"{peaks.get('source')} bf16_tflops_sustained"}
+    rl_exp = {"bound": "alu", "achieved": pairs.sum() / avg_pass_s / 1e12, "peak": mufu_peak, "unit": "Tex2/s",
+              "frac": pairs.sum() / avg_pass_s / 1e12 / mufu_peak, "traffic": traffic,
+              "kernel": "k_fused_halfsweep batched (ex2 pipe)",
+              "per_launch": f"{pairs.sum():.4g} ex2 in {avg_pass_s * 1e3:.3f} ms average over {passes} launches",
+              "peak_source": "152 SMs x 32 ex2/clk/SM x sampled median SM clock"}
+    # the binding unit (closest to its peak) is the roofline; the other is reported beside it
+    rl_primary, rl_secondary = (rl_exp, rl_tensor) if rl_exp["frac"] > rl_tensor["frac"] else (rl_tensor, rl_exp)
     line = {"metric": "aggregate Gpair-evals/s of 512 independent markets in one persistent launch per half-sweep",
             "value": rate / 1e9, "unit": "Gpair-evals/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -527,15 +540,7 @@ def run_batched(args):
                                    "unit (even) or uniform{1..3} (odd) capacities, sigma=1",
                        "markets": len(mks), "pair_evals_per_sweep": pair_evals,
                        "l2": "inputs larger than L2 (about 1 GB of packed factors); no flush"},
-            "roofline": {"bound": "tensor", "achieved": flops / avg_pass_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                         "frac": flops / avg_pass_s / 1e12 / peak,
-                         "traffic": measured_traffic("fused batched 512 markets d32"),
-                         "kernel": "k_fused_halfsweep batched (tcgen05 BF16 MMA, K=64, + ex2 row reduction)",
-                         "per_launch": f"{flops:.4g} flop in {avg_pass_s * 1e3:.3f} ms average over {passes} launches",
-                         "peak_source": f"{peaks.get('source')} bf16_tflops_sustained"},
-            "roofline_exp": {"bound": "alu", "achieved": pairs.sum() / avg_pass_s / 1e12, "peak": mufu_peak,
-                             "unit": "Tex2/s", "frac": pairs.sum() / avg_pass_s / 1e12 / mufu_peak,
-                             "peak_source": "152 SMs x 32 ex2/clk/SM x sampled median SM clock"},
+            "roofline": rl_primary, "roofline_secondary": rl_secondary,
             "clocks": clk, "gpu_launches": 6 * args.steps,
             "timing": "value: K batched sweeps replayed as one CUDA graph, CUDA events on the batch stream"}
     if seq_ms is not None:
@@ -788,7 +793,14 @@ def run_ours(args):
                     "path": "tu_market_update_factors(pinned host F,K,G,L) + tu_ipfp_sweep(1) + "
                             "tu_get_potentials(pinned host)"}}
     if roofline_exp is not None:
-        line["roofline_exp"] = roofline_exp
+        # the binding unit (closest to its peak) is the roofline; the other is reported beside it
+        if roofline_exp["frac"] > roofline["frac"]:
+            roofline_exp["traffic"] = roofline["traffic"]
+            roofline_exp["kernel"] = roofline["kernel"]
+            roofline_exp["per_launch"] = f"{exps:.4g} ex2 (N*M) in {avg_pass_s * 1e3:.2f} ms average over {passes} launches"
+            roofline, roofline_exp = roofline_exp, roofline
+            line["roofline"] = roofline
+        line["roofline_secondary"] = roofline_exp
     if plain is not None:
         plain["speedup_of_value"] = sweeps_per_s / world / plain["sweeps_per_s"]
         line["plain_fp32"] = plain

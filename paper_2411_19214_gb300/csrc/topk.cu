@@ -1,11 +1,11 @@
-// topk.cu -- outputs of a solved market: blocks of mu (Eq. stable_condition,
-// Alg. 1 final line) and ranked partner lists (top-k of log mu per user).
+// topk.cu -- outputs of a solved dense-path market: blocks of mu (Eq.
+// stable_condition, Alg. 1 final line) and ranked partner lists (top-k of log
+// mu per user), read from the materialised kernel (the fused path forms them
+// in the tensor-core pipeline, fused.cu).
 //
 // log mu_xy = phi_xy / (2 sigma) + log u_x + log v_y
 //           = phi_hat_xy / (2 sigma) + ell_x + ell_y,   ell = log u + b / (2 sigma),
-// where phi_hat = <[f|k]_x, [g|l]_y> is the bias-free surplus. The fused path
-// evaluates phi_hat from the packed BF16 factors in FP32; the dense path reads
-// log A-hat = phi_hat / (2 sigma) back from the materialised kernel.
+// where phi_hat is the bias-free surplus and log A-hat = phi_hat / (2 sigma).
 #include "tu_internal.cuh"
 
 namespace tu {
@@ -14,40 +14,11 @@ namespace {
 
 constexpr int kMaxK = 64;
 
-// <a_r, b_c> of two packed BF16 rows (kp a multiple of 64), FP32 accumulation.
-__device__ __forceinline__ float dot_bf16(const __nv_bfloat16* __restrict__ a, const __nv_bfloat16* __restrict__ b,
-                                          int64_t kp) {
-  float s = 0.0f;
-  const uint4* a8 = reinterpret_cast<const uint4*>(a);
-  const uint4* b8 = reinterpret_cast<const uint4*>(b);
-  for (int64_t i = 0; i < kp / 8; ++i) {
-    const uint4 va = __ldg(a8 + i), vb = __ldg(b8 + i);
-    const __nv_bfloat162* pa = reinterpret_cast<const __nv_bfloat162*>(&va);
-    const __nv_bfloat162* pb = reinterpret_cast<const __nv_bfloat162*>(&vb);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float2 fa = __bfloat1622float2(pa[j]), fb = __bfloat1622float2(pb[j]);
-      s = fmaf(fa.x, fb.x, s);
-      s = fmaf(fa.y, fb.y, s);
-    }
-  }
-  return s;
-}
-
+// log A-hat of (own r, partner c) at Ahat[r * rs + c * cs] (A-hat read row- or column-wise)
 struct ScoreSrc {
-  // fused path
-  const __nv_bfloat16* own16;
-  const __nv_bfloat16* par16;
-  int64_t kp;
-  float inv2s;
-  // dense path: log A-hat, element (own r, partner c) at Ahat[r * rs + c * cs]
   const float* Ahat;
   int64_t rs, cs;
-  int dense;
-  __device__ __forceinline__ float phi2s(int64_t r, int64_t c) const {
-    if (dense) return logf(Ahat[r * rs + c * cs]);
-    return dot_bf16(own16 + r * kp, par16 + c * kp, kp) * inv2s;
-  }
+  __device__ __forceinline__ float phi2s(int64_t r, int64_t c) const { return logf(Ahat[r * rs + c * cs]); }
 };
 
 __global__ void k_mu_block(ScoreSrc src, const double* __restrict__ ell_x, const double* __restrict__ ell_y, int64_t x0,
@@ -114,11 +85,6 @@ __global__ void __launch_bounds__(256) k_topk(ScoreSrc src, const double* __rest
 
 static ScoreSrc make_src(tu_market* m, int side) {
   ScoreSrc s{};
-  s.kp = m->kp;
-  s.inv2s = (float)(0.5 / m->sigma);
-  s.dense = (m->path == TU_PATH_DENSE) ? 1 : 0;
-  s.own16 = side == 0 ? m->X.fac16 : m->Y.fac16;
-  s.par16 = side == 0 ? m->Y.fac16 : m->X.fac16;
   s.Ahat = m->Ahat;
   s.rs = side == 0 ? m->ldA : 1;
   s.cs = side == 0 ? 1 : m->ldA;

@@ -226,7 +226,7 @@ cudaError_t launch_fused_topk(tu_market* m, int side, int k, int64_t row0, int64
                               float* hand_v, int32_t* hand_i);
 cudaError_t launch_fused_mu(tu_market* m, int64_t x0, int64_t nx, int64_t y0, int64_t ny, float* out, int64_t ld);
 
-// topk.cu
+// topk.cu (dense-path outputs, read from A-hat)
 cudaError_t launch_mu_block(tu_market* m, int64_t x0, int64_t nx, int64_t y0, int64_t ny, float* out,
                             int64_t ld);
 cudaError_t launch_topk(tu_market* m, int side, int k, int64_t row0, int64_t nrows, int32_t* idx,
