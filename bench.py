@@ -403,6 +403,8 @@ def serving_block(rates, count_per_rate, budget_gb: float = 64.0) -> dict:
                               "warm_resolves": sum(r.warm for r in res), "peak_active": srv.stats["peak_active"],
                               "drain_s": wall - reqs[-1].arrival,
                               "overloaded": len(res) / wall < 0.9 * rate}
+    ok = [r for r in rates if not out[f"{r:g}/s"]["overloaded"]]
+    out["sustainable_per_s"] = max(ok) if ok else None  # highest offered rate served at >= 90 %
     return out
 
 
@@ -731,7 +733,7 @@ def run_ours(args):
     serving = None
     if cfg["path"] == "fused" and not args.no_extras and rank == 0 and not args.fp8:
         plain = plain_fp32_sweep(mk, dev, stream)
-        serving = serving_block((20.0, 200.0), (60, 200))
+        serving = serving_block((20.0, 50.0, 100.0, 200.0), (60, 100, 150, 200))
 
     if rank != 0:
         if world > 1:

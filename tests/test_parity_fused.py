@@ -170,3 +170,23 @@ def test_full_size_single_sweep_sampled(gpu_lib):
         np.testing.assert_allclose(lv[cols], ov, atol=ATOL_LOG)
     finally:
         mkt.close()
+
+
+@pytest.mark.parametrize("path", ["fused", "dense"])
+def test_graph_replay_equals_direct_launches(gpu_lib, path):
+    """Blocks of sweeps replayed from a captured CUDA graph and the same blocks
+    launched kernel by kernel (tu_market_use_graphs) give identical potentials."""
+    tu = gpu_lib
+    mk = _mk(700, 555, 32, seed=12, dtype="bf16" if path == "fused" else "fp32")
+    a = tu.from_synth(mk, path=path)
+    b = tu.from_synth(mk, path=path)
+    try:
+        tu.tu_market_use_graphs(b.handle, False)
+        for _ in range(3):
+            a.sweep(4)
+            b.sweep(4)
+        (au, av), (bu, bv) = a.potentials(), b.potentials()
+        assert torch.equal(au, bu) and torch.equal(av, bv)
+    finally:
+        a.close()
+        b.close()
