@@ -56,7 +56,7 @@ constexpr uint32_t kTmemCols = 512;
 // Epilogue modes of the one fused kernel: the same TMA / MMA pipeline forms
 // the tiles of c * phi_hat + g; the epilogue either reduces them (a half-sweep),
 // keeps the k best columns of every row (ranked lists) or writes mu.
-enum : int { kModeSweep = 0, kModeTopK = 1, kModeMu = 2 };
+enum : int { kModeSweep = 0, kModeTopK = 1, kModeMu = 2, kModeTopKShared = 3 };
 
 struct FusedParams {
   int64_t rows;            // own users of this launch: [row0, row0 + rows)
@@ -224,6 +224,74 @@ __device__ __forceinline__ void chunk_topk(const uint32_t (&v)[32], const float*
   }
 }
 
+// Ranked lists with k <= kSharedTopK (kModeTopKShared): every epilogue
+// thread keeps the k best (score, column) pairs of its row and column half in
+// shared memory, entry i of thread t at [i * kEpiThreads + t] (a warp's
+// accesses to one entry are conflict-free), sorted by decreasing score, equal
+// scores in increasing column order (the order in which a column half's
+// columns arrive). The list starts as k (-inf, INT32_MAX) pairs, so the k-th
+// score is the threshold from the first column on. An insertion shifts at
+// most k - 1 entries in shared memory. Rows whose rankings differ (a
+// converged market, where the potentials cancel the popularity terms) insert
+// at different columns, and a warp runs every lane's insertion in turn; with
+// the list in shared memory each of those costs a few shared-memory round
+// trips instead of a chain through local memory.
+constexpr int kSharedTopK = 14;
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kTopKListBytes = kSharedTopK * kEpiThreads * 8;
+
+__device__ __forceinline__ float lds_f32(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ int32_t lds_s32(uint32_t a) {
+  int32_t v;
+  asm volatile("ld.shared.s32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void sts_f32(uint32_t a, float v) { asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v)); }
+__device__ __forceinline__ void sts_s32(uint32_t a, int32_t v) { asm volatile("st.shared.s32 [%0], %1;" ::"r"(a), "r"(v)); }
+
+// Insert (s, col) into the list at shared addresses lv (scores) and li
+// (columns) of one thread; s beats the current k-th score. Returns the new
+// k-th score. Kept out of line: one copy serves every call site.
+__device__ __noinline__ float list_insert(uint32_t lv, uint32_t li, int k, float s, int32_t col) {
+  constexpr uint32_t kStride = kEpiThreads * 4;
+  uint32_t pos = (uint32_t)(k - 1);
+  while (pos > 0) {
+    const float above = lds_f32(lv + (pos - 1) * kStride);
+    if (!(s > above)) break;
+    sts_f32(lv + pos * kStride, above);
+    sts_s32(li + pos * kStride, lds_s32(li + (pos - 1) * kStride));
+    --pos;
+  }
+  sts_f32(lv + pos * kStride, s);
+  sts_s32(li + pos * kStride, col);
+  return lds_f32(lv + (uint32_t)(k - 1) * kStride);
+}
+
+__device__ __forceinline__ void chunk_topk_shared(const uint32_t (&v)[32], const float* g, float c, int64_t colbase,
+                                                  int k, uint32_t lv, uint32_t li, float& thr) {
+  const float4* g4 = reinterpret_cast<const float4*>(g);
+  float s[32];
+  float mx = -INFINITY;
+#pragma unroll
+  for (int i4 = 0; i4 < 8; ++i4) {
+    const float4 gg = g4[i4];
+    s[4 * i4 + 0] = fmaf(__uint_as_float(v[4 * i4 + 0]), c, gg.x);
+    s[4 * i4 + 1] = fmaf(__uint_as_float(v[4 * i4 + 1]), c, gg.y);
+    s[4 * i4 + 2] = fmaf(__uint_as_float(v[4 * i4 + 2]), c, gg.z);
+    s[4 * i4 + 3] = fmaf(__uint_as_float(v[4 * i4 + 3]), c, gg.w);
+    mx = fmaxf(mx, fmaxf(fmaxf(s[4 * i4 + 0], s[4 * i4 + 1]), fmaxf(s[4 * i4 + 2], s[4 * i4 + 3])));
+  }
+  if (mx > thr) {
+#pragma unroll
+    for (int e = 0; e < 32; ++e)
+      if (s[e] > thr) thr = list_insert(lv, li, k, s[e], (int32_t)(colbase + e));
+  }
+}
+
 // mu block: mu = 2^(c * phi_hat + g + lo) * 2^hi, where hi + lo = (shift + ell_row) log2 e.
 __device__ __forceinline__ void chunk_mu(const uint32_t (&v)[32], const float* g, float c, int64_t colbase, float lo,
                                          int hi, bool row_ok, int64_t r, const FusedParams& p) {
@@ -301,6 +369,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   double* red = reinterpret_cast<double*>(reinterpret_cast<uint8_t*>(bars) + 512);      // 4 x kEpiWarps doubles
   float* rowbuf = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bars) + 1024);   // 2 x 256 floats
+  // ranked lists in shared memory (kModeTopKShared only): after the tail area
+  float* topk_list = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bars) + kTailBytes);
   static_assert(4 * kEpiWarps * 8 <= 512, "reduction area");
   static_assert((2 * STAGES + 2 * kGSlots + 13) * 8 + 8 <= 512, "barrier area");
 
@@ -509,6 +579,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ranked lists: this thread's sorted candidates for its row and column half
     float tv[MODE == kModeTopK ? kMaxTopK : 1];
     int32_t ti[MODE == kModeTopK ? kMaxTopK : 1];
+    // shared-memory lists (k <= kSharedTopK): this thread's entry 0
+    const uint32_t lv = smem_u32(topk_list) + (uint32_t)(ew * 32 + lane) * 4u;
+    const uint32_t li = lv + (uint32_t)(kSharedTopK * kEpiThreads) * 4u;
     int tcnt = 0;
     float thr = -INFINITY;
     int tile_iter = 0;
@@ -542,6 +615,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         tcnt = 0;
         thr = -INFINITY;
       }
+      if constexpr (MODE == kModeTopKShared) {
+        for (int i = 0; i < p.k; ++i) {
+          sts_f32(lv + (uint32_t)(i * kEpiThreads) * 4u, -INFINITY);
+          sts_s32(li + (uint32_t)(i * kEpiThreads) * 4u, 0x7fffffff);
+        }
+        thr = -INFINITY;
+      }
       for (int j = 0; j < npt; ++j) {
         // every lane waits; the outcome is made warp-uniform so that the
         // .sync.aligned TMEM loads below never run with a partial warp
@@ -557,11 +637,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float4* gs4 = reinterpret_cast<const float4*>(gsf);
         const int64_t colbase = p.col0 + (int64_t)j * kFusedPartnerRows + half * 64;
         uint64_t acc[4] = {0ull, 0ull, 0ull, 0ull};
+        // the second 32-column chunk is loaded while the first is processed
         tmem_ld_issue(taddr, va);
         tmem_ld_wait(va);
         tmem_ld_issue(taddr + 32, vb);
         if constexpr (MODE == kModeSweep) chunk_sum(va, gs4, cc, acc);
         if constexpr (MODE == kModeTopK) chunk_topk(va, gsf, p.c, colbase, p.k, tv, ti, &tcnt, thr);
+        if constexpr (MODE == kModeTopKShared) chunk_topk_shared(va, gsf, p.c, colbase, p.k, lv, li, thr);
         if constexpr (MODE == kModeMu) chunk_mu(va, gsf, p.c, colbase, mu_lo, mu_hi, row_ok, r, p);
         tmem_ld_wait(vb);
         // this warp's part of the accumulator buffer has been read: hand it back to the MMA warp
@@ -570,6 +652,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(&tempty[buf]);
         if constexpr (MODE == kModeSweep) chunk_sum(vb, gs4 + 8, cc, acc);
         if constexpr (MODE == kModeTopK) chunk_topk(vb, gsf + 32, p.c, colbase + 32, p.k, tv, ti, &tcnt, thr);
+        if constexpr (MODE == kModeTopKShared)
+          chunk_topk_shared(vb, gsf + 32, p.c, colbase + 32, p.k, lv, li, thr);
         if constexpr (MODE == kModeMu) chunk_mu(vb, gsf + 32, p.c, colbase + 32, mu_lo, mu_hi, row_ok, r, p);
         // the g slot has been read by this warp
         __syncwarp();
@@ -610,6 +694,13 @@ __global__ void __launch_bounds__(kThreads, 1)
               p.hand_i[r * p.k + i] = i < tcnt ? ti[i] : 0x7fffffff;
             }
         }
+        if constexpr (MODE == kModeTopKShared) {
+          if (row_ok)
+            for (int i = 0; i < p.k; ++i) {
+              p.hand_v[r * p.k + i] = lds_f32(lv + (uint32_t)(i * kEpiThreads) * 4u);
+              p.hand_i[r * p.k + i] = lds_s32(li + (uint32_t)(i * kEpiThreads) * 4u);
+            }
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive(&rowfull[pb]);
         continue;
@@ -629,6 +720,27 @@ __global__ void __launch_bounds__(kThreads, 1)
             const bool take_a = a < tcnt && (b >= p.k || tv[a] > bv || (tv[a] == bv && ti[a] < bi));
             const float sv = take_a ? tv[a] : bv;
             p.idx[r * p.k + i] = take_a ? ti[a] : bi;
+            if (p.logmu != nullptr) p.logmu[r * p.k + i] = (float)((double)sv * 0.69314718055994530942 + base);
+            if (take_a) ++a; else ++b;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&rowfree[pb]);
+      }
+      if constexpr (MODE == kModeTopKShared) {
+        if (row_ok) {
+          // merge the two sorted halves (both exactly k entries, padded with
+          // (-inf, INT32_MAX)): higher score first, lower index on ties
+          const double base = shift + p.ell[p.row0 + r];
+          int a = 0, b = 0;
+          for (int i = 0; i < p.k; ++i) {
+            const float av = lds_f32(lv + (uint32_t)(a * kEpiThreads) * 4u);
+            const int32_t ai = lds_s32(li + (uint32_t)(a * kEpiThreads) * 4u);
+            const float bv = p.hand_v[r * p.k + b];
+            const int32_t bi = p.hand_i[r * p.k + b];
+            const bool take_a = av > bv || (av == bv && ai < bi);
+            const float sv = take_a ? av : bv;
+            p.idx[r * p.k + i] = take_a ? ai : bi;
             if (p.logmu != nullptr) p.logmu[r * p.k + i] = (float)((double)sv * 0.69314718055994530942 + base);
             if (take_a) ++a; else ++b;
           }
@@ -759,25 +871,33 @@ cudaError_t make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t k
 constexpr int kStagesKB1 = 6;
 constexpr int kStagesKB2 = 4;
 
-template <int KB, int STAGES, int MODE, bool BATCH, bool F8 = false>
+// Partner-tile stages per instantiation: with a 128-wide inner dimension the
+// shared-memory ranked lists take the room of one stage.
+template <int KB, int MODE>
+constexpr int kStages = KB == 1 ? kStagesKB1 : (MODE == kModeTopKShared ? kStagesKB2 - 1 : kStagesKB2);
+
+template <int KB, int MODE>
+constexpr int kSmemTotal = smem_bytes<KB>(kStages<KB, MODE>) + (MODE == kModeTopKShared ? kTopKListBytes : 0);
+
+template <int KB, int MODE, bool BATCH, bool F8 = false>
 cudaError_t launch_kernel(const CUtensorMap& own, const CUtensorMap& partner, const FusedParams& p, int grid,
                           cudaStream_t stream) {
-  static_assert(smem_bytes<KB>(STAGES) <= 232448, "shared memory budget");
-  k_fused_halfsweep<KB, STAGES, MODE, BATCH, F8><<<grid, kThreads, smem_bytes<KB>(STAGES), stream>>>(own, partner,
-                                                                                                     p);
+  static_assert(kSmemTotal<KB, MODE> <= 232448, "shared memory budget");
+  k_fused_halfsweep<KB, kStages<KB, MODE>, MODE, BATCH, F8>
+      <<<grid, kThreads, kSmemTotal<KB, MODE>, stream>>>(own, partner, p);
   return cudaGetLastError();
 }
 
 template <int MODE, bool BATCH>
 cudaError_t set_attributes_mode() {
-  cudaError_t e = cudaFuncSetAttribute(k_fused_halfsweep<1, kStagesKB1, MODE, BATCH, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>(kStagesKB1));
+  cudaError_t e = cudaFuncSetAttribute(k_fused_halfsweep<1, kStages<1, MODE>, MODE, BATCH, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal<1, MODE>);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fused_halfsweep<1, kStagesKB1, MODE, BATCH, true>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>(kStagesKB1));
+  e = cudaFuncSetAttribute(k_fused_halfsweep<1, kStages<1, MODE>, MODE, BATCH, true>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal<1, MODE>);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_fused_halfsweep<2, kStagesKB2, MODE, BATCH, false>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<2>(kStagesKB2));
+  return cudaFuncSetAttribute(k_fused_halfsweep<2, kStages<2, MODE>, MODE, BATCH, false>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal<2, MODE>);
 }
 
 // Dynamic shared memory opt-in of every instantiation, on the current device.
@@ -785,6 +905,7 @@ cudaError_t set_kernel_attributes() {
   cudaError_t e = set_attributes_mode<kModeSweep, false>();
   if (e == cudaSuccess) e = set_attributes_mode<kModeTopK, false>();
   if (e == cudaSuccess) e = set_attributes_mode<kModeMu, false>();
+  if (e == cudaSuccess) e = set_attributes_mode<kModeTopKShared, false>();
   if (e == cudaSuccess) e = set_attributes_mode<kModeSweep, true>();
   return e;
 }
@@ -795,11 +916,11 @@ cudaError_t launch_any(int64_t kp, bool fp8, const CUtensorMap& own, const CUten
                        const FusedParams& p, int grid, cudaStream_t stream) {
   if (fp8) {
     if (kp != 128) return cudaErrorNotSupported;
-    return launch_kernel<1, kStagesKB1, MODE, BATCH, true>(own, partner, p, grid, stream);
+    return launch_kernel<1, MODE, BATCH, true>(own, partner, p, grid, stream);
   }
   const int kb = (int)(kp / kKBlock);
-  if (kb == 1) return launch_kernel<1, kStagesKB1, MODE, BATCH>(own, partner, p, grid, stream);
-  if (kb == 2) return launch_kernel<2, kStagesKB2, MODE, BATCH>(own, partner, p, grid, stream);
+  if (kb == 1) return launch_kernel<1, MODE, BATCH>(own, partner, p, grid, stream);
+  if (kb == 2) return launch_kernel<2, MODE, BATCH>(own, partner, p, grid, stream);
   return cudaErrorNotSupported;
 }
 
@@ -874,8 +995,11 @@ cudaError_t launch_fused_topk(tu_market* m, int side, int k, int64_t row0, int64
   p.logmu = logmu;
   p.hand_v = hand_v;
   p.hand_i = hand_i;
-  return launch_any<kModeTopK>(m->kp, m->dtype == TU_DTYPE_FP8E4M3, own.tm_own, partner.tm_partner, p,
-                               grid_for_tiles(p.num_own_tiles, m->num_sms), m->stream);
+  const int grid = grid_for_tiles(p.num_own_tiles, m->num_sms);
+  const bool f8 = m->dtype == TU_DTYPE_FP8E4M3;
+  if (k <= kSharedTopK)
+    return launch_any<kModeTopKShared>(m->kp, f8, own.tm_own, partner.tm_partner, p, grid, m->stream);
+  return launch_any<kModeTopK>(m->kp, f8, own.tm_own, partner.tm_partner, p, grid, m->stream);
 }
 
 // mu for own X users [x0, x0 + nx) and partners [y0, y0 + ny) (the Y partner

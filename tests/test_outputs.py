@@ -83,7 +83,8 @@ def test_topk_matches_oracle(gpu_lib, path, side):
         scores = oracle.log_mu(logA, lu, lv)
         if side == 1:
             scores = scores.T
-        for k in (1, 10, 64):
+        # k <= 14: lists in shared memory; larger k: per-thread lists in local memory
+        for k in (1, 10, 14, 15, 64):
             idx, lm = (t.cpu().numpy() for t in mkt.topk(side, k))
             _check_ranked(idx, lm.astype(np.float64), scores, EPS[path])
         # a row range into host buffers
@@ -95,18 +96,40 @@ def test_topk_matches_oracle(gpu_lib, path, side):
         mkt.close()
 
 
-def test_topk_ties_prefer_lower_index(gpu_lib):
+@pytest.mark.parametrize("M,k", [(14, 14), (15, 14), (70, 14), (20, 20), (130, 20)])
+def test_topk_k_near_partner_count(gpu_lib, M, k):
+    """k up to the partner count: a column half of the one partner tile may
+    hold fewer than k partners (its list stays padded) and the padded columns
+    of the tile must never be listed."""
+    tu = gpu_lib
+    mk = make_market(300, M, 8, sigma=0.5, seed=11 + M, bias_x=True, bias_y=True, dtype="bf16")
+    mkt = tu.from_synth(mk, path="fused")
+    try:
+        mkt.sweep(3)
+        lu, lv = (t.double().cpu().numpy() for t in mkt.potentials())
+        logA, _ = dense_logA(mk)
+        scores = oracle.log_mu(logA, lu, lv)
+        idx, lm = (t.cpu().numpy() for t in mkt.topk(0, k))
+        assert idx.min() >= 0 and idx.max() < M
+        _check_ranked(idx, lm.astype(np.float64), scores, EPS["fused"])
+    finally:
+        mkt.close()
+
+
+@pytest.mark.parametrize("k", [14, 20])
+def test_topk_ties_prefer_lower_index(gpu_lib, k):
     """Exactly tied partners (duplicated factor rows, no biases) are listed in
-    increasing index order."""
+    increasing index order, whether the pair shares a column half of a partner
+    tile or not (both list kinds: k = 14 and k = 20)."""
     tu = gpu_lib
     mk = make_market(40, 300, 8, sigma=1.0, seed=3, dtype="bf16")
     mk.G[150:] = mk.G[:150]
     mk.L[150:] = mk.L[:150]
     mkt = tu.from_synth(mk, path="fused")
     try:
-        idx, _ = (t.cpu().numpy() for t in mkt.topk(0, 20))
+        idx, _ = (t.cpu().numpy() for t in mkt.topk(0, k))
         for r in range(idx.shape[0]):
-            for i in range(0, 20, 2):
+            for i in range(0, k, 2):
                 a, b = idx[r, i], idx[r, i + 1]
                 assert b == a + 150 and a < 150, (r, idx[r])
     finally:
