@@ -381,14 +381,16 @@ def serving_block(rates, count_per_rate, budget_gb: float = 64.0) -> dict:
     """Serving: Poisson streams of solve requests (sizes log-uniform in
     [1000, 200000] per side, d in {32, 64}, bf16, 30 % warm-started re-solves of
     perturbed factors) replayed in real time through the continuous-batching
-    server; latency from arrival to the top-10 reply."""
+    server; latency from arrival to the top-10 reply. Every rate replays the
+    same requests (the first `count` of one stream), arrivals scaled to the
+    rate."""
     from paper_2411_19214_gb300 import serve
     from synth import serving_workload
     out = {}
+    stream = serving_workload(max(count_per_rate), rate=1.0, seed=1004)
     for rate, count in zip(rates, count_per_rate):
-        work = serving_workload(count, rate=rate, seed=1004)
-        reqs = [serve.SolveRequest(rid=w["rid"], arrival=w["t"], F=w["F"], K=w["K"], G=w["G"], L=w["L"], n=w["n"],
-                                   m=w["m"], sigma=w["sigma"], key=w["key"]) for w in work]
+        reqs = [serve.SolveRequest(rid=w["rid"], arrival=w["t"] / rate, F=w["F"], K=w["K"], G=w["G"], L=w["L"],
+                                   n=w["n"], m=w["m"], sigma=w["sigma"], key=w["key"]) for w in stream[:count]]
         srv = serve.Server(hbm_budget_bytes=int(budget_gb * (1 << 30)), tol=1e-6, max_sweeps=200,
                            sweeps_per_step=8, k=10)
         t0 = time.perf_counter()
@@ -733,7 +735,8 @@ def run_ours(args):
     serving = None
     if cfg["path"] == "fused" and not args.no_extras and rank == 0 and not args.fp8:
         plain = plain_fp32_sweep(mk, dev, stream)
-        serving = serving_block((20.0, 50.0, 100.0, 200.0), (60, 100, 150, 200))
+        # windows of about 5, 4, 3 and 2 s
+        serving = serving_block((20.0, 50.0, 100.0, 200.0), (100, 200, 300, 400))
 
     if rank != 0:
         if world > 1:

@@ -41,9 +41,10 @@ def round_to_bf16(x: np.ndarray) -> np.ndarray:
     Returns float32 values that are exactly representable in bfloat16.
     """
     a = np.ascontiguousarray(x, dtype=np.float32)
-    bits = a.view(np.uint32).astype(np.uint64)
-    bias = ((bits >> np.uint64(16)) & np.uint64(1)) + np.uint64(0x7FFF)
-    out = ((bits + bias) & np.uint64(0xFFFF0000)).astype(np.uint32)
+    bits = a.view(np.uint32)
+    # finite inputs: bits + bias <= 0xFF7FFFFF + 0x8000 stays below 2^32
+    bias = ((bits >> np.uint32(16)) & np.uint32(1)) + np.uint32(0x7FFF)
+    out = (bits + bias) & np.uint32(0xFFFF0000)
     return out.view(np.float32).reshape(a.shape)
 
 
@@ -255,19 +256,23 @@ def serving_workload(count: int, rate: float = 200.0, lo: int = 1000, hi: int = 
     N(0, 1/d) sliced from a seeded pool, capacities uniform on {1..3}, and a
     fraction of re-solves that repeat an earlier request's market with its
     factors perturbed by N(0, perturb_std^2) (same key, so a server can warm
-    start). Returns a list of dicts with rid, t, key, F, K, G, L, n, m, sigma."""
+    start). Returns a list of dicts with rid, t, key, F, K, G, L, n, m, sigma.
+
+    The arrival times come from a generator of their own: the first requests
+    of a stream are the same for every count and rate, and at rate r their
+    arrivals are the rate-1 arrivals divided by r."""
     rng = np.random.default_rng(seed)
     pools = {}
     for d in dims:
         prng = np.random.default_rng(seed + 17 * d)
         pools[d] = [round_to_bf16(_factors(prng, hi, d, "normal")) for _ in range(4)]
-    t = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    t = np.cumsum(np.random.default_rng([seed, 1]).exponential(1.0, size=count)) / rate
     out = []
     for i in range(count):
         if out and rng.random() < resolve_frac:
             base = out[int(rng.integers(0, len(out)))]
             d = base["F"].shape[1]
-            mats = [round_to_bf16(a + rng.normal(0.0, perturb_std, size=a.shape).astype(np.float32))
+            mats = [round_to_bf16(a + rng.standard_normal(a.shape, dtype=np.float32) * np.float32(perturb_std))
                     for a in (base["F"], base["K"], base["G"], base["L"])]
             out.append(dict(rid=i, t=float(t[i]), key=base["key"], F=mats[0], K=mats[1], G=mats[2], L=mats[3],
                             n=base["n"], m=base["m"], sigma=sigma, resolve=True))
