@@ -9,7 +9,7 @@ tcgen05 half-sweep, FP64 partial reduction), with the residual of the entering
 state folded into the X half-sweep.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload fused|dense|paper|batched]
+                  [--workload fused|dense|paper|batched|ranking|serving]
 
 N > 1 (under torchrun): every rank solves its own market of the same shape
 (independent markets, weak scaling, no collective on the data path).
@@ -205,39 +205,47 @@ def _oracle_worker(args):
 
 class OraclePool:
     """The float64 oracle's X half-sweep over sampled rows, on every host core
-    (one single-threaded process per core, spawned), against all partners."""
+    (one single-threaded process per core, spawned), against all partners.
+    Takes one market or a list (run() then names the market)."""
 
-    def __init__(self, mk):
+    def __init__(self, mks):
         import numpy as np
+        mks = list(mks) if isinstance(mks, (list, tuple)) else [mks]
         self.dir = tempfile.mkdtemp(prefix="oracle_")
-        for name, a in (("F", mk.F), ("K", mk.K), ("G", mk.G), ("L", mk.L), ("n", mk.n), ("m", mk.m)):
-            np.save(os.path.join(self.dir, f"{name}.npy"), a)
-        np.save(os.path.join(self.dir, "bx.npy"),
-                mk.bias_x if mk.bias_x is not None else np.zeros(mk.N, np.float32))
-        np.save(os.path.join(self.dir, "by.npy"),
-                mk.bias_y if mk.bias_y is not None else np.zeros(mk.M, np.float32))
-        self.N, self.M, self.sigma = mk.N, mk.M, mk.sigma
+        self.dirs, self.shapes = [], []
+        for i, mk in enumerate(mks):
+            sub = os.path.join(self.dir, str(i))
+            os.makedirs(sub)
+            for name, a in (("F", mk.F), ("K", mk.K), ("G", mk.G), ("L", mk.L), ("n", mk.n), ("m", mk.m)):
+                np.save(os.path.join(sub, f"{name}.npy"), a)
+            np.save(os.path.join(sub, "bx.npy"), mk.bias_x if mk.bias_x is not None else np.zeros(mk.N, np.float32))
+            np.save(os.path.join(sub, "by.npy"), mk.bias_y if mk.bias_y is not None else np.zeros(mk.M, np.float32))
+            self.dirs.append(sub)
+            self.shapes.append((mk.N, mk.M, mk.sigma))
+        self.N, self.M, self.sigma = self.shapes[0]
         self.cores = os.cpu_count() or 1
         for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
             os.environ[var] = "1"
         self.pool = mp.get_context("spawn").Pool(self.cores)
         self.rng = np.random.default_rng(12345)
 
-    def run(self, rows_per_core: int) -> float:
-        """Wall seconds for cores x rows_per_core sampled rows."""
+    def run(self, rows_per_core: int, market: int = 0) -> float:
+        """Wall seconds for cores x rows_per_core sampled rows of one market
+        (rows_per_core at most that market's N; cores sample independently)."""
         import numpy as np
+        N, _, sigma = self.shapes[market]
         tasks = []
         for _ in range(self.cores):
-            rows = np.sort(self.rng.choice(self.N, rows_per_core, replace=False))
-            tasks.append((self.dir, rows, self.sigma))
+            rows = np.sort(self.rng.choice(N, min(rows_per_core, N), replace=False))
+            tasks.append((self.dirs[market], rows, sigma))
         t0 = time.perf_counter()
         self.pool.map(_oracle_worker, tasks)
         return time.perf_counter() - t0
 
-    def calibrate(self, budget_s: float) -> int:
+    def calibrate(self, budget_s: float, market: int = 0) -> int:
         """rows per core so that one run takes about budget_s."""
-        self.run(2)  # warm the workers (imports, page cache)
-        t = self.run(4)
+        self.run(2, market)  # warm the workers (imports, page cache)
+        t = self.run(4, market)
         per_row = max(t / 4.0, 1e-4)
         return max(4, int(budget_s / per_row))
 
@@ -377,6 +385,12 @@ def plain_fp32_sweep(mk, dev, stream, rows_per_part: int = 8192, parts: int = 2)
         torch.cuda.empty_cache()
 
 
+# offered request rates of the serving sweep and requests per rate (windows of
+# about 5 s up to 50 requests/s, then 3 and 2 s)
+SERVING_RATES = (20.0, 30.0, 40.0, 50.0, 100.0, 200.0)
+SERVING_COUNTS = (100, 150, 200, 250, 300, 400)
+
+
 def serving_block(rates, count_per_rate, budget_gb: float = 64.0) -> dict:
     """Serving: Poisson streams of solve requests (sizes log-uniform in
     [1000, 200000] per side, d in {32, 64}, bf16, 30 % warm-started re-solves of
@@ -398,15 +412,20 @@ def serving_block(rates, count_per_rate, budget_gb: float = 64.0) -> dict:
         wall = time.perf_counter() - t0
         srv.close()
         lat = serve.percentiles([r.latency for r in res])
+        window = reqs[-1].arrival
+        # throughput over the arrival window: replies sent before the last
+        # arrival (the drain after it is one large request's service time,
+        # not a rate)
+        in_window = sum(r.finished <= window for r in res) / window
         out[f"{rate:g}/s"] = {"requests": len(res), "p50_ms": 1e3 * lat["p50"], "p99_ms": 1e3 * lat["p99"],
-                              "mean_ms": 1e3 * lat["mean"], "served_per_s": len(res) / wall,
-                              "offered_per_s": rate, "window_s": reqs[-1].arrival,
+                              "mean_ms": 1e3 * lat["mean"], "served_in_window_per_s": in_window,
+                              "served_per_s_incl_drain": len(res) / wall, "offered_per_s": rate,
+                              "window_s": window, "drain_s": wall - window,
                               "not_converged_at_200_sweeps": sum(not r.converged for r in res),
                               "warm_resolves": sum(r.warm for r in res), "peak_active": srv.stats["peak_active"],
-                              "drain_s": wall - reqs[-1].arrival,
-                              "overloaded": len(res) / wall < 0.9 * rate}
+                              "overloaded": in_window < 0.9 * rate}
     ok = [r for r in rates if not out[f"{r:g}/s"]["overloaded"]]
-    out["sustainable_per_s"] = max(ok) if ok else None  # highest offered rate served at >= 90 %
+    out["sustainable_per_s"] = max(ok) if ok else None  # highest offered rate served at >= 90 % in the window
     return out
 
 
@@ -439,6 +458,84 @@ def run_paper_shapes(args):
         print(json.dumps({"workload": "paper-shaped mini-batch IPFP (Sec. 4.2)", "N": N, "M": N, "D": 50,
                           "ms_per_sweep": ms, "sweeps": args.steps, "gpair_evals_per_s": 2.0 * N * N / ms / 1e6,
                           "dtype": "bf16"}), flush=True)
+
+
+BATCHED_METRIC = "aggregate Gpair-evals/s of 512 independent markets in one persistent launch per half-sweep"
+
+
+def batched_config(mks) -> dict:
+    return {"workload": "batched: 512 markets, N and M log-uniform in [100, 50000], d=32 bf16 N(0,1/d), "
+                        "unit (even) or uniform{1..3} (odd) capacities, sigma=1",
+            "markets": len(mks), "pair_evals_per_sweep": float(sum(2.0 * mk.N * mk.M for mk in mks)),
+            "l2": "inputs larger than L2 (about 1 GB of packed factors); no flush"}
+
+
+def run_reference_batched(args):
+    """--impl reference for the batched workload: the float64 oracle's
+    half-sweep over sampled users of a pair-weighted sample of the 512
+    markets (the markets that carry most of the pair work), every host core,
+    reported as aggregate Gpair-evals/s like the GPU line (rank 0 only)."""
+    import numpy as np
+
+    from synth import batched_markets
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    mks = batched_markets()
+    rng = np.random.default_rng(7)
+    w = np.array([float(mk.N) * mk.M for mk in mks])
+    pick = rng.choice(len(mks), size=6, replace=False, p=w / w.sum())
+    sub = [mks[i] for i in pick]
+    pool = OraclePool(sub)
+    try:
+        rpc = [pool.calibrate(8.0 / len(sub), market=j) for j in range(len(sub))]
+        for _ in range(args.warmup):
+            pool.run(max(1, rpc[0] // 4), market=0)
+        pairs, secs = 0.0, []
+        for _ in range(args.steps):
+            t = 0.0
+            for j, mk in enumerate(sub):
+                t += pool.run(rpc[j], market=j)
+                pairs += pool.cores * min(rpc[j], mk.N) * mk.M
+            secs.append(t)
+    finally:
+        pool.close()
+    rate = pairs / sum(secs)
+    sample = (f"each step: float64 oracle half-sweep rows of 6 markets drawn with probability proportional to "
+              f"N*M ({', '.join(f'{mk.N}x{mk.M}' for mk in sub)}), sampled users against all partners, one "
+              f"process per host core")
+    line = {"impl": "reference", "metric": BATCHED_METRIC, "value": rate / 1e9, "unit": "Gpair-evals/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(secs) / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": batched_config(mks),
+            "cpu_baseline": {"value": rate / 1e9, "unit": "Gpair-evals/s", "cores": pool.cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate / 1e9, "unit": "Gpair-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_paper(args):
+    """--impl reference for the Sec. 4.2 shapes: the float64 oracle's time per
+    sweep at N = M = 1e2 ... 1e6, from a half-sweep of sampled users on every
+    host core, extrapolated to 2 N^2 pair evaluations (rank 0 only)."""
+    from synth import paper_shaped_market
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    for N in (100, 1_000, 10_000, 100_000, 1_000_000):
+        mk = paper_shaped_market(N)
+        pool = OraclePool(mk)
+        try:
+            rpc = pool.calibrate(2.0)
+            t = pool.run(rpc)
+        finally:
+            pool.close()
+        pair_rate = pool.cores * min(rpc, N) * N / t
+        ms = 2.0 * N * N / pair_rate * 1e3
+        print(json.dumps({"impl": "reference", "workload": "paper-shaped mini-batch IPFP (Sec. 4.2)", "N": N, "M": N,
+                          "D": 50, "ms_per_sweep": ms, "gpair_evals_per_s": pair_rate / 1e9, "dtype": "f64",
+                          "cpu_baseline": {"value": ms, "unit": "ms/sweep", "cores": pool.cores, "kind": "oracle",
+                                           "sample": f"float64 oracle X half-sweep of {pool.cores} x {min(rpc, N)} "
+                                                     f"sampled users against all {N} partners, extrapolated"}}),
+              flush=True)
 
 
 def run_batched(args):
@@ -536,14 +633,10 @@ def run_batched(args):
               "peak_source": "152 SMs x 32 ex2/clk/SM x sampled median SM clock"}
     # the binding unit (closest to its peak) is the roofline; the other is reported beside it
     rl_primary, rl_secondary = (rl_exp, rl_tensor) if rl_exp["frac"] > rl_tensor["frac"] else (rl_tensor, rl_exp)
-    line = {"metric": "aggregate Gpair-evals/s of 512 independent markets in one persistent launch per half-sweep",
+    line = {"metric": BATCHED_METRIC,
             "value": rate / 1e9, "unit": "Gpair-evals/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": "batched: 512 markets, N and M log-uniform in [100, 50000], d=32 bf16 N(0,1/d), "
-                                   "unit (even) or uniform{1..3} (odd) capacities, sigma=1",
-                       "markets": len(mks), "pair_evals_per_sweep": pair_evals,
-                       "l2": "inputs larger than L2 (about 1 GB of packed factors); no flush"},
+            "dtype": "bf16", "data": "synthetic", "config": batched_config(mks),
             "roofline": rl_primary, "roofline_secondary": rl_secondary,
             "clocks": clk, "gpu_launches": 6 * args.steps,
             "timing": "value: K batched sweeps replayed as one CUDA graph, CUDA events on the batch stream"}
@@ -567,6 +660,18 @@ def run_batched(args):
                       "slowest": [{"N": mks[i].N, "M": mks[i].M, "sweeps": int(sweeps[i]),
                                    "converged": bool(conv[i])} for i in np.argsort(-sweeps)[:5]]}})
     print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    """The serving sweep of the default line on its own: one replayed stream
+    of solve requests at 20 ... 200 requests/s (see serving_block)."""
+    import paper_2411_19214_gb300 as tu
+    tu.load()
+    t0 = time.perf_counter()
+    out = serving_block(SERVING_RATES, SERVING_COUNTS)
+    print(json.dumps({"workload": "serving (continuous batching of solve requests, top-10 replies)",
+                      "wall_s": time.perf_counter() - t0, "serving": out, "dtype": "bf16", "data": "synthetic"}),
+          flush=True)
 
 
 def run_ranking(args):
@@ -735,8 +840,7 @@ def run_ours(args):
     serving = None
     if cfg["path"] == "fused" and not args.no_extras and rank == 0 and not args.fp8:
         plain = plain_fp32_sweep(mk, dev, stream)
-        # windows of about 5, 4, 3 and 2 s
-        serving = serving_block((20.0, 50.0, 100.0, 200.0), (100, 200, 300, 400))
+        serving = serving_block(SERVING_RATES, SERVING_COUNTS)
 
     if rank != 0:
         if world > 1:
@@ -757,8 +861,8 @@ def run_ours(args):
             peak_source += " x 2 (nominal fp8/bf16 ratio)"
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak,
-                    "traffic": measured_traffic("fused 1Mx1M d64") if args.shape is None and not args.fp8
-                    else None,
+                    "traffic": (measured_traffic("fused fp8 1Mx1M d64" if args.fp8 else "fused 1Mx1M d64")
+                                if args.shape is None else None),
                     "kernel": "k_fused_halfsweep (tcgen05 %s MMA + ex2 row reduction)" % ("e4m3" if args.fp8
                                                                                          else "BF16"),
                     "per_launch": f"{flops:.4g} flop (2*N*M*2d) in {avg_pass_s * 1e3:.2f} ms average over "
@@ -830,7 +934,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["fused", "dense", "paper", "batched", "ranking"], default="fused",
+    ap.add_argument("--workload", choices=["fused", "dense", "paper", "batched", "ranking", "serving"], default="fused",
                     help="paper: the Sec. 4.2 shapes (N = M = 1e2..1e6, D = 50, U[0, 1/sqrt(D)], beta = 1), "
                          "time per sweep, one JSON line per size; batched: 512 independent markets in one "
                          "persistent launch per half-sweep")
@@ -856,6 +960,22 @@ def main():
         return
     if args.workload == "ranking" and args.impl == "ours":
         run_ranking(args)
+        return
+    if args.workload == "serving" and args.impl == "ours":
+        run_serving(args)
+        return
+    if args.impl == "reference" and args.workload in ("ranking", "serving"):
+        # latency and stopping-rule workloads of the GPU library; the float64
+        # oracle has no serving loop and no ranking stop to time (rank 0 prints)
+        if int(os.environ.get("RANK", "0")) == 0:
+            print(json.dumps({"impl": "reference", "unavailable": f"the {args.workload} workload times the GPU "
+                          "library's own loop; the float64 oracle has no counterpart"}), flush=True)
+        return
+    if args.impl == "reference" and args.workload == "batched":
+        run_reference_batched(args)
+        return
+    if args.impl == "reference" and args.workload == "paper":
+        run_reference_paper(args)
         return
     if args.impl == "reference":
         run_reference(args)
