@@ -2,10 +2,13 @@
 // checking, host/device staging, the sweep loop with CUDA-graph replay, and the
 // convergence test of tu_ipfp_solve.
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "tu_internal.cuh"
 
@@ -53,27 +56,109 @@ bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-template <typename T>
-tu_status dev_alloc(tu_market* m, T** p, size_t count) {
+// ------------------------------------------------------------------ memory
+// A market's device memory comes from a stream-ordered pool per device and
+// is allocated and freed in the order of the market's own stream. cudaMalloc
+// and cudaFree synchronise the device: in a loop that creates, updates and
+// destroys markets while others sweep (serving), each of them would drain
+// every other market's queued work. Freed blocks stay in the pool for the next
+// market; the pool is trimmed when the last market of the process goes away.
+// (The dense path's two resident kernel matrices keep cudaMalloc: they are
+// created once per market and their placement was measured.)
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+int g_live_markets = 0;
+
+cudaMemPool_t market_pool(int device) {
+  if (device < 0 || device >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (g_pools[device] == nullptr) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;  // no release at synchronisation points
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[device] = pool;
+  }
+  return g_pools[device];
+}
+
+tu_status dev_alloc_bytes(tu_market* m, void** p, size_t bytes) {
   *p = nullptr;
-  if (count == 0) return TU_OK;
-  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  if (bytes == 0) return TU_OK;
+  cudaMemPool_t pool = market_pool(m->device);
+  if (pool == nullptr) return fail(m, TU_ERR_CUDA, "device memory pool unavailable");
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, m->stream);
   if (e != cudaSuccess) {
     *p = nullptr;
-    return fail_cuda(m, e, "cudaMalloc");
+    return fail_cuda(m, e, "cudaMallocFromPoolAsync");
   }
   return TU_OK;
 }
 
+template <typename T>
+tu_status dev_alloc(tu_market* m, T** p, size_t count) {
+  void* v = nullptr;
+  const tu_status st = dev_alloc_bytes(m, &v, count * sizeof(T));
+  *p = static_cast<T*>(v);
+  return st;
+}
+
+// Stream-ordered release of a dev_alloc block (after the market's queued work).
+template <typename T>
+void dev_free(tu_market* m, T*& p) {
+  if (p != nullptr) cudaFreeAsync(p, m->stream);
+  p = nullptr;
+}
+
+// A market's page-locked host mirrors (results, query snapshot, omega, error
+// word) share one block from slabs of kSlabBlocks: page-locked allocations
+// serialise the device like cudaMalloc. Slabs live for the process.
+struct HostMirror {
+  double results[kResSlots];
+  double query[kResSlots + 1];
+  double omega;
+  int err;
+};
+constexpr size_t kMirrorBytes = (sizeof(HostMirror) + 63) / 64 * 64;
+constexpr int kSlabBlocks = 64;
+std::mutex g_mirror_mu;
+std::vector<void*> g_mirror_free;
+
+HostMirror* mirror_alloc() {
+  std::lock_guard<std::mutex> lk(g_mirror_mu);
+  if (g_mirror_free.empty()) {
+    void* slab = nullptr;
+    if (cudaMallocHost(&slab, kMirrorBytes * kSlabBlocks) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    for (int i = kSlabBlocks - 1; i >= 0; --i) g_mirror_free.push_back(static_cast<char*>(slab) + i * kMirrorBytes);
+  }
+  void* b = g_mirror_free.back();
+  g_mirror_free.pop_back();
+  return new (b) HostMirror();
+}
+
+void mirror_free(void* b) {
+  if (b == nullptr) return;
+  std::lock_guard<std::mutex> lk(g_mirror_mu);
+  g_mirror_free.push_back(b);
+}
+
 tu_status ensure_staging(tu_market* m, size_t bytes) {
   if (m->staging_bytes >= bytes) return TU_OK;
-  if (m->staging != nullptr) {
-    TU_CK(m, cudaStreamSynchronize(m->stream));
-    cudaFree(m->staging);
-    m->staging = nullptr;
-    m->staging_bytes = 0;
-  }
-  TU_CK(m, cudaMalloc(&m->staging, bytes));
+  dev_free(m, m->staging);  // stream-ordered: after the copies that used it
+  m->staging_bytes = 0;
+  TU_TRY(dev_alloc_bytes(m, &m->staging, bytes));
   m->staging_bytes = bytes;
   return TU_OK;
 }
@@ -110,16 +195,16 @@ tu_status side_alloc(tu_market* m, Side& s, int64_t rows, bool has_bias) {
   return TU_OK;
 }
 
-void side_free(Side& s) {
-  cudaFree(s.log_u);
-  cudaFree(s.ell);
-  cudaFree(s.pvec);
-  cudaFree(s.mass);
-  cudaFree(s.lmax);
-  cudaFree(s.b2s);
-  cudaFree(s.fac16);
-  cudaFree(s.fac8);
-  cudaFree(s.fac32);
+void side_free(tu_market* m, Side& s) {
+  dev_free(m, s.log_u);
+  dev_free(m, s.ell);
+  dev_free(m, s.pvec);
+  dev_free(m, s.mass);
+  dev_free(m, s.lmax);
+  dev_free(m, s.b2s);
+  dev_free(m, s.fac16);
+  dev_free(m, s.fac8);
+  dev_free(m, s.fac32);
   s = Side();
 }
 
@@ -138,9 +223,10 @@ tu_status upload_masses(tu_market* m, Side& s, const double* host) {
     double* ones = new (std::nothrow) double[npad];
     if (ones == nullptr) return fail(m, TU_ERR_OOM, "host allocation");
     for (size_t i = 0; i < npad; ++i) ones[i] = 1.0;
-    cudaError_t e = cudaMemcpy(s.mass + s.rows, ones, npad * sizeof(double), cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpyAsync(s.mass + s.rows, ones, npad * sizeof(double), cudaMemcpyHostToDevice, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);  // `ones` is pageable and freed below
     delete[] ones;
-    if (e != cudaSuccess) return fail_cuda(m, e, "cudaMemcpy(mass padding)");
+    if (e != cudaSuccess) return fail_cuda(m, e, "mass padding");
   }
   return TU_OK;
 }
@@ -191,7 +277,7 @@ tu_status load_factors(tu_market* m, const void* F, const void* K, const void* G
   if (st == TU_OK) st = device_view(m, G, by, 0, &a);
   if (st == TU_OK) st = device_view(m, L, by, by, &b);
   if (st == TU_OK) st = pack(m->Y, a, b);
-  cudaFree(fscratch);
+  dev_free(m, fscratch);
   if (st != TU_OK) return st;
   // the multiplier of <a_x, b_y> in the exponent (log2 units)
   m->cmul = (float)std::ldexp(1.4426950408889634 / (2.0 * m->sigma), fp8 ? m->X.fp8_exp + m->Y.fp8_exp : 0);
@@ -203,7 +289,7 @@ tu_status load_factors(tu_market* m, const void* F, const void* K, const void* G
   if (e == cudaSuccess) e = launch_row_norms(m, m->Y, norms + 1);
   if (e == cudaSuccess) e = cudaMemcpyAsync(hn, norms, sizeof(hn), cudaMemcpyDeviceToHost, m->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
-  cudaFree(norms);
+  dev_free(m, norms);
   if (e != cudaSuccess) return fail_cuda(m, e, "factor norms");
   if (!std::isfinite(hn[0]) || !std::isfinite(hn[1]))
     return fail(m, TU_ERR_NONFINITE, "factor matrices contain NaN or Inf");
@@ -452,22 +538,28 @@ void tu_market_destroy(tu_market_t m) {
     cudaEventDestroy(pr.second);
   }
   if (m->graph) cudaGraphExecDestroy(m->graph);
-  side_free(m->X);
-  side_free(m->Y);
-  cudaFree(m->Ahat);
-  cudaFree(m->partials);
-  cudaFree(m->mpartials);
-  cudaFree(m->AhatT);
-  cudaFree(m->results);
-  cudaFree(m->err_dev);
-  cudaFree(m->staging);
-  cudaFree(m->aux);
+  side_free(m, m->X);
+  side_free(m, m->Y);
+  if (m->Ahat) cudaFree(m->Ahat);
+  if (m->AhatT) cudaFree(m->AhatT);
+  dev_free(m, m->partials);
+  dev_free(m, m->mpartials);
+  dev_free(m, m->results);
+  dev_free(m, m->err_dev);
+  dev_free(m, m->staging);
+  dev_free(m, m->aux);
+  dev_free(m, m->omega_dev);
   if (m->done_ev) cudaEventDestroy(m->done_ev);
-  cudaFree(m->omega_dev);
-  cudaFreeHost(m->omega_host);
-  cudaFreeHost(m->query_host);
-  cudaFreeHost(m->results_host);
-  cudaFreeHost(m->err_host);
+  mirror_free(m->results_host);  // the block that holds all four host mirrors
+  {
+    // every market that reaches this point was counted by tu_market_create
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (--g_live_markets == 0 && m->device >= 0 && m->device < kMaxDevices && g_pools[m->device] != nullptr) {
+      // the last market: return the pool's memory once its frees have run
+      if (m->stream) cudaStreamSynchronize(m->stream);
+      cudaMemPoolTrimTo(g_pools[m->device], 0);
+    }
+  }
   delete m;
 }
 
@@ -520,32 +612,39 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
       return TU_ERR_UNSUPPORTED;
     }
   }
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    ++g_live_markets;  // from here on every exit goes through tu_market_destroy
+  }
   if ((st = side_alloc(m, m->X, D.N, D.bias_x != nullptr)) != TU_OK) return bail(st);
   if ((st = side_alloc(m, m->Y, D.M, D.bias_y != nullptr)) != TU_OK) return bail(st);
   if ((st = dev_alloc(m, &m->partials, (size_t)kMaxPartials * 4)) != TU_OK) return bail(st);
   if ((st = dev_alloc(m, &m->mpartials, (size_t)kMaxPartials)) != TU_OK) return bail(st);
   if ((st = dev_alloc(m, &m->results, (size_t)kResSlots)) != TU_OK) return bail(st);
   if ((st = dev_alloc(m, &m->err_dev, 1)) != TU_OK) return bail(st);
-  if (cudaMallocHost(&m->results_host, kResSlots * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost(&m->query_host, (kResSlots + 1) * sizeof(double)) != cudaSuccess ||
-      cudaMallocHost(&m->omega_host, sizeof(double)) != cudaSuccess ||
-      cudaMallocHost(&m->err_host, sizeof(int)) != cudaSuccess) {
-    cudaGetLastError();
-    return bail(TU_ERR_OOM);
+  {
+    HostMirror* hm = mirror_alloc();
+    if (hm == nullptr) return bail(TU_ERR_OOM);
+    m->results_host = hm->results;
+    m->query_host = hm->query;
+    m->omega_host = &hm->omega;
+    m->err_host = &hm->err;
   }
   *m->err_host = 0;
   if (D.path == TU_PATH_DENSE) {
     m->ldA = round_up(D.M, 4);
     m->ldN = round_up(D.N, 4);
-    if ((st = dev_alloc(m, &m->Ahat, (size_t)m->N * m->ldA)) != TU_OK) return bail(st);
-    if ((st = dev_alloc(m, &m->AhatT, (size_t)m->M * m->ldN)) != TU_OK) return bail(st);
+    cudaError_t e = cudaMalloc(&m->Ahat, (size_t)m->N * m->ldA * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&m->AhatT, (size_t)m->M * m->ldN * sizeof(float));
+    if (e != cudaSuccess) return bail(fail_cuda(m, e, "cudaMalloc(A-hat)"));
   }
   // (allocated after the dense matrices: placing this small allocation before
   // them measurably slowed the dense row stream)
   if ((st = dev_alloc(m, &m->omega_dev, 1)) != TU_OK) return bail(st);
   *m->omega_host = 1.0;
-  if (cudaMemcpy(m->omega_dev, m->omega_host, sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
-    return bail(TU_ERR_CUDA);
+  if (cudaMemcpyAsync(m->omega_dev, m->omega_host, sizeof(double), cudaMemcpyHostToDevice, m->stream) !=
+      cudaSuccess)
+    return bail(fail_cuda(m, cudaGetLastError(), "omega"));
   if ((st = upload_masses(m, m->X, D.n)) != TU_OK) return bail(st);
   if ((st = upload_masses(m, m->Y, D.m)) != TU_OK) return bail(st);
   // biases -> b / (2 sigma); potentials start at u = v = 1
@@ -835,7 +934,7 @@ tu_status tu_ipfp_solve_ranking(tu_market_t m, int k, int64_t sample, int check_
       break;
     }
   }
-  cudaFree(buf);
+  dev_free(m, buf);
   if (st != TU_OK) return st;
   if (ctl.enabled()) TU_TRY(set_omega(m, m->omega_cfg > 1.0 ? m->omega_cfg : 1.0));
   double res_inf = INFINITY, res_l1 = INFINITY;
@@ -898,11 +997,9 @@ tu_status tu_topk_partners(tu_market_t m, int side, int k, int64_t row0, int64_t
     // column half go through a nrows x k scratch buffer
     const size_t hb = (size_t)nrows * k * (sizeof(float) + sizeof(int32_t));
     if (m->aux_bytes < hb) {
-      TU_CK(m, cudaStreamSynchronize(m->stream));
-      cudaFree(m->aux);
-      m->aux = nullptr;
+      dev_free(m, m->aux);  // stream-ordered: after the passes that used it
       m->aux_bytes = 0;
-      TU_CK(m, cudaMalloc(&m->aux, hb));
+      TU_TRY(dev_alloc_bytes(m, &m->aux, hb));
       m->aux_bytes = hb;
     }
     float* hv = static_cast<float*>(m->aux);
