@@ -398,6 +398,8 @@ def serving_block(rates, count_per_rate, budget_gb: float = 64.0) -> dict:
     server; latency from arrival to the top-10 reply. Every rate replays the
     same requests (the first `count` of one stream), arrivals scaled to the
     rate."""
+    import numpy as np
+
     from paper_2411_19214_gb300 import serve
     from synth import serving_workload
     out = {}
@@ -417,12 +419,18 @@ def serving_block(rates, count_per_rate, budget_gb: float = 64.0) -> dict:
         # arrival (the drain after it is one large request's service time,
         # not a rate)
         in_window = sum(r.finished <= window for r in res) / window
+        # device work the loop drove: 2 N M pair evaluations per sweep plus
+        # one N x M pass for the top-10 reply
+        shape = {q.rid: q.shape for q in reqs}
+        pair_evals = sum((2.0 * r.sweeps + 1.0) * shape[r.rid][0] * shape[r.rid][1] for r in res)
         out[f"{rate:g}/s"] = {"requests": len(res), "p50_ms": 1e3 * lat["p50"], "p99_ms": 1e3 * lat["p99"],
                               "mean_ms": 1e3 * lat["mean"], "served_in_window_per_s": in_window,
                               "served_per_s_incl_drain": len(res) / wall, "offered_per_s": rate,
                               "window_s": window, "drain_s": wall - window,
                               "not_converged_at_200_sweeps": sum(not r.converged for r in res),
                               "warm_resolves": sum(r.warm for r in res), "peak_active": srv.stats["peak_active"],
+                              "sweeps_mean": float(np.mean([r.sweeps for r in res])),
+                              "gpair_evals_per_s": pair_evals / wall / 1e9,
                               "overloaded": in_window < 0.9 * rate}
     ok = [r for r in rates if not out[f"{r:g}/s"]["overloaded"]]
     out["sustainable_per_s"] = max(ok) if ok else None  # highest offered rate served at >= 90 % in the window
