@@ -18,6 +18,7 @@
 #include <string>
 #include <vector>
 
+#include "trace.h"
 #include "tu_internal.cuh"
 
 using namespace tu;
@@ -455,6 +456,7 @@ double res(const tu_batch* b, int mk, int slot) { return b->results_host[(size_t
 extern "C" {
 
 void tu_batch_destroy(tu_batch_t b) {
+  TU_TRACE("tu_batch_destroy");
   if (b == nullptr) return;
   cudaSetDevice(b->device);
   if (b->stream) cudaStreamSynchronize(b->stream);
@@ -481,6 +483,7 @@ void tu_batch_destroy(tu_batch_t b) {
 const char* tu_batch_last_error(tu_batch_t b) { return b ? b->last_error.c_str() : ""; }
 
 tu_status tu_batch_create(const tu_market_t* markets, int count, void* stream, tu_batch_t* out) {
+  TU_TRACE("tu_batch_create");
   if (out == nullptr) return TU_ERR_INVALID_ARG;
   *out = nullptr;
   if (markets == nullptr || count < 1 || count > kMaxBatch) return TU_ERR_INVALID_ARG;
@@ -605,6 +608,7 @@ tu_status tu_batch_profile_read(tu_batch_t b, double* pass_ms, int64_t* passes) 
 }
 
 tu_status tu_batch_sweep(tu_batch_t b, int nsweeps, double* residual_out) {
+  TU_TRACE("tu_batch_sweep");
   TB_TRY(check_live(b));
   if (nsweeps < 0) return bfail(b, TU_ERR_INVALID_ARG, "nsweeps < 0");
   TB_TRY(wait_members(b));
@@ -625,6 +629,7 @@ tu_status tu_batch_sweep(tu_batch_t b, int nsweeps, double* residual_out) {
 }
 
 tu_status tu_batch_solve(tu_batch_t b, double tol, int max_iter, int warm_start, tu_solve_info* infos) {
+  TU_TRACE("tu_batch_solve");
   TB_TRY(check_live(b));
   if (!(tol >= 0.0) || max_iter < 0) return bfail(b, TU_ERR_INVALID_ARG, "tol < 0 or max_iter < 0");
   TB_TRY(wait_members(b));

@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "trace.h"
 #include "tu_internal.cuh"
 
 using namespace tu;
@@ -530,6 +531,7 @@ tu_status tu_profile_read(tu_market_t m, double* pass_ms, int64_t* passes) {
 }
 
 void tu_market_destroy(tu_market_t m) {
+  TU_TRACE("tu_market_destroy");
   if (m == nullptr) return;
   cudaSetDevice(m->device);
   if (m->stream) cudaStreamSynchronize(m->stream);
@@ -564,6 +566,7 @@ void tu_market_destroy(tu_market_t m) {
 }
 
 tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
+  TU_TRACE("tu_market_create");
   if (out == nullptr || desc == nullptr) return TU_ERR_INVALID_ARG;
   *out = nullptr;
   const tu_market_desc& D = *desc;
@@ -676,6 +679,7 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
 }
 
 tu_status tu_market_update_factors(tu_market_t m, const void* F, const void* K, const void* G, const void* L) {
+  TU_TRACE("tu_market_update_factors");
   TU_TRY(check_live(m));
   if (!F || !K || !G || !L) return fail(m, TU_ERR_INVALID_ARG, "null factor pointer");
   TU_TRY(load_factors(m, F, K, G, L));
@@ -683,6 +687,7 @@ tu_status tu_market_update_factors(tu_market_t m, const void* F, const void* K, 
 }
 
 tu_status tu_ipfp_sweep(tu_market_t m, int nsweeps, double* residual_out) {
+  TU_TRACE("tu_ipfp_sweep");
   TU_TRY(check_live(m));
   if (nsweeps < 0) return fail(m, TU_ERR_INVALID_ARG, "nsweeps < 0");
   TU_TRY(clear_results(m));
@@ -783,6 +788,7 @@ int64_t tu_market_footprint(int64_t N, int64_t M, int64_t d, int path) {
 }
 
 tu_status tu_ipfp_solve(tu_market_t m, double tol, int max_iter, int warm_start, tu_solve_info* info) {
+  TU_TRACE("tu_ipfp_solve");
   TU_TRY(check_live(m));
   if (!(tol >= 0.0) || max_iter < 0) return fail(m, TU_ERR_INVALID_ARG, "tol < 0 or max_iter < 0");
   if (!warm_start) {
@@ -850,6 +856,7 @@ tu_status tu_ipfp_solve(tu_market_t m, double tol, int max_iter, int warm_start,
 
 tu_status tu_ipfp_solve_ranking(tu_market_t m, int k, int64_t sample, int check_every, int patience,
                                 double score_eps, int max_iter, int warm_start, tu_solve_info* info) {
+  TU_TRACE("tu_ipfp_solve_ranking");
   TU_TRY(check_live(m));
   if (k < 1 || k > 63 || k > m->N || k > m->M || sample < 1 || check_every < 1 || patience < 1 ||
       !(score_eps >= 0.0) || max_iter < 0)
@@ -954,6 +961,7 @@ tu_status tu_ipfp_solve_ranking(tu_market_t m, int k, int64_t sample, int check_
 }
 
 tu_status tu_mu_block(tu_market_t m, int64_t x0, int64_t nx, int64_t y0, int64_t ny, float* out, int64_t ld) {
+  TU_TRACE("tu_mu_block");
   TU_TRY(check_live(m));
   if (out == nullptr || x0 < 0 || y0 < 0 || nx < 0 || ny < 0 || x0 + nx > m->N || y0 + ny > m->M || ld < ny)
     return fail(m, TU_ERR_INVALID_ARG, "mu block out of range");
@@ -980,6 +988,7 @@ tu_status tu_mu_block(tu_market_t m, int64_t x0, int64_t nx, int64_t y0, int64_t
 
 tu_status tu_topk_partners(tu_market_t m, int side, int k, int64_t row0, int64_t nrows, int32_t* idx,
                            float* log_mu) {
+  TU_TRACE("tu_topk_partners");
   TU_TRY(check_live(m));
   const int64_t rows = side == 0 ? m->N : m->M;
   const int64_t partners = side == 0 ? m->M : m->N;
@@ -1016,6 +1025,7 @@ tu_status tu_topk_partners(tu_market_t m, int side, int k, int64_t row0, int64_t
 }
 
 tu_status tu_get_potentials(tu_market_t m, float* log_u, float* log_v) {
+  TU_TRACE("tu_get_potentials");
   TU_TRY(check_live(m));
   Side* sides[2] = {&m->X, &m->Y};
   float* outs[2] = {log_u, log_v};
@@ -1035,6 +1045,7 @@ tu_status tu_get_potentials(tu_market_t m, float* log_u, float* log_v) {
 }
 
 tu_status tu_set_potentials(tu_market_t m, const float* log_u, const float* log_v) {
+  TU_TRACE("tu_set_potentials");
   TU_TRY(check_live(m));
   Side* sides[2] = {&m->X, &m->Y};
   const float* ins[2] = {log_u, log_v};

@@ -22,7 +22,19 @@ soon as memory allows and their sweeps overlap on the device:
   and copies them back);
 * re-solves: a request that names the key of a resident market replaces its
   factors (``tu_market_update_factors``) and continues from its potentials
-  (warm start) instead of starting from u = v = 1.
+  (warm start) instead of starting from u = v = 1;
+* failures stay with their request: a malformed request (inconsistent shapes,
+  d above the fused path's limit, capacities that are not finite and
+  positive, sigma <= 0, or a footprint larger than the whole budget) is
+  answered ``invalid`` without being admitted; a library error while creating,
+  updating or sweeping a market (non-finite factors, an exponent range the
+  path refuses, a device-side wait that ran out) answers that request
+  ``error`` and releases its market; a request past its ``deadline`` is
+  answered ``deadline`` (after its in-flight block, without a ranking); the
+  other requests are served as if it had not been there;
+* tracing and metrics: each request is an NVTX range from arrival to reply
+  (when torch provides start/end ranges), and with ``log_path`` every reply
+  appends one JSON line (times, sweeps, residual, status).
 
 Latency is measured from a request's arrival time to its reply.
 """
@@ -32,15 +44,20 @@ from __future__ import annotations
 import collections
 import concurrent.futures as cf
 import dataclasses
+import json
+import math
 import threading
 import time
 from typing import Dict, List, Optional
 
 import numpy as np
 
-from . import (tu_get_potentials, tu_ipfp_sweep, tu_market_create, tu_market_destroy, tu_market_footprint,
-               tu_market_query, tu_market_relax_update, tu_market_set_relaxation, tu_market_update_factors,
-               tu_market_use_graphs, tu_topk_partners)
+from . import (TuError, tu_get_potentials, tu_ipfp_sweep, tu_market_create, tu_market_destroy,
+               tu_market_footprint, tu_market_query, tu_market_relax_update, tu_market_set_relaxation,
+               tu_market_update_factors, tu_market_use_graphs, tu_topk_partners)
+
+# the fused path's factor dimension limit (2d <= 128: one 128-wide MMA inner dimension)
+MAX_D = 64
 
 
 @dataclasses.dataclass
@@ -57,6 +74,7 @@ class SolveRequest:
     bias_x: object = None
     bias_y: object = None
     key: Optional[str] = None  # resident-market key: a later request with the same key warm-starts
+    deadline: Optional[float] = None  # seconds after arrival; past it the request is answered "deadline"
 
     @property
     def shape(self):
@@ -78,10 +96,54 @@ class SolveResult:
     topk_logmu: Optional[np.ndarray] = None
     log_u: Optional[np.ndarray] = None
     log_v: Optional[np.ndarray] = None
+    # "ok" (converged), "not_converged" (sweep cap), "invalid", "error" or "deadline"
+    status: str = "ok"
+    error: Optional[str] = None
 
     @property
     def latency(self) -> float:
         return self.finished - self.arrival
+
+
+def _shape_of(a):
+    return tuple(int(v) for v in getattr(a, "shape", ()))
+
+
+def validate(req: SolveRequest) -> Optional[str]:
+    """Why a request cannot be served (None when it can): host-side checks of
+    shapes, capacities and sigma. Factor values are checked by the library
+    (non-finite entries, exponent range) when the market is created."""
+    fs, ks, gs, ls = (_shape_of(getattr(req, n)) for n in ("F", "K", "G", "L"))
+    if len(fs) != 2 or fs != ks or len(gs) != 2 or gs != ls:
+        return "F and K must share one N x d shape, G and L one M x d shape"
+    N, d = fs
+    M, dy = gs
+    if N < 1 or M < 1 or d < 1 or dy != d:
+        return "N, M, d must be >= 1 and both sides must have the same d"
+    if d > MAX_D:
+        return f"d = {d} exceeds the fused path's limit of {MAX_D}"
+    for name, cap, rows in (("n", req.n, N), ("m", req.m, M)):
+        c = np.asarray(cap, dtype=np.float64)
+        if c.shape != (rows,):
+            return f"{name} must have one capacity per user ({rows})"
+        if not np.all(np.isfinite(c)) or not np.all(c > 0):
+            return f"capacities {name} must be finite and > 0"
+    if not (isinstance(req.sigma, (int, float)) and math.isfinite(req.sigma) and req.sigma > 0):
+        return "sigma must be finite and > 0"
+    for name, b, rows in (("bias_x", req.bias_x, N), ("bias_y", req.bias_y, M)):
+        if b is not None and _shape_of(b) != (rows,):
+            return f"{name} must have one entry per user ({rows})"
+    return None
+
+
+def _nvtx(kind: str, arg):
+    """torch's start/end NVTX ranges (they may span loop iterations), if present."""
+    try:
+        import torch
+        fn = getattr(torch.cuda.nvtx, "range_start" if kind == "start" else "range_end", None)
+        return fn(arg) if fn is not None else None
+    except Exception:  # tracing is best effort
+        return None
 
 
 @dataclasses.dataclass
@@ -101,7 +163,7 @@ class _Slot:
 class Server:
     def __init__(self, hbm_budget_bytes: int, tol: float = 1e-6, max_sweeps: int = 200, sweeps_per_step: int = 8,
                  k: int = 10, max_active: int = 64, keep_potentials: bool = False, relax: bool = True,
-                 workers: int = 4):
+                 workers: int = 4, log_path: Optional[str] = None):
         self.budget = int(hbm_budget_bytes)
         self.tol = tol
         self.max_sweeps = max_sweeps
@@ -112,8 +174,10 @@ class Server:
         self.relax = relax
         self.used = 0
         self.resident: "collections.OrderedDict[str, _Slot]" = collections.OrderedDict()
-        self.stats = dict(admitted=0, evicted=0, warm=0, not_converged=0, peak_active=0, peak_bytes=0)
+        self.stats = dict(admitted=0, evicted=0, warm=0, not_converged=0, peak_active=0, peak_bytes=0, invalid=0,
+                          errors=0, deadline=0)
         self.pool = cf.ThreadPoolExecutor(max_workers=max(1, workers))
+        self.log = open(log_path, "a") if log_path else None
 
     # ------------------------------------------------------------------ helpers
     # Every library call is made from the thread that runs run(); the workers
@@ -155,8 +219,9 @@ class Server:
         return out
 
     def _admit(self, req: SolveRequest):
-        """Budget and residency decisions. Returns (kind, slot, future of the
-        uploaded arrays), or None when the budget is full."""
+        """Budget and residency decisions. Returns (kind, slot or bytes, future
+        of the uploaded arrays), None when the budget is full for now, or
+        ("invalid", reason) when the request can never fit the budget."""
         N, M, d = req.shape
         if req.key is not None and req.key in self.resident:
             slot = self.resident.pop(req.key)
@@ -166,6 +231,8 @@ class Server:
             tu_market_destroy(slot.handle)  # shape changed: a cold solve
             self.used -= slot.bytes
         need = tu_market_footprint(N, M, d, "fused")
+        if need > self.budget:
+            return ("invalid", f"footprint {need} bytes exceeds the budget of {self.budget} bytes")
         while self.used + need > self.budget and self._evict_one():
             pass
         if self.used + need > self.budget:
@@ -175,17 +242,28 @@ class Server:
         return ("cold", need, self.pool.submit(self._upload, req))
 
     def _activate(self, kind, arg, arrays: dict, req: SolveRequest, now: float) -> _Slot:
+        """Create (cold) or refresh (warm) the request's market. A library error
+        propagates as TuError after the market and its bytes are released."""
         import torch
         a = arrays
         if kind == "warm":
             slot = arg
-            tu_market_update_factors(slot.handle, a["F"], a["K"], a["G"], a["L"])
+            try:
+                tu_market_update_factors(slot.handle, a["F"], a["K"], a["G"], a["L"])
+            except TuError:
+                tu_market_destroy(slot.handle)
+                self.used -= slot.bytes
+                raise
             slot.req, slot.admitted, slot.inflight, slot.warm = req, now, False, True
             slot.start_sweeps = slot.sweeps
             return slot
         stream = torch.cuda.Stream()
-        h = tu_market_create(a["F"], a["K"], a["G"], a["L"], req.n, req.m, req.sigma, bias_x=a["bias_x"],
-                             bias_y=a["bias_y"], path="fused", stream=stream)
+        try:
+            h = tu_market_create(a["F"], a["K"], a["G"], a["L"], req.n, req.m, req.sigma, bias_x=a["bias_x"],
+                                 bias_y=a["bias_y"], path="fused", stream=stream)
+        except TuError:
+            self.used -= arg
+            raise
         # a request runs only a few blocks of sweeps: too few to amortise a graph capture
         tu_market_use_graphs(h, False)
         if self.relax:
@@ -217,13 +295,46 @@ class Server:
             host = [None if t is None else t.cpu().numpy() for t in (idx, lm, lu, lv)]
             return SolveResult(rid=req.rid, arrival=req.arrival, admitted=slot.admitted, finished=now_fn(),
                                sweeps=sweeps, residual=residual, converged=residual <= tol, match_count=match,
-                               warm=slot.warm, topk_idx=host[0], topk_logmu=host[1], log_u=host[2], log_v=host[3])
+                               warm=slot.warm, topk_idx=host[0], topk_logmu=host[1], log_u=host[2], log_v=host[3],
+                               status="ok" if residual <= tol else "not_converged")
         return self.pool.submit(fetch)
+
+    @staticmethod
+    def _failed(req: SolveRequest, status: str, error: str, now: float, admitted: float = math.nan,
+                sweeps: int = 0, warm: bool = False) -> SolveResult:
+        return SolveResult(rid=req.rid, arrival=req.arrival, admitted=admitted, finished=now, sweeps=sweeps,
+                           residual=math.nan, converged=False, match_count=math.nan, warm=warm, status=status,
+                           error=error)
+
+    def _release(self, slot: _Slot):
+        """A market whose request failed or ran out of time is not kept resident."""
+        tu_market_destroy(slot.handle)
+        self.used -= slot.bytes
+
+    def _record(self, res: SolveResult, results: Dict[int, SolveResult], ranges: Dict[int, object]):
+        results[res.rid] = res
+        if res.status == "not_converged":
+            self.stats["not_converged"] += 1
+        elif res.status in ("invalid", "deadline"):
+            self.stats[res.status] += 1
+        elif res.status == "error":
+            self.stats["errors"] += 1
+        rng = ranges.pop(res.rid, None)
+        if rng is not None:
+            _nvtx("end", rng)
+        if self.log is not None:
+            self.log.write(json.dumps({
+                "rid": res.rid, "status": res.status, "arrival": res.arrival, "admitted": res.admitted,
+                "finished": res.finished, "latency": res.latency, "sweeps": res.sweeps,
+                "residual": res.residual, "match_count": res.match_count, "warm": res.warm,
+                "error": res.error}) + "\n")
+            self.log.flush()
 
     # ------------------------------------------------------------------ loop
     def run(self, requests: List[SolveRequest], realtime: bool = True) -> List[SolveResult]:
         """Serve `requests` (sorted by arrival). With realtime, arrivals are
-        replayed against the wall clock; otherwise all are available at once."""
+        replayed against the wall clock; otherwise all are available at once.
+        Every request gets exactly one result (see SolveResult.status)."""
         reqs = sorted(requests, key=lambda r: r.arrival)
         t0 = time.perf_counter()
         now_fn = (lambda: time.perf_counter() - t0)
@@ -233,13 +344,30 @@ class Server:
         active: List[_Slot] = []
         finishing: List[tuple] = []   # (future of the result, slot)
         results: Dict[int, SolveResult] = {}
+        ranges: Dict[int, object] = {}
+
+        def expired(req: SolveRequest, now: float) -> bool:
+            return req.deadline is not None and now > req.arrival + req.deadline
+
         try:
             while len(results) < len(reqs):
                 now = now_fn()
                 while nxt < len(reqs) and (not realtime or reqs[nxt].arrival <= now):
-                    pending.append(reqs[nxt])
+                    req = reqs[nxt]
                     nxt += 1
+                    ranges[req.rid] = _nvtx("start", f"request {req.rid}")
+                    why = validate(req)
+                    if why is not None:
+                        self._record(self._failed(req, "invalid", why, now), results, ranges)
+                    else:
+                        pending.append(req)
                 progressed = False
+                # requests whose deadline passed while they waited
+                for req in [q for q in pending if expired(q, now)]:
+                    pending.remove(req)
+                    self._record(self._failed(req, "deadline", "deadline passed before admission", now), results,
+                                 ranges)
+                    progressed = True
                 # admission, first come first served; a request whose key names a
                 # market that is still in use waits until it is resident again
                 busy = {sl.req.key for sl in active} | {x[3].key for x in admitting} | \
@@ -251,22 +379,34 @@ class Server:
                     if adm is None:
                         break
                     req = pending.popleft()
+                    progressed = True
+                    if adm[0] == "invalid":
+                        self._record(self._failed(req, "invalid", adm[1], now_fn()), results, ranges)
+                        continue
                     admitting.append(adm + (req,))
                     busy.add(req.key)
                     self.stats["admitted"] += 1
-                    progressed = True
                 for x in [x for x in admitting if x[2].done()]:
                     admitting.remove(x)
-                    active.append(self._activate(x[0], x[1], x[2].result(), x[3], now_fn()))
+                    kind, arg, fut, req = x
                     progressed = True
+                    try:
+                        arrays = fut.result()
+                        active.append(self._activate(kind, arg, arrays, req, now_fn()))
+                    except TuError as e:
+                        self._record(self._failed(req, "error", str(e), now_fn()), results, ranges)
+                    except Exception as e:  # an upload that failed (e.g. arrays torch cannot take)
+                        if kind == "warm":
+                            self._release(arg)
+                        else:
+                            self.used -= arg
+                        self._record(self._failed(req, "error", f"{type(e).__name__}: {e}", now_fn()), results,
+                                     ranges)
                 self.stats["peak_active"] = max(self.stats["peak_active"], len(active) + len(admitting))
                 # replies that are ready
                 for fut, slot in [x for x in finishing if x[0].done()]:
                     finishing.remove((fut, slot))
-                    res = fut.result()
-                    results[res.rid] = res
-                    if not res.converged:
-                        self.stats["not_converged"] += 1
+                    self._record(fut.result(), results, ranges)
                     key = slot.req.key
                     if key is not None:
                         # keep the market resident for warm-started re-solves
@@ -278,45 +418,71 @@ class Server:
                         self.used -= slot.bytes
                     progressed = True
                 for slot in list(active):
-                    idle, res, match, _ = tu_market_query(slot.handle)
-                    if not idle:
-                        continue
-                    if slot.inflight:
-                        slot.inflight = False
+                    try:
+                        idle, res, match, _ = tu_market_query(slot.handle)
+                        if not idle:
+                            continue
                         done = slot.sweeps - slot.start_sweeps
-                        if res <= self.tol or done >= self.max_sweeps:
+                        if slot.inflight:
+                            slot.inflight = False
+                            if res <= self.tol or done >= self.max_sweeps:
+                                active.remove(slot)
+                                finishing.append((self._reply(slot, res, match, now_fn), slot))
+                                progressed = True
+                                continue
+                        if expired(slot.req, now_fn()):
                             active.remove(slot)
-                            finishing.append((self._reply(slot, res, match, now_fn), slot))
+                            self._release(slot)
+                            self._record(self._failed(slot.req, "deadline", "deadline passed during the solve",
+                                                      now_fn(), slot.admitted, done, slot.warm), results, ranges)
                             progressed = True
                             continue
-                        if self.relax:
+                        if slot.inflight is False and done > 0 and self.relax:
                             tu_market_relax_update(slot.handle, self.tol)
-                    n = min(self.step, self.max_sweeps - (slot.sweeps - slot.start_sweeps))
-                    tu_ipfp_sweep(slot.handle, n)
-                    slot.sweeps += n
-                    slot.inflight = True
-                    progressed = True
+                        n = min(self.step, self.max_sweeps - done)
+                        tu_ipfp_sweep(slot.handle, n)
+                        slot.sweeps += n
+                        slot.inflight = True
+                        progressed = True
+                    except TuError as e:
+                        active.remove(slot)
+                        self._release(slot)
+                        self._record(self._failed(slot.req, "error", str(e), now_fn(), slot.admitted,
+                                                  slot.sweeps - slot.start_sweeps, slot.warm), results, ranges)
+                        progressed = True
                 if not progressed:
                     time.sleep(0.0002)
         finally:
             for x in admitting:
-                x[2].result()
+                try:
+                    x[2].result()
+                except Exception:
+                    pass
                 if x[0] == "warm":
                     active.append(x[1])
                 else:
                     self.used -= x[1]
             for fut, slot in finishing:
-                fut.result()
+                try:
+                    fut.result()
+                except Exception:
+                    pass
                 active.append(slot)
             for slot in active:
                 tu_market_destroy(slot.handle)
                 self.used -= slot.bytes
+            for rng in ranges.values():
+                if rng is not None:
+                    _nvtx("end", rng)
         return [results[r.rid] for r in reqs]
 
     def close(self):
         while self._evict_one():
             pass
         self.pool.shutdown(wait=True)
+        if self.log is not None:
+            self.log.close()
+            self.log = None
 
 
 def percentiles(latencies: List[float]) -> dict:

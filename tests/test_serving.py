@@ -80,3 +80,60 @@ def test_admission_respects_budget(gpu_lib):
     assert len(res) == 6 and srv.stats["peak_bytes"] <= budget
     assert srv.stats["evicted"] >= 2
     srv.close()
+
+
+def test_failures_stay_with_their_request(gpu_lib, tmp_path):
+    """Malformed, failing and late requests among good ones: each gets its own
+    status, its market is released, and the good requests' results are those
+    of a run without them."""
+    import json
+
+    from paper_2411_19214_gb300 import serve
+    good_specs = [(300, 700, 16), (800, 1700, 64), (513, 257, 8)]
+    good = _requests(serve, good_specs, seed=3)
+    bad = []
+    # non-finite factor values: refused by the library when the market is created
+    nan = _requests(serve, [(400, 500, 16)], seed=9)[0]
+    nan.F = nan.F.copy()
+    nan.F[7, 3] = np.nan
+    bad.append(("error", nan))
+    # inconsistent shapes: refused before admission
+    shp = _requests(serve, [(400, 500, 16)], seed=10)[0]
+    shp.K = shp.K[:, :8]
+    bad.append(("invalid", shp))
+    # a footprint larger than the whole budget (zero-stride views: no host memory)
+    N = M = 400_000
+    z = np.broadcast_to(np.float32(0.0), (N, 64))
+    big = serve.SolveRequest(rid=0, arrival=0.0, F=z, K=z, G=z, L=z, n=np.ones(N), m=np.ones(M), sigma=0.5)
+    bad.append(("invalid", big))
+    # a balanced market with popularity biases needs far more sweeps than its deadline allows
+    late = _requests(serve, [(20000, 20000, 32)], seed=11)[0]
+    late.deadline = 0.005
+    bad.append(("deadline", late))
+    reqs = good + [r for _, r in bad]
+    for i, r in enumerate(reqs):
+        r.rid = i
+    log = tmp_path / "serve.jsonl"
+    budget = 64 << 20
+    srv = serve.Server(hbm_budget_bytes=budget, tol=1e-6, max_sweeps=2000, k=10, keep_potentials=True,
+                       log_path=str(log))
+    res = srv.run(reqs, realtime=False)
+    srv.close()
+    assert [r.rid for r in res] == list(range(len(reqs)))
+    for (want, _), r in zip(bad, res[len(good):]):
+        assert r.status == want and r.error, (want, r.status, r.error)
+        assert r.topk_idx is None and not r.converged
+    assert srv.stats["invalid"] == 2 and srv.stats["errors"] == 1 and srv.stats["deadline"] == 1
+    assert srv.used == 0  # every market and reservation was released
+    clean = serve.Server(hbm_budget_bytes=budget, tol=1e-6, max_sweeps=2000, k=10, keep_potentials=True)
+    ref = clean.run(_requests(serve, good_specs, seed=3), realtime=False)
+    clean.close()
+    for a, b in zip(res[:len(good)], ref):
+        assert a.status == "ok" and b.status == "ok"
+        assert a.sweeps == b.sweeps
+        np.testing.assert_array_equal(a.log_u, b.log_u)
+        np.testing.assert_array_equal(a.log_v, b.log_v)
+        np.testing.assert_array_equal(a.topk_idx, b.topk_idx)
+    lines = [json.loads(x) for x in log.read_text().splitlines()]
+    assert sorted(x["rid"] for x in lines) == list(range(len(reqs)))
+    assert {x["rid"]: x["status"] for x in lines} == {r.rid: r.status for r in res}
