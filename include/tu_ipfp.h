@@ -334,6 +334,24 @@ const char* tu_batch_last_error(tu_batch_t b);
  * usable. */
 tu_status tu_selftest_wait_timeout(double limit_seconds, double* waited_seconds);
 
+/* Checked mode, a substitute for a memory sanitizer (no counterpart in the
+ * paper). With enable != 0, markets created afterwards surround every device
+ * buffer they own (factors, potentials, vectors, partials, staging and
+ * scratch, the dense kernel matrices) with 256-byte guard bands of the byte
+ * 0xA5, leaving the buffers themselves and every result unchanged. When such a
+ * buffer is freed (tu_market_destroy, or a scratch buffer that grows) the
+ * bands are read back: a band that changed means a kernel wrote outside the
+ * buffer, and the buffer is counted in tu_guard_violations. Checked mode is
+ * also on when the environment variable TU_CHECKED is "1" when the library is
+ * loaded. It costs one synchronisation of the market's stream per freed
+ * buffer. Batches' own small buffers are not guarded. Always TU_OK. */
+tu_status tu_set_checked_mode(int enable);
+
+/* Guard-band violations found since the library was loaded (0 in a correct
+ * build). If last != NULL and last_size > 0, a description of the latest
+ * violation (NUL-terminated, truncated to last_size) is written there. */
+int64_t tu_guard_violations(char* last, int64_t last_size);
+
 /* Free every resource of the market (safe on NULL). */
 void tu_market_destroy(tu_market_t mkt);
 

@@ -75,6 +75,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tu_market_relax_update": (I32, [V, D]),
         "tu_market_use_graphs": (I32, [V, I32]),
         "tu_selftest_wait_timeout": (I32, [D, ctypes.POINTER(D)]),
+        "tu_set_checked_mode": (I32, [I32]),
+        "tu_guard_violations": (I64, [ctypes.c_char_p, I64]),
         "tu_market_query": (I32, [V, ctypes.POINTER(I32), ctypes.POINTER(D), ctypes.POINTER(D),
                                   ctypes.POINTER(I64)]),
         "tu_market_footprint": (I64, [I64, I64, I64, I32]),
@@ -292,6 +294,19 @@ def tu_selftest_wait_timeout(limit_seconds: float):
     w = ctypes.c_double(float("nan"))
     st = load().tu_selftest_wait_timeout(float(limit_seconds), ctypes.byref(w))
     return st, w.value
+
+
+def tu_set_checked_mode(enable: bool) -> None:
+    """Guard bands around the device buffers of markets created afterwards,
+    verified when they are freed (also on with TU_CHECKED=1 at load)."""
+    load().tu_set_checked_mode(int(bool(enable)))
+
+
+def tu_guard_violations():
+    """(number of buffers found written outside their bounds, description of the latest)."""
+    buf = ctypes.create_string_buffer(256)
+    n = load().tu_guard_violations(buf, len(buf))
+    return int(n), buf.value.decode()
 
 
 def tu_market_use_graphs(h: int, enable: bool) -> None:

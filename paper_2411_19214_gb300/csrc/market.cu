@@ -1,13 +1,16 @@
 // market.cu -- the C ABI (include/tu_ipfp.h): market lifetime, argument
 // checking, host/device staging, the sweep loop with CUDA-graph replay, and the
 // convergence test of tu_ipfp_solve.
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "trace.h"
@@ -92,17 +95,99 @@ cudaMemPool_t market_pool(int device) {
   return g_pools[device];
 }
 
+// Checked mode: guard bands of kGuardByte around every market buffer,
+// verified when the buffer is freed (see tu_set_checked_mode). The band width
+// keeps each buffer 256-byte aligned inside its block.
+constexpr size_t kGuard = 256;
+constexpr unsigned char kGuardByte = 0xA5;
+
+bool checked_from_env() {
+  const char* v = std::getenv("TU_CHECKED");
+  return v != nullptr && std::strcmp(v, "1") == 0;
+}
+
+struct GuardedBlock {
+  void* base;
+  size_t bytes;  // the buffer's own size (between the bands)
+};
+std::atomic<bool> g_checked{checked_from_env()};
+std::mutex g_guard_mu;
+std::unordered_map<void*, GuardedBlock> g_guarded;  // buffer -> its block
+int64_t g_violations = 0;
+std::string g_last_violation;
+
+// Compare the two bands of a guarded buffer with the pattern (after the work
+// queued on `stream`); counts a violation when either changed.
+void verify_guards(void* p, const GuardedBlock& g, cudaStream_t stream) {
+  unsigned char band[2][kGuard];
+  cudaError_t e = cudaMemcpyAsync(band[0], g.base, kGuard, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(band[1], static_cast<char*>(g.base) + kGuard + g.bytes, kGuard, cudaMemcpyDeviceToHost,
+                        stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return;  // the market's own error path reports CUDA failures
+  }
+  for (int side = 0; side < 2; ++side) {
+    for (size_t i = 0; i < kGuard; ++i) {
+      if (band[side][i] != kGuardByte) {
+        char msg[200];
+        snprintf(msg, sizeof(msg), "buffer %p of %zu bytes: %s guard band changed at byte %zu", p, g.bytes,
+                 side == 0 ? "leading" : "trailing", i);
+        std::lock_guard<std::mutex> lk(g_guard_mu);
+        ++g_violations;
+        g_last_violation = msg;
+        return;
+      }
+    }
+  }
+}
+
 tu_status dev_alloc_bytes(tu_market* m, void** p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return TU_OK;
   cudaMemPool_t pool = market_pool(m->device);
   if (pool == nullptr) return fail(m, TU_ERR_CUDA, "device memory pool unavailable");
-  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, m->stream);
-  if (e != cudaSuccess) {
-    *p = nullptr;
-    return fail_cuda(m, e, "cudaMallocFromPoolAsync");
+  const bool guarded = g_checked.load();
+  void* base = nullptr;
+  cudaError_t e = cudaMallocFromPoolAsync(&base, guarded ? bytes + 2 * kGuard : bytes, pool, m->stream);
+  if (e != cudaSuccess) return fail_cuda(m, e, "cudaMallocFromPoolAsync");
+  if (!guarded) {
+    *p = base;
+    return TU_OK;
   }
+  e = cudaMemsetAsync(base, kGuardByte, kGuard, m->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(static_cast<char*>(base) + kGuard + bytes, kGuardByte, kGuard, m->stream);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(base, m->stream);
+    return fail_cuda(m, e, "guard bands");
+  }
+  *p = static_cast<char*>(base) + kGuard;
+  std::lock_guard<std::mutex> lk(g_guard_mu);
+  g_guarded[*p] = GuardedBlock{base, bytes};
   return TU_OK;
+}
+
+// Free a dev_alloc buffer in the order of the market's stream (guarded
+// buffers: after their bands were checked).
+void dev_free_bytes(tu_market* m, void* p) {
+  if (p == nullptr) return;
+  GuardedBlock g{nullptr, 0};
+  {
+    std::lock_guard<std::mutex> lk(g_guard_mu);
+    auto it = g_guarded.find(p);
+    if (it != g_guarded.end()) {
+      g = it->second;
+      g_guarded.erase(it);
+    }
+  }
+  if (g.base == nullptr) {
+    cudaFreeAsync(p, m->stream);
+    return;
+  }
+  verify_guards(p, g, m->stream);
+  cudaFreeAsync(g.base, m->stream);
 }
 
 template <typename T>
@@ -116,7 +201,7 @@ tu_status dev_alloc(tu_market* m, T** p, size_t count) {
 // Stream-ordered release of a dev_alloc block (after the market's queued work).
 template <typename T>
 void dev_free(tu_market* m, T*& p) {
-  if (p != nullptr) cudaFreeAsync(p, m->stream);
+  dev_free_bytes(m, const_cast<void*>(static_cast<const void*>(p)));
   p = nullptr;
 }
 
@@ -509,6 +594,21 @@ const char* tu_status_string(tu_status s) {
 
 const char* tu_market_last_error(tu_market_t m) { return m ? m->last_error.c_str() : ""; }
 
+tu_status tu_set_checked_mode(int enable) {
+  g_checked.store(enable != 0);
+  return TU_OK;
+}
+
+int64_t tu_guard_violations(char* last, int64_t last_size) {
+  std::lock_guard<std::mutex> lk(g_guard_mu);
+  if (last != nullptr && last_size > 0) {
+    const size_t n = g_last_violation.size() < (size_t)(last_size - 1) ? g_last_violation.size() : (size_t)(last_size - 1);
+    std::memcpy(last, g_last_violation.data(), n);
+    last[n] = '\0';
+  }
+  return g_violations;
+}
+
 tu_status tu_profile_enable(tu_market_t m, int enable) {
   TU_TRY(check_live(m));
   m->profiling = enable != 0;
@@ -542,8 +642,19 @@ void tu_market_destroy(tu_market_t m) {
   if (m->graph) cudaGraphExecDestroy(m->graph);
   side_free(m, m->X);
   side_free(m, m->Y);
-  if (m->Ahat) cudaFree(m->Ahat);
-  if (m->AhatT) cudaFree(m->AhatT);
+  for (float** a : {&m->Ahat, &m->AhatT}) {
+    bool guarded;
+    {
+      std::lock_guard<std::mutex> lk(g_guard_mu);
+      guarded = g_guarded.count(*a) != 0;
+    }
+    if (guarded) {
+      dev_free(m, *a);
+    } else if (*a != nullptr) {
+      cudaFree(*a);
+      *a = nullptr;
+    }
+  }
   dev_free(m, m->partials);
   dev_free(m, m->mpartials);
   dev_free(m, m->results);
@@ -637,9 +748,14 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
   if (D.path == TU_PATH_DENSE) {
     m->ldA = round_up(D.M, 4);
     m->ldN = round_up(D.N, 4);
-    cudaError_t e = cudaMalloc(&m->Ahat, (size_t)m->N * m->ldA * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&m->AhatT, (size_t)m->M * m->ldN * sizeof(float));
-    if (e != cudaSuccess) return bail(fail_cuda(m, e, "cudaMalloc(A-hat)"));
+    if (g_checked.load()) {  // checked mode: guarded like the other buffers
+      if ((st = dev_alloc(m, &m->Ahat, (size_t)m->N * m->ldA)) != TU_OK) return bail(st);
+      if ((st = dev_alloc(m, &m->AhatT, (size_t)m->M * m->ldN)) != TU_OK) return bail(st);
+    } else {
+      cudaError_t e = cudaMalloc(&m->Ahat, (size_t)m->N * m->ldA * sizeof(float));
+      if (e == cudaSuccess) e = cudaMalloc(&m->AhatT, (size_t)m->M * m->ldN * sizeof(float));
+      if (e != cudaSuccess) return bail(fail_cuda(m, e, "cudaMalloc(A-hat)"));
+    }
   }
   // (allocated after the dense matrices: placing this small allocation before
   // them measurably slowed the dense row stream)

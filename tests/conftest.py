@@ -24,3 +24,20 @@ def gpu_lib():
     tb.build()
     tu.load()
     return tu
+
+
+@pytest.fixture(autouse=True)
+def _guard_bands(request):
+    """After every GPU test: no market buffer was written outside its bounds.
+    The library counts guard-band violations of buffers it frees; the bands
+    exist when checked mode is on (TU_CHECKED=1 when the library is loaded),
+    so `TU_CHECKED=1 pytest -m gpu` runs the whole suite with them."""
+    if request.node.get_closest_marker("gpu") is None:
+        yield
+        return
+    import paper_2411_19214_gb300 as tu
+    before = tu.tu_guard_violations()[0] if tu._lib is not None else 0
+    yield
+    if tu._lib is not None:
+        n, last = tu.tu_guard_violations()
+        assert n == before, f"{n - before} buffer(s) written outside their bounds; latest: {last}"
