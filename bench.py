@@ -9,7 +9,7 @@ tcgen05 half-sweep, FP64 partial reduction), with the residual of the entering
 state folded into the X half-sweep.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload fused|dense|paper|batched|ranking|serving]
+                  [--workload fused|dense|paper|batched|ranking|serving|dims]
 
 N > 1 (under torchrun): every rank solves its own market of the same shape
 (independent markets, weak scaling, no collective on the data path).
@@ -546,6 +546,73 @@ def run_reference_paper(args):
               flush=True)
 
 
+def run_dims(args):
+    """The paper's dimension sweep (Sec. 4.2: N = M = 1e4, time and memory
+    against the factor dimension), also at 1e5 where the GPU is full: the
+    Sec. 4.2 recipe (U[0, 1/sqrt(D)] factors, n = m = 1, beta = 1) for D in
+    {8, 16, 32, 50, 64}; one JSON line per (N, D) with the time per sweep
+    (`--steps` sweeps replayed as a graph after `--warmup`), the pair rate and
+    the market's device footprint. D = 128 is outside the fused path (2D is
+    the 128-wide MMA inner dimension at most) and is reported as such."""
+    import torch
+
+    import paper_2411_19214_gb300 as tu
+    from synth import paper_shaped_market
+    tu.load()
+    stream = torch.cuda.Stream()
+    for N in (10_000, 100_000):
+        for D in (8, 16, 32, 50, 64):
+            mk = paper_shaped_market(N, D=D)
+            mkt = tu.from_synth(mk, path="fused", stream=stream)
+            try:
+                mkt.sweep(args.warmup)
+                mkt.sweep(args.steps)  # graph capture
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                mkt.sweep(args.steps)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / args.steps
+            finally:
+                mkt.close()
+            kp = ((2 * D + 63) // 64) * 64
+            print(json.dumps({"workload": "dimension sweep (Sec. 4.2 recipe)", "N": N, "M": N, "D": D,
+                              "mma_inner_dim": kp, "ms_per_sweep": ms, "sweeps": args.steps,
+                              "gpair_evals_per_s": 2.0 * N * N / ms / 1e6,
+                              "device_bytes": tu.tu_market_footprint(N, N, D, "fused"), "dtype": "bf16"}),
+                  flush=True)
+        print(json.dumps({"workload": "dimension sweep (Sec. 4.2 recipe)", "N": N, "M": N, "D": 128,
+                          "unsupported": "2D = 256 exceeds the fused path's MMA inner dimension of 128"}),
+              flush=True)
+
+
+def run_reference_dims(args):
+    """--impl reference for the dimension sweep: the float64 oracle's time per
+    sweep at N = M = 1e4 for the same D, from a half-sweep of sampled users on
+    every host core, extrapolated to 2 N^2 pair evaluations (rank 0 only)."""
+    from synth import paper_shaped_market
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    N = 10_000
+    for D in (8, 16, 32, 50, 64):
+        mk = paper_shaped_market(N, D=D)
+        pool = OraclePool(mk)
+        try:
+            rpc = pool.calibrate(2.0)
+            t = pool.run(rpc)
+        finally:
+            pool.close()
+        pair_rate = pool.cores * min(rpc, N) * N / t
+        ms = 2.0 * N * N / pair_rate * 1e3
+        print(json.dumps({"impl": "reference", "workload": "dimension sweep (Sec. 4.2 recipe)", "N": N, "M": N,
+                          "D": D, "ms_per_sweep": ms, "gpair_evals_per_s": pair_rate / 1e9, "dtype": "f64",
+                          "cpu_baseline": {"value": ms, "unit": "ms/sweep", "cores": pool.cores, "kind": "oracle",
+                                           "sample": f"float64 oracle X half-sweep of {pool.cores} x {min(rpc, N)} "
+                                                     f"sampled users against all {N} partners, extrapolated"}}),
+              flush=True)
+
+
 def run_batched(args):
     """Many independent markets in one persistent launch per half-sweep: 512
     markets, per-side sizes log-uniform in [100, 50,000], d = 32 bf16 factors
@@ -942,7 +1009,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["fused", "dense", "paper", "batched", "ranking", "serving"], default="fused",
+    ap.add_argument("--workload", choices=["fused", "dense", "paper", "batched", "ranking", "serving", "dims"],
+                    default="fused",
                     help="paper: the Sec. 4.2 shapes (N = M = 1e2..1e6, D = 50, U[0, 1/sqrt(D)], beta = 1), "
                          "time per sweep, one JSON line per size; batched: 512 independent markets in one "
                          "persistent launch per half-sweep")
@@ -971,6 +1039,12 @@ def main():
         return
     if args.workload == "serving" and args.impl == "ours":
         run_serving(args)
+        return
+    if args.workload == "dims" and args.impl == "ours":
+        run_dims(args)
+        return
+    if args.impl == "reference" and args.workload == "dims":
+        run_reference_dims(args)
         return
     if args.impl == "reference" and args.workload in ("ranking", "serving"):
         # latency and stopping-rule workloads of the GPU library; the float64

@@ -57,7 +57,7 @@ typedef enum {
   TU_ERR_NOT_CONVERGED = 4, /* tu_ipfp_solve hit max_iter; potentials are still valid */
   TU_ERR_NONFINITE = 5,     /* an input or a computed potential is NaN or infinite */
   TU_ERR_TIMEOUT = 6,       /* a device-side wait ran out of its time limit */
-  TU_ERR_UNSUPPORTED = 7    /* valid request this build cannot serve (e.g. d > 64 on the fused path) */
+  TU_ERR_UNSUPPORTED = 7    /* valid request outside what the library supports (e.g. d > 64 on the fused path) */
 } tu_status;
 
 enum { TU_DTYPE_BF16 = 0, TU_DTYPE_FP32 = 1, TU_DTYPE_FP8E4M3 = 2 };

@@ -70,3 +70,11 @@ def test_reference_arm_only_rank0_prints():
 def test_warmup_minimum_is_enforced():
     r = _bench("--impl", "reference", "--warmup", "2", timeout=120)
     assert r.returncode != 0 and "warmup" in (r.stderr + r.stdout)
+
+
+def test_reference_arm_dimension_sweep():
+    lines = _last_json(_bench("--impl", "reference", "--workload", "dims"))
+    assert [d["D"] for d in lines] == [8, 16, 32, 50, 64]
+    for d in lines:
+        assert d["impl"] == "reference" and d["N"] == d["M"] == 10_000 and d["ms_per_sweep"] > 0
+        assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
