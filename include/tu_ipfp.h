@@ -104,7 +104,9 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out);
 
 /* Replace F, K, G, L (same shapes and dtype as at creation; host or device).
  * Potentials are kept, so the next solve can be warm-started. Dense markets
- * rebuild A-hat. */
+ * rebuild A-hat. The same checks as tu_market_create apply (TU_ERR_NONFINITE,
+ * TU_ERR_UNSUPPORTED); after such a refusal the market's factors are
+ * undefined until the next successful update (its potentials are kept). */
 tu_status tu_market_update_factors(tu_market_t mkt, const void* F, const void* K, const void* G,
                                    const void* L);
 

@@ -49,8 +49,11 @@ __global__ void k_max_abs(const float* __restrict__ A, const float* __restrict__
                           unsigned int* __restrict__ out) {
   __shared__ float red[kThreads / 32];
   float best = 0.0f;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
-    best = fmaxf(best, fmaxf(fabsf(A[i]), fabsf(B[i])));
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    const float a = fmaxf(fabsf(A[i]), fabsf(B[i]));
+    // fmaxf drops a NaN operand: a NaN entry counts as +inf, so the host's finiteness check sees it
+    best = (isnan(A[i]) || isnan(B[i])) ? INFINITY : fmaxf(best, a);
+  }
   for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
   if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = best;
   __syncthreads();
@@ -128,7 +131,9 @@ __global__ void k_row_norm_max(const float* __restrict__ f32, const __nv_bfloat1
       s = fmaf(v, v, s);
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    best = fmaxf(best, sqrtf(s));
+    const float nrm = sqrtf(s);
+    // fmaxf drops a NaN operand: a row with a NaN entry counts as an infinite norm
+    best = isnan(nrm) ? INFINITY : fmaxf(best, nrm);
   }
   if (lane == 0) red[warp] = best;
   __syncthreads();
