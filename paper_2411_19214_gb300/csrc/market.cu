@@ -766,20 +766,32 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
     return bail(fail_cuda(m, cudaGetLastError(), "omega"));
   if ((st = upload_masses(m, m->X, D.n)) != TU_OK) return bail(st);
   if ((st = upload_masses(m, m->Y, D.m)) != TU_OK) return bail(st);
-  // biases -> b / (2 sigma); potentials start at u = v = 1
+  // biases -> b / (2 sigma); potentials start at u = v = 1. A non-finite
+  // bias is refused (TU_ERR_NONFINITE) like a non-finite factor.
   {
     const size_t bbytes = (size_t)(D.N > D.M ? D.N : D.M) * sizeof(float);
     if ((st = ensure_staging(m, bbytes)) != TU_OK) return bail(st);
-    const void* bdev = nullptr;
-    if (D.bias_x && (st = device_view(m, D.bias_x, (size_t)D.N * 4, 0, &bdev)) != TU_OK) return bail(st);
-    if (launch_init_side(m, m->X, static_cast<const float*>(bdev), D.bias_x != nullptr) != cudaSuccess)
-      return bail(fail_cuda(m, cudaGetLastError(), "init side X"));
-    if (cudaStreamSynchronize(m->stream) != cudaSuccess) return bail(TU_ERR_CUDA);
-    bdev = nullptr;
-    if (D.bias_y && (st = device_view(m, D.bias_y, (size_t)D.M * 4, 0, &bdev)) != TU_OK) return bail(st);
-    if (launch_init_side(m, m->Y, static_cast<const float*>(bdev), D.bias_y != nullptr) != cudaSuccess)
-      return bail(fail_cuda(m, cudaGetLastError(), "init side Y"));
-    if (cudaStreamSynchronize(m->stream) != cudaSuccess) return bail(TU_ERR_CUDA);
+    float* bmax = nullptr;
+    if ((D.bias_x || D.bias_y) && (st = dev_alloc(m, &bmax, 1)) != TU_OK) return bail(st);
+    auto init = [&](Side& s, const float* bias, int64_t rows, const char* what) -> tu_status {
+      const void* bdev = nullptr;
+      if (bias) {
+        TU_TRY(device_view(m, bias, (size_t)rows * 4, 0, &bdev));
+        float hm = 0.0f;
+        const float* b = static_cast<const float*>(bdev);
+        TU_CK(m, launch_max_abs(m, b, b, rows, bmax));
+        TU_CK(m, cudaMemcpyAsync(&hm, bmax, sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+        TU_CK(m, cudaStreamSynchronize(m->stream));
+        if (!std::isfinite(hm)) return fail(m, TU_ERR_NONFINITE, std::string(what) + " contains NaN or Inf");
+      }
+      TU_CK(m, launch_init_side(m, s, static_cast<const float*>(bdev), bias != nullptr));
+      TU_CK(m, cudaStreamSynchronize(m->stream));  // the staging buffer is reused
+      return TU_OK;
+    };
+    st = init(m->X, D.bias_x, D.N, "bias_x");
+    if (st == TU_OK) st = init(m->Y, D.bias_y, D.M, "bias_y");
+    dev_free(m, bmax);
+    if (st != TU_OK) return bail(st);
   }
   if ((st = load_factors(m, D.F, D.K, D.G, D.L)) != TU_OK) {
     // keep the message for the caller by returning it through a status only

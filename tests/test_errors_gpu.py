@@ -140,6 +140,11 @@ def test_create_errors(gpu_lib):
     F = mk.F.copy()
     F[0, 0] = np.inf
     assert _status(tu.tu_market_create, F, mk.K, mk.G, mk.L, mk.n, mk.m, mk.sigma) == tu.TU_ERR_NONFINITE
+    for name, bad in (("bias_x", np.r_[mk.bias_x[:-1], np.nan]), ("bias_y", np.r_[np.inf, mk.bias_y[1:]])):
+        kw = dict(bias_x=mk.bias_x, bias_y=mk.bias_y)
+        kw[name] = bad.astype(np.float32)
+        st = _status(lambda: tu.tu_market_create(mk.F, mk.K, mk.G, mk.L, mk.n, mk.m, mk.sigma, **kw))
+        assert st == tu.TU_ERR_NONFINITE, name
     # max|a| max|b| / (2 sigma) far above 40: outside the FP32 exponent range of the single shift
     big = make_market(300, 200, 16, sigma=0.5, seed=8, factor_scale=60.0, dtype="fp32")
     st = _status(tu.tu_market_create, big.F, big.K, big.G, big.L, big.n, big.m, big.sigma)
