@@ -6,28 +6,17 @@
 //
 // HBM layout: A-hat (N x ldA, ldA = M rounded up to 4) and its transpose
 // (M x ldN). With both resident, the v step (s = A^T u / 2) is the same row
-// stream as the u step (s = A v / 2): one warp per row, 128-bit coalesced
-// loads with kRowDepth loads in flight per lane, a warp-shuffle reduction and
-// the closed-form update in the epilogue. Deterministic, no partial sums; the
-// price is 2 * N * M * 4 bytes of HBM instead of N * M * 4.
+// stream as the u step (s = A v / 2): each row is streamed once through a
+// shared-memory ring by bulk copies, reduced in a fixed order and updated in
+// closed form (k_dense_rowpass). Deterministic; the price is 2 * N * M * 4
+// bytes of HBM instead of N * M * 4.
 #include "tu_internal.cuh"
 
 namespace tu {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-constexpr int kRowDepth = 8;  // 16-byte loads in flight per lane in the row pass
-
-// Streaming 128-bit load that does not allocate in L1 (A-hat is read once per pass).
-__device__ __forceinline__ float4 ld_stream(const float4* p) {
-  float4 v;
-  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "l"(p));
-  return v;
-}
+constexpr int kThreads = 256;  // the A-hat build
 
 // A-hat and its transpose from the packed FP32 factors (setup, once per factor
 // update). 64 x 64 output tile per CTA; the transposed tile is staged in
@@ -94,38 +83,6 @@ struct PartialAcc {
   }
 };
 
-// Block-level reduction of PartialAcc; thread 0 writes partials[4 * blockIdx.x ..].
-__device__ void block_write_partials(PartialAcc a, double* __restrict__ partials) {
-  __shared__ double s[4][kWarps];
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  for (int o = 16; o > 0; o >>= 1) {
-    a.rmax = fmax(a.rmax, __shfl_xor_sync(0xffffffffu, a.rmax, o));
-    a.rsum += __shfl_xor_sync(0xffffffffu, a.rsum, o);
-    a.sq += __shfl_xor_sync(0xffffffffu, a.sq, o);
-    a.nf += __shfl_xor_sync(0xffffffffu, a.nf, o);
-  }
-  if (lane == 0) {
-    s[0][warp] = a.rmax;
-    s[1][warp] = a.rsum;
-    s[2][warp] = a.sq;
-    s[3][warp] = a.nf;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
-    for (int w = 0; w < kWarps; ++w) {
-      r0 = fmax(r0, s[0][w]);
-      r1 += s[1][w];
-      r2 += s[2][w];
-      r3 += s[3][w];
-    }
-    partials[4 * blockIdx.x + 0] = r0;
-    partials[4 * blockIdx.x + 1] = r1;
-    partials[4 * blockIdx.x + 2] = r2;
-    partials[4 * blockIdx.x + 3] = r3;
-  }
-}
-
 // One half-sweep over a row-major matrix A (rows x ld): for every row r,
 // s_r = 1/2 exp(b_r / 2 sigma) exp(shift) sum_c A[r][c] w_c with
 // w_c = exp(ell_c - shift) of the partner side (zero-padded to ld), then the
@@ -133,124 +90,234 @@ __device__ void block_write_partials(PartialAcc a, double* __restrict__ partials
 // over-relaxed by the device scalar *omega_p (markets with relaxation
 // enabled); the plain instantiation is Eq. iteration exactly.
 //
-// Work split: the CTA's warps form groups of `wpr` warps; a group streams one
-// row, each warp a contiguous 1/wpr of its columns, and rows go to CTAs and
-// groups round-robin. With wpr = 8 a CTA streams one row at a time, so the
-// kernel is balanced to one row per CTA (about 1 % here) rather than to one
-// row per warp (a warp owning 4 or 5 of 20,000 rows left a 20 % tail). Warp
-// partial sums are parked in shared memory; every kSlots rows the 32 lanes of
-// warp 0 combine them in a fixed order and run the closed-form updates in
-// parallel. Four CTAs per SM (64 registers, a few bytes of spill outside the
-// streaming loop) measured 12 % faster than three without spill: occupancy
-// sets the bytes in flight.
-constexpr int kSlots = 32;
+// Roles of a CTA (rows blockIdx.x, blockIdx.x + gridDim.x, ... in turn):
+//   producer warp   one thread streams each row in kChunk-float pieces into a
+//                   kStages ring in shared memory with 1D bulk copies
+//                   (completion counted on the stage's mbarrier), so the
+//                   bytes in flight do not depend on registers or on what
+//                   the other warps are doing;
+//   consumer warps  every warp takes strided float4s of each piece against
+//                   the partner vector, releases the stage, and parks its
+//                   share of the row sum; a block of kSlots rows is handed
+//                   over once complete (double-buffered);
+//   update warp     sums a block's parked shares in a fixed order and runs
+//                   the kSlots closed-form updates in parallel (one per lane),
+//                   off the stream's critical path, then frees the buffer.
+// Every wait is bounded and sets the market's error word when it runs out;
+// the producer then waits for its copies in flight before the CTA exits.
+constexpr int kStages = 4;
+constexpr int kChunk = 4096;  // floats per stage (16 KB)
+constexpr int kConsumerWarps = 8;
+constexpr int kUpdateWarp = kConsumerWarps;
+constexpr int kProducerWarp = kConsumerWarps + 1;
+constexpr int kPassThreads = (kConsumerWarps + 2) * 32;
+constexpr int kSlots = 32;  // rows per block of updates: one per lane of the update warp
+
+struct PassSmem {
+  float ring[kStages][kChunk];
+  float part[2][kSlots][kConsumerWarps];
+  uint64_t full[kStages];   // a piece has landed (transaction count)
+  uint64_t empty[kStages];  // every consumer warp is done with the stage
+  uint64_t done[2];         // a block's row shares are parked
+  uint64_t freed[2];        // the update warp has read the block
+  int abort;
+};
+
+__device__ __forceinline__ void bulk_copy(void* smem_dst, const void* gsrc, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(gsrc)), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void pass_abort(int* err, volatile int* flag) {
+  atomicCAS(err, kErrNone, kErrTimeout);
+  *flag = 1;
+}
 
 template <bool RELAX>
-__global__ void __launch_bounds__(kThreads, 4) k_dense_rowpass(
-    const float* __restrict__ A, int64_t ld, int64_t rows, int wpr, const float* __restrict__ w,
+__global__ void __launch_bounds__(kPassThreads) k_dense_rowpass(
+    const float* __restrict__ A, int64_t ld, int64_t rows, const float* __restrict__ w,
     const double* __restrict__ lmax_partner, const float* __restrict__ b2s, const double* __restrict__ mass,
     double* __restrict__ log_u, double* __restrict__ ell, double* __restrict__ partials, int residual,
-    int update, const double* __restrict__ omega_p) {
-  __shared__ float part[kSlots][kWarps];
+    int update, const double* __restrict__ omega_p, int* __restrict__ err) {
+  extern __shared__ __align__(128) uint8_t pass_smem_raw[];
+  PassSmem& S = *reinterpret_cast<PassSmem*>(pass_smem_raw);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  // plain: the shift is loaded up front, overlapped with the stream (a load at
-  // update time would lengthen every CTA's tail); relaxed: loaded at update
-  // time with omega, so that neither is live across the streaming loop
+  volatile int* abort_flag = &S.abort;
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < kStages; ++t) {
+      mbar_init(&S.full[t], 1);
+      mbar_init(&S.empty[t], kConsumerWarps);
+    }
+    for (int t = 0; t < 2; ++t) {
+      mbar_init(&S.done[t], kConsumerWarps);
+      mbar_init(&S.freed[t], 1);
+    }
+    S.abort = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const int64_t G = gridDim.x;
+  const int64_t nchunks = (ld + kChunk - 1) / kChunk;
+  // rows of this CTA (the grid never exceeds rows)
+  const int64_t nrows = (rows - blockIdx.x + G - 1) / G;
+
+  if (warp == kProducerWarp) {
+    if (lane == 0) {
+      int t = 0;
+      uint32_t ph = 0, issued = 0, issued_ph = 0;
+      bool ok = true;
+      for (int64_t k = 0; k < nrows && ok; ++k) {
+        const float* arow = A + (blockIdx.x + k * G) * ld;
+        for (int64_t c = 0; c < nchunks; ++c) {
+          if (!mbar_wait(&S.empty[t], ph ^ 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          const int64_t c0 = c * kChunk;
+          const uint32_t n = (uint32_t)(ld - c0 < kChunk ? ld - c0 : kChunk);
+          mbar_arrive_expect_tx(&S.full[t], n * 4u);
+          bulk_copy(S.ring[t], arow + c0, n * 4u, &S.full[t]);
+          issued |= 1u << t;
+          issued_ph = (issued_ph & ~(1u << t)) | (ph << t);
+          if (++t == kStages) {
+            t = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+      if (!ok && !*abort_flag) pass_abort(err, abort_flag);
+      // copies in flight complete before the CTA's shared memory is released
+      for (int u = 0; u < kStages; ++u)
+        if (issued & (1u << u)) mbar_wait_drain(&S.full[u], (issued_ph >> u) & 1u, 100000000ull);
+    }
+    return;
+  }
+
+  if (warp < kConsumerWarps) {
+    const float4* w4 = reinterpret_cast<const float4*>(w);
+    int t = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int64_t k = 0; k < nrows && ok; ++k) {
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      for (int64_t c = 0; c < nchunks; ++c) {
+        const bool got = mbar_wait(&S.full[t], ph, abort_flag);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        const int64_t c0 = c * kChunk;
+        const int nq = (int)((ld - c0 < kChunk ? ld - c0 : kChunk) / 4);
+        const float4* r4 = reinterpret_cast<const float4*>(S.ring[t]);
+        const float4* g4 = w4 + c0 / 4;
+        for (int q = warp * 32 + lane; q < nq; q += kConsumerWarps * 32) {
+          const float4 x = r4[q];
+          const float4 y = __ldg(g4 + q);
+          a0 = fmaf(x.x, y.x, a0);
+          a1 = fmaf(x.y, y.y, a1);
+          a2 = fmaf(x.z, y.z, a2);
+          a3 = fmaf(x.w, y.w, a3);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.empty[t]);
+        if (++t == kStages) {
+          t = 0;
+          ph ^= 1u;
+        }
+      }
+      if (!ok) break;
+      float sum = (a0 + a1) + (a2 + a3);
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+      const int slot = (int)(k % kSlots);
+      const int64_t blk = k / kSlots;
+      const int pb = (int)(blk & 1);
+      if (slot == 0 && blk >= 2) {
+        // the update warp has read this buffer's previous block
+        const bool fr = mbar_wait(&S.freed[pb], (uint32_t)(((blk >> 1) - 1) & 1), abort_flag);
+        if (!__all_sync(0xffffffffu, fr)) {
+          ok = false;
+          break;
+        }
+      }
+      if (lane == 0) {
+        S.part[pb][slot][warp] = sum;
+        if (slot == kSlots - 1 || k == nrows - 1) mbar_arrive(&S.done[pb]);
+      }
+    }
+    if (!ok && !*abort_flag) pass_abort(err, abort_flag);
+    return;
+  }
+
+  if (warp != kUpdateWarp) return;
+  PartialAcc acc;
   double shift = 0.0;
   if constexpr (!RELAX) shift = *lmax_partner;
-  const int groups = kWarps / wpr;          // rows in flight per CTA
-  const int grp = warp / wpr, wi = warp % wpr;
-  // column indices in float4 units fit in 32 bits (ld <= 2^31 floats)
-  const int n4 = (int)(ld / 4);
-  const int seg = (n4 + wpr - 1) / wpr;
-  const int c0 = wi * seg;
-  const int c1 = c0 + seg < n4 ? c0 + seg : n4;
-  const float4* w4 = reinterpret_cast<const float4*>(w);
-  PartialAcc acc;
-  int nslot = 0;
-  int64_t first = (int64_t)blockIdx.x * groups;  // first row of the parked block
-  auto flush = [&]() {
-    __syncthreads();
-    if (warp == 0 && lane < nslot) {
-      // slot i holds row first + (i / groups) * gridDim.x * groups + i % groups
-      const int64_t row = first + (int64_t)(lane / groups) * gridDim.x * groups + lane % groups;
-      if (row < rows) {
-        float sum = 0.0f;
-        for (int k = 0; k < wpr; ++k) sum += part[lane][(lane % groups) * wpr + k];
-        double omega = 1.0;
-        if constexpr (RELAX) {
-          shift = __ldg(lmax_partner);
-          omega = (update && omega_p != nullptr) ? __ldg(omega_p) : 1.0;
-        }
-        const RowResult rr = row_update((double)logf(sum), shift, b2s ? b2s[row] : 0.0f, mass[row], log_u[row],
-                                        residual != 0, omega);
-        if (update) {
-          log_u[row] = rr.log_u;
-          ell[row] = rr.ell;
-        }
-        acc.add(rr);
-      }
+  // a block's shares arrive after kSlots rows are streamed: allow for 1 GB/s per CTA
+  const uint64_t block_limit = kWaitLimitNs + (uint64_t)kSlots * (uint64_t)ld * 4ull;
+  bool ok = true;
+  for (int64_t blk = 0; blk * kSlots < nrows; ++blk) {
+    const int pb = (int)(blk & 1);
+    const bool got = mbar_wait(&S.done[pb], (uint32_t)((blk >> 1) & 1), abort_flag, block_limit);
+    if (!__all_sync(0xffffffffu, got)) {
+      ok = false;
+      break;
     }
-    __syncthreads();
-    nslot = 0;
-  };
-  for (int64_t rbase = (int64_t)blockIdx.x * groups; rbase < rows; rbase += (int64_t)gridDim.x * groups) {
-    if (nslot == 0) first = rbase;
-    const int64_t row = rbase + grp;
-    if (row < rows) {
-      const float4* a4 = reinterpret_cast<const float4*>(A + row * ld);
-      float s4[4] = {0.f, 0.f, 0.f, 0.f};
-      // every iteration keeps kRowDepth loads in flight, the last one predicated
-      for (int base = c0; base < c1; base += 32 * kRowDepth) {
-        float4 a[kRowDepth], ww[kRowDepth];
-#pragma unroll
-        for (int u = 0; u < kRowDepth; ++u) {
-          const int j = base + lane + 32 * u;
-          a[u] = j < c1 ? ld_stream(a4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < kRowDepth; ++u) {
-          const int j = base + lane + 32 * u;
-          ww[u] = j < c1 ? __ldg(w4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < kRowDepth; ++u)
-          s4[u & 3] =
-              fmaf(a[u].x, ww[u].x, fmaf(a[u].y, ww[u].y, fmaf(a[u].z, ww[u].z, fmaf(a[u].w, ww[u].w, s4[u & 3]))));
+    const int64_t k = blk * kSlots + lane;
+    if (k < nrows) {
+      const int64_t row = blockIdx.x + k * G;
+      float sum = 0.0f;
+      for (int cw = 0; cw < kConsumerWarps; ++cw) sum += S.part[pb][lane][cw];
+      double omega = 1.0;
+      if constexpr (RELAX) {
+        shift = __ldg(lmax_partner);
+        omega = (update && omega_p != nullptr) ? __ldg(omega_p) : 1.0;
       }
-      float s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) part[nslot + grp][warp % kWarps] = s;
+      const RowResult rr = row_update((double)logf(sum), shift, b2s ? b2s[row] : 0.0f, mass[row], log_u[row],
+                                      residual != 0, omega);
+      if (update) {
+        log_u[row] = rr.log_u;
+        ell[row] = rr.ell;
+      }
+      acc.add(rr);
     }
-    nslot += groups;
-    if (nslot == kSlots) flush();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&S.freed[pb]);
   }
-  if (nslot > 0) flush();
-  block_write_partials(acc, partials);
+  if (!ok && !*abort_flag) pass_abort(err, abort_flag);
+  // this warp holds every partial of the CTA
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.rmax = fmax(acc.rmax, __shfl_xor_sync(0xffffffffu, acc.rmax, o));
+    acc.rsum += __shfl_xor_sync(0xffffffffu, acc.rsum, o);
+    acc.sq += __shfl_xor_sync(0xffffffffu, acc.sq, o);
+    acc.nf += __shfl_xor_sync(0xffffffffu, acc.nf, o);
+  }
+  if (lane == 0) {
+    partials[4 * blockIdx.x + 0] = acc.rmax;
+    partials[4 * blockIdx.x + 1] = acc.rsum;
+    partials[4 * blockIdx.x + 2] = acc.sq;
+    partials[4 * blockIdx.x + 3] = acc.nf;
+  }
 }
 
-// Warps per row: as many as keep every lane of a warp busy for at least one
-// full kRowDepth iteration (8, 4, 2 or 1).
-int warps_per_row(int64_t ld) {
-  const int64_t n4 = ld / 4;
-  int wpr = kWarps;
-  while (wpr > 1 && n4 / wpr < 32 * kRowDepth) wpr /= 2;
-  return wpr;
-}
-
-int rowpass_grid(tu_market* m, int64_t rows, int64_t ld) {
+// CTAs of a pass: as many as fit on the device at once (the ring's shared
+// memory allows a few per SM), at most one per row.
+int rowpass_grid(tu_market* m, int64_t rows) {
   static int per_sm = 0;
   if (per_sm == 0) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dense_rowpass<false>, kThreads, 0) != cudaSuccess ||
-        b < 1)
-      b = 2;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dense_rowpass<false>, kPassThreads,
+                                                      sizeof(PassSmem)) != cudaSuccess ||
+        b < 1) {
+      cudaGetLastError();
+      b = 1;
+    }
     per_sm = b;
   }
-  int64_t g = (int64_t)m->num_sms * per_sm;  // exactly one resident wave, grid-stride over rows
-  const int64_t groups = kWarps / warps_per_row(ld);
-  const int64_t need = (rows + groups - 1) / groups;
-  if (g > need) g = need;
+  int64_t g = (int64_t)m->num_sms * per_sm;
+  if (g > rows) g = rows;
   if (g > kMaxPartials) g = kMaxPartials;
   return (int)(g < 1 ? 1 : g);
 }
@@ -258,6 +325,14 @@ int rowpass_grid(tu_market* m, int64_t rows, int64_t ld) {
 }  // namespace
 
 cudaError_t launch_dense_build(tu_market* m) {
+  // the row pass's ring exceeds the default 48 KB of dynamic shared memory
+  // (set here, at creation and factor updates, never inside a graph capture)
+  cudaError_t e = cudaFuncSetAttribute(k_dense_rowpass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(PassSmem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_dense_rowpass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(PassSmem));
+  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)((m->M + 63) / 64), (unsigned)((m->N + 63) / 64));
   k_dense_build<<<grid, kThreads, 0, m->stream>>>(m->X.fac32, m->Y.fac32, m->N, m->M, m->kp,
                                                   (float)(0.5 / m->sigma), m->Ahat, m->ldA, m->AhatT, m->ldN);
@@ -265,19 +340,21 @@ cudaError_t launch_dense_build(tu_market* m) {
 }
 
 cudaError_t launch_dense_rowpass(tu_market* m, int residual, int update, int* nparts_out) {
-  const int g = rowpass_grid(m, m->N, m->ldA);
+  const int g = rowpass_grid(m, m->N);
   auto kern = m->omega_cfg != 1.0 ? k_dense_rowpass<true> : k_dense_rowpass<false>;
-  kern<<<g, kThreads, 0, m->stream>>>(m->Ahat, m->ldA, m->N, warps_per_row(m->ldA), m->Y.pvec, m->Y.lmax, m->X.b2s,
-                                      m->X.mass, m->X.log_u, m->X.ell, m->partials, residual, update, m->omega_dev);
+  kern<<<g, kPassThreads, sizeof(PassSmem), m->stream>>>(m->Ahat, m->ldA, m->N, m->Y.pvec, m->Y.lmax, m->X.b2s,
+                                                         m->X.mass, m->X.log_u, m->X.ell, m->partials, residual,
+                                                         update, m->omega_dev, m->err_dev);
   *nparts_out = g;
   return cudaGetLastError();
 }
 
 cudaError_t launch_dense_colpass(tu_market* m, int update, int* nparts_out) {
-  const int g = rowpass_grid(m, m->M, m->ldN);
+  const int g = rowpass_grid(m, m->M);
   auto kern = m->omega_cfg != 1.0 ? k_dense_rowpass<true> : k_dense_rowpass<false>;
-  kern<<<g, kThreads, 0, m->stream>>>(m->AhatT, m->ldN, m->M, warps_per_row(m->ldN), m->X.pvec, m->X.lmax, m->Y.b2s,
-                                      m->Y.mass, m->Y.log_u, m->Y.ell, m->partials, 0, update, m->omega_dev);
+  kern<<<g, kPassThreads, sizeof(PassSmem), m->stream>>>(m->AhatT, m->ldN, m->M, m->X.pvec, m->X.lmax, m->Y.b2s,
+                                                         m->Y.mass, m->Y.log_u, m->Y.ell, m->partials, 0, update,
+                                                         m->omega_dev, m->err_dev);
   *nparts_out = g;
   return cudaGetLastError();
 }
