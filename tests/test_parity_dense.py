@@ -114,3 +114,31 @@ def test_full_size_job_market_sampled(gpu_lib):
         np.testing.assert_allclose(lv[cols], ov, atol=ATOL_LOG)
     finally:
         mkt.close()
+
+
+@pytest.mark.parametrize("N,M", [(70_000, 2_000), (2_000, 70_000)])
+def test_many_rows_per_cta_sampled(gpu_lib, N, M):
+    """Tall and wide markets: one of the two passes gives every CTA more than
+    two blocks of 32 rows, so the row pass reuses its double-buffered blocks
+    of parked row sums (the path a 20,000-row pass does not reach). Two
+    sweeps, then one more checked on sampled rows and columns (the first and
+    last rows included) against the oracle's update from the GPU's own state."""
+    tu = gpu_lib
+    mk = make_market(N, M, 16, sigma=0.5, seed=N + 7, bias_y=True, m_kind="uniform1to5", dtype="fp32")
+    mkt = tu.from_synth(mk, path="dense")
+    try:
+        mkt.sweep(2)
+        lu0, lv0 = (t.double().cpu().numpy() for t in mkt.potentials())
+        mkt.sweep(1)
+        lu, lv = (t.double().cpu().numpy() for t in mkt.potentials())
+        rng = np.random.default_rng(2)
+        rows = np.unique(np.r_[0, N - 1, rng.choice(N, 62, replace=False)])
+        cols = np.unique(np.r_[0, M - 1, rng.choice(M, 62, replace=False)])
+        f = mk.f64()
+        _, ou = oracle.sampled_row_update(mk.F, mk.K, mk.G, mk.L, f["sigma"], f["n"], lv0, rows, None, mk.bias_y)
+        np.testing.assert_allclose(lu[rows], ou, atol=ATOL_LOG)
+        _, ov = oracle.sampled_row_update(mk.G, mk.L, mk.F, mk.K, f["sigma"], f["m"], lu, cols, mk.bias_y, None)
+        np.testing.assert_allclose(lv[cols], ov, atol=ATOL_LOG)
+        assert np.all(np.isfinite(lu)) and np.all(np.isfinite(lv))
+    finally:
+        mkt.close()
