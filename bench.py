@@ -867,7 +867,7 @@ def run_ours(args):
 
         # output stage: ranked top-10 lists for every X user (one pass over N x M)
         topk_ms = None
-        if cfg["path"] == "fused" and not args.no_extras:
+        if not args.no_extras:
             idx = torch.empty((mk.N, 10), dtype=torch.int32, device=dev)
             lmv = torch.empty((mk.N, 10), dtype=torch.float32, device=dev)
             # warm with the full row count: it also grows the ranked lists' hand-over
@@ -995,7 +995,9 @@ def run_ours(args):
                                   "gpair_evals_per_s": mk.N * mk.M / (topk_ms / 1e3) / 1e9,
                                   "vs_half_sweep": topk_ms / (avg_pass_s * 1e3),
                                   "what": "tu_topk_partners(side X, k=10) for every X user over all partners "
-                                          "(one tensor-core pass over N x M), after one untimed call"}
+                                          + ("(one tensor-core pass over N x M)" if cfg["path"] == "fused" else
+                                             "(one SIMT pass over the resident A-hat)")
+                                          + ", after one untimed call"}
     if cpu is not None:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)

@@ -30,38 +30,70 @@ __global__ void k_mu_block(ScoreSrc src, const double* __restrict__ ell_x, const
   out[(x - x0) * ld + (y - y0)] = (float)exp(lm);
 }
 
-// One warp per own row: each lane keeps a sorted top-k of the partners it
-// visits (increasing index, so equal scores keep the lower index first), then
-// the 32 lists are merged by k rounds of a warp-wide argmax.
-__global__ void __launch_bounds__(256) k_topk(ScoreSrc src, const double* __restrict__ ell_own,
-                                              const double* __restrict__ ell_par, int64_t partners, int k,
-                                              int64_t row0, int64_t nrows, int32_t* __restrict__ idx,
+// One warp per own row of a row-major matrix A (A-hat for side 0, its
+// resident transpose for side 1, so every row is read coalesced, float4 per
+// lane). The order of log mu within a row is the order of the FP32 score
+// log2(A[r][c]) + g_c, with g = (ell - shift) log2(e) of the partner side
+// (the partner vector in log2 mode, -inf padded); each lane keeps a sorted
+// top-k of the partners it visits (increasing index, so equal scores keep
+// the lower index first) behind a threshold test, in shared memory for
+// k <= kSharedK (local memory otherwise); then the 32 lists are merged by k
+// rounds of a warp-wide argmax, and log mu of the k winners is evaluated in
+// FP64 from A-hat and the potentials.
+constexpr int kSharedK = 16;
+
+template <bool SHARED>
+__global__ void __launch_bounds__(256) k_topk(const float* __restrict__ A, int64_t ld, const float* __restrict__ g,
+                                              const double* __restrict__ ell_own, const double* __restrict__ ell_par,
+                                              int k, int64_t row0, int64_t nrows, int32_t* __restrict__ idx,
                                               float* __restrict__ logmu) {
+  __shared__ float s_v[SHARED ? kSharedK : 1][256];
+  __shared__ int32_t s_i[SHARED ? kSharedK : 1][256];
+  float l_v[SHARED ? 1 : kMaxK];
+  int32_t l_i[SHARED ? 1 : kMaxK];
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int64_t r = (int64_t)blockIdx.x * 8 + warp;
-  if (r >= nrows) return;
+  if (r >= nrows) return;  // the whole warp leaves: no block-wide synchronisation follows
   const int64_t row = row0 + r;
-  float sv[kMaxK];
-  int si[kMaxK];
+  auto V = [&](int i) -> float& {
+    if constexpr (SHARED) return s_v[i][threadIdx.x];
+    else return l_v[i];
+  };
+  auto I = [&](int i) -> int32_t& {
+    if constexpr (SHARED) return s_i[i][threadIdx.x];
+    else return l_i[i];
+  };
   int cnt = 0;
-  for (int64_t c = lane; c < partners; c += 32) {
-    const float s = (float)((double)src.phi2s(row, c) + ell_par[c]);
-    if (cnt == k && !(s > sv[k - 1])) continue;
-    int pos = (cnt < k) ? cnt : k - 1;
-    while (pos > 0 && s > sv[pos - 1]) {
-      sv[pos] = sv[pos - 1];
-      si[pos] = si[pos - 1];
+  float thr = -INFINITY;  // the k-th best of this lane once it holds k entries
+  auto insert = [&](float sc, int32_t c) {
+    int pos = cnt < k ? cnt : k - 1;
+    while (pos > 0 && sc > V(pos - 1)) {
+      V(pos) = V(pos - 1);
+      I(pos) = I(pos - 1);
       --pos;
     }
-    sv[pos] = s;
-    si[pos] = (int)c;
+    V(pos) = sc;
+    I(pos) = c;
     if (cnt < k) ++cnt;
+    if (cnt == k) thr = V(k - 1);
+  };
+  const float4* a4 = reinterpret_cast<const float4*>(A + row * ld);
+  const float4* g4 = reinterpret_cast<const float4*>(g);
+  const int64_t n4 = ld / 4;
+  for (int64_t q = lane; q < n4; q += 32) {
+    const float4 av = a4[q];
+    const float4 gv = __ldg(g4 + q);
+    const float sc[4] = {log2f(av.x) + gv.x, log2f(av.y) + gv.y, log2f(av.z) + gv.z, log2f(av.w) + gv.w};
+    const int32_t c = (int32_t)(4 * q);
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (sc[e] > thr) insert(sc[e], c + e);
   }
   const double base = ell_own[row];
   int head = 0;
   for (int out_i = 0; out_i < k; ++out_i) {
-    float bs = (head < cnt) ? sv[head] : -INFINITY;
-    int bi = (head < cnt) ? si[head] : 0x7fffffff;
+    float bs = (head < cnt) ? V(head) : -INFINITY;
+    int bi = (head < cnt) ? I(head) : 0x7fffffff;
     int bl = lane;
     for (int o = 16; o > 0; o >>= 1) {
       const float os = __shfl_xor_sync(0xffffffffu, bs, o);
@@ -76,7 +108,7 @@ __global__ void __launch_bounds__(256) k_topk(ScoreSrc src, const double* __rest
     if (lane == bl) ++head;
     if (lane == 0) {
       idx[r * k + out_i] = bi;
-      if (logmu != nullptr) logmu[r * k + out_i] = (float)((double)bs + base);
+      if (logmu != nullptr) logmu[r * k + out_i] = (float)(log((double)A[row * ld + bi]) + ell_par[bi] + base);
     }
   }
 }
@@ -99,10 +131,18 @@ cudaError_t launch_mu_block(tu_market* m, int64_t x0, int64_t nx, int64_t y0, in
 }
 
 cudaError_t launch_topk(tu_market* m, int side, int k, int64_t row0, int64_t nrows, int32_t* idx, float* logmu) {
-  const Side& own = side == 0 ? m->X : m->Y;
-  const Side& par = side == 0 ? m->Y : m->X;
+  Side& own = side == 0 ? m->X : m->Y;
+  Side& par = side == 0 ? m->Y : m->X;
+  // the partner vector in log2 mode: g = (ell - shift) log2(e), -inf padded
+  cudaError_t e = launch_prep(m, par, 1);
+  if (e != cudaSuccess) return e;
+  const float* A = side == 0 ? m->Ahat : m->AhatT;
+  const int64_t ld = side == 0 ? m->ldA : m->ldN;
   const unsigned grid = (unsigned)((nrows + 7) / 8);
-  k_topk<<<grid, 256, 0, m->stream>>>(make_src(m, side), own.ell, par.ell, par.rows, k, row0, nrows, idx, logmu);
+  if (k <= kSharedK)
+    k_topk<true><<<grid, 256, 0, m->stream>>>(A, ld, par.pvec, own.ell, par.ell, k, row0, nrows, idx, logmu);
+  else
+    k_topk<false><<<grid, 256, 0, m->stream>>>(A, ld, par.pvec, own.ell, par.ell, k, row0, nrows, idx, logmu);
   return cudaGetLastError();
 }
 
