@@ -80,14 +80,41 @@ __global__ void __launch_bounds__(256) k_topk(const float* __restrict__ A, int64
   const float4* a4 = reinterpret_cast<const float4*>(A + row * ld);
   const float4* g4 = reinterpret_cast<const float4*>(g);
   const int64_t n4 = ld / 4;
-  for (int64_t q = lane; q < n4; q += 32) {
-    const float4 av = a4[q];
-    const float4 gv = __ldg(g4 + q);
-    const float sc[4] = {log2f(av.x) + gv.x, log2f(av.y) + gv.y, log2f(av.z) + gv.z, log2f(av.w) + gv.w};
+  // Row bound: the k-th largest of the 32 lanes' best scores is at most the
+  // row's k-th best (those k scores are distinct entries of the lists), so a
+  // score below it cannot be listed; refreshed every 8 steps (k <= 32).
+  float row_lb = -INFINITY;
+  int step = 0;
+  // warp-uniform trip count (the bound's shuffles need every lane); lanes past
+  // the row's end see -inf scores
+  for (int64_t q0 = 0; q0 < n4; q0 += 32, ++step) {
+    const int64_t q = q0 + lane;
+    float sc[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    if (q < n4) {
+      const float4 av = a4[q];
+      const float4 gv = __ldg(g4 + q);
+      sc[0] = log2f(av.x) + gv.x;
+      sc[1] = log2f(av.y) + gv.y;
+      sc[2] = log2f(av.z) + gv.z;
+      sc[3] = log2f(av.w) + gv.w;
+    }
     const int32_t c = (int32_t)(4 * q);
 #pragma unroll
     for (int e = 0; e < 4; ++e)
-      if (sc[e] > thr) insert(sc[e], c + e);
+      if (sc[e] > thr && sc[e] >= row_lb) insert(sc[e], c + e);
+    if (k <= 32 && (step & 7) == 7) {
+      float m = cnt > 0 ? V(0) : -INFINITY;
+      float kth = -INFINITY;
+      for (int j = 0; j < k; ++j) {
+        float best = m;
+        for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+        kth = best;
+        // remove one occurrence of the maximum (the lowest lane holding it)
+        const unsigned holders = __ballot_sync(0xffffffffu, m == best);
+        if (lane == __ffs(holders) - 1) m = -INFINITY;
+      }
+      row_lb = kth;
+    }
   }
   const double base = ell_own[row];
   int head = 0;
