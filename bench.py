@@ -1030,6 +1030,9 @@ def main():
         args.shape = tuple(int(v) for v in args.shape.split(","))
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
+    if (args.impl == "ours" and args.workload in ("paper", "batched", "ranking", "serving", "dims")
+            and int(os.environ.get("WORLD_SIZE", "1")) > 1 and int(os.environ.get("RANK", "0")) != 0):
+        return  # single-GPU workloads: rank 0 runs them (on its own device) and prints the line
     if args.workload == "paper" and args.impl == "ours":
         run_paper_shapes(args)
         return
