@@ -78,3 +78,14 @@ def test_reference_arm_dimension_sweep():
     for d in lines:
         assert d["impl"] == "reference" and d["N"] == d["M"] == 10_000 and d["ms_per_sweep"] > 0
         assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+
+
+@pytest.mark.parametrize("workload", ["paper", "batched", "ranking", "serving", "dims"])
+def test_single_gpu_workloads_leave_other_ranks_idle(workload):
+    """Under torchrun the single-GPU workloads run on rank 0 only: another
+    rank exits 0 at once, without touching a device or printing a line."""
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--workload", workload, "--gpus", "2"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=120, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
