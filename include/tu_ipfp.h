@@ -215,8 +215,11 @@ tu_status tu_market_relax_update(tu_market_t mkt, double tol);
  * then *residual = max_x |r_x| / n_x of the state that entered the last sweep
  * (row equations of Eq. IPFP, reduced in FP64 inside that sweep's X
  * half-sweep), *match_count = sum m - sum v^2 after it, and *sweeps = sweeps
- * completed since creation. While busy (*idle = 0) the other outputs are not
- * written. Any output pointer may be NULL. */
+ * completed since creation. After a call that certifies its result
+ * (tu_ipfp_sweep with residual_out, tu_ipfp_solve, tu_ipfp_solve_ranking),
+ * *residual is that certified residual of the returned state. While busy
+ * (*idle = 0) the other outputs are not written. Any output pointer may be
+ * NULL. */
 tu_status tu_market_query(tu_market_t mkt, int* idle, double* residual, double* match_count, int64_t* sweeps);
 
 /* Device memory a market of this shape holds (bytes), for admission control:

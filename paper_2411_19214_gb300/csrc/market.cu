@@ -505,6 +505,14 @@ tu_status certify(tu_market* m, double* res_inf, double* res_l1) {
   TU_TRY(read_results(m));
   if (res_inf) *res_inf = m->results_host[kResXInf];
   if (res_l1) *res_l1 = m->results_host[kResXL1] / m->X.sum_mass;
+  // tu_market_query then describes this synchronous call: every sweep done,
+  // the certified residual and the match count of the returned state
+  std::memcpy(m->query_host, m->results_host, kResSlots * sizeof(double));
+  const int no_error = kErrNone;
+  std::memcpy(m->query_host + kResSlots, &no_error, sizeof(int));
+  if (m->done_ev == nullptr) TU_CK(m, cudaEventCreateWithFlags(&m->done_ev, cudaEventDisableTiming));
+  TU_CK(m, cudaEventRecord(m->done_ev, m->stream));
+  m->query_sweeps = m->sweeps_enqueued;
   return TU_OK;
 }
 

@@ -172,6 +172,39 @@ def test_full_size_single_sweep_sampled(gpu_lib):
         mkt.close()
 
 
+def test_full_size_residual_certificate(gpu_lib):
+    """1e6 x 1e6, the benchmark market: the residual the library reports for
+    the state after four sweeps (max_x |r_x| / n_x over all 1e6 rows, reduced
+    in FP64 on the device) is certified on 1,024 sampled rows, whose row sums
+    the oracle recomputes in FP64 from the GPU's own potentials: none may
+    exceed it. The reported match count equals sum m - sum v^2 of the
+    returned potentials (FP64 on the host)."""
+    tu = gpu_lib
+    mk = fused_market()
+    stream = torch.cuda.Stream()
+    mkt = tu.from_synth(mk, path="fused", stream=stream, partition=65536)
+    try:
+        mkt.sweep(3)
+        reported = tu.tu_ipfp_sweep(mkt.handle, 1, residual=True)
+        # the query describes the certifying call: all four sweeps, its residual
+        idle, qres, match, sweeps = tu.tu_market_query(mkt.handle)
+        assert idle and sweeps == 4 and qres == reported
+        lu, lv = (t.double().cpu().numpy() for t in mkt.potentials())
+        rng = np.random.default_rng(11)
+        rows = np.sort(rng.choice(mk.N, 1024, replace=False))
+        f = mk.f64()
+        log_s, _ = oracle.sampled_row_update(mk.F, mk.K, mk.G, mk.L, f["sigma"], f["n"], lv, rows, mk.bias_x,
+                                             mk.bias_y)
+        u = np.exp(lu[rows])
+        r = u * u + 2.0 * u * np.exp(log_s) - f["n"][rows]
+        sampled = np.max(np.abs(r) / f["n"][rows])
+        assert np.isfinite(reported) and 0.0 < sampled <= reported * (1.0 + 1e-4) + 1e-9, (sampled, reported)
+        host_match = float(np.sum(f["m"]) - np.sum(np.exp(2.0 * lv)))
+        assert match == pytest.approx(host_match, rel=1e-6), (match, host_match)
+    finally:
+        mkt.close()
+
+
 @pytest.mark.parametrize("path", ["fused", "dense"])
 def test_graph_replay_equals_direct_launches(gpu_lib, path):
     """Blocks of sweeps replayed from a captured CUDA graph and the same blocks
