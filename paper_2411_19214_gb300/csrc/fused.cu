@@ -340,11 +340,18 @@ __device__ __forceinline__ int item_step() {
 // of per CTA.
 // F8: e4m3 factors, 128 per 128-byte row (KB = 1), tcgen05.mma kind::f8f6f4;
 // the per-side power-of-two scales are folded into p.c.
-template <int KB, int STAGES, int MODE, bool BATCH, bool F8>
+// SMALL: own tiles of 128 rows (one MMA chain; the epilogue warps of the
+// second sub-tile take part in every barrier but load and compute nothing),
+// for markets whose 256-row tiles would leave SMs idle: twice the CTAs, each
+// finishing its rows in about half the time. Every row's arithmetic is the
+// same as with 256-row tiles.
+template <int KB, int STAGES, int MODE, bool BATCH, bool F8, bool SMALL = false>
 __global__ void __launch_bounds__(kThreads, 1)
     k_fused_halfsweep(const __grid_constant__ CUtensorMap tm_own, const __grid_constant__ CUtensorMap tm_partner,
                       const FusedParams p) {
   static_assert(!BATCH || MODE == kModeSweep, "batched launches run half-sweeps only");
+  static_assert(!(BATCH && SMALL), "batched launches use 256-row own tiles");
+  constexpr int kOwn = SMALL ? kFusedOwnRows / 2 : kFusedOwnRows;  // rows of an own tile
   static_assert(!F8 || KB == 1, "e4m3 rows are one 128-byte block");
   constexpr int ABUF = kABufs<KB>;
   extern __shared__ uint8_t smem_raw[];
@@ -441,7 +448,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const CUtensorMap* map_partner = BATCH ? &bd->tm_partner : &tm_partner;
         const float* gsrc = BATCH ? bd->g : p.g + p.col0;
         const int npt = BATCH ? bd->num_partner_tiles : p.num_partner_tiles;
-        const int64_t arow = BATCH ? (int64_t)t * kFusedOwnRows : p.row0 + (int64_t)t * kFusedOwnRows;
+        // (SMALL: the 256-row box also brings the next tile's rows, unused)
+        const int64_t arow = BATCH ? (int64_t)t * kFusedOwnRows : p.row0 + (int64_t)t * kOwn;
         if (!mbar_wait(&a_empty[ab], a_phase ^ 1u, abort_flag)) {
           ok = false;
           break;
@@ -526,7 +534,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           tc_fence_after();
           const uint32_t b0 = smem_u32(sB + stage * KB * kPartnerBytesPerKB);
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
+          for (int h = 0; h < (SMALL ? 1 : 2); ++h) {
             const uint32_t d_tmem = tmem_base + (uint32_t)(buf * 256 + h * 128);
 #pragma unroll
             for (int k = 0; k < KB * 4; ++k) {
@@ -598,8 +606,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const double shift = BATCH ? *bd->lmax : shift0;
       const int npt = BATCH ? bd->num_partner_tiles : p.num_partner_tiles;
       const int rloc = h * 128 + q * 32 + lane;          // row within the own tile
-      const int64_t r = (int64_t)t * kFusedOwnRows + rloc;  // row within the launch
-      const bool row_ok = r < (BATCH ? bd->rows : p.rows);
+      const int64_t r = (int64_t)t * kOwn + rloc;         // row within the launch
+      const bool row_ok = rloc < kOwn && r < (BATCH ? bd->rows : p.rows);
       float sum = 0.0f, comp = 0.0f;
       float mu_lo = 0.0f;
       int mu_hi = 0;
@@ -637,24 +645,30 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float4* gs4 = reinterpret_cast<const float4*>(gsf);
         const int64_t colbase = p.col0 + (int64_t)j * kFusedPartnerRows + half * 64;
         uint64_t acc[4] = {0ull, 0ull, 0ull, 0ull};
-        // the second 32-column chunk is loaded while the first is processed
-        tmem_ld_issue(taddr, va);
-        tmem_ld_wait(va);
-        tmem_ld_issue(taddr + 32, vb);
-        if constexpr (MODE == kModeSweep) chunk_sum(va, gs4, cc, acc);
-        if constexpr (MODE == kModeTopK) chunk_topk(va, gsf, p.c, colbase, p.k, tv, ti, &tcnt, thr);
-        if constexpr (MODE == kModeTopKShared) chunk_topk_shared(va, gsf, p.c, colbase, p.k, lv, li, thr);
-        if constexpr (MODE == kModeMu) chunk_mu(va, gsf, p.c, colbase, mu_lo, mu_hi, row_ok, r, p);
-        tmem_ld_wait(vb);
+        // SMALL: the second sub-tile's warps keep step with the barriers only
+        const bool idle = SMALL && h == 1;
+        if (!idle) {
+          // the second 32-column chunk is loaded while the first is processed
+          tmem_ld_issue(taddr, va);
+          tmem_ld_wait(va);
+          tmem_ld_issue(taddr + 32, vb);
+          if constexpr (MODE == kModeSweep) chunk_sum(va, gs4, cc, acc);
+          if constexpr (MODE == kModeTopK) chunk_topk(va, gsf, p.c, colbase, p.k, tv, ti, &tcnt, thr);
+          if constexpr (MODE == kModeTopKShared) chunk_topk_shared(va, gsf, p.c, colbase, p.k, lv, li, thr);
+          if constexpr (MODE == kModeMu) chunk_mu(va, gsf, p.c, colbase, mu_lo, mu_hi, row_ok, r, p);
+          tmem_ld_wait(vb);
+        }
         // this warp's part of the accumulator buffer has been read: hand it back to the MMA warp
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[buf]);
-        if constexpr (MODE == kModeSweep) chunk_sum(vb, gs4 + 8, cc, acc);
-        if constexpr (MODE == kModeTopK) chunk_topk(vb, gsf + 32, p.c, colbase + 32, p.k, tv, ti, &tcnt, thr);
-        if constexpr (MODE == kModeTopKShared)
-          chunk_topk_shared(vb, gsf + 32, p.c, colbase + 32, p.k, lv, li, thr);
-        if constexpr (MODE == kModeMu) chunk_mu(vb, gsf + 32, p.c, colbase + 32, mu_lo, mu_hi, row_ok, r, p);
+        if (!idle) {
+          if constexpr (MODE == kModeSweep) chunk_sum(vb, gs4 + 8, cc, acc);
+          if constexpr (MODE == kModeTopK) chunk_topk(vb, gsf + 32, p.c, colbase + 32, p.k, tv, ti, &tcnt, thr);
+          if constexpr (MODE == kModeTopKShared)
+            chunk_topk_shared(vb, gsf + 32, p.c, colbase + 32, p.k, lv, li, thr);
+          if constexpr (MODE == kModeMu) chunk_mu(vb, gsf + 32, p.c, colbase + 32, mu_lo, mu_hi, row_ok, r, p);
+        }
         // the g slot has been read by this warp
         __syncwarp();
         if (lane == 0) mbar_arrive(&gempty[gs]);
@@ -879,25 +893,32 @@ constexpr int kStages = KB == 1 ? kStagesKB1 : (MODE == kModeTopKShared ? kStage
 template <int KB, int MODE>
 constexpr int kSmemTotal = smem_bytes<KB>(kStages<KB, MODE>) + (MODE == kModeTopKShared ? kTopKListBytes : 0);
 
-template <int KB, int MODE, bool BATCH, bool F8 = false>
+template <int KB, int MODE, bool BATCH, bool F8 = false, bool SMALL = false>
 cudaError_t launch_kernel(const CUtensorMap& own, const CUtensorMap& partner, const FusedParams& p, int grid,
                           cudaStream_t stream) {
   static_assert(kSmemTotal<KB, MODE> <= 232448, "shared memory budget");
-  k_fused_halfsweep<KB, kStages<KB, MODE>, MODE, BATCH, F8>
+  k_fused_halfsweep<KB, kStages<KB, MODE>, MODE, BATCH, F8, SMALL>
       <<<grid, kThreads, kSmemTotal<KB, MODE>, stream>>>(own, partner, p);
   return cudaGetLastError();
 }
 
-template <int MODE, bool BATCH>
-cudaError_t set_attributes_mode() {
-  cudaError_t e = cudaFuncSetAttribute(k_fused_halfsweep<1, kStages<1, MODE>, MODE, BATCH, false>,
+template <int MODE, bool BATCH, bool SMALL>
+cudaError_t set_attributes_variant() {
+  cudaError_t e = cudaFuncSetAttribute(k_fused_halfsweep<1, kStages<1, MODE>, MODE, BATCH, false, SMALL>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal<1, MODE>);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fused_halfsweep<1, kStages<1, MODE>, MODE, BATCH, true>,
+  e = cudaFuncSetAttribute(k_fused_halfsweep<1, kStages<1, MODE>, MODE, BATCH, true, SMALL>,
                            cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal<1, MODE>);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_fused_halfsweep<2, kStages<2, MODE>, MODE, BATCH, false>,
+  return cudaFuncSetAttribute(k_fused_halfsweep<2, kStages<2, MODE>, MODE, BATCH, false, SMALL>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal<2, MODE>);
+}
+
+template <int MODE, bool BATCH>
+cudaError_t set_attributes_mode() {
+  cudaError_t e = set_attributes_variant<MODE, BATCH, false>();
+  if (e == cudaSuccess && !BATCH) e = set_attributes_variant<MODE, false, true>();
+  return e;
 }
 
 // Dynamic shared memory opt-in of every instantiation, on the current device.
@@ -911,26 +932,48 @@ cudaError_t set_kernel_attributes() {
 }
 
 // kp: packed width in elements (bf16: 64 or 128; e4m3: 128, one 128-byte block).
-template <int MODE, bool BATCH = false>
-cudaError_t launch_any(int64_t kp, bool fp8, const CUtensorMap& own, const CUtensorMap& partner,
-                       const FusedParams& p, int grid, cudaStream_t stream) {
+template <int MODE, bool BATCH = false, bool SMALL = false>
+cudaError_t launch_variant(int64_t kp, bool fp8, const CUtensorMap& own, const CUtensorMap& partner,
+                           const FusedParams& p, int grid, cudaStream_t stream) {
   if (fp8) {
     if (kp != 128) return cudaErrorNotSupported;
-    return launch_kernel<1, MODE, BATCH, true>(own, partner, p, grid, stream);
+    return launch_kernel<1, MODE, BATCH, true, SMALL>(own, partner, p, grid, stream);
   }
   const int kb = (int)(kp / kKBlock);
-  if (kb == 1) return launch_kernel<1, MODE, BATCH>(own, partner, p, grid, stream);
-  if (kb == 2) return launch_kernel<2, MODE, BATCH>(own, partner, p, grid, stream);
+  if (kb == 1) return launch_kernel<1, MODE, BATCH, false, SMALL>(own, partner, p, grid, stream);
+  if (kb == 2) return launch_kernel<2, MODE, BATCH, false, SMALL>(own, partner, p, grid, stream);
   return cudaErrorNotSupported;
 }
 
-FusedParams base_params(int64_t rows, int64_t row0, int64_t col0, int64_t ncols, float c) {
+// small: 128-row own tiles (single-market launches only; see use_small_tiles)
+template <int MODE, bool BATCH = false>
+cudaError_t launch_any(int64_t kp, bool fp8, const CUtensorMap& own, const CUtensorMap& partner,
+                       const FusedParams& p, int grid, cudaStream_t stream, bool small = false) {
+  if constexpr (!BATCH) {
+    if (small) return launch_variant<MODE, false, true>(kp, fp8, own, partner, p, grid, stream);
+  }
+  return launch_variant<MODE, BATCH, false>(kp, fp8, own, partner, p, grid, stream);
+}
+
+// 128-row own tiles when they finish sooner: a CTA with one MMA chain ends its
+// tile in about half the time of a 256-row tile (half the epilogue warps share
+// each scheduler), so in units of a 256-row wave the small tiles take
+// ceil(tiles128 / SMs) / 2 and the large ones ceil(tiles256 / SMs).
+bool use_small_tiles(int64_t rows, int num_sms) {
+  const int64_t t256 = (rows + kFusedOwnRows - 1) / kFusedOwnRows;
+  const int64_t t128 = (rows + kFusedOwnRows / 2 - 1) / (kFusedOwnRows / 2);
+  const int64_t w256 = (t256 + num_sms - 1) / num_sms, w128 = (t128 + num_sms - 1) / num_sms;
+  return w128 < 2 * w256;
+}
+
+FusedParams base_params(int64_t rows, int64_t row0, int64_t col0, int64_t ncols, float c, bool small = false) {
   FusedParams p{};
+  const int own_rows = small ? kFusedOwnRows / 2 : kFusedOwnRows;
   p.rows = rows;
   p.row0 = row0;
   p.col0 = col0;
   p.ncols = ncols;
-  p.num_own_tiles = (int)((rows + kFusedOwnRows - 1) / kFusedOwnRows);
+  p.num_own_tiles = (int)((rows + own_rows - 1) / own_rows);
   p.num_partner_tiles = (int)((ncols + kFusedPartnerRows - 1) / kFusedPartnerRows);
   p.c = c;
   return p;
@@ -959,7 +1002,8 @@ cudaError_t fused_prepare(tu_market* m) {
 cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int update, int* nparts_out) {
   Side& own = side == 0 ? m->X : m->Y;
   Side& partner = side == 0 ? m->Y : m->X;
-  FusedParams p = base_params(own.rows, 0, 0, partner.rows, m->cmul);
+  const bool small = use_small_tiles(own.rows, m->num_sms);
+  FusedParams p = base_params(own.rows, 0, 0, partner.rows, m->cmul, small);
   p.g = partner.pvec;
   p.lmax = partner.lmax;
   p.b2s = own.b2s;
@@ -974,7 +1018,7 @@ cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int upd
   const int grid = grid_for_tiles(p.num_own_tiles, m->num_sms);
   *nparts_out = grid;
   return launch_any<kModeSweep>(m->kp, m->dtype == TU_DTYPE_FP8E4M3, own.tm_own, partner.tm_partner, p, grid,
-                                m->stream);
+                                m->stream, small);
 }
 
 // Ranked lists of own users [row0, row0 + nrows) over all partners (the
@@ -984,7 +1028,8 @@ cudaError_t launch_fused_topk(tu_market* m, int side, int k, int64_t row0, int64
                               float* logmu, float* hand_v, int32_t* hand_i) {
   Side& own = side == 0 ? m->X : m->Y;
   Side& partner = side == 0 ? m->Y : m->X;
-  FusedParams p = base_params(nrows, row0, 0, partner.rows, m->cmul);
+  const bool small = use_small_tiles(nrows, m->num_sms);
+  FusedParams p = base_params(nrows, row0, 0, partner.rows, m->cmul, small);
   p.g = partner.pvec;
   p.lmax = partner.lmax;
   p.ell = own.ell;
@@ -998,15 +1043,16 @@ cudaError_t launch_fused_topk(tu_market* m, int side, int k, int64_t row0, int64
   const int grid = grid_for_tiles(p.num_own_tiles, m->num_sms);
   const bool f8 = m->dtype == TU_DTYPE_FP8E4M3;
   if (k <= kSharedTopK)
-    return launch_any<kModeTopKShared>(m->kp, f8, own.tm_own, partner.tm_partner, p, grid, m->stream);
-  return launch_any<kModeTopK>(m->kp, f8, own.tm_own, partner.tm_partner, p, grid, m->stream);
+    return launch_any<kModeTopKShared>(m->kp, f8, own.tm_own, partner.tm_partner, p, grid, m->stream, small);
+  return launch_any<kModeTopK>(m->kp, f8, own.tm_own, partner.tm_partner, p, grid, m->stream, small);
 }
 
 // mu for own X users [x0, x0 + nx) and partners [y0, y0 + ny) (the Y partner
 // vector must have been prepared in log2 mode).
 cudaError_t launch_fused_mu(tu_market* m, int64_t x0, int64_t nx, int64_t y0, int64_t ny, float* out, int64_t ld) {
   const int64_t c0 = y0 & ~(int64_t)3;  // the g bulk copies start 16-byte aligned
-  FusedParams p = base_params(nx, x0, c0, y0 + ny - c0, m->cmul);
+  const bool small = use_small_tiles(nx, m->num_sms);
+  FusedParams p = base_params(nx, x0, c0, y0 + ny - c0, m->cmul, small);
   p.g = m->Y.pvec;
   p.lmax = m->Y.lmax;
   p.ell = m->X.ell;
@@ -1017,7 +1063,7 @@ cudaError_t launch_fused_mu(tu_market* m, int64_t x0, int64_t nx, int64_t y0, in
   p.y0 = y0;
   p.ny = ny;
   return launch_any<kModeMu>(m->kp, m->dtype == TU_DTYPE_FP8E4M3, m->X.tm_own, m->Y.tm_partner, p,
-                             grid_for_tiles(p.num_own_tiles, m->num_sms), m->stream);
+                             grid_for_tiles(p.num_own_tiles, m->num_sms), m->stream, small);
 }
 
 // Same kernel on caller-described buffers (no market object): used by the
