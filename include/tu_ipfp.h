@@ -196,6 +196,17 @@ tu_status tu_market_set_relaxation(tu_market_t mkt, double omega);
  * threads turn graphs off. No counterpart in the paper. */
 tu_status tu_market_use_graphs(tu_market_t mkt, int enable);
 
+/* Own-tile height of the fused path (no counterpart in the paper). With
+ * enable = 1 (the default), a market whose 256-row own tiles would leave SMs
+ * idle while its 128-row tiles all fit one wave uses 128-row tiles: twice the
+ * CTAs, each ending its tile sooner, so an isolated market of up to
+ * 128 x (SM count) users per side solves faster (a 1e4 x 1e4 sweep 0.171 ->
+ * 0.132 ms). A 128-row tile delivers about two thirds of a 256-row tile's
+ * per-SM throughput, so callers that keep the GPU full with many markets at
+ * once (a serving loop) set 0. Results are bit-identical either way (every
+ * row's arithmetic is the same). Dense markets ignore it. */
+tu_status tu_market_set_small_tiles(tu_market_t mkt, int enable);
+
 /* Automatic over-relaxation for asynchronous sweeps (no counterpart in the
  * paper). For a market whose relaxation setting is 0 (automatic), feed the
  * residual of the last completed tu_ipfp_sweep block (the value

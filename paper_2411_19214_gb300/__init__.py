@@ -76,6 +76,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tu_market_use_graphs": (I32, [V, I32]),
         "tu_selftest_wait_timeout": (I32, [D, ctypes.POINTER(D)]),
         "tu_set_checked_mode": (I32, [I32]),
+        "tu_market_set_small_tiles": (I32, [V, I32]),
         "tu_guard_violations": (I64, [ctypes.c_char_p, I64]),
         "tu_market_query": (I32, [V, ctypes.POINTER(I32), ctypes.POINTER(D), ctypes.POINTER(D),
                                   ctypes.POINTER(I64)]),
@@ -307,6 +308,11 @@ def tu_guard_violations():
     buf = ctypes.create_string_buffer(256)
     n = load().tu_guard_violations(buf, len(buf))
     return int(n), buf.value.decode()
+
+
+def tu_market_set_small_tiles(h: int, enable: bool) -> None:
+    """128-row own tiles for markets that leave SMs idle (default on); off for loops that keep the GPU full."""
+    _check(load().tu_market_set_small_tiles(h, int(bool(enable))), "tu_market_set_small_tiles", h)
 
 
 def tu_market_use_graphs(h: int, enable: bool) -> None:

@@ -955,15 +955,16 @@ cudaError_t launch_any(int64_t kp, bool fp8, const CUtensorMap& own, const CUten
   return launch_variant<MODE, BATCH, false>(kp, fp8, own, partner, p, grid, stream);
 }
 
-// 128-row own tiles when they finish sooner: a CTA with one MMA chain ends its
-// tile in about half the time of a 256-row tile (half the epilogue warps share
-// each scheduler), so in units of a 256-row wave the small tiles take
-// ceil(tiles128 / SMs) / 2 and the large ones ceil(tiles256 / SMs).
-bool use_small_tiles(int64_t rows, int num_sms) {
+// 128-row own tiles when they all fit one wave (and the market allows them):
+// a CTA with one MMA chain ends its tile in about 0.73 of the time of a
+// 256-row tile (measured at 1e4 x 1e4), so the small tiles win only while
+// SMs would otherwise stay idle; on a GPU already full (other markets' work
+// on other streams) they lose a third of the per-SM throughput.
+bool use_small_tiles(const tu_market* m, int64_t rows) {
+  if (!m->small_tiles) return false;
   const int64_t t256 = (rows + kFusedOwnRows - 1) / kFusedOwnRows;
   const int64_t t128 = (rows + kFusedOwnRows / 2 - 1) / (kFusedOwnRows / 2);
-  const int64_t w256 = (t256 + num_sms - 1) / num_sms, w128 = (t128 + num_sms - 1) / num_sms;
-  return w128 < 2 * w256;
+  return t256 < m->num_sms && t128 <= m->num_sms;
 }
 
 FusedParams base_params(int64_t rows, int64_t row0, int64_t col0, int64_t ncols, float c, bool small = false) {
@@ -1002,7 +1003,7 @@ cudaError_t fused_prepare(tu_market* m) {
 cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int update, int* nparts_out) {
   Side& own = side == 0 ? m->X : m->Y;
   Side& partner = side == 0 ? m->Y : m->X;
-  const bool small = use_small_tiles(own.rows, m->num_sms);
+  const bool small = use_small_tiles(m, own.rows);
   FusedParams p = base_params(own.rows, 0, 0, partner.rows, m->cmul, small);
   p.g = partner.pvec;
   p.lmax = partner.lmax;
@@ -1028,7 +1029,7 @@ cudaError_t launch_fused_topk(tu_market* m, int side, int k, int64_t row0, int64
                               float* logmu, float* hand_v, int32_t* hand_i) {
   Side& own = side == 0 ? m->X : m->Y;
   Side& partner = side == 0 ? m->Y : m->X;
-  const bool small = use_small_tiles(nrows, m->num_sms);
+  const bool small = use_small_tiles(m, nrows);
   FusedParams p = base_params(nrows, row0, 0, partner.rows, m->cmul, small);
   p.g = partner.pvec;
   p.lmax = partner.lmax;
@@ -1051,7 +1052,7 @@ cudaError_t launch_fused_topk(tu_market* m, int side, int k, int64_t row0, int64
 // vector must have been prepared in log2 mode).
 cudaError_t launch_fused_mu(tu_market* m, int64_t x0, int64_t nx, int64_t y0, int64_t ny, float* out, int64_t ld) {
   const int64_t c0 = y0 & ~(int64_t)3;  // the g bulk copies start 16-byte aligned
-  const bool small = use_small_tiles(nx, m->num_sms);
+  const bool small = use_small_tiles(m, nx);
   FusedParams p = base_params(nx, x0, c0, y0 + ny - c0, m->cmul, small);
   p.g = m->Y.pvec;
   p.lmax = m->Y.lmax;

@@ -872,6 +872,19 @@ tu_status tu_market_use_graphs(tu_market_t m, int enable) {
   return TU_OK;
 }
 
+tu_status tu_market_set_small_tiles(tu_market_t m, int enable) {
+  TU_TRY(check_live(m));
+  if ((enable != 0) != m->small_tiles && m->graph != nullptr) {
+    // captured sweeps use the kernel of the previous setting
+    TU_CK(m, cudaStreamSynchronize(m->stream));
+    cudaGraphExecDestroy(m->graph);
+    m->graph = nullptr;
+    m->graph_sweeps = 0;
+  }
+  m->small_tiles = enable != 0;
+  return TU_OK;
+}
+
 tu_status tu_market_relax_update(tu_market_t m, double tol) {
   TU_TRY(check_live(m));
   if (!(tol >= 0.0)) return fail(m, TU_ERR_INVALID_ARG, "tol < 0");

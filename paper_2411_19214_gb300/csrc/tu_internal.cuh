@@ -108,6 +108,7 @@ struct tu_market {
   cudaGraphExec_t graph = nullptr; // captured block of sweeps
   int graph_sweeps = 0;
   bool use_graphs = true;          // tu_market_use_graphs
+  bool small_tiles = true;         // tu_market_set_small_tiles: 128-row own tiles when they fit one wave
   bool poisoned = false;
   std::string last_error;
   // benchmark timing (tu_profile_enable / tu_profile_read)

@@ -54,7 +54,7 @@ import numpy as np
 
 from . import (TuError, tu_get_potentials, tu_ipfp_sweep, tu_market_create, tu_market_destroy,
                tu_market_footprint, tu_market_query, tu_market_relax_update, tu_market_set_relaxation,
-               tu_market_update_factors, tu_market_use_graphs, tu_topk_partners)
+               tu_market_set_small_tiles, tu_market_update_factors, tu_market_use_graphs, tu_topk_partners)
 
 # the fused path's factor dimension limit (2d <= 128: one 128-wide MMA inner dimension)
 MAX_D = 64
@@ -266,6 +266,8 @@ class Server:
             raise
         # a request runs only a few blocks of sweeps: too few to amortise a graph capture
         tu_market_use_graphs(h, False)
+        # many markets share the GPU: 256-row own tiles keep the per-SM throughput
+        tu_market_set_small_tiles(h, False)
         if self.relax:
             tu_market_set_relaxation(h, 0.0)
         return _Slot(handle=h, stream=stream, shape=req.shape, bytes=arg, req=req, admitted=now)

@@ -223,3 +223,35 @@ def test_graph_replay_equals_direct_launches(gpu_lib, path):
     finally:
         a.close()
         b.close()
+
+
+def test_small_tiles_bit_identical(gpu_lib):
+    """A market of 5,000 x 3,000 users takes 128-row own tiles (its 256-row
+    tiles would leave SMs idle); every row's arithmetic is the same as with
+    256-row tiles, so sweeps, ranked lists and mu blocks agree bit for bit
+    with the setting off, also when it changes between captured blocks."""
+    tu = gpu_lib
+    mk = make_market(5000, 3000, 32, sigma=0.5, seed=8, bias_x=True, bias_y=True, n_kind="uniform_real",
+                     m_kind="uniform_real", dtype="bf16")
+    a, b = tu.from_synth(mk), tu.from_synth(mk)
+    try:
+        tu.tu_market_set_small_tiles(b.handle, False)
+        a.sweep(5)
+        b.sweep(5)
+        for x, y in zip(a.potentials(), b.potentials()):
+            assert torch.equal(x, y)
+        for side in (0, 1):
+            ia, la = a.topk(side, 10)
+            ib, lb = b.topk(side, 10)
+            assert torch.equal(ia, ib) and torch.equal(la, lb)
+        assert torch.equal(a.mu_block(0, 300, 5, 700), b.mu_block(0, 300, 5, 700))
+        # toggled between blocks (the captured sweeps follow the setting)
+        tu.tu_market_set_small_tiles(a.handle, False)
+        tu.tu_market_set_small_tiles(b.handle, True)
+        a.sweep(4)
+        b.sweep(4)
+        for x, y in zip(a.potentials(), b.potentials()):
+            assert torch.equal(x, y)
+    finally:
+        a.close()
+        b.close()
