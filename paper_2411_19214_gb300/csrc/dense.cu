@@ -29,47 +29,52 @@ __global__ void __launch_bounds__(256) k_dense_build(const float* __restrict__ A
   __shared__ float Bs[16][64 + 4];
   __shared__ float Ts[64][64 + 1];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  const int64_t row0 = (int64_t)blockIdx.y * 64, col0 = (int64_t)blockIdx.x * 64;
-  float acc[4][4] = {};
-  for (int64_t k0 = 0; k0 < kp; k0 += 16) {
-    for (int e = threadIdx.x; e < 16 * 64; e += kThreads) {
-      const int r = e / 16, kk = e % 16;
-      const int64_t gr = row0 + r, gc = col0 + r;
-      As[kk][r] = (gr < N) ? AX[gr * kp + k0 + kk] : 0.0f;
-      Bs[kk][r] = (gc < M) ? AY[gc * kp + k0 + kk] : 0.0f;
+  const int64_t col0 = (int64_t)blockIdx.x * 64;
+  // row tiles in steps of the grid's height (at most 65,535), so that any N
+  // fits one launch; the trip count is the same for every thread of a block
+  for (int64_t row0 = (int64_t)blockIdx.y * 64; row0 < N; row0 += (int64_t)gridDim.y * 64) {
+    float acc[4][4] = {};
+    for (int64_t k0 = 0; k0 < kp; k0 += 16) {
+      for (int e = threadIdx.x; e < 16 * 64; e += kThreads) {
+        const int r = e / 16, kk = e % 16;
+        const int64_t gr = row0 + r, gc = col0 + r;
+        As[kk][r] = (gr < N) ? AX[gr * kp + k0 + kk] : 0.0f;
+        Bs[kk][r] = (gc < M) ? AY[gc * kp + k0 + kk] : 0.0f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        float a[4], b[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int64_t r = row0 + ty * 4 + i;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int64_t c = col0 + tx * 4 + j;
+        const float v = (r < N && c < M) ? expf(acc[i][j] * inv2s) : 0.0f;
+        Ts[tx * 4 + j][ty * 4 + i] = v;
+        if (r < N && c < ldA) Ahat[r * ldA + c] = v;
+      }
     }
     __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < 16; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    // transposed tile: row c of A-hat^T holds column c of A-hat
+    for (int e = threadIdx.x; e < 64 * 64; e += kThreads) {
+      const int cl = e / 64, rl = e % 64;
+      const int64_t c = col0 + cl, r = row0 + rl;
+      if (c < M && r < ldN) AhatT[c * ldN + r] = (r < N) ? Ts[cl][rl] : 0.0f;
     }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int64_t r = row0 + ty * 4 + i;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int64_t c = col0 + tx * 4 + j;
-      const float v = (r < N && c < M) ? expf(acc[i][j] * inv2s) : 0.0f;
-      Ts[tx * 4 + j][ty * 4 + i] = v;
-      if (r < N && c < ldA) Ahat[r * ldA + c] = v;
-    }
-  }
-  __syncthreads();
-  // transposed tile: row c of A-hat^T holds column c of A-hat
-  for (int e = threadIdx.x; e < 64 * 64; e += kThreads) {
-    const int cl = e / 64, rl = e % 64;
-    const int64_t c = col0 + cl, r = row0 + rl;
-    if (c < M && r < ldN) AhatT[c * ldN + r] = (r < N) ? Ts[cl][rl] : 0.0f;
+    __syncthreads();  // Ts is rewritten by the next row tile
   }
 }
 
@@ -333,7 +338,8 @@ cudaError_t launch_dense_build(tu_market* m) {
     e = cudaFuncSetAttribute(k_dense_rowpass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(PassSmem));
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)((m->M + 63) / 64), (unsigned)((m->N + 63) / 64));
+  const int64_t row_tiles = (m->N + 63) / 64;
+  dim3 grid((unsigned)((m->M + 63) / 64), (unsigned)(row_tiles < 65535 ? row_tiles : 65535));
   k_dense_build<<<grid, kThreads, 0, m->stream>>>(m->X.fac32, m->Y.fac32, m->N, m->M, m->kp,
                                                   (float)(0.5 / m->sigma), m->Ahat, m->ldA, m->AhatT, m->ldN);
   return cudaGetLastError();

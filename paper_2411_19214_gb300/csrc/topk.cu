@@ -24,10 +24,12 @@ struct ScoreSrc {
 __global__ void k_mu_block(ScoreSrc src, const double* __restrict__ ell_x, const double* __restrict__ ell_y, int64_t x0,
                            int64_t nx, int64_t y0, int64_t ny, float* __restrict__ out, int64_t ld) {
   const int64_t y = y0 + (int64_t)blockIdx.x * 32 + threadIdx.x;
-  const int64_t x = x0 + (int64_t)blockIdx.y * 8 + threadIdx.y;
-  if (x >= x0 + nx || y >= y0 + ny) return;
-  const double lm = (double)src.phi2s(x, y) + ell_x[x] + ell_y[y];
-  out[(x - x0) * ld + (y - y0)] = (float)exp(lm);
+  if (y >= y0 + ny) return;
+  // rows in steps of the grid's height (at most 65,535 blocks of 8 rows)
+  for (int64_t x = x0 + (int64_t)blockIdx.y * 8 + threadIdx.y; x < x0 + nx; x += (int64_t)gridDim.y * 8) {
+    const double lm = (double)src.phi2s(x, y) + ell_x[x] + ell_y[y];
+    out[(x - x0) * ld + (y - y0)] = (float)exp(lm);
+  }
 }
 
 // One warp per own row of a row-major matrix A (A-hat for side 0, its
@@ -152,7 +154,8 @@ static ScoreSrc make_src(tu_market* m, int side) {
 
 cudaError_t launch_mu_block(tu_market* m, int64_t x0, int64_t nx, int64_t y0, int64_t ny, float* out, int64_t ld) {
   dim3 block(32, 8);
-  dim3 grid((unsigned)((ny + 31) / 32), (unsigned)((nx + 7) / 8));
+  const int64_t row_blocks = (nx + 7) / 8;
+  dim3 grid((unsigned)((ny + 31) / 32), (unsigned)(row_blocks < 65535 ? row_blocks : 65535));
   k_mu_block<<<grid, block, 0, m->stream>>>(make_src(m, 0), m->X.ell, m->Y.ell, x0, nx, y0, ny, out, ld);
   return cudaGetLastError();
 }

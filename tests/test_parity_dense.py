@@ -142,3 +142,44 @@ def test_many_rows_per_cta_sampled(gpu_lib, N, M):
         assert np.all(np.isfinite(lu)) and np.all(np.isfinite(lv))
     finally:
         mkt.close()
+
+
+def test_tall_market_beyond_one_grid_height(gpu_lib):
+    """4,300,000 x 8: more row tiles of 64 than one grid's height (65,535)
+    holds, so building A-hat strides over row tiles, and a 600,000-row mu
+    block has more than 65,535 blocks of 8 rows. Two sweeps, then one more
+    checked on sampled rows (both sides of the grid-height bound and the last
+    row included) and on every column against the oracle's update from the
+    GPU's own state; then the mu block of the last 600,000 rows."""
+    tu = gpu_lib
+    N, M = 4_300_000, 8
+    assert (N + 63) // 64 > 65535
+    mk = make_market(N, M, 4, sigma=0.5, seed=29, bias_y=True, m_kind="uniform1to5", dtype="fp32")
+    mkt = tu.from_synth(mk, path="dense")
+    try:
+        mkt.sweep(2)
+        lu0, lv0 = (t.double().cpu().numpy() for t in mkt.potentials())
+        mkt.sweep(1)
+        lu, lv = (t.double().cpu().numpy() for t in mkt.potentials())
+        rng = np.random.default_rng(3)
+        edge = 64 * 65535
+        rows = np.unique(np.r_[0, edge - 1, edge, edge + 63, N - 1, rng.choice(N, 59, replace=False)])
+        f = mk.f64()
+        _, ou = oracle.sampled_row_update(mk.F, mk.K, mk.G, mk.L, f["sigma"], f["n"], lv0, rows, None, mk.bias_y)
+        np.testing.assert_allclose(lu[rows], ou, atol=ATOL_LOG)
+        _, ov = oracle.sampled_row_update(mk.G, mk.L, mk.F, mk.K, f["sigma"], f["m"], lu, np.arange(M), mk.bias_y,
+                                          None)
+        # a column sum runs over 4.3e6 terms: each of the pass's 1,024 FP32
+        # accumulators adds about N / 1024 positive terms (relative error at
+        # most that many units of 2^-24), then about 20 more roundings combine
+        # them; a row tile left unbuilt would move log v by about 0.025
+        col_atol = ATOL_LOG + (N / 1024 + 32) * 2.0**-24
+        np.testing.assert_allclose(lv, ov, atol=col_atol)
+        nx = 600_000
+        x0 = N - nx
+        mu = mkt.mu_block(x0, nx, 0, M).double().cpu().numpy()
+        Phi = oracle.phi_dense(f["F"][x0:], f["K"][x0:], f["G"], f["L"], None, f["bias_y"])
+        ref = np.exp(oracle.log_mu(oracle.log_kernel(Phi, f["sigma"]), lu[x0:], lv))
+        np.testing.assert_allclose(mu, ref, rtol=MU_RTOL_FP32)
+    finally:
+        mkt.close()
