@@ -46,6 +46,7 @@ import concurrent.futures as cf
 import dataclasses
 import json
 import math
+import numbers
 import threading
 import time
 from typing import Dict, List, Optional
@@ -128,7 +129,10 @@ def validate(req: SolveRequest) -> Optional[str]:
             return f"{name} must have one capacity per user ({rows})"
         if not np.all(np.isfinite(c)) or not np.all(c > 0):
             return f"capacities {name} must be finite and > 0"
-    if not (isinstance(req.sigma, (int, float)) and math.isfinite(req.sigma) and req.sigma > 0):
+    # any real scalar (Python or numpy), not a bool, array or string
+    if isinstance(req.sigma, (bool, np.bool_)) or not isinstance(req.sigma, (numbers.Real, np.floating)):
+        return "sigma must be finite and > 0"
+    if not (math.isfinite(float(req.sigma)) and float(req.sigma) > 0):
         return "sigma must be finite and > 0"
     for name, b, rows in (("bias_x", req.bias_x, N), ("bias_y", req.bias_y, M)):
         if b is not None and _shape_of(b) != (rows,):

@@ -19,6 +19,9 @@ def _req(serve, **over):
 def test_valid_request_passes():
     from paper_2411_19214_gb300 import serve
     assert serve.validate(_req(serve)) is None
+    # sigma as any real scalar: Python int or numpy float32 / float64
+    for sigma in (1, np.float32(0.5), np.float64(0.25)):
+        assert serve.validate(_req(serve, sigma=sigma)) is None, sigma
 
 
 @pytest.mark.parametrize("over,needle", [
@@ -33,6 +36,10 @@ def test_valid_request_passes():
     (dict(m=-np.ones(40)), "finite and > 0"),
     (dict(sigma=0.0), "sigma"),
     (dict(sigma=float("inf")), "sigma"),
+    (dict(sigma=np.float32("nan")), "sigma"),
+    (dict(sigma=True), "sigma"),
+    (dict(sigma="0.5"), "sigma"),
+    (dict(sigma=np.array([0.5])), "sigma"),
     (dict(bias_x=np.zeros(31, np.float32)), "bias_x"),
     (dict(bias_y=np.zeros((40, 1), np.float32)), "bias_y"),
 ])
