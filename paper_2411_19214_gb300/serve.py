@@ -17,9 +17,9 @@ soon as memory allows and their sweeps overlap on the device:
   by the library's automatic controller (``tu_market_relax_update``); a market
   whose last block reports residual <= tol (row equations of Eq. IPFP, FP64)
   or that reached the sweep cap is finished;
-* reply: the ranked top-k partners of every X user (``tu_topk_partners``
-  into device buffers on the market's stream; a worker thread waits for them
-  and copies them back);
+* reply: the ranked top-k partners of every X user, all M of them when a
+  market has fewer than k (``tu_topk_partners`` into device buffers on the
+  market's stream; a worker thread waits for them and copies them back);
 * re-solves: a request that names the key of a resident market replaces its
   factors (``tu_market_update_factors``) and continues from its potentials
   (warm start) instead of starting from u = v = 1;
@@ -282,11 +282,12 @@ class Server:
         import torch
         req = slot.req
         N, M, _ = req.shape
+        k = min(self.k, M)  # a market with fewer partners than k ranks all of them
         with torch.cuda.stream(slot.stream):
-            idx = torch.empty((N, self.k), dtype=torch.int32, device="cuda")
-            lm = torch.empty((N, self.k), dtype=torch.float32, device="cuda")
+            idx = torch.empty((N, k), dtype=torch.int32, device="cuda")
+            lm = torch.empty((N, k), dtype=torch.float32, device="cuda")
             lu = lv = None
-            tu_topk_partners(slot.handle, 0, self.k, 0, N, idx, lm)
+            tu_topk_partners(slot.handle, 0, k, 0, N, idx, lm)
             if self.keep_potentials:
                 lu = torch.empty(N, dtype=torch.float32, device="cuda")
                 lv = torch.empty(M, dtype=torch.float32, device="cuda")
@@ -432,8 +433,11 @@ class Server:
                         if slot.inflight:
                             slot.inflight = False
                             if res <= self.tol or done >= self.max_sweeps:
+                                # the reply is enqueued first: if that fails, the
+                                # handler below still finds the slot in `active`
+                                fut = self._reply(slot, res, match, now_fn)
                                 active.remove(slot)
-                                finishing.append((self._reply(slot, res, match, now_fn), slot))
+                                finishing.append((fut, slot))
                                 progressed = True
                                 continue
                         if expired(slot.req, now_fn()):
