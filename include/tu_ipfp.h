@@ -98,7 +98,11 @@ typedef struct {
  * exponent range fits FP32: max_x |a_x| * max_y |b_y| / (2 sigma) <= 40, where
  * a_x = (f_x, k_x), b_y = (g_y, l_y) (a Cauchy-Schwarz bound on the bias-free
  * part of phi / (2 sigma)); otherwise TU_ERR_UNSUPPORTED. Biases have no limit:
- * they are folded into the potentials in log space. On success *out owns device memory of about
+ * they are folded into the potentials in log space. Sizes: 1 <= N, M <= 2^31
+ * and 1 <= d <= 4096 (TU_ERR_INVALID_ARG otherwise); the fused path takes
+ * d <= 64 (2d fills one 128-wide MMA inner dimension), FP8 factors only on the
+ * fused path, and a dense market at most 200 GB of A-hat and its transpose
+ * (TU_ERR_UNSUPPORTED otherwise). On success *out owns device memory of about
  * (N + M) * 2 * d * 2 bytes (fused) or 2 * N * M * 4 bytes (dense) plus O(N + M). */
 tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out);
 
