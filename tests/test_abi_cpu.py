@@ -64,9 +64,25 @@ def test_invalid_arguments_rejected_before_cuda(lib):
     d = tu.MarketDesc(N=0, M=4, d=3, dtype=1, path=0)
     h = ctypes.c_void_p()
     assert lib.tu_market_create(ctypes.byref(d), ctypes.byref(h)) == tu.TU_ERR_INVALID_ARG
-    # fused path is limited to d <= 64
-    d = tu.MarketDesc(N=4, M=4, d=65, dtype=1, path=0, F=1, K=1, G=1, L=1, n=1, m=1, sigma=1.0)
-    assert lib.tu_market_create(ctypes.byref(d), ctypes.byref(h)) == tu.TU_ERR_UNSUPPORTED
+    # the size limits of the header's create contract, each with its status;
+    # every one is decided before the library touches CUDA (the pointers are
+    # placeholders that are never read)
+    ptrs = dict(F=1, K=1, G=1, L=1, n=1, m=1, sigma=1.0)
+    limits = [
+        (dict(N=(1 << 31) + 1, M=4, d=3, dtype=1, path=1), tu.TU_ERR_INVALID_ARG),
+        (dict(N=4, M=(1 << 31) + 1, d=3, dtype=1, path=1), tu.TU_ERR_INVALID_ARG),
+        (dict(N=4, M=4, d=4097, dtype=1, path=1), tu.TU_ERR_INVALID_ARG),
+        (dict(N=4, M=4, d=3, dtype=3, path=0), tu.TU_ERR_INVALID_ARG),  # unknown dtype
+        (dict(N=4, M=4, d=3, dtype=1, path=2), tu.TU_ERR_INVALID_ARG),  # unknown path
+        (dict(N=4, M=4, d=65, dtype=1, path=0), tu.TU_ERR_UNSUPPORTED),  # fused: 2d <= 128
+        (dict(N=4, M=4, d=65, dtype=tu.TU_DTYPE_FP8E4M3, path=0), tu.TU_ERR_UNSUPPORTED),
+        (dict(N=4, M=4, d=3, dtype=tu.TU_DTYPE_FP8E4M3, path=1), tu.TU_ERR_UNSUPPORTED),  # FP8: fused only
+        # dense: A-hat and its transpose, 2 x 4 B x 160,000 x 160,000 = 205 GB > 200 GB
+        (dict(N=160_000, M=160_000, d=3, dtype=1, path=1), tu.TU_ERR_UNSUPPORTED),
+    ]
+    for shape, want in limits:
+        d = tu.MarketDesc(**shape, **ptrs)
+        assert lib.tu_market_create(ctypes.byref(d), ctypes.byref(h)) == want, shape
     # calls on a null market
     assert lib.tu_ipfp_sweep(None, 1, None) == tu.TU_ERR_INVALID_ARG
     lib.tu_market_destroy(None)
