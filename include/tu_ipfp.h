@@ -103,7 +103,9 @@ typedef struct {
  * d <= 64 (2d fills one 128-wide MMA inner dimension), FP8 factors only on the
  * fused path, and a dense market at most 200 GB of A-hat and its transpose
  * (TU_ERR_UNSUPPORTED otherwise). On success *out owns device memory of about
- * (N + M) * 2 * d * 2 bytes (fused) or 2 * N * M * 4 bytes (dense) plus O(N + M). */
+ * (N + M) * 2 * d * 2 bytes (fused) or 2 * N * M * 4 bytes (dense), a staging
+ * buffer for factor uploads of 2 * max(N, M) * d * (2 for BF16, else 4) bytes,
+ * and O(N + M); tu_market_footprint gives the total. */
 tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out);
 
 /* Replace F, K, G, L (same shapes and dtype as at creation; host or device).

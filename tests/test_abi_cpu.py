@@ -96,3 +96,55 @@ def test_binding_rejects_shape_mismatch(lib):
                             np.ones(5), 1.0)
     with pytest.raises(TypeError):
         tu.tu_market_create(F.astype(np.float64), F, F, F, np.ones(4), np.ones(4), 1.0)
+
+
+def test_noalloc_and_batch_arguments_rejected_before_cuda(lib):
+    """The allocation-free half-sweep and the batch calls decide their
+    documented refusals before touching CUDA (placeholder pointers, 16-byte
+    aligned, are never read)."""
+    INV, UNS = tu.TU_ERR_INVALID_ARG, tu.TU_ERR_UNSUPPORTED
+    P = 1 << 20  # a placeholder device address
+
+    def noalloc(rows=100, cols=200, kp=64, own=P, par=P, mass=P, lu_in=P, lv=P, out=P, sigma=0.5):
+        return lib.tu_fused_halfsweep_noalloc(rows, cols, kp, own, par, None, mass, lu_in, None, lv, sigma, out,
+                                              None, None)
+
+    cases = [
+        (dict(rows=0), INV), (dict(cols=0), INV), (dict(sigma=0.0), INV), (dict(sigma=float("inf")), INV),
+        (dict(sigma=float("nan")), INV), (dict(own=None), INV), (dict(par=None), INV), (dict(mass=None), INV),
+        (dict(lu_in=None), INV), (dict(lv=None), INV), (dict(out=None), INV),
+        (dict(rows=65537), UNS), (dict(cols=1048577), UNS), (dict(kp=96), UNS), (dict(kp=256), UNS),
+        (dict(own=P + 8), INV), (dict(par=P + 4), INV),  # packed factors must be 16-byte aligned
+    ]
+    for kw, want in cases:
+        assert noalloc(**kw) == want, kw
+    V = ctypes.c_void_p
+    h = V()
+    two_null = (V * 2)(None, None)
+    assert lib.tu_batch_create(None, 1, None, ctypes.byref(h)) == INV
+    assert lib.tu_batch_create(two_null, 0, None, ctypes.byref(h)) == INV
+    assert lib.tu_batch_create(two_null, 65537, None, ctypes.byref(h)) == INV
+    assert lib.tu_batch_create(two_null, 2, None, ctypes.byref(h)) == INV  # NULL members
+    assert lib.tu_batch_create(two_null, 2, None, None) == INV
+    assert lib.tu_batch_sweep(None, 1, None) == INV
+    assert lib.tu_batch_solve(None, 1e-6, 10, 0, None) == INV
+    assert lib.tu_batch_profile_enable(None, 1) == INV
+    assert lib.tu_batch_profile_read(None, None, None) == INV
+    lib.tu_batch_destroy(None)
+    assert lib.tu_batch_last_error(None) == b""
+
+
+def test_footprint_counts_the_documented_buffers(lib):
+    """tu_market_footprint (pure host arithmetic) holds at least the buffers
+    the header names: the packed factors (fused) or A-hat and its transpose
+    (dense), and the upload staging; 0 for an invalid shape."""
+    for N, M, d in [(1, 1, 1), (1000, 3000, 16), (1_000_000, 1_000_000, 64), (20_000, 10_000, 32)]:
+        fused = tu.tu_market_footprint(N, M, d, "fused")
+        dense = tu.tu_market_footprint(N, M, d, "dense")
+        staging = 2 * max(N, M) * d * 2
+        assert fused >= (N + M) * 2 * d * 2 + staging
+        assert dense >= 2 * N * M * 4 + staging
+        # the per-user state and fixed scratch are O(N + M), a few hundred bytes per user at most
+        assert fused - (N + M) * 2 * d * 2 - 2 * max(N, M) * d * 4 <= 300 * (N + M) + (1 << 20)
+    assert tu.tu_market_footprint(0, 5, 3, "fused") == 0
+    assert tu.tu_market_footprint(5, 5, 0, "dense") == 0
