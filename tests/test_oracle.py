@@ -350,6 +350,28 @@ def test_row_residual_direct():
     assert r_l1 == pytest.approx(np.sum(np.abs(r_direct)) / np.sum(n), rel=1e-12)
 
 
+def test_col_residual_direct():
+    """The column equations of Eq. IPFP written out in the linear domain,
+    m_y = v_y^2 + v_y sum_x A_xy u_x, at arbitrary potentials; and zero (to
+    rounding) right after a Y half-sweep, which solves exactly those
+    equations for v."""
+    rng = np.random.default_rng(29)
+    F, K, G, L, bx, by, n, m = _random_market(rng, 7, 5)
+    beta = 0.8
+    Phi = oracle.phi_dense(F, K, G, L, bx, by)
+    lu, lv = rng.normal(size=7) - 1, rng.normal(size=5) - 1
+    A = np.exp(Phi / (2 * beta))
+    u, v = np.exp(lu), np.exp(lv)
+    r_direct = v * v + v * (A.T @ u) - m
+    logA = oracle.log_kernel(Phi, beta)
+    r_inf, r_l1, r = oracle.col_residual(logA, m, lu, lv)
+    np.testing.assert_allclose(r, r_direct, rtol=1e-12)
+    assert r_inf == pytest.approx(np.max(np.abs(r_direct) / m), rel=1e-12)
+    assert r_l1 == pytest.approx(np.sum(np.abs(r_direct)) / np.sum(m), rel=1e-12)
+    lv_new = oracle.half_sweep_y(logA, lu, m)
+    assert oracle.col_residual(logA, m, lu, lv_new)[0] < 1e-13
+
+
 def test_sampled_row_update_equals_dense_half_sweep():
     mk = make_market(50, 333, 8, sigma=0.5, seed=23, bias_x=True, bias_y=True, dtype="bf16")
     f = mk.f64()
