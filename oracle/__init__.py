@@ -20,7 +20,9 @@ Pins (in ``tests/test_oracle.py``, all run on the CPU):
 * the literal Alg. 1 update (printed form) on well-conditioned markets;
 * invariants at the fixed point (marginals, total mass identity, permutation
   equivariance, side swap, mass scaling) and batch == mini-batch iterates;
-* brute-force sorting for the ranked lists.
+* brute-force sorting for the ranked lists;
+* the translation step (an extension) against a brute-force maximisation of
+  the dual along its line and a 60-digit root of its quadratic.
 """
 
 from .ipfp import (  # noqa: F401
@@ -31,6 +33,8 @@ from .ipfp import (  # noqa: F401
     half_sweep_x,
     half_sweep_y,
     ipfp_batch,
+    dual_value,
+    translation_step,
     ipfp_batch_literal,
     ipfp_minibatch,
     row_residual,

@@ -137,10 +137,68 @@ def col_residual(logA, m, log_u, log_v):
 
 
 # ---------------------------------------------------------------------------
+# Translation step (an extension: exact line search of the dual)
+# ---------------------------------------------------------------------------
+
+def dual_value(logA, n, m, log_u, log_v):
+    """The concave function whose stationarity conditions are Eq. IPFP:
+        D(a, b) = sum_x n_x a_x + sum_y m_y b_y - 1/2 sum_x e^{2 a_x} - 1/2 sum_y e^{2 b_y}
+                  - sum_xy A_xy e^{a_x + b_y},     a = log u, b = log v.
+    d D / d a_x = n_x - u_x^2 - u_x sum_y A_xy v_y is the first line of Eq. IPFP
+    (and d D / d b_y the second), so IPFP, which solves the row equations and
+    then the column equations exactly, is block coordinate ascent on D
+    (Sec. 3.1 describes IPFP as a coordinate method on the dual of
+    Eq. primary optimization). Evaluated with the maximum factored out of
+    the pair sum."""
+    lu = np.asarray(log_u, np.float64)
+    lv = np.asarray(log_v, np.float64)
+    pair = logA + lu[:, None] + lv[None, :]
+    mx = np.max(pair)
+    return float(np.dot(n, lu) + np.dot(m, lv) - 0.5 * np.sum(np.exp(2.0 * lu)) - 0.5 * np.sum(np.exp(2.0 * lv))
+                 - np.exp(mx) * np.sum(np.exp(pair - mx)))
+
+
+def translation_step(log_p, log_o, mass_p, mass_o):
+    """Exact maximisation of ``dual_value`` along (log p + tau, log o - tau).
+
+    Not in the paper (Sec. 5 names acceleration techniques from optimal
+    transport as future work). Moving one side's log potentials up by tau and
+    the other side's down by tau leaves every pair term A_xy u_x v_y unchanged,
+    so along that line the dual is
+        D(tau) = const + tau (sum mass_p - sum mass_o) - 1/2 e^{2 tau} P - 1/2 e^{-2 tau} O,
+    P = sum e^{2 log p}, O = sum e^{2 log o}. D is strictly concave in tau and
+    D'(tau) = 0 is, with z = e^{2 tau} > 0, the quadratic
+        P z^2 - Dm z - O = 0,   Dm = sum mass_p - sum mass_o,
+    whose positive root is z = (Dm + R) / (2 P) = 2 O / (R - Dm),
+    R = sqrt(Dm^2 + 4 P O). The first form is used for Dm >= 0 and the second
+    for Dm < 0, so no subtraction cancels; P and O are carried as logarithms
+    (log-sum-exp), so potentials of any size are handled.
+    At the returned point sum mass_p - P' = sum mass_o - O': the two forms of
+    the match count (Eq. IPFP summed over each side) agree.
+
+    Returns (log_p + tau, log_o - tau, tau).
+    """
+    lp = np.asarray(log_p, np.float64)
+    lo = np.asarray(log_o, np.float64)
+    log_P = _logsumexp(2.0 * lp, axis=0)
+    log_O = _logsumexp(2.0 * lo, axis=0)
+    dm = float(np.sum(mass_p) - np.sum(mass_o))
+    log_4po = np.log(4.0) + log_P + log_O
+    log_R = 0.5 * (np.logaddexp(2.0 * np.log(abs(dm)), log_4po) if dm != 0.0 else log_4po)
+    if dm >= 0.0:
+        log_num = np.logaddexp(np.log(dm), log_R) if dm > 0.0 else log_R
+        log_z = log_num - np.log(2.0) - log_P
+    else:
+        log_z = np.log(2.0) + log_O - np.logaddexp(log_R, np.log(-dm))
+    tau = 0.5 * float(log_z)
+    return lp + tau, lo - tau, tau
+
+
+# ---------------------------------------------------------------------------
 # Batch IPFP (Alg. 1)
 # ---------------------------------------------------------------------------
 
-def ipfp_batch(Phi, n, m, beta, max_sweeps, tol=None, log_u=None, log_v=None, omega=1.0):
+def ipfp_batch(Phi, n, m, beta, max_sweeps, tol=None, log_u=None, log_v=None, omega=1.0, translate=False):
     """Batch IPFP, Alg. 1 / Eq. iteration_matrix, in logs.
 
     Starts from u = v = 1 (Alg. 1 initialisation) unless a warm start
@@ -151,6 +209,14 @@ def ipfp_batch(Phi, n, m, beta, max_sweeps, tol=None, log_u=None, log_v=None, om
     omega != 1 (an extension, not in the paper) over-relaxes each update in
     the log domain, log u <- log u + omega * (update - log u), and likewise for
     v; a fixed point of the relaxed sweep is a fixed point of Eq. iteration.
+
+    translate (an extension, not in the paper): before each half-sweep, the
+    ``translation_step`` between the side just updated (the partner of the
+    half-sweep) and the side about to be updated: before the u step,
+    log v + tau, log u - tau; before the v step, log u + tau', log v - tau'.
+    Each step maximises the same concave dual as the half-sweeps, so the
+    fixed point is that of Eq. iteration. With tol, the residual is that of
+    the state after the first translation (the state the u step starts from).
 
     Returns a dict: log_u, log_v, sweeps (number of sweeps run), res_inf,
     res_l1 (of the returned state) and trace (res_inf before each sweep when
@@ -163,6 +229,8 @@ def ipfp_batch(Phi, n, m, beta, max_sweeps, tol=None, log_u=None, log_v=None, om
     trace = []
     sweeps = 0
     for _ in range(int(max_sweeps)):
+        if translate:
+            lv, lu, _ = translation_step(lv, lu, m, n)
         if tol is not None:
             r_inf, _, _ = row_residual(logA, n, lu, lv)
             trace.append(r_inf)
@@ -170,9 +238,13 @@ def ipfp_batch(Phi, n, m, beta, max_sweeps, tol=None, log_u=None, log_v=None, om
                 break
         if omega == 1.0:
             lu = half_sweep_x(logA, lv, n)
-            lv = half_sweep_y(logA, lu, m)
         else:
             lu = lu + omega * (half_sweep_x(logA, lv, n) - lu)
+        if translate:
+            lu, lv, _ = translation_step(lu, lv, n, m)
+        if omega == 1.0:
+            lv = half_sweep_y(logA, lu, m)
+        else:
             lv = lv + omega * (half_sweep_y(logA, lu, m) - lv)
         sweeps += 1
     r_inf, r_l1, _ = row_residual(logA, n, lu, lv)

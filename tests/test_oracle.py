@@ -506,3 +506,219 @@ def test_relaxation_cuts_sweeps_on_a_balanced_market():
     fast = oracle.ipfp_batch(Phi, f["n"], f["m"], 1.0, max_sweeps=20000, tol=1e-8, omega=1.6)
     assert fast["sweeps"] * 2 < plain["sweeps"]
     np.testing.assert_allclose(fast["log_u"], plain["log_u"], atol=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# Translation step (an extension): exact line search of the dual
+# ---------------------------------------------------------------------------
+
+def _line_argmax(f, lo=-40.0, hi=40.0):
+    """Brute-force maximiser of a concave function of one variable: a grid,
+    then golden-section search on the bracket around the best grid point."""
+    ts = np.linspace(lo, hi, 4001)
+    vals = [f(t) for t in ts]
+    i = int(np.argmax(vals))
+    a, b = ts[max(i - 1, 0)], ts[min(i + 1, len(ts) - 1)]
+    g = (np.sqrt(5.0) - 1.0) / 2.0
+    c, d = b - g * (b - a), a + g * (b - a)
+    for _ in range(200):
+        if f(c) > f(d):
+            b = d
+        else:
+            a = c
+        c, d = b - g * (b - a), a + g * (b - a)
+    return 0.5 * (a + b)
+
+
+@pytest.mark.parametrize("seed,shape,cap", [(41, (5, 7), True), (42, (6, 3), True), (43, (4, 4), False)])
+def test_translation_step_maximises_the_dual_on_its_line(seed, shape, cap):
+    """The closed-form tau is the maximiser of the full dual (pair sum
+    included) along (log u + tau, log v - tau), found by brute force, and
+    the dual rises."""
+    rng = np.random.default_rng(seed)
+    F, K, G, L, bx, by, n, m = _random_market(rng, *shape, cap=cap)
+    beta = 0.7
+    logA = oracle.log_kernel(oracle.phi_dense(F, K, G, L, bx, by), beta)
+    lu = rng.normal(-1.0, 0.8, shape[0])
+    lv = rng.normal(-2.5, 0.8, shape[1])
+    lu2, lv2, tau = oracle.translation_step(lu, lv, n, m)
+    t_bf = _line_argmax(lambda t: oracle.dual_value(logA, n, m, lu + t, lv - t))
+    assert abs(tau - t_bf) < 1e-7, (tau, t_bf)
+    np.testing.assert_allclose(lu2, lu + tau, atol=0)
+    np.testing.assert_allclose(lv2, lv - tau, atol=0)
+    assert oracle.dual_value(logA, n, m, lu2, lv2) >= oracle.dual_value(logA, n, m, lu, lv)
+    # with the sides exchanged the step is the same move
+    lv3, lu3, tau_y = oracle.translation_step(lv, lu, m, n)
+    assert abs(tau_y + tau) < 1e-12
+
+
+def test_translation_step_equalises_the_match_counts():
+    """At the step's optimum the derivative along the line, summed Eq. IPFP
+    rows minus summed columns, vanishes: sum n - sum u^2 = sum m - sum v^2."""
+    rng = np.random.default_rng(44)
+    for N, M in [(30, 20), (20, 30), (25, 25)]:
+        n = rng.uniform(0.2, 3.0, N)
+        m = rng.uniform(0.2, 3.0, M)
+        lu = rng.normal(0.5, 2.0, N)
+        lv = rng.normal(-3.0, 2.0, M)
+        lu2, lv2, _ = oracle.translation_step(lu, lv, n, m)
+        cx, cy = oracle.match_count(n, lu2, m, lv2)
+        assert abs(cx - cy) <= 1e-12 * (np.sum(n) + np.sum(m)), (cx, cy)
+
+
+@pytest.mark.parametrize("center_p,center_o,dm", [(0.0, 0.0, 0.0), (150.0, -200.0, 3.0), (-300.0, 250.0, -2.0),
+                                                  (-20.0, -25.0, 2.0 ** -30), (5.0, 4.0, -7.5)])
+def test_translation_step_against_high_precision(center_p, center_o, dm):
+    """tau against the positive root of P z^2 - Dm z - O = 0 solved with
+    60 significant digits, on potentials whose squares over- or underflow
+    float64 and for both signs of the mass difference."""
+    rng = np.random.default_rng(45)
+    lp = center_p + rng.normal(0.0, 1.0, 6)
+    lo = center_o + rng.normal(0.0, 1.0, 6)
+    # dyadic capacities: both sums, and so the mass difference, are exact in float64
+    mass_o = rng.integers(8, 17, 5) / 8.0
+    mass_p = np.concatenate([rng.integers(1, 5, 5) / 8.0, [0.0]])
+    mass_p[5] = np.sum(mass_o) + dm - np.sum(mass_p[:5]) + 8.0
+    mass_o = np.concatenate([mass_o, [8.0]])
+    dm_exact = mp.fsum([mp.mpf(float(x)) for x in mass_p]) - mp.fsum([mp.mpf(float(x)) for x in mass_o])
+    _, _, tau = oracle.translation_step(lp, lo, mass_p, mass_o)
+    mp.mp.dps = 60
+    P = mp.fsum([mp.e ** (2 * mp.mpf(float(x))) for x in lp])
+    O_ = mp.fsum([mp.e ** (2 * mp.mpf(float(x))) for x in lo])
+    z = (dm_exact + mp.sqrt(dm_exact ** 2 + 4 * P * O_)) / (2 * P)
+    tau_exact = mp.log(z) / 2
+    assert abs(tau - float(tau_exact)) <= 1e-12 * max(1.0, abs(float(tau_exact))), (tau, tau_exact)
+
+
+@pytest.mark.parametrize("shape", [(3, 4), (6, 6), (7, 2)])
+def test_translated_iteration_reaches_the_dual_fixed_point(shape):
+    rng = np.random.default_rng(46)
+    F, K, G, L, bx, by, n, m = _random_market(rng, *shape)
+    beta = 0.8
+    Phi = oracle.phi_dense(F, K, G, L, bx, by)
+    r = oracle.ipfp_batch(Phi, n, m, beta, max_sweeps=100000, tol=1e-13, translate=True)
+    assert r["res_inf"] <= 1e-12
+    a, b = _newton_dual(Phi, n, m, beta)
+    np.testing.assert_allclose(r["log_u"], a, atol=1e-11)
+    np.testing.assert_allclose(r["log_v"], b, atol=1e-11)
+
+
+def test_translated_sweep_by_hand():
+    """One translated sweep of a 2x2 market written out in the linear domain:
+    v e^{tau}, u e^{-tau} with z = e^{2 tau} the positive root of
+    (sum v^2) z^2 - (sum m - sum n) z - sum u^2 = 0; the printed u update;
+    u e^{tau'}, v e^{-tau'} with the roles exchanged; the printed v update."""
+    Phi = np.array([[0.4, -0.6], [1.0, 0.2]])
+    beta, n, m = 0.5, np.array([1.0, 2.0]), np.array([2.5, 1.0])
+    u, v = np.exp(np.array([-0.3, 0.1])), np.exp(np.array([0.2, -0.5]))
+    A = np.exp(Phi / (2 * beta))
+
+    def root(p2, o2, dmass):
+        return (dmass + np.sqrt(dmass * dmass + 4 * p2 * o2)) / (2 * p2)
+
+    z = root(np.sum(v * v), np.sum(u * u), np.sum(m) - np.sum(n))
+    v, u = v * np.sqrt(z), u / np.sqrt(z)
+    s = 0.5 * A @ v
+    u = np.sqrt(n + s * s) - s
+    z = root(np.sum(u * u), np.sum(v * v), np.sum(n) - np.sum(m))
+    u, v = u * np.sqrt(z), v / np.sqrt(z)
+    s = 0.5 * A.T @ u
+    v = np.sqrt(m + s * s) - s
+    r = oracle.ipfp_batch(Phi, n, m, beta, max_sweeps=1, log_u=np.array([-0.3, 0.1]),
+                          log_v=np.array([0.2, -0.5]), translate=True)
+    np.testing.assert_allclose(np.exp(r["log_u"]), u, rtol=1e-13)
+    np.testing.assert_allclose(np.exp(r["log_v"]), v, rtol=1e-13)
+
+
+def test_translated_iteration_ascends_the_dual():
+    """Every half-sweep and every translation step raises the dual."""
+    mk = make_market(40, 40, 8, sigma=0.5, seed=47, bias_x=True, bias_y=True, dtype="fp32")
+    f = mk.f64()
+    logA = oracle.log_kernel(oracle.phi_dense(f["F"], f["K"], f["G"], f["L"], f["bias_x"], f["bias_y"]), 0.5)
+    n, m = f["n"], f["m"]
+    lu, lv = np.zeros(40), np.zeros(40)
+    prev = oracle.dual_value(logA, n, m, lu, lv)
+    for _ in range(6):
+        for step in ("ty", "x", "tx", "y"):
+            if step == "ty":
+                lv, lu, _ = oracle.translation_step(lv, lu, m, n)
+            elif step == "x":
+                lu = oracle.half_sweep_x(logA, lv, n)
+            elif step == "tx":
+                lu, lv, _ = oracle.translation_step(lu, lv, n, m)
+            else:
+                lv = oracle.half_sweep_y(logA, lu, m)
+            cur = oracle.dual_value(logA, n, m, lu, lv)
+            assert cur >= prev - 1e-9 * abs(prev), (step, cur, prev)
+            prev = cur
+
+
+def test_translation_cuts_sweeps_on_a_balanced_market():
+    """The slow mode of a balanced market is the translation itself: with the
+    step, a 200 x 200 market with popularity biases reaches 1e-8 in a handful
+    of sweeps instead of thousands, at the same fixed point."""
+    mk = make_market(200, 200, 16, sigma=0.5, seed=48, bias_x=True, bias_y=True, dtype="fp32")
+    f = mk.f64()
+    Phi = oracle.phi_dense(f["F"], f["K"], f["G"], f["L"], f["bias_x"], f["bias_y"])
+    fast = oracle.ipfp_batch(Phi, f["n"], f["m"], 0.5, max_sweeps=200, tol=1e-8, translate=True)
+    assert fast["res_inf"] <= 1e-8 and fast["sweeps"] <= 12, fast["sweeps"]
+    plain = oracle.ipfp_batch(Phi, f["n"], f["m"], 0.5, max_sweeps=200, tol=1e-8)
+    assert plain["res_inf"] > 1e-3  # still far from it after 200 plain sweeps
+    a, b = _newton_dual(Phi, f["n"], f["m"], 0.5, iters=200)
+    np.testing.assert_allclose(fast["log_u"], a, atol=1e-7)
+    np.testing.assert_allclose(fast["log_v"], b, atol=1e-7)
+
+
+_TRANSLATION_STEP = O.translation_step
+
+
+def _bad_same_sign(lp, lo, mass_p, mass_o):
+    _, _, tau = _TRANSLATION_STEP(lp, lo, mass_p, mass_o)
+    return np.asarray(lp) + tau, np.asarray(lo) + tau, tau
+
+
+def _bad_no_half(lp, lo, mass_p, mass_o):
+    _, _, tau = _TRANSLATION_STEP(lp, lo, mass_p, mass_o)
+    return np.asarray(lp) + 2 * tau, np.asarray(lo) - 2 * tau, 2 * tau
+
+
+def _bad_masses_exchanged(lp, lo, mass_p, mass_o):
+    return _TRANSLATION_STEP(lp, lo, mass_o, mass_p)
+
+
+def _bad_other_root(lp, lo, mass_p, mass_o):
+    P = np.sum(np.exp(2 * np.asarray(lp)))
+    Oo = np.sum(np.exp(2 * np.asarray(lo)))
+    dm = float(np.sum(mass_p) - np.sum(mass_o))
+    tau = 0.5 * np.log(abs((dm - np.sqrt(dm * dm + 4 * P * Oo)) / (2 * P)))
+    return np.asarray(lp) + tau, np.asarray(lo) - tau, tau
+
+
+TRANSLATION_MISTAKES = {
+    "tau applied with the same sign to both sides": _bad_same_sign,
+    "tau without the 1/2 (log z)": _bad_no_half,
+    "masses of the two sides exchanged": _bad_masses_exchanged,
+    "the other root of the quadratic (its magnitude)": _bad_other_root,
+}
+
+
+def _translation_pins_pass():
+    try:
+        for args in [(41, (5, 7), True), (43, (4, 4), False)]:
+            test_translation_step_maximises_the_dual_on_its_line(*args)
+        test_translation_step_equalises_the_match_counts()
+        test_translated_sweep_by_hand()
+        test_translated_iteration_reaches_the_dual_fixed_point((3, 4))
+    except (AssertionError, ValueError, FloatingPointError, np.linalg.LinAlgError):
+        return False
+    return True
+
+
+def test_planted_translation_mistakes_are_caught(monkeypatch):
+    assert _translation_pins_pass()
+    for name, bad in TRANSLATION_MISTAKES.items():
+        with monkeypatch.context() as mpatch:
+            mpatch.setattr(O, "translation_step", bad)
+            mpatch.setattr(oracle, "translation_step", bad)
+            assert not _translation_pins_pass(), f"planted mistake not caught: {name}"
+    assert _translation_pins_pass()
