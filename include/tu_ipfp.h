@@ -117,7 +117,9 @@ tu_status tu_market_update_factors(tu_market_t mkt, const void* F, const void* K
                                    const void* L);
 
 /* Run nsweeps >= 0 full sweeps of Eq. iteration (u from v, then v from the new u;
- * Alg. 1 loop body / Alg. 2 loop body). If residual_out != NULL, synchronise and
+ * Alg. 1 loop body / Alg. 2 loop body), each half-sweep preceded by the
+ * translation step unless tu_market_set_translation(mkt, 0) turned it off
+ * (that step leaves the fixed point unchanged). If residual_out != NULL, synchronise and
  * store the row residual of the resulting potentials:
  *     max_x |u_x^2 + u_x sum_y A_xy v_y - n_x| / n_x     (row equations of Eq. IPFP),
  * which costs one extra half-sweep of work. */
@@ -189,10 +191,45 @@ tu_status tu_set_potentials(tu_market_t mkt, const float* log_u, const float* lo
  *                        tu_ipfp_solve applies it once the residual is below 0.1;
  *   omega = 0            automatic: tu_ipfp_solve runs plain sweeps until the
  *                        per-sweep decay q of the residual has settled, then uses
- *                        omega = 2 / (1 + sqrt(1 - q)) (successive over-relaxation);
+ *                        omega = 2 / (1 + sqrt(1 - q)) (successive over-relaxation),
+ *                        lowered linearly towards 1 over the last decade of the
+ *                        residual above tol (a relaxed sweep amplifies the FP32
+ *                        rounding of the row sums by about omega / (2 - omega));
+ * a fixed omega is applied as set, down to tol;
  * in both relaxed modes tu_ipfp_solve halves omega - 1 whenever the residual
  * grows tenfold over the best seen. Other values: TU_ERR_INVALID_ARG. */
 tu_status tu_market_set_relaxation(tu_market_t mkt, double omega);
+
+/* The relaxation controller of tu_ipfp_solve on a given residual trace, for
+ * tests and tuning (no counterpart in the paper; no CUDA call, no market).
+ * A fresh controller with setting `omega` (0 or [1, 2), as
+ * tu_market_set_relaxation) observes, in order, the residual residual[i] read
+ * after done[i] sweeps (done strictly increasing, >= 1) against `tol`, and
+ * omega_out[i] receives the factor it sets for the sweeps that follow.
+ * Invalid settings, tol < 0, count < 0, NULL arrays with count > 0 or a
+ * non-increasing done: TU_ERR_INVALID_ARG. */
+tu_status tu_relax_schedule(double omega, double tol, const int* done, const double* residual, int count,
+                            double* omega_out);
+
+/* Translation step, an acceleration the paper does not have (its Sec. 5 names
+ * acceleration techniques from optimal transport as future work). IPFP solves
+ * the row equations of Eq. IPFP exactly, then the column equations: block
+ * coordinate ascent on the concave dual
+ *     D(a, b) = sum n a + sum m b - 1/2 sum e^{2a} - 1/2 sum e^{2b} - sum_xy A_xy e^{a_x + b_y}
+ * (a = log u, b = log v), whose gradient is Eq. IPFP. With enable = 1 (the
+ * default) every half-sweep of a sweep is preceded by the exact maximisation
+ * of D along one more direction: the side updated last moves by +tau in log
+ * space and the side about to be updated by -tau. That move leaves every
+ * mu_xy = A_xy u_x v_y unchanged, so tau has a closed form from sum u^2,
+ * sum v^2, sum n and sum m (O(N + M) work, no pair work): tau = 1/2 log z, z the
+ * positive root of P z^2 - (sum mass_P - sum mass_O) z - O = 0 with P, O the
+ * sums of squared potentials of the two sides. Every step raises D, so the
+ * iteration reaches the fixed point of Eq. iteration; on balanced markets,
+ * whose slow mode is exactly this move (plain IPFP needs O(N) sweeps there),
+ * it needs a handful of sweeps instead. enable = 0: Eq. iteration exactly.
+ * The certifying pass of tu_ipfp_sweep's residual_out and of the solves
+ * never moves the state. Other values: TU_ERR_INVALID_ARG. */
+tu_status tu_market_set_translation(tu_market_t mkt, int enable);
 
 /* Blocks of k > 1 sweeps replay a captured CUDA graph on the market's stream
  * (enable = 1, the default), or are launched kernel by kernel (0). Capturing
@@ -302,8 +339,9 @@ typedef struct tu_batch* tu_batch_t;
 
 /* Group `count` markets (1 <= count <= 65536), all created with TU_PATH_FUSED
  * on the current device with the same packed width (2d rounded up to 64 or
- * 128). The batch references the markets (their buffers, tensor maps, sigma
- * and relaxation setting at creation); destroy the batch before any of them.
+ * 128). The batch references the markets (their buffers, tensor maps, sigma,
+ * relaxation and translation settings at creation); destroy the batch before
+ * any of them.
  * Batch work is ordered on `stream` (a cudaStream_t, or NULL for the legacy
  * default stream); every batch call first waits for work already enqueued on
  * the members' own streams, and the caller orders later member calls after

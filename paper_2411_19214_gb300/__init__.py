@@ -77,6 +77,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tu_selftest_wait_timeout": (I32, [D, ctypes.POINTER(D)]),
         "tu_set_checked_mode": (I32, [I32]),
         "tu_market_set_small_tiles": (I32, [V, I32]),
+        "tu_market_set_translation": (I32, [V, I32]),
+        "tu_relax_schedule": (I32, [D, D, V, V, I32, V]),
         "tu_guard_violations": (I64, [ctypes.c_char_p, I64]),
         "tu_market_query": (I32, [V, ctypes.POINTER(I32), ctypes.POINTER(D), ctypes.POINTER(D),
                                   ctypes.POINTER(I64)]),
@@ -315,6 +317,25 @@ def tu_market_set_small_tiles(h: int, enable: bool) -> None:
     _check(load().tu_market_set_small_tiles(h, int(bool(enable))), "tu_market_set_small_tiles", h)
 
 
+def tu_relax_schedule(omega: float, tol: float, done, residual) -> np.ndarray:
+    """The factors the solve's relaxation controller (setting ``omega``) sets
+    after observing residual[i] at done[i] sweeps (host-only, no GPU)."""
+    d = np.ascontiguousarray(done, dtype=np.int32)
+    r = np.ascontiguousarray(residual, dtype=np.float64)
+    if d.shape != r.shape or d.ndim != 1:
+        raise ValueError("done and residual must be 1-D arrays of one length")
+    out = np.empty(len(d), np.float64)
+    st = load().tu_relax_schedule(float(omega), float(tol), d.ctypes.data, r.ctypes.data, len(d), out.ctypes.data)
+    _check(st, "tu_relax_schedule")
+    return out
+
+
+def tu_market_set_translation(h: int, enable: bool) -> None:
+    """Translation step before every half-sweep of a sweep (default on; same
+    fixed point): off gives Eq. iteration exactly."""
+    _check(load().tu_market_set_translation(h, int(bool(enable))), "tu_market_set_translation", h)
+
+
 def tu_market_use_graphs(h: int, enable: bool) -> None:
     """Replay captured CUDA graphs for blocks of sweeps (default), or launch directly (multi-threaded callers)."""
     _check(load().tu_market_use_graphs(h, int(bool(enable))), "tu_market_use_graphs", h)
@@ -435,6 +456,9 @@ class Market:
 
     def set_relaxation(self, omega: float) -> None:
         tu_market_set_relaxation(self.handle, omega)
+
+    def set_translation(self, enable: bool) -> None:
+        tu_market_set_translation(self.handle, enable)
 
     def potentials(self):
         import torch

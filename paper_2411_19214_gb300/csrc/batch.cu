@@ -50,6 +50,7 @@ size_t round4(size_t v) { return (v + 3) & ~(size_t)3; }
 
 static_assert(alignof(BatchDesc) >= 128 && sizeof(BatchDesc) % 128 == 0,
               "descriptor arrays keep every tensor map 128-byte aligned");
+static_assert(kPrepThreads == kTauThreads, "the batched translation step runs the single-market routine's block size");
 
 }  // namespace
 
@@ -92,30 +93,44 @@ namespace {
 
 // Partner preparation of a listed market: shift = max ell, then the FP32
 // vector g = (ell - shift) log2(e), -inf padded (the single-market kernels
-// compute the same values in two launches).
+// compute the same values in two launches). In sweeps (sweep = 1) of a market
+// with the translation step, tau comes first, from the same routine and block
+// size as the single-market k_prep_tau (so the same bits), and the FP64 state
+// moves: partner log u and ell by +tau, own log u and ell by -tau; g is written
+// from the values before the move (it depends on ell - max ell only) and the
+// shift becomes max ell + tau.
 __global__ void __launch_bounds__(kPrepThreads) k_batch_prep(const BatchDesc* __restrict__ desc,
                                                             const int* __restrict__ list,
-                                                            const int* __restrict__ n_list) {
+                                                            const int* __restrict__ n_list, int sweep) {
   if ((int)blockIdx.x >= *n_list) return;
   const BatchDesc& d = desc[list[blockIdx.x]];
   __shared__ double red[kPrepThreads / 32];
-  __shared__ double shift_s;
+  const bool translate = sweep && d.translate;
+  const double tau =
+      translate ? block_translation_tau(d.partner_log_u, d.partner_rows, d.log_u, d.rows, d.dm, red) : 0.0;
   double mx = -INFINITY;
   for (int64_t i = threadIdx.x; i < d.partner_rows; i += blockDim.x) mx = fmax(mx, d.partner_ell[i]);
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = mx;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double b = -INFINITY;
-    for (int w = 0; w < kPrepThreads / 32; ++w) b = fmax(b, red[w]);
-    if (!(b > -INFINITY && b < INFINITY)) b = 0.0;  // non-finite potentials are reported elsewhere
-    shift_s = b;
-    *d.lmax = b;
+  double shift = block_reduce_max(mx, red);
+  if (!(shift > -INFINITY && shift < INFINITY)) shift = 0.0;  // non-finite potentials are reported elsewhere
+  if (threadIdx.x == 0) *d.lmax = shift + tau;
+  for (int64_t i = threadIdx.x; i < d.partner_rows_pad; i += blockDim.x) {
+    if (i < d.partner_rows) {
+      const double e = d.partner_ell[i];
+      d.g[i] = (float)((e - shift) * 1.4426950408889634);
+      if (translate) {
+        d.partner_ell[i] = e + tau;
+        d.partner_log_u[i] += tau;
+      }
+    } else {
+      d.g[i] = -INFINITY;
+    }
   }
-  __syncthreads();
-  const double shift = shift_s;
-  for (int64_t i = threadIdx.x; i < d.partner_rows_pad; i += blockDim.x)
-    d.g[i] = i < d.partner_rows ? (float)((d.partner_ell[i] - shift) * 1.4426950408889634) : -INFINITY;
+  if (translate) {
+    for (int64_t i = threadIdx.x; i < d.rows; i += blockDim.x) {
+      d.log_u[i] -= tau;
+      d.ell[i] -= tau;
+    }
+  }
 }
 
 // FP64 reduction of a listed market's per-tile partials into its result slots.
@@ -350,7 +365,7 @@ cudaError_t enqueue_half(tu_batch* b, int si, int side, int residual, int update
   const Schedule& S = b->sched[si];
   const int* n = S.dev;
   const int* list = S.dev + S.off_list;
-  k_batch_prep<<<b->count, kPrepThreads, 0, b->stream>>>(b->desc_dev[side], list, n);
+  k_batch_prep<<<b->count, kPrepThreads, 0, b->stream>>>(b->desc_dev[side], list, n, update);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if ((e = profile_mark(b, true)) != cudaSuccess) return e;
@@ -539,6 +554,9 @@ tu_status tu_batch_create(const tu_market_t* markets, int count, void* stream, t
       d.log_u = own.log_u;
       d.ell = own.ell;
       d.partner_ell = par.ell;
+      d.partner_log_u = par.log_u;
+      d.dm = par.sum_mass - own.sum_mass;
+      d.translate = m->translate ? 1 : 0;
       d.g = par.pvec;
       d.lmax = par.lmax;
       d.omega = b->omega_dev + i;
@@ -665,10 +683,12 @@ tu_status tu_batch_solve(tu_batch_t b, double tol, int max_iter, int warm_start,
       active.push_back(mk);
     }
   }
-  int done = 0;
+  int done = 0, last_k = 0;
+  std::vector<double> r_prev(count, -1.0), r_last(count, -1.0);
   while (!active.empty() && done < max_iter) {
     // sweeps between host checks: about 2e9 pair evaluations per check, 1..64
-    // (at most 16 while a market adapts its relaxation factor)
+    // (at most 16 while a market adapts its relaxation factor), and no more than
+    // the active market closest to tol needs at its measured decay (plan_block)
     double pairs = 0.0;
     bool relaxing = false;
     for (int mk : active) {
@@ -678,7 +698,13 @@ tu_status tu_batch_solve(tu_batch_t b, double tol, int max_iter, int warm_start,
     int block = (int)std::ceil(2e9 / pairs);
     block = block < 1 ? 1 : (block > 64 ? 64 : block);
     if (relaxing && block > 16) block = 16;
-    const int k = (max_iter - done) < block ? (max_iter - done) : block;
+    int k = block;
+    for (int mk : active) {
+      const int want = plan_block(last_k, r_prev[mk], r_last[mk], tol, block);
+      if (want < k) k = want;
+    }
+    if (k > max_iter - done) k = max_iter - done;
+    last_k = k;
     TB_TRY(sched_set(b, b->sched[0], active));
     TB_TRY(enqueue_sweeps(b, k));
     TB_TRY(read_results(b));
@@ -693,6 +719,8 @@ tu_status tu_batch_solve(tu_batch_t b, double tol, int max_iter, int warm_start,
         continue;
       }
       const double r = res(b, mk, kResXInf);
+      r_prev[mk] = r_last[mk];
+      r_last[mk] = r;
       if (r <= tol) {
         cand.push_back(mk);
         continue;

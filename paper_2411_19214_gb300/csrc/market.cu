@@ -426,7 +426,8 @@ cudaError_t profile_mark(tu_market* m, bool start) {
 // One half-sweep: prepare the partner potentials, run the pass, reduce partials.
 cudaError_t enqueue_half(tu_market* m, int side, int residual, int update) {
   Side& partner = side == 0 ? m->Y : m->X;
-  cudaError_t e = launch_prep(m, partner, m->path == TU_PATH_FUSED ? 1 : 0);
+  // sweeps (update = 1) take the translation step; a certifying pass leaves the state as it is
+  cudaError_t e = launch_prep(m, partner, m->path == TU_PATH_FUSED ? 1 : 0, update && m->translate ? 1 : 0);
   if (e != cudaSuccess) return e;
   if ((e = profile_mark(m, true)) != cudaSuccess) return e;
   int nparts = 0;
@@ -567,6 +568,10 @@ double tu::RelaxControl::observe(int done, double r, double tol) {
       if (target < 1.01) target = 1.0;
       best = r;
     }
+    if (cfg > 1.0) {  // a fixed factor is applied as set (only the safeguard above lowers it)
+      omega = target;
+      return omega;
+    }
     double w = std::log10(r / tol);
     w = w < 0.0 ? 0.0 : (w > 1.0 ? 1.0 : w);
     const double next = 1.0 + (target - 1.0) * w;
@@ -665,6 +670,7 @@ void tu_market_destroy(tu_market_t m) {
   }
   dev_free(m, m->partials);
   dev_free(m, m->mpartials);
+  dev_free(m, m->tau_dev);
   dev_free(m, m->results);
   dev_free(m, m->err_dev);
   dev_free(m, m->staging);
@@ -742,6 +748,7 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
   if ((st = side_alloc(m, m->Y, D.M, D.bias_y != nullptr)) != TU_OK) return bail(st);
   if ((st = dev_alloc(m, &m->partials, (size_t)kMaxPartials * 4)) != TU_OK) return bail(st);
   if ((st = dev_alloc(m, &m->mpartials, (size_t)kMaxPartials)) != TU_OK) return bail(st);
+  if ((st = dev_alloc(m, &m->tau_dev, 1)) != TU_OK) return bail(st);
   if ((st = dev_alloc(m, &m->results, (size_t)kResSlots)) != TU_OK) return bail(st);
   if ((st = dev_alloc(m, &m->err_dev, 1)) != TU_OK) return bail(st);
   {
@@ -885,6 +892,32 @@ tu_status tu_market_set_small_tiles(tu_market_t m, int enable) {
   return TU_OK;
 }
 
+tu_status tu_relax_schedule(double omega, double tol, const int* done, const double* residual, int count,
+                            double* omega_out) {
+  if (!(omega == 0.0 || (omega >= 1.0 && omega < 2.0)) || !(tol >= 0.0) || count < 0) return TU_ERR_INVALID_ARG;
+  if (count > 0 && (done == nullptr || residual == nullptr || omega_out == nullptr)) return TU_ERR_INVALID_ARG;
+  RelaxControl ctl(omega);
+  for (int i = 0; i < count; ++i) {
+    if (done[i] < 1 || (i > 0 && done[i] <= done[i - 1])) return TU_ERR_INVALID_ARG;
+    omega_out[i] = ctl.observe(done[i], residual[i], tol);
+  }
+  return TU_OK;
+}
+
+tu_status tu_market_set_translation(tu_market_t m, int enable) {
+  TU_TRY(check_live(m));
+  if (enable != 0 && enable != 1) return fail(m, TU_ERR_INVALID_ARG, "enable must be 0 or 1");
+  if ((enable != 0) != m->translate && m->graph != nullptr) {
+    // captured sweeps use the preparation of the previous setting
+    TU_CK(m, cudaStreamSynchronize(m->stream));
+    cudaGraphExecDestroy(m->graph);
+    m->graph = nullptr;
+    m->graph_sweeps = 0;
+  }
+  m->translate = enable != 0;
+  return relax_reset(m);
+}
+
 tu_status tu_market_relax_update(tu_market_t m, double tol) {
   TU_TRY(check_live(m));
   if (!(tol >= 0.0)) return fail(m, TU_ERR_INVALID_ARG, "tol < 0");
@@ -945,12 +978,14 @@ tu_status tu_ipfp_solve(tu_market_t m, double tol, int max_iter, int warm_start,
     TU_CK(m, launch_reset_potentials(m, m->Y));
   }
   TU_TRY(clear_results(m));
-  // sweeps between host checks: about 2e9 pair evaluations per check, 1..64
+  // sweeps between host checks: planned from the measured decay (plan_block),
+  // at most about 2e9 pair evaluations per check and 64 sweeps
   const double pairs = (double)m->N * (double)m->M;
   int block = (int)std::ceil(2e9 / pairs);
   if (block < 1) block = 1;
   if (block > 64) block = 64;
-  int done = 0;
+  int done = 0, last_k = 0;
+  double r_prev = -1.0, r_last = -1.0;
   double res_inf = INFINITY, res_l1 = INFINITY;
   tu_status status = TU_ERR_NOT_CONVERGED;
   // over-relaxation (RelaxControl): omega is re-chosen after every block
@@ -969,12 +1004,16 @@ tu_status tu_ipfp_solve(tu_market_t m, double tol, int max_iter, int warm_start,
     // sweep until the residual folded into the X half-sweeps (state entering
     // the last sweep of a block) reaches tol, then certify the returned state
     while (done < max_iter) {
-      const int k = (max_iter - done) < block ? (max_iter - done) : block;
+      int k = plan_block(last_k, r_prev, r_last, tol, block);
+      if (k > max_iter - done) k = max_iter - done;
       TU_TRY(enqueue_sweeps(m, k));
       m->sweeps_enqueued += k;
       TU_TRY(read_results(m));
       done += k;
       const double r = m->results_host[kResXInf];
+      r_prev = r_last;
+      r_last = r;
+      last_k = k;
       if (r <= tol) break;
       if (!relax) continue;
       const double next = ctl.observe(done, r, tol);
@@ -1030,7 +1069,7 @@ tu_status tu_ipfp_solve_ranking(tu_market_t m, int k, int64_t sample, int check_
   auto rank_lists = [&]() -> tu_status {
     for (int side = 0; side < 2; ++side) {
       const size_t off = side == 0 ? 0 : n0;
-      cudaError_t e = launch_prep(m, side == 0 ? m->Y : m->X, m->path == TU_PATH_FUSED ? 1 : 0);
+      cudaError_t e = launch_prep(m, side == 0 ? m->Y : m->X, m->path == TU_PATH_FUSED ? 1 : 0, 0);
       if (e == cudaSuccess) {
         if (m->path == TU_PATH_FUSED) {
           float* hv = reinterpret_cast<float*>(buf + 2 * nidx);
@@ -1121,7 +1160,7 @@ tu_status tu_mu_block(tu_market_t m, int64_t x0, int64_t nx, int64_t y0, int64_t
   TU_TRY(output_view(m, out, bytes, 0, &dst, &host));
   if (m->path == TU_PATH_FUSED) {
     // Y potentials prepared in log2 mode, then the tensor-core mu epilogue
-    TU_CK(m, launch_prep(m, m->Y, 1));
+    TU_CK(m, launch_prep(m, m->Y, 1, 0));
     TU_CK(m, launch_fused_mu(m, x0, nx, y0, ny, static_cast<float*>(dst), ld));
   } else {
     TU_CK(m, launch_mu_block(m, x0, nx, y0, ny, static_cast<float*>(dst), ld));
@@ -1162,7 +1201,7 @@ tu_status tu_topk_partners(tu_market_t m, int side, int k, int64_t row0, int64_t
     }
     float* hv = static_cast<float*>(m->aux);
     int32_t* hi_ = reinterpret_cast<int32_t*>(hv + (size_t)nrows * k);
-    TU_CK(m, launch_prep(m, side == 0 ? m->Y : m->X, 1));
+    TU_CK(m, launch_prep(m, side == 0 ? m->Y : m->X, 1, 0));
     TU_CK(m, launch_fused_topk(m, side, k, row0, nrows, static_cast<int32_t*>(di), static_cast<float*>(dv), hv, hi_));
   } else {
     TU_CK(m, launch_topk(m, side, k, row0, nrows, static_cast<int32_t*>(di), static_cast<float*>(dv)));

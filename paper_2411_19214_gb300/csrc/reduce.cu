@@ -161,12 +161,29 @@ __global__ void k_prep_max(const double* __restrict__ ell, int64_t rows, double*
   }
 }
 
+// Translation step of a sweep's half-sweep (one CTA of kTauThreads): tau from
+// the two sides' potentials, into *tau_out. The batched preparation computes
+// the same value with the same routine and block size.
+__global__ void __launch_bounds__(kTauThreads) k_prep_tau(const double* __restrict__ log_p, int64_t rows_p,
+                                                          const double* __restrict__ log_o, int64_t rows_o, double dm,
+                                                          double* __restrict__ tau_out) {
+  __shared__ double red[kTauThreads / 32];
+  const double tau = block_translation_tau(log_p, rows_p, log_o, rows_o, dm, red);
+  if (threadIdx.x == 0) *tau_out = tau;
+}
+
 // Partner preparation, phase 2: shift = max ell; write the vector the
 // half-sweep consumes. fused_mode 1: (ell - shift) * log2(e), padding -inf
 // (exp2 of it is 0); fused_mode 0: exp(ell - shift), padding 0.
-__global__ void k_prep_write(const double* __restrict__ ell, int64_t rows, int64_t rows_pad,
-                             const double* __restrict__ mpartials, int nparts, int fused_mode,
-                             float* __restrict__ out, double* __restrict__ lmax) {
+// With tau (the translation step, computed by k_prep_tau), the FP64 state
+// moves: log p, ell_p += tau (partner side), log o, ell_o -= tau (own side).
+// The prepared vector depends only on ell_p - max ell_p, which the move leaves
+// unchanged, so it is written from the values before the move and the shift
+// becomes max ell_p + tau.
+__global__ void k_prep_write(double* __restrict__ ell, double* __restrict__ log_p, int64_t rows, int64_t rows_pad,
+                             double* __restrict__ log_o, double* __restrict__ ell_o, int64_t rows_o,
+                             const double* __restrict__ tau_in, const double* __restrict__ mpartials, int nparts,
+                             int fused_mode, float* __restrict__ out, double* __restrict__ lmax) {
   __shared__ double red[kThreads / 32];
   __shared__ double shift_s;
   double mx = -INFINITY;
@@ -174,26 +191,38 @@ __global__ void k_prep_write(const double* __restrict__ ell, int64_t rows, int64
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = mx;
   __syncthreads();
+  const double tau = tau_in != nullptr ? *tau_in : 0.0;
   if (threadIdx.x == 0) {
     double b = -INFINITY;
     for (int w = 0; w < kThreads / 32; ++w) b = fmax(b, red[w]);
     if (!(b > -INFINITY && b < INFINITY)) b = 0.0;  // non-finite potentials are reported elsewhere
     shift_s = b;
-    if (blockIdx.x == 0) *lmax = b;
+    if (blockIdx.x == 0) *lmax = b + tau;
   }
   __syncthreads();
   const double shift = shift_s;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows_pad;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    float v;
-    if (i < rows) {
-      // the FP64 state is rounded once, to the FP32 vector the half-sweep streams
-      const double z = ell[i] - shift;
-      v = fused_mode ? (float)(z * 1.4426950408889634) : (float)exp(z);
-    } else {
-      v = fused_mode ? -INFINITY : 0.0f;
+  const int64_t n = tau_in != nullptr && rows_o > rows_pad ? rows_o : rows_pad;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i < rows_pad) {
+      float v;
+      if (i < rows) {
+        // the FP64 state is rounded once, to the FP32 vector the half-sweep streams
+        const double e = ell[i];
+        const double z = e - shift;
+        v = fused_mode ? (float)(z * 1.4426950408889634) : (float)exp(z);
+        if (tau_in != nullptr) {
+          ell[i] = e + tau;
+          log_p[i] += tau;
+        }
+      } else {
+        v = fused_mode ? -INFINITY : 0.0f;
+      }
+      out[i] = v;
     }
-    out[i] = v;
+    if (tau_in != nullptr && i < rows_o) {
+      log_o[i] -= tau;
+      ell_o[i] -= tau;
+    }
   }
 }
 
@@ -321,12 +350,18 @@ cudaError_t launch_pack_fp8(tu_market* m, Side& s, const float* A, const float* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_prep(tu_market* m, Side& partner, int fused_mode) {
+cudaError_t launch_prep(tu_market* m, Side& partner, int fused_mode, int translate) {
+  Side& own = &partner == &m->Y ? m->X : m->Y;
   int g1 = grid_for(partner.rows, m->num_sms, 4);
   if (g1 > kMaxPartials) g1 = kMaxPartials;
   k_prep_max<<<g1, kThreads, 0, m->stream>>>(partner.ell, partner.rows, m->mpartials);
-  const int g2 = grid_for(partner.rows_pad, m->num_sms, 4);
-  k_prep_write<<<g2, kThreads, 0, m->stream>>>(partner.ell, partner.rows, partner.rows_pad, m->mpartials, g1,
+  if (translate)
+    k_prep_tau<<<1, kTauThreads, 0, m->stream>>>(partner.log_u, partner.rows, own.log_u, own.rows,
+                                                 partner.sum_mass - own.sum_mass, m->tau_dev);
+  const int64_t n2 = translate && own.rows > partner.rows_pad ? own.rows : partner.rows_pad;
+  const int g2 = grid_for(n2, m->num_sms, 4);
+  k_prep_write<<<g2, kThreads, 0, m->stream>>>(partner.ell, partner.log_u, partner.rows, partner.rows_pad, own.log_u,
+                                                own.ell, own.rows, translate ? m->tau_dev : nullptr, m->mpartials, g1,
                                                 fused_mode, partner.pvec, partner.lmax);
   return cudaGetLastError();
 }

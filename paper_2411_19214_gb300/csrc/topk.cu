@@ -164,7 +164,7 @@ cudaError_t launch_topk(tu_market* m, int side, int k, int64_t row0, int64_t nro
   Side& own = side == 0 ? m->X : m->Y;
   Side& par = side == 0 ? m->Y : m->X;
   // the partner vector in log2 mode: g = (ell - shift) log2(e), -inf padded
-  cudaError_t e = launch_prep(m, par, 1);
+  cudaError_t e = launch_prep(m, par, 1, 0);
   if (e != cudaSuccess) return e;
   const float* A = side == 0 ? m->Ahat : m->AhatT;
   const int64_t ld = side == 0 ? m->ldA : m->ldN;

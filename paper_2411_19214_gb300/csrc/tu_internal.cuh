@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <string>
 #include <utility>
 #include <vector>
@@ -58,11 +59,12 @@ struct Side {
 
 // Over-relaxation controller of the solve loops (host side, one per market).
 // Plain sweeps until the residual is below 0.1 and (in automatic mode) the
-// per-sweep decay q of the plain iteration has settled, then
-// omega = 2 / (1 + sqrt(1 - q)) (successive over-relaxation), tapered towards
-// 1 as the residual approaches tol: the relaxed sweep amplifies the FP32
-// rounding of the row sums by about omega / (2 - omega). The excess over 1 is
-// halved whenever the residual grows tenfold over the best seen.
+// per-sweep decay q of the plain iteration has settled, then the fixed factor,
+// or in automatic mode omega = 2 / (1 + sqrt(1 - q)) (successive
+// over-relaxation) tapered towards 1 over the last decade above tol (the
+// relaxed sweep amplifies the FP32 rounding of the row sums by about
+// omega / (2 - omega)). In both modes the excess over 1 is halved whenever the
+// residual grows tenfold over the best seen.
 struct RelaxControl {
   static constexpr int kProbe = 10;  // sweeps between convergence-rate estimates
   double cfg = 1.0;                  // 1: plain; (1, 2): fixed; 0: automatic
@@ -77,6 +79,23 @@ struct RelaxControl {
   // after `done` sweeps (r > tol). Returns the omega of the next block.
   double observe(int done, double r, double tol);
 };
+
+// Sweeps in the next block of a solve loop (the residual is read back between
+// blocks). The first block is one sweep; each later one is at most twice the
+// previous block, cut to the sweeps the per-sweep decay measured over the last
+// block needs to take the residual to tol, and at most `cap`. r_prev and r are
+// the residuals read after the last two blocks (r_prev < 0: none yet), last_k
+// the sweeps of the last block (0: none yet).
+inline int plan_block(int last_k, double r_prev, double r, double tol, int cap) {
+  int k = last_k <= 0 ? 1 : 2 * last_k;
+  if (last_k > 0 && r_prev > 0.0 && r > tol && r < r_prev && tol > 0.0) {
+    const double log_q = std::log(r / r_prev) / (double)last_k;
+    const double need = std::ceil(std::log(tol / r) / log_q);
+    if (need >= 1.0 && need < (double)k) k = (int)need;
+  }
+  if (k > cap) k = cap;
+  return k < 1 ? 1 : k;
+}
 
 }  // namespace tu
 
@@ -93,8 +112,9 @@ struct tu_market {
   tu::Side X, Y;
   float* Ahat = nullptr;     // dense path: N x ldA fp32
   int64_t ldA = 0;
-  double* partials = nullptr;   // kMaxPartials x 3 doubles
+  double* partials = nullptr;   // kMaxPartials x 4 doubles
   double* mpartials = nullptr;  // kMaxPartials doubles (max reduction)
+  double* tau_dev = nullptr;    // device scalar: the translation step of the current half-sweep
   float* AhatT = nullptr;       // dense path: transpose of A-hat, M x ldN fp32
   int64_t ldN = 0;
   double* results = nullptr;       // device, kResSlots
@@ -109,6 +129,7 @@ struct tu_market {
   int graph_sweeps = 0;
   bool use_graphs = true;          // tu_market_use_graphs
   bool small_tiles = true;         // tu_market_set_small_tiles: 128-row own tiles when they fit one wave
+  bool translate = true;           // tu_market_set_translation: translation step before every half-sweep
   bool poisoned = false;
   std::string last_error;
   // benchmark timing (tu_profile_enable / tu_profile_read)
@@ -136,7 +157,9 @@ struct tu_market {
 namespace tu {
 
 // reduce.cu
-cudaError_t launch_prep(tu_market* m, Side& partner, int fused_mode);
+// Prepare the partner's FP32 vector and shift for a half-sweep of the other
+// side; with translate, first apply the translation step between the two sides.
+cudaError_t launch_prep(tu_market* m, Side& partner, int fused_mode, int translate);
 cudaError_t launch_finalize(tu_market* m, int nparts, int is_x, int residual);
 cudaError_t launch_pack_factors(tu_market* m, Side& s, const void* A, const void* B, int src_dtype);
 cudaError_t launch_init_side(tu_market* m, Side& s, const float* bias_dev, int has_bias);
@@ -190,10 +213,13 @@ struct BatchDesc {
   const double* mass;          // own capacities
   double* log_u;               // own potentials (in: old, out: new)
   double* ell;                 // own ell (out)
-  const double* partner_ell;   // partner ell (read by the preparation kernel)
+  double* partner_ell;         // partner ell (read, and moved by the translation step, in the preparation kernel)
+  double* partner_log_u;       // partner log potentials (moved by the translation step)
   float* g;                    // partner prepared vector (written by the preparation kernel)
   double* lmax;                // partner shift (written by the preparation kernel)
   const double* omega;         // over-relaxation factor of this market (device scalar)
+  double dm;                   // sum of partner capacities - sum of own capacities (translation step)
+  int translate;               // the market's translation-step setting at batch creation
   int64_t rows;                // own users
   int64_t partner_rows;        // partner users
   int64_t partner_rows_pad;    // partner vector length (multiple of kRowPad)
@@ -260,12 +286,15 @@ struct RowResult {
 // With residual, r = u_old^2 + 2 u_old s - n is the row equation of Eq. IPFP
 // evaluated at the state entering the half-sweep.
 //
-// Precision: the sums are FP32, so every transcendental here is evaluated in
-// FP32 (FP64 transcendentals are slow on this part) while the additions whose
-// operands may be large and cancel (log s, log u, ell: |.| up to ~100 with
-// popularity biases) stay in FP64. For z = log s - 1/2 log n > 0,
+// Precision: the sums are FP32, so the transcendentals of the update are
+// evaluated in FP32 (FP64 transcendentals are slow on this part) while the
+// additions whose operands may be large and cancel (log s, log u, ell: |.| up
+// to ~100 with popularity biases) stay in FP64. For z = log s - 1/2 log n > 0,
 // asinh(e^z) = z + c(z) with c(z) = log1p(sqrt(1 + e^{-2z})) in (ln 2, 0.89],
 // so only the bounded correction c is rounded to FP32 (absolute error ~1e-7).
+// The terms of the FP64 reductions (u^2 and 2 u s of the residual, u^2 of the
+// match count) are FP64 exponentials of the FP64 state: two or three per row
+// and half-sweep, against thousands of pair terms.
 //
 // omega != 1 over-relaxes the update in the log domain:
 // log u <- log u_old + omega * (update - log u_old) (same fixed point).
@@ -277,8 +306,7 @@ __device__ __forceinline__ RowResult row_update(double ln_sum, double shift, flo
   o.r_abs = 0.0;
   if (residual) {
     // r = u^2 + 2 u s - n with u^2 = e^{2 log u}, 2 u s = e^{log u + log s + ln 2}
-    const double r = (double)expf((float)(2.0 * log_u_old)) +
-                     (double)expf((float)(log_u_old + log_s + 0.69314718055994530942)) - mass;
+    const double r = exp(2.0 * log_u_old) + exp(log_u_old + log_s + 0.69314718055994530942) - mass;
     o.r_abs = fabs(r);
     o.r_rel = fabs(r) / mass;
   }
@@ -295,8 +323,97 @@ __device__ __forceinline__ RowResult row_update(double ln_sum, double shift, flo
   const double lu = omega == 1.0 ? lu_upd : log_u_old + omega * (lu_upd - log_u_old);
   o.log_u = lu;
   o.ell = lu + (double)b2s;
-  o.u2 = (double)expf((float)(2.0 * lu));
+  o.u2 = exp(2.0 * lu);
   return o;
+}
+
+// ---- translation step --------------------------------------------------------
+// Block size of every kernel that computes the translation step. The single-
+// market preparation and the batched one run the same routine with the same
+// block size, so both give the same tau bit for bit (the batch's potentials
+// stay bit-identical to the market's own sweeps).
+constexpr int kTauThreads = 512;
+
+// Block-wide reductions (every thread returns the result; `red` holds
+// blockDim.x / 32 doubles). Sums in a fixed order: a butterfly within each warp
+// (lane 0's value is kept), then the warps in order.
+__device__ __forceinline__ double block_reduce_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = v;
+  __syncthreads();
+  double b = -INFINITY;
+  for (int w = 0; w < (int)blockDim.x / 32; ++w) b = fmax(b, red[w]);
+  __syncthreads();
+  return b;
+}
+__device__ __forceinline__ double block_reduce_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = v;
+  __syncthreads();
+  double b = 0.0;
+  for (int w = 0; w < (int)blockDim.x / 32; ++w) b = __dadd_rn(b, red[w]);
+  __syncthreads();
+  return b;
+}
+
+// log sum_i exp(2 x_i) over one block, with the maximum factored out. Each
+// scaled term e^d (d <= 0) is e^{fl(d)} in FP32 times (1 + (d - fl(d))), which
+// keeps the rounding of d to FP32 out of the term; the terms are summed in
+// FP64. A NaN x gives NaN.
+__device__ __forceinline__ double block_log_sum_exp2(const double* __restrict__ x, int64_t n, double* red) {
+  double mx = -INFINITY;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, 2.0 * x[i]);
+  const double top = block_reduce_max(mx, red);
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double d = __dadd_rn(2.0 * x[i], -top);
+    const float dh = (float)d;
+    s = __fma_rn((double)expf(dh), __dadd_rn(1.0, __dadd_rn(d, -(double)dh)), s);
+  }
+  return top + log(block_reduce_sum(s, red));
+}
+
+__device__ __forceinline__ double log_add_exp(double a, double b) {
+  const double hi = fmax(a, b), lo = fmin(a, b);
+  return __dadd_rn(hi, log1p(exp(__dadd_rn(lo, -hi))));
+}
+
+// The translation step (an extension; Sec. 5 names acceleration from optimal
+// transport as future work). IPFP is block coordinate ascent on the concave
+// dual whose stationarity conditions are Eq. IPFP. Moving the partner side's
+// log potentials up by tau and the own side's down by tau leaves every pair
+// term A_xy u_x v_y unchanged, so along that line the dual reads
+//   const + tau (sum mass_P - sum mass_O) - 1/2 e^{2 tau} P - 1/2 e^{-2 tau} O,
+// P = sum_P e^{2 log p}, O = sum_O e^{2 log o}, and its maximiser is
+// tau = 1/2 log z with z the positive root of P z^2 - dm z - O = 0,
+// dm = sum mass_P - sum mass_O: z = (dm + R) / (2 P) for dm >= 0 and
+// 2 O / (R - dm) for dm < 0 (no cancellation), R = sqrt(dm^2 + 4 P O), all in
+// logarithms. Non-finite inputs (non-finite potentials, which the half-sweep
+// reports) give tau = 0.
+__device__ __forceinline__ double translation_tau(double log_p, double log_o, double dm) {
+  const double ln2 = 0.69314718055994530942;
+  const double log_4po = __dadd_rn(__dadd_rn(2.0 * ln2, log_p), log_o);
+  const double log_r = dm != 0.0 ? 0.5 * log_add_exp(2.0 * log(fabs(dm)), log_4po) : 0.5 * log_4po;
+  double log_z;
+  if (dm >= 0.0) {
+    const double log_num = dm > 0.0 ? log_add_exp(log(dm), log_r) : log_r;
+    log_z = __dadd_rn(__dadd_rn(log_num, -ln2), -log_p);
+  } else {
+    log_z = __dadd_rn(__dadd_rn(ln2, log_o), -log_add_exp(log_r, log(-dm)));
+  }
+  const double tau = 0.5 * log_z;
+  return isfinite(tau) ? tau : 0.0;
+}
+
+// tau for the partner side P (potentials log_p, rows_p) and own side O over
+// one block of kTauThreads threads (every thread returns it); `red` holds
+// kTauThreads / 32 doubles.
+__device__ __forceinline__ double block_translation_tau(const double* __restrict__ log_p, int64_t rows_p,
+                                                        const double* __restrict__ log_o, int64_t rows_o, double dm,
+                                                        double* red) {
+  const double lp = block_log_sum_exp2(log_p, rows_p, red);
+  const double lo = block_log_sum_exp2(log_o, rows_o, red);
+  return translation_tau(lp, lo, dm);
 }
 
 __device__ __forceinline__ uint64_t global_timer_ns() {

@@ -13,7 +13,8 @@ soon as memory allows and their sweeps overlap on the device:
   flowing; the market is then created from device pointers;
 * progress: every active market has at most one block of sweeps in flight
   (``tu_ipfp_sweep`` enqueues, ``tu_market_query`` checks without waiting);
-  with ``relax`` the market's over-relaxation factor is chosen between blocks
+  every market sweeps with the library's translation step (``translate``; off:
+  Eq. iteration exactly); with ``relax`` the market's over-relaxation factor is chosen between blocks
   by the library's automatic controller (``tu_market_relax_update``); a market
   whose last block reports residual <= tol (row equations of Eq. IPFP, FP64)
   or that reached the sweep cap is finished;
@@ -55,7 +56,8 @@ import numpy as np
 
 from . import (TuError, tu_get_potentials, tu_ipfp_sweep, tu_market_create, tu_market_destroy,
                tu_market_footprint, tu_market_query, tu_market_relax_update, tu_market_set_relaxation,
-               tu_market_set_small_tiles, tu_market_update_factors, tu_market_use_graphs, tu_topk_partners)
+               tu_market_set_small_tiles, tu_market_set_translation, tu_market_update_factors, tu_market_use_graphs,
+               tu_topk_partners)
 
 # the fused path's factor dimension limit (2d <= 128: one 128-wide MMA inner dimension)
 MAX_D = 64
@@ -162,12 +164,28 @@ class _Slot:
     start_sweeps: int = 0
     inflight: bool = False
     warm: bool = False
+    last_k: int = 0        # sweeps of the last block of this request
+    r_prev: float = -1.0   # residuals read after the last two blocks (-1: none yet)
+    r_last: float = -1.0
+
+
+def _plan_block(last_k: int, r_prev: float, r: float, tol: float, cap: int) -> int:
+    """Sweeps of a request's next block: 1 first, then at most twice the last
+    block, cut to what the per-sweep decay measured over the last block needs to
+    reach tol, at most ``cap`` (the policy of the library's solve loops)."""
+    k = 1 if last_k <= 0 else 2 * last_k
+    if last_k > 0 and r_prev > 0.0 and tol < r < r_prev and tol > 0.0:
+        log_q = math.log(r / r_prev) / last_k
+        need = math.ceil(math.log(tol / r) / log_q)
+        if 1 <= need < k:
+            k = need
+    return max(1, min(k, cap))
 
 
 class Server:
     def __init__(self, hbm_budget_bytes: int, tol: float = 1e-6, max_sweeps: int = 200, sweeps_per_step: int = 8,
                  k: int = 10, max_active: int = 64, keep_potentials: bool = False, relax: bool = True,
-                 workers: int = 4, log_path: Optional[str] = None):
+                 workers: int = 4, log_path: Optional[str] = None, translate: bool = True):
         self.budget = int(hbm_budget_bytes)
         self.tol = tol
         self.max_sweeps = max_sweeps
@@ -176,6 +194,7 @@ class Server:
         self.max_active = max_active
         self.keep_potentials = keep_potentials
         self.relax = relax
+        self.translate = translate
         self.used = 0
         self.resident: "collections.OrderedDict[str, _Slot]" = collections.OrderedDict()
         self.stats = dict(admitted=0, evicted=0, warm=0, not_converged=0, peak_active=0, peak_bytes=0, invalid=0,
@@ -260,6 +279,7 @@ class Server:
                 raise
             slot.req, slot.admitted, slot.inflight, slot.warm = req, now, False, True
             slot.start_sweeps = slot.sweeps
+            slot.last_k, slot.r_prev, slot.r_last = 0, -1.0, -1.0
             return slot
         stream = torch.cuda.Stream()
         try:
@@ -272,6 +292,8 @@ class Server:
         tu_market_use_graphs(h, False)
         # many markets share the GPU: 256-row own tiles keep the per-SM throughput
         tu_market_set_small_tiles(h, False)
+        if not self.translate:
+            tu_market_set_translation(h, False)  # Eq. iteration exactly
         if self.relax:
             tu_market_set_relaxation(h, 0.0)
         return _Slot(handle=h, stream=stream, shape=req.shape, bytes=arg, req=req, admitted=now)
@@ -432,6 +454,7 @@ class Server:
                         done = slot.sweeps - slot.start_sweeps
                         if slot.inflight:
                             slot.inflight = False
+                            slot.r_prev, slot.r_last = slot.r_last, res
                             if res <= self.tol or done >= self.max_sweeps:
                                 # the reply is enqueued first: if that fails, the
                                 # handler below still finds the slot in `active`
@@ -449,9 +472,11 @@ class Server:
                             continue
                         if slot.inflight is False and done > 0 and self.relax:
                             tu_market_relax_update(slot.handle, self.tol)
-                        n = min(self.step, self.max_sweeps - done)
+                        n = min(_plan_block(slot.last_k, slot.r_prev, slot.r_last, self.tol, self.step),
+                                self.max_sweeps - done)
                         tu_ipfp_sweep(slot.handle, n)
                         slot.sweeps += n
+                        slot.last_k = n
                         slot.inflight = True
                         progressed = True
                     except TuError as e:

@@ -73,12 +73,15 @@ def test_batch_sweeps_bit_identical_to_single_and_match_oracle(gpu_lib):
 
 def test_batch_solve_matches_oracle_fixed_points(gpu_lib):
     tu = gpu_lib
-    # unbalanced markets converge in tens of sweeps, the near-balanced one in
-    # hundreds: the fast ones leave the launch early
+    # with Eq. iteration (translation step off) unbalanced markets converge in
+    # tens of sweeps, the near-balanced one in hundreds: the fast ones leave
+    # the launch early
     shapes = [(400, 900, 32), (900, 400, 32), (300, 330, 32), (64, 1000, 16), (1200, 700, 32)]
     mks = [_mk(N, M, d, seed=101 + i, sigma=1.0, bias_x=False, bias_y=(i % 2 == 0), n_kind="uniform1to3",
                m_kind="unit") for i, (N, M, d) in enumerate(shapes)]
     mkts = [tu.from_synth(mk) for mk in mks]
+    for mkt in mkts:
+        mkt.set_translation(False)
     batch = tu.Batch(mkts)
     try:
         st, infos = batch.solve(tol=1e-6, max_iter=20000)
@@ -137,6 +140,8 @@ def test_batch_not_converged_reports_per_market(gpu_lib):
     mks = [_mk(300, 900, 32, seed=1, sigma=1.0, bias_x=False, bias_y=False, n_kind="unit", m_kind="unit"),
            _mk(600, 600, 32, seed=2, sigma=1.0, bias_x=True, bias_y=True, n_kind="unit", m_kind="unit")]
     mkts = [tu.from_synth(mk) for mk in mks]
+    for mkt in mkts:
+        mkt.set_translation(False)  # Eq. iteration: the balanced market is slow
     batch = tu.Batch(mkts)
     try:
         st, infos = batch.solve(tol=1e-6, max_iter=40)
@@ -156,6 +161,8 @@ def test_batch_auto_relaxation_same_fixed_point(gpu_lib):
     other = _mk(300, 1000, 32, seed=18, sigma=1.0, bias_x=False, bias_y=False, n_kind="unit", m_kind="unit")
     plain = tu.from_synth(mk)
     relaxed = [tu.from_synth(mk), tu.from_synth(other)]
+    for m in [plain] + relaxed:
+        m.set_translation(False)  # relaxation against Eq. iteration itself
     for m in relaxed:
         m.set_relaxation(0.0)
     batch = tu.Batch(relaxed)
@@ -172,6 +179,41 @@ def test_batch_auto_relaxation_same_fixed_point(gpu_lib):
         batch.close()
         for m in [plain] + relaxed:
             m.close()
+
+
+def test_batch_translated_solve_matches_oracle_fixed_points(gpu_lib):
+    """With the translation step (the default), balanced and unbalanced
+    markets with and without popularity biases all reach tol in a few sweeps,
+    at the oracle's fixed points; each market's state equals that many solo
+    sweeps bit for bit."""
+    tu = gpu_lib
+    shapes = [(600, 600, 32), (400, 900, 32), (900, 400, 32), (1000, 1000, 16), (64, 1000, 16)]
+    mks = [_mk(N, M, d, seed=201 + i, sigma=0.5, bias_x=(i % 2 == 0), bias_y=True, n_kind="unit", m_kind="unit")
+           for i, (N, M, d) in enumerate(shapes)]
+    mkts = [tu.from_synth(mk) for mk in mks]
+    batch = tu.Batch(mkts)
+    try:
+        st, infos = batch.solve(tol=1e-6, max_iter=2000)
+        assert st == tu.TU_OK, infos
+        for mk, mkt, info in zip(mks, mkts, infos):
+            assert info["converged"] and info["sweeps"] <= 40, (mk.recipe, info)
+            r, logA, f = oracle_solve(mk)
+            mu_ref = np.exp(oracle.log_mu(logA, r["log_u"], r["log_v"]))
+            mu = mkt.mu_block().double().cpu().numpy()
+            np.testing.assert_allclose(mu, mu_ref, rtol=MU_RTOL_BF16, atol=0, err_msg=mk.recipe)
+            cx = oracle.match_count(f["n"], r["log_u"])
+            assert abs(info["match_count"] - cx) <= MATCH_RTOL * cx, (info, cx)
+            solo = tu.from_synth(mk)
+            try:
+                solo.sweep(info["sweeps"])
+                (au, av), (bu, bv) = _pot(solo), _pot(mkt)
+                assert torch.equal(au, bu) and torch.equal(av, bv), (mk.recipe, info)
+            finally:
+                solo.close()
+    finally:
+        batch.close()
+        for mkt in mkts:
+            mkt.close()
 
 
 def test_batch_invalid_arguments(gpu_lib):
@@ -202,10 +244,13 @@ def test_batched_workload_full_size_sampled(gpu_lib):
     [100, 50,000], d = 32): one batched sweep; for a sample of markets
     (including the largest) the oracle recomputes sampled rows of the X
     half-sweep from u = v = 1 and sampled columns of the Y half-sweep from the
-    device's new log u; four markets are compared bit for bit with solo sweeps."""
+    device's new log u; four markets are compared bit for bit with solo sweeps.
+    The translation step is off (one sweep of Eq. iteration)."""
     tu = gpu_lib
     mks = batched_markets()
     mkts = [tu.from_synth(mk) for mk in mks]
+    for mkt in mkts:
+        mkt.set_translation(False)
     batch = tu.Batch(mkts)
     rng = np.random.default_rng(5)
     try:
@@ -226,6 +271,7 @@ def test_batched_workload_full_size_sampled(gpu_lib):
         for i in sample[:4]:
             solo = tu.from_synth(mks[i])
             try:
+                solo.set_translation(False)
                 solo.sweep(1)
                 (au, av), (bu, bv) = _pot(solo), _pot(mkts[i])
                 assert torch.equal(au, bu) and torch.equal(av, bv), mks[i].recipe

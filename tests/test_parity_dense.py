@@ -24,18 +24,20 @@ MU_RTOL_FP32 = 1e-5
 SHAPES = [(700, 555, 32), (1, 333, 8), (333, 1, 8), (2048, 1001, 32), (97, 4099, 5)]
 
 
+@pytest.mark.parametrize("translate", [True, False], ids=["translated", "plain"])
 @pytest.mark.parametrize("N,M,d", SHAPES, ids=lambda v: str(v))
-def test_sweeps_match_oracle(gpu_lib, N, M, d):
+def test_sweeps_match_oracle(gpu_lib, N, M, d, translate):
     tu = gpu_lib
     mk = make_market(N, M, d, sigma=0.5, seed=N + 3 * M, bias_y=True, m_kind="uniform1to5", dtype="fp32")
     mkt = tu.from_synth(mk, path="dense")
     try:
+        mkt.set_translation(translate)
         done = 0
         for target in (1, 3, 8):
             mkt.sweep(target - done)
             done = target
             lu, lv = (t.double().cpu().numpy() for t in mkt.potentials())
-            ou, ov = oracle_sweeps(mk, target)
+            ou, ov = oracle_sweeps(mk, target, translate=translate)
             np.testing.assert_allclose(lu, ou, rtol=0, atol=ATOL_LOG, err_msg=f"log u after {target} sweeps")
             np.testing.assert_allclose(lv, ov, rtol=0, atol=ATOL_LOG, err_msg=f"log v after {target} sweeps")
     finally:
@@ -95,11 +97,12 @@ def test_plain_balanced_market_fixed_point(gpu_lib):
 def test_full_size_job_market_sampled(gpu_lib):
     """20000 x 10000, d = 32: three sweeps on the GPU, then one more sweep
     checked on 64 sampled rows and columns against the oracle's update from
-    the GPU's own state."""
+    the GPU's own state (translation step off: one sweep of Eq. iteration)."""
     tu = gpu_lib
     mk = dense_job_market()
     mkt = tu.from_synth(mk, path="dense")
     try:
+        mkt.set_translation(False)
         mkt.sweep(3)
         lu0, lv0 = (t.double().cpu().numpy() for t in mkt.potentials())
         mkt.sweep(1)
@@ -122,11 +125,13 @@ def test_many_rows_per_cta_sampled(gpu_lib, N, M):
     two blocks of 32 rows, so the row pass reuses its double-buffered blocks
     of parked row sums (the path a 20,000-row pass does not reach). Two
     sweeps, then one more checked on sampled rows and columns (the first and
-    last rows included) against the oracle's update from the GPU's own state."""
+    last rows included) against the oracle's update from the GPU's own state
+    (translation step off: one sweep of Eq. iteration)."""
     tu = gpu_lib
     mk = make_market(N, M, 16, sigma=0.5, seed=N + 7, bias_y=True, m_kind="uniform1to5", dtype="fp32")
     mkt = tu.from_synth(mk, path="dense")
     try:
+        mkt.set_translation(False)
         mkt.sweep(2)
         lu0, lv0 = (t.double().cpu().numpy() for t in mkt.potentials())
         mkt.sweep(1)
@@ -150,13 +155,15 @@ def test_tall_market_beyond_one_grid_height(gpu_lib):
     block has more than 65,535 blocks of 8 rows. Two sweeps, then one more
     checked on sampled rows (both sides of the grid-height bound and the last
     row included) and on every column against the oracle's update from the
-    GPU's own state; then the mu block of the last 600,000 rows."""
+    GPU's own state; then the mu block of the last 600,000 rows (translation
+    step off: one sweep of Eq. iteration)."""
     tu = gpu_lib
     N, M = 4_300_000, 8
     assert (N + 63) // 64 > 65535
     mk = make_market(N, M, 4, sigma=0.5, seed=29, bias_y=True, m_kind="uniform1to5", dtype="fp32")
     mkt = tu.from_synth(mk, path="dense")
     try:
+        mkt.set_translation(False)
         mkt.sweep(2)
         lu0, lv0 = (t.double().cpu().numpy() for t in mkt.potentials())
         mkt.sweep(1)

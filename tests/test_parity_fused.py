@@ -40,18 +40,22 @@ SHAPES = [(700, 555, 64), (256, 128, 64), (1000, 1000, 16), (333, 1201, 50), (1,
           (5, 7, 1)]
 
 
+@pytest.mark.parametrize("translate", [True, False], ids=["translated", "plain"])
 @pytest.mark.parametrize("N,M,d", SHAPES, ids=lambda v: str(v))
-def test_sweeps_match_oracle(gpu_lib, N, M, d):
+def test_sweeps_match_oracle(gpu_lib, N, M, d, translate):
+    """Iterates after 1, 2 and 7 sweeps: with the translation step before each
+    half-sweep (the default) and without it (Eq. iteration exactly)."""
     tu = gpu_lib
     mk = _mk(N, M, d, seed=N * 7 + M)
     mkt = tu.from_synth(mk, path="fused")
     try:
+        mkt.set_translation(translate)
         done = 0
         for target in (1, 2, 7):
             mkt.sweep(target - done)
             done = target
             lu, lv = (t.double().cpu().numpy() for t in mkt.potentials())
-            ou, ov = oracle_sweeps(mk, target)
+            ou, ov = oracle_sweeps(mk, target, translate=translate)
             np.testing.assert_allclose(lu, ou, rtol=0, atol=ATOL_LOG, err_msg=f"log u after {target} sweeps")
             np.testing.assert_allclose(lv, ov, rtol=0, atol=ATOL_LOG, err_msg=f"log v after {target} sweeps")
     finally:
@@ -149,12 +153,14 @@ def test_not_converged_status(gpu_lib):
 def test_full_size_single_sweep_sampled(gpu_lib):
     """1e6 x 1e6, d = 64, bf16, lognormal biases both sides: one sweep from
     u = v = 1, checked on 64 sampled rows and 64 sampled columns against the
-    oracle's mini-batch update of those users (Eq. iteration_minibatch)."""
+    oracle's mini-batch update of those users (Eq. iteration_minibatch). The
+    translation step is off: this checks one sweep of Eq. iteration."""
     tu = gpu_lib
     mk = fused_market()
     stream = torch.cuda.Stream()
     mkt = tu.from_synth(mk, path="fused", stream=stream, partition=65536)
     try:
+        mkt.set_translation(False)
         mkt.sweep(1)
         lu, lv = (t.double().cpu().numpy() for t in mkt.potentials())
         rng = np.random.default_rng(0)

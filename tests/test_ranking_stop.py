@@ -47,11 +47,12 @@ def test_stop_lists_equal_fixed_point_lists(gpu_lib, path):
             ok = _separated(scores, 10)
             assert np.all(got[ok] == want[ok])
         # the stop comes no later than a tight solve (1e-6: the FP32 floor of
-        # the fused path's residual is a few 1e-7)
+        # the fused path's residual is a few 1e-7) plus the `patience` passing
+        # checks the rule waits for once the lists have settled
         tight = tu.from_synth(mk, path=path)
         try:
             full = tight.solve(tol=1e-6, max_iter=20000)
-            assert full["converged"] and info["sweeps"] <= full["sweeps"] + 2, (info, full)
+            assert full["converged"] and info["sweeps"] <= full["sweeps"] + 2 * 3 + 2, (info, full)
         finally:
             tight.close()
     finally:
@@ -60,10 +61,12 @@ def test_stop_lists_equal_fixed_point_lists(gpu_lib, path):
 
 def test_stop_on_slow_market_and_arguments(gpu_lib):
     tu = gpu_lib
-    # balanced with popularity biases: thousands of sweeps to 1e-6, rankings settle far earlier
+    # balanced with popularity biases: with Eq. iteration (translation step
+    # off) thousands of sweeps to 1e-6, rankings settle far earlier
     mk = make_market(400, 400, 32, sigma=0.5, seed=5, bias_x=True, bias_y=True)
     mkt = tu.from_synth(mk)
     try:
+        mkt.set_translation(False)
         info = mkt.solve_ranking(k=5, sample=400, check_every=5, patience=4, max_iter=20000)
         assert info["converged"] and info["residual_inf"] > 1e-6, info
         tight = mkt.solve(tol=1e-6, max_iter=50000, warm_start=True)

@@ -106,7 +106,8 @@ def test_failures_stay_with_their_request(gpu_lib, tmp_path):
     z = np.broadcast_to(np.float32(0.0), (N, 64))
     big = serve.SolveRequest(rid=0, arrival=0.0, F=z, K=z, G=z, L=z, n=np.ones(N), m=np.ones(M), sigma=0.5)
     bad.append(("invalid", big))
-    # a balanced market with popularity biases needs far more sweeps than its deadline allows
+    # with Eq. iteration (the server below runs without the translation step) a
+    # balanced market with popularity biases needs far more sweeps than its deadline allows
     late = _requests(serve, [(20000, 20000, 32)], seed=11)[0]
     late.deadline = 0.005
     bad.append(("deadline", late))
@@ -116,7 +117,7 @@ def test_failures_stay_with_their_request(gpu_lib, tmp_path):
     log = tmp_path / "serve.jsonl"
     budget = 64 << 20
     srv = serve.Server(hbm_budget_bytes=budget, tol=1e-6, max_sweeps=2000, k=10, keep_potentials=True,
-                       log_path=str(log))
+                       log_path=str(log), translate=False)
     res = srv.run(reqs, realtime=False)
     srv.close()
     assert [r.rid for r in res] == list(range(len(reqs)))
@@ -125,7 +126,8 @@ def test_failures_stay_with_their_request(gpu_lib, tmp_path):
         assert r.topk_idx is None and not r.converged
     assert srv.stats["invalid"] == 2 and srv.stats["errors"] == 1 and srv.stats["deadline"] == 1
     assert srv.used == 0  # every market and reservation was released
-    clean = serve.Server(hbm_budget_bytes=budget, tol=1e-6, max_sweeps=2000, k=10, keep_potentials=True)
+    clean = serve.Server(hbm_budget_bytes=budget, tol=1e-6, max_sweeps=2000, k=10, keep_potentials=True,
+                         translate=False)
     ref = clean.run(_requests(serve, good_specs, seed=3), realtime=False)
     clean.close()
     for a, b in zip(res[:len(good)], ref):

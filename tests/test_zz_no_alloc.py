@@ -43,6 +43,7 @@ def test_noalloc_matches_market_half_sweep_twice(gpu_lib, N, M, d, kp):
     # existing entry points: residual of the state, then the u step of one sweep
     mkt = tu.from_synth(mk, path="fused")
     try:
+        mkt.set_translation(False)  # the u step of Eq. iteration, as the entry point computes
         mkt.set_potentials(lu0_t, lv0_t)
         res_market = tu.tu_ipfp_sweep(mkt.handle, 0, residual=True)
         mkt.sweep(1)
