@@ -16,6 +16,15 @@ namespace tu {
 
 namespace {
 
+// s += x * w with Kahan compensation c (the running error of s, subtracted
+// from the next term); the product enters the compensated add unrounded.
+__device__ __forceinline__ void kahan_fma(float& s, float& c, float x, float w) {
+  const float y = fmaf(x, w, -c);
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
 constexpr int kThreads = 256;  // the A-hat build
 
 // A-hat and its transpose from the packed FP32 factors (setup, once per factor
@@ -207,7 +216,12 @@ __global__ void __launch_bounds__(kPassThreads) k_dense_rowpass(
     uint32_t ph = 0;
     bool ok = true;
     for (int64_t k = 0; k < nrows && ok; ++k) {
+      // four compensated (Kahan) sums per lane: a row of a few million terms
+      // gives each accumulator thousands of them, where a plain FP32 sum
+      // would drift by that many units of 2^-24; the pass is memory-bound,
+      // so the three extra operations per term are free
       float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+      float e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f;  // their compensations
       for (int64_t c = 0; c < nchunks; ++c) {
         const bool got = mbar_wait(&S.full[t], ph, abort_flag);
         if (!__all_sync(0xffffffffu, got)) {
@@ -221,10 +235,10 @@ __global__ void __launch_bounds__(kPassThreads) k_dense_rowpass(
         for (int q = warp * 32 + lane; q < nq; q += kConsumerWarps * 32) {
           const float4 x = r4[q];
           const float4 y = __ldg(g4 + q);
-          a0 = fmaf(x.x, y.x, a0);
-          a1 = fmaf(x.y, y.y, a1);
-          a2 = fmaf(x.z, y.z, a2);
-          a3 = fmaf(x.w, y.w, a3);
+          kahan_fma(a0, e0, x.x, y.x);
+          kahan_fma(a1, e1, x.y, y.y);
+          kahan_fma(a2, e2, x.z, y.z);
+          kahan_fma(a3, e3, x.w, y.w);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.empty[t]);
@@ -234,7 +248,7 @@ __global__ void __launch_bounds__(kPassThreads) k_dense_rowpass(
         }
       }
       if (!ok) break;
-      float sum = (a0 + a1) + (a2 + a3);
+      float sum = ((a0 - e0) + (a1 - e1)) + ((a2 - e2) + (a3 - e3));
       for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
       const int slot = (int)(k % kSlots);
       const int64_t blk = k / kSlots;
@@ -273,14 +287,14 @@ __global__ void __launch_bounds__(kPassThreads) k_dense_rowpass(
     const int64_t k = blk * kSlots + lane;
     if (k < nrows) {
       const int64_t row = blockIdx.x + k * G;
-      float sum = 0.0f;
-      for (int cw = 0; cw < kConsumerWarps; ++cw) sum += S.part[pb][lane][cw];
+      double sum = 0.0;
+      for (int cw = 0; cw < kConsumerWarps; ++cw) sum += (double)S.part[pb][lane][cw];
       double omega = 1.0;
       if constexpr (RELAX) {
         shift = __ldg(lmax_partner);
         omega = (update && omega_p != nullptr) ? __ldg(omega_p) : 1.0;
       }
-      const RowResult rr = row_update((double)logf(sum), shift, b2s ? b2s[row] : 0.0f, mass[row], log_u[row],
+      const RowResult rr = row_update(log_row_sum(sum), shift, b2s ? b2s[row] : 0.0f, mass[row], log_u[row],
                                       residual != 0, omega);
       if (update) {
         log_u[row] = rr.log_u;

@@ -763,7 +763,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(&rowfree[pb]);
       }
       if constexpr (MODE == kModeSweep) {
-        const float total = (sum - comp) + rb[rloc];
+        const double total = ((double)sum - (double)comp) + (double)rb[rloc];
         __syncwarp();
         if (lane == 0) mbar_arrive(&rowfree[pb]);
         const int64_t row = p.row0 + r;
@@ -772,7 +772,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           double* log_u = BATCH ? bd->log_u : p.log_u;
           double* ell = BATCH ? bd->ell : p.ell;
           const double omega = BATCH ? ((bd->omega != nullptr && p.update) ? *bd->omega : 1.0) : omega0;
-          const RowResult rr = row_update((double)logf(total), shift, b2s ? b2s[row] : 0.0f,
+          const RowResult rr = row_update(log_row_sum(total), shift, b2s ? b2s[row] : 0.0f,
                                           (BATCH ? bd->mass : p.mass)[row], log_u[row], p.residual != 0, omega);
           if (p.update) {
             log_u[row] = rr.log_u;

@@ -277,6 +277,20 @@ struct RowResult {
   double r_rel, r_abs, u2;
 };
 
+// ln x of a positive row sum x (FP64, formed from FP32 partial sums), to an
+// absolute error of about 6e-8 whatever the size of x. x = m 2^e with m in
+// [0.5, 1), so ln x = e ln 2 + ln m, and ln m is logf of m rounded to FP32 plus
+// the first-order term of that rounding; |ln m| < 0.7 keeps logf's rounding
+// small. (logf(x) itself rounds to half an FP32 ulp of ln x: 4.8e-7 for the
+// sums of ~1e6 terms of a large market, ln x ~ 14, which would put a floor of
+// ~1e-6 under the residual.)
+__device__ __forceinline__ double log_row_sum(double x) {
+  int e;
+  const double m = frexp(x, &e);
+  const float mf = (float)m;
+  return (double)e * 0.69314718055994530942 + (double)logf(mf) + (double)((float)(m - (double)mf) / mf);
+}
+
 // The closed-form update of Eq. iteration for one user, in logs.
 //   ln_sum   : log of sum_y exp(phi_hat_xy / (2 sigma) + ell_y - shift)
 //   shift    : the partner-side shift (max_y ell_y) taken out of the sum
@@ -292,9 +306,9 @@ struct RowResult {
 // to ~100 with popularity biases) stay in FP64. For z = log s - 1/2 log n > 0,
 // asinh(e^z) = z + c(z) with c(z) = log1p(sqrt(1 + e^{-2z})) in (ln 2, 0.89],
 // so only the bounded correction c is rounded to FP32 (absolute error ~1e-7).
-// The terms of the FP64 reductions (u^2 and 2 u s of the residual, u^2 of the
-// match count) are FP64 exponentials of the FP64 state: two or three per row
-// and half-sweep, against thousands of pair terms.
+// The residual's terms (u^2 and 2 u s) are FP64 exponentials of the FP64
+// state, so the reported residual carries no FP32 rounding. The u^2 summed for
+// the match count (sum n - sum u^2, where sum u^2 is a small part) stays FP32.
 //
 // omega != 1 over-relaxes the update in the log domain:
 // log u <- log u_old + omega * (update - log u_old) (same fixed point).
@@ -323,7 +337,7 @@ __device__ __forceinline__ RowResult row_update(double ln_sum, double shift, flo
   const double lu = omega == 1.0 ? lu_upd : log_u_old + omega * (lu_upd - log_u_old);
   o.log_u = lu;
   o.ell = lu + (double)b2s;
-  o.u2 = exp(2.0 * lu);
+  o.u2 = (double)expf((float)(2.0 * lu));
   return o;
 }
 

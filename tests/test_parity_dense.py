@@ -176,12 +176,14 @@ def test_tall_market_beyond_one_grid_height(gpu_lib):
         np.testing.assert_allclose(lu[rows], ou, atol=ATOL_LOG)
         _, ov = oracle.sampled_row_update(mk.G, mk.L, mk.F, mk.K, f["sigma"], f["m"], lu, np.arange(M), mk.bias_y,
                                           None)
-        # a column sum runs over 4.3e6 terms: each of the pass's 1,024 FP32
-        # accumulators adds about N / 1024 positive terms (relative error at
-        # most that many units of 2^-24), then about 20 more roundings combine
-        # them; a row tile left unbuilt would move log v by about 0.025
-        col_atol = ATOL_LOG + (N / 1024 + 32) * 2.0**-24
-        np.testing.assert_allclose(lv, ov, atol=col_atol)
+        # a column sum runs over 4.3e6 terms: each of the pass's 1,024
+        # accumulators is a compensated (Kahan) FP32 sum of about N / 1024
+        # terms, so the column update meets the FP32 bar like a short row; a
+        # row tile left unbuilt would move log v by about 0.025
+        col_err = float(np.max(np.abs(lv - ov)))
+        row_err = float(np.max(np.abs(lu[rows] - ou)))
+        print(f"4.3e6 x 8: max |log u - oracle| {row_err:.2e} (sampled rows), max |log v - oracle| {col_err:.2e}")
+        np.testing.assert_allclose(lv, ov, atol=ATOL_LOG)
         nx = 600_000
         x0 = N - nx
         mu = mkt.mu_block(x0, nx, 0, M).double().cpu().numpy()
