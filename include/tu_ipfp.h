@@ -121,8 +121,8 @@ tu_status tu_market_update_factors(tu_market_t mkt, const void* F, const void* K
  * translation step unless tu_market_set_translation(mkt, 0) turned it off
  * (that step leaves the fixed point unchanged). If residual_out != NULL, synchronise and
  * store the row residual of the resulting potentials:
- *     max_x |u_x^2 + u_x sum_y A_xy v_y - n_x| / n_x     (row equations of Eq. IPFP),
- * which costs one extra half-sweep of work. */
+ *     max_x |u_x^2 + u_x sum_y A_xy v_y - n_x| / n_x     (row equations of Eq. IPFP,
+ * terms and reduction in FP64), which costs one extra half-sweep of work. */
 tu_status tu_ipfp_sweep(tu_market_t mkt, int nsweeps, double* residual_out);
 
 typedef struct {
@@ -135,9 +135,10 @@ typedef struct {
 
 /* Sweep until residual_inf <= tol or max_iter sweeps (Alg. 1 with a stopping
  * rule; the paper runs a fixed count). warm_start = 0 resets to u = v = 1 first;
- * 1 continues from the current potentials. The residual of each sweep's input
- * state is reduced in FP64 inside the X half-sweep; the returned state is
- * certified by one final residual pass. Returns TU_OK, TU_ERR_NOT_CONVERGED
+ * 1 continues from the current potentials. An estimate of the residual of each
+ * sweep's input state (FP32 terms, FP64 reduction) is reduced inside the X
+ * half-sweep and decides when to stop; the returned state is certified by one
+ * final residual pass with FP64 terms. Returns TU_OK, TU_ERR_NOT_CONVERGED
  * (potentials valid), or an error. info may be NULL. */
 tu_status tu_ipfp_solve(tu_market_t mkt, double tol, int max_iter, int warm_start, tu_solve_info* info);
 
@@ -268,7 +269,8 @@ tu_status tu_market_relax_update(tu_market_t mkt, double tol);
  * that work has finished. *idle = 1 when every sweep enqueued so far is done;
  * then *residual = max_x |r_x| / n_x of the state that entered the last sweep
  * (row equations of Eq. IPFP, reduced in FP64 inside that sweep's X
- * half-sweep), *match_count = sum m - sum v^2 after it, and *sweeps = sweeps
+ * half-sweep from terms formed in FP32: an estimate within about 2e-7),
+ * *match_count = sum m - sum v^2 after it, and *sweeps = sweeps
  * completed since creation. After a call that certifies its result
  * (tu_ipfp_sweep with residual_out, tu_ipfp_solve, tu_ipfp_solve_ranking),
  * *residual is that certified residual of the returned state. While busy

@@ -50,7 +50,6 @@ size_t round4(size_t v) { return (v + 3) & ~(size_t)3; }
 
 static_assert(alignof(BatchDesc) >= 128 && sizeof(BatchDesc) % 128 == 0,
               "descriptor arrays keep every tensor map 128-byte aligned");
-static_assert(kPrepThreads == kTauThreads, "the batched translation step runs the single-market routine's block size");
 
 }  // namespace
 
@@ -91,58 +90,36 @@ namespace {
 // Kernels: one CTA per listed market
 // ---------------------------------------------------------------------------
 
-// Partner preparation of a listed market: shift = max ell, then the FP32
-// vector g = (ell - shift) log2(e), -inf padded (the single-market kernels
-// compute the same values in two launches). In sweeps (sweep = 1) of a market
-// with the translation step, tau comes first, from the same routine and block
-// size as the single-market k_prep_tau (so the same bits), and the FP64 state
-// moves: partner log u and ell by +tau, own log u and ell by -tau; g is written
-// from the values before the move (it depends on ell - max ell only) and the
-// shift becomes max ell + tau.
+// Partner preparation of a listed market: the FP32 vector
+// g = (ell - max ell) log2(e), -inf padded, from the partner's shift kept in
+// the market's scalars, and the pass's scalars (prep_scalars: the translation
+// step in sweeps, sweep = 1, of a market that takes it; the partner shift; the
+// own offset) -- the single-market preparation computes the same values.
 __global__ void __launch_bounds__(kPrepThreads) k_batch_prep(const BatchDesc* __restrict__ desc,
                                                             const int* __restrict__ list,
                                                             const int* __restrict__ n_list, int sweep) {
   if ((int)blockIdx.x >= *n_list) return;
   const BatchDesc& d = desc[list[blockIdx.x]];
-  __shared__ double red[kPrepThreads / 32];
-  const bool translate = sweep && d.translate;
-  const double tau =
-      translate ? block_translation_tau(d.partner_log_u, d.partner_rows, d.log_u, d.rows, d.dm, red) : 0.0;
-  double mx = -INFINITY;
-  for (int64_t i = threadIdx.x; i < d.partner_rows; i += blockDim.x) mx = fmax(mx, d.partner_ell[i]);
-  double shift = block_reduce_max(mx, red);
-  if (!(shift > -INFINITY && shift < INFINITY)) shift = 0.0;  // non-finite potentials are reported elsewhere
-  if (threadIdx.x == 0) *d.lmax = shift + tau;
-  for (int64_t i = threadIdx.x; i < d.partner_rows_pad; i += blockDim.x) {
-    if (i < d.partner_rows) {
-      const double e = d.partner_ell[i];
-      d.g[i] = (float)((e - shift) * 1.4426950408889634);
-      if (translate) {
-        d.partner_ell[i] = e + tau;
-        d.partner_log_u[i] += tau;
-      }
-    } else {
-      d.g[i] = -INFINITY;
-    }
-  }
-  if (translate) {
-    for (int64_t i = threadIdx.x; i < d.rows; i += blockDim.x) {
-      d.log_u[i] -= tau;
-      d.ell[i] -= tau;
-    }
-  }
+  const double top = d.st[kStLmax + (1 - d.own_side)];  // not written by prep_scalars
+  if (threadIdx.x == 0) prep_scalars(d.st, d.own_side, sweep && d.translate);
+  for (int64_t i = threadIdx.x; i < d.partner_rows_pad; i += blockDim.x)
+    d.g[i] = i < d.partner_rows ? (float)((d.partner_ell[i] - top) * 1.4426950408889634) : -INFINITY;
 }
 
-// FP64 reduction of a listed market's per-tile partials into its result slots.
+// FP64 reduction of a listed market's per-tile partials into its result slots;
+// after an updating pass, also the own side's groups into the market's scalars
+// (the single-market finalize's routine with the same block size).
 __global__ void __launch_bounds__(kFinThreads) k_batch_finalize(const BatchDesc* __restrict__ desc,
                                                                const int* __restrict__ list,
                                                                const int* __restrict__ n_list,
                                                                const double* __restrict__ partials, int is_x,
-                                                               int residual, double* __restrict__ results) {
+                                                               int residual, int update,
+                                                               double* __restrict__ results) {
   if ((int)blockIdx.x >= *n_list) return;
   const int mk = list[blockIdx.x];
   const BatchDesc& d = desc[mk];
   __shared__ double s_max[kFinThreads], s_l1[kFinThreads], s_sq[kFinThreads], s_nf[kFinThreads];
+  __shared__ float redf[2 * kFinThreads / 32];
   const int64_t s0 = (int64_t)d.slot0 * kBatchSlotWarps;
   const int64_t s1 = s0 + (int64_t)d.num_own_tiles * kBatchSlotWarps;
   double mx = 0.0, l1 = 0.0, sq = 0.0, nf = 0.0;
@@ -179,20 +156,68 @@ __global__ void __launch_bounds__(kFinThreads) k_batch_finalize(const BatchDesc*
     }
     r[kResNonfin] += s_nf[0];
   }
+  if (update) {
+    const GroupTotal g = block_reduce_groups(d.grp, (d.rows + kGroupRows - 1) / kGroupRows, redf);
+    if (threadIdx.x == 0) finish_scalars(d.st, d.own_side, g, d.dm_next);
+  }
 }
 
-// u = v = 1 (Alg. 1 / Alg. 2 initialisation) for the listed markets.
+// u = v = 1 (Alg. 1 / Alg. 2 initialisation) for the listed markets, then
+// their groups and scalars as the single-market rescan computes them.
 __global__ void __launch_bounds__(kFinThreads) k_batch_reset(const BatchDesc* __restrict__ desc_x,
                                                             const BatchDesc* __restrict__ desc_y,
                                                             const int* __restrict__ list,
                                                             const int* __restrict__ n_list) {
   if ((int)blockIdx.x >= *n_list) return;
   const int mk = list[blockIdx.x];
+  __shared__ float redf[2 * kFinThreads / 32];
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  GroupTotal tot[2];
   for (int s = 0; s < 2; ++s) {
     const BatchDesc& d = (s == 0 ? desc_x : desc_y)[mk];
+    // each warp resets the rows of the groups it then forms
+    const int64_t ng = (d.rows + kGroupRows - 1) / kGroupRows;
+    for (int64_t g = warp; g < ng; g += kFinThreads / 32) {
+      const int64_t i = g * kGroupRows + lane;
+      const bool valid = i < d.rows;
+      const double e = (valid && d.b2s != nullptr) ? (double)d.b2s[i] : 0.0;
+      if (valid) {
+        d.log_u[i] = 0.0;
+        d.ell[i] = e;
+      }
+      const float4 gv = warp_group(0.0, e, valid);
+      if (lane == 0) d.grp[g] = gv;
+    }
+    __syncthreads();
+    tot[s] = block_reduce_groups(d.grp, ng, redf);
+  }
+  // the next half-sweep updates X against Y: dm = sum m - sum n
+  if (threadIdx.x == 0) rescan_scalars(desc_x[mk].st, tot[0], tot[1], -desc_x[mk].dm_next);
+}
+
+// End of a block of batched sweeps: the listed markets' pending offsets
+// written into their arrays and folded into their scalars.
+__global__ void __launch_bounds__(kFinThreads) k_batch_flush(const BatchDesc* __restrict__ desc_x,
+                                                            const BatchDesc* __restrict__ desc_y,
+                                                            const int* __restrict__ list,
+                                                            const int* __restrict__ n_list) {
+  if ((int)blockIdx.x >= *n_list) return;
+  const int mk = list[blockIdx.x];
+  double* st = desc_x[mk].st;
+  const double off[2] = {st[kStOff + 0], st[kStOff + 1]};
+  for (int s = 0; s < 2; ++s) {
+    if (off[s] == 0.0) continue;
+    const BatchDesc& d = (s == 0 ? desc_x : desc_y)[mk];
     for (int64_t i = threadIdx.x; i < d.rows; i += blockDim.x) {
-      d.log_u[i] = 0.0;
-      d.ell[i] = d.b2s != nullptr ? (double)d.b2s[i] : 0.0;
+      d.log_u[i] += off[s];
+      d.ell[i] += off[s];
+    }
+  }
+  __syncthreads();  // every thread has read the offsets
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2; ++s) {
+      st[kStLmax + s] += off[s];
+      st[kStOff + s] = 0.0;
     }
   }
 }
@@ -383,14 +408,21 @@ cudaError_t enqueue_half(tu_batch* b, int si, int side, int residual, int update
   if ((e = launch_fused_batch(L, b->stream)) != cudaSuccess) return e;
   if ((e = profile_mark(b, false)) != cudaSuccess) return e;
   k_batch_finalize<<<b->count, kFinThreads, 0, b->stream>>>(b->desc_dev[side], list, n, b->partials,
-                                                           side == 0 ? 1 : 0, residual, b->results);
+                                                           side == 0 ? 1 : 0, residual, update, b->results);
   return cudaGetLastError();
 }
 
 cudaError_t enqueue_sweep(tu_batch* b) {
-  cudaError_t e = enqueue_half(b, 0, 0, 1, 1);
+  cudaError_t e = enqueue_half(b, 0, 0, kResidualEstimate, 1);
   if (e != cudaSuccess) return e;
   return enqueue_half(b, 0, 1, 0, 1);
+}
+
+// After a block of sweeps over schedule 0: pending offsets into the arrays.
+cudaError_t enqueue_flush(tu_batch* b) {
+  const Schedule& S = b->sched[0];
+  k_batch_flush<<<b->count, kFinThreads, 0, b->stream>>>(b->desc_dev[0], b->desc_dev[1], S.dev + S.off_list, S.dev);
+  return cudaGetLastError();
 }
 
 bool stream_capturable(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread; }
@@ -401,6 +433,7 @@ tu_status enqueue_sweeps(tu_batch* b, int k) {
   if (k <= 0) return TU_OK;
   if (!stream_capturable(b->stream) || k == 1 || b->profiling) {
     for (int i = 0; i < k; ++i) TB_CK(b, enqueue_sweep(b));
+    TB_CK(b, enqueue_flush(b));
     return TU_OK;
   }
   auto found = b->graphs.find(k);
@@ -409,6 +442,7 @@ tu_status enqueue_sweeps(tu_batch* b, int k) {
     TB_CK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < k && e == cudaSuccess; ++i) e = enqueue_sweep(b);
+    if (e == cudaSuccess) e = enqueue_flush(b);
     const cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (e != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -444,7 +478,7 @@ tu_status read_results(tu_batch* b) {
 // Residual of the current potentials of `members` (one X pass without update).
 tu_status certify(tu_batch* b, const std::vector<int>& members) {
   TB_TRY(sched_set(b, b->sched[1], members));
-  TB_CK(b, enqueue_half(b, 1, 0, 1, 0));
+  TB_CK(b, enqueue_half(b, 1, 0, kResidualExact, 0));
   return read_results(b);
 }
 
@@ -554,11 +588,12 @@ tu_status tu_batch_create(const tu_market_t* markets, int count, void* stream, t
       d.log_u = own.log_u;
       d.ell = own.ell;
       d.partner_ell = par.ell;
-      d.partner_log_u = par.log_u;
-      d.dm = par.sum_mass - own.sum_mass;
+      d.dm_next = own.sum_mass - par.sum_mass;
+      d.own_side = side;
+      d.st = m->st;
+      d.grp = own.grp;
       d.translate = m->translate ? 1 : 0;
       d.g = par.pvec;
-      d.lmax = par.lmax;
       d.omega = b->omega_dev + i;
       d.rows = own.rows;
       d.partner_rows = par.rows;

@@ -153,9 +153,10 @@ __device__ __forceinline__ void pass_abort(int* err, volatile int* flag) {
 template <bool RELAX>
 __global__ void __launch_bounds__(kPassThreads) k_dense_rowpass(
     const float* __restrict__ A, int64_t ld, int64_t rows, const float* __restrict__ w,
-    const double* __restrict__ lmax_partner, const float* __restrict__ b2s, const double* __restrict__ mass,
-    double* __restrict__ log_u, double* __restrict__ ell, double* __restrict__ partials, int residual,
-    int update, const double* __restrict__ omega_p, int* __restrict__ err) {
+    const double* __restrict__ st, const float* __restrict__ b2s, const double* __restrict__ mass,
+    double* __restrict__ log_u, double* __restrict__ ell, float4* __restrict__ grp, int64_t grp_blocks,
+    double* __restrict__ partials, int residual, int update, const double* __restrict__ omega_p,
+    int* __restrict__ err) {
   extern __shared__ __align__(128) uint8_t pass_smem_raw[];
   PassSmem& S = *reinterpret_cast<PassSmem*>(pass_smem_raw);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -272,8 +273,12 @@ __global__ void __launch_bounds__(kPassThreads) k_dense_rowpass(
 
   if (warp != kUpdateWarp) return;
   PartialAcc acc;
-  double shift = 0.0;
-  if constexpr (!RELAX) shift = *lmax_partner;
+  // the pass's partner shift and own offset (market scalars set by the preparation)
+  double shift = 0.0, own_off = 0.0;
+  if constexpr (!RELAX) {
+    shift = st[kStShift];
+    own_off = st[kStOwnOff];
+  }
   // a block's shares arrive after kSlots rows are streamed: allow for 1 GB/s per CTA
   const uint64_t block_limit = kWaitLimitNs + (uint64_t)kSlots * (uint64_t)ld * 4ull;
   bool ok = true;
@@ -285,25 +290,44 @@ __global__ void __launch_bounds__(kPassThreads) k_dense_rowpass(
       break;
     }
     const int64_t k = blk * kSlots + lane;
+    double lu_new = 0.0, ell_new = 0.0;
     if (k < nrows) {
       const int64_t row = blockIdx.x + k * G;
-      double sum = 0.0;
-      for (int cw = 0; cw < kConsumerWarps; ++cw) sum += (double)S.part[pb][lane][cw];
+      // the eight warps' shares, added with their roundings kept (two-sum)
+      float sum = 0.0f, err = 0.0f;
+      for (int cw = 0; cw < kConsumerWarps; ++cw) {
+        float e;
+        sum = two_sum(sum, S.part[pb][lane][cw], e);
+        err = __fadd_rn(err, e);
+      }
       double omega = 1.0;
       if constexpr (RELAX) {
-        shift = __ldg(lmax_partner);
+        shift = __ldg(st + kStShift);
+        own_off = __ldg(st + kStOwnOff);
         omega = (update && omega_p != nullptr) ? __ldg(omega_p) : 1.0;
       }
-      const RowResult rr = row_update(log_row_sum(sum), shift, b2s ? b2s[row] : 0.0f, mass[row], log_u[row],
-                                      residual != 0, omega);
+      const RowResult rr = row_update(log_row_sum(sum, err, 0.0f), shift, b2s ? b2s[row] : 0.0f, mass[row],
+                                      log_u[row] + own_off, residual, omega);
       if (update) {
         log_u[row] = rr.log_u;
         ell[row] = rr.ell;
       }
+      lu_new = rr.log_u;
+      ell_new = rr.ell;
       acc.add(rr);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&S.freed[pb]);
+    if (update) {
+      // the block's rows (this CTA's rows blk * 32 .. blk * 32 + 31) form group blk * G + blockIdx.x
+      const float4 gv = warp_group(lu_new, ell_new, k < nrows);
+      if (lane == 0) grp[blk * G + blockIdx.x] = gv;
+    }
+  }
+  if (update && ok && lane == 0) {
+    // groups of the blocks this CTA does not have (the grid's rows are
+    // dealt round-robin, so some CTAs have one block fewer) contribute nothing
+    for (int64_t blk = (nrows + kSlots - 1) / kSlots; blk < grp_blocks; ++blk) grp[blk * G + blockIdx.x] = empty_group();
   }
   if (!ok && !*abort_flag) pass_abort(err, abort_flag);
   // this warp holds every partial of the CTA
@@ -359,23 +383,27 @@ cudaError_t launch_dense_build(tu_market* m) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_dense_rowpass(tu_market* m, int residual, int update, int* nparts_out) {
+cudaError_t launch_dense_rowpass(tu_market* m, int residual, int update, int* nparts_out, int64_t* ngroups_out) {
   const int g = rowpass_grid(m, m->N);
+  const int64_t blocks = ((m->N + g - 1) / g + kSlots - 1) / kSlots;  // update blocks of the fullest CTA
   auto kern = m->omega_cfg != 1.0 ? k_dense_rowpass<true> : k_dense_rowpass<false>;
-  kern<<<g, kPassThreads, sizeof(PassSmem), m->stream>>>(m->Ahat, m->ldA, m->N, m->Y.pvec, m->Y.lmax, m->X.b2s,
-                                                         m->X.mass, m->X.log_u, m->X.ell, m->partials, residual,
-                                                         update, m->omega_dev, m->err_dev);
+  kern<<<g, kPassThreads, sizeof(PassSmem), m->stream>>>(m->Ahat, m->ldA, m->N, m->Y.pvec, m->st, m->X.b2s,
+                                                         m->X.mass, m->X.log_u, m->X.ell, m->X.grp, blocks,
+                                                         m->partials, residual, update, m->omega_dev, m->err_dev);
   *nparts_out = g;
+  *ngroups_out = blocks * g;
   return cudaGetLastError();
 }
 
-cudaError_t launch_dense_colpass(tu_market* m, int update, int* nparts_out) {
+cudaError_t launch_dense_colpass(tu_market* m, int update, int* nparts_out, int64_t* ngroups_out) {
   const int g = rowpass_grid(m, m->M);
+  const int64_t blocks = ((m->M + g - 1) / g + kSlots - 1) / kSlots;
   auto kern = m->omega_cfg != 1.0 ? k_dense_rowpass<true> : k_dense_rowpass<false>;
-  kern<<<g, kPassThreads, sizeof(PassSmem), m->stream>>>(m->AhatT, m->ldN, m->M, m->X.pvec, m->X.lmax, m->Y.b2s,
-                                                         m->Y.mass, m->Y.log_u, m->Y.ell, m->partials, 0, update,
-                                                         m->omega_dev, m->err_dev);
+  kern<<<g, kPassThreads, sizeof(PassSmem), m->stream>>>(m->AhatT, m->ldN, m->M, m->X.pvec, m->st, m->Y.b2s,
+                                                         m->Y.mass, m->Y.log_u, m->Y.ell, m->Y.grp, blocks,
+                                                         m->partials, 0, update, m->omega_dev, m->err_dev);
   *nparts_out = g;
+  *ngroups_out = blocks * g;
   return cudaGetLastError();
 }
 

@@ -68,6 +68,8 @@ struct FusedParams {
   float c;                 // log2(e) / (2 sigma)
   const float* g;          // partner prepared potentials (index = partner user), -inf padded
   const double* lmax;      // partner shift (natural log)
+  const double* own_off;   // offset added to the stored own potentials, or nullptr for 0   (sweep)
+  float4* grp;             // own-side groups written by an updating pass, or nullptr        (sweep)
   const float* b2s;        // own bias / (2 sigma), or nullptr          (sweep)
   const double* mass;      // own capacities                             (sweep)
   double* log_u;           // own potentials (in: old, out: new)          (sweep)
@@ -576,8 +578,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t cb = __float_as_uint(p.c);
       cc = ((uint64_t)cb << 32) | cb;
     }
-    // single market: the shift and omega of the launch (batched: per item)
+    // single market: the shift, own offset and omega of the launch (batched: per item)
     const double shift0 = BATCH ? 0.0 : __ldg(p.lmax);
+    // (ranked lists and mu blocks run on potentials without pending offsets:
+    // every block of sweeps ends by writing them into the arrays)
+    const double own_off0 = (MODE == kModeSweep && !BATCH && p.own_off != nullptr) ? *p.own_off : 0.0;
     const double omega0 = (!BATCH && p.omega != nullptr && p.update) ? *p.omega : 1.0;
     int buf = 0, gs = 0;
     uint32_t tphase = 0, gphase = 0;
@@ -603,7 +608,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t cb = __float_as_uint(bd->c);
         cc = ((uint64_t)cb << 32) | cb;
       }
-      const double shift = BATCH ? *bd->lmax : shift0;
+      const double shift = BATCH ? bd->st[kStShift] : shift0;
       const int npt = BATCH ? bd->num_partner_tiles : p.num_partner_tiles;
       const int rloc = h * 128 + q * 32 + lane;          // row within the own tile
       const int64_t r = (int64_t)t * kOwn + rloc;         // row within the launch
@@ -763,25 +768,39 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(&rowfree[pb]);
       }
       if constexpr (MODE == kModeSweep) {
-        const double total = ((double)sum - (double)comp) + (double)rb[rloc];
+        const float other = rb[rloc];
         __syncwarp();
         if (lane == 0) mbar_arrive(&rowfree[pb]);
         const int64_t row = p.row0 + r;
+        double lu_new = 0.0, ell_new = 0.0;
         if (row_ok) {
           const float* b2s = BATCH ? bd->b2s : p.b2s;
           double* log_u = BATCH ? bd->log_u : p.log_u;
           double* ell = BATCH ? bd->ell : p.ell;
           const double omega = BATCH ? ((bd->omega != nullptr && p.update) ? *bd->omega : 1.0) : omega0;
-          const RowResult rr = row_update(log_row_sum(total), shift, b2s ? b2s[row] : 0.0f,
-                                          (BATCH ? bd->mass : p.mass)[row], log_u[row], p.residual != 0, omega);
+          const double own_off = BATCH ? bd->st[kStOwnOff] : own_off0;
+          const RowResult rr = row_update(log_row_sum(sum, -comp, other), shift, b2s ? b2s[row] : 0.0f,
+                                          (BATCH ? bd->mass : p.mass)[row], log_u[row] + own_off,
+                                          p.residual, omega);
           if (p.update) {
             log_u[row] = rr.log_u;
             ell[row] = rr.ell;
           }
+          lu_new = rr.log_u;
+          ell_new = rr.ell;
           r_max = fmax(r_max, rr.r_rel);
           r_sum += rr.r_abs;
           sq += rr.u2;
           if (!isfinite(rr.log_u) || !isfinite(rr.ell)) nf += 1.0;
+        }
+        // this warp's 32 rows form one group of the own side (the finalize
+        // reduces the groups into the side's shift and sum of u^2)
+        float4* grp = BATCH ? bd->grp : p.grp;
+        const int64_t g = (int64_t)t * (kOwn / kGroupRows) + (h * 128 + q * 32) / kGroupRows;
+        if (p.update && grp != nullptr && !(SMALL && h == 1) &&
+            g * kGroupRows < (BATCH ? bd->rows : p.rows)) {
+          const float4 gv = warp_group(lu_new, ell_new, row_ok);
+          if (lane == 0) grp[g] = gv;
         }
         if constexpr (BATCH) {
           // partials of this own tile and warp (warps ew = 0..7 own the row
@@ -1006,7 +1025,9 @@ cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int upd
   const bool small = use_small_tiles(m, own.rows);
   FusedParams p = base_params(own.rows, 0, 0, partner.rows, m->cmul, small);
   p.g = partner.pvec;
-  p.lmax = partner.lmax;
+  p.lmax = m->st + kStShift;
+  p.own_off = m->st + kStOwnOff;
+  p.grp = own.grp;
   p.b2s = own.b2s;
   p.mass = own.mass;
   p.log_u = own.log_u;
@@ -1032,7 +1053,7 @@ cudaError_t launch_fused_topk(tu_market* m, int side, int k, int64_t row0, int64
   const bool small = use_small_tiles(m, nrows);
   FusedParams p = base_params(nrows, row0, 0, partner.rows, m->cmul, small);
   p.g = partner.pvec;
-  p.lmax = partner.lmax;
+  p.lmax = m->st + kStShift;
   p.ell = own.ell;
   p.partials = m->partials;
   p.err = m->err_dev;
@@ -1055,7 +1076,7 @@ cudaError_t launch_fused_mu(tu_market* m, int64_t x0, int64_t nx, int64_t y0, in
   const bool small = use_small_tiles(m, nx);
   FusedParams p = base_params(nx, x0, c0, y0 + ny - c0, m->cmul, small);
   p.g = m->Y.pvec;
-  p.lmax = m->Y.lmax;
+  p.lmax = m->st + kStShift;
   p.ell = m->X.ell;
   p.partials = m->partials;
   p.err = m->err_dev;

@@ -269,7 +269,9 @@ tu_status side_alloc(tu_market* m, Side& s, int64_t rows, bool has_bias) {
   TU_TRY(dev_alloc(m, &s.ell, s.rows_pad));
   TU_TRY(dev_alloc(m, &s.pvec, s.rows_pad));
   TU_TRY(dev_alloc(m, &s.mass, s.rows_pad));
-  TU_TRY(dev_alloc(m, &s.lmax, 1));
+  // groups of 32 rows; the dense pass's layout (rows dealt round-robin over up
+  // to kMaxPartials CTAs) needs at most rows / 32 + 2 * kMaxPartials of them
+  TU_TRY(dev_alloc(m, &s.grp, (size_t)(s.rows_pad / kGroupRows + 2 * kMaxPartials)));
   if (has_bias) TU_TRY(dev_alloc(m, &s.b2s, s.rows_pad));
   if (m->path == TU_PATH_FUSED && m->dtype == TU_DTYPE_FP8E4M3) {
     TU_TRY(dev_alloc(m, &s.fac8, (size_t)rows * 128));
@@ -286,7 +288,7 @@ void side_free(tu_market* m, Side& s) {
   dev_free(m, s.ell);
   dev_free(m, s.pvec);
   dev_free(m, s.mass);
-  dev_free(m, s.lmax);
+  dev_free(m, s.grp);
   dev_free(m, s.b2s);
   dev_free(m, s.fac16);
   dev_free(m, s.fac8);
@@ -423,7 +425,8 @@ cudaError_t profile_mark(tu_market* m, bool start) {
   return e;
 }
 
-// One half-sweep: prepare the partner potentials, run the pass, reduce partials.
+// One half-sweep: prepare the partner potentials and the pass's scalars, run
+// the pass, reduce its partials (and, after an update, the own side's groups).
 cudaError_t enqueue_half(tu_market* m, int side, int residual, int update) {
   Side& partner = side == 0 ? m->Y : m->X;
   // sweeps (update = 1) take the translation step; a certifying pass leaves the state as it is
@@ -431,27 +434,37 @@ cudaError_t enqueue_half(tu_market* m, int side, int residual, int update) {
   if (e != cudaSuccess) return e;
   if ((e = profile_mark(m, true)) != cudaSuccess) return e;
   int nparts = 0;
+  int64_t ngroups = ((side == 0 ? m->N : m->M) + kGroupRows - 1) / kGroupRows;
   if (m->path == TU_PATH_FUSED) {
     e = launch_fused_halfsweep(m, side, residual, update, &nparts);
   } else if (side == 0) {
-    e = launch_dense_rowpass(m, residual, update, &nparts);
+    e = launch_dense_rowpass(m, residual, update, &nparts, &ngroups);
   } else {
-    e = launch_dense_colpass(m, update, &nparts);
+    e = launch_dense_colpass(m, update, &nparts, &ngroups);
   }
   if (e != cudaSuccess) return e;
   if ((e = profile_mark(m, false)) != cudaSuccess) return e;
-  return launch_finalize(m, nparts, side == 0 ? 1 : 0, residual);
+  return launch_finalize(m, nparts, side == 0 ? 1 : 0, residual, update, ngroups);
 }
 
 // One sweep of Eq. iteration: u from v (with the residual of the entering
 // state), then v from the new u.
 cudaError_t enqueue_sweep(tu_market* m) {
-  cudaError_t e = enqueue_half(m, 0, 1, 1);
+  cudaError_t e = enqueue_half(m, 0, kResidualEstimate, 1);
   if (e != cudaSuccess) return e;
   return enqueue_half(m, 1, 0, 1);
 }
 
 bool stream_capturable(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread; }
+
+// k sweeps, then the translation steps still pending as offsets written into
+// the potentials (so every other call sees plain arrays).
+cudaError_t enqueue_block(tu_market* m, int k) {
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < k && e == cudaSuccess; ++i) e = enqueue_sweep(m);
+  if (e == cudaSuccess && k > 0) e = launch_flush(m);
+  return e;
+}
 
 // Enqueue k sweeps, replaying a captured graph of k sweeps when possible.
 tu_status enqueue_sweeps(tu_market* m, int k) {
@@ -464,8 +477,7 @@ tu_status enqueue_sweeps(tu_market* m, int k) {
       }
       cudaGraph_t g = nullptr;
       TU_CK(m, cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e = cudaSuccess;
-      for (int i = 0; i < k && e == cudaSuccess; ++i) e = enqueue_sweep(m);
+      cudaError_t e = enqueue_block(m, k);
       cudaError_t e2 = cudaStreamEndCapture(m->stream, &g);
       if (e != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -480,7 +492,7 @@ tu_status enqueue_sweeps(tu_market* m, int k) {
     TU_CK(m, cudaGraphLaunch(m->graph, m->stream));
     return TU_OK;
   }
-  for (int i = 0; i < k; ++i) TU_CK(m, enqueue_sweep(m));
+  TU_CK(m, enqueue_block(m, k));
   return TU_OK;
 }
 
@@ -502,7 +514,7 @@ tu_status clear_results(tu_market* m) {
 
 // Residual of the current potentials (one X pass without update).
 tu_status certify(tu_market* m, double* res_inf, double* res_l1) {
-  TU_CK(m, enqueue_half(m, 0, 1, 0));
+  TU_CK(m, enqueue_half(m, 0, kResidualExact, 0));
   TU_TRY(read_results(m));
   if (res_inf) *res_inf = m->results_host[kResXInf];
   if (res_l1) *res_l1 = m->results_host[kResXL1] / m->X.sum_mass;
@@ -669,8 +681,7 @@ void tu_market_destroy(tu_market_t m) {
     }
   }
   dev_free(m, m->partials);
-  dev_free(m, m->mpartials);
-  dev_free(m, m->tau_dev);
+  dev_free(m, m->st);
   dev_free(m, m->results);
   dev_free(m, m->err_dev);
   dev_free(m, m->staging);
@@ -747,8 +758,7 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
   if ((st = side_alloc(m, m->X, D.N, D.bias_x != nullptr)) != TU_OK) return bail(st);
   if ((st = side_alloc(m, m->Y, D.M, D.bias_y != nullptr)) != TU_OK) return bail(st);
   if ((st = dev_alloc(m, &m->partials, (size_t)kMaxPartials * 4)) != TU_OK) return bail(st);
-  if ((st = dev_alloc(m, &m->mpartials, (size_t)kMaxPartials)) != TU_OK) return bail(st);
-  if ((st = dev_alloc(m, &m->tau_dev, 1)) != TU_OK) return bail(st);
+  if ((st = dev_alloc(m, &m->st, (size_t)kStSlots)) != TU_OK) return bail(st);
   if ((st = dev_alloc(m, &m->results, (size_t)kResSlots)) != TU_OK) return bail(st);
   if ((st = dev_alloc(m, &m->err_dev, 1)) != TU_OK) return bail(st);
   {
@@ -816,6 +826,9 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
     cudaError_t e = fused_prepare(m);
     if (e != cudaSuccess) return bail(fail_cuda(m, e, "fused_prepare"));
   }
+  if (cudaMemsetAsync(m->st, 0, kStSlots * sizeof(double), m->stream) != cudaSuccess ||
+      launch_rescan(m) != cudaSuccess)
+    return bail(fail_cuda(m, cudaGetLastError(), "scalars of the initial potentials"));
   if (clear_results(m) != TU_OK || cudaStreamSynchronize(m->stream) != cudaSuccess) return bail(TU_ERR_CUDA);
   *out = m;
   return TU_OK;
@@ -976,6 +989,7 @@ tu_status tu_ipfp_solve(tu_market_t m, double tol, int max_iter, int warm_start,
   if (!warm_start) {
     TU_CK(m, launch_reset_potentials(m, m->X));
     TU_CK(m, launch_reset_potentials(m, m->Y));
+    TU_CK(m, launch_rescan(m));
   }
   TU_TRY(clear_results(m));
   // sweeps between host checks: planned from the measured decay (plan_block),
@@ -1052,6 +1066,7 @@ tu_status tu_ipfp_solve_ranking(tu_market_t m, int k, int64_t sample, int check_
   if (!warm_start) {
     TU_CK(m, launch_reset_potentials(m, m->X));
     TU_CK(m, launch_reset_potentials(m, m->Y));
+    TU_CK(m, launch_rescan(m));
   }
   TU_TRY(clear_results(m));
   // per side: the users checked and the list length (k + 1 when there is a next partner)
@@ -1245,6 +1260,7 @@ tu_status tu_set_potentials(tu_market_t m, const float* log_u, const float* log_
     TU_CK(m, launch_set_potentials(m, *sides[i], static_cast<const float*>(src)));
     TU_CK(m, cudaStreamSynchronize(m->stream));
   }
+  TU_CK(m, launch_rescan(m));
   return relax_reset(m);
 }
 

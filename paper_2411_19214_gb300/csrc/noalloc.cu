@@ -239,7 +239,7 @@ extern "C" tu_status tu_fused_halfsweep_noalloc(int64_t rows, int64_t cols, int6
   r.ell = ell;
   r.partials = partials;
   r.err = err;
-  r.residual = residual_out != nullptr ? 1 : 0;
+  r.residual = residual_out != nullptr ? kResidualExact : kResidualNone;
   int nparts = 0;
   if (launch_fused_halfsweep_raw(r, s, ds.num_sms, &nparts) != cudaSuccess) {
     cudaGetLastError();

@@ -144,92 +144,92 @@ __global__ void k_row_norm_max(const float* __restrict__ f32, const __nv_bfloat1
   }
 }
 
-// Partner preparation, phase 1: per-block maximum of ell.
-__global__ void k_prep_max(const double* __restrict__ ell, int64_t rows, double* __restrict__ mpartials) {
-  __shared__ double red[kThreads / 32];
-  double mx = -INFINITY;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
-       i += (int64_t)gridDim.x * blockDim.x)
-    mx = fmax(mx, ell[i]);
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = mx;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double b = -INFINITY;
-    for (int w = 0; w < kThreads / 32; ++w) b = fmax(b, red[w]);
-    mpartials[blockIdx.x] = b;
+// Partner preparation: the vector the half-sweep consumes, from the partner's
+// stored ell and its maximum (a per-market scalar kept by the finalize
+// kernels): fused_mode 1: (ell - max) * log2(e), padding -inf (exp2 of it is
+// 0); fused_mode 0: exp(ell - max), padding 0. The vector depends on
+// ell - max ell only, so no translation step or offset changes it; thread 0
+// of block 0 records the pass's scalars (prep_scalars: its translation step,
+// the partner shift it adds back and the own offset). No other thread reads
+// the scalars it writes.
+__global__ void k_prep(const double* __restrict__ ell, int64_t rows, int64_t rows_pad, double* __restrict__ st,
+                       int own, int translate, int fused_mode, float* __restrict__ out) {
+  const double top = st[kStLmax + (1 - own)];
+  if (blockIdx.x == 0 && threadIdx.x == 0) prep_scalars(st, own, translate);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows_pad;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float v;
+    if (i < rows) {
+      // the FP64 state is rounded once, to the FP32 vector the half-sweep streams
+      const double z = ell[i] - top;
+      v = fused_mode ? (float)(z * 1.4426950408889634) : (float)exp(z);
+    } else {
+      v = fused_mode ? -INFINITY : 0.0f;
+    }
+    out[i] = v;
   }
 }
 
-// Translation step of a sweep's half-sweep (one CTA of kTauThreads): tau from
-// the two sides' potentials, into *tau_out. The batched preparation computes
-// the same value with the same routine and block size.
-__global__ void __launch_bounds__(kTauThreads) k_prep_tau(const double* __restrict__ log_p, int64_t rows_p,
-                                                          const double* __restrict__ log_o, int64_t rows_o, double dm,
-                                                          double* __restrict__ tau_out) {
-  __shared__ double red[kTauThreads / 32];
-  const double tau = block_translation_tau(log_p, rows_p, log_o, rows_o, dm, red);
-  if (threadIdx.x == 0) *tau_out = tau;
+// Groups of a side's stored potentials (one warp per 32 rows), as a half-sweep
+// writes them for the rows it updates.
+__global__ void k_scan_groups(const double* __restrict__ log_u, const double* __restrict__ ell, int64_t rows,
+                              float4* __restrict__ grp) {
+  const int64_t ng = (rows + kGroupRows - 1) / kGroupRows;
+  const int lane = threadIdx.x % 32;
+  for (int64_t g = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32; g < ng;
+       g += (int64_t)gridDim.x * blockDim.x / 32) {
+    const int64_t r = g * kGroupRows + lane;
+    const bool valid = r < rows;
+    const float4 gv = warp_group(valid ? log_u[r] : 0.0, valid ? ell[r] : 0.0, valid);
+    if (lane == 0) grp[g] = gv;
+  }
 }
 
-// Partner preparation, phase 2: shift = max ell; write the vector the
-// half-sweep consumes. fused_mode 1: (ell - shift) * log2(e), padding -inf
-// (exp2 of it is 0); fused_mode 0: exp(ell - shift), padding 0.
-// With tau (the translation step, computed by k_prep_tau), the FP64 state
-// moves: log p, ell_p += tau (partner side), log o, ell_o -= tau (own side).
-// The prepared vector depends only on ell_p - max ell_p, which the move leaves
-// unchanged, so it is written from the values before the move and the shift
-// becomes max ell_p + tau.
-__global__ void k_prep_write(double* __restrict__ ell, double* __restrict__ log_p, int64_t rows, int64_t rows_pad,
-                             double* __restrict__ log_o, double* __restrict__ ell_o, int64_t rows_o,
-                             const double* __restrict__ tau_in, const double* __restrict__ mpartials, int nparts,
-                             int fused_mode, float* __restrict__ out, double* __restrict__ lmax) {
-  __shared__ double red[kThreads / 32];
-  __shared__ double shift_s;
-  double mx = -INFINITY;
-  for (int i = threadIdx.x; i < nparts; i += blockDim.x) mx = fmax(mx, mpartials[i]);
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = mx;
-  __syncthreads();
-  const double tau = tau_in != nullptr ? *tau_in : 0.0;
-  if (threadIdx.x == 0) {
-    double b = -INFINITY;
-    for (int w = 0; w < kThreads / 32; ++w) b = fmax(b, red[w]);
-    if (!(b > -INFINITY && b < INFINITY)) b = 0.0;  // non-finite potentials are reported elsewhere
-    shift_s = b;
-    if (blockIdx.x == 0) *lmax = b + tau;
-  }
-  __syncthreads();
-  const double shift = shift_s;
-  const int64_t n = tau_in != nullptr && rows_o > rows_pad ? rows_o : rows_pad;
+// Scalars of both sides from their groups (one block): shifts and sums,
+// offsets cleared, and tau for the next half-sweep, which updates X against Y.
+__global__ void k_rescan_scalars(const float4* __restrict__ grp_x, int64_t ng_x, const float4* __restrict__ grp_y,
+                                 int64_t ng_y, double dm_next, double* __restrict__ st) {
+  __shared__ float red[2 * kThreads / 32];
+  const GroupTotal x = block_reduce_groups(grp_x, ng_x, red);
+  const GroupTotal y = block_reduce_groups(grp_y, ng_y, red);
+  if (threadIdx.x == 0) rescan_scalars(st, x, y, dm_next);
+}
+
+// End of a block of sweeps: write the sides' offsets into their arrays (the
+// scalars are folded by k_flush_scalars afterwards, so every block reads the
+// offsets before any is cleared).
+__global__ void k_flush(double* __restrict__ lu_x, double* __restrict__ ell_x, int64_t nx, double* __restrict__ lu_y,
+                        double* __restrict__ ell_y, int64_t ny, const double* __restrict__ st) {
+  const double ox = st[kStOff + 0], oy = st[kStOff + 1];
+  const int64_t n = nx > ny ? nx : ny;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    if (i < rows_pad) {
-      float v;
-      if (i < rows) {
-        // the FP64 state is rounded once, to the FP32 vector the half-sweep streams
-        const double e = ell[i];
-        const double z = e - shift;
-        v = fused_mode ? (float)(z * 1.4426950408889634) : (float)exp(z);
-        if (tau_in != nullptr) {
-          ell[i] = e + tau;
-          log_p[i] += tau;
-        }
-      } else {
-        v = fused_mode ? -INFINITY : 0.0f;
-      }
-      out[i] = v;
+    if (ox != 0.0 && i < nx) {
+      lu_x[i] += ox;
+      ell_x[i] += ox;
     }
-    if (tau_in != nullptr && i < rows_o) {
-      log_o[i] -= tau;
-      ell_o[i] -= tau;
+    if (oy != 0.0 && i < ny) {
+      lu_y[i] += oy;
+      ell_y[i] += oy;
     }
   }
 }
 
-// FP64 reduction of the per-CTA partials (max r/n, sum |r|, sum u^2, non-finite count).
-__global__ void k_finalize(const double* __restrict__ partials, int nparts, int is_x, int residual,
+__global__ void k_flush_scalars(double* __restrict__ st) {
+  for (int s = 0; s < 2; ++s) {
+    st[kStLmax + s] += st[kStOff + s];
+    st[kStOff + s] = 0.0;
+  }
+}
+
+// FP64 reduction of the per-CTA partials (max r/n, sum |r|, sum u^2, non-finite
+// count). After a pass that updated its side (update), also that side's groups
+// into the market scalars (finish_scalars), with the same routine and block
+// size as the batched finalize.
+__global__ void k_finalize(const double* __restrict__ partials, int nparts, int is_x, int residual, int update,
+                           const float4* __restrict__ grp, int64_t ngroups, double dm_next, double* __restrict__ st,
                            double* __restrict__ results) {
-  __shared__ double s_max[kThreads], s_l1[kThreads], s_sq[kThreads], s_nf[kThreads];
+  __shared__ double red[4][kThreads / 32];
+  __shared__ float redf[2 * kThreads / 32];
   double mx = 0.0, l1 = 0.0, sq = 0.0, nf = 0.0;
   for (int i = threadIdx.x; i < nparts; i += blockDim.x) {
     mx = fmax(mx, partials[4 * i + 0]);
@@ -237,31 +237,40 @@ __global__ void k_finalize(const double* __restrict__ partials, int nparts, int 
     sq += partials[4 * i + 2];
     nf += partials[4 * i + 3];
   }
-  s_max[threadIdx.x] = mx;
-  s_l1[threadIdx.x] = l1;
-  s_sq[threadIdx.x] = sq;
-  s_nf[threadIdx.x] = nf;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) {
-      s_max[threadIdx.x] = fmax(s_max[threadIdx.x], s_max[threadIdx.x + w]);
-      s_l1[threadIdx.x] += s_l1[threadIdx.x + w];
-      s_sq[threadIdx.x] += s_sq[threadIdx.x + w];
-      s_nf[threadIdx.x] += s_nf[threadIdx.x + w];
-    }
-    __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+    sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    nf += __shfl_xor_sync(0xffffffffu, nf, o);
   }
+  const int w = threadIdx.x / 32;
+  if (threadIdx.x % 32 == 0) {
+    red[0][w] = mx;
+    red[1][w] = l1;
+    red[2][w] = sq;
+    red[3][w] = nf;
+  }
+  GroupTotal g{};
+  if (update) g = block_reduce_groups(grp, ngroups, redf);  // synchronises the block
+  else __syncthreads();
   if (threadIdx.x == 0) {
+    for (int k = 1; k < kThreads / 32; ++k) {
+      mx = fmax(mx, red[0][k]);
+      l1 += red[1][k];
+      sq += red[2][k];
+      nf += red[3][k];
+    }
     if (is_x) {
       if (residual) {
-        results[kResXInf] = s_max[0];
-        results[kResXL1] = s_l1[0];
+        results[kResXInf] = mx;
+        results[kResXL1] = l1;
       }
-      results[kResXSq] = s_sq[0];
+      results[kResXSq] = sq;
     } else {
-      results[kResYSq] = s_sq[0];
+      results[kResYSq] = sq;
     }
-    results[kResNonfin] += s_nf[0];
+    results[kResNonfin] += nf;
+    if (update) finish_scalars(st, is_x ? 0 : 1, g, dm_next);
   }
 }
 
@@ -351,18 +360,31 @@ cudaError_t launch_pack_fp8(tu_market* m, Side& s, const float* A, const float* 
 }
 
 cudaError_t launch_prep(tu_market* m, Side& partner, int fused_mode, int translate) {
-  Side& own = &partner == &m->Y ? m->X : m->Y;
-  int g1 = grid_for(partner.rows, m->num_sms, 4);
-  if (g1 > kMaxPartials) g1 = kMaxPartials;
-  k_prep_max<<<g1, kThreads, 0, m->stream>>>(partner.ell, partner.rows, m->mpartials);
-  if (translate)
-    k_prep_tau<<<1, kTauThreads, 0, m->stream>>>(partner.log_u, partner.rows, own.log_u, own.rows,
-                                                 partner.sum_mass - own.sum_mass, m->tau_dev);
-  const int64_t n2 = translate && own.rows > partner.rows_pad ? own.rows : partner.rows_pad;
-  const int g2 = grid_for(n2, m->num_sms, 4);
-  k_prep_write<<<g2, kThreads, 0, m->stream>>>(partner.ell, partner.log_u, partner.rows, partner.rows_pad, own.log_u,
-                                                own.ell, own.rows, translate ? m->tau_dev : nullptr, m->mpartials, g1,
-                                                fused_mode, partner.pvec, partner.lmax);
+  const int own = &partner == &m->Y ? 0 : 1;
+  const int g = grid_for(partner.rows_pad, m->num_sms, 4);
+  k_prep<<<g, kThreads, 0, m->stream>>>(partner.ell, partner.rows, partner.rows_pad, m->st, own, translate, fused_mode,
+                                        partner.pvec);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rescan(tu_market* m) {
+  for (Side* s : {&m->X, &m->Y}) {
+    const int64_t ng = (s->rows + kGroupRows - 1) / kGroupRows;
+    int g = (int)((ng * 32 + kThreads - 1) / kThreads);
+    if (g > m->num_sms * 8) g = m->num_sms * 8;
+    k_scan_groups<<<g < 1 ? 1 : g, kThreads, 0, m->stream>>>(s->log_u, s->ell, s->rows, s->grp);
+  }
+  k_rescan_scalars<<<1, kThreads, 0, m->stream>>>(m->X.grp, (m->X.rows + kGroupRows - 1) / kGroupRows, m->Y.grp,
+                                                  (m->Y.rows + kGroupRows - 1) / kGroupRows,
+                                                  m->Y.sum_mass - m->X.sum_mass, m->st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flush(tu_market* m) {
+  const int64_t n = m->X.rows > m->Y.rows ? m->X.rows : m->Y.rows;
+  k_flush<<<grid_for(n, m->num_sms, 4), kThreads, 0, m->stream>>>(m->X.log_u, m->X.ell, m->X.rows, m->Y.log_u,
+                                                                   m->Y.ell, m->Y.rows, m->st);
+  k_flush_scalars<<<1, 1, 0, m->stream>>>(m->st);
   return cudaGetLastError();
 }
 
@@ -370,12 +392,15 @@ cudaError_t launch_sum_sq(tu_market* m, Side& s, int is_x) {
   int g = grid_for(s.rows, m->num_sms, 4);
   if (g > kMaxPartials) g = kMaxPartials;
   k_sum_sq<<<g, kThreads, 0, m->stream>>>(s.log_u, s.rows, m->partials);
-  k_finalize<<<1, kThreads, 0, m->stream>>>(m->partials, g, is_x, 0, m->results);
+  k_finalize<<<1, kThreads, 0, m->stream>>>(m->partials, g, is_x, 0, 0, nullptr, 0, 0.0, m->st, m->results);
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(tu_market* m, int nparts, int is_x, int residual) {
-  k_finalize<<<1, kThreads, 0, m->stream>>>(m->partials, nparts, is_x, residual, m->results);
+cudaError_t launch_finalize(tu_market* m, int nparts, int is_x, int residual, int update, int64_t ngroups) {
+  Side& own = is_x ? m->X : m->Y;
+  Side& par = is_x ? m->Y : m->X;
+  k_finalize<<<1, kThreads, 0, m->stream>>>(m->partials, nparts, is_x, residual, update, own.grp, ngroups,
+                                            own.sum_mass - par.sum_mass, m->st, m->results);
   return cudaGetLastError();
 }
 

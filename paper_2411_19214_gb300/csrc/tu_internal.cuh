@@ -36,6 +36,30 @@ enum : int {
   kResSlots = 8
 };
 
+// Per-market FP64 scalars on the device (tu_market::st), kept up to date by
+// the preparation and finalize kernels of every half-sweep, so that no O(N)
+// pass is needed to prepare a half-sweep or to take the translation step.
+// Side s: 0 = X, 1 = Y.
+enum : int {
+  kStLmax = 0,     // [2] max over the side of its stored ell
+  kStLogS = 2,     // [2] log sum e^{2 log u} over the side's true potentials
+  kStOff = 4,      // [2] true log u = stored log u + offset (a translation not yet written to the arrays)
+  kStTauNext = 6,  // the translation step for the next half-sweep of a sweep
+  kStTauUsed = 7,  // the translation step the current half-sweep's preparation applied
+  kStShift = 8,    // the current half-sweep's partner shift: lmax + offset + tau (natural log)
+  kStOwnOff = 9,   // the current half-sweep's own-side offset: offset - tau
+  kStSlots = 16
+};
+
+// Per-32-row group of a side (Side::grp, a float4): max 2 log u, sum of
+// e^{2 log u - max}, max ell; written by the side's own half-sweep.
+constexpr int kGroupRows = 32;
+
+// Residual of the state entering an X half-sweep (the pass's `residual`):
+// none, an estimate with FP32 terms (inside sweeps) or exact FP64 terms
+// (certifying passes).
+enum : int { kResidualNone = 0, kResidualEstimate = 1, kResidualExact = 2 };
+
 // device error word codes (first error wins)
 enum : int { kErrNone = 0, kErrTimeout = 1, kErrNonfinite = 2 };
 
@@ -47,7 +71,7 @@ struct Side {
   float* b2s = nullptr;     // b / (2 sigma), rows_pad, or nullptr without bias
   double* mass = nullptr;   // capacities, rows_pad (padding 1)
   float* pvec = nullptr;    // this side's potentials prepared for the other side's half-sweep, rows_pad
-  double* lmax = nullptr;   // device scalar: max_i ell_i
+  float4* grp = nullptr;    // per-32-row groups {max 2 log u, scaled sum, max ell, 0}, rows_pad / 32 + 2 kMaxPartials
   double sum_mass = 0.0;    // host copy of sum of capacities
   __nv_bfloat16* fac16 = nullptr;  // packed [F | K] (or [G | L]) rows x kp, bf16, zero padded
   uint8_t* fac8 = nullptr;         // FP8 markets: packed rows x 128 e4m3 of [F | K] * 2^-fp8_exp
@@ -113,8 +137,7 @@ struct tu_market {
   float* Ahat = nullptr;     // dense path: N x ldA fp32
   int64_t ldA = 0;
   double* partials = nullptr;   // kMaxPartials x 4 doubles
-  double* mpartials = nullptr;  // kMaxPartials doubles (max reduction)
-  double* tau_dev = nullptr;    // device scalar: the translation step of the current half-sweep
+  double* st = nullptr;          // device scalars (kSt*): shifts, sums, offsets and steps of both sides
   float* AhatT = nullptr;       // dense path: transpose of A-hat, M x ldN fp32
   int64_t ldN = 0;
   double* results = nullptr;       // device, kResSlots
@@ -157,10 +180,17 @@ struct tu_market {
 namespace tu {
 
 // reduce.cu
-// Prepare the partner's FP32 vector and shift for a half-sweep of the other
-// side; with translate, first apply the translation step between the two sides.
+// Prepare the partner's FP32 vector for a half-sweep of the other side and the
+// pass's scalars (with translate, the translation step taken before it).
 cudaError_t launch_prep(tu_market* m, Side& partner, int fused_mode, int translate);
-cudaError_t launch_finalize(tu_market* m, int nparts, int is_x, int residual);
+// Reduce a pass's partials; after an update, also the own side's groups into
+// the market scalars (ngroups: groups the pass wrote).
+cudaError_t launch_finalize(tu_market* m, int nparts, int is_x, int residual, int update, int64_t ngroups);
+// Groups and scalars of both sides from their stored potentials (after the
+// potentials were set from outside a sweep).
+cudaError_t launch_rescan(tu_market* m);
+// Write the sides' pending offsets into their arrays (end of a block of sweeps).
+cudaError_t launch_flush(tu_market* m);
 cudaError_t launch_pack_factors(tu_market* m, Side& s, const void* A, const void* B, int src_dtype);
 cudaError_t launch_init_side(tu_market* m, Side& s, const float* bias_dev, int has_bias);
 cudaError_t launch_reset_potentials(tu_market* m, Side& s);
@@ -175,8 +205,8 @@ cudaError_t launch_sum_sq(tu_market* m, Side& s, int is_x);  // results[kResXSq 
 
 // dense.cu
 cudaError_t launch_dense_build(tu_market* m);
-cudaError_t launch_dense_rowpass(tu_market* m, int residual, int update, int* nparts_out);
-cudaError_t launch_dense_colpass(tu_market* m, int update, int* nparts_out);
+cudaError_t launch_dense_rowpass(tu_market* m, int residual, int update, int* nparts_out, int64_t* ngroups_out);
+cudaError_t launch_dense_colpass(tu_market* m, int update, int* nparts_out, int64_t* ngroups_out);
 
 // fused.cu
 cudaError_t fused_prepare(tu_market* m);  // tensor maps + kernel attributes
@@ -213,12 +243,13 @@ struct BatchDesc {
   const double* mass;          // own capacities
   double* log_u;               // own potentials (in: old, out: new)
   double* ell;                 // own ell (out)
-  double* partner_ell;         // partner ell (read, and moved by the translation step, in the preparation kernel)
-  double* partner_log_u;       // partner log potentials (moved by the translation step)
+  const double* partner_ell;   // partner ell (read by the preparation kernel)
   float* g;                    // partner prepared vector (written by the preparation kernel)
-  double* lmax;                // partner shift (written by the preparation kernel)
+  double* st;                  // the market's scalars (kSt*; shift and own offset of the pass)
+  float4* grp;                 // own-side groups (written by the pass, reduced by the finalize)
   const double* omega;         // over-relaxation factor of this market (device scalar)
-  double dm;                   // sum of partner capacities - sum of own capacities (translation step)
+  double dm_next;              // sum of own capacities - sum of partner capacities (the next step's tau)
+  int own_side;                // 0: X is own, 1: Y is own
   int translate;               // the market's translation-step setting at batch creation
   int64_t rows;                // own users
   int64_t partner_rows;        // partner users
@@ -277,18 +308,28 @@ struct RowResult {
   double r_rel, r_abs, u2;
 };
 
-// ln x of a positive row sum x (FP64, formed from FP32 partial sums), to an
-// absolute error of about 6e-8 whatever the size of x. x = m 2^e with m in
-// [0.5, 1), so ln x = e ln 2 + ln m, and ln m is logf of m rounded to FP32 plus
-// the first-order term of that rounding; |ln m| < 0.7 keeps logf's rounding
-// small. (logf(x) itself rounds to half an FP32 ulp of ln x: 4.8e-7 for the
-// sums of ~1e6 terms of a large market, ln x ~ 14, which would put a floor of
-// ~1e-6 under the residual.)
-__device__ __forceinline__ double log_row_sum(double x) {
-  int e;
-  const double m = frexp(x, &e);
-  const float mf = (float)m;
-  return (double)e * 0.69314718055994530942 + (double)logf(mf) + (double)((float)(m - (double)mf) / mf);
+// ln (a + b + c) of a positive row sum given as three FP32 parts, to an
+// absolute error of about 6e-8 whatever the size of the sum. The parts are
+// added in FP32 with the rounding error of each addition kept (Knuth's
+// two-sum), x = hi + lo; hi = m 2^e with m in [0.5, 1), so
+// ln x = e ln 2 + ln m + lo / hi, and |ln m| < 0.7 keeps logf's rounding small.
+// (logf(x) itself rounds to half an FP32 ulp of ln x: 4.8e-7 for the sums of
+// ~1e6 terms of a large market, ln x ~ 14, which would put a floor of ~1e-6
+// under the residual.)
+__device__ __forceinline__ float two_sum(float a, float b, float& err) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return s;
+}
+__device__ __forceinline__ double log_row_sum(float a, float b, float c) {
+  float e1, e2;
+  const float s1 = two_sum(a, b, e1);
+  const float hi = two_sum(s1, c, e2);
+  const float lo = __fadd_rn(e1, e2);
+  int ex;
+  const float m = frexpf(hi, &ex);
+  return __dadd_rn((double)ex * 0.69314718055994530942, (double)__fadd_rn(logf(m), __fdividef(lo, hi)));
 }
 
 // The closed-form update of Eq. iteration for one user, in logs.
@@ -306,21 +347,30 @@ __device__ __forceinline__ double log_row_sum(double x) {
 // to ~100 with popularity biases) stay in FP64. For z = log s - 1/2 log n > 0,
 // asinh(e^z) = z + c(z) with c(z) = log1p(sqrt(1 + e^{-2z})) in (ln 2, 0.89],
 // so only the bounded correction c is rounded to FP32 (absolute error ~1e-7).
-// The residual's terms (u^2 and 2 u s) are FP64 exponentials of the FP64
-// state, so the reported residual carries no FP32 rounding. The u^2 summed for
-// the match count (sum n - sum u^2, where sum u^2 is a small part) stays FP32.
+// The residual r = u^2 + 2 u s - n (residual = kResidualExact) is formed from
+// FP64 exponentials of the FP64 state, so a certified residual carries no FP32
+// rounding; inside sweeps (kResidualEstimate), where it only decides when to
+// certify, its terms are FP32 exponentials (absolute error ~2e-7 of n), which
+// keeps two FP64 exponentials per row out of the half-sweep (FP64 throughput
+// is a small fraction of FP32 on this part). The u^2 summed for the match
+// count (sum n - sum u^2, where sum u^2 is a small part) is FP32.
 //
 // omega != 1 over-relaxes the update in the log domain:
 // log u <- log u_old + omega * (update - log u_old) (same fixed point).
 __device__ __forceinline__ RowResult row_update(double ln_sum, double shift, float b2s, double mass,
-                                                double log_u_old, bool residual, double omega = 1.0) {
+                                                double log_u_old, int residual, double omega = 1.0) {
   RowResult o;
   const double log_s = kLnHalf + (double)b2s + shift + ln_sum;
   o.r_rel = 0.0;
   o.r_abs = 0.0;
-  if (residual) {
+  if (residual == kResidualExact) {
     // r = u^2 + 2 u s - n with u^2 = e^{2 log u}, 2 u s = e^{log u + log s + ln 2}
     const double r = exp(2.0 * log_u_old) + exp(log_u_old + log_s + 0.69314718055994530942) - mass;
+    o.r_abs = fabs(r);
+    o.r_rel = fabs(r) / mass;
+  } else if (residual == kResidualEstimate) {
+    const double r = (double)expf((float)(2.0 * log_u_old)) +
+                     (double)expf((float)(log_u_old + log_s + 0.69314718055994530942)) - mass;
     o.r_abs = fabs(r);
     o.r_rel = fabs(r) / mass;
   }
@@ -341,22 +391,37 @@ __device__ __forceinline__ RowResult row_update(double ln_sum, double shift, flo
   return o;
 }
 
-// ---- translation step --------------------------------------------------------
-// Block size of every kernel that computes the translation step. The single-
-// market preparation and the batched one run the same routine with the same
-// block size, so both give the same tau bit for bit (the batch's potentials
-// stay bit-identical to the market's own sweeps).
-constexpr int kTauThreads = 512;
+// ---- translation step and the per-side scalars -------------------------------
+// The translation step moves the log potentials of the side updated last by
+// +tau and those of the side about to be updated by -tau. Everything it needs
+// is kept in the per-market scalars (kSt*): the sums sum e^{2 log u} of both
+// sides and the sides' shifts. The half-sweep that updates a side writes one
+// (max 2 log u, scaled sum, max ell) group per 32 rows; a single-block
+// finalize reduces the groups in a fixed order (the single-market and the
+// batched finalize run the same routine with the same block size, so the
+// batch's potentials stay bit-identical to the market's own sweeps) and
+// computes tau for the next half-sweep; the move itself is recorded as a
+// per-side offset and written to the arrays only when a side is next updated
+// (for the updated side) or at the end of a block of sweeps.
 
 // Block-wide reductions (every thread returns the result; `red` holds
 // blockDim.x / 32 doubles). Sums in a fixed order: a butterfly within each warp
-// (lane 0's value is kept), then the warps in order.
+// (every lane ends with the same value), then the warps in order.
 __device__ __forceinline__ double block_reduce_max(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = v;
   __syncthreads();
   double b = -INFINITY;
   for (int w = 0; w < (int)blockDim.x / 32; ++w) b = fmax(b, red[w]);
+  __syncthreads();
+  return b;
+}
+__device__ __forceinline__ float block_reduce_maxf(float v, float* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = v;
+  __syncthreads();
+  float b = -INFINITY;
+  for (int w = 0; w < (int)blockDim.x / 32; ++w) b = fmaxf(b, red[w]);
   __syncthreads();
   return b;
 }
@@ -370,26 +435,81 @@ __device__ __forceinline__ double block_reduce_sum(double v, double* red) {
   return b;
 }
 
-// log sum_i exp(2 x_i) over one block, with the maximum factored out. Each
-// scaled term e^d (d <= 0) is e^{fl(d)} in FP32 times (1 + (d - fl(d))), which
-// keeps the rounding of d to FP32 out of the term; the terms are summed in
-// FP64. A NaN x gives NaN.
-__device__ __forceinline__ double block_log_sum_exp2(const double* __restrict__ x, int64_t n, double* red) {
-  double mx = -INFINITY;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, 2.0 * x[i]);
-  const double top = block_reduce_max(mx, red);
-  double s = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const double d = __dadd_rn(2.0 * x[i], -top);
-    const float dh = (float)d;
-    s = __fma_rn((double)expf(dh), __dadd_rn(1.0, __dadd_rn(d, -(double)dh)), s);
+// The group of one warp's 32 rows (lanes with valid = false contribute
+// nothing), as {m, s, e, 0}: a reference m near the max of 2 log u (the max of
+// the FP32-rounded values), the sum s of e^{2 log u - m} (the argument formed
+// in FP64, the terms in FP32, summed by an FP32 butterfly whose result every
+// lane shares), and e, a max of ell (of the FP32-rounded values; it serves as
+// a shift, and e^{ell - shift} may exceed 1 by a rounding). Warp-collective;
+// every lane returns the same group. A NaN potential makes s NaN (the
+// translation step then falls back to tau = 0). One FP64 operation per row:
+// FP64 throughput is a small fraction of FP32 on this part.
+__device__ __forceinline__ float4 warp_group(double lu, double ell, bool valid) {
+  float m = valid ? (float)(2.0 * lu) : -INFINITY;
+  float e = valid ? (float)ell : -INFINITY;
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    e = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, o));
   }
-  return top + log(block_reduce_sum(s, red));
+  float t = (valid && m > -INFINITY) ? expf((float)__dadd_rn(2.0 * lu, -(double)m)) : 0.0f;
+  if (valid && isnan(lu)) t = NAN;
+  for (int o = 16; o > 0; o >>= 1) t = __fadd_rn(t, __shfl_xor_sync(0xffffffffu, t, o));
+  return make_float4(m, t, e, 0.0f);
 }
 
-__device__ __forceinline__ double log_add_exp(double a, double b) {
-  const double hi = fmax(a, b), lo = fmin(a, b);
-  return __dadd_rn(hi, log1p(exp(__dadd_rn(lo, -hi))));
+// The empty group (no rows).
+__device__ __forceinline__ float4 empty_group() { return make_float4(-INFINITY, 0.0f, -INFINITY, 0.0f); }
+
+// (hi, lo) += (h2, l2): an FP32 sum carried with its rounding error. The
+// two-sum is error-free and symmetric in its operands, so butterfly partners
+// end with the same pair.
+__device__ __forceinline__ void pair_add(float& hi, float& lo, float h2, float l2) {
+  float e;
+  hi = two_sum(hi, h2, e);
+  lo = __fadd_rn(__fadd_rn(lo, l2), e);
+}
+
+// Reduce `ng` groups in a fixed order (every thread returns the results):
+// lmax = max e (the side's shift), and log sum e^{2 log u} = top + ln(hi + lo),
+// where top = max m and hi + lo = sum s e^{m - top} (FP32 terms summed with
+// their rounding errors kept; the logarithm is taken by the caller, once).
+struct GroupTotal {
+  float lmax, top, hi, lo;
+};
+__device__ __forceinline__ GroupTotal block_reduce_groups(const float4* __restrict__ grp, int64_t ng, float* red) {
+  float mm = -INFINITY, me = -INFINITY;
+  for (int64_t i = threadIdx.x; i < ng; i += blockDim.x) {
+    const float4 q = grp[i];
+    mm = fmaxf(mm, q.x);
+    me = fmaxf(me, q.z);
+  }
+  GroupTotal r;
+  r.top = block_reduce_maxf(mm, red);
+  r.lmax = block_reduce_maxf(me, red);
+  float hi = 0.0f, lo = 0.0f;
+  for (int64_t i = threadIdx.x; i < ng; i += blockDim.x) {
+    const float4 q = grp[i];
+    if (q.x > -INFINITY || isnan(q.y)) pair_add(hi, lo, q.y * expf(q.x - r.top), 0.0f);
+  }
+  for (int o = 16; o > 0; o >>= 1)
+    pair_add(hi, lo, __shfl_xor_sync(0xffffffffu, hi, o), __shfl_xor_sync(0xffffffffu, lo, o));
+  if (threadIdx.x % 32 == 0) {
+    red[2 * (threadIdx.x / 32)] = hi;
+    red[2 * (threadIdx.x / 32) + 1] = lo;
+  }
+  __syncthreads();
+  hi = 0.0f;
+  lo = 0.0f;
+  for (int w = 0; w < (int)blockDim.x / 32; ++w) pair_add(hi, lo, red[2 * w], red[2 * w + 1]);
+  __syncthreads();
+  r.hi = hi;
+  r.lo = lo;
+  return r;
+}
+
+// log sum e^{2 log u} of a reduced side (one thread).
+__device__ __forceinline__ double group_log_sum(const GroupTotal& t) {
+  return (double)t.top + log_row_sum(t.hi, t.lo, 0.0f);
 }
 
 // The translation step (an extension; Sec. 5 names acceleration from optimal
@@ -400,34 +520,77 @@ __device__ __forceinline__ double log_add_exp(double a, double b) {
 //   const + tau (sum mass_P - sum mass_O) - 1/2 e^{2 tau} P - 1/2 e^{-2 tau} O,
 // P = sum_P e^{2 log p}, O = sum_O e^{2 log o}, and its maximiser is
 // tau = 1/2 log z with z the positive root of P z^2 - dm z - O = 0,
-// dm = sum mass_P - sum mass_O: z = (dm + R) / (2 P) for dm >= 0 and
-// 2 O / (R - dm) for dm < 0 (no cancellation), R = sqrt(dm^2 + 4 P O), all in
-// logarithms. Non-finite inputs (non-finite potentials, which the half-sweep
-// reports) give tau = 0.
+// dm = sum mass_P - sum mass_O, given log_p = log P and log_o = log O.
+// dm = 0: z = sqrt(O / P). Otherwise, with L = log |dm|,
+// w = log(4 P O / dm^2) and q = log(1 + sqrt(1 + e^w)), the root
+// z = (dm + R) / (2 P) for dm > 0 and 2 O / (R - dm) for dm < 0,
+// R = sqrt(dm^2 + 4 P O) = |dm| sqrt(1 + e^w), is
+// log z = L + q - log 2 - log P (dm > 0) or log 2 + log O - L - q (dm < 0),
+// with no cancellation; for |w| > 60, q = w / 2 or log 2 to double precision.
+// Non-finite inputs (non-finite potentials, which the half-sweep reports)
+// give tau = 0.
 __device__ __forceinline__ double translation_tau(double log_p, double log_o, double dm) {
   const double ln2 = 0.69314718055994530942;
-  const double log_4po = __dadd_rn(__dadd_rn(2.0 * ln2, log_p), log_o);
-  const double log_r = dm != 0.0 ? 0.5 * log_add_exp(2.0 * log(fabs(dm)), log_4po) : 0.5 * log_4po;
   double log_z;
-  if (dm >= 0.0) {
-    const double log_num = dm > 0.0 ? log_add_exp(log(dm), log_r) : log_r;
-    log_z = __dadd_rn(__dadd_rn(log_num, -ln2), -log_p);
+  if (dm == 0.0) {
+    log_z = 0.5 * __dadd_rn(log_o, -log_p);
   } else {
-    log_z = __dadd_rn(__dadd_rn(ln2, log_o), -log_add_exp(log_r, log(-dm)));
+    const double L = log(fabs(dm));
+    const double w = __dadd_rn(__dadd_rn(__dadd_rn(2.0 * ln2, log_p), log_o), -2.0 * L);
+    const double q = w > 60.0 ? 0.5 * w : (w < -60.0 ? ln2 : log1p(sqrt(1.0 + exp(w))));
+    log_z = dm > 0.0 ? __dadd_rn(__dadd_rn(__dadd_rn(L, q), -ln2), -log_p)
+                     : __dadd_rn(__dadd_rn(__dadd_rn(ln2, log_o), -L), -q);
   }
   const double tau = 0.5 * log_z;
   return isfinite(tau) ? tau : 0.0;
 }
 
-// tau for the partner side P (potentials log_p, rows_p) and own side O over
-// one block of kTauThreads threads (every thread returns it); `red` holds
-// kTauThreads / 32 doubles.
-__device__ __forceinline__ double block_translation_tau(const double* __restrict__ log_p, int64_t rows_p,
-                                                        const double* __restrict__ log_o, int64_t rows_o, double dm,
-                                                        double* red) {
-  const double lp = block_log_sum_exp2(log_p, rows_p, red);
-  const double lo = block_log_sum_exp2(log_o, rows_o, red);
-  return translation_tau(lp, lo, dm);
+// Scalars of a half-sweep that updates side `own` (one thread, before the
+// pass): the translation step it takes (tau = 0 unless `translate`), the
+// partner shift the pass adds back (natural log) and the own offset under
+// which it reads the entering potentials.
+__device__ __forceinline__ void prep_scalars(double* st, int own, int translate) {
+  const int par = 1 - own;
+  const double tau = translate ? st[kStTauNext] : 0.0;
+  st[kStTauUsed] = tau;
+  st[kStShift] = st[kStLmax + par] + st[kStOff + par] + tau;
+  st[kStOwnOff] = st[kStOff + own] - tau;
+}
+
+// Scalars after a half-sweep that updated side `own` (one thread): the own
+// side's shift and sum from its groups (its arrays now hold true values), the
+// step taken before the pass recorded on the partner, and tau for the next
+// half-sweep, which updates the partner against this side
+// (dm_next = sum mass_own - sum mass_partner).
+__device__ __forceinline__ double finite_or_zero(double v) { return (v > -INFINITY && v < INFINITY) ? v : 0.0; }
+__device__ __forceinline__ void finish_scalars(double* st, int own, const GroupTotal& g, double dm_next) {
+  const int par = 1 - own;
+  const double tau = st[kStTauUsed];
+  const double log_s_own = group_log_sum(g);
+  // non-finite potentials are reported by the pass (its non-finite count)
+  st[kStLmax + own] = finite_or_zero((double)g.lmax);
+  st[kStLogS + own] = log_s_own;
+  st[kStOff + own] = 0.0;
+  st[kStOff + par] += tau;
+  st[kStLogS + par] += 2.0 * tau;
+  st[kStTauUsed] = 0.0;
+  st[kStTauNext] = translation_tau(log_s_own, st[kStLogS + par], dm_next);
+}
+
+// Scalars of both sides from their reduced groups (one thread; potentials set
+// from outside a sweep): shifts, sums, no offsets, and tau for the next
+// half-sweep, which updates X against Y (dm = sum m - sum n).
+__device__ __forceinline__ void rescan_scalars(double* st, const GroupTotal& x, const GroupTotal& y,
+                                               double dm_y_minus_x) {
+  const double sx = group_log_sum(x), sy = group_log_sum(y);
+  st[kStLmax + 0] = finite_or_zero((double)x.lmax);
+  st[kStLmax + 1] = finite_or_zero((double)y.lmax);
+  st[kStLogS + 0] = sx;
+  st[kStLogS + 1] = sy;
+  st[kStOff + 0] = 0.0;
+  st[kStOff + 1] = 0.0;
+  st[kStTauUsed] = 0.0;
+  st[kStTauNext] = translation_tau(sy, sx, dm_y_minus_x);
 }
 
 __device__ __forceinline__ uint64_t global_timer_ns() {
