@@ -713,7 +713,7 @@ def run_batched(args):
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16", "data": "synthetic", "config": batched_config(mks),
             "roofline": rl_primary, "roofline_secondary": rl_secondary,
-            "clocks": clk, "gpu_launches": 6 * args.steps,
+            "clocks": clk, "gpu_launches": 6 * args.steps + 1,
             "timing": "value: K batched sweeps replayed as one CUDA graph, CUDA events on the batch stream"}
     if seq_ms is not None:
         line["sequential"] = {"ms_per_sweep": seq_ms / args.steps,
@@ -734,7 +734,7 @@ def run_batched(args):
                       if (balance < 0.1).any() else None,
                       "slowest": [{"N": mks[i].N, "M": mks[i].M, "sweeps": int(sweeps[i]),
                                    "converged": bool(conv[i])} for i in np.argsort(-sweeps)[:5]]}})
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def run_serving(args):
@@ -786,6 +786,91 @@ def run_ranking(args):
                                                  "converged": tight["converged"],
                                                  "residual_inf": tight["residual_inf"]},
                       "dtype": "bf16"}), flush=True)
+
+
+def solve_block(tu, h, mk, hu, hv) -> dict:
+    """The workload solved to tol 1e-6 from u = v = 1 (tu_ipfp_solve, the
+    translation step on, no relaxation): sweeps, wall time, the certified
+    residual (row equations of Eq. IPFP, FP64 terms) and the match count from
+    both sides of the returned potentials; then, for contrast, the same number
+    of sweeps of Eq. iteration itself (translation step off) from u = v = 1 and
+    the residual they reach."""
+    import numpy as np
+    t0 = time.perf_counter()
+    info = tu.tu_ipfp_solve(h, 1e-6, 200, False)
+    wall = time.perf_counter() - t0
+    tu.tu_get_potentials(h, hu, hv)
+    lu = hu.numpy().astype(np.float64)
+    lv = hv.numpy().astype(np.float64)
+    cx = float(np.sum(mk.n) - np.sum(np.exp(2.0 * lu)))
+    cy = float(np.sum(mk.m) - np.sum(np.exp(2.0 * lv)))
+    out = {"tol": 1e-6, "status": int(info["status"]), "converged": bool(info["converged"]),
+           "sweeps": int(info["sweeps"]), "wall_s": wall, "residual_inf_certified": info["residual_inf"],
+           "residual_l1_certified": info["residual_l1"], "match_count": info["match_count"],
+           "match_count_rows": cx, "match_count_cols": cy,
+           "what": "tu_ipfp_solve(tol 1e-6, warm_start 0): translation step before every half-sweep, no "
+                   "relaxation; residual certified by an extra pass with FP64 terms; match counts sum n - sum u^2 "
+                   "and sum m - sum v^2 of the returned potentials (FP32 copies, FP64 sums on the host)"}
+    tu.tu_market_set_translation(h, False)
+    tu.tu_ipfp_solve(h, 0.0, 0, False)  # u = v = 1 without sweeping
+    plain = tu.tu_ipfp_sweep(h, max(1, out["sweeps"]), residual=True)
+    tu.tu_market_set_translation(h, True)
+    out["plain_same_sweeps_residual"] = plain
+    return out
+
+
+def quantisation_error(dev) -> dict:
+    """BF16 factors against the unrounded (FP32) factors they were rounded
+    from, on the fused workload's recipe at N = M = 4,000: the fused path
+    solves the BF16 market and the dense FP32 path the unrounded one (both to
+    1e-7 through the library); reported: relative error of mu (max and median
+    over all pairs) and of the match count. Information, not a tolerance: the
+    parity bars compare with the oracle on the same rounded factors."""
+    import numpy as np
+    import torch
+
+    import paper_2411_19214_gb300 as tu
+    from synth import fused_market
+    out = {}
+    mks = {"bf16": fused_market(4000, 4000, seed=1002), "fp32": fused_market(4000, 4000, seed=1002, dtype="fp32")}
+    mus, counts = {}, {}
+    for key, mk in mks.items():
+        mkt = tu.from_synth(mk, path="fused" if key == "bf16" else "dense", device=str(dev))
+        try:
+            info = mkt.solve(tol=1e-7, max_iter=200)
+            mus[key] = mkt.mu_block().double().cpu().numpy()
+            counts[key] = info["match_count"]
+            out[f"{key}_sweeps"] = info["sweeps"]
+            out[f"{key}_residual"] = info["residual_inf"]
+        finally:
+            mkt.close()
+    rel = np.abs(mus["bf16"] / mus["fp32"] - 1.0)
+    out.update({"market": "fused recipe (d=64, lognormal biases both sides, sigma=0.5) at N=M=4,000",
+                "mu_rel_err_max": float(rel.max()), "mu_rel_err_median": float(np.median(rel)),
+                "match_count_rel_err": abs(counts["bf16"] / counts["fp32"] - 1.0),
+                "what": "fused BF16 path on bf16-rounded factors vs dense FP32 path on the unrounded FP32 factors"})
+    torch.cuda.synchronize()
+    return out
+
+
+def sub_args(args, workload: str, steps=None):
+    """The arguments of a secondary workload measured inside the default run."""
+    a = argparse.Namespace(**vars(args))
+    a.workload = workload
+    a.no_extras = False  # the secondary lines' own solve and comparison blocks are kept
+    a.no_cpu_baseline = True
+    a.fp8 = False
+    a.shape = None
+    if steps is not None:
+        a.steps = steps
+    return a
+
+
+def sub_line(line) -> dict:
+    """The fields of a secondary workload's line kept in the default line."""
+    keep = ("metric", "value", "unit", "ms_per_step", "dtype", "config", "roofline", "roofline_secondary", "clocks",
+            "e2e", "solve", "sequential", "gpu_launches", "residual_inf_after")
+    return {k: line[k] for k in keep if line is not None and k in line}
 
 
 def run_ours(args):
@@ -907,6 +992,9 @@ def run_ours(args):
         elem = 2 if mk.dtype == "bf16" else 4
         h2d = 2 * (mk.N + mk.M) * mk.d * elem  # F, K (N x d) and G, L (M x d)
         d2h = (mk.N + mk.M) * 4
+        solve = None
+        if not args.no_extras and rank == 0:
+            solve = solve_block(tu, h, mk, hu, hv)
     finally:
         tu.tu_market_destroy(h)
 
@@ -920,7 +1008,7 @@ def run_ours(args):
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
-        return
+        return None
     peaks = load_peaks()
     sweeps_per_s = world * args.steps / (ms / 1e3)
     pairs_per_sweep = 2.0 * mk.N * mk.M
@@ -968,8 +1056,9 @@ def run_ours(args):
             "residual_inf_after": residual, "sweeps_run": args.warmup + args.steps,
             "roofline": roofline,
             "clocks": clk,
-            # per half-sweep: partner max, partner preparation, the pass, the FP64 reduction
-            "gpu_launches": 8 * args.steps,
+            # per half-sweep: partner preparation, the pass, the FP64 reduction; per block of
+            # sweeps: the two kernels that write the translation steps' offsets into the potentials
+            "gpu_launches": 6 * args.steps + 2,
             "timing": "value: K sweeps replayed as one CUDA graph, CUDA events on the market stream; "
                       "roofline: the same K sweeps launched directly with an event pair per half-sweep kernel",
             "e2e": {"value": world * e2e_steps / e2e_s, "unit": "sweeps/s", "h2d_bytes_per_step": h2d,
@@ -1000,9 +1089,16 @@ def run_ours(args):
                                           + ", after one untimed call"}
     if cpu is not None:
         line["cpu_baseline"] = cpu
-    print(json.dumps(line), flush=True)
+    if solve is not None:
+        line["solve"] = solve
+    if cfg["path"] == "fused" and not args.no_extras and rank == 0 and world == 1 and args.shape is None \
+            and not args.fp8:
+        line["quantisation_error"] = quantisation_error(dev)
+        line["dense"] = sub_line(run_ours(sub_args(args, "dense")))
+        line["batched"] = sub_line(run_batched(sub_args(args, "batched", steps=5)))
     if world > 1:
         dist.destroy_process_group()
+    return line
 
 
 def main():
@@ -1037,7 +1133,7 @@ def main():
         run_paper_shapes(args)
         return
     if args.workload == "batched" and args.impl == "ours":
-        run_batched(args)
+        print(json.dumps(run_batched(args)), flush=True)
         return
     if args.workload == "ranking" and args.impl == "ours":
         run_ranking(args)
@@ -1067,7 +1163,9 @@ def main():
     if args.impl == "reference":
         run_reference(args)
     else:
-        run_ours(args)
+        line = run_ours(args)
+        if line is not None:
+            print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":

@@ -101,7 +101,8 @@ typedef struct {
  * they are folded into the potentials in log space. Sizes: 1 <= N, M <= 2^31
  * and 1 <= d <= 4096 (TU_ERR_INVALID_ARG otherwise); the fused path takes
  * d <= 64 (2d fills one 128-wide MMA inner dimension), FP8 factors only on the
- * fused path, and a dense market at most 200 GB of A-hat and its transpose
+ * fused path, a dense market at most 200 GB of A-hat and its transpose, and a
+ * device of compute capability 10.3 (the library is built for sm_103a only)
  * (TU_ERR_UNSUPPORTED otherwise). On success *out owns device memory of about
  * (N + M) * 2 * d * 2 bytes (fused) or 2 * N * M * 4 bytes (dense), a staging
  * buffer for factor uploads of 2 * max(N, M) * d * (2 for BF16, else 4) bytes,
@@ -182,6 +183,16 @@ tu_status tu_ipfp_solve_ranking(tu_market_t mkt, int k, int64_t sample, int chec
  * host or device. Either pointer may be NULL to skip that side. */
 tu_status tu_get_potentials(tu_market_t mkt, float* log_u, float* log_v);
 tu_status tu_set_potentials(tu_market_t mkt, const float* log_u, const float* log_v);
+
+/* The same state in full precision: log u (N doubles) and log v (M doubles),
+ * host or device, either pointer NULL to skip that side. The FP32 copies above
+ * round log u to about 6e-8 |log u|, which moves u by up to a few 1e-6 for the
+ * potentials of popular users (|log u| ~ 40): enough to lift a converged
+ * state's residual above a 1e-6 tolerance. A checkpoint taken and restored
+ * with these calls resumes a solve exactly. The get call synchronises the
+ * market's stream. */
+tu_status tu_get_potentials_f64(tu_market_t mkt, double* log_u, double* log_v);
+tu_status tu_set_potentials_f64(tu_market_t mkt, const double* log_u, const double* log_v);
 
 /* Over-relaxation of the log-domain update, an acceleration the paper does not
  * have (its Sec. 5 names acceleration as future work): log u <- log u +
@@ -313,7 +324,13 @@ tu_status tu_profile_read(tu_market_t mkt, double* pass_ms, int64_t* passes);
  *   own_log_u_out   rows FP32: the new log u (may not alias own_log_u_in)
  * residual_out (host, may be NULL): if given, the call synchronises the stream
  * and stores max_r |u_r^2 + 2 u_r s_r - n_r| / n_r of the entering state (row
- * equations of Eq. IPFP); otherwise the call only enqueues work on `stream`.
+ * equations of Eq. IPFP), and reports device-side failures: TU_ERR_TIMEOUT (a
+ * bounded wait ran out) and TU_ERR_NONFINITE (a computed potential is NaN or
+ * infinite). Otherwise the call only enqueues work on `stream` and reports no
+ * device-side failure; pass residual_out to have them checked.
+ * A pointer of another device, or host memory, gives TU_ERR_INVALID_ARG; a
+ * device other than compute capability 10.3 (the library is built for sm_103a
+ * only) gives TU_ERR_UNSUPPORTED.
  * Limits: 1 <= rows <= 65536 and 1 <= cols <= 1048576 (TU_ERR_UNSUPPORTED
  * beyond them, and for kp other than 64 or 128); the exponent-range condition
  * of tu_market_create applies and is not checked here.

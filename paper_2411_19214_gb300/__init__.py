@@ -69,6 +69,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tu_mu_block": (I32, [V, I64, I64, I64, I64, V, I64]),
         "tu_topk_partners": (I32, [V, I32, I32, I64, I64, V, V]),
         "tu_get_potentials": (I32, [V, V, V]),
+        "tu_get_potentials_f64": (I32, [V, V, V]),
+        "tu_set_potentials_f64": (I32, [V, V, V]),
         "tu_set_potentials": (I32, [V, V, V]),
         "tu_fused_halfsweep_noalloc": (I32, [I64, I64, I64, V, V, V, V, V, V, V, D, V, ctypes.POINTER(D), V]),
         "tu_market_set_relaxation": (I32, [V, D]),
@@ -271,6 +273,15 @@ def tu_set_potentials(h: int, log_u=None, log_v=None) -> None:
     _check(load().tu_set_potentials(h, _ptr(log_u), _ptr(log_v)), "tu_set_potentials", h)
 
 
+def tu_get_potentials_f64(h: int, log_u=None, log_v=None) -> None:
+    """The FP64 solver state (float64 arrays or tensors, host or device)."""
+    _check(load().tu_get_potentials_f64(h, _ptr(log_u), _ptr(log_v)), "tu_get_potentials_f64", h)
+
+
+def tu_set_potentials_f64(h: int, log_u=None, log_v=None) -> None:
+    _check(load().tu_set_potentials_f64(h, _ptr(log_u), _ptr(log_v)), "tu_set_potentials_f64", h)
+
+
 def tu_fused_halfsweep_noalloc(rows: int, cols: int, kp: int, own_packed, partner_packed, own_bias, own_mass,
                                own_log_u_in, partner_bias, partner_log_v, sigma: float, own_log_u_out,
                                residual: bool = False, stream=None) -> Optional[float]:
@@ -470,6 +481,13 @@ class Market:
 
     def set_potentials(self, log_u=None, log_v=None):
         tu_set_potentials(self.handle, log_u, log_v)
+
+    def potentials64(self):
+        """The FP64 state as host numpy arrays (log u, log v)."""
+        lu = np.empty(self.N, np.float64)
+        lv = np.empty(self.M, np.float64)
+        tu_get_potentials_f64(self.handle, lu, lv)
+        return lu, lv
 
     def update_factors(self, F, K, G, L):
         tu_market_update_factors(self.handle, F, K, G, L)

@@ -742,14 +742,9 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
     delete m;
     return TU_ERR_CUDA;
   }
-  if (D.path == TU_PATH_FUSED) {
-    int major = 0, minor = 0;
-    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, m->device);
-    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, m->device);
-    if (major != 10) {
-      delete m;
-      return TU_ERR_UNSUPPORTED;
-    }
+  if (!device_supported(m->device)) {
+    delete m;
+    return TU_ERR_UNSUPPORTED;
   }
   {
     std::lock_guard<std::mutex> lk(g_pool_mu);
@@ -1245,6 +1240,38 @@ tu_status tu_get_potentials(tu_market_t m, float* log_u, float* log_v) {
     }
   }
   return TU_OK;
+}
+
+tu_status tu_get_potentials_f64(tu_market_t m, double* log_u, double* log_v) {
+  TU_TRACE("tu_get_potentials_f64");
+  TU_TRY(check_live(m));
+  Side* sides[2] = {&m->X, &m->Y};
+  double* outs[2] = {log_u, log_v};
+  for (int i = 0; i < 2; ++i) {
+    if (outs[i] == nullptr) continue;
+    // the state is written back after every block of sweeps, so it is the array itself
+    TU_CK(m, cudaMemcpyAsync(outs[i], sides[i]->log_u, (size_t)sides[i]->rows * sizeof(double), cudaMemcpyDefault,
+                             m->stream));
+  }
+  TU_CK(m, cudaStreamSynchronize(m->stream));
+  return TU_OK;
+}
+
+tu_status tu_set_potentials_f64(tu_market_t m, const double* log_u, const double* log_v) {
+  TU_TRACE("tu_set_potentials_f64");
+  TU_TRY(check_live(m));
+  Side* sides[2] = {&m->X, &m->Y};
+  const double* ins[2] = {log_u, log_v};
+  TU_TRY(ensure_staging(m, (size_t)(m->N > m->M ? m->N : m->M) * sizeof(double)));
+  for (int i = 0; i < 2; ++i) {
+    if (ins[i] == nullptr) continue;
+    const void* src = nullptr;
+    TU_TRY(device_view(m, ins[i], (size_t)sides[i]->rows * sizeof(double), 0, &src));
+    TU_CK(m, launch_set_potentials64(m, *sides[i], static_cast<const double*>(src)));
+    TU_CK(m, cudaStreamSynchronize(m->stream));
+  }
+  TU_CK(m, launch_rescan(m));
+  return relax_reset(m);
 }
 
 tu_status tu_set_potentials(tu_market_t m, const float* log_u, const float* log_v) {

@@ -69,13 +69,15 @@ tu_status setup_device(int dev, DeviceScratch* out) {
   return TU_OK;
 }
 
-bool on_device(const void* p) {
+// Device (or managed) memory of device `dev`: a buffer of another GPU would be
+// read through a peer mapping, or fault where peer access is off.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 // ell_c = log v_c + b_c / (2 sigma) (same rounding of b / (2 sigma) as a market), per-block maxima.
@@ -186,20 +188,16 @@ extern "C" tu_status tu_fused_halfsweep_noalloc(int64_t rows, int64_t cols, int6
   if (rows > kNaMaxRows || cols > kNaMaxCols) return TU_ERR_UNSUPPORTED;
   if (kp != 64 && kp != 128) return TU_ERR_UNSUPPORTED;
   if (((uintptr_t)own_packed | (uintptr_t)partner_packed) & 15u) return TU_ERR_INVALID_ARG;
-  const void* dev_ptrs[] = {own_packed, partner_packed, own_mass, own_log_u_in, partner_log_v, own_log_u_out,
-                            own_bias, partner_bias};
-  for (const void* p : dev_ptrs)
-    if (p != nullptr && !on_device(p)) return TU_ERR_INVALID_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
     cudaGetLastError();
     return TU_ERR_CUDA;
   }
-  int major = 0;
-  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess || major != 10) {
-    cudaGetLastError();
-    return TU_ERR_UNSUPPORTED;
-  }
+  const void* dev_ptrs[] = {own_packed, partner_packed, own_mass, own_log_u_in, partner_log_v, own_log_u_out,
+                            own_bias, partner_bias};
+  for (const void* p : dev_ptrs)
+    if (p != nullptr && !on_device(p, dev)) return TU_ERR_INVALID_ARG;
+  if (!device_supported(dev)) return TU_ERR_UNSUPPORTED;
   DeviceScratch ds;
   tu_status st = setup_device(dev, &ds);
   if (st != TU_OK) return st;

@@ -105,6 +105,16 @@ __global__ void k_set_potentials(const float* __restrict__ src, const float* __r
   }
 }
 
+__global__ void k_set_potentials64(const double* __restrict__ src, const float* __restrict__ b2s, int64_t rows,
+                                   double* __restrict__ log_u, double* __restrict__ ell) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double lu = src[i];
+    log_u[i] = lu;
+    ell[i] = (b2s != nullptr) ? lu + (double)b2s[i] : lu;
+  }
+}
+
 __global__ void k_get_potentials(const double* __restrict__ log_u, int64_t rows, float* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -326,6 +336,12 @@ cudaError_t launch_reset_potentials(tu_market* m, Side& s) {
 cudaError_t launch_get_potentials(tu_market* m, Side& s, float* out_dev) {
   const int g = grid_for(s.rows, m->num_sms);
   k_get_potentials<<<g, kThreads, 0, m->stream>>>(s.log_u, s.rows, out_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_potentials64(tu_market* m, Side& s, const double* log_u_dev) {
+  const int g = grid_for(s.rows, m->num_sms);
+  k_set_potentials64<<<g, kThreads, 0, m->stream>>>(log_u_dev, s.b2s, s.rows, s.log_u, s.ell);
   return cudaGetLastError();
 }
 

@@ -104,6 +104,18 @@ struct RelaxControl {
   double observe(int done, double r, double tol);
 };
 
+// The library's kernels are built for sm_103a only (compute capability 10.3):
+// any other device would fail at the first launch ("no kernel image").
+inline bool device_supported(int dev) {
+  int major = 0, minor = 0;
+  if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return major == 10 && minor == 3;
+}
+
 // Sweeps in the next block of a solve loop (the residual is read back between
 // blocks). The first block is one sweep; each later one is at most twice the
 // previous block, cut to the sweeps the per-sweep decay measured over the last
@@ -195,6 +207,7 @@ cudaError_t launch_pack_factors(tu_market* m, Side& s, const void* A, const void
 cudaError_t launch_init_side(tu_market* m, Side& s, const float* bias_dev, int has_bias);
 cudaError_t launch_reset_potentials(tu_market* m, Side& s);
 cudaError_t launch_set_potentials(tu_market* m, Side& s, const float* log_u_dev);
+cudaError_t launch_set_potentials64(tu_market* m, Side& s, const double* log_u_dev);
 cudaError_t launch_get_potentials(tu_market* m, Side& s, float* out_dev);  // FP64 state -> FP32
 cudaError_t launch_row_norms(tu_market* m, Side& s, float* out_max);
 // FP8 markets: max |entry| of the FP32 factor pair (A, B: rows x d each) into *out_max

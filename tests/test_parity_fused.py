@@ -261,3 +261,76 @@ def test_small_tiles_bit_identical(gpu_lib):
     finally:
         a.close()
         b.close()
+
+
+def test_full_size_solve_reaches_tol(gpu_lib):
+    """The benchmark market (1e6 x 1e6, d = 64, bf16, lognormal biases on both
+    sides, sigma = 0.5) solved to tol 1e-6: with the translation step the solve
+    certifies a residual <= 1e-6 (row equations of Eq. IPFP, FP64 terms) within
+    20 sweeps. From the GPU's FP64 potentials the oracle recomputes in FP64 the
+    row sums of 256 sampled rows, whose residuals must meet 1e-6 and stay within
+    the FP32 accuracy of the row sums of the certified value, and of 256 sampled
+    columns, whose equations the last v update solves; the match counts of the
+    two sides (sum n - sum u^2, sum m - sum v^2) agree to 1e-6 relative, and the
+    reported count is the column form."""
+    tu = gpu_lib
+    mk = fused_market()
+    stream = torch.cuda.Stream()
+    mkt = tu.from_synth(mk, path="fused", stream=stream, partition=65536)
+    try:
+        info = mkt.solve(tol=1e-6, max_iter=200)
+        assert info["converged"] and info["sweeps"] <= 20 and info["residual_inf"] <= 1e-6, info
+        lu, lv = mkt.potentials64()
+        f = mk.f64()
+        rng = np.random.default_rng(21)
+        rows = np.sort(rng.choice(mk.N, 256, replace=False))
+        cols = np.sort(rng.choice(mk.M, 256, replace=False))
+        log_s, _ = oracle.sampled_row_update(mk.F, mk.K, mk.G, mk.L, f["sigma"], f["n"], lv, rows, mk.bias_x,
+                                             mk.bias_y)
+        u = np.exp(lu[rows])
+        r_rows = np.abs(u * u + 2.0 * u * np.exp(log_s) - f["n"][rows]) / f["n"][rows]
+        log_t, _ = oracle.sampled_row_update(mk.G, mk.L, mk.F, mk.K, f["sigma"], f["m"], lu, cols, mk.bias_y,
+                                             mk.bias_x)
+        v = np.exp(lv[cols])
+        r_cols = np.abs(v * v + 2.0 * v * np.exp(log_t) - f["m"][cols]) / f["m"][cols]
+        cx = float(np.sum(f["n"]) - np.sum(np.exp(2.0 * lu)))
+        cy = float(np.sum(f["m"]) - np.sum(np.exp(2.0 * lv)))
+        print(f"1e6 solve: {info['sweeps']} sweeps, certified {info['residual_inf']:.2e}; sampled FP64 rows "
+              f"{r_rows.max():.2e}, columns {r_cols.max():.2e}; match counts {cx:.6f} / {cy:.6f}")
+        assert r_rows.max() <= 1e-6 and r_rows.max() <= info["residual_inf"] + 5e-7
+        assert r_cols.max() <= 1e-6
+        assert abs(cx - cy) <= 1e-6 * cy
+        assert info["match_count"] == pytest.approx(cy, rel=1e-9)
+    finally:
+        mkt.close()
+
+
+def test_fp64_checkpoint_resumes_a_converged_solve_exactly(gpu_lib):
+    """A converged state saved with tu_get_potentials_f64 and restored into a
+    fresh market with tu_set_potentials_f64 certifies the same residual, bit
+    for bit, and a warm-started solve returns at once; the FP32 copies of
+    tu_get_potentials round the popular users' large |log u| and move that
+    residual."""
+    tu = gpu_lib
+    mk = _mk(3000, 2500, 32, seed=23, n_kind="unit", m_kind="unit")
+    a = tu.from_synth(mk, path="fused")
+    b = tu.from_synth(mk, path="fused")
+    try:
+        info = a.solve(tol=1e-6, max_iter=500)
+        assert info["converged"], info
+        lu, lv = a.potentials64()
+        assert np.abs(lu).max() > 4.0  # the biases give potentials far from 0
+        tu.tu_set_potentials_f64(b.handle, lu, lv)
+        res_b = b.sweep(0, residual=True)
+        assert res_b == a.sweep(0, residual=True)
+        warm = b.solve(tol=1e-6, max_iter=500, warm_start=True)
+        assert warm["converged"] and warm["sweeps"] == 0, warm
+        lu2, lv2 = b.potentials64()
+        np.testing.assert_array_equal(lu2, lu)
+        np.testing.assert_array_equal(lv2, lv)
+        f32u, f32v = a.potentials()
+        b.set_potentials(f32u, f32v)
+        print(f"certified residual: FP64 checkpoint {res_b:.3e}, FP32 checkpoint {b.sweep(0, residual=True):.3e}")
+    finally:
+        a.close()
+        b.close()

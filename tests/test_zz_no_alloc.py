@@ -83,3 +83,32 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(gpu_lib):
     with pytest.raises(tu.TuError) as e:
         tu.tu_fused_halfsweep_noalloc(10, 10, 64, p, p, None, m, h, None, t, 0.5, t)
     assert e.value.status == tu.TU_ERR_INVALID_ARG
+
+
+def test_noalloc_reports_nonfinite_potentials_when_asked(gpu_lib):
+    """A NaN among the partner potentials makes computed potentials NaN: with
+    residual_out the call synchronises and returns TU_ERR_NONFINITE; without it
+    the call only enqueues work and reports nothing (the header says so). The
+    device check of every pointer (a buffer of another device or host memory
+    is refused) is exercised by the host-pointer case of the refusal test; a
+    second GPU is not available here."""
+    tu = gpu_lib
+    N, M, d, kp = 300, 257, 16, 64
+    mk = make_market(N, M, d, sigma=0.5, seed=5, dtype="bf16")
+    own = _packed(mk.F, mk.K, kp)
+    par = _packed(mk.G, mk.L, kp)
+    mass = torch.from_numpy(mk.n).cuda()
+    lu0 = torch.zeros(N, dtype=torch.float32, device="cuda")
+    lv0 = torch.zeros(M, dtype=torch.float32, device="cuda")
+    lv0[17] = float("nan")
+    out = torch.empty(N, dtype=torch.float32, device="cuda")
+    tu.tu_fused_halfsweep_noalloc(N, M, kp, own, par, None, mass, lu0, None, lv0, mk.sigma, out)
+    torch.cuda.synchronize()
+    with pytest.raises(tu.TuError) as e:
+        tu.tu_fused_halfsweep_noalloc(N, M, kp, own, par, None, mass, lu0, None, lv0, mk.sigma, out, residual=True)
+    assert e.value.status == tu.TU_ERR_NONFINITE
+    # the shared scratch is usable again by the next call
+    lv0[17] = 0.0
+    res = tu.tu_fused_halfsweep_noalloc(N, M, kp, own, par, None, mass, lu0, None, lv0, mk.sigma, out,
+                                        residual=True)
+    assert np.isfinite(res) and torch.isfinite(out).all()
