@@ -194,6 +194,30 @@ tu_status tu_set_potentials(tu_market_t mkt, const float* log_u, const float* lo
 tu_status tu_get_potentials_f64(tu_market_t mkt, double* log_u, double* log_v);
 tu_status tu_set_potentials_f64(tu_market_t mkt, const double* log_u, const double* log_v);
 
+/* One shard of a market split across GPUs (Sec. 3.3: within a half-sweep each
+ * user's update depends only on the other side's fixed potentials, so the
+ * users of a side can be split into contiguous shards, one per GPU, each
+ * GPU holding every factor). side 0 updates X users [lo, hi) from the
+ * market's current log v (the u step of Eq. iteration), side 1 updates Y users
+ * [lo, hi) from the current log u (the v step); the other users of that side
+ * keep their potentials. No translation step is taken (it needs both sides'
+ * sums over all shards: the caller computes it from the gathered potentials
+ * and writes them back with tu_set_potentials_f64); after the pass the
+ * market's kept shifts and sums are recomputed from the stored potentials
+ * (an O(N + M) pass), so any call may follow. residual_out (host, 2
+ * doubles, may be NULL): max |r| / mass and sum |r| over the shard's users of
+ * the equations of Eq. IPFP for that side (rows for side 0, columns for side
+ * 1) at the entering state, FP64 terms; the MAX and SUM over shards give the
+ * market's. Requires the fused path (TU_ERR_UNSUPPORTED otherwise) and
+ * 0 <= lo <= hi <= users of the side (TU_ERR_INVALID_ARG otherwise).
+ * Synchronises the market's stream. */
+tu_status tu_ipfp_half_sweep_range(tu_market_t mkt, int side, int64_t lo, int64_t hi, double* residual_out);
+
+/* FP64 log potentials of users [lo, hi) of one side (side 0: log u, 1: log v)
+ * into out (hi - lo doubles, host or device), e.g. a shard's share of an
+ * all-gather. Synchronises the market's stream. */
+tu_status tu_get_potentials_range_f64(tu_market_t mkt, int side, int64_t lo, int64_t hi, double* out);
+
 /* Over-relaxation of the log-domain update, an acceleration the paper does not
  * have (its Sec. 5 names acceleration as future work): log u <- log u +
  * omega * (update - log u), and the same for v. A fixed point of the relaxed

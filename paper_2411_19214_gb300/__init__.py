@@ -70,6 +70,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tu_topk_partners": (I32, [V, I32, I32, I64, I64, V, V]),
         "tu_get_potentials": (I32, [V, V, V]),
         "tu_get_potentials_f64": (I32, [V, V, V]),
+        "tu_get_potentials_range_f64": (I32, [V, I32, I64, I64, V]),
+        "tu_ipfp_half_sweep_range": (I32, [V, I32, I64, I64, ctypes.POINTER(D)]),
         "tu_set_potentials_f64": (I32, [V, V, V]),
         "tu_set_potentials": (I32, [V, V, V]),
         "tu_fused_halfsweep_noalloc": (I32, [I64, I64, I64, V, V, V, V, V, V, V, D, V, ctypes.POINTER(D), V]),
@@ -280,6 +282,22 @@ def tu_get_potentials_f64(h: int, log_u=None, log_v=None) -> None:
 
 def tu_set_potentials_f64(h: int, log_u=None, log_v=None) -> None:
     _check(load().tu_set_potentials_f64(h, _ptr(log_u), _ptr(log_v)), "tu_set_potentials_f64", h)
+
+
+def tu_get_potentials_range_f64(h: int, side: int, lo: int, hi: int, out) -> None:
+    """FP64 log potentials of users [lo, hi) of one side into `out` (hi - lo doubles)."""
+    _check(load().tu_get_potentials_range_f64(h, int(side), int(lo), int(hi), _ptr(out)),
+           "tu_get_potentials_range_f64", h)
+
+
+def tu_ipfp_half_sweep_range(h: int, side: int, lo: int, hi: int, residual: bool = False):
+    """Half-sweep of side `side` restricted to its users [lo, hi) (one shard of a
+    market split across GPUs); with residual, (max |r| / mass, sum |r|) of the
+    shard's equations at the entering state."""
+    out = (ctypes.c_double * 2)()
+    _check(load().tu_ipfp_half_sweep_range(h, int(side), int(lo), int(hi), out if residual else None),
+           "tu_ipfp_half_sweep_range", h)
+    return (out[0], out[1]) if residual else None
 
 
 def tu_fused_halfsweep_noalloc(rows: int, cols: int, kp: int, own_packed, partner_packed, own_bias, own_mass,

@@ -1019,15 +1019,21 @@ cudaError_t fused_prepare(tu_market* m) {
   return set_kernel_attributes();
 }
 
-cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int update, int* nparts_out) {
+cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int update, int* nparts_out,
+                                   int64_t row0, int64_t nrows) {
   Side& own = side == 0 ? m->X : m->Y;
   Side& partner = side == 0 ? m->Y : m->X;
-  const bool small = use_small_tiles(m, own.rows);
-  FusedParams p = base_params(own.rows, 0, 0, partner.rows, m->cmul, small);
+  const bool whole = nrows < 0;
+  if (whole) {
+    row0 = 0;
+    nrows = own.rows;
+  }
+  const bool small = use_small_tiles(m, nrows);
+  FusedParams p = base_params(nrows, row0, 0, partner.rows, m->cmul, small);
   p.g = partner.pvec;
   p.lmax = m->st + kStShift;
   p.own_off = m->st + kStOwnOff;
-  p.grp = own.grp;
+  p.grp = whole ? own.grp : nullptr;  // a range of rows does not write the side's groups
   p.b2s = own.b2s;
   p.mass = own.mass;
   p.log_u = own.log_u;

@@ -1257,6 +1257,46 @@ tu_status tu_get_potentials_f64(tu_market_t m, double* log_u, double* log_v) {
   return TU_OK;
 }
 
+tu_status tu_get_potentials_range_f64(tu_market_t m, int side, int64_t lo, int64_t hi, double* out) {
+  TU_TRACE("tu_get_potentials_range_f64");
+  TU_TRY(check_live(m));
+  if (side != 0 && side != 1) return fail(m, TU_ERR_INVALID_ARG, "side must be 0 or 1");
+  const Side& s = side == 0 ? m->X : m->Y;
+  if (lo < 0 || hi < lo || hi > s.rows) return fail(m, TU_ERR_INVALID_ARG, "range outside the side's users");
+  if (out == nullptr && hi > lo) return fail(m, TU_ERR_INVALID_ARG, "null output");
+  if (hi > lo)
+    TU_CK(m, cudaMemcpyAsync(out, s.log_u + lo, (size_t)(hi - lo) * sizeof(double), cudaMemcpyDefault, m->stream));
+  TU_CK(m, cudaStreamSynchronize(m->stream));
+  return TU_OK;
+}
+
+tu_status tu_ipfp_half_sweep_range(tu_market_t m, int side, int64_t lo, int64_t hi, double* residual_out) {
+  TU_TRACE("tu_ipfp_half_sweep_range");
+  TU_TRY(check_live(m));
+  if (side != 0 && side != 1) return fail(m, TU_ERR_INVALID_ARG, "side must be 0 or 1");
+  if (m->path != TU_PATH_FUSED) return fail(m, TU_ERR_UNSUPPORTED, "row ranges need the fused path");
+  Side& own = side == 0 ? m->X : m->Y;
+  Side& partner = side == 0 ? m->Y : m->X;
+  if (lo < 0 || hi < lo || hi > own.rows) return fail(m, TU_ERR_INVALID_ARG, "range outside the side's users");
+  TU_TRY(clear_results(m));
+  if (hi > lo) {
+    // no translation step: a shard's caller owns the step (it needs both sides' global sums)
+    TU_CK(m, launch_prep(m, partner, 1, 0));
+    int nparts = 0;
+    TU_CK(m, launch_fused_halfsweep(m, side, residual_out ? kResidualExact : kResidualNone, 1, &nparts, lo, hi - lo));
+    // the partials only; then the side's groups and the market's scalars from
+    // the stored potentials (the next preparation reads the side's shift)
+    TU_CK(m, launch_finalize(m, nparts, 1, residual_out ? 1 : 0, 0, 0));
+    TU_CK(m, launch_rescan(m));
+  }
+  TU_TRY(read_results(m));
+  if (residual_out != nullptr) {
+    residual_out[0] = m->results_host[kResXInf];
+    residual_out[1] = m->results_host[kResXL1];
+  }
+  return TU_OK;
+}
+
 tu_status tu_set_potentials_f64(tu_market_t m, const double* log_u, const double* log_v) {
   TU_TRACE("tu_set_potentials_f64");
   TU_TRY(check_live(m));

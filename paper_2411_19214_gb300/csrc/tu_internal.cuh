@@ -223,7 +223,9 @@ cudaError_t launch_dense_colpass(tu_market* m, int update, int* nparts_out, int6
 
 // fused.cu
 cudaError_t fused_prepare(tu_market* m);  // tensor maps + kernel attributes
-cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int update, int* nparts_out);
+// The whole own side (nrows < 0), or own users [row0, row0 + nrows) only (no groups written).
+cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int update, int* nparts_out,
+                                   int64_t row0 = 0, int64_t nrows = -1);
 
 // The fused half-sweep on caller-described device buffers (no market object).
 struct FusedRaw {
