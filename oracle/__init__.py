@@ -45,4 +45,5 @@ from .ipfp import (  # noqa: F401
     welfare,
     topk_partners,
     sampled_row_update,
+    expected_matches,
 )

@@ -420,3 +420,29 @@ def sampled_row_update(F, K, G, L, beta, mass, log_v, rows, bias_x=None, bias_y=
         run_max = new_max
     log_s = LOG_HALF + run_max + np.log(run_sum)
     return log_s, scaling_update(log_s, np.asarray(mass, np.float64)[rows])
+
+
+# ---------------------------------------------------------------------------
+# Expected number of matches of ranked lists (Sec. 4.1)
+# ---------------------------------------------------------------------------
+
+def expected_matches(P, Q, lists_x, lists_y):
+    """Expected matches of the ranked lists shown to both sides, under the
+    position-based model with examination v(k) = 1 / exp(k - 1) (Sec. 4.1).
+    Reading (the paper takes the measure from Su et al. without restating it):
+    x and y match when each examines and likes the other, so the expectation
+    is the sum over all pairs of v(pos_x(y)) P[x, y] v(pos_y(x)) Q[y, x], with
+    v = 0 for a partner missing from a list. lists_x[x] is the sequence of y's
+    shown to x (best first), lists_y[y] that of x's shown to y. A plain double
+    loop over the pairs."""
+    N, M = len(lists_x), len(lists_y)
+    total = 0.0
+    for x in range(N):
+        for y in range(M):
+            lx = list(lists_x[x])
+            ly = list(lists_y[y])
+            if y in lx and x in ly:
+                kx = lx.index(y) + 1
+                ky = ly.index(x) + 1
+                total += np.exp(-(kx - 1)) * P[x][y] * np.exp(-(ky - 1)) * Q[y][x]
+    return float(total)

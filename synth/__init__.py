@@ -22,4 +22,5 @@ from .markets import (  # noqa: F401
     batched_markets,
     serving_request_sizes,
     serving_workload,
+    crowding_market,
 )

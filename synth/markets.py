@@ -299,3 +299,35 @@ def serving_request_sizes(count: int, rate: float = 200.0, lo: int = 1000, hi: i
     resolve = rng.random(count) < 0.3
     return [dict(t=float(ti), N=int(a), M=int(b), d=int(di), resolve=bool(r))
             for ti, (a, b), di, r in zip(t, sizes, d, resolve)]
+
+
+def crowding_market(N: int = 1000, M: int = 500, lam: float = 0.5, d: int = 32, sigma: float = 1.0,
+                    seed: int = 1006):
+    """A market with controlled preference crowding (Sec. 4.1's synthetic
+    experiment: 1,000 candidates, 500 employers, crowding lambda in
+    {0, 0.25, 0.5, 0.75}, beta = 1). Reading of its generator (the paper
+    describes it in words): the probability that candidate x likes employer y
+    interpolates an independent uniform draw and a value that falls with the
+    employer's index, p_xy = (1 - lambda) U_xy + lambda (1 - y / M), and
+    likewise q_yx = (1 - lambda) U'_yx + lambda (1 - x / N) for the employer's
+    side; lambda = 0 is no crowding, larger lambda concentrates everyone's
+    preferences on the same low-index users. The matching model's factors are
+    the best rank-d approximations of the two preference matrices (truncated
+    SVD, standing in for the paper's implicit-ALS fit to sampled
+    interactions): F G^T ~ P, K L^T ~ Q^T, so phi = <f_x, g_y> + <k_x, l_y>.
+    Returns (Market with float32 factors, P (N x M), Q (M x N)), P and Q in
+    float64."""
+    rng = np.random.default_rng(seed)
+    P = (1.0 - lam) * rng.random((N, M)) + lam * (1.0 - np.arange(M) / M)[None, :]
+    Q = (1.0 - lam) * rng.random((M, N)) + lam * (1.0 - np.arange(N) / N)[None, :]
+
+    def rank_d(A):
+        Uu, s, Vt = np.linalg.svd(A, full_matrices=False)
+        r = np.sqrt(s[:d])
+        return (Uu[:, :d] * r).astype(np.float32), (Vt[:d].T * r).astype(np.float32)
+
+    F, G = rank_d(P)        # F G^T ~ P      (N x d, M x d)
+    L, K = rank_d(Q)        # L K^T ~ Q, so K L^T ~ Q^T
+    mk = Market(F, K, G, L, None, None, np.ones(N), np.ones(M), float(sigma), "fp32", seed,
+                f"crowding N={N} M={M} lambda={lam} d={d}")
+    return mk, P, Q
