@@ -94,11 +94,20 @@ typedef struct {
 
 /* Create a market from factor matrices and capacities (Sec. 3.3, Alg. 2 inputs).
  * Potentials start at u = v = 1 (Alg. 1 / Alg. 2 initialisation).
- * Validates sizes, pointers, sigma > 0, capacities > 0 and finite, and that the
- * exponent range fits FP32: max_x |a_x| * max_y |b_y| / (2 sigma) <= 40, where
+ * Validates sizes, pointers, sigma > 0, capacities > 0 and finite. The
+ * exponent range, bound = max_x |a_x| * max_y |b_y| / (2 sigma) with
  * a_x = (f_x, k_x), b_y = (g_y, l_y) (a Cauchy-Schwarz bound on the bias-free
- * part of phi / (2 sigma)); otherwise TU_ERR_UNSUPPORTED. Biases have no limit:
- * they are folded into the potentials in log space. Sizes: 1 <= N, M <= 2^31
+ * part of phi / (2 sigma)), decides the arithmetic: up to 40, one shift per
+ * half-sweep keeps every FP32 term in range; beyond ("wide" markets, strong
+ * preferences or small sigma), the fused path first finds every row's largest
+ * exponent (a second pass over the pairs, about 1.6x the half-sweep's time)
+ * and subtracts it, and the dense path refuses the market
+ * (TU_ERR_UNSUPPORTED: its materialised FP32 A-hat would overflow). In wide
+ * markets the FP32 accumulation of phi carries an absolute error of about
+ * bound x 2^-24 x sqrt(2d) per exponent, above the 1e-7 of narrow ones, and
+ * the attainable residual is about bound x 2^-24 (the FP32 spacing of the
+ * large exponents and partner potentials that dominate a row). Biases
+ * have no limit: they are folded into the potentials in log space. Sizes: 1 <= N, M <= 2^31
  * and 1 <= d <= 4096 (TU_ERR_INVALID_ARG otherwise); the fused path takes
  * d <= 64 (2d fills one 128-wide MMA inner dimension), FP8 factors only on the
  * fused path, a dense market at most 200 GB of A-hat and its transpose, and a
@@ -356,8 +365,9 @@ tu_status tu_profile_read(tu_market_t mkt, double* pass_ms, int64_t* passes);
  * device other than compute capability 10.3 (the library is built for sm_103a
  * only) gives TU_ERR_UNSUPPORTED.
  * Limits: 1 <= rows <= 65536 and 1 <= cols <= 1048576 (TU_ERR_UNSUPPORTED
- * beyond them, and for kp other than 64 or 128); the exponent-range condition
- * of tu_market_create applies and is not checked here.
+ * beyond them, and for kp other than 64 or 128); the factors must lie in the
+ * single-shift range of tu_market_create (bound <= 40), which is not checked
+ * here (there is no second pass for wide markets).
  * Scratch: one file-scope __device__ array of 5,644,576 bytes that every GPU
  * loading the library holds until the process exits; its device address is
  * resolved on the first call on each device (with that device current), so
@@ -384,7 +394,8 @@ typedef struct tu_batch* tu_batch_t;
  * on the current device with the same packed width (2d rounded up to 64 or
  * 128). The batch references the markets (their buffers, tensor maps, sigma,
  * relaxation and translation settings at creation); destroy the batch before
- * any of them.
+ * any of them. Wide markets (see tu_market_create) cannot join a batch
+ * (TU_ERR_UNSUPPORTED).
  * Batch work is ordered on `stream` (a cudaStream_t, or NULL for the legacy
  * default stream); every batch call first waits for work already enqueued on
  * the members' own streams, and the caller orders later member calls after

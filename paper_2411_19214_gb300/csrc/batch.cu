@@ -542,6 +542,8 @@ tu_status tu_batch_create(const tu_market_t* markets, int count, void* stream, t
     if (m == nullptr || m->poisoned || m->path != TU_PATH_FUSED) return TU_ERR_INVALID_ARG;
     if (m->kp != ms[0]->kp || m->device != ms[0]->device) return TU_ERR_INVALID_ARG;
     if ((m->dtype == TU_DTYPE_FP8E4M3) != (ms[0]->dtype == TU_DTYPE_FP8E4M3)) return TU_ERR_INVALID_ARG;
+    // the batched kernel keeps one shift per market and half-sweep
+    if (m->wide) return TU_ERR_UNSUPPORTED;
   }
   {
     std::vector<tu_market*> sorted(ms);

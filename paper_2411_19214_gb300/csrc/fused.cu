@@ -56,7 +56,11 @@ constexpr uint32_t kTmemCols = 512;
 // Epilogue modes of the one fused kernel: the same TMA / MMA pipeline forms
 // the tiles of c * phi_hat + g; the epilogue either reduces them (a half-sweep),
 // keeps the k best columns of every row (ranked lists) or writes mu.
-enum : int { kModeSweep = 0, kModeTopK = 1, kModeMu = 2, kModeTopKShared = 3 };
+// Markets whose factor range is too wide for one shift per half-sweep (see
+// market.cu) take two passes: kModeRowMax writes every own row's largest
+// exponent c * phi_hat + g, and kModeSweepShift is a half-sweep that
+// subtracts it before ex2 (so every row's largest term is 2^0).
+enum : int { kModeSweep = 0, kModeTopK = 1, kModeMu = 2, kModeTopKShared = 3, kModeRowMax = 4, kModeSweepShift = 5 };
 
 struct FusedParams {
   int64_t rows;            // own users of this launch: [row0, row0 + rows)
@@ -94,6 +98,9 @@ struct FusedParams {
   int64_t ld;
   int64_t y0;
   int64_t ny;
+  // wide markets: per own row (index row0 + r), the largest exponent in log2
+  // units (written by kModeRowMax, subtracted by kModeSweepShift)
+  float* rowmax;
 };
 
 // Own-tile buffers: with a 64-wide inner dimension the next own tile is loaded
@@ -170,6 +177,44 @@ __device__ __forceinline__ void pair_step(uint64_t& acc, uint32_t phi0, uint32_t
 
 __device__ __forceinline__ float unpack_sum(uint64_t a) {
   return __uint_as_float((uint32_t)a) + __uint_as_float((uint32_t)(a >> 32));
+}
+
+// acc(2 lanes) += (ex2(phi0 * c + g0 - S), ex2(phi1 * c + g1 - S)): the same
+// step with the row's shift ss = (-S, -S) added before ex2 (wide markets).
+__device__ __forceinline__ void pair_step_shift(uint64_t& acc, uint32_t phi0, uint32_t phi1, float g0, float g1,
+                                                uint64_t cc, uint64_t ss) {
+  asm("{\n\t.reg .b64 a, gg, t, e;\n\t.reg .f32 t0, t1, e0, e1;\n\t"
+      "mov.b64 a, {%1, %2};\n\t"
+      "mov.b64 gg, {%3, %4};\n\t"
+      "fma.rn.f32x2 t, a, %5, gg;\n\t"
+      "add.rn.f32x2 t, t, %6;\n\t"
+      "mov.b64 {t0, t1}, t;\n\t"
+      "ex2.approx.ftz.f32 e0, t0;\n\t"
+      "ex2.approx.ftz.f32 e1, t1;\n\t"
+      "mov.b64 e, {e0, e1};\n\t"
+      "add.rn.f32x2 %0, %0, e;\n\t}"
+      : "+l"(acc)
+      : "r"(phi0), "r"(phi1), "f"(g0), "f"(g1), "l"(cc), "l"(ss));
+}
+
+__device__ __forceinline__ void chunk_sum_shift(const uint32_t (&v)[32], const float4* gs4, uint64_t cc, uint64_t ss,
+                                                uint64_t (&acc)[4]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float4 gg = gs4[i];
+    pair_step_shift(acc[(2 * i) & 3], v[4 * i + 0], v[4 * i + 1], gg.x, gg.y, cc, ss);
+    pair_step_shift(acc[(2 * i + 1) & 3], v[4 * i + 2], v[4 * i + 3], gg.z, gg.w, cc, ss);
+  }
+}
+
+// Largest exponent c * phi + g of one 32-column chunk, folded into mx.
+__device__ __forceinline__ void chunk_max(const uint32_t (&v)[32], const float4* gs4, float c, float& mx) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float4 gg = gs4[i];
+    mx = fmaxf(mx, fmaxf(fmaxf(fmaf(__uint_as_float(v[4 * i + 0]), c, gg.x), fmaf(__uint_as_float(v[4 * i + 1]), c, gg.y)),
+                         fmaxf(fmaf(__uint_as_float(v[4 * i + 2]), c, gg.z), fmaf(__uint_as_float(v[4 * i + 3]), c, gg.w))));
+  }
 }
 
 // Sum over one 32-column chunk: 16 packed pairs into four packed accumulators.
@@ -302,8 +347,11 @@ __device__ __forceinline__ void chunk_mu(const uint32_t (&v)[32], const float* g
 #pragma unroll
   for (int i = 0; i < 32; ++i) {
     const int64_t col = colbase + i;
-    if (col >= p.y0 && col < p.y0 + p.ny)
-      orow[col - p.y0] = ldexpf(ex2_approx(fmaf(__uint_as_float(v[i]), c, g[i]) + lo), hi);
+    if (col >= p.y0 && col < p.y0 + p.ny) {
+      const float t = fmaf(__uint_as_float(v[i]), c, g[i]) + lo;
+      // (wide markets: an exponent beyond the FP32 range is brought back by hi first)
+      orow[col - p.y0] = fabsf(t) <= 100.0f ? ldexpf(ex2_approx(t), hi) : ex2_approx(t + (float)hi);
+    }
   }
 }
 
@@ -352,6 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     k_fused_halfsweep(const __grid_constant__ CUtensorMap tm_own, const __grid_constant__ CUtensorMap tm_partner,
                       const FusedParams p) {
   static_assert(!BATCH || MODE == kModeSweep, "batched launches run half-sweeps only");
+  constexpr bool kSweepLike = MODE == kModeSweep || MODE == kModeSweepShift;
   static_assert(!(BATCH && SMALL), "batched launches use 256-row own tiles");
   constexpr int kOwn = SMALL ? kFusedOwnRows / 2 : kFusedOwnRows;  // rows of an own tile
   static_assert(!F8 || KB == 1, "e4m3 rows are one 128-byte block");
@@ -582,7 +631,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const double shift0 = BATCH ? 0.0 : __ldg(p.lmax);
     // (ranked lists and mu blocks run on potentials without pending offsets:
     // every block of sweeps ends by writing them into the arrays)
-    const double own_off0 = (MODE == kModeSweep && !BATCH && p.own_off != nullptr) ? *p.own_off : 0.0;
+    const double own_off0 = (kSweepLike && !BATCH && p.own_off != nullptr) ? *p.own_off : 0.0;
     const double omega0 = (!BATCH && p.omega != nullptr && p.update) ? *p.omega : 1.0;
     int buf = 0, gs = 0;
     uint32_t tphase = 0, gphase = 0;
@@ -616,6 +665,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       float sum = 0.0f, comp = 0.0f;
       float mu_lo = 0.0f;
       int mu_hi = 0;
+      // wide markets: the row's largest exponent (found here, or subtracted here)
+      float rmax = -INFINITY;
+      uint64_t rshift = 0ull;
+      if constexpr (MODE == kModeSweepShift) {
+        const float sft = row_ok ? -p.rowmax[p.row0 + r] : 0.0f;
+        rshift = ((uint64_t)__float_as_uint(sft) << 32) | __float_as_uint(sft);
+      }
       if constexpr (MODE == kModeMu) {
         if (row_ok) {
           const double off = (shift + p.ell[p.row0 + r]) * 1.4426950408889634;
@@ -658,6 +714,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           tmem_ld_wait(va);
           tmem_ld_issue(taddr + 32, vb);
           if constexpr (MODE == kModeSweep) chunk_sum(va, gs4, cc, acc);
+          if constexpr (MODE == kModeSweepShift) chunk_sum_shift(va, gs4, cc, rshift, acc);
+          if constexpr (MODE == kModeRowMax) chunk_max(va, gs4, p.c, rmax);
           if constexpr (MODE == kModeTopK) chunk_topk(va, gsf, p.c, colbase, p.k, tv, ti, &tcnt, thr);
           if constexpr (MODE == kModeTopKShared) chunk_topk_shared(va, gsf, p.c, colbase, p.k, lv, li, thr);
           if constexpr (MODE == kModeMu) chunk_mu(va, gsf, p.c, colbase, mu_lo, mu_hi, row_ok, r, p);
@@ -669,6 +727,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) mbar_arrive(&tempty[buf]);
         if (!idle) {
           if constexpr (MODE == kModeSweep) chunk_sum(vb, gs4 + 8, cc, acc);
+          if constexpr (MODE == kModeSweepShift) chunk_sum_shift(vb, gs4 + 8, cc, rshift, acc);
+          if constexpr (MODE == kModeRowMax) chunk_max(vb, gs4 + 8, p.c, rmax);
           if constexpr (MODE == kModeTopK) chunk_topk(vb, gsf + 32, p.c, colbase + 32, p.k, tv, ti, &tcnt, thr);
           if constexpr (MODE == kModeTopKShared)
             chunk_topk_shared(vb, gsf + 32, p.c, colbase + 32, p.k, lv, li, thr);
@@ -677,7 +737,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // the g slot has been read by this warp
         __syncwarp();
         if (lane == 0) mbar_arrive(&gempty[gs]);
-        if constexpr (MODE == kModeSweep) {
+        if constexpr (kSweepLike) {
           // compensated (Kahan) accumulation of the per-tile partial sums
           const float tile =
               (unpack_sum(acc[0]) + unpack_sum(acc[1])) + (unpack_sum(acc[2]) + unpack_sum(acc[3]));
@@ -705,7 +765,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           ok = false;
           break;
         }
-        if constexpr (MODE == kModeSweep) rb[rloc] = sum - comp;
+        if constexpr (kSweepLike) rb[rloc] = sum - comp;
+        if constexpr (MODE == kModeRowMax) rb[rloc] = rmax;
         if constexpr (MODE == kModeTopK) {
           if (row_ok)
             for (int i = 0; i < p.k; ++i) {
@@ -767,7 +828,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&rowfree[pb]);
       }
-      if constexpr (MODE == kModeSweep) {
+      if constexpr (MODE == kModeRowMax) {
+        const float other = rb[rloc];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&rowfree[pb]);
+        if (row_ok) p.rowmax[p.row0 + r] = fmaxf(rmax, other);
+      }
+      if constexpr (kSweepLike) {
         const float other = rb[rloc];
         __syncwarp();
         if (lane == 0) mbar_arrive(&rowfree[pb]);
@@ -779,7 +846,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           double* ell = BATCH ? bd->ell : p.ell;
           const double omega = BATCH ? ((bd->omega != nullptr && p.update) ? *bd->omega : 1.0) : omega0;
           const double own_off = BATCH ? bd->st[kStOwnOff] : own_off0;
-          const RowResult rr = row_update(log_row_sum(sum, -comp, other), shift, b2s ? b2s[row] : 0.0f,
+          double ln_sum = log_row_sum(sum, -comp, other);
+          // wide markets: the row's shift comes back into the sum's logarithm
+          if constexpr (MODE == kModeSweepShift)
+            ln_sum = __fma_rn(-(double)__uint_as_float((uint32_t)rshift), 0.69314718055994530942, ln_sum);
+          const RowResult rr = row_update(ln_sum, shift, b2s ? b2s[row] : 0.0f,
                                           (BATCH ? bd->mass : p.mass)[row], log_u[row] + own_off,
                                           p.residual, omega);
           if (p.update) {
@@ -823,7 +894,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
     if (!ok && !*abort_flag) raise_error(p.err, abort_flag, kErrTimeout);
-    if constexpr (MODE == kModeSweep && !BATCH) {
+    if constexpr (kSweepLike && !BATCH) {
       // reduce the CTA's partials over the epilogue threads
       for (int o = 16; o > 0; o >>= 1) {
         r_max = fmax(r_max, __shfl_xor_sync(0xffffffffu, r_max, o));
@@ -947,6 +1018,8 @@ cudaError_t set_kernel_attributes() {
   if (e == cudaSuccess) e = set_attributes_mode<kModeMu, false>();
   if (e == cudaSuccess) e = set_attributes_mode<kModeTopKShared, false>();
   if (e == cudaSuccess) e = set_attributes_mode<kModeSweep, true>();
+  if (e == cudaSuccess) e = set_attributes_mode<kModeRowMax, false>();
+  if (e == cudaSuccess) e = set_attributes_mode<kModeSweepShift, false>();
   return e;
 }
 
@@ -1045,8 +1118,15 @@ cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int upd
   p.omega = m->omega_dev;
   const int grid = grid_for_tiles(p.num_own_tiles, m->num_sms);
   *nparts_out = grid;
-  return launch_any<kModeSweep>(m->kp, m->dtype == TU_DTYPE_FP8E4M3, own.tm_own, partner.tm_partner, p, grid,
-                                m->stream, small);
+  const bool f8 = m->dtype == TU_DTYPE_FP8E4M3;
+  if (m->wide) {
+    // two passes: every own row's largest exponent, then the half-sweep with it subtracted
+    p.rowmax = m->rowmax;
+    cudaError_t e = launch_any<kModeRowMax>(m->kp, f8, own.tm_own, partner.tm_partner, p, grid, m->stream, small);
+    if (e != cudaSuccess) return e;
+    return launch_any<kModeSweepShift>(m->kp, f8, own.tm_own, partner.tm_partner, p, grid, m->stream, small);
+  }
+  return launch_any<kModeSweep>(m->kp, f8, own.tm_own, partner.tm_partner, p, grid, m->stream, small);
 }
 
 // Ranked lists of own users [row0, row0 + nrows) over all partners (the

@@ -382,11 +382,18 @@ tu_status load_factors(tu_market* m, const void* F, const void* K, const void* G
   if (!std::isfinite(hn[0]) || !std::isfinite(hn[1]))
     return fail(m, TU_ERR_NONFINITE, "factor matrices contain NaN or Inf");
   const double bound = (double)hn[0] * (double)hn[1] / (2.0 * m->sigma);  // FP8: norms of the quantized rows
-  if (bound > 40.0) {
+  // One shift per half-sweep (the partner side's max ell) keeps every exponent
+  // within +-bound log2(e) of the row's largest: up to 40, FP32 holds the
+  // terms and their sums. Beyond, the fused path finds each row's largest
+  // exponent first (a second pass over the pairs) and subtracts it; the dense
+  // path's materialised A-hat itself would leave the FP32 range.
+  const bool wide = bound > 40.0;
+  if (wide && m->path == TU_PATH_DENSE) {
     char buf[160];
-    snprintf(buf, sizeof(buf), "max|a_x| * max|b_y| / (2 sigma) = %.3g exceeds 40 (FP32 exponent range)", bound);
+    snprintf(buf, sizeof(buf), "max|a_x| * max|b_y| / (2 sigma) = %.3g exceeds 40 (FP32 range of A-hat)", bound);
     return fail(m, TU_ERR_UNSUPPORTED, buf);
   }
+  m->wide = wide;
   if (m->path == TU_PATH_DENSE) TU_CK(m, launch_dense_build(m));
   TU_CK(m, cudaStreamSynchronize(m->stream));
   if (m->graph != nullptr) {
@@ -682,6 +689,7 @@ void tu_market_destroy(tu_market_t m) {
   }
   dev_free(m, m->partials);
   dev_free(m, m->st);
+  dev_free(m, m->rowmax);
   dev_free(m, m->results);
   dev_free(m, m->err_dev);
   dev_free(m, m->staging);
@@ -752,6 +760,11 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
   }
   if ((st = side_alloc(m, m->X, D.N, D.bias_x != nullptr)) != TU_OK) return bail(st);
   if ((st = side_alloc(m, m->Y, D.M, D.bias_y != nullptr)) != TU_OK) return bail(st);
+  // fused path: per-row shifts of wide markets, one buffer for the larger side
+  if (D.path == TU_PATH_FUSED &&
+      (st = dev_alloc(m, &m->rowmax, (size_t)(m->X.rows_pad > m->Y.rows_pad ? m->X.rows_pad : m->Y.rows_pad))) !=
+          TU_OK)
+    return bail(st);
   if ((st = dev_alloc(m, &m->partials, (size_t)kMaxPartials * 4)) != TU_OK) return bail(st);
   if ((st = dev_alloc(m, &m->st, (size_t)kStSlots)) != TU_OK) return bail(st);
   if ((st = dev_alloc(m, &m->results, (size_t)kResSlots)) != TU_OK) return bail(st);
@@ -970,7 +983,7 @@ int64_t tu_market_footprint(int64_t N, int64_t M, int64_t d, int path) {
   // staging for host factor uploads (two matrices of the larger side)
   bytes += 2 * (N > M ? N : M) * d * 4;
   if (path == TU_PATH_FUSED) {
-    bytes += (N + M) * kp * 2;
+    bytes += (N + M) * kp * 2 + (np > mp ? np : mp) * 4;  // factors, per-row shifts
   } else {
     bytes += (N + M) * kp * 4 + N * round_up(M, 4) * 4 + M * round_up(N, 4) * 4;
   }

@@ -165,6 +165,8 @@ struct tu_market {
   bool use_graphs = true;          // tu_market_use_graphs
   bool small_tiles = true;         // tu_market_set_small_tiles: 128-row own tiles when they fit one wave
   bool translate = true;           // tu_market_set_translation: translation step before every half-sweep
+  bool wide = false;               // factor range beyond one shift per half-sweep: per-row shifts (two passes)
+  float* rowmax = nullptr;         // fused path: per own row, the largest exponent (log2), max(N, M) padded
   bool poisoned = false;
   std::string last_error;
   // benchmark timing (tu_profile_enable / tu_profile_read)
