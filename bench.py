@@ -42,17 +42,18 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # workloads
 # ---------------------------------------------------------------------------
 
-def make_workload(name: str, rank: int, shape=None, fp8: bool = False):
+def make_workload(name: str, rank: int, shape=None, fp8=None):
     from synth import dense_job_market, fused_market
     kw = {} if shape is None else {"N": shape[0], "M": shape[1]}
     if name == "fused" and fp8:
         # the same market with unrounded FP32 factors, quantized to e4m3 by the library
         mk = fused_market(seed=1002 + 97 * rank, dtype="fp32", **kw)
-        cfg = {"workload": "fused mini-batch IPFP (Alg. 2) with FP8 e4m3 factors (one power-of-two scale per "
-                           "side, tcgen05 kind::f8f6f4): N=M=1,000,000 users, d=64 per factor, factors N(0,1/d), "
+        scales = "one power-of-two scale per row" if fp8 == "rows" else "one power-of-two scale per side"
+        cfg = {"workload": f"fused mini-batch IPFP (Alg. 2) with FP8 e4m3 factors ({scales}, tcgen05 "
+                           "kind::f8f6f4): N=M=1,000,000 users, d=64 per factor, factors N(0,1/d), "
                            "lognormal(0,1) popularity bias on both sides, n=m=1, sigma=0.5",
                "N": mk.N, "M": mk.M, "d": mk.d, "sigma": mk.sigma, "partition": 65536, "path": "fused",
-               "factors": "e4m3",
+               "factors": f"e4m3, {scales}",
                "l2": "inputs larger than L2: each half-sweep streams the 128 MB partner factor matrix "
                      "(L2 is 129 MB); no flush between steps"}
         if shape is not None:
@@ -550,10 +551,10 @@ def run_dims(args):
     """The paper's dimension sweep (Sec. 4.2: N = M = 1e4, time and memory
     against the factor dimension), also at 1e5 where the GPU is full: the
     Sec. 4.2 recipe (U[0, 1/sqrt(D)] factors, n = m = 1, beta = 1) for D in
-    {8, 16, 32, 50, 64}; one JSON line per (N, D) with the time per sweep
-    (`--steps` sweeps replayed as a graph after `--warmup`), the pair rate and
-    the market's device footprint. D = 128 is outside the fused path (2D is
-    the 128-wide MMA inner dimension at most) and is reported as such."""
+    {8, 16, 32, 50, 64, 100, 128}; one JSON line per (N, D) with the time per
+    sweep (`--steps` sweeps replayed as a graph after `--warmup`), the pair
+    rate and the market's device footprint. The MMA inner dimension is 2D
+    padded to 64, 128 or 256."""
     import torch
 
     import paper_2411_19214_gb300 as tu
@@ -561,7 +562,7 @@ def run_dims(args):
     tu.load()
     stream = torch.cuda.Stream()
     for N in (10_000, 100_000):
-        for D in (8, 16, 32, 50, 64):
+        for D in (8, 16, 32, 50, 64, 100, 128):
             mk = paper_shaped_market(N, D=D)
             mkt = tu.from_synth(mk, path="fused", stream=stream)
             try:
@@ -576,15 +577,14 @@ def run_dims(args):
                 ms = e0.elapsed_time(e1) / args.steps
             finally:
                 mkt.close()
-            kp = ((2 * D + 63) // 64) * 64
+            kp = 64
+            while kp < 2 * D:
+                kp *= 2
             print(json.dumps({"workload": "dimension sweep (Sec. 4.2 recipe)", "N": N, "M": N, "D": D,
                               "mma_inner_dim": kp, "ms_per_sweep": ms, "sweeps": args.steps,
                               "gpair_evals_per_s": 2.0 * N * N / ms / 1e6,
                               "device_bytes": tu.tu_market_footprint(N, N, D, "fused"), "dtype": "bf16"}),
                   flush=True)
-        print(json.dumps({"workload": "dimension sweep (Sec. 4.2 recipe)", "N": N, "M": N, "D": 128,
-                          "unsupported": "2D = 256 exceeds the fused path's MMA inner dimension of 128"}),
-              flush=True)
 
 
 def run_reference_dims(args):
@@ -595,7 +595,7 @@ def run_reference_dims(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return
     N = 10_000
-    for D in (8, 16, 32, 50, 64):
+    for D in (8, 16, 32, 50, 64, 100, 128):
         mk = paper_shaped_market(N, D=D)
         pool = OraclePool(mk)
         try:
@@ -896,7 +896,7 @@ def sub_args(args, workload: str, steps=None):
     a.workload = workload
     a.no_extras = False  # the secondary lines' own solve and comparison blocks are kept
     a.no_cpu_baseline = True
-    a.fp8 = False
+    a.fp8 = None
     a.shape = None
     if steps is not None:
         a.steps = steps
@@ -1061,8 +1061,8 @@ def run_ours(args):
             peak_source += " x 2 (nominal fp8/bf16 ratio)"
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak,
-                    "traffic": (measured_traffic("fused fp8 1Mx1M d64" if args.fp8 else "fused 1Mx1M d64")
-                                if args.shape is None else None),
+                    "traffic": (measured_traffic(f"fused fp8 {args.fp8} 1Mx1M d64" if args.fp8
+                                                 else "fused 1Mx1M d64") if args.shape is None else None),
                     "kernel": "k_fused_halfsweep (tcgen05 %s MMA + ex2 row reduction)" % ("e4m3" if args.fp8
                                                                                          else "BF16"),
                     "per_launch": f"{flops:.4g} flop (2*N*M*2d) in {avg_pass_s * 1e3:.2f} ms average over "
@@ -1151,8 +1151,9 @@ def main():
                          "time per sweep, one JSON line per size; batched: 512 independent markets in one "
                          "persistent launch per half-sweep")
     ap.add_argument("--max-iter", type=int, default=20000, help="sweep cap of the batched solve")
-    ap.add_argument("--fp8", action="store_true",
-                    help="fused workload with e4m3 factors (the library quantizes the FP32 factors)")
+    ap.add_argument("--fp8", nargs="?", const="rows", choices=["rows", "side"], default=None,
+                    help="fused workload with e4m3 factors (the library quantizes the FP32 factors with "
+                         "per-row power-of-two scales, or with one per side)")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",

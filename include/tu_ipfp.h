@@ -21,8 +21,9 @@
  *
  * Two paths compute the same iteration:
  *   TU_PATH_FUSED  mini-batch IPFP (Alg. 2 / Eq. iteration_minibatch): Phi is
- *                  formed tile by tile from BF16 factors on the tensor cores
- *                  and never stored; requires d <= 64.
+ *                  formed tile by tile from BF16 (or e4m3) factors on the
+ *                  tensor cores and never stored; requires d <= 128 (e4m3:
+ *                  256).
  *   TU_PATH_DENSE  batch IPFP (Alg. 1 / Eq. iteration_matrix): the FP32 kernel
  *                  A-hat = exp((Phi - b^X - b^Y) / (2 sigma)) is materialised
  *                  once, with its transpose (2*N*M*4 bytes), and one of the
@@ -57,26 +58,34 @@ typedef enum {
   TU_ERR_NOT_CONVERGED = 4, /* tu_ipfp_solve hit max_iter; potentials are still valid */
   TU_ERR_NONFINITE = 5,     /* an input or a computed potential is NaN or infinite */
   TU_ERR_TIMEOUT = 6,       /* a device-side wait ran out of its time limit */
-  TU_ERR_UNSUPPORTED = 7    /* valid request outside what the library supports (e.g. d > 64 on the fused path) */
+  TU_ERR_UNSUPPORTED = 7    /* valid request outside what the library supports (e.g. d > 128 on the fused path) */
 } tu_status;
 
-enum { TU_DTYPE_BF16 = 0, TU_DTYPE_FP32 = 1, TU_DTYPE_FP8E4M3 = 2 };
+enum { TU_DTYPE_BF16 = 0, TU_DTYPE_FP32 = 1, TU_DTYPE_FP8E4M3 = 2, TU_DTYPE_FP8E4M3_SIDE = 3 };
 enum { TU_PATH_FUSED = 0, TU_PATH_DENSE = 1 };
 
 typedef struct {
   int64_t N;             /* users on side X, >= 1 */
   int64_t M;             /* users on side Y, >= 1 */
-  int64_t d;             /* factor dimension D of Sec. 3.3, >= 1 (fused path: <= 64) */
+  int64_t d;             /* factor dimension D of Sec. 3.3, >= 1 (fused path: <= 128, FP8 <= 256) */
   int32_t dtype;         /* element type of F, K, G, L: TU_DTYPE_BF16 (uint16 bit patterns) or TU_DTYPE_FP32.
                             The fused path computes with BF16 (FP32 inputs are rounded to nearest even);
                             the dense path computes with FP32 (BF16 inputs are widened exactly).
-                            TU_DTYPE_FP8E4M3 (fused path only, 2d <= 128): F, K, G, L are FP32 and
-                            the market computes with e4m3 factors (OCP FP8: 4 exponent bits, bias 7,
-                            3 mantissa bits, largest finite 448) on the FP8 tensor cores: each side's
-                            [F | K] (resp. [G | L]) is scaled by 2^-k, k the smallest integer with
-                            max |entry| <= 448 * 2^k, and rounded to nearest even (saturating); the
-                            product is scaled back by 2^(k_X + k_Y) in FP32. This is a lower-precision
-                            model of phi (about 3 % per entry), not the BF16 one. */
+                            TU_DTYPE_FP8E4M3 (fused path only, d <= 256): the market computes with
+                            e4m3 factors (OCP FP8: 4 exponent bits, bias 7, 3 mantissa bits, largest
+                            finite 448) and one FP32 scale per row on the FP8 tensor cores. Without
+                            fscale_x / fscale_y, F, K, G, L are FP32 and the library quantizes: row
+                            x of [F | K] (resp. y of [G | L]) is scaled by 2^-k_x, k_x the smallest
+                            integer with max |entry| <= 448 * 2^k_x, and rounded to nearest even
+                            (saturating), with scale 2^k_x. The MMA multiplies e4m3 values exactly
+                            (FP32 accumulation) and the product of rows x and y is scaled by
+                            scale_x * scale_y in FP32. This is a lower-precision model of phi (about
+                            3 % per entry), not the BF16 one.
+                            TU_DTYPE_FP8E4M3_SIDE: the same from FP32 factors with one power-of-two
+                            scale per side (k the smallest integer with max |entry| of the side <=
+                            448 * 2^k), folded into the exponent multiplier: the faster FP8 mode
+                            (the per-row scales cost one multiply per pair), for sides whose rows
+                            have similar norms (small rows lose precision to e4m3 subnormals). */
   int32_t path;          /* TU_PATH_FUSED or TU_PATH_DENSE */
   const void* F;         /* N x d row-major, host or device; copied (the market owns its copy) */
   const void* K;         /* N x d row-major, host or device; copied */
@@ -90,6 +99,10 @@ typedef struct {
   int64_t partition;     /* rows per mini-batch of Alg. 2 (0: whole side). Results do not depend on it:
                             within a half-sweep every u_x depends only on the fixed v. */
   void* stream;          /* cudaStream_t for all work of this market (NULL: the legacy default stream) */
+  const float* fscale_x; /* FP8 only, or NULL: per-row scales of X (N FP32, host or device). With them
+                            F and K are the caller's e4m3 bytes (N x d each), row x of [F | K] standing
+                            for fscale_x[x] times its e4m3 values. Both scales or neither. */
+  const float* fscale_y; /* likewise for G and L (M scales) */
 } tu_market_desc;
 
 /* Create a market from factor matrices and capacities (Sec. 3.3, Alg. 2 inputs).
@@ -109,8 +122,9 @@ typedef struct {
  * large exponents and partner potentials that dominate a row). Biases
  * have no limit: they are folded into the potentials in log space. Sizes: 1 <= N, M <= 2^31
  * and 1 <= d <= 4096 (TU_ERR_INVALID_ARG otherwise); the fused path takes
- * d <= 64 (2d fills one 128-wide MMA inner dimension), FP8 factors only on the
- * fused path, a dense market at most 200 GB of A-hat and its transpose, and a
+ * d <= 128 (BF16; the MMA inner dimension 2d is padded to 64, 128 or 256, so
+ * 64 < d <= 128 costs as much as d = 128) and FP8 d <= 256 (2d padded to 128,
+ * 256 or 512), FP8 factors only on the fused path, a dense market at most 200 GB of A-hat and its transpose, and a
  * device of compute capability 10.3 (the library is built for sm_103a only)
  * (TU_ERR_UNSUPPORTED otherwise). On success *out owns device memory of about
  * (N + M) * 2 * d * 2 bytes (fused) or 2 * N * M * 4 bytes (dense), a staging
@@ -122,9 +136,18 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out);
  * Potentials are kept, so the next solve can be warm-started. Dense markets
  * rebuild A-hat. The same checks as tu_market_create apply (TU_ERR_NONFINITE,
  * TU_ERR_UNSUPPORTED); after such a refusal the market's factors are
- * undefined until the next successful update (its potentials are kept). */
+ * undefined until the next successful update (its potentials are kept). A
+ * market created with FP8 caller scales takes tu_market_update_factors_fp8
+ * instead (TU_ERR_INVALID_ARG here). */
 tu_status tu_market_update_factors(tu_market_t mkt, const void* F, const void* K, const void* G,
                                    const void* L);
+
+/* The same for a market created with fscale_x / fscale_y: new e4m3 bytes
+ * F, K (N x d), G, L (M x d) and their per-row scales (host or device).
+ * TU_ERR_INVALID_ARG for any other market; TU_ERR_NONFINITE for a non-finite
+ * scale. */
+tu_status tu_market_update_factors_fp8(tu_market_t mkt, const void* F, const void* K, const void* G,
+                                       const void* L, const float* fscale_x, const float* fscale_y);
 
 /* Run nsweeps >= 0 full sweeps of Eq. iteration (u from v, then v from the new u;
  * Alg. 1 loop body / Alg. 2 loop body), each half-sweep preceded by the
@@ -391,11 +414,12 @@ tu_status tu_fused_halfsweep_noalloc(int64_t rows, int64_t cols, int64_t kp, con
 typedef struct tu_batch* tu_batch_t;
 
 /* Group `count` markets (1 <= count <= 65536), all created with TU_PATH_FUSED
- * on the current device with the same packed width (2d rounded up to 64 or
- * 128). The batch references the markets (their buffers, tensor maps, sigma,
- * relaxation and translation settings at creation); destroy the batch before
- * any of them. Wide markets (see tu_market_create) cannot join a batch
- * (TU_ERR_UNSUPPORTED).
+ * on the current device with the same packed width (BF16: 2d rounded up to 64
+ * or 128; FP8: d <= 64) and the same dtype. The batch references the markets
+ * (their buffers, tensor maps, sigma, relaxation and translation settings at
+ * creation); destroy the batch before any of them. Wide markets (see
+ * tu_market_create) and markets with d > 64 (BF16 with 2d > 128) cannot join
+ * a batch (TU_ERR_UNSUPPORTED).
  * Batch work is ordered on `stream` (a cudaStream_t, or NULL for the legacy
  * default stream); every batch call first waits for work already enqueued on
  * the members' own streams, and the caller orders later member calls after

@@ -22,7 +22,7 @@ from . import build as _build
 
 TU_OK, TU_ERR_INVALID_ARG, TU_ERR_OOM, TU_ERR_CUDA, TU_ERR_NOT_CONVERGED, TU_ERR_NONFINITE, TU_ERR_TIMEOUT, \
     TU_ERR_UNSUPPORTED = range(8)
-TU_DTYPE_BF16, TU_DTYPE_FP32, TU_DTYPE_FP8E4M3 = 0, 1, 2
+TU_DTYPE_BF16, TU_DTYPE_FP32, TU_DTYPE_FP8E4M3, TU_DTYPE_FP8E4M3_SIDE = 0, 1, 2, 3
 TU_PATH_FUSED, TU_PATH_DENSE = 0, 1
 
 LIB_PATH = _build.LIB
@@ -35,7 +35,8 @@ class MarketDesc(ctypes.Structure):
                 ("F", ctypes.c_void_p), ("K", ctypes.c_void_p), ("G", ctypes.c_void_p), ("L", ctypes.c_void_p),
                 ("bias_x", ctypes.c_void_p), ("bias_y", ctypes.c_void_p),
                 ("n", ctypes.c_void_p), ("m", ctypes.c_void_p),
-                ("sigma", ctypes.c_double), ("partition", ctypes.c_int64), ("stream", ctypes.c_void_p)]
+                ("sigma", ctypes.c_double), ("partition", ctypes.c_int64), ("stream", ctypes.c_void_p),
+                ("fscale_x", ctypes.c_void_p), ("fscale_y", ctypes.c_void_p)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -63,6 +64,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     sigs = {
         "tu_market_create": (I32, [ctypes.POINTER(MarketDesc), ctypes.POINTER(V)]),
         "tu_market_update_factors": (I32, [V, V, V, V, V]),
+        "tu_market_update_factors_fp8": (I32, [V, V, V, V, V, V, V]),
         "tu_ipfp_sweep": (I32, [V, I32, ctypes.POINTER(D)]),
         "tu_ipfp_solve": (I32, [V, D, I32, I32, ctypes.POINTER(SolveInfo)]),
         "tu_ipfp_solve_ranking": (I32, [V, I32, I64, I32, I32, D, I32, I32, ctypes.POINTER(SolveInfo)]),
@@ -111,7 +113,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
 def exported_symbols() -> list:
     """Names of the ABI functions the loaded library exports."""
     lib = load()
-    names = ["tu_market_create", "tu_market_update_factors", "tu_ipfp_sweep", "tu_ipfp_solve",
+    names = ["tu_market_create", "tu_market_update_factors", "tu_market_update_factors_fp8", "tu_ipfp_sweep",
+             "tu_ipfp_solve",
              "tu_ipfp_solve_ranking", "tu_mu_block",
              "tu_topk_partners", "tu_get_potentials", "tu_set_potentials", "tu_profile_enable",
              "tu_profile_read", "tu_market_destroy", "tu_status_string", "tu_market_last_error",
@@ -192,23 +195,47 @@ def _stream_handle(stream) -> Optional[int]:
 # the C functions, same names
 # ---------------------------------------------------------------------------
 
+def _is_bytes(a) -> bool:
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            return a.dtype == torch.uint8
+    except ImportError:  # pragma: no cover
+        pass
+    return isinstance(a, np.ndarray) and a.dtype == np.uint8
+
+
 def tu_market_create(F, K, G, L, n, m, sigma: float, *, bias_x=None, bias_y=None, path: str = "fused",
-                     partition: int = 0, stream=None, fp8: bool = False) -> int:
+                     partition: int = 0, stream=None, fp8: bool = False, fscale_x=None, fscale_y=None) -> int:
     """Create a market; returns the opaque handle (int). n, m: host float64.
-    fp8: compute with e4m3 factors (F, K, G, L must be float32; the library
-    quantizes them with one power-of-two scale per side)."""
+    fp8: compute with e4m3 factors. True (or "rows"): per-row scales, F, K, G,
+    L float32 (the library quantizes every row with its own power-of-two
+    scale), or, with fscale_x / fscale_y (float32, N and M), uint8 e4m3 bytes
+    quantized by the caller. "side": one power-of-two scale per side (float32
+    factors; the faster FP8 kernel)."""
+    if fp8 not in (False, True, "rows", "side"):
+        raise ValueError("fp8 must be False, True / 'rows' or 'side'")
     lib = load()
     N, d = _shape(F)
     M, d2 = _shape(G)
     if _shape(K) != (N, d) or _shape(L) != (M, d2) or d != d2:
         raise ValueError("F, K must be N x d and G, L must be M x d")
-    dt = _dtype_code(F)
-    if any(_dtype_code(x) != dt for x in (K, G, L)):
-        raise TypeError("F, K, G, L must share one dtype")
-    if fp8:
-        if dt != TU_DTYPE_FP32:
-            raise TypeError("fp8 markets take float32 factors")
+    if fscale_x is not None or fscale_y is not None:
+        if fp8 not in (True, "rows") or fscale_x is None or fscale_y is None:
+            raise ValueError("fscale_x and fscale_y come together, with per-row fp8")
+        if not all(_is_bytes(x) for x in (F, K, G, L)):
+            raise TypeError("caller-scaled fp8 markets take uint8 e4m3 bytes")
+        if _shape(fscale_x) != (N,) or _shape(fscale_y) != (M,):
+            raise ValueError("fscale_x must have N entries and fscale_y M entries")
         dt = TU_DTYPE_FP8E4M3
+    else:
+        dt = _dtype_code(F)
+        if any(_dtype_code(x) != dt for x in (K, G, L)):
+            raise TypeError("F, K, G, L must share one dtype")
+        if fp8:
+            if dt != TU_DTYPE_FP32:
+                raise TypeError("fp8 markets take float32 factors")
+            dt = TU_DTYPE_FP8E4M3_SIDE if fp8 == "side" else TU_DTYPE_FP8E4M3
     n = np.ascontiguousarray(n, dtype=np.float64)
     m = np.ascontiguousarray(m, dtype=np.float64)
     if n.shape != (N,) or m.shape != (M,):
@@ -216,7 +243,7 @@ def tu_market_create(F, K, G, L, n, m, sigma: float, *, bias_x=None, bias_y=None
     desc = MarketDesc(N=N, M=M, d=d, dtype=dt, path=TU_PATH_FUSED if path == "fused" else TU_PATH_DENSE,
                       F=_ptr(F), K=_ptr(K), G=_ptr(G), L=_ptr(L), bias_x=_ptr(bias_x), bias_y=_ptr(bias_y),
                       n=_ptr(n), m=_ptr(m), sigma=float(sigma), partition=int(partition),
-                      stream=_stream_handle(stream))
+                      stream=_stream_handle(stream), fscale_x=_ptr(fscale_x), fscale_y=_ptr(fscale_y))
     if path not in ("fused", "dense"):
         raise ValueError("path must be 'fused' or 'dense'")
     h = ctypes.c_void_p()
@@ -226,6 +253,11 @@ def tu_market_create(F, K, G, L, n, m, sigma: float, *, bias_x=None, bias_y=None
 
 def tu_market_update_factors(h: int, F, K, G, L) -> None:
     _check(load().tu_market_update_factors(h, _ptr(F), _ptr(K), _ptr(G), _ptr(L)), "tu_market_update_factors", h)
+
+
+def tu_market_update_factors_fp8(h: int, F, K, G, L, fscale_x, fscale_y) -> None:
+    _check(load().tu_market_update_factors_fp8(h, _ptr(F), _ptr(K), _ptr(G), _ptr(L), _ptr(fscale_x),
+                                               _ptr(fscale_y)), "tu_market_update_factors_fp8", h)
 
 
 def tu_ipfp_sweep(h: int, nsweeps: int, residual: bool = False) -> Optional[float]:
@@ -465,13 +497,14 @@ class Market:
     """Owning wrapper of a market handle (torch CUDA tensors for outputs)."""
 
     def __init__(self, F, K, G, L, n, m, sigma, *, bias_x=None, bias_y=None, path="fused", partition=0,
-                 stream=None, device="cuda", fp8=False):
+                 stream=None, device="cuda", fp8=False, fscale_x=None, fscale_y=None):
         self.N, self.d = _shape(F)
         self.M = _shape(G)[0]
         self.device = device
         self.stream = stream
         self.handle = tu_market_create(F, K, G, L, n, m, sigma, bias_x=bias_x, bias_y=bias_y, path=path,
-                                       partition=partition, stream=stream, fp8=fp8)
+                                       partition=partition, stream=stream, fp8=fp8, fscale_x=fscale_x,
+                                       fscale_y=fscale_y)
 
     def sweep(self, nsweeps: int, residual: bool = False):
         return tu_ipfp_sweep(self.handle, nsweeps, residual)
@@ -594,9 +627,10 @@ class Batch:
 
 
 def from_synth(mk, path: str = "fused", device: str = "cuda", stream=None, partition: int = 0,
-               fp8: bool = False) -> Market:
-    """Create a :class:`Market` on the device from a ``synth.Market`` (fp8: its
-    float32 factors, quantized by the library to e4m3)."""
+               fp8=False) -> Market:
+    """Create a :class:`Market` on the device from a ``synth.Market`` (fp8:
+    True / "rows" or "side", its float32 factors, quantized by the library to
+    e4m3 with per-row or per-side scales)."""
     import torch
 
     def dev(a):

@@ -59,10 +59,9 @@ struct tu_batch {
   int num_sms = 0;
   int grid = 0;  // CTAs of the batched half-sweep: one per SM
   int64_t kp = 0;
-  int fp8 = 0;  // e4m3 markets (every member alike)
+  int dtype = 0;  // the members' dtype (e4m3 markets: every member alike)
   cudaStream_t stream = nullptr;
   std::vector<tu_market*> markets;
-  std::vector<float> cmul;          // each market's exponent multiplier as uploaded (FP8 scales may change)
   std::vector<double> relax_cfg;    // each market's relaxation setting at creation
   BatchDesc* desc_dev[2] = {nullptr, nullptr};  // [side][market]
   std::vector<int> own_tiles[2];    // per market
@@ -281,23 +280,15 @@ tu_status check_live(tu_batch* b) {
   return TU_OK;
 }
 
-// Work already enqueued on the members' streams completes before batch work;
-// a member whose factors were replaced since (FP8: new scales) gets its
-// exponent multiplier re-uploaded.
+// Work already enqueued on the members' streams completes before batch work
+// (factors replaced since land in place: the descriptors hold the members'
+// buffers, and the exponent multiplier depends on sigma only).
 tu_status wait_members(tu_batch* b) {
   std::vector<cudaStream_t> seen;
   for (tu_market* m : b->markets) {
     if (m->stream == b->stream || std::find(seen.begin(), seen.end(), m->stream) != seen.end()) continue;
     seen.push_back(m->stream);
     TB_CK(b, cudaStreamSynchronize(m->stream));
-  }
-  for (int i = 0; i < b->count; ++i) {
-    const float c = b->markets[i]->cmul;
-    if (c == b->cmul[i]) continue;
-    TB_CK(b, cudaStreamSynchronize(b->stream));
-    for (int side = 0; side < 2; ++side)
-      TB_CK(b, cudaMemcpy(&b->desc_dev[side][i].c, &c, sizeof(float), cudaMemcpyHostToDevice));
-    b->cmul[i] = c;
   }
   return TU_OK;
 }
@@ -402,7 +393,7 @@ cudaError_t enqueue_half(tu_batch* b, int si, int side, int residual, int update
   L.err = b->err_dev;
   L.grid = b->grid;
   L.kp = b->kp;
-  L.fp8 = b->fp8;
+  L.dtype = b->dtype;
   L.residual = residual;
   L.update = update;
   if ((e = launch_fused_batch(L, b->stream)) != cudaSuccess) return e;
@@ -541,9 +532,11 @@ tu_status tu_batch_create(const tu_market_t* markets, int count, void* stream, t
     tu_market* m = ms[i];
     if (m == nullptr || m->poisoned || m->path != TU_PATH_FUSED) return TU_ERR_INVALID_ARG;
     if (m->kp != ms[0]->kp || m->device != ms[0]->device) return TU_ERR_INVALID_ARG;
-    if ((m->dtype == TU_DTYPE_FP8E4M3) != (ms[0]->dtype == TU_DTYPE_FP8E4M3)) return TU_ERR_INVALID_ARG;
-    // the batched kernel keeps one shift per market and half-sweep
-    if (m->wide) return TU_ERR_UNSUPPORTED;
+    // one operand format (BF16 and FP32 inputs are both computed in BF16)
+    if ((is_fp8(m->dtype) || is_fp8(ms[0]->dtype)) && m->dtype != ms[0]->dtype) return TU_ERR_INVALID_ARG;
+    // the batched kernel keeps one shift per market and half-sweep, and is
+    // built for packed rows of one or two 128-byte k blocks (e4m3: one)
+    if (m->wide || m->kp > 128) return TU_ERR_UNSUPPORTED;
   }
   {
     std::vector<tu_market*> sorted(ms);
@@ -561,7 +554,7 @@ tu_status tu_batch_create(const tu_market_t* markets, int count, void* stream, t
   b->num_sms = ms[0]->num_sms;
   b->grid = b->num_sms;
   b->kp = ms[0]->kp;
-  b->fp8 = ms[0]->dtype == TU_DTYPE_FP8E4M3 ? 1 : 0;
+  b->dtype = ms[0]->dtype;
   b->stream = static_cast<cudaStream_t>(stream);
   b->markets = ms;
   if (cudaSetDevice(b->device) != cudaSuccess) return bail(TU_ERR_CUDA);
@@ -604,6 +597,8 @@ tu_status tu_batch_create(const tu_market_t* markets, int count, void* stream, t
       d.num_partner_tiles = (int)((par.rows + kFusedPartnerRows - 1) / kFusedPartnerRows);
       d.slot0 = (int)slot;
       d.c = m->cmul;
+      d.fs_own = own.fs;
+      d.fs_par = par.fs;
       b->own_tiles[side][i] = d.num_own_tiles;
       b->partner_tiles[side][i] = d.num_partner_tiles;
       slot += d.num_own_tiles;
@@ -631,8 +626,6 @@ tu_status tu_batch_create(const tu_market_t* markets, int count, void* stream, t
         return TU_OK;
       }()) != TU_OK)
     return bail(st);
-  b->cmul.resize(count);
-  for (int i = 0; i < count; ++i) b->cmul[i] = ms[i]->cmul;
   b->relax_cfg.resize(count);
   for (int i = 0; i < count; ++i) b->relax_cfg[i] = ms[i]->omega_cfg;
   if (reset_omega(b) != TU_OK || clear_results(b) != TU_OK || cudaStreamSynchronize(b->stream) != cudaSuccess)

@@ -16,9 +16,11 @@
 //   warp 0     : producer (one elected thread): TMA loads of the own tile
 //                [F|K]_j (256 rows x kp) once per own tile (double-buffered
 //                when kp = 64) and of partner tiles (128 rows x kp) through a
-//                STAGES-deep shared-memory ring, plus a bulk copy of each
-//                partner tile's 128 g values into an 8-slot ring that the
-//                epilogue reads with broadcast loads.
+//                STAGES-deep shared-memory ring (a stage is a whole partner
+//                tile, or with four 128-byte k blocks per row one k block of
+//                it), plus a bulk copy of each partner tile's 128 g values
+//                (e4m3 factors: and of its 128 row scales) into an 8-slot ring
+//                that the epilogue reads with broadcast loads.
 //   warp 1     : MMA issuer (one thread): two tcgen05.mma M=128 N=128 chains
 //                (own rows 0-127 and 128-255) per partner tile into one of two
 //                TMEM accumulator buffers (2 x 256 columns = all 512).
@@ -101,21 +103,35 @@ struct FusedParams {
   // wide markets: per own row (index row0 + r), the largest exponent in log2
   // units (written by kModeRowMax, subtracted by kModeSweepShift)
   float* rowmax;
+  // e4m3 factors: per-row scales of the own side (index row0 + r) and of the
+  // partner side (index = partner user); the product of row r and partner
+  // column j is fs_own[r] * fs_par[j] * <e4m3 row r, e4m3 row j>
+  const float* fs_own;
+  const float* fs_par;
 };
 
-// Own-tile buffers: with a 64-wide inner dimension the next own tile is loaded
-// while the current one is still in use (short items of batched launches);
-// with 128 there is room for one only.
+// Own-tile buffers: with one 128-byte k block per row the next own tile is
+// loaded while the current one is still in use (short items of batched
+// launches); with two or four there is room for one only.
 template <int KB>
 constexpr int kABufs = KB == 1 ? 2 : 1;
 
-// shared memory: [A: ABUFS x KB x 32 KB][B: STAGES x KB x 16 KB][g ring: 8 x 512 B]
-//                [barriers and flags: 512 B][reduction: 512 B][row hand-over: 2 x 256 floats]
+// k blocks per partner stage: with four k blocks per row (d up to 128 in
+// BF16, 256 in e4m3) a whole 64 KB partner tile would leave room for one
+// stage beside the 128 KB own tile, so a stage then carries one k block and a
+// partner tile takes four stages.
+constexpr int kbs_for(int KB) { return KB == 4 ? 1 : KB; }
+
+// Operand formats: BF16, e4m3 with one scale per side, e4m3 with one per row.
+enum : int { kFmtBF16 = 0, kFmtE4M3Side = 1, kFmtE4M3Rows = 2 };
+
+// shared memory: [A: ABUFS x KB x 32 KB][B: STAGES x KBS x 16 KB][g ring: 8 x 512 B]
+//                [per-row scales: scale ring 8 x 512 B][barriers and flags: 512 B]
+//                [reduction: 512 B][row hand-over: 2 x 256 floats]
 constexpr int kTailBytes = 512 + 512 + 2 * kFusedOwnRows * 4;
-template <int KB>
-constexpr int smem_bytes(int stages) {
-  return 1024 /*alignment slack*/ + kABufs<KB> * KB * kOwnBytesPerKB + stages * KB * kPartnerBytesPerKB +
-         kGSlots * kGBytes + kTailBytes;
+constexpr int smem_bytes(int KB, int fmt, int stages) {
+  return 1024 /*alignment slack*/ + (KB == 1 ? 2 : 1) * KB * kOwnBytesPerKB +
+         stages * kbs_for(KB) * kPartnerBytesPerKB + kGSlots * kGBytes * (fmt == kFmtE4M3Rows ? 2 : 1) + kTailBytes;
 }
 
 __device__ __forceinline__ void raise_error(int* err, volatile int* abort_flag, int code) {
@@ -175,6 +191,52 @@ __device__ __forceinline__ void pair_step(uint64_t& acc, uint32_t phi0, uint32_t
       : "r"(phi0), "r"(phi1), "f"(g0), "f"(g1), "l"(cc));
 }
 
+// e4m3 factors: acc += (ex2(phi0 f0 c + g0), ex2(phi1 f1 c + g1)), f the
+// partner rows' scales (the own row's scale is folded into c).
+__device__ __forceinline__ void pair_step_scaled(uint64_t& acc, uint32_t phi0, uint32_t phi1, float g0, float g1,
+                                                 float f0, float f1, uint64_t cc) {
+  asm("{\n\t.reg .b64 a, gg, ff, t, e;\n\t.reg .f32 t0, t1, e0, e1;\n\t"
+      "mov.b64 a, {%1, %2};\n\t"
+      "mov.b64 gg, {%3, %4};\n\t"
+      "mov.b64 ff, {%5, %6};\n\t"
+      "mul.rn.f32x2 t, a, ff;\n\t"
+      "fma.rn.f32x2 t, t, %7, gg;\n\t"
+      "mov.b64 {t0, t1}, t;\n\t"
+      "ex2.approx.ftz.f32 e0, t0;\n\t"
+      "ex2.approx.ftz.f32 e1, t1;\n\t"
+      "mov.b64 e, {e0, e1};\n\t"
+      "add.rn.f32x2 %0, %0, e;\n\t}"
+      : "+l"(acc)
+      : "r"(phi0), "r"(phi1), "f"(g0), "f"(g1), "f"(f0), "f"(f1), "l"(cc));
+}
+
+// The same with the row's shift ss = (-S, -S) added before ex2 (wide markets).
+__device__ __forceinline__ void pair_step_scaled_shift(uint64_t& acc, uint32_t phi0, uint32_t phi1, float g0,
+                                                       float g1, float f0, float f1, uint64_t cc, uint64_t ss) {
+  asm("{\n\t.reg .b64 a, gg, ff, t, e;\n\t.reg .f32 t0, t1, e0, e1;\n\t"
+      "mov.b64 a, {%1, %2};\n\t"
+      "mov.b64 gg, {%3, %4};\n\t"
+      "mov.b64 ff, {%5, %6};\n\t"
+      "mul.rn.f32x2 t, a, ff;\n\t"
+      "fma.rn.f32x2 t, t, %7, gg;\n\t"
+      "add.rn.f32x2 t, t, %8;\n\t"
+      "mov.b64 {t0, t1}, t;\n\t"
+      "ex2.approx.ftz.f32 e0, t0;\n\t"
+      "ex2.approx.ftz.f32 e1, t1;\n\t"
+      "mov.b64 e, {e0, e1};\n\t"
+      "add.rn.f32x2 %0, %0, e;\n\t}"
+      : "+l"(acc)
+      : "r"(phi0), "r"(phi1), "f"(g0), "f"(g1), "f"(f0), "f"(f1), "l"(cc), "l"(ss));
+}
+
+// phi of column i of a chunk, times the partner row's scale (e4m3 factors
+// with per-row scales)
+template <bool RS>
+__device__ __forceinline__ float scaled_phi(uint32_t v, const float* fs, int i) {
+  if constexpr (RS) return __uint_as_float(v) * fs[i];
+  return __uint_as_float(v);
+}
+
 __device__ __forceinline__ float unpack_sum(uint64_t a) {
   return __uint_as_float((uint32_t)a) + __uint_as_float((uint32_t)(a >> 32));
 }
@@ -197,33 +259,46 @@ __device__ __forceinline__ void pair_step_shift(uint64_t& acc, uint32_t phi0, ui
       : "r"(phi0), "r"(phi1), "f"(g0), "f"(g1), "l"(cc), "l"(ss));
 }
 
-__device__ __forceinline__ void chunk_sum_shift(const uint32_t (&v)[32], const float4* gs4, uint64_t cc, uint64_t ss,
-                                                uint64_t (&acc)[4]) {
+template <bool RS>
+__device__ __forceinline__ void chunk_sum_shift(const uint32_t (&v)[32], const float4* gs4, const float4* fs4,
+                                                uint64_t cc, uint64_t ss, uint64_t (&acc)[4]) {
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const float4 gg = gs4[i];
-    pair_step_shift(acc[(2 * i) & 3], v[4 * i + 0], v[4 * i + 1], gg.x, gg.y, cc, ss);
-    pair_step_shift(acc[(2 * i + 1) & 3], v[4 * i + 2], v[4 * i + 3], gg.z, gg.w, cc, ss);
+    if constexpr (RS) {
+      const float4 ff = fs4[i];
+      pair_step_scaled_shift(acc[(2 * i) & 3], v[4 * i + 0], v[4 * i + 1], gg.x, gg.y, ff.x, ff.y, cc, ss);
+      pair_step_scaled_shift(acc[(2 * i + 1) & 3], v[4 * i + 2], v[4 * i + 3], gg.z, gg.w, ff.z, ff.w, cc, ss);
+    } else {
+      pair_step_shift(acc[(2 * i) & 3], v[4 * i + 0], v[4 * i + 1], gg.x, gg.y, cc, ss);
+      pair_step_shift(acc[(2 * i + 1) & 3], v[4 * i + 2], v[4 * i + 3], gg.z, gg.w, cc, ss);
+    }
   }
 }
 
 // Largest exponent c * phi + g of one 32-column chunk, folded into mx.
-__device__ __forceinline__ void chunk_max(const uint32_t (&v)[32], const float4* gs4, float c, float& mx) {
+template <bool RS>
+__device__ __forceinline__ void chunk_max(const uint32_t (&v)[32], const float* g, const float* fs, float c,
+                                          float& mx) {
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const float4 gg = gs4[i];
-    mx = fmaxf(mx, fmaxf(fmaxf(fmaf(__uint_as_float(v[4 * i + 0]), c, gg.x), fmaf(__uint_as_float(v[4 * i + 1]), c, gg.y)),
-                         fmaxf(fmaf(__uint_as_float(v[4 * i + 2]), c, gg.z), fmaf(__uint_as_float(v[4 * i + 3]), c, gg.w))));
-  }
+  for (int i = 0; i < 32; ++i) mx = fmaxf(mx, fmaf(scaled_phi<RS>(v[i], fs, i), c, g[i]));
 }
 
 // Sum over one 32-column chunk: 16 packed pairs into four packed accumulators.
-__device__ __forceinline__ void chunk_sum(const uint32_t (&v)[32], const float4* gs4, uint64_t cc, uint64_t (&acc)[4]) {
+template <bool RS>
+__device__ __forceinline__ void chunk_sum(const uint32_t (&v)[32], const float4* gs4, const float4* fs4, uint64_t cc,
+                                          uint64_t (&acc)[4]) {
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
     const float4 gg = gs4[i];
-    pair_step(acc[(2 * i) & 3], v[4 * i + 0], v[4 * i + 1], gg.x, gg.y, cc);
-    pair_step(acc[(2 * i + 1) & 3], v[4 * i + 2], v[4 * i + 3], gg.z, gg.w, cc);
+    if constexpr (RS) {
+      const float4 ff = fs4[i];
+      pair_step_scaled(acc[(2 * i) & 3], v[4 * i + 0], v[4 * i + 1], gg.x, gg.y, ff.x, ff.y, cc);
+      pair_step_scaled(acc[(2 * i + 1) & 3], v[4 * i + 2], v[4 * i + 3], gg.z, gg.w, ff.z, ff.w, cc);
+    } else {
+      pair_step(acc[(2 * i) & 3], v[4 * i + 0], v[4 * i + 1], gg.x, gg.y, cc);
+      pair_step(acc[(2 * i + 1) & 3], v[4 * i + 2], v[4 * i + 3], gg.z, gg.w, cc);
+    }
   }
 }
 
@@ -250,18 +325,19 @@ __device__ __noinline__ float top_insert(float* tv, int32_t* ti, int* cnt, int k
 // Ranked lists: score = c * phi_hat + g (log2 units, shifted; same order as
 // log mu within a row). The chunk's maximum is compared with the running k-th
 // best first, so most chunks cost one FFMA and one max per column.
-__device__ __forceinline__ void chunk_topk(const uint32_t (&v)[32], const float* g, float c, int64_t colbase, int k,
-                                           float* tv, int32_t* ti, int* cnt, float& thr) {
+template <bool RS>
+__device__ __forceinline__ void chunk_topk(const uint32_t (&v)[32], const float* g, const float* fs, float c,
+                                           int64_t colbase, int k, float* tv, int32_t* ti, int* cnt, float& thr) {
   const float4* g4 = reinterpret_cast<const float4*>(g);
   float s[32];
   float mx = -INFINITY;
 #pragma unroll
   for (int i4 = 0; i4 < 8; ++i4) {
     const float4 gg = g4[i4];
-    s[4 * i4 + 0] = fmaf(__uint_as_float(v[4 * i4 + 0]), c, gg.x);
-    s[4 * i4 + 1] = fmaf(__uint_as_float(v[4 * i4 + 1]), c, gg.y);
-    s[4 * i4 + 2] = fmaf(__uint_as_float(v[4 * i4 + 2]), c, gg.z);
-    s[4 * i4 + 3] = fmaf(__uint_as_float(v[4 * i4 + 3]), c, gg.w);
+    s[4 * i4 + 0] = fmaf(scaled_phi<RS>(v[4 * i4 + 0], fs, 4 * i4 + 0), c, gg.x);
+    s[4 * i4 + 1] = fmaf(scaled_phi<RS>(v[4 * i4 + 1], fs, 4 * i4 + 1), c, gg.y);
+    s[4 * i4 + 2] = fmaf(scaled_phi<RS>(v[4 * i4 + 2], fs, 4 * i4 + 2), c, gg.z);
+    s[4 * i4 + 3] = fmaf(scaled_phi<RS>(v[4 * i4 + 3], fs, 4 * i4 + 3), c, gg.w);
     mx = fmaxf(mx, fmaxf(fmaxf(s[4 * i4 + 0], s[4 * i4 + 1]), fmaxf(s[4 * i4 + 2], s[4 * i4 + 3])));
   }
   if (mx > thr) {
@@ -318,18 +394,19 @@ __device__ __noinline__ float list_insert(uint32_t lv, uint32_t li, int k, float
   return lds_f32(lv + (uint32_t)(k - 1) * kStride);
 }
 
-__device__ __forceinline__ void chunk_topk_shared(const uint32_t (&v)[32], const float* g, float c, int64_t colbase,
-                                                  int k, uint32_t lv, uint32_t li, float& thr) {
+template <bool RS>
+__device__ __forceinline__ void chunk_topk_shared(const uint32_t (&v)[32], const float* g, const float* fs, float c,
+                                                  int64_t colbase, int k, uint32_t lv, uint32_t li, float& thr) {
   const float4* g4 = reinterpret_cast<const float4*>(g);
   float s[32];
   float mx = -INFINITY;
 #pragma unroll
   for (int i4 = 0; i4 < 8; ++i4) {
     const float4 gg = g4[i4];
-    s[4 * i4 + 0] = fmaf(__uint_as_float(v[4 * i4 + 0]), c, gg.x);
-    s[4 * i4 + 1] = fmaf(__uint_as_float(v[4 * i4 + 1]), c, gg.y);
-    s[4 * i4 + 2] = fmaf(__uint_as_float(v[4 * i4 + 2]), c, gg.z);
-    s[4 * i4 + 3] = fmaf(__uint_as_float(v[4 * i4 + 3]), c, gg.w);
+    s[4 * i4 + 0] = fmaf(scaled_phi<RS>(v[4 * i4 + 0], fs, 4 * i4 + 0), c, gg.x);
+    s[4 * i4 + 1] = fmaf(scaled_phi<RS>(v[4 * i4 + 1], fs, 4 * i4 + 1), c, gg.y);
+    s[4 * i4 + 2] = fmaf(scaled_phi<RS>(v[4 * i4 + 2], fs, 4 * i4 + 2), c, gg.z);
+    s[4 * i4 + 3] = fmaf(scaled_phi<RS>(v[4 * i4 + 3], fs, 4 * i4 + 3), c, gg.w);
     mx = fmaxf(mx, fmaxf(fmaxf(s[4 * i4 + 0], s[4 * i4 + 1]), fmaxf(s[4 * i4 + 2], s[4 * i4 + 3])));
   }
   if (mx > thr) {
@@ -340,15 +417,17 @@ __device__ __forceinline__ void chunk_topk_shared(const uint32_t (&v)[32], const
 }
 
 // mu block: mu = 2^(c * phi_hat + g + lo) * 2^hi, where hi + lo = (shift + ell_row) log2 e.
-__device__ __forceinline__ void chunk_mu(const uint32_t (&v)[32], const float* g, float c, int64_t colbase, float lo,
-                                         int hi, bool row_ok, int64_t r, const FusedParams& p) {
+template <bool RS>
+__device__ __forceinline__ void chunk_mu(const uint32_t (&v)[32], const float* g, const float* fs, float c,
+                                         int64_t colbase, float lo, int hi, bool row_ok, int64_t r,
+                                         const FusedParams& p) {
   if (!row_ok) return;
   float* orow = p.out + r * p.ld;
 #pragma unroll
   for (int i = 0; i < 32; ++i) {
     const int64_t col = colbase + i;
     if (col >= p.y0 && col < p.y0 + p.ny) {
-      const float t = fmaf(__uint_as_float(v[i]), c, g[i]) + lo;
+      const float t = fmaf(scaled_phi<RS>(v[i], fs, i), c, g[i]) + lo;
       // (wide markets: an exponent beyond the FP32 range is brought back by hi first)
       orow[col - p.y0] = fabsf(t) <= 100.0f ? ldexpf(ex2_approx(t), hi) : ex2_approx(t + (float)hi);
     }
@@ -388,14 +467,18 @@ __device__ __forceinline__ int item_step() {
 // to different markets (tensor maps, vectors and sizes from BatchDesc); the
 // residual partials are then written per own tile and epilogue warp instead
 // of per CTA.
-// F8: e4m3 factors, 128 per 128-byte row (KB = 1), tcgen05.mma kind::f8f6f4;
-// the per-side power-of-two scales are folded into p.c.
+// KB: 128-byte k blocks per packed row (1, 2 or 4: BF16 kp = 64, 128, 256;
+// e4m3 kp = 128, 256, 512).
+// FMT: kFmtBF16, or e4m3 factors on tcgen05.mma kind::f8f6f4 with one scale
+// per side (kFmtE4M3Side: both folded into p.c) or per row (kFmtE4M3Rows: the
+// own row's scale is folded into the row's exponent multiplier, the partner
+// rows' scales multiply the accumulator entries in the epilogue).
 // SMALL: own tiles of 128 rows (one MMA chain; the epilogue warps of the
 // second sub-tile take part in every barrier but load and compute nothing),
 // for markets whose 256-row tiles would leave SMs idle: twice the CTAs, each
 // finishing its rows in about half the time. Every row's arithmetic is the
 // same as with 256-row tiles.
-template <int KB, int STAGES, int MODE, bool BATCH, bool F8, bool SMALL = false>
+template <int KB, int STAGES, int MODE, bool BATCH, int FMT, bool SMALL = false>
 __global__ void __launch_bounds__(kThreads, 1)
     k_fused_halfsweep(const __grid_constant__ CUtensorMap tm_own, const __grid_constant__ CUtensorMap tm_partner,
                       const FusedParams p) {
@@ -403,15 +486,22 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr bool kSweepLike = MODE == kModeSweep || MODE == kModeSweepShift;
   static_assert(!(BATCH && SMALL), "batched launches use 256-row own tiles");
   constexpr int kOwn = SMALL ? kFusedOwnRows / 2 : kFusedOwnRows;  // rows of an own tile
-  static_assert(!F8 || KB == 1, "e4m3 rows are one 128-byte block");
+  static_assert(KB == 1 || KB == 2 || KB == 4, "128-byte k blocks per row");
+  constexpr bool F8 = FMT != kFmtBF16;      // e4m3 operands
+  constexpr bool RS = FMT == kFmtE4M3Rows;  // per-row scales
   constexpr int ABUF = kABufs<KB>;
+  constexpr int KBS = kbs_for(KB);   // k blocks per partner stage
+  constexpr int SPT = KB / KBS;      // stages per partner tile
+  constexpr int XB = F8 ? 128 : kKBlock;  // elements per 128-byte k block (TMA x coordinate step)
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_u32 = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + (((raw_u32 + 1023u) & ~1023u) - raw_u32);
   uint8_t* sA = smem;
   uint8_t* sB = smem + ABUF * KB * kOwnBytesPerKB;
-  float* sG = reinterpret_cast<float*>(sB + STAGES * KB * kPartnerBytesPerKB);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(sG) + kGSlots * kGBytes);
+  float* sG = reinterpret_cast<float*>(sB + STAGES * KBS * kPartnerBytesPerKB);
+  float* sF = sG + kGSlots * kFusedPartnerRows;  // per-row scales: partner scale ring
+  uint64_t* bars =
+      reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(sG) + kGSlots * kGBytes * (RS ? 2 : 1));
   uint64_t* full = bars;
   uint64_t* empty = bars + STAGES;
   uint64_t* gfull = bars + 2 * STAGES;
@@ -498,6 +588,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const CUtensorMap* map_own = BATCH ? &bd->tm_own : &tm_own;
         const CUtensorMap* map_partner = BATCH ? &bd->tm_partner : &tm_partner;
         const float* gsrc = BATCH ? bd->g : p.g + p.col0;
+        const float* fsrc = BATCH ? bd->fs_par : p.fs_par + p.col0;
         const int npt = BATCH ? bd->num_partner_tiles : p.num_partner_tiles;
         // (SMALL: the 256-row box also brings the next tile's rows, unused)
         const int64_t arow = BATCH ? (int64_t)t * kFusedOwnRows : p.row0 + (int64_t)t * kOwn;
@@ -507,32 +598,37 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         mbar_arrive_expect_tx(&a_full[ab], KB * kOwnBytesPerKB);
         for (int kb = 0; kb < KB; ++kb)
-          tma_load_2d(sA + (ab * KB + kb) * kOwnBytesPerKB, map_own, &a_full[ab], kb * kKBlock, (int)arow);
+          tma_load_2d(sA + (ab * KB + kb) * kOwnBytesPerKB, map_own, &a_full[ab], kb * XB, (int)arow);
         ++a_armed[ab];
         if (++ab == ABUF) {
           ab = 0;
           a_phase ^= 1u;
         }
-        for (int j = 0; j < npt; ++j) {
-          if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
-            ok = false;
-            break;
+        for (int j = 0; j < npt && ok; ++j) {
+          for (int sp = 0; sp < SPT; ++sp) {
+            if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
+              ok = false;
+              break;
+            }
+            mbar_arrive_expect_tx(&full[stage], KBS * kPartnerBytesPerKB);
+            for (int kb = 0; kb < KBS; ++kb)
+              tma_load_2d(sB + (stage * KBS + kb) * kPartnerBytesPerKB, map_partner, &full[stage],
+                          (sp * KBS + kb) * XB, (int)(p.col0 + (int64_t)j * kFusedPartnerRows));
+            ++armed[stage];
+            if (++stage == STAGES) {
+              stage = 0;
+              phase ^= 1u;
+            }
           }
-          mbar_arrive_expect_tx(&full[stage], KB * kPartnerBytesPerKB);
-          for (int kb = 0; kb < KB; ++kb)
-            tma_load_2d(sB + (stage * KB + kb) * kPartnerBytesPerKB, map_partner, &full[stage], kb * kKBlock,
-                        (int)(p.col0 + (int64_t)j * kFusedPartnerRows));
-          ++armed[stage];
-          if (++stage == STAGES) {
-            stage = 0;
-            phase ^= 1u;
-          }
+          if (!ok) break;
           if (!mbar_wait(&gempty[gs], gphase ^ 1u, abort_flag)) {
             ok = false;
             break;
           }
-          mbar_arrive_expect_tx(&gfull[gs], kGBytes);
+          mbar_arrive_expect_tx(&gfull[gs], RS ? 2 * kGBytes : kGBytes);
           bulk_load(sG + gs * kFusedPartnerRows, gsrc + (int64_t)j * kFusedPartnerRows, kGBytes, &gfull[gs]);
+          if constexpr (RS)
+            bulk_load(sF + gs * kFusedPartnerRows, fsrc + (int64_t)j * kFusedPartnerRows, kGBytes, &gfull[gs]);
           ++garmed[gs];
           if (++gs == kGSlots) {
             gs = 0;
@@ -577,35 +673,44 @@ __global__ void __launch_bounds__(kThreads, 1)
           ab = 0;
           a_phase ^= 1u;
         }
-        for (int j = 0; j < npt; ++j) {
-          if (!mbar_wait(&full[stage], phase, abort_flag) || !mbar_wait(&tempty[buf], tphase ^ 1u, abort_flag)) {
+        for (int j = 0; j < npt && ok; ++j) {
+          if (!mbar_wait(&tempty[buf], tphase ^ 1u, abort_flag)) {
             ok = false;
             break;
           }
-          tc_fence_after();
-          const uint32_t b0 = smem_u32(sB + stage * KB * kPartnerBytesPerKB);
+          for (int sp = 0; sp < SPT; ++sp) {
+            if (!mbar_wait(&full[stage], phase, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t b0 = smem_u32(sB + stage * KBS * kPartnerBytesPerKB);
 #pragma unroll
-          for (int h = 0; h < (SMALL ? 1 : 2); ++h) {
-            const uint32_t d_tmem = tmem_base + (uint32_t)(buf * 256 + h * 128);
+            for (int h = 0; h < (SMALL ? 1 : 2); ++h) {
+              const uint32_t d_tmem = tmem_base + (uint32_t)(buf * 256 + h * 128);
 #pragma unroll
-            for (int k = 0; k < KB * 4; ++k) {
-              const int kb = k >> 2, kk = k & 3;
-              const uint64_t adesc = sdesc_sw128(a0 + kb * kOwnBytesPerKB + h * 128 * 128 + kk * 32);
-              const uint64_t bdesc = sdesc_sw128(b0 + kb * kPartnerBytesPerKB + kk * 32);
-              if constexpr (F8) {
-                umma_e4m3(d_tmem, adesc, bdesc, idesc, k > 0 ? 1u : 0u);
-              } else {
-                umma_bf16(d_tmem, adesc, bdesc, idesc, k > 0 ? 1u : 0u);
+              for (int k = 0; k < KBS * 4; ++k) {
+                const int kbl = k >> 2, kk = k & 3;
+                const int kb = sp * KBS + kbl;  // k block within the packed row
+                const uint64_t adesc = sdesc_sw128(a0 + kb * kOwnBytesPerKB + h * 128 * 128 + kk * 32);
+                const uint64_t bdesc = sdesc_sw128(b0 + kbl * kPartnerBytesPerKB + kk * 32);
+                const uint32_t accum = (sp > 0 || k > 0) ? 1u : 0u;
+                if constexpr (F8) {
+                  umma_e4m3(d_tmem, adesc, bdesc, idesc, accum);
+                } else {
+                  umma_bf16(d_tmem, adesc, bdesc, idesc, accum);
+                }
               }
             }
+            umma_commit(&empty[stage]);
+            if (++stage == STAGES) {
+              stage = 0;
+              phase ^= 1u;
+            }
           }
-          umma_commit(&empty[stage]);
+          if (!ok) break;
           umma_commit(&tfull[buf]);
           if (j == npt - 1) umma_commit(a_release);
-          if (++stage == STAGES) {
-            stage = 0;
-            phase ^= 1u;
-          }
           buf ^= 1;
           if (buf == 0) tphase ^= 1u;
         }
@@ -622,11 +727,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int q = warp & 3;           // TMEM lane quadrant this warp may access
     const int h = (ew >> 2) & 1;      // own sub-tile: rows [h*128, h*128+128)
     const int half = ew >> 3;         // columns [half*64, half*64+64) of every partner tile
-    uint64_t cc;
-    {
-      const uint32_t cb = __float_as_uint(p.c);
-      cc = ((uint64_t)cb << 32) | cb;
-    }
+    uint64_t cc = 0ull;
+    float crow = p.c;  // this thread's row's exponent multiplier (e4m3: times the row's scale)
     // single market: the shift, own offset and omega of the launch (batched: per item)
     const double shift0 = BATCH ? 0.0 : __ldg(p.lmax);
     // (ranked lists and mu blocks run on potentials without pending offsets:
@@ -654,14 +756,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         const ItemRef w = batch_item(p, it);
         bd = w.d;
         t = w.t;
-        const uint32_t cb = __float_as_uint(bd->c);
-        cc = ((uint64_t)cb << 32) | cb;
       }
       const double shift = BATCH ? bd->st[kStShift] : shift0;
       const int npt = BATCH ? bd->num_partner_tiles : p.num_partner_tiles;
       const int rloc = h * 128 + q * 32 + lane;          // row within the own tile
       const int64_t r = (int64_t)t * kOwn + rloc;         // row within the launch
       const bool row_ok = rloc < kOwn && r < (BATCH ? bd->rows : p.rows);
+      crow = BATCH ? bd->c : p.c;
+      if constexpr (RS) {
+        const float* fso = BATCH ? bd->fs_own : p.fs_own;
+        if (row_ok) crow *= fso[(BATCH ? 0 : p.row0) + r];
+      }
+      {
+        const uint32_t cb = __float_as_uint(crow);
+        cc = ((uint64_t)cb << 32) | cb;
+      }
       float sum = 0.0f, comp = 0.0f;
       float mu_lo = 0.0f;
       int mu_hi = 0;
@@ -704,6 +813,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256 + h * 128 + half * 64);
         const float* gsf = sG + gs * kFusedPartnerRows + half * 64;
         const float4* gs4 = reinterpret_cast<const float4*>(gsf);
+        const float* fsf = sF + gs * kFusedPartnerRows + half * 64;  // (per-row scales only)
+        const float4* fs4 = reinterpret_cast<const float4*>(fsf);
         const int64_t colbase = p.col0 + (int64_t)j * kFusedPartnerRows + half * 64;
         uint64_t acc[4] = {0ull, 0ull, 0ull, 0ull};
         // SMALL: the second sub-tile's warps keep step with the barriers only
@@ -713,12 +824,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           tmem_ld_issue(taddr, va);
           tmem_ld_wait(va);
           tmem_ld_issue(taddr + 32, vb);
-          if constexpr (MODE == kModeSweep) chunk_sum(va, gs4, cc, acc);
-          if constexpr (MODE == kModeSweepShift) chunk_sum_shift(va, gs4, cc, rshift, acc);
-          if constexpr (MODE == kModeRowMax) chunk_max(va, gs4, p.c, rmax);
-          if constexpr (MODE == kModeTopK) chunk_topk(va, gsf, p.c, colbase, p.k, tv, ti, &tcnt, thr);
-          if constexpr (MODE == kModeTopKShared) chunk_topk_shared(va, gsf, p.c, colbase, p.k, lv, li, thr);
-          if constexpr (MODE == kModeMu) chunk_mu(va, gsf, p.c, colbase, mu_lo, mu_hi, row_ok, r, p);
+          if constexpr (MODE == kModeSweep) chunk_sum<RS>(va, gs4, fs4, cc, acc);
+          if constexpr (MODE == kModeSweepShift) chunk_sum_shift<RS>(va, gs4, fs4, cc, rshift, acc);
+          if constexpr (MODE == kModeRowMax) chunk_max<RS>(va, gsf, fsf, crow, rmax);
+          if constexpr (MODE == kModeTopK) chunk_topk<RS>(va, gsf, fsf, crow, colbase, p.k, tv, ti, &tcnt, thr);
+          if constexpr (MODE == kModeTopKShared)
+            chunk_topk_shared<RS>(va, gsf, fsf, crow, colbase, p.k, lv, li, thr);
+          if constexpr (MODE == kModeMu) chunk_mu<RS>(va, gsf, fsf, crow, colbase, mu_lo, mu_hi, row_ok, r, p);
           tmem_ld_wait(vb);
         }
         // this warp's part of the accumulator buffer has been read: hand it back to the MMA warp
@@ -726,13 +838,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[buf]);
         if (!idle) {
-          if constexpr (MODE == kModeSweep) chunk_sum(vb, gs4 + 8, cc, acc);
-          if constexpr (MODE == kModeSweepShift) chunk_sum_shift(vb, gs4 + 8, cc, rshift, acc);
-          if constexpr (MODE == kModeRowMax) chunk_max(vb, gs4 + 8, p.c, rmax);
-          if constexpr (MODE == kModeTopK) chunk_topk(vb, gsf + 32, p.c, colbase + 32, p.k, tv, ti, &tcnt, thr);
+          if constexpr (MODE == kModeSweep) chunk_sum<RS>(vb, gs4 + 8, fs4 + 8, cc, acc);
+          if constexpr (MODE == kModeSweepShift) chunk_sum_shift<RS>(vb, gs4 + 8, fs4 + 8, cc, rshift, acc);
+          if constexpr (MODE == kModeRowMax) chunk_max<RS>(vb, gsf + 32, fsf + 32, crow, rmax);
+          if constexpr (MODE == kModeTopK)
+            chunk_topk<RS>(vb, gsf + 32, fsf + 32, crow, colbase + 32, p.k, tv, ti, &tcnt, thr);
           if constexpr (MODE == kModeTopKShared)
-            chunk_topk_shared(vb, gsf + 32, p.c, colbase + 32, p.k, lv, li, thr);
-          if constexpr (MODE == kModeMu) chunk_mu(vb, gsf + 32, p.c, colbase + 32, mu_lo, mu_hi, row_ok, r, p);
+            chunk_topk_shared<RS>(vb, gsf + 32, fsf + 32, crow, colbase + 32, p.k, lv, li, thr);
+          if constexpr (MODE == kModeMu)
+            chunk_mu<RS>(vb, gsf + 32, fsf + 32, crow, colbase + 32, mu_lo, mu_hi, row_ok, r, p);
         }
         // the g slot has been read by this warp
         __syncwarp();
@@ -972,36 +1086,70 @@ cudaError_t make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t k
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-constexpr int kStagesKB1 = 6;
-constexpr int kStagesKB2 = 4;
+constexpr int kSmemLimit = 232448;  // dynamic shared memory per CTA (227 KB)
 
-// Partner-tile stages per instantiation: with a 128-wide inner dimension the
-// shared-memory ranked lists take the room of one stage.
-template <int KB, int MODE>
-constexpr int kStages = KB == 1 ? kStagesKB1 : (MODE == kModeTopKShared ? kStagesKB2 - 1 : kStagesKB2);
+// Partner stages per instantiation: as many as fit beside the own tile(s), the
+// g (and scale) rings, the tail and (kModeTopKShared) the ranked lists, at
+// most 6 whole tiles (one k block per row), 4 (two) or 5 single k blocks
+// (four: 1.25 partner tiles in flight).
+constexpr int stages_for(int KB, int MODE, int fmt) {
+  const int fixed = smem_bytes(KB, fmt, 0) + (MODE == kModeTopKShared ? kTopKListBytes : 0);
+  const int fit = (kSmemLimit - fixed) / (kbs_for(KB) * kPartnerBytesPerKB);
+  const int cap = KB == 1 ? 6 : (KB == 2 ? 4 : 5);
+  return fit < cap ? fit : cap;
+}
 
-template <int KB, int MODE>
-constexpr int kSmemTotal = smem_bytes<KB>(kStages<KB, MODE>) + (MODE == kModeTopKShared ? kTopKListBytes : 0);
+template <int KB, int MODE, int FMT>
+constexpr int kStages = stages_for(KB, MODE, FMT);
 
-template <int KB, int MODE, bool BATCH, bool F8 = false, bool SMALL = false>
+template <int KB, int MODE, int FMT>
+constexpr int kSmemTotal =
+    smem_bytes(KB, FMT, kStages<KB, MODE, FMT>) + (MODE == kModeTopKShared ? kTopKListBytes : 0);
+
+// Instantiations that exist: batched launches take one or two k blocks
+// (e4m3: one); the shared-memory ranked lists leave too little room for
+// partner stages beside a four-block own tile (those lists use kModeTopK).
+template <int KB, int MODE, bool BATCH, int FMT>
+constexpr bool kBuilt = !(BATCH && (KB == 4 || (FMT != kFmtBF16 && KB != 1))) && !(MODE == kModeTopKShared && KB == 4);
+
+template <int KB, int MODE, bool BATCH, int FMT = kFmtBF16, bool SMALL = false>
 cudaError_t launch_kernel(const CUtensorMap& own, const CUtensorMap& partner, const FusedParams& p, int grid,
                           cudaStream_t stream) {
-  static_assert(kSmemTotal<KB, MODE> <= 232448, "shared memory budget");
-  k_fused_halfsweep<KB, kStages<KB, MODE>, MODE, BATCH, F8, SMALL>
-      <<<grid, kThreads, kSmemTotal<KB, MODE>, stream>>>(own, partner, p);
-  return cudaGetLastError();
+  if constexpr (!kBuilt<KB, MODE, BATCH, FMT>) {
+    return cudaErrorNotSupported;
+  } else {
+    static_assert(kStages<KB, MODE, FMT> >= 2, "at least two partner stages");
+    static_assert(kSmemTotal<KB, MODE, FMT> <= kSmemLimit, "shared memory budget");
+    k_fused_halfsweep<KB, kStages<KB, MODE, FMT>, MODE, BATCH, FMT, SMALL>
+        <<<grid, kThreads, kSmemTotal<KB, MODE, FMT>, stream>>>(own, partner, p);
+    return cudaGetLastError();
+  }
+}
+
+template <int KB, int MODE, bool BATCH, int FMT, bool SMALL>
+cudaError_t set_attribute_one() {
+  if constexpr (!kBuilt<KB, MODE, BATCH, FMT>) {
+    return cudaSuccess;
+  } else {
+    return cudaFuncSetAttribute(k_fused_halfsweep<KB, kStages<KB, MODE, FMT>, MODE, BATCH, FMT, SMALL>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal<KB, MODE, FMT>);
+  }
+}
+
+template <int MODE, bool BATCH, bool SMALL, int FMT>
+cudaError_t set_attributes_fmt() {
+  cudaError_t e = set_attribute_one<1, MODE, BATCH, FMT, SMALL>();
+  if (e == cudaSuccess) e = set_attribute_one<2, MODE, BATCH, FMT, SMALL>();
+  if (e == cudaSuccess) e = set_attribute_one<4, MODE, BATCH, FMT, SMALL>();
+  return e;
 }
 
 template <int MODE, bool BATCH, bool SMALL>
 cudaError_t set_attributes_variant() {
-  cudaError_t e = cudaFuncSetAttribute(k_fused_halfsweep<1, kStages<1, MODE>, MODE, BATCH, false, SMALL>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal<1, MODE>);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_fused_halfsweep<1, kStages<1, MODE>, MODE, BATCH, true, SMALL>,
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal<1, MODE>);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_fused_halfsweep<2, kStages<2, MODE>, MODE, BATCH, false, SMALL>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal<2, MODE>);
+  cudaError_t e = set_attributes_fmt<MODE, BATCH, SMALL, kFmtBF16>();
+  if (e == cudaSuccess) e = set_attributes_fmt<MODE, BATCH, SMALL, kFmtE4M3Side>();
+  if (e == cudaSuccess) e = set_attributes_fmt<MODE, BATCH, SMALL, kFmtE4M3Rows>();
+  return e;
 }
 
 template <int MODE, bool BATCH>
@@ -1023,28 +1171,40 @@ cudaError_t set_kernel_attributes() {
   return e;
 }
 
-// kp: packed width in elements (bf16: 64 or 128; e4m3: 128, one 128-byte block).
-template <int MODE, bool BATCH = false, bool SMALL = false>
-cudaError_t launch_variant(int64_t kp, bool fp8, const CUtensorMap& own, const CUtensorMap& partner,
-                           const FusedParams& p, int grid, cudaStream_t stream) {
-  if (fp8) {
-    if (kp != 128) return cudaErrorNotSupported;
-    return launch_kernel<1, MODE, BATCH, true, SMALL>(own, partner, p, grid, stream);
-  }
-  const int kb = (int)(kp / kKBlock);
-  if (kb == 1) return launch_kernel<1, MODE, BATCH, false, SMALL>(own, partner, p, grid, stream);
-  if (kb == 2) return launch_kernel<2, MODE, BATCH, false, SMALL>(own, partner, p, grid, stream);
+// 128-byte k blocks of a packed row: kp elements of 2 bytes (BF16) or 1 (e4m3).
+int k_blocks(int64_t kp, int fmt) { return (int)(fmt != kFmtBF16 ? kp / 128 : kp / kKBlock); }
+
+// The operand format of a market's dtype.
+int fmt_of(int dtype) {
+  return dtype == TU_DTYPE_FP8E4M3 ? kFmtE4M3Rows : (dtype == TU_DTYPE_FP8E4M3_SIDE ? kFmtE4M3Side : kFmtBF16);
+}
+
+template <int MODE, bool BATCH, bool SMALL, int FMT>
+cudaError_t launch_fmt(int kb, const CUtensorMap& own, const CUtensorMap& partner, const FusedParams& p, int grid,
+                       cudaStream_t stream) {
+  if (kb == 1) return launch_kernel<1, MODE, BATCH, FMT, SMALL>(own, partner, p, grid, stream);
+  if (kb == 2) return launch_kernel<2, MODE, BATCH, FMT, SMALL>(own, partner, p, grid, stream);
+  if (kb == 4) return launch_kernel<4, MODE, BATCH, FMT, SMALL>(own, partner, p, grid, stream);
   return cudaErrorNotSupported;
+}
+
+template <int MODE, bool BATCH = false, bool SMALL = false>
+cudaError_t launch_variant(int64_t kp, int fmt, const CUtensorMap& own, const CUtensorMap& partner,
+                           const FusedParams& p, int grid, cudaStream_t stream) {
+  const int kb = k_blocks(kp, fmt);
+  if (fmt == kFmtE4M3Rows) return launch_fmt<MODE, BATCH, SMALL, kFmtE4M3Rows>(kb, own, partner, p, grid, stream);
+  if (fmt == kFmtE4M3Side) return launch_fmt<MODE, BATCH, SMALL, kFmtE4M3Side>(kb, own, partner, p, grid, stream);
+  return launch_fmt<MODE, BATCH, SMALL, kFmtBF16>(kb, own, partner, p, grid, stream);
 }
 
 // small: 128-row own tiles (single-market launches only; see use_small_tiles)
 template <int MODE, bool BATCH = false>
-cudaError_t launch_any(int64_t kp, bool fp8, const CUtensorMap& own, const CUtensorMap& partner,
+cudaError_t launch_any(int64_t kp, int fmt, const CUtensorMap& own, const CUtensorMap& partner,
                        const FusedParams& p, int grid, cudaStream_t stream, bool small = false) {
   if constexpr (!BATCH) {
-    if (small) return launch_variant<MODE, false, true>(kp, fp8, own, partner, p, grid, stream);
+    if (small) return launch_variant<MODE, false, true>(kp, fmt, own, partner, p, grid, stream);
   }
-  return launch_variant<MODE, BATCH, false>(kp, fp8, own, partner, p, grid, stream);
+  return launch_variant<MODE, BATCH, false>(kp, fmt, own, partner, p, grid, stream);
 }
 
 // 128-row own tiles when they all fit one wave (and the market allows them):
@@ -1081,7 +1241,7 @@ int grid_for_tiles(int tiles, int num_sms) {
 }  // namespace
 
 cudaError_t fused_prepare(tu_market* m) {
-  const bool f8 = m->dtype == TU_DTYPE_FP8E4M3;
+  const bool f8 = is_fp8(m->dtype);
   const void* x = f8 ? (const void*)m->X.fac8 : (const void*)m->X.fac16;
   const void* y = f8 ? (const void*)m->Y.fac8 : (const void*)m->Y.fac16;
   cudaError_t e;
@@ -1116,17 +1276,19 @@ cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int upd
   p.residual = residual;
   p.update = update;
   p.omega = m->omega_dev;
+  p.fs_own = own.fs;
+  p.fs_par = partner.fs;
   const int grid = grid_for_tiles(p.num_own_tiles, m->num_sms);
   *nparts_out = grid;
-  const bool f8 = m->dtype == TU_DTYPE_FP8E4M3;
+  const int fmt = fmt_of(m->dtype);
   if (m->wide) {
     // two passes: every own row's largest exponent, then the half-sweep with it subtracted
     p.rowmax = m->rowmax;
-    cudaError_t e = launch_any<kModeRowMax>(m->kp, f8, own.tm_own, partner.tm_partner, p, grid, m->stream, small);
+    cudaError_t e = launch_any<kModeRowMax>(m->kp, fmt, own.tm_own, partner.tm_partner, p, grid, m->stream, small);
     if (e != cudaSuccess) return e;
-    return launch_any<kModeSweepShift>(m->kp, f8, own.tm_own, partner.tm_partner, p, grid, m->stream, small);
+    return launch_any<kModeSweepShift>(m->kp, fmt, own.tm_own, partner.tm_partner, p, grid, m->stream, small);
   }
-  return launch_any<kModeSweep>(m->kp, f8, own.tm_own, partner.tm_partner, p, grid, m->stream, small);
+  return launch_any<kModeSweep>(m->kp, fmt, own.tm_own, partner.tm_partner, p, grid, m->stream, small);
 }
 
 // Ranked lists of own users [row0, row0 + nrows) over all partners (the
@@ -1148,11 +1310,13 @@ cudaError_t launch_fused_topk(tu_market* m, int side, int k, int64_t row0, int64
   p.logmu = logmu;
   p.hand_v = hand_v;
   p.hand_i = hand_i;
+  p.fs_own = own.fs;
+  p.fs_par = partner.fs;
   const int grid = grid_for_tiles(p.num_own_tiles, m->num_sms);
-  const bool f8 = m->dtype == TU_DTYPE_FP8E4M3;
-  if (k <= kSharedTopK)
-    return launch_any<kModeTopKShared>(m->kp, f8, own.tm_own, partner.tm_partner, p, grid, m->stream, small);
-  return launch_any<kModeTopK>(m->kp, f8, own.tm_own, partner.tm_partner, p, grid, m->stream, small);
+  const int fmt = fmt_of(m->dtype);
+  if (k <= kSharedTopK && k_blocks(m->kp, fmt) < 4)
+    return launch_any<kModeTopKShared>(m->kp, fmt, own.tm_own, partner.tm_partner, p, grid, m->stream, small);
+  return launch_any<kModeTopK>(m->kp, fmt, own.tm_own, partner.tm_partner, p, grid, m->stream, small);
 }
 
 // mu for own X users [x0, x0 + nx) and partners [y0, y0 + ny) (the Y partner
@@ -1170,7 +1334,9 @@ cudaError_t launch_fused_mu(tu_market* m, int64_t x0, int64_t nx, int64_t y0, in
   p.ld = ld;
   p.y0 = y0;
   p.ny = ny;
-  return launch_any<kModeMu>(m->kp, m->dtype == TU_DTYPE_FP8E4M3, m->X.tm_own, m->Y.tm_partner, p,
+  p.fs_own = m->X.fs;
+  p.fs_par = m->Y.fs;
+  return launch_any<kModeMu>(m->kp, fmt_of(m->dtype), m->X.tm_own, m->Y.tm_partner, p,
                              grid_for_tiles(p.num_own_tiles, m->num_sms), m->stream, small);
 }
 
@@ -1195,7 +1361,7 @@ cudaError_t launch_fused_halfsweep_raw(const FusedRaw& r, cudaStream_t stream, i
   p.update = 1;
   const int grid = grid_for_tiles(p.num_own_tiles, num_sms);
   *nparts_out = grid;
-  return launch_any<kModeSweep>(r.kp, false, own_map, partner_map, p, grid, stream);
+  return launch_any<kModeSweep>(r.kp, kFmtBF16, own_map, partner_map, p, grid, stream);
 }
 
 // One half-sweep over the items of many markets (batched launch). The
@@ -1214,7 +1380,7 @@ cudaError_t launch_fused_batch(const BatchLaunch& b, cudaStream_t stream) {
   p.update = b.update;
   CUtensorMap unused;
   memset(&unused, 0, sizeof(unused));
-  return launch_any<kModeSweep, true>(b.kp, b.fp8 != 0, unused, unused, p, b.grid, stream);
+  return launch_any<kModeSweep, true>(b.kp, fmt_of(b.dtype), unused, unused, p, b.grid, stream);
 }
 
 }  // namespace tu

@@ -25,6 +25,14 @@ const char* kStatusNames[] = {"TU_OK",          "TU_ERR_INVALID_ARG", "TU_ERR_OO
 
 int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
+// Packed row length of the fused path: 2d elements rounded up to one, two or
+// four 128-byte k blocks (BF16: 64, 128 or 256 elements; e4m3: 128, 256 or 512).
+int64_t fused_row_length(int64_t d, bool fp8) {
+  int64_t kp = fp8 ? 128 : kKBlock;
+  while (kp < 2 * d) kp *= 2;
+  return kp;
+}
+
 tu_status fail(tu_market* m, tu_status s, const std::string& msg) {
   if (m != nullptr) m->last_error = msg;
   return s;
@@ -273,8 +281,9 @@ tu_status side_alloc(tu_market* m, Side& s, int64_t rows, bool has_bias) {
   // to kMaxPartials CTAs) needs at most rows / 32 + 2 * kMaxPartials of them
   TU_TRY(dev_alloc(m, &s.grp, (size_t)(s.rows_pad / kGroupRows + 2 * kMaxPartials)));
   if (has_bias) TU_TRY(dev_alloc(m, &s.b2s, s.rows_pad));
-  if (m->path == TU_PATH_FUSED && m->dtype == TU_DTYPE_FP8E4M3) {
-    TU_TRY(dev_alloc(m, &s.fac8, (size_t)rows * 128));
+  if (m->path == TU_PATH_FUSED && is_fp8(m->dtype)) {
+    TU_TRY(dev_alloc(m, &s.fac8, (size_t)rows * m->kp));
+    TU_TRY(dev_alloc(m, &s.fs, s.rows_pad));
   } else if (m->path == TU_PATH_FUSED) {
     TU_TRY(dev_alloc(m, &s.fac16, (size_t)rows * m->kp));
   } else {
@@ -292,6 +301,7 @@ void side_free(tu_market* m, Side& s) {
   dev_free(m, s.b2s);
   dev_free(m, s.fac16);
   dev_free(m, s.fac8);
+  dev_free(m, s.fs);
   dev_free(m, s.fac32);
   s = Side();
 }
@@ -319,8 +329,8 @@ tu_status upload_masses(tu_market* m, Side& s, const double* host) {
   return TU_OK;
 }
 
-// FP8: smallest integer k with maxabs <= 448 * 2^k (exact comparisons with
-// powers of two; 0 for an all-zero side).
+// FP8 with one scale per side: smallest integer k with maxabs <= 448 * 2^k
+// (exact comparisons with powers of two; 0 for an all-zero side).
 int fp8_side_exponent(float maxabs) {
   if (!(maxabs > 0.0f)) return 0;
   int e = 0;
@@ -331,44 +341,72 @@ int fp8_side_exponent(float maxabs) {
   return k;
 }
 
-// FP8: quantize one side's FP32 factor pair (device pointers) into s.fac8.
-tu_status pack_side_fp8(tu_market* m, Side& s, const void* a, const void* b, float* scratch) {
-  float mx = 0.0f;
-  TU_CK(m, launch_max_abs(m, static_cast<const float*>(a), static_cast<const float*>(b), s.rows * m->d, scratch));
-  TU_CK(m, cudaMemcpyAsync(&mx, scratch, sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+// FP8: quantize one side's factor pair (device pointers) into s.fac8 and its
+// row scales s.fs: from FP32 rows (each row scaled by its own power of two,
+// or TU_DTYPE_FP8E4M3_SIDE: all by the side's), or, with caller scales sc,
+// from e4m3 bytes the caller quantized.
+tu_status pack_side_fp8(tu_market* m, Side& s, const void* a, const void* b, const float* sc, unsigned int* bad) {
+  unsigned int hbad = 0;
+  TU_CK(m, cudaMemsetAsync(bad, 0, sizeof(unsigned int), m->stream));
+  if (sc != nullptr) {
+    TU_CK(m, launch_pack_fp8_bytes(m, s, static_cast<const uint8_t*>(a), static_cast<const uint8_t*>(b), sc, bad));
+  } else {
+    int side_k = kPerRowScale;
+    if (m->dtype == TU_DTYPE_FP8E4M3_SIDE) {
+      float mx = 0.0f;
+      float* scratch = reinterpret_cast<float*>(bad + 1);
+      TU_CK(m, launch_max_abs(m, static_cast<const float*>(a), static_cast<const float*>(b), s.rows * m->d, scratch));
+      TU_CK(m, cudaMemcpyAsync(&mx, scratch, sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+      TU_CK(m, cudaStreamSynchronize(m->stream));
+      if (!std::isfinite(mx)) return fail(m, TU_ERR_NONFINITE, "factor matrices contain NaN or Inf");
+      side_k = s.fp8_exp = fp8_side_exponent(mx);
+    }
+    TU_CK(m, launch_pack_fp8_rows(m, s, static_cast<const float*>(a), static_cast<const float*>(b), side_k, bad));
+  }
+  TU_CK(m, cudaMemcpyAsync(&hbad, bad, sizeof(hbad), cudaMemcpyDeviceToHost, m->stream));
   TU_CK(m, cudaStreamSynchronize(m->stream));
-  if (!std::isfinite(mx)) return fail(m, TU_ERR_NONFINITE, "factor matrices contain NaN or Inf");
-  s.fp8_exp = fp8_side_exponent(mx);
-  TU_CK(m, launch_pack_fp8(m, s, static_cast<const float*>(a), static_cast<const float*>(b), s.fp8_exp));
+  if (hbad != 0)
+    return fail(m, TU_ERR_NONFINITE, sc ? "FP8 row scales contain NaN or Inf" : "factor matrices contain NaN or Inf");
   return TU_OK;
 }
 
 // Pack both factor pairs (and rebuild the dense kernel) from caller pointers.
-tu_status load_factors(tu_market* m, const void* F, const void* K, const void* G, const void* L) {
-  const bool fp8 = m->dtype == TU_DTYPE_FP8E4M3;
-  const size_t esz = m->dtype == TU_DTYPE_BF16 ? 2 : 4;
+// fsx, fsy: FP8 markets created with caller scales: the per-row scales of the
+// e4m3 bytes F, K (resp. G, L), host or device; otherwise nullptr.
+tu_status load_factors(tu_market* m, const void* F, const void* K, const void* G, const void* L,
+                       const float* fsx = nullptr, const float* fsy = nullptr) {
+  const bool fp8 = is_fp8(m->dtype);
+  const bool prescaled = fp8 && m->fp8_caller_scales;
+  const size_t esz = prescaled ? 1 : (m->dtype == TU_DTYPE_BF16 ? 2 : 4);
   const size_t bx = (size_t)m->N * m->d * esz, by = (size_t)m->M * m->d * esz;
-  TU_TRY(ensure_staging(m, 2 * (bx > by ? bx : by)));
-  float* fscratch = nullptr;
-  if (fp8) TU_TRY(dev_alloc(m, &fscratch, 1));
-  auto pack = [&](Side& s, const void* a, const void* b) -> tu_status {
-    if (fp8) return pack_side_fp8(m, s, a, b, fscratch);
+  // (caller scales follow the two factor matrices in the staging buffer)
+  const size_t sx = prescaled ? round_up((int64_t)(2 * bx), 256) : 0, sy = prescaled ? round_up((int64_t)(2 * by), 256) : 0;
+  const size_t stage = 2 * (bx > by ? bx : by) + (prescaled ? 256 + 4 * (size_t)(m->N > m->M ? m->N : m->M) : 0);
+  TU_TRY(ensure_staging(m, stage));
+  unsigned int* bad = nullptr;  // [0]: the pack kernels' flag, [1]: a float scratch
+  if (fp8) TU_TRY(dev_alloc(m, &bad, 2));
+  auto pack = [&](Side& s, const void* a, const void* b, const float* sc) -> tu_status {
+    if (fp8) return pack_side_fp8(m, s, a, b, sc, bad);
     TU_CK(m, launch_pack_factors(m, s, a, b, m->dtype));
     return TU_OK;
   };
-  const void *a = nullptr, *b = nullptr;
+  const void *a = nullptr, *b = nullptr, *sc = nullptr;
   tu_status st = device_view(m, F, bx, 0, &a);
   if (st == TU_OK) st = device_view(m, K, bx, bx, &b);
-  if (st == TU_OK) st = pack(m->X, a, b);
+  if (st == TU_OK && prescaled) st = device_view(m, fsx, (size_t)m->N * 4, sx, &sc);
+  if (st == TU_OK) st = pack(m->X, a, b, static_cast<const float*>(sc));
   if (st == TU_OK && cudaStreamSynchronize(m->stream) != cudaSuccess)  // the staging buffer is reused
     st = fail_cuda(m, cudaGetLastError(), "cudaStreamSynchronize");
   if (st == TU_OK) st = device_view(m, G, by, 0, &a);
   if (st == TU_OK) st = device_view(m, L, by, by, &b);
-  if (st == TU_OK) st = pack(m->Y, a, b);
-  dev_free(m, fscratch);
+  if (st == TU_OK && prescaled) st = device_view(m, fsy, (size_t)m->M * 4, sy, &sc);
+  if (st == TU_OK) st = pack(m->Y, a, b, static_cast<const float*>(sc));
+  dev_free(m, bad);
   if (st != TU_OK) return st;
-  // the multiplier of <a_x, b_y> in the exponent (log2 units)
-  m->cmul = (float)std::ldexp(1.4426950408889634 / (2.0 * m->sigma), fp8 ? m->X.fp8_exp + m->Y.fp8_exp : 0);
+  // the multiplier of <a_x, b_y> in the exponent (log2 units; FP8 with per-row
+  // scales: those are applied in the kernels; with one scale per side: folded in)
+  m->cmul = (float)std::ldexp(1.4426950408889634 / (2.0 * m->sigma),
+                              m->dtype == TU_DTYPE_FP8E4M3_SIDE ? m->X.fp8_exp + m->Y.fp8_exp : 0);
   // exponent-range check (Cauchy-Schwarz bound of |phi_hat| / (2 sigma))
   float* norms = nullptr;
   TU_TRY(dev_alloc(m, &norms, 2));
@@ -716,13 +754,18 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
   const tu_market_desc& D = *desc;
   if (D.N < 1 || D.M < 1 || D.d < 1 || D.N > (int64_t)1 << 31 || D.M > (int64_t)1 << 31 || D.d > 4096)
     return TU_ERR_INVALID_ARG;
-  if (D.dtype != TU_DTYPE_BF16 && D.dtype != TU_DTYPE_FP32 && D.dtype != TU_DTYPE_FP8E4M3) return TU_ERR_INVALID_ARG;
+  if (D.dtype != TU_DTYPE_BF16 && D.dtype != TU_DTYPE_FP32 && !is_fp8(D.dtype)) return TU_ERR_INVALID_ARG;
   if (D.path != TU_PATH_FUSED && D.path != TU_PATH_DENSE) return TU_ERR_INVALID_ARG;
   if (!D.F || !D.K || !D.G || !D.L || !D.n || !D.m) return TU_ERR_INVALID_ARG;
   if (!(D.sigma > 0.0) || !std::isfinite(D.sigma)) return TU_ERR_INVALID_ARG;
   if (D.partition < 0) return TU_ERR_INVALID_ARG;
-  if (D.path == TU_PATH_FUSED && 2 * D.d > 2 * kKBlock) return TU_ERR_UNSUPPORTED;
-  if (D.dtype == TU_DTYPE_FP8E4M3 && D.path != TU_PATH_FUSED) return TU_ERR_UNSUPPORTED;
+  // caller-quantized FP8: both sides' scales, e4m3 factors only
+  if ((D.fscale_x != nullptr) != (D.fscale_y != nullptr)) return TU_ERR_INVALID_ARG;
+  if (D.fscale_x != nullptr && D.dtype != TU_DTYPE_FP8E4M3) return TU_ERR_INVALID_ARG;
+  // fused path: packed rows of 1, 2 or 4 128-byte k blocks
+  if (D.path == TU_PATH_FUSED && !is_fp8(D.dtype) && D.d > 128) return TU_ERR_UNSUPPORTED;
+  if (is_fp8(D.dtype) && D.d > 256) return TU_ERR_UNSUPPORTED;
+  if (is_fp8(D.dtype) && D.path != TU_PATH_FUSED) return TU_ERR_UNSUPPORTED;
   // the dense path keeps A-hat and its transpose resident
   if (D.path == TU_PATH_DENSE &&
       (double)D.N * (double)round_up(D.M, 4) * 4.0 + (double)D.M * (double)round_up(D.N, 4) * 4.0 > 200e9)
@@ -733,7 +776,8 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
   m->N = D.N;
   m->M = D.M;
   m->d = D.d;
-  m->kp = D.dtype == TU_DTYPE_FP8E4M3 ? 128 : round_up(2 * D.d, kKBlock);
+  m->kp = D.path == TU_PATH_FUSED ? fused_row_length(D.d, is_fp8(D.dtype)) : round_up(2 * D.d, kKBlock);
+  m->fp8_caller_scales = D.fscale_x != nullptr;
   m->dtype = D.dtype;
   m->path = D.path;
   m->sigma = D.sigma;
@@ -826,7 +870,7 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
     dev_free(m, bmax);
     if (st != TU_OK) return bail(st);
   }
-  if ((st = load_factors(m, D.F, D.K, D.G, D.L)) != TU_OK) {
+  if ((st = load_factors(m, D.F, D.K, D.G, D.L, D.fscale_x, D.fscale_y)) != TU_OK) {
     // keep the message for the caller by returning it through a status only
     return bail(st);
   }
@@ -846,7 +890,18 @@ tu_status tu_market_update_factors(tu_market_t m, const void* F, const void* K, 
   TU_TRACE("tu_market_update_factors");
   TU_TRY(check_live(m));
   if (!F || !K || !G || !L) return fail(m, TU_ERR_INVALID_ARG, "null factor pointer");
+  if (m->fp8_caller_scales) return fail(m, TU_ERR_INVALID_ARG, "caller-scaled FP8 market: use the scaled update");
   TU_TRY(load_factors(m, F, K, G, L));
+  return relax_reset(m);
+}
+
+tu_status tu_market_update_factors_fp8(tu_market_t m, const void* F, const void* K, const void* G, const void* L,
+                                       const float* fscale_x, const float* fscale_y) {
+  TU_TRACE("tu_market_update_factors_fp8");
+  TU_TRY(check_live(m));
+  if (!F || !K || !G || !L || !fscale_x || !fscale_y) return fail(m, TU_ERR_INVALID_ARG, "null pointer");
+  if (!m->fp8_caller_scales) return fail(m, TU_ERR_INVALID_ARG, "not a caller-scaled FP8 market");
+  TU_TRY(load_factors(m, F, K, G, L, fscale_x, fscale_y));
   return relax_reset(m);
 }
 
@@ -977,7 +1032,7 @@ tu_status tu_market_query(tu_market_t m, int* idle, double* residual, double* ma
 
 int64_t tu_market_footprint(int64_t N, int64_t M, int64_t d, int path) {
   if (N < 1 || M < 1 || d < 1) return 0;
-  const int64_t kp = round_up(2 * d, kKBlock);
+  const int64_t kp = path == TU_PATH_FUSED ? fused_row_length(d, false) : round_up(2 * d, kKBlock);
   const int64_t np = round_up(N, kRowPad), mp = round_up(M, kRowPad);
   int64_t bytes = (np + mp) * (8 + 8 + 4 + 8 + 4) + (int64_t)kMaxPartials * 5 * 8 + 4096;
   // staging for host factor uploads (two matrices of the larger side)

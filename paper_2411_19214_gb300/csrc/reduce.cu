@@ -64,21 +64,82 @@ __global__ void k_max_abs(const float* __restrict__ A, const float* __restrict__
   }
 }
 
-// FP8 packing: row r of the output is [A_r | B_r | 0] * 2^-k rounded to the
-// nearest e4m3 value (ties to even), saturating at +-448; 128 bytes per row.
-__global__ void k_pack_fp8(const float* __restrict__ A, const float* __restrict__ B, int64_t rows, int64_t d,
-                           float scale, uint8_t* __restrict__ out) {
-  const int64_t total = rows * 128;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i / 128;
-    const int64_t k = i - r * 128;
-    float v = 0.0f;
+// FP8 packing with per-row scales (one warp per row): row r of the output is
+// [A_r | B_r | 0] * 2^-k_r rounded to the nearest e4m3 value (ties to even,
+// saturating at +-448), kp bytes, with k_r the smallest integer such that
+// max_i |entry| <= 448 * 2^k_r (exact: 448 = 0.875 * 2^9 and frexpf is exact),
+// and fs[r] = 2^k_r the scale that multiplies the row back; an all-zero row
+// has k_r = 0. With side_k != kPerRowScale every row takes k_r = side_k (one
+// scale per side). Rows [rows, rows_pad) get fs = 1. A NaN or infinite entry
+// sets *bad.
+__global__ void k_pack_fp8_rows(const float* __restrict__ A, const float* __restrict__ B, int64_t rows,
+                                int64_t rows_pad, int64_t d, int64_t kp, int side_k, uint8_t* __restrict__ out,
+                                float* __restrict__ fs, unsigned int* __restrict__ bad) {
+  const int lane = threadIdx.x % 32;
+  const int64_t wpb = blockDim.x / 32;
+  for (int64_t r = blockIdx.x * wpb + threadIdx.x / 32; r < rows_pad; r += (int64_t)gridDim.x * wpb) {
+    if (r >= rows) {
+      if (lane == 0) fs[r] = 1.0f;
+      continue;
+    }
+    float mx = 0.0f;
+    bool nonfinite = false;
+    for (int64_t i = lane; i < 2 * d; i += 32) {
+      const float v = i < d ? A[r * d + i] : B[r * d + (i - d)];
+      nonfinite |= !isfinite(v);
+      mx = fmaxf(mx, fabsf(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (__any_sync(0xffffffffu, nonfinite)) {
+      if (lane == 0) atomicOr(bad, 1u);
+      continue;
+    }
+    int k = side_k;
+    if (side_k == kPerRowScale && mx > 0.0f) {
+      int e = 0;
+      frexpf(mx, &e);
+      k = mx <= ldexpf(448.0f, e - 9) ? e - 9 : e - 8;
+      if (k < -100) k = -100;  // (rows of subnormal size: 2^100 keeps the scaled entries finite)
+    } else if (side_k == kPerRowScale) {
+      k = 0;
+    }
+    const float inv = ldexpf(1.0f, -k);
+    if (lane == 0) fs[r] = ldexpf(1.0f, k);
+    for (int64_t i = lane; i < kp; i += 32) {
+      float v = 0.0f;
+      if (i < d) {
+        v = A[r * d + i];
+      } else if (i < 2 * d) {
+        v = B[r * d + (i - d)];
+      }
+      out[r * kp + i] = (uint8_t)__nv_cvt_float_to_fp8(v * inv, __NV_SATFINITE, __NV_E4M3);
+    }
+  }
+}
+
+// FP8 packing of caller-quantized rows: [A_r | B_r | 0] copied as bytes (kp
+// per row), fs[r] = sc[r]; rows [rows, rows_pad) get fs = 1. A non-finite
+// scale sets *bad.
+__global__ void k_pack_fp8_bytes(const uint8_t* __restrict__ A, const uint8_t* __restrict__ B,
+                                 const float* __restrict__ sc, int64_t rows, int64_t rows_pad, int64_t d, int64_t kp,
+                                 uint8_t* __restrict__ out, float* __restrict__ fs, unsigned int* __restrict__ bad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows * kp;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / kp;
+    const int64_t k = i - r * kp;
+    uint8_t v = 0;
     if (k < d) {
       v = A[r * d + k];
     } else if (k < 2 * d) {
       v = B[r * d + (k - d)];
     }
-    out[i] = (uint8_t)__nv_cvt_float_to_fp8(v * scale, __NV_SATFINITE, __NV_E4M3);
+    out[i] = v;
+  }
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows_pad;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    const float v = r < rows ? sc[r] : 1.0f;
+    if (!isfinite(v)) atomicOr(bad, 1u);
+    fs[r] = v;
   }
 }
 
@@ -122,8 +183,8 @@ __global__ void k_get_potentials(const double* __restrict__ log_u, int64_t rows,
 }
 
 __global__ void k_row_norm_max(const float* __restrict__ f32, const __nv_bfloat16* __restrict__ f16,
-                               const uint8_t* __restrict__ f8, float f8scale, int64_t rows, int64_t kp,
-                               unsigned int* __restrict__ out) {
+                               const uint8_t* __restrict__ f8, const float* __restrict__ fs, int64_t rows,
+                               int64_t kp, unsigned int* __restrict__ out) {
   __shared__ float red[kThreads / 32];
   float best = 0.0f;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -134,7 +195,7 @@ __global__ void k_row_norm_max(const float* __restrict__ f32, const __nv_bfloat1
       float v;
       if (f8 != nullptr) {
         const __half_raw h = __nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)f8[r * kp + k], __NV_E4M3);
-        v = __half2float(__half(h)) * f8scale;
+        v = __half2float(__half(h)) * fs[r];
       } else {
         v = f32 ? f32[r * kp + k] : __bfloat162float(f16[r * kp + k]);
       }
@@ -356,8 +417,8 @@ cudaError_t launch_row_norms(tu_market* m, Side& s, float* out_max) {
   if (e != cudaSuccess) return e;
   int64_t blocks = (s.rows + (kThreads / 32) - 1) / (kThreads / 32);
   if (blocks > (int64_t)m->num_sms * 8) blocks = (int64_t)m->num_sms * 8;
-  k_row_norm_max<<<(int)blocks, kThreads, 0, m->stream>>>(s.fac32, s.fac16, s.fac8, ldexpf(1.0f, s.fp8_exp), s.rows,
-                                                          m->kp, reinterpret_cast<unsigned int*>(out_max));
+  k_row_norm_max<<<(int)blocks, kThreads, 0, m->stream>>>(s.fac32, s.fac16, s.fac8, s.fs, s.rows, m->kp,
+                                                          reinterpret_cast<unsigned int*>(out_max));
   return cudaGetLastError();
 }
 
@@ -369,9 +430,17 @@ cudaError_t launch_max_abs(tu_market* m, const float* A, const float* B, int64_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_pack_fp8(tu_market* m, Side& s, const float* A, const float* B, int k) {
-  const int g = grid_for(s.rows * 128, m->num_sms, 16);
-  k_pack_fp8<<<g, kThreads, 0, m->stream>>>(A, B, s.rows, m->d, ldexpf(1.0f, -k), s.fac8);
+cudaError_t launch_pack_fp8_rows(tu_market* m, Side& s, const float* A, const float* B, int side_k,
+                                 unsigned int* bad) {
+  const int g = grid_for(s.rows_pad * 32, m->num_sms, 8);  // one warp per row
+  k_pack_fp8_rows<<<g, kThreads, 0, m->stream>>>(A, B, s.rows, s.rows_pad, m->d, m->kp, side_k, s.fac8, s.fs, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_fp8_bytes(tu_market* m, Side& s, const uint8_t* A, const uint8_t* B, const float* sc,
+                                  unsigned int* bad) {
+  const int g = grid_for(s.rows * m->kp, m->num_sms, 16);
+  k_pack_fp8_bytes<<<g, kThreads, 0, m->stream>>>(A, B, sc, s.rows, s.rows_pad, m->d, m->kp, s.fac8, s.fs, bad);
   return cudaGetLastError();
 }
 

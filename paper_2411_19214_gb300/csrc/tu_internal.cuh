@@ -74,8 +74,9 @@ struct Side {
   float4* grp = nullptr;    // per-32-row groups {max 2 log u, scaled sum, max ell, 0}, rows_pad / 32 + 2 kMaxPartials
   double sum_mass = 0.0;    // host copy of sum of capacities
   __nv_bfloat16* fac16 = nullptr;  // packed [F | K] (or [G | L]) rows x kp, bf16, zero padded
-  uint8_t* fac8 = nullptr;         // FP8 markets: packed rows x 128 e4m3 of [F | K] * 2^-fp8_exp
-  int fp8_exp = 0;                 // FP8 markets: this side's power-of-two scale k
+  uint8_t* fac8 = nullptr;         // FP8 markets: packed rows x kp e4m3 of [F | K] / fs (zero padded)
+  float* fs = nullptr;             // FP8 markets: per-row scales, rows_pad (padding 1)
+  int fp8_exp = 0;                 // FP8 markets with one scale per side: its exponent (fs = 2^fp8_exp)
   float* fac32 = nullptr;          // packed rows x kp, fp32 (dense path), zero padded
   CUtensorMap tm_own;       // TMA map, box kKBlock x kFusedOwnRows
   CUtensorMap tm_partner;   // TMA map, box kKBlock x kFusedPartnerRows
@@ -103,6 +104,9 @@ struct RelaxControl {
   // after `done` sweeps (r > tol). Returns the omega of the next block.
   double observe(int done, double r, double tol);
 };
+
+// e4m3 markets (per-row or per-side scales)
+inline bool is_fp8(int dtype) { return dtype == TU_DTYPE_FP8E4M3 || dtype == TU_DTYPE_FP8E4M3_SIDE; }
 
 // The library's kernels are built for sm_103a only (compute capability 10.3):
 // any other device would fail at the first launch ("no kernel image").
@@ -137,7 +141,9 @@ inline int plan_block(int last_k, double r_prev, double r, double tol, int cap) 
 
 struct tu_market {
   int64_t N = 0, M = 0, d = 0;
-  int64_t kp = 0;           // packed inner dimension: 2d rounded up to a multiple of 64 (FP8: 128)
+  int64_t kp = 0;           // packed row length in elements: fused BF16 64, 128 or 256, FP8 128, 256
+                            // or 512 bytes (fused_row_length); dense FP32 2d rounded up to 64
+  bool fp8_caller_scales = false;  // FP8 created from caller e4m3 bytes and per-row scales
   float cmul = 0.0f;        // fused path: log2(e) / (2 sigma), times 2^(k_X + k_Y) for FP8 markets
   int dtype = 0, path = 0;
   double sigma = 1.0;
@@ -215,7 +221,11 @@ cudaError_t launch_row_norms(tu_market* m, Side& s, float* out_max);
 // FP8 markets: max |entry| of the FP32 factor pair (A, B: rows x d each) into *out_max
 cudaError_t launch_max_abs(tu_market* m, const float* A, const float* B, int64_t count, float* out_max);
 // FP8 markets: pack [A | B | 0] * 2^-k into s.fac8 (rows x 128 e4m3, round to nearest even, saturating)
-cudaError_t launch_pack_fp8(tu_market* m, Side& s, const float* A, const float* B, int k);
+constexpr int kPerRowScale = -1000000;  // launch_pack_fp8_rows: each row its own scale
+cudaError_t launch_pack_fp8_rows(tu_market* m, Side& s, const float* A, const float* B, int side_k,
+                                 unsigned int* bad);
+cudaError_t launch_pack_fp8_bytes(tu_market* m, Side& s, const uint8_t* A, const uint8_t* B, const float* sc,
+                                  unsigned int* bad);
 cudaError_t launch_sum_sq(tu_market* m, Side& s, int is_x);  // results[kResXSq or kResYSq] = sum exp(2 log u)
 
 // dense.cu
@@ -263,6 +273,8 @@ struct BatchDesc {
   const double* partner_ell;   // partner ell (read by the preparation kernel)
   float* g;                    // partner prepared vector (written by the preparation kernel)
   double* st;                  // the market's scalars (kSt*; shift and own offset of the pass)
+  const float* fs_own;         // e4m3 markets: own per-row scales, else nullptr
+  const float* fs_par;         // e4m3 markets: partner per-row scales, else nullptr
   float4* grp;                 // own-side groups (written by the pass, reduced by the finalize)
   const double* omega;         // over-relaxation factor of this market (device scalar)
   double dm_next;              // sum of own capacities - sum of partner capacities (the next step's tau)
@@ -290,8 +302,8 @@ struct BatchLaunch {
   double* partials;        // device, [slot][kBatchSlotWarps][4]
   int* err;
   int grid;
-  int64_t kp;              // 64 or 128, the same for every market
-  int fp8;                 // e4m3 factors (kp = 128 bytes per row), the same for every market
+  int64_t kp;              // 64 or 128 (BF16), the same for every market
+  int dtype;               // the members' dtype (e4m3 markets: kp = 128 bytes per row, the same format)
   int residual;
   int update;
 };

@@ -11,8 +11,11 @@ from .markets import (  # noqa: F401
     make_market,
     round_to_bf16,
     round_to_e4m3,
-    fp8_side_exponent,
+    fp8_exponent,
+    fp8_row_exponents,
     fp8_quantized,
+    fp8_encoded,
+    e4m3_bits,
     bf16_bits,
     dense_job_market,
     fused_market,

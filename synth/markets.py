@@ -139,30 +139,66 @@ def round_to_e4m3(x) -> np.ndarray:
     return np.copysign(r, x)
 
 
-def fp8_side_exponent(A, B) -> int:
-    """Smallest integer k with max |entry| of A and B <= 448 * 2^k (0 if both are zero)."""
-    mx = float(max(np.max(np.abs(A)), np.max(np.abs(B))))
-    if not mx > 0.0:
-        return 0
-    k = math.frexp(mx / E4M3_MAX)[1]
-    while math.ldexp(E4M3_MAX, k - 1) >= mx:
-        k -= 1
-    while math.ldexp(E4M3_MAX, k) < mx:
-        k += 1
-    return k
+def fp8_exponent(mx) -> np.ndarray:
+    """Smallest integer k with mx <= 448 * 2^k, elementwise (0 where mx is 0)."""
+    mx = np.asarray(mx, np.float64)
+    k = np.frexp(np.where(mx > 0.0, mx / E4M3_MAX, 1.0))[1].astype(np.int64)
+    k = np.where(np.ldexp(E4M3_MAX, k - 1) >= mx, k - 1, k)
+    k = np.where(np.ldexp(E4M3_MAX, k) < mx, k + 1, k)
+    return np.where(mx > 0.0, k, 0)
 
 
-def fp8_quantized(mk: "Market"):
-    """The factors an FP8 market computes with: each side's [F | K] (resp.
-    [G | L]) scaled by 2^-k (fp8_side_exponent of that side), rounded to e4m3
-    and scaled back; exact in float32. Returns (market, (k_X, k_Y))."""
-    kx = fp8_side_exponent(mk.F, mk.K)
-    ky = fp8_side_exponent(mk.G, mk.L)
+def fp8_row_exponents(A, B) -> np.ndarray:
+    """Per row r of [A | B]: the smallest integer k_r with max_i |entry| <= 448 * 2^k_r."""
+    mx = np.maximum(np.max(np.abs(np.asarray(A, np.float64)), axis=1), np.max(np.abs(np.asarray(B, np.float64)), axis=1))
+    return fp8_exponent(mx)
+
+
+def fp8_quantized(mk: "Market", per: str = "row"):
+    """The factors an FP8 market computes with: row r of [F | K] (resp. of
+    [G | L]) scaled by 2^-k_r (fp8_row_exponents; per="side": every row by the
+    side's exponent, that of the side's largest |entry|), rounded to e4m3 and
+    scaled back; exact in float32. Returns (market, (k_X, k_Y)) with the
+    per-row exponents."""
+    kx = fp8_row_exponents(mk.F, mk.K)
+    ky = fp8_row_exponents(mk.G, mk.L)
+    if per == "side":
+        kx = np.full_like(kx, fp8_exponent(max(np.abs(mk.F).max(), np.abs(mk.K).max())))
+        ky = np.full_like(ky, fp8_exponent(max(np.abs(mk.G).max(), np.abs(mk.L).max())))
 
     def q(a, k):
-        return (round_to_e4m3(np.asarray(a, np.float64) * 2.0 ** -k) * 2.0 ** k).astype(np.float32)
+        sc = np.ldexp(1.0, k)[:, None]
+        return (round_to_e4m3(np.asarray(a, np.float64) / sc) * sc).astype(np.float32)
 
     return dataclasses.replace(mk, F=q(mk.F, kx), K=q(mk.K, kx), G=q(mk.G, ky), L=q(mk.L, ky), dtype="fp8"), (kx, ky)
+
+
+def e4m3_bits(x) -> np.ndarray:
+    """Bit patterns (uint8) of e4m3 values x (already on the e4m3 grid):
+    sign, 4 exponent bits with bias 7, 3 mantissa bits; exponent field 0 holds
+    the subnormals, multiples of 2^-9."""
+    x = np.asarray(x, np.float64)
+    a = np.abs(x)
+    sub = a < 2.0 ** -6
+    _, ex = np.frexp(np.where(sub, 1.0, a))
+    e = ex - 1
+    field = np.where(sub, 0, e + 7)
+    mant = np.where(sub, a / 2.0 ** -9, (np.where(sub, 1.0, a) / np.ldexp(1.0, e) - 1.0) * 8.0)
+    bits = (np.signbit(x).astype(np.int64) << 7) | (field.astype(np.int64) << 3) | np.rint(mant).astype(np.int64)
+    return bits.astype(np.uint8)
+
+
+def fp8_encoded(mk: "Market"):
+    """The same quantization as fp8_quantized as a caller would hand it over:
+    e4m3 bytes of F, K, G, L (uint8) and per-row FP32 scales 2^k."""
+    kx = fp8_row_exponents(mk.F, mk.K)
+    ky = fp8_row_exponents(mk.G, mk.L)
+
+    def enc(a, k):
+        return e4m3_bits(round_to_e4m3(np.asarray(a, np.float64) / np.ldexp(1.0, k)[:, None]))
+
+    return (enc(mk.F, kx), enc(mk.K, kx), enc(mk.G, ky), enc(mk.L, ky),
+            np.ldexp(1.0, kx).astype(np.float32), np.ldexp(1.0, ky).astype(np.float32))
 
 
 def make_market(N: int, M: int, d: int, *, sigma: float, seed: int,

@@ -72,10 +72,15 @@ def test_invalid_arguments_rejected_before_cuda(lib):
         (dict(N=(1 << 31) + 1, M=4, d=3, dtype=1, path=1), tu.TU_ERR_INVALID_ARG),
         (dict(N=4, M=(1 << 31) + 1, d=3, dtype=1, path=1), tu.TU_ERR_INVALID_ARG),
         (dict(N=4, M=4, d=4097, dtype=1, path=1), tu.TU_ERR_INVALID_ARG),
-        (dict(N=4, M=4, d=3, dtype=3, path=0), tu.TU_ERR_INVALID_ARG),  # unknown dtype
+        (dict(N=4, M=4, d=3, dtype=4, path=0), tu.TU_ERR_INVALID_ARG),  # unknown dtype
+        (dict(N=4, M=4, d=3, dtype=tu.TU_DTYPE_FP8E4M3_SIDE, path=1), tu.TU_ERR_UNSUPPORTED),  # FP8: fused only
+        (dict(N=4, M=4, d=3, dtype=tu.TU_DTYPE_FP8E4M3_SIDE, path=0, fscale_x=1, fscale_y=1), tu.TU_ERR_INVALID_ARG),
         (dict(N=4, M=4, d=3, dtype=1, path=2), tu.TU_ERR_INVALID_ARG),  # unknown path
-        (dict(N=4, M=4, d=65, dtype=1, path=0), tu.TU_ERR_UNSUPPORTED),  # fused: 2d <= 128
-        (dict(N=4, M=4, d=65, dtype=tu.TU_DTYPE_FP8E4M3, path=0), tu.TU_ERR_UNSUPPORTED),
+        (dict(N=4, M=4, d=129, dtype=1, path=0), tu.TU_ERR_UNSUPPORTED),  # fused: d <= 128
+        (dict(N=4, M=4, d=257, dtype=tu.TU_DTYPE_FP8E4M3, path=0), tu.TU_ERR_UNSUPPORTED),  # FP8: d <= 256
+        # caller FP8 scales: both sides, FP8 markets only
+        (dict(N=4, M=4, d=3, dtype=tu.TU_DTYPE_FP8E4M3, path=0, fscale_x=1), tu.TU_ERR_INVALID_ARG),
+        (dict(N=4, M=4, d=3, dtype=1, path=0, fscale_x=1, fscale_y=1), tu.TU_ERR_INVALID_ARG),
         (dict(N=4, M=4, d=3, dtype=tu.TU_DTYPE_FP8E4M3, path=1), tu.TU_ERR_UNSUPPORTED),  # FP8: fused only
         # dense: A-hat and its transpose, 2 x 4 B x 160,000 x 160,000 = 205 GB > 200 GB
         (dict(N=160_000, M=160_000, d=3, dtype=1, path=1), tu.TU_ERR_UNSUPPORTED),

@@ -74,7 +74,7 @@ def test_warmup_minimum_is_enforced():
 
 def test_reference_arm_dimension_sweep():
     lines = _last_json(_bench("--impl", "reference", "--workload", "dims"))
-    assert [d["D"] for d in lines] == [8, 16, 32, 50, 64]
+    assert [d["D"] for d in lines] == [8, 16, 32, 50, 64, 100, 128]
     for d in lines:
         assert d["impl"] == "reference" and d["N"] == d["M"] == 10_000 and d["ms_per_sweep"] > 0
         assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1

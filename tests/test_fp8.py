@@ -1,7 +1,7 @@
 """GPU parity of FP8 (e4m3) markets against the FP64 oracle run on the same
 quantized factors (synth.fp8_quantized: the oracle side's own e4m3 rounding
-and per-side power-of-two scale; the CUDA path quantizes with its own
-conversion kernel).
+and per-row power-of-two scales; the CUDA path quantizes with its own
+conversion kernel, or takes the caller's bytes and scales).
 
 The tensor cores multiply e4m3 values exactly and accumulate in FP32, so the
 kernel's error budget is that of the BF16 path (ATOL_LOG, derived in
@@ -14,7 +14,7 @@ import pytest
 import torch
 
 import oracle
-from synth import fp8_quantized, fused_market, make_market
+from synth import fp8_encoded, fp8_quantized, fused_market, make_market
 
 from _parity import oracle_solve, oracle_sweeps
 
@@ -31,13 +31,15 @@ def _mk(N, M, d, seed, **kw):
     return make_market(N, M, d, seed=seed, **base)
 
 
-def test_fp8_phi_matches_quantized_factors(gpu_lib):
+@pytest.mark.parametrize("per", ["row", "side"])
+def test_fp8_phi_matches_quantized_factors(gpu_lib, per):
     """With u = v = 1, log mu = phi / (2 sigma): every pair checks the quantized
-    inner product (and that the market is not computing with BF16 factors)."""
+    inner product (and that the market is not computing with BF16 factors),
+    with per-row and per-side scales."""
     tu = gpu_lib
     mk = _mk(700, 555, 64, seed=5, bias_x=False, bias_y=False)
-    q, _ = fp8_quantized(mk)
-    mkt = tu.from_synth(mk, fp8=True)
+    q, _ = fp8_quantized(mk, per)
+    mkt = tu.from_synth(mk, fp8="rows" if per == "row" else "side")
     try:
         lu = torch.zeros(mk.N, dtype=torch.float32, device="cuda")
         lv = torch.zeros(mk.M, dtype=torch.float32, device="cuda")
@@ -53,13 +55,17 @@ def test_fp8_phi_matches_quantized_factors(gpu_lib):
         mkt.close()
 
 
-@pytest.mark.parametrize("N,M,d", [(700, 555, 64), (256, 128, 64), (333, 1201, 50), (1, 300, 24), (300, 1, 24),
-                                   (1000, 1000, 16)], ids=lambda v: str(v))
-def test_fp8_sweeps_match_oracle(gpu_lib, N, M, d):
+# d = 65..128: packed rows of two 128-byte k blocks; d = 129..256: four
+@pytest.mark.parametrize("N,M,d,per", [(700, 555, 64, "row"), (256, 128, 64, "row"), (333, 1201, 50, "row"),
+                                       (1, 300, 24, "row"), (300, 1, 24, "row"), (1000, 1000, 16, "row"),
+                                       (700, 555, 128, "row"), (257, 129, 65, "row"), (300, 700, 200, "row"),
+                                       (700, 555, 64, "side"), (1, 300, 24, "side"), (300, 700, 200, "side")],
+                         ids=lambda v: str(v))
+def test_fp8_sweeps_match_oracle(gpu_lib, N, M, d, per):
     tu = gpu_lib
     mk = _mk(N, M, d, seed=N + 3 * M)
-    q, _ = fp8_quantized(mk)
-    mkt = tu.from_synth(mk, fp8=True)
+    q, _ = fp8_quantized(mk, per)
+    mkt = tu.from_synth(mk, fp8="rows" if per == "row" else "side")
     try:
         for target in (1, 4):
             mkt.sweep(target if target == 1 else target - 1)
@@ -99,12 +105,13 @@ def test_fp8_solve_and_ranked_lists(gpu_lib):
         mkt.close()
 
 
-def test_fp8_batch_bit_identical_to_solo(gpu_lib):
+@pytest.mark.parametrize("mode", ["rows", "side"])
+def test_fp8_batch_bit_identical_to_solo(gpu_lib, mode):
     tu = gpu_lib
     shapes = [(700, 555, 64), (300, 1000, 48), (1, 300, 24), (513, 257, 64)]
     mks = [_mk(N, M, d, seed=50 + i) for i, (N, M, d) in enumerate(shapes)]
-    solo = [tu.from_synth(mk, fp8=True) for mk in mks]
-    grouped = [tu.from_synth(mk, fp8=True) for mk in mks]
+    solo = [tu.from_synth(mk, fp8=mode) for mk in mks]
+    grouped = [tu.from_synth(mk, fp8=mode) for mk in mks]
     batch = tu.Batch(grouped)
     try:
         batch.sweep(3)
@@ -128,13 +135,22 @@ def test_fp8_invalid_combinations(gpu_lib):
     assert e.value.status == tu.TU_ERR_UNSUPPORTED
     a = tu.from_synth(mk, fp8=True)
     b = tu.from_synth(_mk(100, 120, 64, seed=4, dtype="bf16"))
+    # the batched kernel takes BF16 rows of up to two k blocks (d <= 64) and e4m3 rows of one
+    c = tu.from_synth(_mk(100, 120, 100, seed=5, dtype="bf16"))
+    f = tu.from_synth(_mk(100, 120, 100, seed=6), fp8=True)
+    s = tu.from_synth(_mk(100, 120, 32, seed=7), fp8="side")
     try:
-        with pytest.raises(tu.TuError) as e:
-            tu.tu_batch_create([a.handle, b.handle])
-        assert e.value.status == tu.TU_ERR_INVALID_ARG
+        for other in (b, s):  # one operand format per batch
+            with pytest.raises(tu.TuError) as e:
+                tu.tu_batch_create([a.handle, other.handle])
+            assert e.value.status == tu.TU_ERR_INVALID_ARG
+        for h in (c.handle, f.handle):
+            with pytest.raises(tu.TuError) as e:
+                tu.tu_batch_create([h])
+            assert e.value.status == tu.TU_ERR_UNSUPPORTED
     finally:
-        a.close()
-        b.close()
+        for m in (a, b, c, f, s):
+            m.close()
 
 
 def test_fp8_full_size_sampled_sweep(gpu_lib):
@@ -160,3 +176,90 @@ def test_fp8_full_size_sampled_sweep(gpu_lib):
         np.testing.assert_allclose(lv[cols], ov, rtol=0, atol=ATOL_LOG)
     finally:
         mkt.close()
+
+
+def _scaled_rows(mk, fx=1e-4, fy=1e-3):
+    """The market with every other X row and every third Y row scaled down
+    (factors of very different norms within a side)."""
+    import dataclasses
+    sx = np.where(np.arange(mk.N) % 2 == 0, fx, 1.0).astype(np.float32)[:, None]
+    sy = np.where(np.arange(mk.M) % 3 == 0, fy, 1.0).astype(np.float32)[:, None]
+    return dataclasses.replace(mk, F=mk.F * sx, K=mk.K * sx, G=mk.G * sy, L=mk.L * sy)
+
+
+def test_fp8_row_scales_with_rows_of_different_norms(gpu_lib):
+    """Rows 1e-4 (X) and 1e-3 (Y) the size of the others: each row keeps its
+    own scale, phi of every pair matches the quantized factors (u = v = 1),
+    and the sweeps match the oracle."""
+    tu = gpu_lib
+    mk = _scaled_rows(_mk(640, 384, 64, seed=31, bias_x=False, bias_y=False))
+    q, (kx, ky) = fp8_quantized(mk)
+    assert kx.max() - kx.min() >= 12 and ky.max() - ky.min() >= 8  # the scales differ per row
+    mkt = tu.from_synth(mk, fp8=True)
+    try:
+        mkt.set_potentials(torch.zeros(mk.N, dtype=torch.float32, device="cuda"),
+                           torch.zeros(mk.M, dtype=torch.float32, device="cuda"))
+        got = torch.log(mkt.mu_block().double()).cpu().numpy()
+        f = q.f64()
+        want = oracle.phi_dense(f["F"], f["K"], f["G"], f["L"], None, None) / (2 * mk.sigma)
+        np.testing.assert_allclose(got, want, rtol=0, atol=2e-6 * max(1.0, np.abs(want).max()))
+        mkt.sweep(3)
+        lu, lv = (t.double().cpu().numpy() for t in mkt.potentials())
+        ou, ov = oracle_sweeps(q, 3)
+        np.testing.assert_allclose(lu, ou, rtol=0, atol=ATOL_LOG)
+        np.testing.assert_allclose(lv, ov, rtol=0, atol=ATOL_LOG)
+    finally:
+        mkt.close()
+
+
+def test_fp8_caller_scales_equal_library_quantization(gpu_lib):
+    """A caller that quantizes the rows itself (e4m3 bytes and per-row FP32
+    scales, synth.fp8_encoded; device or host buffers) gets the library's own
+    quantization of the same FP32 factors bit for bit; the scaled update
+    replaces them like a new market's."""
+    tu = gpu_lib
+    mk = _scaled_rows(_mk(700, 555, 100, seed=21))
+    mk2 = _mk(700, 555, 100, seed=22)
+
+    def cuda(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+    enc = fp8_encoded(mk)
+    lib_q = tu.from_synth(mk, fp8=True)
+    bx, by = cuda(mk.bias_x), cuda(mk.bias_y)
+    dev = tu.Market(*(cuda(a) for a in enc[:4]), mk.n, mk.m, mk.sigma, bias_x=bx, bias_y=by, fp8=True,
+                    fscale_x=cuda(enc[4]), fscale_y=cuda(enc[5]))
+    host = tu.Market(*enc[:4], mk.n, mk.m, mk.sigma, bias_x=bx, bias_y=by, fp8=True, fscale_x=enc[4],
+                     fscale_y=enc[5])
+    other = tu.from_synth(mk2, fp8=True)
+    try:
+        for m in (lib_q, dev, host):
+            m.sweep(3)
+        ref = lib_q.potentials()
+        for m in (dev, host):
+            got = m.potentials()
+            assert torch.equal(got[0], ref[0]) and torch.equal(got[1], ref[1])
+        # scaled update: the factors of mk2 (biases of mk stay), warm-started potentials kept
+        enc2 = fp8_encoded(mk2)
+        tu.tu_market_update_factors_fp8(dev.handle, *(cuda(a) for a in enc2))
+        tu.tu_market_update_factors(lib_q.handle, *(torch.from_numpy(a).cuda() for a in (mk2.F, mk2.K, mk2.G,
+                                                                                         mk2.L)))
+        dev.sweep(2)
+        lib_q.sweep(2)
+        a, b = dev.potentials(), lib_q.potentials()
+        assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+        # each market takes only its own kind of update
+        with pytest.raises(tu.TuError) as e:
+            tu.tu_market_update_factors(dev.handle, *(cuda(a) for a in enc2[:4]))
+        assert e.value.status == tu.TU_ERR_INVALID_ARG
+        with pytest.raises(tu.TuError) as e:
+            tu.tu_market_update_factors_fp8(other.handle, *(cuda(a) for a in enc2))
+        assert e.value.status == tu.TU_ERR_INVALID_ARG
+        bad = enc2[4].copy()
+        bad[5] = np.nan
+        with pytest.raises(tu.TuError) as e:
+            tu.tu_market_update_factors_fp8(dev.handle, *(cuda(a) for a in enc2[:4]), cuda(bad), cuda(enc2[5]))
+        assert e.value.status == tu.TU_ERR_NONFINITE
+    finally:
+        for m in (lib_q, dev, host, other):
+            m.close()

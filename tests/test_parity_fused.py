@@ -36,8 +36,9 @@ def _mk(N, M, d, seed, **kw):
     return make_market(N, M, d, seed=seed, **base)
 
 
+# d = 96 and 128: packed rows of four 128-byte k blocks (partner stages of one block each)
 SHAPES = [(700, 555, 64), (256, 128, 64), (1000, 1000, 16), (333, 1201, 50), (1, 300, 24), (300, 1, 24),
-          (5, 7, 1)]
+          (5, 7, 1), (700, 555, 128), (513, 300, 96)]
 
 
 @pytest.mark.parametrize("translate", [True, False], ids=["translated", "plain"])
