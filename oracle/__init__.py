@@ -22,7 +22,9 @@ Pins (in ``tests/test_oracle.py``, all run on the CPU):
   equivariance, side swap, mass scaling) and batch == mini-batch iterates;
 * brute-force sorting for the ranked lists;
 * the translation step (an extension) against a brute-force maximisation of
-  the dual along its line and a 60-digit root of its quadratic.
+  the dual along its line and a 60-digit root of its quadratic;
+* the Jacobi order (an extension) against Gauss-Seidel: its iterates are two
+  interleaved Gauss-Seidel sequences.
 """
 
 from .ipfp import (  # noqa: F401
@@ -33,6 +35,7 @@ from .ipfp import (  # noqa: F401
     half_sweep_x,
     half_sweep_y,
     ipfp_batch,
+    ipfp_jacobi,
     dual_value,
     translation_step,
     ipfp_batch_literal,

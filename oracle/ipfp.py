@@ -251,6 +251,32 @@ def ipfp_batch(Phi, n, m, beta, max_sweeps, tol=None, log_u=None, log_v=None, om
     return dict(log_u=lu, log_v=lv, sweeps=sweeps, res_inf=r_inf, res_l1=r_l1, trace=trace)
 
 
+def ipfp_jacobi(Phi, n, m, beta, max_sweeps, tol=None, log_u=None, log_v=None):
+    """The Jacobi variant of Eq. iteration (an extension, not in the paper):
+    both half-sweeps of a sweep read the state entering it, u' from the old v
+    and v' from the old u, so one pass over the pairs could feed both. Same
+    fixed point (Eq. IPFP). With tol, the loop stops before a sweep whose
+    entering state has row residual <= tol. Returns a dict like ipfp_batch,
+    with states: the (log u, log v) after every sweep."""
+    logA = log_kernel(Phi, beta)
+    N, M = logA.shape
+    lu = np.zeros(N) if log_u is None else np.array(log_u, dtype=np.float64)
+    lv = np.zeros(M) if log_v is None else np.array(log_v, dtype=np.float64)
+    trace, states = [], []
+    sweeps = 0
+    for _ in range(int(max_sweeps)):
+        if tol is not None:
+            r_inf, _, _ = row_residual(logA, n, lu, lv)
+            trace.append(r_inf)
+            if r_inf <= tol:
+                break
+        lu, lv = half_sweep_x(logA, lv, n), half_sweep_y(logA, lu, m)
+        states.append((lu, lv))
+        sweeps += 1
+    r_inf, r_l1, _ = row_residual(logA, n, lu, lv)
+    return dict(log_u=lu, log_v=lv, sweeps=sweeps, res_inf=r_inf, res_l1=r_l1, trace=trace, states=states)
+
+
 def ipfp_batch_literal(P, Q, n, m, beta, iters):
     """Alg. 1 exactly as printed, in the linear domain and with the printed
     update sqrt(s^2 + n) - s. Only for small, well-conditioned markets (it

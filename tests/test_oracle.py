@@ -722,3 +722,64 @@ def test_planted_translation_mistakes_are_caught(monkeypatch):
             mpatch.setattr(oracle, "translation_step", bad)
             assert not _translation_pins_pass(), f"planted mistake not caught: {name}"
     assert _translation_pins_pass()
+
+
+# ---------------------------------------------------------------------------
+# Jacobi order (an extension): both half-sweeps from the entering state
+# ---------------------------------------------------------------------------
+
+def test_jacobi_one_sweep_by_hand():
+    """1x2 market from u = v = 1: u' from the old v, v' from the old u = 1
+    (Gauss-Seidel would use the new u), written out by hand."""
+    Phi = np.array([[0.4, -0.6]])
+    beta, n, m = 0.5, np.array([1.0]), np.array([2.0, 1.0])
+    A = np.exp(Phi / (2 * beta))[0]
+    s = 0.5 * (A[0] + A[1])
+    u = np.sqrt(n[0] + s * s) - s
+    v = [np.sqrt(m[j] + (0.5 * A[j]) ** 2) - 0.5 * A[j] for j in range(2)]
+    r = oracle.ipfp_jacobi(Phi, n, m, beta, max_sweeps=1)
+    assert np.exp(r["log_u"][0]) == pytest.approx(u, rel=1e-14)
+    np.testing.assert_allclose(np.exp(r["log_v"]), v, rtol=1e-14)
+    gs = oracle.ipfp_batch(Phi, n, m, beta, max_sweeps=1)
+    assert abs(gs["log_v"][0] - r["log_v"][0]) > 1e-3  # not the Gauss-Seidel order
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 12])
+def test_jacobi_is_two_interleaved_gauss_seidel_runs(k):
+    """Jacobi states (U_t, V_t), U_{t+1} = f(V_t), V_{t+1} = g(U_t), hold two
+    independent Gauss-Seidel sequences: started from v_0, k Gauss-Seidel
+    sweeps give (U_{2k-1}, V_{2k}); started from v = g(u_0) = V_1, they give
+    (U_{2k}, V_{2k+1}). Bit for bit: the same half-sweeps in the same order."""
+    rng = np.random.default_rng(40 + k)
+    F, K, G, L, bx, by, n, m = _random_market(rng, 9, 7)
+    Phi = oracle.phi_dense(F, K, G, L, bx, by)
+    beta = 0.8
+    u0, v0 = rng.normal(0, 0.5, 9), rng.normal(0, 0.5, 7)
+    jac = oracle.ipfp_jacobi(Phi, n, m, beta, max_sweeps=2 * k + 1, log_u=u0, log_v=v0)
+    S = [(u0, v0)] + jac["states"]
+    a = oracle.ipfp_batch(Phi, n, m, beta, max_sweeps=k, log_u=u0, log_v=v0)
+    np.testing.assert_array_equal(a["log_u"], S[2 * k - 1][0])
+    np.testing.assert_array_equal(a["log_v"], S[2 * k][1])
+    b = oracle.ipfp_batch(Phi, n, m, beta, max_sweeps=k, log_u=u0, log_v=S[1][1])
+    np.testing.assert_array_equal(b["log_u"], S[2 * k][0])
+    np.testing.assert_array_equal(b["log_v"], S[2 * k + 1][1])
+
+
+def test_jacobi_same_fixed_point_twice_the_sweeps():
+    """Consequence of the interleaving: the Jacobi order reaches the fixed
+    point of Eq. IPFP, and needs at least twice the sweeps of Gauss-Seidel to
+    the same residual (measured 2.0-2.5: its state pairs the u of one chain
+    with the v of the other), so halving the pair work of a sweep would at best
+    break even."""
+    ratios = []
+    for seed in (1, 2, 3):
+        rng = np.random.default_rng(seed)
+        F, K, G, L, bx, by, n, m = _random_market(rng, 40, 30, cap=seed != 3)
+        Phi = oracle.phi_dense(F, K, G, L, bx, by)
+        gs = oracle.ipfp_batch(Phi, n, m, 1.0, max_sweeps=100000, tol=1e-10)
+        jac = oracle.ipfp_jacobi(Phi, n, m, 1.0, max_sweeps=200000, tol=1e-10)
+        assert jac["res_inf"] <= 1e-10
+        np.testing.assert_allclose(jac["log_u"], gs["log_u"], atol=1e-8)
+        np.testing.assert_allclose(jac["log_v"], gs["log_v"], atol=1e-8)
+        ratios.append(jac["sweeps"] / gs["sweeps"])
+    assert all(r >= 1.9 for r in ratios), ratios
