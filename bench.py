@@ -442,31 +442,46 @@ def run_paper_shapes(args):
     """Sec. 4.2 of the paper: average time per IPFP iteration of the mini-batch
     method for N = M in {1e2, ..., 1e6}, D = 50, factors U[0, 1/sqrt(D)],
     n = m = 1, beta = 1 (the paper averages over I = 100 iterations). Here:
-    `--steps` sweeps per size (graph replay), after `--warmup` sweeps."""
+    `--steps` sweeps per size (graph replay), after `--warmup` sweeps, with
+    the default launch shape and then with the shape the autotuner picks
+    (tu_market_autotune: own-tile height and partner split timed on the
+    market), plus two sizes between the paper's where the number of waves
+    of own tiles is small and uneven (4e4: 157 tiles of 256 rows; 3e5)."""
     import torch
 
     import paper_2411_19214_gb300 as tu
     from synth import paper_shaped_market
     tu.load()
+    tu.tu_autotune_cache_clear()
     stream = torch.cuda.Stream()
-    for N in (100, 1_000, 10_000, 100_000, 1_000_000):
+
+    def timed(mkt):
+        mkt.sweep(args.warmup)
+        mkt.sweep(args.steps)  # graph capture
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mkt.sweep(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    for N in (100, 1_000, 10_000, 40_000, 100_000, 300_000, 1_000_000):
         mk = paper_shaped_market(N)
         mkt = tu.from_synth(mk, path="fused", stream=stream)
         try:
-            mkt.sweep(args.warmup)
-            mkt.sweep(args.steps)  # graph capture
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            mkt.sweep(args.steps)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / args.steps
+            ms = timed(mkt)
+            tune = tu.tu_market_autotune(mkt.handle, reps=3)
+            ms_tuned = timed(mkt)
         finally:
             mkt.close()
         print(json.dumps({"workload": "paper-shaped mini-batch IPFP (Sec. 4.2)", "N": N, "M": N, "D": 50,
                           "ms_per_sweep": ms, "sweeps": args.steps, "gpair_evals_per_s": 2.0 * N * N / ms / 1e6,
+                          "autotuned": {"ms_per_sweep": ms_tuned, "small_tiles": tune["small_tiles"],
+                                        "split": tune["split"], "candidates": tune["candidates"],
+                                        "gpair_evals_per_s": 2.0 * N * N / ms_tuned / 1e6},
                           "dtype": "bf16"}), flush=True)
+    tu.tu_autotune_cache_clear()
 
 
 BATCHED_METRIC = "aggregate Gpair-evals/s of 512 independent markets in one persistent launch per half-sweep"

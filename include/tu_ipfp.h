@@ -307,16 +307,62 @@ tu_status tu_market_set_translation(tu_market_t mkt, int enable);
  * threads turn graphs off. No counterpart in the paper. */
 tu_status tu_market_use_graphs(tu_market_t mkt, int enable);
 
-/* Own-tile height of the fused path (no counterpart in the paper). With
- * enable = 1 (the default), a market whose 256-row own tiles would leave SMs
- * idle while its 128-row tiles all fit one wave uses 128-row tiles: twice the
- * CTAs, each ending its tile sooner, so an isolated market of up to
- * 128 x (SM count) users per side solves faster (a 1e4 x 1e4 sweep 0.171 ->
- * 0.132 ms). A 128-row tile delivers about two thirds of a 256-row tile's
- * per-SM throughput, so callers that keep the GPU full with many markets at
- * once (a serving loop) set 0. Results are bit-identical either way (every
- * row's arithmetic is the same). Dense markets ignore it. */
-tu_status tu_market_set_small_tiles(tu_market_t mkt, int enable);
+/* Launch shape of the fused half-sweep (no counterpart in the paper; results
+ * are the same fixed point whatever the shape).
+ * Own-tile height, mode = 0: 256-row own tiles; 1 (the default): 128-row
+ * tiles when a market's 256-row tiles would leave SMs idle while its 128-row
+ * tiles all fit one wave (twice the CTAs, each ending its tile sooner: an
+ * isolated 1e4 x 1e4 sweep 0.171 -> 0.132 ms); 2: always 128-row tiles. A
+ * 128-row tile delivers about two thirds of a 256-row tile's per-SM
+ * throughput, so callers that keep the GPU full with many markets at once (a
+ * serving loop) set 0. Results are bit-identical across modes (every row's
+ * arithmetic is the same). Dense markets ignore it. TU_ERR_INVALID_ARG for
+ * another mode. */
+tu_status tu_market_set_small_tiles(tu_market_t mkt, int mode);
+
+/* Partner split, 1 <= split <= 8 (fused markets; TU_ERR_UNSUPPORTED on the
+ * dense path): each own tile's partner tiles are cut into `split` contiguous
+ * ranges handled by different CTAs, and the CTA that completes a tile's
+ * block of rows sums the ranges' partial row sums in range order and updates
+ * the rows, so a market with few waves of own tiles fills the GPU in finer
+ * steps (1e5 users: 391 tiles of 256 rows are 2.6 waves on 148 SMs, in
+ * thirds 7.9). The sums are the same terms in another order (results agree
+ * to rounding, not bit for bit with split = 1). Allocates split x max(N, M)
+ * x 16 bytes of partial sums on first use. Applies to whole-side sweeps of
+ * markets within the single-shift range (see tu_market_create). */
+tu_status tu_market_set_split(tu_market_t mkt, int split);
+
+/* The market's launch shape: own-tile mode and partner split (either
+ * pointer may be NULL). */
+tu_status tu_market_get_shape(tu_market_t mkt, int* small_mode, int* split);
+
+/* Autotuner of the launch shape: times the candidate (own-tile height,
+ * partner split) pairs on this market, reps non-updating sweeps each after
+ * one untimed sweep (the potentials are not changed), keeps the fastest for
+ * the market and records it in a process-wide cache keyed by the market's
+ * shape (quarter-octave buckets of N and M, the packed row length, the FP8
+ * dtype or BF16, the SM count); fused markets created later with a cached
+ * shape take the tuned launch shape. Candidates: the default shape, 256-row
+ * tiles, 128-row tiles (fewer than 4 waves of 256-row tiles), and splits
+ * 2, 3, 4, 6, 8 (fewer than 8 waves; not for wide markets). Synchronises.
+ * TU_ERR_UNSUPPORTED on the dense path, TU_ERR_INVALID_ARG unless
+ * 1 <= reps <= 1000. */
+typedef struct {
+  int small_tiles;    /* chosen own-tile mode (as tu_market_set_small_tiles) */
+  int split;          /* chosen partner split */
+  double ms;          /* ms per sweep of the chosen shape */
+  double ms_default;  /* ms per sweep of the default shape (mode 1, split 1) */
+  int candidates;     /* shapes timed */
+} tu_tune_info;
+tu_status tu_market_autotune(tu_market_t mkt, int reps, tu_tune_info* info);
+
+/* The autotuner's cache as a JSON file (one entry per line; load merges the
+ * file's entries, which replace cached ones with the same key). Save or load
+ * of a path that cannot be opened, or load of a malformed file:
+ * TU_ERR_INVALID_ARG (nothing is merged). */
+tu_status tu_autotune_cache_save(const char* path);
+tu_status tu_autotune_cache_load(const char* path);
+void tu_autotune_cache_clear(void);
 
 /* Automatic over-relaxation for asynchronous sweeps (no counterpart in the
  * paper). For a market whose relaxation setting is 0 (automatic), feed the

@@ -44,6 +44,11 @@ class SolveInfo(ctypes.Structure):
                 ("residual_l1", ctypes.c_double), ("match_count", ctypes.c_double)]
 
 
+class TuneInfo(ctypes.Structure):
+    _fields_ = [("small_tiles", ctypes.c_int32), ("split", ctypes.c_int32), ("ms", ctypes.c_double),
+                ("ms_default", ctypes.c_double), ("candidates", ctypes.c_int32)]
+
+
 class TuError(RuntimeError):
     def __init__(self, status: int, where: str, detail: str = ""):
         self.status = status
@@ -83,6 +88,12 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tu_selftest_wait_timeout": (I32, [D, ctypes.POINTER(D)]),
         "tu_set_checked_mode": (I32, [I32]),
         "tu_market_set_small_tiles": (I32, [V, I32]),
+        "tu_market_set_split": (I32, [V, I32]),
+        "tu_market_get_shape": (I32, [V, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
+        "tu_market_autotune": (I32, [V, I32, ctypes.POINTER(TuneInfo)]),
+        "tu_autotune_cache_save": (I32, [ctypes.c_char_p]),
+        "tu_autotune_cache_load": (I32, [ctypes.c_char_p]),
+        "tu_autotune_cache_clear": (None, []),
         "tu_market_set_translation": (I32, [V, I32]),
         "tu_relax_schedule": (I32, [D, D, V, V, I32, V]),
         "tu_guard_violations": (I64, [ctypes.c_char_p, I64]),
@@ -373,9 +384,42 @@ def tu_guard_violations():
     return int(n), buf.value.decode()
 
 
-def tu_market_set_small_tiles(h: int, enable: bool) -> None:
-    """128-row own tiles for markets that leave SMs idle (default on); off for loops that keep the GPU full."""
-    _check(load().tu_market_set_small_tiles(h, int(bool(enable))), "tu_market_set_small_tiles", h)
+def tu_market_set_small_tiles(h: int, mode) -> None:
+    """Own-tile height: 0 / False 256-row tiles; 1 / True (default) 128-row tiles for markets whose
+    256-row tiles leave SMs idle; 2 always 128-row tiles."""
+    _check(load().tu_market_set_small_tiles(h, int(mode)), "tu_market_set_small_tiles", h)
+
+
+def tu_market_set_split(h: int, split: int) -> None:
+    """Partner split of the fused half-sweep (1..8 partner ranges per own tile)."""
+    _check(load().tu_market_set_split(h, int(split)), "tu_market_set_split", h)
+
+
+def tu_market_get_shape(h: int) -> tuple:
+    """(own-tile mode, partner split) of a market."""
+    a, b = ctypes.c_int(), ctypes.c_int()
+    _check(load().tu_market_get_shape(h, ctypes.byref(a), ctypes.byref(b)), "tu_market_get_shape", h)
+    return a.value, b.value
+
+
+def tu_market_autotune(h: int, reps: int = 3) -> dict:
+    """Time the candidate launch shapes on this market, keep the fastest and cache it by shape."""
+    info = TuneInfo()
+    _check(load().tu_market_autotune(h, int(reps), ctypes.byref(info)), "tu_market_autotune", h)
+    return dict(small_tiles=info.small_tiles, split=info.split, ms=info.ms, ms_default=info.ms_default,
+                candidates=info.candidates)
+
+
+def tu_autotune_cache_save(path: str) -> None:
+    _check(load().tu_autotune_cache_save(os.fsencode(path)), "tu_autotune_cache_save")
+
+
+def tu_autotune_cache_load(path: str) -> None:
+    _check(load().tu_autotune_cache_load(os.fsencode(path)), "tu_autotune_cache_load")
+
+
+def tu_autotune_cache_clear() -> None:
+    load().tu_autotune_cache_clear()
 
 
 def tu_relax_schedule(omega: float, tol: float, done, residual) -> np.ndarray:

@@ -108,6 +108,14 @@ struct FusedParams {
   // column j is fs_own[r] * fs_par[j] * <e4m3 row r, e4m3 row j>
   const float* fs_own;
   const float* fs_par;
+  // partner split (single-market half-sweeps, 1 = off): an item is an own
+  // tile and one of `split` contiguous ranges of its partner tiles; each
+  // epilogue warp writes its rows' partial sums to part[s * rows + r], and the
+  // warp that completes a (tile, 32-row block), counted in split_cnt, sums
+  // the partials in range order and updates the rows
+  int split;
+  float4* part;
+  int* split_cnt;
 };
 
 // Own-tile buffers: with one 128-byte k block per row the next own tile is
@@ -455,7 +463,19 @@ __device__ __forceinline__ int item_begin(const FusedParams& p) {
 template <bool BATCH>
 __device__ __forceinline__ int item_end(const FusedParams& p) {
   if constexpr (BATCH) return p.cta_start[blockIdx.x + 1];
-  return p.num_own_tiles;
+  return p.num_own_tiles * p.split;
+}
+
+// An item of a single-market launch: own tile t and its partner tiles
+// [jb, je) (range s of p.split equal parts).
+struct Span {
+  int t, s, jb, je;
+};
+__device__ __forceinline__ Span single_span(const FusedParams& p, int it) {
+  const int S = p.split;
+  const int t = it / S, s = it - t * S;
+  const int npt = p.num_partner_tiles;
+  return {t, s, (int)((int64_t)s * npt / S), (int)((int64_t)(s + 1) * npt / S)};
 }
 template <bool BATCH>
 __device__ __forceinline__ int item_step() {
@@ -574,22 +594,27 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool ok = true;
       for (int it = item_begin<BATCH>(p); it < item_end<BATCH>(p) && ok; it += item_step<BATCH>()) {
         const BatchDesc* bd = nullptr;
-        int t = it;
+        int t, jb = 0, je;
         if constexpr (BATCH) {
           const ItemRef w = batch_item(p, it);
           bd = w.d;
           t = w.t;
+          je = bd->num_partner_tiles;
           if (bd != prev) {
             tensormap_acquire(&bd->tm_own);
             tensormap_acquire(&bd->tm_partner);
             prev = bd;
           }
+        } else {
+          const Span sp = single_span(p, it);
+          t = sp.t;
+          jb = sp.jb;
+          je = sp.je;
         }
         const CUtensorMap* map_own = BATCH ? &bd->tm_own : &tm_own;
         const CUtensorMap* map_partner = BATCH ? &bd->tm_partner : &tm_partner;
         const float* gsrc = BATCH ? bd->g : p.g + p.col0;
         const float* fsrc = BATCH ? bd->fs_par : p.fs_par + p.col0;
-        const int npt = BATCH ? bd->num_partner_tiles : p.num_partner_tiles;
         // (SMALL: the 256-row box also brings the next tile's rows, unused)
         const int64_t arow = BATCH ? (int64_t)t * kFusedOwnRows : p.row0 + (int64_t)t * kOwn;
         if (!mbar_wait(&a_empty[ab], a_phase ^ 1u, abort_flag)) {
@@ -604,7 +629,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           ab = 0;
           a_phase ^= 1u;
         }
-        for (int j = 0; j < npt && ok; ++j) {
+        for (int j = jb; j < je && ok; ++j) {
           for (int sp = 0; sp < SPT; ++sp) {
             if (!mbar_wait(&empty[stage], phase ^ 1u, abort_flag)) {
               ok = false;
@@ -656,11 +681,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0, tphase = 0, a_phase = 0;
       bool ok = true;
       for (int it = item_begin<BATCH>(p); it < item_end<BATCH>(p) && ok; it += item_step<BATCH>()) {
-        int npt;
+        int jb = 0, je;
         if constexpr (BATCH) {
-          npt = batch_item(p, it).d->num_partner_tiles;
+          je = batch_item(p, it).d->num_partner_tiles;
         } else {
-          npt = p.num_partner_tiles;
+          const Span sp = single_span(p, it);
+          jb = sp.jb;
+          je = sp.je;
         }
         if (!mbar_wait(&a_full[ab], a_phase, abort_flag)) {
           ok = false;
@@ -673,7 +700,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           ab = 0;
           a_phase ^= 1u;
         }
-        for (int j = 0; j < npt && ok; ++j) {
+        for (int j = jb; j < je && ok; ++j) {
           if (!mbar_wait(&tempty[buf], tphase ^ 1u, abort_flag)) {
             ok = false;
             break;
@@ -710,7 +737,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           if (!ok) break;
           umma_commit(&tfull[buf]);
-          if (j == npt - 1) umma_commit(a_release);
+          if (j == je - 1) umma_commit(a_release);
           buf ^= 1;
           if (buf == 0) tphase ^= 1u;
         }
@@ -751,14 +778,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     int tile_iter = 0;
     for (int it = item_begin<BATCH>(p); it < item_end<BATCH>(p) && ok; it += item_step<BATCH>(), ++tile_iter) {
       const BatchDesc* bd = nullptr;
-      int t = it;
+      int t, split_s = 0, jb = 0, je;
       if constexpr (BATCH) {
         const ItemRef w = batch_item(p, it);
         bd = w.d;
         t = w.t;
+        je = bd->num_partner_tiles;
+      } else {
+        const Span sp = single_span(p, it);
+        t = sp.t;
+        split_s = sp.s;
+        jb = sp.jb;
+        je = sp.je;
       }
       const double shift = BATCH ? bd->st[kStShift] : shift0;
-      const int npt = BATCH ? bd->num_partner_tiles : p.num_partner_tiles;
       const int rloc = h * 128 + q * 32 + lane;          // row within the own tile
       const int64_t r = (int64_t)t * kOwn + rloc;         // row within the launch
       const bool row_ok = rloc < kOwn && r < (BATCH ? bd->rows : p.rows);
@@ -800,7 +833,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         thr = -INFINITY;
       }
-      for (int j = 0; j < npt; ++j) {
+      for (int j = jb; j < je; ++j) {
         // every lane waits; the outcome is made warp-uniform so that the
         // .sync.aligned TMEM loads below never run with a partial warp
         const bool got = mbar_wait(&tfull[buf], tphase, abort_flag) && mbar_wait(&gfull[gs], gphase, abort_flag);
@@ -953,6 +986,35 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&rowfree[pb]);
         const int64_t row = p.row0 + r;
+        // the row's sum as three FP32 parts (a split: summed over its ranges)
+        float s_hi = sum, s_lo = -comp, s_o = other;
+        if constexpr (MODE == kModeSweep && !BATCH) {
+          if (p.split > 1) {
+            // this range's partial; the warp that completes the (tile, 32-row
+            // block) sums all ranges in order and updates the rows (no wait:
+            // the other warps of this block move on)
+            const int64_t blk = (int64_t)t * (kFusedOwnRows / 32) + (h * 128 + q * 32) / 32;
+            if (row_ok) p.part[(int64_t)split_s * p.rows + r] = make_float4(sum, -comp, other, 0.0f);
+            __threadfence();
+            __syncwarp();
+            int prev = 0;
+            if (lane == 0) prev = atomicAdd(p.split_cnt + blk, 1);
+            prev = __shfl_sync(0xffffffffu, prev, 0);
+            if (prev != p.split - 1) continue;
+            if (lane == 0) p.split_cnt[blk] = 0;  // ready for the next launch
+            __threadfence();
+            s_hi = s_lo = s_o = 0.0f;
+            if (row_ok)
+              for (int qs = 0; qs < p.split; ++qs) {
+                const float4 v = __ldcg(p.part + (int64_t)qs * p.rows + r);
+                float e1, e2, e3;
+                s_hi = two_sum(s_hi, v.x, e1);
+                s_hi = two_sum(s_hi, v.y, e2);
+                s_hi = two_sum(s_hi, v.z, e3);
+                s_lo = __fadd_rn(s_lo, __fadd_rn(e1, __fadd_rn(e2, e3)));
+              }
+          }
+        }
         double lu_new = 0.0, ell_new = 0.0;
         if (row_ok) {
           const float* b2s = BATCH ? bd->b2s : p.b2s;
@@ -960,7 +1022,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           double* ell = BATCH ? bd->ell : p.ell;
           const double omega = BATCH ? ((bd->omega != nullptr && p.update) ? *bd->omega : 1.0) : omega0;
           const double own_off = BATCH ? bd->st[kStOwnOff] : own_off0;
-          double ln_sum = log_row_sum(sum, -comp, other);
+          double ln_sum = log_row_sum(s_hi, s_lo, s_o);
           // wide markets: the row's shift comes back into the sum's logarithm
           if constexpr (MODE == kModeSweepShift)
             ln_sum = __fma_rn(-(double)__uint_as_float((uint32_t)rshift), 0.69314718055994530942, ln_sum);
@@ -1213,7 +1275,8 @@ cudaError_t launch_any(int64_t kp, int fmt, const CUtensorMap& own, const CUtens
 // SMs would otherwise stay idle; on a GPU already full (other markets' work
 // on other streams) they lose a third of the per-SM throughput.
 bool use_small_tiles(const tu_market* m, int64_t rows) {
-  if (!m->small_tiles) return false;
+  if (m->small_mode == 0) return false;
+  if (m->small_mode == 2) return true;
   const int64_t t256 = (rows + kFusedOwnRows - 1) / kFusedOwnRows;
   const int64_t t128 = (rows + kFusedOwnRows / 2 - 1) / (kFusedOwnRows / 2);
   return t256 < m->num_sms && t128 <= m->num_sms;
@@ -1229,6 +1292,7 @@ FusedParams base_params(int64_t rows, int64_t row0, int64_t col0, int64_t ncols,
   p.num_own_tiles = (int)((rows + own_rows - 1) / own_rows);
   p.num_partner_tiles = (int)((ncols + kFusedPartnerRows - 1) / kFusedPartnerRows);
   p.c = c;
+  p.split = 1;
   return p;
 }
 
@@ -1278,7 +1342,13 @@ cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int upd
   p.omega = m->omega_dev;
   p.fs_own = own.fs;
   p.fs_par = partner.fs;
-  const int grid = grid_for_tiles(p.num_own_tiles, m->num_sms);
+  if (whole && !m->wide && m->split > 1 && m->split_part != nullptr) {
+    // partner split: at most one range per partner tile
+    p.split = m->split < p.num_partner_tiles ? m->split : p.num_partner_tiles;
+    p.part = m->split_part;
+    p.split_cnt = m->split_cnt;
+  }
+  const int grid = grid_for_tiles(p.num_own_tiles * p.split, m->num_sms);
   *nparts_out = grid;
   const int fmt = fmt_of(m->dtype);
   if (m->wide) {

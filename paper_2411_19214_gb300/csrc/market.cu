@@ -7,9 +7,12 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -728,6 +731,8 @@ void tu_market_destroy(tu_market_t m) {
   dev_free(m, m->partials);
   dev_free(m, m->st);
   dev_free(m, m->rowmax);
+  dev_free(m, m->split_part);
+  dev_free(m, m->split_cnt);
   dev_free(m, m->results);
   dev_free(m, m->err_dev);
   dev_free(m, m->staging);
@@ -746,6 +751,10 @@ void tu_market_destroy(tu_market_t m) {
   }
   delete m;
 }
+
+namespace {
+void apply_tuned(tu_market* m);  // (the autotuner, below)
+}  // namespace
 
 tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
   TU_TRACE("tu_market_create");
@@ -877,6 +886,7 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
   if (D.path == TU_PATH_FUSED) {
     cudaError_t e = fused_prepare(m);
     if (e != cudaSuccess) return bail(fail_cuda(m, e, "fused_prepare"));
+    apply_tuned(m);
   }
   if (cudaMemsetAsync(m->st, 0, kStSlots * sizeof(double), m->stream) != cudaSuccess ||
       launch_rescan(m) != cudaSuccess)
@@ -955,17 +965,236 @@ tu_status tu_market_use_graphs(tu_market_t m, int enable) {
   return TU_OK;
 }
 
-tu_status tu_market_set_small_tiles(tu_market_t m, int enable) {
-  TU_TRY(check_live(m));
-  if ((enable != 0) != m->small_tiles && m->graph != nullptr) {
-    // captured sweeps use the kernel of the previous setting
-    TU_CK(m, cudaStreamSynchronize(m->stream));
-    cudaGraphExecDestroy(m->graph);
-    m->graph = nullptr;
-    m->graph_sweeps = 0;
-  }
-  m->small_tiles = enable != 0;
+// ---------------------------------------------------------------------------
+// Launch shape of the fused half-sweep (own-tile height, partner split) and
+// its autotuner
+// ---------------------------------------------------------------------------
+
+namespace {
+
+// captured sweeps hold the launch shape they were captured with
+tu_status drop_graph(tu_market* m) {
+  if (m->graph == nullptr) return TU_OK;
+  TU_CK(m, cudaStreamSynchronize(m->stream));
+  cudaGraphExecDestroy(m->graph);
+  m->graph = nullptr;
+  m->graph_sweeps = 0;
   return TU_OK;
+}
+
+// partial row sums (split x the larger side) and the arrival counters (8 per
+// own tile of 128 rows or more), zeroed
+tu_status ensure_split_buffers(tu_market* m, int split) {
+  if (split <= m->split_cap) return TU_OK;
+  TU_CK(m, cudaStreamSynchronize(m->stream));  // no pass still uses the old buffers
+  dev_free(m, m->split_part);
+  dev_free(m, m->split_cnt);
+  m->split_cap = 0;
+  const int64_t rows = m->X.rows_pad > m->Y.rows_pad ? m->X.rows_pad : m->Y.rows_pad;
+  const int64_t blocks = (rows / (kFusedOwnRows / 2) + 1) * (kFusedOwnRows / 32);
+  TU_TRY(dev_alloc(m, &m->split_part, (size_t)split * rows));
+  TU_TRY(dev_alloc(m, &m->split_cnt, (size_t)blocks));
+  TU_CK(m, cudaMemsetAsync(m->split_cnt, 0, (size_t)blocks * sizeof(int), m->stream));
+  m->split_cap = split;
+  return TU_OK;
+}
+
+tu_status set_shape(tu_market* m, int small_mode, int split) {
+  if (small_mode == m->small_mode && split == m->split) return TU_OK;
+  TU_TRY(drop_graph(m));
+  if (split > 1) TU_TRY(ensure_split_buffers(m, split));
+  m->small_mode = small_mode;
+  m->split = split;
+  return TU_OK;
+}
+
+// The tuned shapes, by market shape: quarter-octave buckets of N and M, the
+// packed row length, the operand format and the SM count.
+struct TuneKey {
+  int nb, mb;
+  int64_t kp;
+  int fmt;
+  int sms;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(nb, mb, kp, fmt, sms) < std::tie(o.nb, o.mb, o.kp, o.fmt, o.sms);
+  }
+};
+struct TuneVal {
+  int small_mode, split;
+  double ms, ms_default;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+
+int octave_bucket(int64_t n) { return (int)std::floor(4.0 * std::log2((double)n)); }
+TuneKey tune_key(const tu_market* m) {
+  return {octave_bucket(m->N), octave_bucket(m->M), m->kp, is_fp8(m->dtype) ? m->dtype : 0, m->num_sms};
+}
+
+// A new fused market takes the shape tuned for its bucket, if any (a failed
+// allocation of the split buffers leaves the default shape).
+void apply_tuned(tu_market* m) {
+  TuneVal v{};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tune_key(m));
+    if (it == g_tune.end()) return;
+    v = it->second;
+  }
+  if (set_shape(m, v.small_mode, v.split) != TU_OK) {
+    m->last_error.clear();
+    m->small_mode = 1;
+    m->split = 1;
+  }
+}
+
+// ms per sweep (both half-sweeps, no update, as a certifying pass runs them)
+// of the current shape, over reps after one untimed sweep
+tu_status time_shape(tu_market* m, int reps, double* ms) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  TU_CK(m, cudaEventCreate(&e0));
+  cudaError_t e = cudaEventCreate(&e1);
+  for (int r = -1; r < reps && e == cudaSuccess; ++r) {
+    if (r == 0) e = cudaEventRecord(e0, m->stream);
+    if (e == cudaSuccess) e = enqueue_half(m, 0, kResidualEstimate, 0);
+    if (e == cudaSuccess) e = enqueue_half(m, 1, kResidualNone, 0);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, m->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  if (e1 != nullptr) cudaEventDestroy(e1);
+  if (e != cudaSuccess) return fail_cuda(m, e, "autotune timing");
+  *ms = (double)t / reps;
+  return TU_OK;
+}
+
+}  // namespace
+
+tu_status tu_market_set_small_tiles(tu_market_t m, int mode) {
+  TU_TRY(check_live(m));
+  if (mode < 0 || mode > 2) return fail(m, TU_ERR_INVALID_ARG, "small-tile mode must be 0, 1 or 2");
+  return set_shape(m, mode, m->split);
+}
+
+tu_status tu_market_set_split(tu_market_t m, int split) {
+  TU_TRY(check_live(m));
+  if (m->path != TU_PATH_FUSED) return fail(m, TU_ERR_UNSUPPORTED, "the partner split is a fused-path shape");
+  if (split < 1 || split > kMaxSplit) return fail(m, TU_ERR_INVALID_ARG, "split must be in [1, 8]");
+  return set_shape(m, m->small_mode, split);
+}
+
+tu_status tu_market_get_shape(tu_market_t m, int* small_mode, int* split) {
+  TU_TRY(check_live(m));
+  if (small_mode != nullptr) *small_mode = m->small_mode;
+  if (split != nullptr) *split = m->split;
+  return TU_OK;
+}
+
+tu_status tu_market_autotune(tu_market_t m, int reps, tu_tune_info* info) {
+  TU_TRACE("tu_market_autotune");
+  TU_TRY(check_live(m));
+  if (m->path != TU_PATH_FUSED) return fail(m, TU_ERR_UNSUPPORTED, "the autotuner chooses fused-path shapes");
+  if (reps < 1 || reps > 1000) return fail(m, TU_ERR_INVALID_ARG, "reps must be in [1, 1000]");
+  TU_CK(m, cudaStreamSynchronize(m->stream));
+  TU_TRY(drop_graph(m));
+  const int64_t rows = m->N > m->M ? m->N : m->M;
+  const int64_t tiles = (rows + kFusedOwnRows - 1) / kFusedOwnRows;
+  const int64_t ptiles = ((m->N < m->M ? m->N : m->M) + kFusedPartnerRows - 1) / kFusedPartnerRows;
+  // candidates: the default shape first; 128-row tiles and partner splits
+  // only where waves are few enough for their granularity to matter
+  std::vector<std::pair<int, int>> cand = {{1, 1}, {0, 1}};
+  if (tiles < 4 * (int64_t)m->num_sms) cand.push_back({2, 1});
+  if (tiles < 8 * (int64_t)m->num_sms && !m->wide)
+    for (int s : {2, 3, 4, 6, 8})
+      if (s <= ptiles) {
+        cand.push_back({0, s});
+        if (tiles < 2 * (int64_t)m->num_sms) cand.push_back({2, s});
+      }
+  const int small0 = m->small_mode, split0 = m->split;
+  double best = 0.0, ms_default = 0.0;
+  int bi = -1;
+  tu_status st = TU_OK;
+  for (size_t i = 0; i < cand.size() && st == TU_OK; ++i) {
+    double ms = 0.0;
+    st = set_shape(m, cand[i].first, cand[i].second);
+    if (st == TU_OK) st = time_shape(m, reps, &ms);
+    if (st != TU_OK) break;
+    if (i == 0) ms_default = ms;
+    if (bi < 0 || ms < best) {
+      best = ms;
+      bi = (int)i;
+    }
+  }
+  if (st != TU_OK) {
+    set_shape(m, small0, split0);
+    return st;
+  }
+  TU_TRY(set_shape(m, cand[bi].first, cand[bi].second));
+  TU_TRY(clear_results(m));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[tune_key(m)] = TuneVal{cand[bi].first, cand[bi].second, best, ms_default};
+  }
+  if (info != nullptr) {
+    info->small_tiles = cand[bi].first;
+    info->split = cand[bi].second;
+    info->ms = best;
+    info->ms_default = ms_default;
+    info->candidates = (int)cand.size();
+  }
+  return TU_OK;
+}
+
+tu_status tu_autotune_cache_save(const char* path) {
+  if (path == nullptr) return TU_ERR_INVALID_ARG;
+  std::ofstream f(path);
+  if (!f) return TU_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  f << "{\"tu_autotune\": 1, \"entries\": [\n";
+  size_t i = 0;
+  for (const auto& kv : g_tune) {
+    char line[320];
+    snprintf(line, sizeof(line),
+             "{\"n_bucket\": %d, \"m_bucket\": %d, \"kp\": %lld, \"dtype\": %d, \"sms\": %d, "
+             "\"small_tiles\": %d, \"split\": %d, \"ms\": %.6g, \"ms_default\": %.6g}%s\n",
+             kv.first.nb, kv.first.mb, (long long)kv.first.kp, kv.first.fmt, kv.first.sms, kv.second.small_mode,
+             kv.second.split, kv.second.ms, kv.second.ms_default, ++i < g_tune.size() ? "," : "");
+    f << line;
+  }
+  f << "]}\n";
+  return f.good() ? TU_OK : TU_ERR_INVALID_ARG;
+}
+
+tu_status tu_autotune_cache_load(const char* path) {
+  if (path == nullptr) return TU_ERR_INVALID_ARG;
+  std::ifstream f(path);
+  if (!f) return TU_ERR_INVALID_ARG;
+  std::map<TuneKey, TuneVal> read;
+  std::string line;
+  while (std::getline(f, line)) {
+    TuneKey k{};
+    TuneVal v{};
+    long long kp = 0;
+    if (line.find("\"n_bucket\"") == std::string::npos) continue;
+    if (sscanf(line.c_str(),
+               " {\"n_bucket\": %d, \"m_bucket\": %d, \"kp\": %lld, \"dtype\": %d, \"sms\": %d, "
+               "\"small_tiles\": %d, \"split\": %d, \"ms\": %lf, \"ms_default\": %lf",
+               &k.nb, &k.mb, &kp, &k.fmt, &k.sms, &v.small_mode, &v.split, &v.ms, &v.ms_default) != 9)
+      return TU_ERR_INVALID_ARG;
+    if (v.small_mode < 0 || v.small_mode > 2 || v.split < 1 || v.split > kMaxSplit) return TU_ERR_INVALID_ARG;
+    k.kp = kp;
+    read[k] = v;
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (const auto& kv : read) g_tune[kv.first] = kv.second;
+  return TU_OK;
+}
+
+void tu_autotune_cache_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
 }
 
 tu_status tu_relax_schedule(double omega, double tol, const int* done, const double* residual, int count,

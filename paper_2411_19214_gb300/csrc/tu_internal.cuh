@@ -54,6 +54,7 @@ enum : int {
 // Per-32-row group of a side (Side::grp, a float4): max 2 log u, sum of
 // e^{2 log u - max}, max ell; written by the side's own half-sweep.
 constexpr int kGroupRows = 32;
+constexpr int kMaxSplit = 8;  // partner ranges per own tile (tu_market_set_split)
 
 // Residual of the state entering an X half-sweep (the pass's `residual`):
 // none, an estimate with FP32 terms (inside sweeps) or exact FP64 terms
@@ -169,7 +170,12 @@ struct tu_market {
   cudaGraphExec_t graph = nullptr; // captured block of sweeps
   int graph_sweeps = 0;
   bool use_graphs = true;          // tu_market_use_graphs
-  bool small_tiles = true;         // tu_market_set_small_tiles: 128-row own tiles when they fit one wave
+  int small_mode = 1;              // tu_market_set_small_tiles: 0 256-row own tiles, 1 128-row when they
+                                   // fit one wave, 2 always 128-row
+  int split = 1;                   // tu_market_set_split: partner ranges per own tile (fused sweeps)
+  float4* split_part = nullptr;    // split > 1: partial row sums, split x max(N, M)
+  int* split_cnt = nullptr;        // split > 1: arrivals per (own tile, 32-row block), zeroed
+  int split_cap = 0;               // the split the buffers were sized for
   bool translate = true;           // tu_market_set_translation: translation step before every half-sweep
   bool wide = false;               // factor range beyond one shift per half-sweep: per-row shifts (two passes)
   float* rowmax = nullptr;         // fused path: per own row, the largest exponent (log2), max(N, M) padded
