@@ -1222,7 +1222,7 @@ cudaError_t set_attributes_mode() {
 }
 
 // Dynamic shared memory opt-in of every instantiation, on the current device.
-cudaError_t set_kernel_attributes() {
+cudaError_t set_kernel_attributes_now() {
   cudaError_t e = set_attributes_mode<kModeSweep, false>();
   if (e == cudaSuccess) e = set_attributes_mode<kModeTopK, false>();
   if (e == cudaSuccess) e = set_attributes_mode<kModeMu, false>();
@@ -1230,6 +1230,23 @@ cudaError_t set_kernel_attributes() {
   if (e == cudaSuccess) e = set_attributes_mode<kModeSweep, true>();
   if (e == cudaSuccess) e = set_attributes_mode<kModeRowMax, false>();
   if (e == cudaSuccess) e = set_attributes_mode<kModeSweepShift, false>();
+  return e;
+}
+
+// The opt-in is a property of each function in the device's context: made
+// once per device (about 130 instantiations, a driver call each), not per
+// market, so that creating markets stays cheap for a loop that creates many.
+cudaError_t set_kernel_attributes() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return set_kernel_attributes_now();
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return cudaSuccess;
+  e = set_kernel_attributes_now();
+  if (e == cudaSuccess) done[dev] = true;
   return e;
 }
 

@@ -1494,6 +1494,10 @@ tu_status tu_topk_partners(tu_market_t m, int side, int k, int64_t row0, int64_t
   const size_t ib = (size_t)nrows * k * sizeof(int32_t), vb = (size_t)nrows * k * sizeof(float);
   void *di, *dv = nullptr;
   bool hi, hv = false;
+  // host outputs share the staging buffer: size it for both before either
+  // view points into it (growing it later would free the first view's block)
+  if (!is_device_ptr(idx) || (log_mu != nullptr && !is_device_ptr(log_mu)))
+    TU_TRY(ensure_staging(m, (size_t)round_up((int64_t)ib, 256) + vb));
   TU_TRY(output_view(m, idx, ib, 0, &di, &hi));
   if (log_mu != nullptr) TU_TRY(output_view(m, log_mu, vb, round_up((int64_t)ib, 256), &dv, &hv));
   if (m->path == TU_PATH_FUSED) {

@@ -54,13 +54,15 @@ from typing import Dict, List, Optional
 
 import numpy as np
 
-from . import (TuError, tu_get_potentials, tu_ipfp_sweep, tu_market_create, tu_market_destroy,
-               tu_market_footprint, tu_market_query, tu_market_relax_update, tu_market_set_relaxation,
-               tu_market_set_small_tiles, tu_market_set_translation, tu_market_update_factors, tu_market_use_graphs,
-               tu_topk_partners)
+from . import (TuError, tu_batch_create, tu_batch_destroy, tu_batch_solve, tu_get_potentials, tu_ipfp_sweep,
+               tu_market_create, tu_market_destroy, tu_market_footprint, tu_market_query, tu_market_relax_update,
+               tu_market_set_relaxation, tu_market_set_small_tiles, tu_market_set_translation,
+               tu_market_update_factors, tu_market_use_graphs, tu_topk_partners)
 
-# the fused path's factor dimension limit (2d <= 128: one 128-wide MMA inner dimension)
-MAX_D = 64
+# the fused path's factor dimension limit (2d padded to at most 256: four 128-byte k blocks)
+MAX_D = 128
+# the batched launch takes packed rows of up to two k blocks (d <= 64)
+MAX_D_BATCHED = 64
 
 
 @dataclasses.dataclass
@@ -526,3 +528,182 @@ def percentiles(latencies: List[float]) -> dict:
         return {"p50": None, "p99": None, "mean": None}
     return {"p50": float(np.percentile(a, 50)), "p99": float(np.percentile(a, 99)), "mean": float(a.mean()),
             "max": float(a[-1])}
+
+
+class WindowServer:
+    """Micro-batching over the batched persistent launch, the alternative to
+    :class:`Server`'s stream per market: requests that arrive within
+    ``window_s`` of the oldest waiting one (at most ``max_batch``) are made
+    markets on one stream, grouped by packed row length (d <= 32: 64
+    elements, else 128), and each group is solved by ``tu_batch_solve``: one
+    persistent launch per half-sweep for the whole group, converged markets
+    leaving it; then every request gets its top-k reply. A re-solve of a
+    resident market (same key and shape) replaces its factors and joins its
+    group from its current potentials (new markets start from u = v = 1).
+    Admission by HBM footprint with LRU eviction of idle resident markets,
+    and validation, as in Server. The host thread blocks in the batched
+    solve, so requests that arrive meanwhile wait for the next window. d above
+    the batched launch's limit (64) is answered ``invalid``."""
+
+    def __init__(self, hbm_budget_bytes: int, tol: float = 1e-6, max_sweeps: int = 200, k: int = 10,
+                 window_s: float = 0.01, max_batch: int = 64, relax: bool = True, translate: bool = True):
+        import torch
+        self.budget = int(hbm_budget_bytes)
+        self.tol = tol
+        self.max_sweeps = max_sweeps
+        self.k = k
+        self.window = window_s
+        self.max_batch = max_batch
+        self.relax = relax
+        self.translate = translate
+        self.used = 0
+        self.resident: "collections.OrderedDict[str, tuple]" = collections.OrderedDict()  # key -> (handle, shape, bytes)
+        self.stream = torch.cuda.Stream()
+        self.stats = dict(admitted=0, evicted=0, warm=0, groups=0, largest_group=0, invalid=0, errors=0)
+
+    def _evict_one(self) -> bool:
+        if not self.resident:
+            return False
+        _, (h, _, nbytes) = self.resident.popitem(last=False)
+        tu_market_destroy(h)
+        self.used -= nbytes
+        self.stats["evicted"] += 1
+        return True
+
+    def _market(self, req: SolveRequest):
+        """(handle, bytes, warm) of the request's market, or a failure string."""
+        N, M, d = req.shape
+        if req.key is not None and req.key in self.resident:
+            h, shape, nbytes = self.resident.pop(req.key)
+            if shape == req.shape:
+                try:
+                    tu_market_update_factors(h, *(np.ascontiguousarray(getattr(req, a)) for a in "FKGL"))
+                except TuError as e:
+                    tu_market_destroy(h)
+                    self.used -= nbytes
+                    return f"error: {e}"
+                self.stats["warm"] += 1
+                return h, nbytes, True
+            tu_market_destroy(h)
+            self.used -= nbytes
+        need = tu_market_footprint(N, M, d, "fused")
+        if need > self.budget:
+            return f"invalid: footprint {need} bytes exceeds the budget of {self.budget} bytes"
+        while self.used + need > self.budget and self._evict_one():
+            pass
+        if self.used + need > self.budget:
+            return "wait"
+        try:
+            h = tu_market_create(*(np.ascontiguousarray(getattr(req, a)) for a in "FKGL"), req.n, req.m, req.sigma,
+                                 bias_x=req.bias_x, bias_y=req.bias_y, path="fused", stream=self.stream)
+        except TuError as e:
+            return f"error: {e}"
+        self.used += need
+        if not self.translate:
+            tu_market_set_translation(h, False)
+        if self.relax:
+            tu_market_set_relaxation(h, 0.0)
+        return h, need, False
+
+    def _solve_group(self, group, now_fn, results) -> list:
+        """Solve one group; returns the requests that found no room yet."""
+        made = []  # (req, handle, bytes, warm, admitted)
+        deferred = []
+        for req in group:
+            now = now_fn()
+            r = self._market(req)
+            if r == "wait":
+                deferred.append(req)
+                continue
+            if isinstance(r, str):
+                status = "invalid" if r.startswith("invalid") else "error"
+                self.stats["invalid" if status == "invalid" else "errors"] += 1
+                results[req.rid] = Server._failed(req, status, r.split(": ", 1)[-1], now)
+                continue
+            self.stats["admitted"] += 1
+            made.append((req, r[0], r[1], r[2], now))
+        if not made:
+            return deferred
+        self.stats["groups"] += 1
+        self.stats["largest_group"] = max(self.stats["largest_group"], len(made))
+        try:
+            b = tu_batch_create([x[1] for x in made], stream=self.stream)
+            try:
+                _, infos = tu_batch_solve(b, self.tol, self.max_sweeps, len(made), warm_start=True)
+            finally:
+                tu_batch_destroy(b)
+        except TuError as e:
+            for req, h, nbytes, warm, adm in made:
+                tu_market_destroy(h)
+                self.used -= nbytes
+                self.stats["errors"] += 1
+                results[req.rid] = Server._failed(req, "error", str(e), now_fn(), adm, 0, warm)
+            return deferred
+        for (req, h, nbytes, warm, adm), info in zip(made, infos):
+            N, M, _ = req.shape
+            k = min(self.k, M)
+            idx = np.empty((N, k), np.int32)
+            lm = np.empty((N, k), np.float32)
+            try:
+                tu_topk_partners(h, 0, k, 0, N, idx, lm)
+            except TuError as e:
+                tu_market_destroy(h)
+                self.used -= nbytes
+                results[req.rid] = Server._failed(req, "error", str(e), now_fn(), adm, info["sweeps"], warm)
+                continue
+            ok = info["residual_inf"] <= self.tol
+            results[req.rid] = SolveResult(rid=req.rid, arrival=req.arrival, admitted=adm, finished=now_fn(),
+                                           sweeps=info["sweeps"], residual=info["residual_inf"], converged=ok,
+                                           match_count=info["match_count"], warm=warm, topk_idx=idx,
+                                           topk_logmu=lm, status="ok" if ok else "not_converged")
+            if req.key is not None:
+                self.resident[req.key] = (h, req.shape, nbytes)
+            else:
+                tu_market_destroy(h)
+                self.used -= nbytes
+        return deferred
+
+    def run(self, requests: List[SolveRequest], realtime: bool = True) -> List[SolveResult]:
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        t0 = time.perf_counter()
+        now_fn = (lambda: time.perf_counter() - t0)
+        nxt = 0
+        pending: List[SolveRequest] = []
+        results: Dict[int, SolveResult] = {}
+        while len(results) < len(reqs):
+            now = now_fn()
+            while nxt < len(reqs) and (not realtime or reqs[nxt].arrival <= now):
+                req = reqs[nxt]
+                nxt += 1
+                why = validate(req)
+                if why is None and req.shape[2] > MAX_D_BATCHED:
+                    why = f"d = {req.shape[2]} exceeds the batched launch's limit of {MAX_D_BATCHED}"
+                if why is not None:
+                    self.stats["invalid"] += 1
+                    results[req.rid] = Server._failed(req, "invalid", why, now)
+                else:
+                    pending.append(req)
+            full = len(pending) >= self.max_batch
+            due = pending and (now - pending[0].arrival >= self.window or nxt == len(reqs) or not realtime)
+            if not (full or due):
+                time.sleep(0.0002)
+                continue
+            take, pending = pending[:self.max_batch], pending[self.max_batch:]
+            # a key may appear once per group (its market is one member)
+            seen, group, later = set(), [], []
+            for q in take:
+                if q.key is not None and q.key in seen:
+                    later.append(q)
+                else:
+                    seen.add(q.key)
+                    group.append(q)
+            for narrow in (True, False):
+                part = [q for q in group if (q.shape[2] <= 32) == narrow]
+                if part:
+                    later += self._solve_group(part, now_fn, results)
+            pending = sorted(later, key=lambda r: r.arrival) + pending
+        return [results[r.rid] for r in reqs]
+
+    def close(self):
+        while self._evict_one():
+            pass

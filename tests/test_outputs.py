@@ -186,3 +186,31 @@ def test_fused_topk_and_mu_full_size_sampled(gpu_lib):
         np.testing.assert_allclose(np.log(got), ref, rtol=0, atol=3e-5)
     finally:
         mkt.close()
+
+
+@pytest.mark.parametrize("path", ["fused", "dense"])
+def test_topk_into_host_buffers_larger_than_the_staging(gpu_lib, path):
+    """Ranked lists into host buffers whose two outputs together exceed the
+    market's staging buffer as its creation left it (513 x 257, d = 8, k = 10:
+    41 KB of outputs, 33 KB of staged factors): both views are taken from one
+    staging buffer sized for both, and the lists equal those written into
+    device buffers."""
+    tu = gpu_lib
+    mk = make_market(513, 257, 8, sigma=0.5, seed=5, bias_x=True, bias_y=True, n_kind="uniform1to3",
+                     m_kind="uniform1to3", dtype="fp32")
+    F, K, G, L = (np.ascontiguousarray(a, np.float32) for a in (mk.F, mk.K, mk.G, mk.L))
+    h = tu.tu_market_create(F, K, G, L, mk.n, mk.m, mk.sigma, bias_x=mk.bias_x, bias_y=mk.bias_y, path=path)
+    try:
+        tu.tu_ipfp_sweep(h, 5)
+        for side, rows in ((0, mk.N), (1, mk.M)):
+            idx_h = np.empty((rows, 10), np.int32)
+            lm_h = np.empty((rows, 10), np.float32)
+            tu.tu_topk_partners(h, side, 10, 0, rows, idx_h, lm_h)
+            idx_d = torch.empty((rows, 10), dtype=torch.int32, device="cuda")
+            lm_d = torch.empty((rows, 10), dtype=torch.float32, device="cuda")
+            tu.tu_topk_partners(h, side, 10, 0, rows, idx_d, lm_d)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(idx_h, idx_d.cpu().numpy())
+            np.testing.assert_array_equal(lm_h, lm_d.cpu().numpy())
+    finally:
+        tu.tu_market_destroy(h)

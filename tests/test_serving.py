@@ -139,3 +139,42 @@ def test_failures_stay_with_their_request(gpu_lib, tmp_path):
     lines = [json.loads(x) for x in log.read_text().splitlines()]
     assert sorted(x["rid"] for x in lines) == list(range(len(reqs)))
     assert {x["rid"]: x["status"] for x in lines} == {r.rid: r.status for r in res}
+
+
+def test_window_server_micro_batches(gpu_lib):
+    """The micro-batching server (WindowServer: requests of a window solved
+    together by one batched launch per half-sweep) answers every request with
+    the fixed point the stream-per-market server reaches: converged, match
+    counts within the residual's reach, the same top-10 partners wherever the
+    two solves' scores are separated; a re-solve warm-starts from the
+    resident market; d above the batched launch's limit is answered invalid."""
+    from paper_2411_19214_gb300 import serve
+    specs = SPECS + [(3000, 2500, 32)]
+    base = serve.Server(hbm_budget_bytes=8 << 30, tol=1e-6, max_sweeps=400, k=10)
+    ref = base.run(_requests(serve, specs), realtime=False)
+    base.close()
+    win = serve.WindowServer(hbm_budget_bytes=8 << 30, tol=1e-6, max_sweeps=400, k=10, max_batch=4)
+    reqs = _requests(serve, specs)
+    for r in reqs:
+        r.key = f"m{r.rid}"
+    wide = _requests(serve, [(100, 120, 96)], seed=77)[0]
+    wide.rid = len(reqs)
+    res = win.run(reqs + [wide], realtime=False)
+    # windows of 4 requests, each split by packed row length (d <= 32 or not):
+    # {0, 2} and {1, 3}, then {4, 5, 6}
+    assert win.stats["groups"] == 3 and win.stats["largest_group"] == 3
+    for a, b in zip(res[:len(specs)], ref):
+        assert a.status == "ok" and a.converged and b.converged and a.residual <= 1e-6
+        assert a.match_count == pytest.approx(b.match_count, rel=1e-5)
+        assert a.topk_idx.shape == b.topk_idx.shape
+        assert np.mean(a.topk_idx == b.topk_idx) > 0.99
+    assert res[-1].status == "invalid"
+    # a re-solve of the same markets: warm, far fewer sweeps
+    again = _requests(serve, specs)
+    for r in again:
+        r.key = f"m{r.rid}"
+    res2 = win.run(again, realtime=False)
+    win.close()
+    assert win.stats["warm"] == len(specs)
+    assert all(r.status == "ok" and r.warm for r in res2)
+    assert sum(r.sweeps for r in res2) < sum(r.sweeps for r in res[:len(specs)]) / 2

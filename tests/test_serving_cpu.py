@@ -28,8 +28,8 @@ def test_valid_request_passes():
     (dict(K=np.zeros((30, 7), np.float32)), "share one"),
     (dict(L=np.zeros((41, 8), np.float32)), "share one"),
     (dict(G=np.zeros((40, 9), np.float32), L=np.zeros((40, 9), np.float32)), "same d"),
-    (dict(F=np.zeros((30, 65), np.float32), K=np.zeros((30, 65), np.float32),
-          G=np.zeros((40, 65), np.float32), L=np.zeros((40, 65), np.float32)), "limit"),
+    (dict(F=np.zeros((30, 129), np.float32), K=np.zeros((30, 129), np.float32),
+          G=np.zeros((40, 129), np.float32), L=np.zeros((40, 129), np.float32)), "limit"),
     (dict(n=np.ones(29)), "one capacity per user"),
     (dict(m=np.r_[np.ones(39), 0.0]), "finite and > 0"),
     (dict(n=np.r_[np.ones(29), np.nan]), "finite and > 0"),
