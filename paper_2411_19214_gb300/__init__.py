@@ -224,8 +224,10 @@ def tu_market_create(F, K, G, L, n, m, sigma: float, *, bias_x=None, bias_y=None
     scale), or, with fscale_x / fscale_y (float32, N and M), uint8 e4m3 bytes
     quantized by the caller. "side": one power-of-two scale per side (float32
     factors; the faster FP8 kernel)."""
+    if fp8 is None:
+        fp8 = False
     if fp8 not in (False, True, "rows", "side"):
-        raise ValueError("fp8 must be False, True / 'rows' or 'side'")
+        raise ValueError("fp8 must be False / None, True / 'rows' or 'side'")
     lib = load()
     N, d = _shape(F)
     M, d2 = _shape(G)

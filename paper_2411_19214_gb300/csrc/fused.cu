@@ -460,10 +460,11 @@ __device__ __forceinline__ int item_begin(const FusedParams& p) {
   if constexpr (BATCH) return p.cta_start[blockIdx.x];
   return blockIdx.x;
 }
-template <bool BATCH>
+template <bool BATCH, bool SPLIT>
 __device__ __forceinline__ int item_end(const FusedParams& p) {
   if constexpr (BATCH) return p.cta_start[blockIdx.x + 1];
-  return p.num_own_tiles * p.split;
+  if constexpr (SPLIT) return p.num_own_tiles * p.split;
+  return p.num_own_tiles;
 }
 
 // An item of a single-market launch: own tile t and its partner tiles
@@ -471,7 +472,9 @@ __device__ __forceinline__ int item_end(const FusedParams& p) {
 struct Span {
   int t, s, jb, je;
 };
+template <bool SPLIT>
 __device__ __forceinline__ Span single_span(const FusedParams& p, int it) {
+  if constexpr (!SPLIT) return {it, 0, 0, p.num_partner_tiles};
   const int S = p.split;
   const int t = it / S, s = it - t * S;
   const int npt = p.num_partner_tiles;
@@ -498,11 +501,12 @@ __device__ __forceinline__ int item_step() {
 // for markets whose 256-row tiles would leave SMs idle: twice the CTAs, each
 // finishing its rows in about half the time. Every row's arithmetic is the
 // same as with 256-row tiles.
-template <int KB, int STAGES, int MODE, bool BATCH, int FMT, bool SMALL = false>
+template <int KB, int STAGES, int MODE, bool BATCH, int FMT, bool SMALL = false, bool SPLIT = false>
 __global__ void __launch_bounds__(kThreads, 1)
     k_fused_halfsweep(const __grid_constant__ CUtensorMap tm_own, const __grid_constant__ CUtensorMap tm_partner,
                       const FusedParams p) {
   static_assert(!BATCH || MODE == kModeSweep, "batched launches run half-sweeps only");
+  static_assert(!SPLIT || (MODE == kModeSweep && !BATCH), "partner splits are single-market half-sweeps");
   constexpr bool kSweepLike = MODE == kModeSweep || MODE == kModeSweepShift;
   static_assert(!(BATCH && SMALL), "batched launches use 256-row own tiles");
   constexpr int kOwn = SMALL ? kFusedOwnRows / 2 : kFusedOwnRows;  // rows of an own tile
@@ -592,7 +596,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int s = 0; s < kGSlots; ++s) garmed[s] = 0;
       const BatchDesc* prev = nullptr;
       bool ok = true;
-      for (int it = item_begin<BATCH>(p); it < item_end<BATCH>(p) && ok; it += item_step<BATCH>()) {
+      for (int it = item_begin<BATCH>(p); it < item_end<BATCH, SPLIT>(p) && ok; it += item_step<BATCH>()) {
         const BatchDesc* bd = nullptr;
         int t, jb = 0, je;
         if constexpr (BATCH) {
@@ -606,7 +610,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             prev = bd;
           }
         } else {
-          const Span sp = single_span(p, it);
+          const Span sp = single_span<SPLIT>(p, it);
           t = sp.t;
           jb = sp.jb;
           je = sp.je;
@@ -680,12 +684,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       int stage = 0, buf = 0, ab = 0;
       uint32_t phase = 0, tphase = 0, a_phase = 0;
       bool ok = true;
-      for (int it = item_begin<BATCH>(p); it < item_end<BATCH>(p) && ok; it += item_step<BATCH>()) {
+      for (int it = item_begin<BATCH>(p); it < item_end<BATCH, SPLIT>(p) && ok; it += item_step<BATCH>()) {
         int jb = 0, je;
         if constexpr (BATCH) {
           je = batch_item(p, it).d->num_partner_tiles;
         } else {
-          const Span sp = single_span(p, it);
+          const Span sp = single_span<SPLIT>(p, it);
           jb = sp.jb;
           je = sp.je;
         }
@@ -776,7 +780,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int tcnt = 0;
     float thr = -INFINITY;
     int tile_iter = 0;
-    for (int it = item_begin<BATCH>(p); it < item_end<BATCH>(p) && ok; it += item_step<BATCH>(), ++tile_iter) {
+    for (int it = item_begin<BATCH>(p); it < item_end<BATCH, SPLIT>(p) && ok; it += item_step<BATCH>(), ++tile_iter) {
       const BatchDesc* bd = nullptr;
       int t, split_s = 0, jb = 0, je;
       if constexpr (BATCH) {
@@ -785,7 +789,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         t = w.t;
         je = bd->num_partner_tiles;
       } else {
-        const Span sp = single_span(p, it);
+        const Span sp = single_span<SPLIT>(p, it);
         t = sp.t;
         split_s = sp.s;
         jb = sp.jb;
@@ -988,8 +992,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t row = p.row0 + r;
         // the row's sum as three FP32 parts (a split: summed over its ranges)
         float s_hi = sum, s_lo = -comp, s_o = other;
-        if constexpr (MODE == kModeSweep && !BATCH) {
-          if (p.split > 1) {
+        if constexpr (SPLIT) {
+          {
             // this range's partial; the warp that completes the (tile, 32-row
             // block) sums all ranges in order and updates the rows (no wait:
             // the other warps of this block move on)
@@ -1171,46 +1175,49 @@ constexpr int kSmemTotal =
 // Instantiations that exist: batched launches take one or two k blocks
 // (e4m3: one); the shared-memory ranked lists leave too little room for
 // partner stages beside a four-block own tile (those lists use kModeTopK).
-template <int KB, int MODE, bool BATCH, int FMT>
-constexpr bool kBuilt = !(BATCH && (KB == 4 || (FMT != kFmtBF16 && KB != 1))) && !(MODE == kModeTopKShared && KB == 4);
+// SPLIT: the partner-split instantiation (single-market half-sweeps with
+// tu_market_set_split > 1); the default kernel carries none of its code.
+template <int KB, int MODE, bool BATCH, int FMT, bool SPLIT = false>
+constexpr bool kBuilt = !(BATCH && (KB == 4 || (FMT != kFmtBF16 && KB != 1))) &&
+                        !(MODE == kModeTopKShared && KB == 4) && !(SPLIT && (MODE != kModeSweep || BATCH));
 
-template <int KB, int MODE, bool BATCH, int FMT = kFmtBF16, bool SMALL = false>
+template <int KB, int MODE, bool BATCH, int FMT = kFmtBF16, bool SMALL = false, bool SPLIT = false>
 cudaError_t launch_kernel(const CUtensorMap& own, const CUtensorMap& partner, const FusedParams& p, int grid,
                           cudaStream_t stream) {
-  if constexpr (!kBuilt<KB, MODE, BATCH, FMT>) {
+  if constexpr (!kBuilt<KB, MODE, BATCH, FMT, SPLIT>) {
     return cudaErrorNotSupported;
   } else {
     static_assert(kStages<KB, MODE, FMT> >= 2, "at least two partner stages");
     static_assert(kSmemTotal<KB, MODE, FMT> <= kSmemLimit, "shared memory budget");
-    k_fused_halfsweep<KB, kStages<KB, MODE, FMT>, MODE, BATCH, FMT, SMALL>
+    k_fused_halfsweep<KB, kStages<KB, MODE, FMT>, MODE, BATCH, FMT, SMALL, SPLIT>
         <<<grid, kThreads, kSmemTotal<KB, MODE, FMT>, stream>>>(own, partner, p);
     return cudaGetLastError();
   }
 }
 
-template <int KB, int MODE, bool BATCH, int FMT, bool SMALL>
+template <int KB, int MODE, bool BATCH, int FMT, bool SMALL, bool SPLIT = false>
 cudaError_t set_attribute_one() {
-  if constexpr (!kBuilt<KB, MODE, BATCH, FMT>) {
+  if constexpr (!kBuilt<KB, MODE, BATCH, FMT, SPLIT>) {
     return cudaSuccess;
   } else {
-    return cudaFuncSetAttribute(k_fused_halfsweep<KB, kStages<KB, MODE, FMT>, MODE, BATCH, FMT, SMALL>,
+    return cudaFuncSetAttribute(k_fused_halfsweep<KB, kStages<KB, MODE, FMT>, MODE, BATCH, FMT, SMALL, SPLIT>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal<KB, MODE, FMT>);
   }
 }
 
-template <int MODE, bool BATCH, bool SMALL, int FMT>
+template <int MODE, bool BATCH, bool SMALL, int FMT, bool SPLIT = false>
 cudaError_t set_attributes_fmt() {
-  cudaError_t e = set_attribute_one<1, MODE, BATCH, FMT, SMALL>();
-  if (e == cudaSuccess) e = set_attribute_one<2, MODE, BATCH, FMT, SMALL>();
-  if (e == cudaSuccess) e = set_attribute_one<4, MODE, BATCH, FMT, SMALL>();
+  cudaError_t e = set_attribute_one<1, MODE, BATCH, FMT, SMALL, SPLIT>();
+  if (e == cudaSuccess) e = set_attribute_one<2, MODE, BATCH, FMT, SMALL, SPLIT>();
+  if (e == cudaSuccess) e = set_attribute_one<4, MODE, BATCH, FMT, SMALL, SPLIT>();
   return e;
 }
 
-template <int MODE, bool BATCH, bool SMALL>
+template <int MODE, bool BATCH, bool SMALL, bool SPLIT = false>
 cudaError_t set_attributes_variant() {
-  cudaError_t e = set_attributes_fmt<MODE, BATCH, SMALL, kFmtBF16>();
-  if (e == cudaSuccess) e = set_attributes_fmt<MODE, BATCH, SMALL, kFmtE4M3Side>();
-  if (e == cudaSuccess) e = set_attributes_fmt<MODE, BATCH, SMALL, kFmtE4M3Rows>();
+  cudaError_t e = set_attributes_fmt<MODE, BATCH, SMALL, kFmtBF16, SPLIT>();
+  if (e == cudaSuccess) e = set_attributes_fmt<MODE, BATCH, SMALL, kFmtE4M3Side, SPLIT>();
+  if (e == cudaSuccess) e = set_attributes_fmt<MODE, BATCH, SMALL, kFmtE4M3Rows, SPLIT>();
   return e;
 }
 
@@ -1218,6 +1225,10 @@ template <int MODE, bool BATCH>
 cudaError_t set_attributes_mode() {
   cudaError_t e = set_attributes_variant<MODE, BATCH, false>();
   if (e == cudaSuccess && !BATCH) e = set_attributes_variant<MODE, false, true>();
+  if (MODE == kModeSweep && !BATCH) {
+    if (e == cudaSuccess) e = set_attributes_variant<MODE, false, false, true>();
+    if (e == cudaSuccess) e = set_attributes_variant<MODE, false, true, true>();
+  }
   return e;
 }
 
@@ -1258,28 +1269,36 @@ int fmt_of(int dtype) {
   return dtype == TU_DTYPE_FP8E4M3 ? kFmtE4M3Rows : (dtype == TU_DTYPE_FP8E4M3_SIDE ? kFmtE4M3Side : kFmtBF16);
 }
 
-template <int MODE, bool BATCH, bool SMALL, int FMT>
+template <int MODE, bool BATCH, bool SMALL, int FMT, bool SPLIT>
 cudaError_t launch_fmt(int kb, const CUtensorMap& own, const CUtensorMap& partner, const FusedParams& p, int grid,
                        cudaStream_t stream) {
-  if (kb == 1) return launch_kernel<1, MODE, BATCH, FMT, SMALL>(own, partner, p, grid, stream);
-  if (kb == 2) return launch_kernel<2, MODE, BATCH, FMT, SMALL>(own, partner, p, grid, stream);
-  if (kb == 4) return launch_kernel<4, MODE, BATCH, FMT, SMALL>(own, partner, p, grid, stream);
+  if (kb == 1) return launch_kernel<1, MODE, BATCH, FMT, SMALL, SPLIT>(own, partner, p, grid, stream);
+  if (kb == 2) return launch_kernel<2, MODE, BATCH, FMT, SMALL, SPLIT>(own, partner, p, grid, stream);
+  if (kb == 4) return launch_kernel<4, MODE, BATCH, FMT, SMALL, SPLIT>(own, partner, p, grid, stream);
   return cudaErrorNotSupported;
 }
 
-template <int MODE, bool BATCH = false, bool SMALL = false>
+template <int MODE, bool BATCH = false, bool SMALL = false, bool SPLIT = false>
 cudaError_t launch_variant(int64_t kp, int fmt, const CUtensorMap& own, const CUtensorMap& partner,
                            const FusedParams& p, int grid, cudaStream_t stream) {
   const int kb = k_blocks(kp, fmt);
-  if (fmt == kFmtE4M3Rows) return launch_fmt<MODE, BATCH, SMALL, kFmtE4M3Rows>(kb, own, partner, p, grid, stream);
-  if (fmt == kFmtE4M3Side) return launch_fmt<MODE, BATCH, SMALL, kFmtE4M3Side>(kb, own, partner, p, grid, stream);
-  return launch_fmt<MODE, BATCH, SMALL, kFmtBF16>(kb, own, partner, p, grid, stream);
+  if (fmt == kFmtE4M3Rows)
+    return launch_fmt<MODE, BATCH, SMALL, kFmtE4M3Rows, SPLIT>(kb, own, partner, p, grid, stream);
+  if (fmt == kFmtE4M3Side)
+    return launch_fmt<MODE, BATCH, SMALL, kFmtE4M3Side, SPLIT>(kb, own, partner, p, grid, stream);
+  return launch_fmt<MODE, BATCH, SMALL, kFmtBF16, SPLIT>(kb, own, partner, p, grid, stream);
 }
 
 // small: 128-row own tiles (single-market launches only; see use_small_tiles)
 template <int MODE, bool BATCH = false>
 cudaError_t launch_any(int64_t kp, int fmt, const CUtensorMap& own, const CUtensorMap& partner,
                        const FusedParams& p, int grid, cudaStream_t stream, bool small = false) {
+  if constexpr (!BATCH && MODE == kModeSweep) {
+    if (p.split > 1) {
+      if (small) return launch_variant<MODE, false, true, true>(kp, fmt, own, partner, p, grid, stream);
+      return launch_variant<MODE, false, false, true>(kp, fmt, own, partner, p, grid, stream);
+    }
+  }
   if constexpr (!BATCH) {
     if (small) return launch_variant<MODE, false, true>(kp, fmt, own, partner, p, grid, stream);
   }

@@ -153,3 +153,20 @@ def test_footprint_counts_the_documented_buffers(lib):
         assert fused - (N + M) * 2 * d * 2 - 2 * max(N, M) * d * 4 <= 300 * (N + M) + (1 << 20)
     assert tu.tu_market_footprint(0, 5, 3, "fused") == 0
     assert tu.tu_market_footprint(5, 5, 0, "dense") == 0
+
+
+def test_binding_fp8_argument(lib):
+    """fp8 = None or False is a BF16/FP32 market, True / "rows" / "side" an
+    FP8 one (float32 factors); anything else is refused before the library.
+    Without a GPU a well-formed call reaches the library, which answers
+    TU_ERR_CUDA (or TU_ERR_UNSUPPORTED for a device it was not built for)."""
+    F = np.zeros((4, 3), np.float32)
+    for v in (None, False, True, "rows", "side"):
+        with pytest.raises(tu.TuError) as e:
+            tu.tu_market_create(F, F, F, F, np.ones(4), np.ones(4), 1.0, fp8=v)
+        assert e.value.status in (tu.TU_ERR_CUDA, tu.TU_ERR_UNSUPPORTED)
+    with pytest.raises(ValueError):
+        tu.tu_market_create(F, F, F, F, np.ones(4), np.ones(4), 1.0, fp8="per-tile")
+    with pytest.raises(TypeError):
+        tu.tu_market_create(F.astype(np.uint16), F.astype(np.uint16), F.astype(np.uint16), F.astype(np.uint16),
+                            np.ones(4), np.ones(4), 1.0, fp8=True)
