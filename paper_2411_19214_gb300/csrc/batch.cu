@@ -101,8 +101,12 @@ __global__ void __launch_bounds__(kPrepThreads) k_batch_prep(const BatchDesc* __
   const BatchDesc& d = desc[list[blockIdx.x]];
   const double top = d.st[kStLmax + (1 - d.own_side)];  // not written by prep_scalars
   if (threadIdx.x == 0) prep_scalars(d.st, d.own_side, sweep && d.translate);
-  for (int64_t i = threadIdx.x; i < d.partner_rows_pad; i += blockDim.x)
-    d.g[i] = i < d.partner_rows ? (float)((d.partner_ell[i] - top) * 1.4426950408889634) : -INFINITY;
+  const float inv_c = 1.0f / d.c;  // (the single-market preparation's 1 / c, rounded alike)
+  for (int64_t i = threadIdx.x; i < d.partner_rows_pad; i += blockDim.x) {
+    const float v = i < d.partner_rows ? (float)((d.partner_ell[i] - top) * 1.4426950408889634) : -INFINITY;
+    d.g[i] = v;
+    if (d.gfold != nullptr) write_fold_row(reinterpret_cast<uint4*>(d.gfold), i, v, inv_c);
+  }
 }
 
 // FP64 reduction of a listed market's per-tile partials into its result slots;
@@ -599,6 +603,7 @@ tu_status tu_batch_create(const tu_market_t* markets, int count, void* stream, t
       d.c = m->cmul;
       d.fs_own = own.fs;
       d.fs_par = par.fs;
+      d.gfold = par.fold;
       b->own_tiles[side][i] = d.num_own_tiles;
       b->partner_tiles[side][i] = d.num_partner_tiles;
       slot += d.num_own_tiles;

@@ -116,6 +116,11 @@ struct FusedParams {
   int split;
   float4* part;
   int* split_cnt;
+  // folded g (BF16 half-sweeps, kp = 64): the partner side's g / c as the
+  // K = 16 operand of one extra MMA per chain and partner tile, 4 KB per
+  // partner tile of 128 rows in the unswizzled K-major layout (written by the
+  // preparation kernel)
+  const uint8_t* gfold;
 };
 
 // Own-tile buffers: with one 128-byte k block per row the next own tile is
@@ -137,9 +142,21 @@ enum : int { kFmtBF16 = 0, kFmtE4M3Side = 1, kFmtE4M3Rows = 2 };
 //                [per-row scales: scale ring 8 x 512 B][barriers and flags: 512 B]
 //                [reduction: 512 B][row hand-over: 2 x 256 floats]
 constexpr int kTailBytes = 512 + 512 + 2 * kFusedOwnRows * 4;
-constexpr int smem_bytes(int KB, int fmt, int stages) {
-  return 1024 /*alignment slack*/ + (KB == 1 ? 2 : 1) * KB * kOwnBytesPerKB +
-         stages * kbs_for(KB) * kPartnerBytesPerKB + kGSlots * kGBytes * (fmt == kFmtE4M3Rows ? 2 : 1) + kTailBytes;
+// folded g: the partner tile's K = 16 operand rides in its (last) stage, the
+// own side's constant operand (ones in columns 0-2) is one tile of its own.
+// Taken for rows of one k block (d <= 32), where the tensor pipe has room for
+// a fifth MMA per chain and the epilogue sheds its g loads: batched d = 32
+// half-sweep 5.44 -> 5.12 ms, a 1e5 d = 32 sweep 3.54 -> 3.37 ms; with two k
+// blocks (d = 33..64) the ninth MMA costs more than it saves (1e6 d = 64
+// half-sweep 184.5 -> 187.1 ms), so those keep g in the shared ring.
+constexpr int kFoldBytes = kFusedPartnerRows * 32;
+constexpr bool fold_for(int KB, int MODE, bool BATCH, int fmt, bool nofold) {
+  return MODE == kModeSweep && fmt == kFmtBF16 && KB == 1 && !nofold;
+}
+constexpr int stage_bytes(int KB, bool fold) { return kbs_for(KB) * kPartnerBytesPerKB + (fold ? kFoldBytes : 0); }
+constexpr int smem_bytes(int KB, int fmt, int stages, bool fold = false) {
+  return 1024 /*alignment slack*/ + (KB == 1 ? 2 : 1) * KB * kOwnBytesPerKB + stages * stage_bytes(KB, fold) +
+         (fold ? kFoldBytes : 0) + kGSlots * kGBytes * (fmt == kFmtE4M3Rows ? 2 : 1) + kTailBytes;
 }
 
 __device__ __forceinline__ void raise_error(int* err, volatile int* abort_flag, int code) {
@@ -235,6 +252,25 @@ __device__ __forceinline__ void pair_step_scaled_shift(uint64_t& acc, uint32_t p
       "add.rn.f32x2 %0, %0, e;\n\t}"
       : "+l"(acc)
       : "r"(phi0), "r"(phi1), "f"(g0), "f"(g1), "f"(f0), "f"(f1), "l"(cc), "l"(ss));
+}
+
+// Folded g: acc += (ex2(D0 * c), ex2(D1 * c)), D = phi + g / c from the MMA.
+__device__ __forceinline__ void pair_step_fold(uint64_t& acc, uint32_t d0, uint32_t d1, uint64_t cc) {
+  asm("{\n\t.reg .b64 a, t, e;\n\t.reg .f32 t0, t1, e0, e1;\n\t"
+      "mov.b64 a, {%1, %2};\n\t"
+      "mul.rn.f32x2 t, a, %3;\n\t"
+      "mov.b64 {t0, t1}, t;\n\t"
+      "ex2.approx.ftz.f32 e0, t0;\n\t"
+      "ex2.approx.ftz.f32 e1, t1;\n\t"
+      "mov.b64 e, {e0, e1};\n\t"
+      "add.rn.f32x2 %0, %0, e;\n\t}"
+      : "+l"(acc)
+      : "r"(d0), "r"(d1), "l"(cc));
+}
+
+__device__ __forceinline__ void chunk_sum_fold(const uint32_t (&v)[32], uint64_t cc, uint64_t (&acc)[4]) {
+#pragma unroll
+  for (int i = 0; i < 16; ++i) pair_step_fold(acc[i & 3], v[2 * i], v[2 * i + 1], cc);
 }
 
 // phi of column i of a chunk, times the partner row's scale (e4m3 factors
@@ -501,7 +537,8 @@ __device__ __forceinline__ int item_step() {
 // for markets whose 256-row tiles would leave SMs idle: twice the CTAs, each
 // finishing its rows in about half the time. Every row's arithmetic is the
 // same as with 256-row tiles.
-template <int KB, int STAGES, int MODE, bool BATCH, int FMT, bool SMALL = false, bool SPLIT = false>
+template <int KB, int STAGES, int MODE, bool BATCH, int FMT, bool SMALL = false, bool SPLIT = false,
+          bool NOFOLD = false>
 __global__ void __launch_bounds__(kThreads, 1)
     k_fused_halfsweep(const __grid_constant__ CUtensorMap tm_own, const __grid_constant__ CUtensorMap tm_partner,
                       const FusedParams p) {
@@ -517,12 +554,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int KBS = kbs_for(KB);   // k blocks per partner stage
   constexpr int SPT = KB / KBS;      // stages per partner tile
   constexpr int XB = F8 ? 128 : kKBlock;  // elements per 128-byte k block (TMA x coordinate step)
+  constexpr bool FOLD = fold_for(KB, MODE, BATCH, FMT, NOFOLD);  // g added by an extra MMA
+  constexpr int SB = stage_bytes(KB, FOLD);                        // bytes per partner stage
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_u32 = smem_u32(smem_raw);
   uint8_t* smem = smem_raw + (((raw_u32 + 1023u) & ~1023u) - raw_u32);
   uint8_t* sA = smem;
   uint8_t* sB = smem + ABUF * KB * kOwnBytesPerKB;
-  float* sG = reinterpret_cast<float*>(sB + STAGES * KBS * kPartnerBytesPerKB);
+  uint8_t* sOnes = sB + STAGES * SB;  // folded g: the own side's constant operand
+  float* sG = reinterpret_cast<float*>(sOnes + (FOLD ? kFoldBytes : 0));
   float* sF = sG + kGSlots * kFusedPartnerRows;  // per-row scales: partner scale ring
   uint64_t* bars =
       reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(sG) + kGSlots * kGBytes * (RS ? 2 : 1));
@@ -580,6 +620,17 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) {
     tmem_alloc(tmem_slot, kTmemCols);
     tmem_relinquish();
+  }
+  if constexpr (FOLD) {
+    // the own side's operand of the extra MMA: BF16 ones in columns 0-2 of
+    // every row (16-byte chunk q holds columns 0-7 when (q / 8) is even),
+    // made visible to the tensor core's (async) proxy
+    if (threadIdx.x < kFoldBytes / 16) {
+      const bool cols0_7 = ((threadIdx.x / 8) % 2) == 0;
+      reinterpret_cast<uint4*>(sOnes)[threadIdx.x] =
+          cols0_7 ? make_uint4(0x3F803F80u, 0x00003F80u, 0u, 0u) : make_uint4(0u, 0u, 0u, 0u);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   tc_fence_before();
   __syncthreads();
@@ -639,10 +690,14 @@ __global__ void __launch_bounds__(kThreads, 1)
               ok = false;
               break;
             }
-            mbar_arrive_expect_tx(&full[stage], KBS * kPartnerBytesPerKB);
+            const bool fold_here = FOLD && sp == SPT - 1;  // the tile's g operand rides in its last stage
+            mbar_arrive_expect_tx(&full[stage], KBS * kPartnerBytesPerKB + (fold_here ? kFoldBytes : 0));
             for (int kb = 0; kb < KBS; ++kb)
-              tma_load_2d(sB + (stage * KBS + kb) * kPartnerBytesPerKB, map_partner, &full[stage],
+              tma_load_2d(sB + stage * SB + kb * kPartnerBytesPerKB, map_partner, &full[stage],
                           (sp * KBS + kb) * XB, (int)(p.col0 + (int64_t)j * kFusedPartnerRows));
+            if (fold_here)
+              bulk_load(sB + stage * SB + KBS * kPartnerBytesPerKB,
+                        (BATCH ? bd->gfold : p.gfold) + (int64_t)j * kFoldBytes, kFoldBytes, &full[stage]);
             ++armed[stage];
             if (++stage == STAGES) {
               stage = 0;
@@ -715,7 +770,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               break;
             }
             tc_fence_after();
-            const uint32_t b0 = smem_u32(sB + stage * KBS * kPartnerBytesPerKB);
+            const uint32_t b0 = smem_u32(sB + stage * SB);
 #pragma unroll
             for (int h = 0; h < (SMALL ? 1 : 2); ++h) {
               const uint32_t d_tmem = tmem_base + (uint32_t)(buf * 256 + h * 128);
@@ -731,6 +786,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 } else {
                   umma_bf16(d_tmem, adesc, bdesc, idesc, accum);
                 }
+              }
+              if constexpr (FOLD) {
+                // D += ones x (g / c): every row gets the partner column's g / c
+                if (sp == SPT - 1)
+                  umma_bf16(d_tmem, sdesc_none(smem_u32(sOnes), 128, 256),
+                            sdesc_none(b0 + KBS * kPartnerBytesPerKB, 128, 256), idesc, 1u);
               }
             }
             umma_commit(&empty[stage]);
@@ -861,7 +922,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           tmem_ld_issue(taddr, va);
           tmem_ld_wait(va);
           tmem_ld_issue(taddr + 32, vb);
-          if constexpr (MODE == kModeSweep) chunk_sum<RS>(va, gs4, fs4, cc, acc);
+          if constexpr (FOLD) chunk_sum_fold(va, cc, acc);
+          if constexpr (MODE == kModeSweep && !FOLD) chunk_sum<RS>(va, gs4, fs4, cc, acc);
           if constexpr (MODE == kModeSweepShift) chunk_sum_shift<RS>(va, gs4, fs4, cc, rshift, acc);
           if constexpr (MODE == kModeRowMax) chunk_max<RS>(va, gsf, fsf, crow, rmax);
           if constexpr (MODE == kModeTopK) chunk_topk<RS>(va, gsf, fsf, crow, colbase, p.k, tv, ti, &tcnt, thr);
@@ -875,7 +937,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[buf]);
         if (!idle) {
-          if constexpr (MODE == kModeSweep) chunk_sum<RS>(vb, gs4 + 8, fs4 + 8, cc, acc);
+          if constexpr (FOLD) chunk_sum_fold(vb, cc, acc);
+          if constexpr (MODE == kModeSweep && !FOLD) chunk_sum<RS>(vb, gs4 + 8, fs4 + 8, cc, acc);
           if constexpr (MODE == kModeSweepShift) chunk_sum_shift<RS>(vb, gs4 + 8, fs4 + 8, cc, rshift, acc);
           if constexpr (MODE == kModeRowMax) chunk_max<RS>(vb, gsf + 32, fsf + 32, crow, rmax);
           if constexpr (MODE == kModeTopK)
@@ -1158,50 +1221,59 @@ constexpr int kSmemLimit = 232448;  // dynamic shared memory per CTA (227 KB)
 // g (and scale) rings, the tail and (kModeTopKShared) the ranked lists, at
 // most 6 whole tiles (one k block per row), 4 (two) or 5 single k blocks
 // (four: 1.25 partner tiles in flight).
-constexpr int stages_for(int KB, int MODE, int fmt) {
-  const int fixed = smem_bytes(KB, fmt, 0) + (MODE == kModeTopKShared ? kTopKListBytes : 0);
-  const int fit = (kSmemLimit - fixed) / (kbs_for(KB) * kPartnerBytesPerKB);
+constexpr int stages_for(int KB, int MODE, int fmt, bool fold) {
+  const int fixed = smem_bytes(KB, fmt, 0, fold) + (MODE == kModeTopKShared ? kTopKListBytes : 0);
+  const int fit = (kSmemLimit - fixed) / stage_bytes(KB, fold);
   const int cap = KB == 1 ? 6 : (KB == 2 ? 4 : 5);
   return fit < cap ? fit : cap;
 }
 
-template <int KB, int MODE, int FMT>
-constexpr int kStages = stages_for(KB, MODE, FMT);
+template <int KB, int MODE, int FMT, bool FOLD>
+constexpr int kStages = stages_for(KB, MODE, FMT, FOLD);
 
-template <int KB, int MODE, int FMT>
+template <int KB, int MODE, int FMT, bool FOLD>
 constexpr int kSmemTotal =
-    smem_bytes(KB, FMT, kStages<KB, MODE, FMT>) + (MODE == kModeTopKShared ? kTopKListBytes : 0);
+    smem_bytes(KB, FMT, kStages<KB, MODE, FMT, FOLD>, FOLD) + (MODE == kModeTopKShared ? kTopKListBytes : 0);
 
 // Instantiations that exist: batched launches take one or two k blocks
 // (e4m3: one); the shared-memory ranked lists leave too little room for
 // partner stages beside a four-block own tile (those lists use kModeTopK).
 // SPLIT: the partner-split instantiation (single-market half-sweeps with
 // tu_market_set_split > 1); the default kernel carries none of its code.
-template <int KB, int MODE, bool BATCH, int FMT, bool SPLIT = false>
+// NOFOLD: the BF16 half-sweep with g from the shared ring instead of the
+// extra MMA, for callers without the folded operand (the allocation-free
+// entry point).
+template <int KB, int MODE, bool BATCH, int FMT, bool SPLIT = false, bool SMALL = false, bool NOFOLD = false>
 constexpr bool kBuilt = !(BATCH && (KB == 4 || (FMT != kFmtBF16 && KB != 1))) &&
-                        !(MODE == kModeTopKShared && KB == 4) && !(SPLIT && (MODE != kModeSweep || BATCH));
+                        !(MODE == kModeTopKShared && KB == 4) && !(SPLIT && (MODE != kModeSweep || BATCH)) &&
+                        !(NOFOLD && (!fold_for(KB, MODE, BATCH, FMT, false) || SPLIT || SMALL));
 
-template <int KB, int MODE, bool BATCH, int FMT = kFmtBF16, bool SMALL = false, bool SPLIT = false>
+template <int KB, int MODE, bool BATCH, int FMT = kFmtBF16, bool SMALL = false, bool SPLIT = false,
+          bool NOFOLD = false>
 cudaError_t launch_kernel(const CUtensorMap& own, const CUtensorMap& partner, const FusedParams& p, int grid,
                           cudaStream_t stream) {
-  if constexpr (!kBuilt<KB, MODE, BATCH, FMT, SPLIT>) {
+  if constexpr (!kBuilt<KB, MODE, BATCH, FMT, SPLIT, SMALL, NOFOLD>) {
     return cudaErrorNotSupported;
   } else {
-    static_assert(kStages<KB, MODE, FMT> >= 2, "at least two partner stages");
-    static_assert(kSmemTotal<KB, MODE, FMT> <= kSmemLimit, "shared memory budget");
-    k_fused_halfsweep<KB, kStages<KB, MODE, FMT>, MODE, BATCH, FMT, SMALL, SPLIT>
-        <<<grid, kThreads, kSmemTotal<KB, MODE, FMT>, stream>>>(own, partner, p);
+    constexpr bool FD = fold_for(KB, MODE, BATCH, FMT, NOFOLD);
+    static_assert(kStages<KB, MODE, FMT, FD> >= 2, "at least two partner stages");
+    static_assert(kSmemTotal<KB, MODE, FMT, FD> <= kSmemLimit, "shared memory budget");
+    if (FD && !BATCH && p.gfold == nullptr) return cudaErrorInvalidValue;  // the folded operand must be prepared
+    k_fused_halfsweep<KB, kStages<KB, MODE, FMT, FD>, MODE, BATCH, FMT, SMALL, SPLIT, NOFOLD>
+        <<<grid, kThreads, kSmemTotal<KB, MODE, FMT, FD>, stream>>>(own, partner, p);
     return cudaGetLastError();
   }
 }
 
-template <int KB, int MODE, bool BATCH, int FMT, bool SMALL, bool SPLIT = false>
+template <int KB, int MODE, bool BATCH, int FMT, bool SMALL, bool SPLIT = false, bool NOFOLD = false>
 cudaError_t set_attribute_one() {
-  if constexpr (!kBuilt<KB, MODE, BATCH, FMT, SPLIT>) {
+  if constexpr (!kBuilt<KB, MODE, BATCH, FMT, SPLIT, SMALL, NOFOLD>) {
     return cudaSuccess;
   } else {
-    return cudaFuncSetAttribute(k_fused_halfsweep<KB, kStages<KB, MODE, FMT>, MODE, BATCH, FMT, SMALL, SPLIT>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal<KB, MODE, FMT>);
+    constexpr bool FD = fold_for(KB, MODE, BATCH, FMT, NOFOLD);
+    return cudaFuncSetAttribute(
+        k_fused_halfsweep<KB, kStages<KB, MODE, FMT, FD>, MODE, BATCH, FMT, SMALL, SPLIT, NOFOLD>,
+        cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemTotal<KB, MODE, FMT, FD>);
   }
 }
 
@@ -1241,6 +1313,8 @@ cudaError_t set_kernel_attributes_now() {
   if (e == cudaSuccess) e = set_attributes_mode<kModeSweep, true>();
   if (e == cudaSuccess) e = set_attributes_mode<kModeRowMax, false>();
   if (e == cudaSuccess) e = set_attributes_mode<kModeSweepShift, false>();
+  // the allocation-free entry point's unfolded half-sweep (rows of one k block)
+  if (e == cudaSuccess) e = set_attribute_one<1, kModeSweep, false, kFmtBF16, false, false, true>();
   return e;
 }
 
@@ -1378,6 +1452,7 @@ cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int upd
   p.omega = m->omega_dev;
   p.fs_own = own.fs;
   p.fs_par = partner.fs;
+  p.gfold = partner.fold;
   if (whole && !m->wide && m->split > 1 && m->split_part != nullptr) {
     // partner split: at most one range per partner tile
     p.split = m->split < p.num_partner_tiles ? m->split : p.num_partner_tiles;
@@ -1467,6 +1542,9 @@ cudaError_t launch_fused_halfsweep_raw(const FusedRaw& r, cudaStream_t stream, i
   p.update = 1;
   const int grid = grid_for_tiles(p.num_own_tiles, num_sms);
   *nparts_out = grid;
+  // (no folded operand here: the instantiation with g from the shared ring)
+  if (r.kp == kKBlock) return launch_kernel<1, kModeSweep, false, kFmtBF16, false, false, true>(own_map, partner_map, p,
+                                                                                              grid, stream);
   return launch_any<kModeSweep>(r.kp, kFmtBF16, own_map, partner_map, p, grid, stream);
 }
 

@@ -289,6 +289,8 @@ tu_status side_alloc(tu_market* m, Side& s, int64_t rows, bool has_bias) {
     TU_TRY(dev_alloc(m, &s.fs, s.rows_pad));
   } else if (m->path == TU_PATH_FUSED) {
     TU_TRY(dev_alloc(m, &s.fac16, (size_t)rows * m->kp));
+    // the partner tiles' g / c operand of the fused kernel's extra MMA
+    if (m->kp == kKBlock) TU_TRY(dev_alloc(m, &s.fold, (size_t)s.rows_pad * 32));
   } else {
     TU_TRY(dev_alloc(m, &s.fac32, (size_t)rows * m->kp));
   }
@@ -305,6 +307,7 @@ void side_free(tu_market* m, Side& s) {
   dev_free(m, s.fac16);
   dev_free(m, s.fac8);
   dev_free(m, s.fs);
+  dev_free(m, s.fold);
   dev_free(m, s.fac32);
   s = Side();
 }
@@ -1268,6 +1271,7 @@ int64_t tu_market_footprint(int64_t N, int64_t M, int64_t d, int path) {
   bytes += 2 * (N > M ? N : M) * d * 4;
   if (path == TU_PATH_FUSED) {
     bytes += (N + M) * kp * 2 + (np > mp ? np : mp) * 4;  // factors, per-row shifts
+    if (kp == kKBlock) bytes += (np + mp) * 32;              // the extra MMA's g / c operand
   } else {
     bytes += (N + M) * kp * 4 + N * round_up(M, 4) * 4 + M * round_up(N, 4) * 4;
   }

@@ -224,7 +224,8 @@ __global__ void k_row_norm_max(const float* __restrict__ f32, const __nv_bfloat1
 // the partner shift it adds back and the own offset). No other thread reads
 // the scalars it writes.
 __global__ void k_prep(const double* __restrict__ ell, int64_t rows, int64_t rows_pad, double* __restrict__ st,
-                       int own, int translate, int fused_mode, float* __restrict__ out) {
+                       int own, int translate, int fused_mode, float* __restrict__ out, uint4* __restrict__ fold,
+                       float inv_c) {
   const double top = st[kStLmax + (1 - own)];
   if (blockIdx.x == 0 && threadIdx.x == 0) prep_scalars(st, own, translate);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows_pad;
@@ -238,6 +239,7 @@ __global__ void k_prep(const double* __restrict__ ell, int64_t rows, int64_t row
       v = fused_mode ? -INFINITY : 0.0f;
     }
     out[i] = v;
+    if (fold != nullptr) write_fold_row(fold, i, v, inv_c);
   }
 }
 
@@ -448,7 +450,8 @@ cudaError_t launch_prep(tu_market* m, Side& partner, int fused_mode, int transla
   const int own = &partner == &m->Y ? 0 : 1;
   const int g = grid_for(partner.rows_pad, m->num_sms, 4);
   k_prep<<<g, kThreads, 0, m->stream>>>(partner.ell, partner.rows, partner.rows_pad, m->st, own, translate, fused_mode,
-                                        partner.pvec);
+                                        partner.pvec, fused_mode ? reinterpret_cast<uint4*>(partner.fold) : nullptr,
+                                        1.0f / m->cmul);  // (the batched preparation rounds 1 / c alike)
   return cudaGetLastError();
 }
 

@@ -77,6 +77,8 @@ struct Side {
   __nv_bfloat16* fac16 = nullptr;  // packed [F | K] (or [G | L]) rows x kp, bf16, zero padded
   uint8_t* fac8 = nullptr;         // FP8 markets: packed rows x kp e4m3 of [F | K] / fs (zero padded)
   float* fs = nullptr;             // FP8 markets: per-row scales, rows_pad (padding 1)
+  uint8_t* fold = nullptr;         // BF16 fused markets, kp = 64: this side's g / c as the K = 16 operand of
+                                   // the partner tiles' extra MMA (rows_pad x 32 bytes, tcgen05 layout)
   int fp8_exp = 0;                 // FP8 markets with one scale per side: its exponent (fs = 2^fp8_exp)
   float* fac32 = nullptr;          // packed rows x kp, fp32 (dense path), zero padded
   CUtensorMap tm_own;       // TMA map, box kKBlock x kFusedOwnRows
@@ -278,6 +280,8 @@ struct BatchDesc {
   double* ell;                 // own ell (out)
   const double* partner_ell;   // partner ell (read by the preparation kernel)
   float* g;                    // partner prepared vector (written by the preparation kernel)
+  uint8_t* gfold;              // BF16, kp = 64: the partner's g / c operand of the extra MMA (written by the
+                               // preparation kernel), else nullptr
   double* st;                  // the market's scalars (kSt*; shift and own offset of the pass)
   const float* fs_own;         // e4m3 markets: own per-row scales, else nullptr
   const float* fs_par;         // e4m3 markets: partner per-row scales, else nullptr
@@ -759,6 +763,44 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 //   bits  0-13 start address >> 4     bits 16-29 leading byte offset >> 4 (unused here: 1)
 //   bits 32-45 stride byte offset >> 4 (1024 B)   bits 46-47 descriptor version (1)
 //   bits 61-63 layout: 2 = 128-byte swizzle
+// With fold (BF16 fused markets, packed rows of one k block, d <= 32): for
+// every partner row i, g_i / c split into three BF16 values hi + mid + lo
+// (24 significant bits; -inf padding gives hi = -inf, mid = lo = 0), written
+// as the row's K = 16 operand of the fused kernel's extra MMA (columns 0-2,
+// the rest zero) in the unswizzled K-major tcgen05 layout of 128-row tiles:
+// byte (i / 128) * 4096 + ((i % 128) / 8) * 256 + (k / 8) * 128 + (i % 8) * 16 + (k % 8) * 2.
+__device__ __forceinline__ void write_fold_row(uint4* fold, int64_t i, float g, float inv_c) {
+  unsigned short b[3] = {0, 0, 0};
+  if (isinf(g)) {
+    b[0] = __bfloat16_as_ushort(__float2bfloat16_rn(g));
+  } else {
+    const float v = g * inv_c;
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(hi);
+    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+    b[0] = __bfloat16_as_ushort(hi);
+    b[1] = __bfloat16_as_ushort(mid);
+    b[2] = __bfloat16_as_ushort(lo);
+  }
+  const int64_t t = i / 128, r = i % 128;
+  const int64_t q = t * 256 + (r / 8) * 16 + (r % 8);  // 16-byte chunk of columns 0-7
+  fold[q] = make_uint4((uint32_t)b[0] | ((uint32_t)b[1] << 16), (uint32_t)b[2], 0u, 0u);
+  fold[q + 8] = make_uint4(0u, 0u, 0u, 0u);  // columns 8-15
+}
+
+// Shared-memory descriptor of an unswizzled K-major operand: core matrices of
+// 8 rows x 16 bytes, `lbo` bytes apart along K and `sbo` bytes apart along
+// M / N (version 1, layout type 0).
+__device__ __forceinline__ uint64_t sdesc_none(uint32_t smem_addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t desc = 0;
+  desc |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);
+  desc |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  desc |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  desc |= (uint64_t)1u << 46;
+  return desc;
+}
+
 __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t smem_addr) {
   uint64_t desc = 0;
   desc |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);
