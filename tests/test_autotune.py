@@ -131,3 +131,25 @@ def test_shape_arguments(gpu_lib):
     finally:
         mkt.close()
         dense.close()
+
+
+@pytest.mark.parametrize("per,split,mode", [("rows", 3, 0), ("side", 2, 2), ("rows", 4, 2)])
+def test_split_fp8_sweeps_match_oracle(gpu_lib, per, split, mode):
+    """The split instantiations of the e4m3 kernels (per-row scales: the
+    partner ranges carry their rows' scales; per-side: folded into c)."""
+    from synth import fp8_quantized
+    tu = gpu_lib
+    mk = make_market(2100, 1500, 64, sigma=0.5, seed=split + len(per), bias_x=True, bias_y=True,
+                     n_kind="uniform_real", m_kind="uniform_real", dtype="fp32")
+    q, _ = fp8_quantized(mk, "row" if per == "rows" else "side")
+    mkt = tu.from_synth(mk, fp8=per)
+    try:
+        tu.tu_market_set_small_tiles(mkt.handle, mode)
+        tu.tu_market_set_split(mkt.handle, split)
+        mkt.sweep(4)
+        lu, lv = mkt.potentials64()
+        ou, ov = oracle_sweeps(q, 4)
+        np.testing.assert_allclose(lu, ou, rtol=0, atol=ATOL_LOG)
+        np.testing.assert_allclose(lv, ov, rtol=0, atol=ATOL_LOG)
+    finally:
+        mkt.close()

@@ -130,3 +130,27 @@ def test_wide_markets_refused_where_one_shift_is_needed(gpu_lib):
     finally:
         wide.close()
         narrow.close()
+
+
+@pytest.mark.parametrize("per", ["row", "side"])
+def test_wide_fp8_market_sweeps_match_oracle(gpu_lib, per):
+    """The two-pass wide path with e4m3 factors (per-row scales multiply the
+    accumulator entries in both passes; per-side scales fold into c),
+    against the oracle on the same quantized factors."""
+    from synth import fp8_quantized
+    tu = gpu_lib
+    mk = make_market(600, 450, 64, sigma=0.01, seed=35, bias_x=True, bias_y=True, n_kind="uniform_real",
+                     m_kind="uniform_real", dtype="fp32")
+    q, _ = fp8_quantized(mk, per)
+    assert _bound(q) > 100.0
+    atol = _atol(q)
+    mkt = tu.from_synth(mk, fp8="rows" if per == "row" else "side")
+    try:
+        mkt.sweep(3)
+        lu, lv = mkt.potentials64()
+        ou, ov = oracle_sweeps(q, 3)
+        err = max(np.abs(lu - ou).max(), np.abs(lv - ov).max())
+        print(f"\nwide FP8 ({per} scales, bound {_bound(q):.0f}): max |log potential error| {err:.2e}, allowed {atol:.2e}")
+        assert err <= atol
+    finally:
+        mkt.close()
