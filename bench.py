@@ -924,6 +924,7 @@ def sub_args(args, workload: str, steps=None):
     a.no_extras = False  # the secondary lines' own solve and comparison blocks are kept
     a.no_cpu_baseline = True
     a.fp8 = None
+    a.partner_blocks = 0
     a.shape = None
     if steps is not None:
         a.steps = steps
@@ -972,6 +973,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     h = tu.tu_market_create(Fd, Kd, Gd, Ld, mk.n, mk.m, mk.sigma, bias_x=bx, bias_y=by,
                             path=cfg["path"], partition=partition, stream=stream, fp8=args.fp8)
+    if getattr(args, "partner_blocks", 0) and cfg["path"] == "fused":
+        tu.tu_market_set_partner_blocks(h, args.partner_blocks)
+        cfg = dict(cfg, partner_blocks=args.partner_blocks)
     try:
         # warm-up: W single sweeps, then one untimed block of K sweeps that
         # captures the CUDA graph the timed block replays
@@ -1181,6 +1185,9 @@ def main():
     ap.add_argument("--fp8", nargs="?", const="rows", choices=["rows", "side"], default=None,
                     help="fused workload with e4m3 factors (the library quantizes the FP32 factors with "
                          "per-row power-of-two scales, or with one per side)")
+    ap.add_argument("--partner-blocks", type=int, default=0,
+                    help="fused workload: stream the partner matrix in this many blocks, one after another "
+                         "(tu_market_set_partner_blocks), instead of the default launch shape")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",

@@ -332,8 +332,17 @@ tu_status tu_market_set_small_tiles(tu_market_t mkt, int mode);
  * markets within the single-shift range (see tu_market_create). */
 tu_status tu_market_set_split(tu_market_t mkt, int split);
 
-/* The market's launch shape: own-tile mode and partner split (either
- * pointer may be NULL). */
+/* Partner blocks, 1 <= blocks <= 8 (fused markets; TU_ERR_UNSUPPORTED on the
+ * dense path): the same partial sums as a split into `blocks` ranges, but
+ * with the items ordered range by range, so that all CTAs stream one block of
+ * the partner matrix against every own tile before the next block. A block
+ * small enough for L2 is then read from memory about once per half-sweep
+ * instead of once per wave of own tiles (the partner matrix of a 1e6 x 1e6,
+ * d = 64 market is 256 MB, L2 129 MB). Replaces any split. */
+tu_status tu_market_set_partner_blocks(tu_market_t mkt, int blocks);
+
+/* The market's launch shape: own-tile mode and partner split, a negative
+ * split -b for b partner blocks (either pointer may be NULL). */
 tu_status tu_market_get_shape(tu_market_t mkt, int* small_mode, int* split);
 
 /* Autotuner of the launch shape: times the candidate (own-tile height,
@@ -343,13 +352,15 @@ tu_status tu_market_get_shape(tu_market_t mkt, int* small_mode, int* split);
  * shape (quarter-octave buckets of N and M, the packed row length, the FP8
  * dtype or BF16, the SM count); fused markets created later with a cached
  * shape take the tuned launch shape. Candidates: the default shape, 256-row
- * tiles, 128-row tiles (fewer than 4 waves of 256-row tiles), and splits
- * 2, 3, 4, 6, 8 (fewer than 8 waves; not for wide markets). Synchronises.
+ * tiles, 128-row tiles (fewer than 4 waves of 256-row tiles), splits 2, 3,
+ * 4, 6, 8 (fewer than 8 waves) and partner blocks 2, 3, 4, 6 (partner
+ * matrices above 96 MB, at least 2 waves); splits and blocks not for wide
+ * markets. Synchronises.
  * TU_ERR_UNSUPPORTED on the dense path, TU_ERR_INVALID_ARG unless
  * 1 <= reps <= 1000. */
 typedef struct {
   int small_tiles;    /* chosen own-tile mode (as tu_market_set_small_tiles) */
-  int split;          /* chosen partner split */
+  int split;          /* chosen partner split (negative: -b partner blocks) */
   double ms;          /* ms per sweep of the chosen shape */
   double ms_default;  /* ms per sweep of the default shape (mode 1, split 1) */
   int candidates;     /* shapes timed */

@@ -90,6 +90,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
         "tu_market_set_small_tiles": (I32, [V, I32]),
         "tu_market_set_split": (I32, [V, I32]),
         "tu_market_get_shape": (I32, [V, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
+        "tu_market_set_partner_blocks": (I32, [V, I32]),
         "tu_market_autotune": (I32, [V, I32, ctypes.POINTER(TuneInfo)]),
         "tu_autotune_cache_save": (I32, [ctypes.c_char_p]),
         "tu_autotune_cache_load": (I32, [ctypes.c_char_p]),
@@ -397,8 +398,13 @@ def tu_market_set_split(h: int, split: int) -> None:
     _check(load().tu_market_set_split(h, int(split)), "tu_market_set_split", h)
 
 
+def tu_market_set_partner_blocks(h: int, blocks: int) -> None:
+    """Partner blocks (1..8), streamed one after another by all CTAs so that each stays in L2."""
+    _check(load().tu_market_set_partner_blocks(h, int(blocks)), "tu_market_set_partner_blocks", h)
+
+
 def tu_market_get_shape(h: int) -> tuple:
-    """(own-tile mode, partner split) of a market."""
+    """(own-tile mode, partner split; -b for b partner blocks) of a market."""
     a, b = ctypes.c_int(), ctypes.c_int()
     _check(load().tu_market_get_shape(h, ctypes.byref(a), ctypes.byref(b)), "tu_market_get_shape", h)
     return a.value, b.value

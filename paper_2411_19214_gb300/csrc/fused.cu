@@ -114,6 +114,7 @@ struct FusedParams {
   // warp that completes a (tile, 32-row block), counted in split_cnt, sums
   // the partials in range order and updates the rows
   int split;
+  int range_major;         // items ordered range by range (every own tile against range 0 first)
   float4* part;
   int* split_cnt;
   // folded g (BF16 half-sweeps, kp = 64): the partner side's g / c as the
@@ -504,7 +505,10 @@ __device__ __forceinline__ int item_end(const FusedParams& p) {
 }
 
 // An item of a single-market launch: own tile t and its partner tiles
-// [jb, je) (range s of p.split equal parts).
+// [jb, je) (range s of p.split equal parts). Items are ordered tile by tile
+// (the ranges of one own tile on neighbouring CTAs), or with range_major
+// range by range, so that all CTAs stream one range of the partner matrix
+// (small enough to stay in L2) against every own tile before the next.
 struct Span {
   int t, s, jb, je;
 };
@@ -512,7 +516,14 @@ template <bool SPLIT>
 __device__ __forceinline__ Span single_span(const FusedParams& p, int it) {
   if constexpr (!SPLIT) return {it, 0, 0, p.num_partner_tiles};
   const int S = p.split;
-  const int t = it / S, s = it - t * S;
+  int t, s;
+  if (p.range_major) {
+    s = it / p.num_own_tiles;
+    t = it - s * p.num_own_tiles;
+  } else {
+    t = it / S;
+    s = it - t * S;
+  }
   const int npt = p.num_partner_tiles;
   return {t, s, (int)((int64_t)s * npt / S), (int)((int64_t)(s + 1) * npt / S)};
 }
@@ -1456,6 +1467,7 @@ cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int upd
   if (whole && !m->wide && m->split > 1 && m->split_part != nullptr) {
     // partner split: at most one range per partner tile
     p.split = m->split < p.num_partner_tiles ? m->split : p.num_partner_tiles;
+    p.range_major = m->split_blocks ? 1 : 0;
     p.part = m->split_part;
     p.split_cnt = m->split_cnt;
   }

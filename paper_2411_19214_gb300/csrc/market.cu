@@ -1002,13 +1002,20 @@ tu_status ensure_split_buffers(tu_market* m, int split) {
   return TU_OK;
 }
 
-tu_status set_shape(tu_market* m, int small_mode, int split) {
-  if (small_mode == m->small_mode && split == m->split) return TU_OK;
+tu_status set_shape(tu_market* m, int small_mode, int split, bool blocks) {
+  if (small_mode == m->small_mode && split == m->split && blocks == m->split_blocks) return TU_OK;
   TU_TRY(drop_graph(m));
   if (split > 1) TU_TRY(ensure_split_buffers(m, split));
   m->small_mode = small_mode;
   m->split = split;
+  m->split_blocks = split > 1 && blocks;
   return TU_OK;
+}
+
+// A shape code: split s > 0 (ranges of one own tile side by side) or -b
+// (b partner blocks one after another), as tu_market_get_shape reports it.
+tu_status set_shape_code(tu_market* m, int small_mode, int code) {
+  return set_shape(m, small_mode, code < 0 ? -code : code, code < 0);
 }
 
 // The tuned shapes, by market shape: quarter-octave buckets of N and M, the
@@ -1044,7 +1051,7 @@ void apply_tuned(tu_market* m) {
     if (it == g_tune.end()) return;
     v = it->second;
   }
-  if (set_shape(m, v.small_mode, v.split) != TU_OK) {
+  if (set_shape_code(m, v.small_mode, v.split) != TU_OK) {
     m->last_error.clear();
     m->small_mode = 1;
     m->split = 1;
@@ -1078,20 +1085,28 @@ tu_status time_shape(tu_market* m, int reps, double* ms) {
 tu_status tu_market_set_small_tiles(tu_market_t m, int mode) {
   TU_TRY(check_live(m));
   if (mode < 0 || mode > 2) return fail(m, TU_ERR_INVALID_ARG, "small-tile mode must be 0, 1 or 2");
-  return set_shape(m, mode, m->split);
+  return set_shape(m, mode, m->split, m->split_blocks);
 }
 
 tu_status tu_market_set_split(tu_market_t m, int split) {
   TU_TRY(check_live(m));
   if (m->path != TU_PATH_FUSED) return fail(m, TU_ERR_UNSUPPORTED, "the partner split is a fused-path shape");
   if (split < 1 || split > kMaxSplit) return fail(m, TU_ERR_INVALID_ARG, "split must be in [1, 8]");
-  return set_shape(m, m->small_mode, split);
+  return set_shape(m, m->small_mode, split, false);
+}
+
+tu_status tu_market_set_partner_blocks(tu_market_t m, int blocks) {
+  TU_TRY(check_live(m));
+  if (m->path != TU_PATH_FUSED) return fail(m, TU_ERR_UNSUPPORTED, "partner blocks are a fused-path shape");
+  if (blocks < 1 || blocks > kMaxSplit) return fail(m, TU_ERR_INVALID_ARG, "blocks must be in [1, 8]");
+  return set_shape(m, m->small_mode, blocks, true);
 }
 
 tu_status tu_market_get_shape(tu_market_t m, int* small_mode, int* split) {
   TU_TRY(check_live(m));
   if (small_mode != nullptr) *small_mode = m->small_mode;
-  if (split != nullptr) *split = m->split;
+  // (partner blocks are reported as a negative split)
+  if (split != nullptr) *split = m->split_blocks ? -m->split : m->split;
   return TU_OK;
 }
 
@@ -1105,8 +1120,10 @@ tu_status tu_market_autotune(tu_market_t m, int reps, tu_tune_info* info) {
   const int64_t rows = m->N > m->M ? m->N : m->M;
   const int64_t tiles = (rows + kFusedOwnRows - 1) / kFusedOwnRows;
   const int64_t ptiles = ((m->N < m->M ? m->N : m->M) + kFusedPartnerRows - 1) / kFusedPartnerRows;
-  // candidates: the default shape first; 128-row tiles and partner splits
-  // only where waves are few enough for their granularity to matter
+  // candidates (own-tile mode, shape code): the default shape first;
+  // 128-row tiles and partner splits only where waves are few enough for
+  // their granularity to matter; partner blocks where the partner matrix is
+  // several times the L2 a block should fit
   std::vector<std::pair<int, int>> cand = {{1, 1}, {0, 1}};
   if (tiles < 4 * (int64_t)m->num_sms) cand.push_back({2, 1});
   if (tiles < 8 * (int64_t)m->num_sms && !m->wide)
@@ -1115,13 +1132,17 @@ tu_status tu_market_autotune(tu_market_t m, int reps, tu_tune_info* info) {
         cand.push_back({0, s});
         if (tiles < 2 * (int64_t)m->num_sms) cand.push_back({2, s});
       }
-  const int small0 = m->small_mode, split0 = m->split;
+  const double partner_bytes = (double)(m->N > m->M ? m->N : m->M) * (double)m->kp * (is_fp8(m->dtype) ? 1.0 : 2.0);
+  if (partner_bytes > 96e6 && tiles >= 2 * (int64_t)m->num_sms && !m->wide)
+    for (int b : {2, 3, 4, 6})
+      if (b <= ptiles) cand.push_back({0, -b});
+  const int small0 = m->small_mode, split0 = m->split_blocks ? -m->split : m->split;
   double best = 0.0, ms_default = 0.0;
   int bi = -1;
   tu_status st = TU_OK;
   for (size_t i = 0; i < cand.size() && st == TU_OK; ++i) {
     double ms = 0.0;
-    st = set_shape(m, cand[i].first, cand[i].second);
+    st = set_shape_code(m, cand[i].first, cand[i].second);
     if (st == TU_OK) st = time_shape(m, reps, &ms);
     if (st != TU_OK) break;
     if (i == 0) ms_default = ms;
@@ -1131,10 +1152,10 @@ tu_status tu_market_autotune(tu_market_t m, int reps, tu_tune_info* info) {
     }
   }
   if (st != TU_OK) {
-    set_shape(m, small0, split0);
+    set_shape_code(m, small0, split0);
     return st;
   }
-  TU_TRY(set_shape(m, cand[bi].first, cand[bi].second));
+  TU_TRY(set_shape_code(m, cand[bi].first, cand[bi].second));
   TU_TRY(clear_results(m));
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1186,7 +1207,8 @@ tu_status tu_autotune_cache_load(const char* path) {
                "\"small_tiles\": %d, \"split\": %d, \"ms\": %lf, \"ms_default\": %lf",
                &k.nb, &k.mb, &kp, &k.fmt, &k.sms, &v.small_mode, &v.split, &v.ms, &v.ms_default) != 9)
       return TU_ERR_INVALID_ARG;
-    if (v.small_mode < 0 || v.small_mode > 2 || v.split < 1 || v.split > kMaxSplit) return TU_ERR_INVALID_ARG;
+    if (v.small_mode < 0 || v.small_mode > 2 || v.split == 0 || v.split < -kMaxSplit || v.split > kMaxSplit)
+      return TU_ERR_INVALID_ARG;
     k.kp = kp;
     read[k] = v;
   }

@@ -175,6 +175,7 @@ struct tu_market {
   int small_mode = 1;              // tu_market_set_small_tiles: 0 256-row own tiles, 1 128-row when they
                                    // fit one wave, 2 always 128-row
   int split = 1;                   // tu_market_set_split: partner ranges per own tile (fused sweeps)
+  bool split_blocks = false;       // tu_market_set_partner_blocks: the ranges run one after another
   float4* split_part = nullptr;    // split > 1: partial row sums, split x max(N, M)
   int* split_cnt = nullptr;        // split > 1: arrivals per (own tile, 32-row block), zeroed
   int split_cap = 0;               // the split the buffers were sized for

@@ -153,3 +153,31 @@ def test_split_fp8_sweeps_match_oracle(gpu_lib, per, split, mode):
         np.testing.assert_allclose(lv, ov, rtol=0, atol=ATOL_LOG)
     finally:
         mkt.close()
+
+
+@pytest.mark.parametrize("N,M,blocks,mode", [(3000, 2100, 3, 0), (2049, 1100, 4, 2), (700, 100, 3, 0),
+                                             (5000, 5000, 2, 1)], ids=lambda v: str(v))
+def test_partner_blocks_match_oracle(gpu_lib, N, M, blocks, mode):
+    """Partner blocks: the split's partial sums with the items ordered block
+    by block (all own tiles against block 0 first); iterates of captured
+    sweeps against the oracle, and the shape reported as -blocks."""
+    tu = gpu_lib
+    mk = _mk(N, M, seed=N + M + 10 * blocks)
+    mkt = tu.from_synth(mk)
+    try:
+        tu.tu_market_set_small_tiles(mkt.handle, mode)
+        tu.tu_market_set_partner_blocks(mkt.handle, blocks)
+        assert tu.tu_market_get_shape(mkt.handle) == (mode, -blocks)
+        mkt.sweep(1)
+        mkt.sweep(5)
+        lu, lv = (t.double().cpu().numpy() for t in mkt.potentials())
+        ou, ov = oracle_sweeps(mk, 6)
+        np.testing.assert_allclose(lu, ou, rtol=0, atol=ATOL_LOG)
+        np.testing.assert_allclose(lv, ov, rtol=0, atol=ATOL_LOG)
+        tu.tu_market_set_split(mkt.handle, 2)  # a split replaces the blocks
+        assert tu.tu_market_get_shape(mkt.handle) == (mode, 2)
+        for bad in (0, 9):
+            with pytest.raises(tu.TuError):
+                tu.tu_market_set_partner_blocks(mkt.handle, bad)
+    finally:
+        mkt.close()
