@@ -115,6 +115,11 @@ struct FusedParams {
   // the partials in range order and updates the rows
   int split;
   int range_major;         // items ordered range by range (every own tile against range 0 first)
+  // L2 residency of the partner matrix (single-market launches): this
+  // fraction of its lines is loaded evict-last, so that a partner matrix
+  // larger than L2 keeps a fixed part resident across the waves of own tiles
+  // (0: no hint)
+  float l2_keep;
   float4* part;
   int* split_cnt;
   // folded g (BF16 half-sweeps, kp = 64): the partner side's g / c as the
@@ -653,6 +658,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       int stage = 0, gs = 0, ab = 0;
       uint32_t phase = 0, gphase = 0, a_phase = 0;
+      const bool hint = !BATCH && p.l2_keep > 0.0f;
+      const uint64_t keep_policy = hint ? l2_policy_keep_fraction(p.l2_keep) : 0ull;
       uint32_t armed[STAGES], garmed[kGSlots], a_armed[2] = {0u, 0u};
       for (int s = 0; s < STAGES; ++s) armed[s] = 0;
       for (int s = 0; s < kGSlots; ++s) garmed[s] = 0;
@@ -703,9 +710,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             const bool fold_here = FOLD && sp == SPT - 1;  // the tile's g operand rides in its last stage
             mbar_arrive_expect_tx(&full[stage], KBS * kPartnerBytesPerKB + (fold_here ? kFoldBytes : 0));
-            for (int kb = 0; kb < KBS; ++kb)
-              tma_load_2d(sB + stage * SB + kb * kPartnerBytesPerKB, map_partner, &full[stage],
-                          (sp * KBS + kb) * XB, (int)(p.col0 + (int64_t)j * kFusedPartnerRows));
+            for (int kb = 0; kb < KBS; ++kb) {
+              const int px = (sp * KBS + kb) * XB, py = (int)(p.col0 + (int64_t)j * kFusedPartnerRows);
+              if (hint) {
+                tma_load_2d_hint(sB + stage * SB + kb * kPartnerBytesPerKB, map_partner, &full[stage], px, py,
+                                 keep_policy);
+              } else {
+                tma_load_2d(sB + stage * SB + kb * kPartnerBytesPerKB, map_partner, &full[stage], px, py);
+              }
+            }
             if (fold_here)
               bulk_load(sB + stage * SB + KBS * kPartnerBytesPerKB,
                         (BATCH ? bd->gfold : p.gfold) + (int64_t)j * kFoldBytes, kFoldBytes, &full[stage]);
@@ -1464,6 +1477,12 @@ cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int upd
   p.fs_own = own.fs;
   p.fs_par = partner.fs;
   p.gfold = partner.fold;
+  {
+    // partner matrices larger than L2: keep a fixed 70 % of L2's worth resident
+    const double pbytes = (double)partner.rows * (double)m->kp * (is_fp8(m->dtype) ? 1.0 : 2.0);
+    const double keep = 0.7 * (double)m->l2_bytes;
+    p.l2_keep = (m->l2_bytes > 0 && pbytes > keep) ? (float)(keep / pbytes) : 0.0f;
+  }
   if (whole && !m->wide && m->split > 1 && m->split_part != nullptr) {
     // partner split: at most one range per partner tile
     p.split = m->split < p.num_partner_tiles ? m->split : p.num_partner_tiles;

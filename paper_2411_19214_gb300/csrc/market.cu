@@ -811,6 +811,14 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
     return TU_ERR_UNSUPPORTED;
   }
   {
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, m->device) != cudaSuccess) {
+      cudaGetLastError();
+      l2 = 0;
+    }
+    m->l2_bytes = l2;
+  }
+  {
     std::lock_guard<std::mutex> lk(g_pool_mu);
     ++g_live_markets;  // from here on every exit goes through tu_market_destroy
   }

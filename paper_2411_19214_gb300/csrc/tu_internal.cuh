@@ -176,6 +176,7 @@ struct tu_market {
                                    // fit one wave, 2 always 128-row
   int split = 1;                   // tu_market_set_split: partner ranges per own tile (fused sweeps)
   bool split_blocks = false;       // tu_market_set_partner_blocks: the ranges run one after another
+  int64_t l2_bytes = 0;            // the device's L2 size (partner tiles: evict-last / evict-first policy)
   float4* split_part = nullptr;    // split > 1: partial row sums, split x max(N, M)
   int* split_cnt = nullptr;        // split > 1: arrivals per (own tile, 32-row block), zeroed
   int split_cap = 0;               // the split the buffers were sized for
@@ -704,6 +705,23 @@ __device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* m
       "[%2];" ::"r"(smem_u32(smem_dst)),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
       : "memory");
+}
+// The same with an L2 cache policy (createpolicy) for the loaded lines.
+__device__ __forceinline__ void tma_load_2d_hint(void* smem_dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                                 uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%3, "
+      "%4}], [%2], %5;" ::"r"(smem_u32(smem_dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "l"(policy)
+      : "memory");
+}
+// L2 policy: the given fraction of the accessed lines evict last, the rest
+// with their priority unchanged (evict-first would drop a line before the
+// other CTAs of the same wave read it).
+__device__ __forceinline__ uint64_t l2_policy_keep_fraction(float fraction) {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.L2::evict_unchanged.b64 %0, %1;" : "=l"(pol) : "f"(fraction));
+  return pol;
 }
 __device__ __forceinline__ void tma_prefetch_map(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
