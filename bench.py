@@ -45,6 +45,8 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 def make_workload(name: str, rank: int, shape=None, fp8=None):
     from synth import dense_job_market, fused_market
     kw = {} if shape is None else {"N": shape[0], "M": shape[1]}
+    if shape is not None and len(shape) > 2 and name == "fused":
+        kw["d"] = shape[2]  # (profiling cases of other row lengths)
     if name == "fused" and fp8:
         # the same market with unrounded FP32 factors, quantized to e4m3 by the library
         mk = fused_market(seed=1002 + 97 * rank, dtype="fp32", **kw)
@@ -57,7 +59,7 @@ def make_workload(name: str, rank: int, shape=None, fp8=None):
                "l2": "inputs larger than L2: each half-sweep streams the 128 MB partner factor matrix "
                      "(L2 is 129 MB); no flush between steps"}
         if shape is not None:
-            cfg["workload"] = f"fused FP8 IPFP, reduced shape N={mk.N}, M={mk.M}, same recipe"
+            cfg["workload"] = f"fused FP8 IPFP, reduced shape N={mk.N}, M={mk.M}, d={mk.d}, same recipe"
         return mk, cfg, 65536
     if name == "fused":
         mk = fused_market(seed=1002 + 97 * rank, **kw)
@@ -68,7 +70,7 @@ def make_workload(name: str, rank: int, shape=None, fp8=None):
                "l2": "inputs larger than L2: each half-sweep streams the 256 MB partner factor matrix "
                      "(L2 is 129 MB); no flush between steps"}
         if shape is not None:
-            cfg["workload"] = f"fused mini-batch IPFP (Alg. 2), reduced shape N={mk.N}, M={mk.M}, same recipe"
+            cfg["workload"] = f"fused mini-batch IPFP (Alg. 2), reduced shape N={mk.N}, M={mk.M}, d={mk.d}, same recipe"
         return mk, cfg, 65536
     if name == "dense":
         mk = dense_job_market(seed=1001 + 97 * rank, **kw)
@@ -1193,7 +1195,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the plain-FP32 comparison and the ranked-list timing")
     ap.add_argument("--shape", default=None,
-                    help="N,M override of the workload's sizes (same recipe; for small profiling cases)")
+                    help="N,M[,d] override of the workload's sizes (same recipe; for small profiling cases)")
     args = ap.parse_args()
     if args.shape:
         args.shape = tuple(int(v) for v in args.shape.split(","))
