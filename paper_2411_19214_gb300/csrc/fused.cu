@@ -150,14 +150,19 @@ enum : int { kFmtBF16 = 0, kFmtE4M3Side = 1, kFmtE4M3Rows = 2 };
 constexpr int kTailBytes = 512 + 512 + 2 * kFusedOwnRows * 4;
 // folded g: the partner tile's K = 16 operand rides in its (last) stage, the
 // own side's constant operand (ones in columns 0-2) is one tile of its own.
-// Taken for rows of one k block (d <= 32), where the tensor pipe has room for
-// a fifth MMA per chain and the epilogue sheds its g loads: batched d = 32
-// half-sweep 5.44 -> 5.12 ms, a 1e5 d = 32 sweep 3.54 -> 3.37 ms; with two k
-// blocks (d = 33..64) the ninth MMA costs more than it saves (1e6 d = 64
-// half-sweep 184.5 -> 187.1 ms), so those keep g in the shared ring.
+// Taken for rows of one k block (d <= 32 in BF16, d <= 64 in e4m3 with one
+// scale per side), where the tensor pipe has room for a fifth MMA per chain
+// and the epilogue sheds its g loads: batched d = 32 half-sweep 5.44 -> 5.12
+// ms, a 1e5 d = 32 sweep 3.54 -> 3.37 ms; with two BF16 k blocks (d =
+// 33..64) the ninth MMA costs more than it saves (1e6 d = 64 half-sweep
+// 184.5 -> 187.1 ms), so those keep g in the shared ring. e4m3 rows with one
+// scale per side: 1e6 d = 64 half-sweep 149.4 -> 142.5 ms; there the fold MMA
+// is a separate kind::f16 MMA (BF16 ones x BF16 g / c) into the same FP32
+// accumulator. e4m3 rows with per-row scales cannot fold: the own row's scale
+// multiplies phi, so no per-column constant added to it gives g in every row.
 constexpr int kFoldBytes = kFusedPartnerRows * 32;
 constexpr bool fold_for(int KB, int MODE, bool BATCH, int fmt, bool nofold) {
-  return MODE == kModeSweep && fmt == kFmtBF16 && KB == 1 && !nofold;
+  return MODE == kModeSweep && (fmt == kFmtBF16 || fmt == kFmtE4M3Side) && KB == 1 && !nofold;
 }
 constexpr int stage_bytes(int KB, bool fold) { return kbs_for(KB) * kPartnerBytesPerKB + (fold ? kFoldBytes : 0); }
 constexpr int smem_bytes(int KB, int fmt, int stages, bool fold = false) {
@@ -760,6 +765,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc = F8 ? idesc_e4m3_f32(128, kFusedPartnerRows) : idesc_bf16_f32(128, kFusedPartnerRows);
+      constexpr uint32_t idesc_fold = idesc_bf16_f32(128, kFusedPartnerRows);  // (BF16 in every format)
       int stage = 0, buf = 0, ab = 0;
       uint32_t phase = 0, tphase = 0, a_phase = 0;
       bool ok = true;
@@ -815,7 +821,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // D += ones x (g / c): every row gets the partner column's g / c
                 if (sp == SPT - 1)
                   umma_bf16(d_tmem, sdesc_none(smem_u32(sOnes), 128, 256),
-                            sdesc_none(b0 + KBS * kPartnerBytesPerKB, 128, 256), idesc, 1u);
+                            sdesc_none(b0 + KBS * kPartnerBytesPerKB, 128, 256), idesc_fold, 1u);
               }
             }
             umma_commit(&empty[stage]);

@@ -287,6 +287,8 @@ tu_status side_alloc(tu_market* m, Side& s, int64_t rows, bool has_bias) {
   if (m->path == TU_PATH_FUSED && is_fp8(m->dtype)) {
     TU_TRY(dev_alloc(m, &s.fac8, (size_t)rows * m->kp));
     TU_TRY(dev_alloc(m, &s.fs, s.rows_pad));
+    // one scale per side and 128-byte rows: the extra MMA's g / c operand
+    if (m->dtype == TU_DTYPE_FP8E4M3_SIDE && m->kp == 128) TU_TRY(dev_alloc(m, &s.fold, (size_t)s.rows_pad * 32));
   } else if (m->path == TU_PATH_FUSED) {
     TU_TRY(dev_alloc(m, &s.fac16, (size_t)rows * m->kp));
     // the partner tiles' g / c operand of the fused kernel's extra MMA
