@@ -112,9 +112,10 @@ typedef struct {
  * a_x = (f_x, k_x), b_y = (g_y, l_y) (a Cauchy-Schwarz bound on the bias-free
  * part of phi / (2 sigma)), decides the arithmetic: up to 40, one shift per
  * half-sweep keeps every FP32 term in range; beyond ("wide" markets, strong
- * preferences or small sigma), the fused path first finds every row's largest
- * exponent (a second pass over the pairs, about 1.6x the half-sweep's time)
- * and subtracts it, and the dense path refuses the market
+ * preferences or small sigma), the fused path keeps a running maximum of
+ * every row's exponents and rescales the row's sum by an exact power of two
+ * whenever it grows (one pass over the pairs), and the dense path refuses the
+ * market
  * (TU_ERR_UNSUPPORTED: its materialised FP32 A-hat would overflow). In wide
  * markets the FP32 accumulation of phi carries an absolute error of about
  * bound x 2^-24 x sqrt(2d) per exponent, above the 1e-7 of narrow ones, and
@@ -447,7 +448,7 @@ tu_status tu_profile_read(tu_market_t mkt, double* pass_ms, int64_t* passes);
  * Limits: 1 <= rows <= 65536 and 1 <= cols <= 1048576 (TU_ERR_UNSUPPORTED
  * beyond them, and for kp other than 64 or 128); the factors must lie in the
  * single-shift range of tu_market_create (bound <= 40), which is not checked
- * here (there is no second pass for wide markets).
+ * here (there is no running-maximum variant for wide markets).
  * Scratch: one file-scope __device__ array of 5,644,576 bytes that every GPU
  * loading the library holds until the process exits; its device address is
  * resolved on the first call on each device (with that device current), so

@@ -59,10 +59,10 @@ constexpr uint32_t kTmemCols = 512;
 // the tiles of c * phi_hat + g; the epilogue either reduces them (a half-sweep),
 // keeps the k best columns of every row (ranked lists) or writes mu.
 // Markets whose factor range is too wide for one shift per half-sweep (see
-// market.cu) take two passes: kModeRowMax writes every own row's largest
-// exponent c * phi_hat + g, and kModeSweepShift is a half-sweep that
-// subtracts it before ex2 (so every row's largest term is 2^0).
-enum : int { kModeSweep = 0, kModeTopK = 1, kModeMu = 2, kModeTopKShared = 3, kModeRowMax = 4, kModeSweepShift = 5 };
+// market.cu) take kModeSweepWide: a half-sweep that keeps a running maximum
+// per row and rescales the row's sum whenever it grows (the log-domain
+// rescale of an online softmax), so that no term's exponent exceeds 0.
+enum : int { kModeSweep = 0, kModeTopK = 1, kModeMu = 2, kModeTopKShared = 3, kModeSweepWide = 4 };
 
 struct FusedParams {
   int64_t rows;            // own users of this launch: [row0, row0 + rows)
@@ -100,9 +100,6 @@ struct FusedParams {
   int64_t ld;
   int64_t y0;
   int64_t ny;
-  // wide markets: per own row (index row0 + r), the largest exponent in log2
-  // units (written by kModeRowMax, subtracted by kModeSweepShift)
-  float* rowmax;
   // e4m3 factors: per-row scales of the own side (index row0 + r) and of the
   // partner side (index = partner user); the product of row r and partner
   // column j is fs_own[r] * fs_par[j] * <e4m3 row r, e4m3 row j>
@@ -246,25 +243,6 @@ __device__ __forceinline__ void pair_step_scaled(uint64_t& acc, uint32_t phi0, u
       : "r"(phi0), "r"(phi1), "f"(g0), "f"(g1), "f"(f0), "f"(f1), "l"(cc));
 }
 
-// The same with the row's shift ss = (-S, -S) added before ex2 (wide markets).
-__device__ __forceinline__ void pair_step_scaled_shift(uint64_t& acc, uint32_t phi0, uint32_t phi1, float g0,
-                                                       float g1, float f0, float f1, uint64_t cc, uint64_t ss) {
-  asm("{\n\t.reg .b64 a, gg, ff, t, e;\n\t.reg .f32 t0, t1, e0, e1;\n\t"
-      "mov.b64 a, {%1, %2};\n\t"
-      "mov.b64 gg, {%3, %4};\n\t"
-      "mov.b64 ff, {%5, %6};\n\t"
-      "mul.rn.f32x2 t, a, ff;\n\t"
-      "fma.rn.f32x2 t, t, %7, gg;\n\t"
-      "add.rn.f32x2 t, t, %8;\n\t"
-      "mov.b64 {t0, t1}, t;\n\t"
-      "ex2.approx.ftz.f32 e0, t0;\n\t"
-      "ex2.approx.ftz.f32 e1, t1;\n\t"
-      "mov.b64 e, {e0, e1};\n\t"
-      "add.rn.f32x2 %0, %0, e;\n\t}"
-      : "+l"(acc)
-      : "r"(phi0), "r"(phi1), "f"(g0), "f"(g1), "f"(f0), "f"(f1), "l"(cc), "l"(ss));
-}
-
 // Folded g: acc += (ex2(D0 * c), ex2(D1 * c)), D = phi + g / c from the MMA.
 __device__ __forceinline__ void pair_step_fold(uint64_t& acc, uint32_t d0, uint32_t d1, uint64_t cc) {
   asm("{\n\t.reg .b64 a, t, e;\n\t.reg .f32 t0, t1, e0, e1;\n\t"
@@ -296,49 +274,6 @@ __device__ __forceinline__ float unpack_sum(uint64_t a) {
   return __uint_as_float((uint32_t)a) + __uint_as_float((uint32_t)(a >> 32));
 }
 
-// acc(2 lanes) += (ex2(phi0 * c + g0 - S), ex2(phi1 * c + g1 - S)): the same
-// step with the row's shift ss = (-S, -S) added before ex2 (wide markets).
-__device__ __forceinline__ void pair_step_shift(uint64_t& acc, uint32_t phi0, uint32_t phi1, float g0, float g1,
-                                                uint64_t cc, uint64_t ss) {
-  asm("{\n\t.reg .b64 a, gg, t, e;\n\t.reg .f32 t0, t1, e0, e1;\n\t"
-      "mov.b64 a, {%1, %2};\n\t"
-      "mov.b64 gg, {%3, %4};\n\t"
-      "fma.rn.f32x2 t, a, %5, gg;\n\t"
-      "add.rn.f32x2 t, t, %6;\n\t"
-      "mov.b64 {t0, t1}, t;\n\t"
-      "ex2.approx.ftz.f32 e0, t0;\n\t"
-      "ex2.approx.ftz.f32 e1, t1;\n\t"
-      "mov.b64 e, {e0, e1};\n\t"
-      "add.rn.f32x2 %0, %0, e;\n\t}"
-      : "+l"(acc)
-      : "r"(phi0), "r"(phi1), "f"(g0), "f"(g1), "l"(cc), "l"(ss));
-}
-
-template <bool RS>
-__device__ __forceinline__ void chunk_sum_shift(const uint32_t (&v)[32], const float4* gs4, const float4* fs4,
-                                                uint64_t cc, uint64_t ss, uint64_t (&acc)[4]) {
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const float4 gg = gs4[i];
-    if constexpr (RS) {
-      const float4 ff = fs4[i];
-      pair_step_scaled_shift(acc[(2 * i) & 3], v[4 * i + 0], v[4 * i + 1], gg.x, gg.y, ff.x, ff.y, cc, ss);
-      pair_step_scaled_shift(acc[(2 * i + 1) & 3], v[4 * i + 2], v[4 * i + 3], gg.z, gg.w, ff.z, ff.w, cc, ss);
-    } else {
-      pair_step_shift(acc[(2 * i) & 3], v[4 * i + 0], v[4 * i + 1], gg.x, gg.y, cc, ss);
-      pair_step_shift(acc[(2 * i + 1) & 3], v[4 * i + 2], v[4 * i + 3], gg.z, gg.w, cc, ss);
-    }
-  }
-}
-
-// Largest exponent c * phi + g of one 32-column chunk, folded into mx.
-template <bool RS>
-__device__ __forceinline__ void chunk_max(const uint32_t (&v)[32], const float* g, const float* fs, float c,
-                                          float& mx) {
-#pragma unroll
-  for (int i = 0; i < 32; ++i) mx = fmaxf(mx, fmaf(scaled_phi<RS>(v[i], fs, i), c, g[i]));
-}
-
 // Sum over one 32-column chunk: 16 packed pairs into four packed accumulators.
 template <bool RS>
 __device__ __forceinline__ void chunk_sum(const uint32_t (&v)[32], const float4* gs4, const float4* fs4, uint64_t cc,
@@ -355,6 +290,107 @@ __device__ __forceinline__ void chunk_sum(const uint32_t (&v)[32], const float4*
       pair_step(acc[(2 * i + 1) & 3], v[4 * i + 2], v[4 * i + 3], gg.z, gg.w, cc);
     }
   }
+}
+
+// ---- wide markets: one pass with a running maximum per row -----------------
+
+// t = (phi0, phi1) * c + (g0, g1); e4m3 per-row scales: (phi0 f0, phi1 f1) * c + (g0, g1)
+template <bool RS>
+__device__ __forceinline__ uint64_t pair_exponents(uint32_t phi0, uint32_t phi1, float g0, float g1, float f0,
+                                                   float f1, uint64_t cc) {
+  uint64_t t;
+  if constexpr (RS) {
+    asm("{\n\t.reg .b64 a, gg, ff, x;\n\t"
+        "mov.b64 a, {%1, %2};\n\t"
+        "mov.b64 gg, {%3, %4};\n\t"
+        "mov.b64 ff, {%5, %6};\n\t"
+        "mul.rn.f32x2 x, a, ff;\n\t"
+        "fma.rn.f32x2 %0, x, %7, gg;\n\t}"
+        : "=l"(t)
+        : "r"(phi0), "r"(phi1), "f"(g0), "f"(g1), "f"(f0), "f"(f1), "l"(cc));
+  } else {
+    asm("{\n\t.reg .b64 a, gg;\n\t"
+        "mov.b64 a, {%1, %2};\n\t"
+        "mov.b64 gg, {%3, %4};\n\t"
+        "fma.rn.f32x2 %0, a, %5, gg;\n\t}"
+        : "=l"(t)
+        : "r"(phi0), "r"(phi1), "f"(g0), "f"(g1), "l"(cc));
+  }
+  return t;
+}
+
+// acc(2 lanes) += (ex2(t0 + m), ex2(t1 + m)), mm = (m, m)
+__device__ __forceinline__ void ex2_add_shifted(uint64_t& acc, uint64_t t, uint64_t mm) {
+  asm("{\n\t.reg .b64 x, e;\n\t.reg .f32 x0, x1, e0, e1;\n\t"
+      "add.rn.f32x2 x, %1, %2;\n\t"
+      "mov.b64 {x0, x1}, x;\n\t"
+      "ex2.approx.ftz.f32 e0, x0;\n\t"
+      "ex2.approx.ftz.f32 e1, x1;\n\t"
+      "mov.b64 e, {e0, e1};\n\t"
+      "add.rn.f32x2 %0, %0, e;\n\t}"
+      : "+l"(acc)
+      : "l"(t), "l"(mm));
+}
+
+// acc(2 lanes) *= (s, s)
+__device__ __forceinline__ void scale2(uint64_t& acc, float s) {
+  const uint64_t ss = ((uint64_t)__float_as_uint(s) << 32) | __float_as_uint(s);
+  asm("mul.rn.f32x2 %0, %0, %1;" : "+l"(acc) : "l"(ss));
+}
+
+// The larger of a, b and c; NaN if any of them is NaN.
+__device__ __forceinline__ float max3_nan(float a, float b, float c) {
+  float r;
+  asm("max.NaN.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// 2^d for an integer-valued d <= 0, as an exact power of two; 0 for d below
+// -126 (FP32's normal range), for -inf and for NaN.
+__device__ __forceinline__ float exp2_int(float d) {
+  return d >= -126.0f ? __int_as_float((127 + (int)d) << 23) : 0.0f;
+}
+
+// One 32-column chunk of a wide market's row: the exponents t = c * phi + g,
+// their largest; when that exceeds the row's running shift M (an integer,
+// -inf before the first term) the shift becomes M' = ceil(max) and all the
+// row has summed so far (this tile's packed partials acc, the compensated
+// sum over the earlier tiles) is multiplied by 2^(M - M'), a power of two,
+// so exactly; then acc += 2^(t - M). Every term is at most 1, and the row's
+// log-sum is log(sum) + M ln 2.
+template <bool RS>
+__device__ __forceinline__ void chunk_sum_wide(uint32_t (&v)[32], const float4* gs4, const float4* fs4, uint64_t cc,
+                                               uint64_t (&acc)[4], float& M, float& sum, float& comp) {
+  // the exponents replace the loaded values in place
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float4 gg = gs4[i];
+    float4 ff = make_float4(1.f, 1.f, 1.f, 1.f);
+    if constexpr (RS) ff = fs4[i];
+    const uint64_t t0 = pair_exponents<RS>(v[4 * i + 0], v[4 * i + 1], gg.x, gg.y, ff.x, ff.y, cc);
+    const uint64_t t1 = pair_exponents<RS>(v[4 * i + 2], v[4 * i + 3], gg.z, gg.w, ff.z, ff.w, cc);
+    v[4 * i + 0] = (uint32_t)t0;
+    v[4 * i + 1] = (uint32_t)(t0 >> 32);
+    v[4 * i + 2] = (uint32_t)t1;
+    v[4 * i + 3] = (uint32_t)(t1 >> 32);
+  }
+  float mx = -INFINITY;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) mx = max3_nan(mx, __uint_as_float(v[2 * k]), __uint_as_float(v[2 * k + 1]));
+  if (!(mx <= M)) {  // a larger maximum (or NaN, which then reaches the sum)
+    const float Mn = ceilf(mx);
+    const float sc = exp2_int(M - Mn);
+    sum *= sc;
+    comp *= sc;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) scale2(acc[k], sc);
+    M = Mn;
+  }
+  if (M == -INFINITY) return;  // every exponent so far is -inf: no terms
+  const uint64_t mm = ((uint64_t)__float_as_uint(-M) << 32) | __float_as_uint(-M);
+#pragma unroll
+  for (int k = 0; k < 16; ++k)
+    ex2_add_shifted(acc[k & 3], ((uint64_t)v[2 * k + 1] << 32) | v[2 * k], mm);
 }
 
 constexpr int kMaxTopK = 64;
@@ -417,6 +453,11 @@ __device__ __forceinline__ void chunk_topk(const uint32_t (&v)[32], const float*
 constexpr int kSharedTopK = 14;
 constexpr int kEpiThreads = kEpiWarps * 32;
 constexpr int kTopKListBytes = kSharedTopK * kEpiThreads * 8;
+constexpr int kWideShiftBytes = 2 * kFusedOwnRows * 4;  // kModeSweepWide: the row hand-over's shifts
+// shared memory a mode needs after the tail area
+constexpr int mode_extra_bytes(int mode) {
+  return mode == kModeTopKShared ? kTopKListBytes : (mode == kModeSweepWide ? kWideShiftBytes : 0);
+}
 
 __device__ __forceinline__ float lds_f32(uint32_t a) {
   float v;
@@ -565,7 +606,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                       const FusedParams p) {
   static_assert(!BATCH || MODE == kModeSweep, "batched launches run half-sweeps only");
   static_assert(!SPLIT || (MODE == kModeSweep && !BATCH), "partner splits are single-market half-sweeps");
-  constexpr bool kSweepLike = MODE == kModeSweep || MODE == kModeSweepShift;
+  constexpr bool kSweepLike = MODE == kModeSweep || MODE == kModeSweepWide;
   static_assert(!(BATCH && SMALL), "batched launches use 256-row own tiles");
   constexpr int kOwn = SMALL ? kFusedOwnRows / 2 : kFusedOwnRows;  // rows of an own tile
   static_assert(KB == 1 || KB == 2 || KB == 4, "128-byte k blocks per row");
@@ -604,6 +645,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   float* rowbuf = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bars) + 1024);   // 2 x 256 floats
   // ranked lists in shared memory (kModeTopKShared only): after the tail area
   float* topk_list = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bars) + kTailBytes);
+  // the running shifts of the second column half's rows (kModeSweepWide only): the same place
+  float* wide_shift = topk_list;  // 2 x 256 floats
   static_assert(4 * kEpiWarps * 8 <= 512, "reduction area");
   static_assert((2 * STAGES + 2 * kGSlots + 13) * 8 + 8 <= 512, "barrier area");
 
@@ -902,13 +945,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       float sum = 0.0f, comp = 0.0f;
       float mu_lo = 0.0f;
       int mu_hi = 0;
-      // wide markets: the row's largest exponent (found here, or subtracted here)
-      float rmax = -INFINITY;
-      uint64_t rshift = 0ull;
-      if constexpr (MODE == kModeSweepShift) {
-        const float sft = row_ok ? -p.rowmax[p.row0 + r] : 0.0f;
-        rshift = ((uint64_t)__float_as_uint(sft) << 32) | __float_as_uint(sft);
-      }
+      float wide_m = -INFINITY;  // wide markets: the row's running shift (an integer, log2 units)
       if constexpr (MODE == kModeMu) {
         if (row_ok) {
           const double off = (shift + p.ell[p.row0 + r]) * 1.4426950408889634;
@@ -954,8 +991,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           tmem_ld_issue(taddr + 32, vb);
           if constexpr (FOLD) chunk_sum_fold(va, cc, acc);
           if constexpr (MODE == kModeSweep && !FOLD) chunk_sum<RS>(va, gs4, fs4, cc, acc);
-          if constexpr (MODE == kModeSweepShift) chunk_sum_shift<RS>(va, gs4, fs4, cc, rshift, acc);
-          if constexpr (MODE == kModeRowMax) chunk_max<RS>(va, gsf, fsf, crow, rmax);
+          if constexpr (MODE == kModeSweepWide) chunk_sum_wide<RS>(va, gs4, fs4, cc, acc, wide_m, sum, comp);
           if constexpr (MODE == kModeTopK) chunk_topk<RS>(va, gsf, fsf, crow, colbase, p.k, tv, ti, &tcnt, thr);
           if constexpr (MODE == kModeTopKShared)
             chunk_topk_shared<RS>(va, gsf, fsf, crow, colbase, p.k, lv, li, thr);
@@ -969,8 +1005,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!idle) {
           if constexpr (FOLD) chunk_sum_fold(vb, cc, acc);
           if constexpr (MODE == kModeSweep && !FOLD) chunk_sum<RS>(vb, gs4 + 8, fs4 + 8, cc, acc);
-          if constexpr (MODE == kModeSweepShift) chunk_sum_shift<RS>(vb, gs4 + 8, fs4 + 8, cc, rshift, acc);
-          if constexpr (MODE == kModeRowMax) chunk_max<RS>(vb, gsf + 32, fsf + 32, crow, rmax);
+          if constexpr (MODE == kModeSweepWide) chunk_sum_wide<RS>(vb, gs4 + 8, fs4 + 8, cc, acc, wide_m, sum, comp);
           if constexpr (MODE == kModeTopK)
             chunk_topk<RS>(vb, gsf + 32, fsf + 32, crow, colbase + 32, p.k, tv, ti, &tcnt, thr);
           if constexpr (MODE == kModeTopKShared)
@@ -1010,7 +1045,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           break;
         }
         if constexpr (kSweepLike) rb[rloc] = sum - comp;
-        if constexpr (MODE == kModeRowMax) rb[rloc] = rmax;
+        if constexpr (MODE == kModeSweepWide) wide_shift[pb * kFusedOwnRows + rloc] = wide_m;
         if constexpr (MODE == kModeTopK) {
           if (row_ok)
             for (int i = 0; i < p.k; ++i) {
@@ -1072,14 +1107,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         if (lane == 0) mbar_arrive(&rowfree[pb]);
       }
-      if constexpr (MODE == kModeRowMax) {
-        const float other = rb[rloc];
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&rowfree[pb]);
-        if (row_ok) p.rowmax[p.row0 + r] = fmaxf(rmax, other);
-      }
       if constexpr (kSweepLike) {
-        const float other = rb[rloc];
+        float other = rb[rloc];
+        float row_m = 0.0f;  // wide markets: the shift of the row's sum (log2 units)
+        if constexpr (MODE == kModeSweepWide) {
+          // the two halves' sums onto the larger of their shifts (exact powers of two)
+          const float other_m = wide_shift[pb * kFusedOwnRows + rloc];
+          row_m = fmaxf(wide_m, other_m);
+          const float own_scale = exp2_int(wide_m - row_m);
+          sum *= own_scale;
+          comp *= own_scale;
+          other *= exp2_int(other_m - row_m);
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive(&rowfree[pb]);
         const int64_t row = p.row0 + r;
@@ -1121,8 +1160,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const double own_off = BATCH ? bd->st[kStOwnOff] : own_off0;
           double ln_sum = log_row_sum(s_hi, s_lo, s_o);
           // wide markets: the row's shift comes back into the sum's logarithm
-          if constexpr (MODE == kModeSweepShift)
-            ln_sum = __fma_rn(-(double)__uint_as_float((uint32_t)rshift), 0.69314718055994530942, ln_sum);
+          if constexpr (MODE == kModeSweepWide) ln_sum = __fma_rn((double)row_m, 0.69314718055994530942, ln_sum);
           const RowResult rr = row_update(ln_sum, shift, b2s ? b2s[row] : 0.0f,
                                           (BATCH ? bd->mass : p.mass)[row], log_u[row] + own_off,
                                           p.residual, omega);
@@ -1252,7 +1290,7 @@ constexpr int kSmemLimit = 232448;  // dynamic shared memory per CTA (227 KB)
 // most 6 whole tiles (one k block per row), 4 (two) or 5 single k blocks
 // (four: 1.25 partner tiles in flight).
 constexpr int stages_for(int KB, int MODE, int fmt, bool fold) {
-  const int fixed = smem_bytes(KB, fmt, 0, fold) + (MODE == kModeTopKShared ? kTopKListBytes : 0);
+  const int fixed = smem_bytes(KB, fmt, 0, fold) + mode_extra_bytes(MODE);
   const int fit = (kSmemLimit - fixed) / stage_bytes(KB, fold);
   const int cap = KB == 1 ? 6 : (KB == 2 ? 4 : 5);
   return fit < cap ? fit : cap;
@@ -1263,7 +1301,7 @@ constexpr int kStages = stages_for(KB, MODE, FMT, FOLD);
 
 template <int KB, int MODE, int FMT, bool FOLD>
 constexpr int kSmemTotal =
-    smem_bytes(KB, FMT, kStages<KB, MODE, FMT, FOLD>, FOLD) + (MODE == kModeTopKShared ? kTopKListBytes : 0);
+    smem_bytes(KB, FMT, kStages<KB, MODE, FMT, FOLD>, FOLD) + mode_extra_bytes(MODE);
 
 // Instantiations that exist: batched launches take one or two k blocks
 // (e4m3: one); the shared-memory ranked lists leave too little room for
@@ -1341,8 +1379,7 @@ cudaError_t set_kernel_attributes_now() {
   if (e == cudaSuccess) e = set_attributes_mode<kModeMu, false>();
   if (e == cudaSuccess) e = set_attributes_mode<kModeTopKShared, false>();
   if (e == cudaSuccess) e = set_attributes_mode<kModeSweep, true>();
-  if (e == cudaSuccess) e = set_attributes_mode<kModeRowMax, false>();
-  if (e == cudaSuccess) e = set_attributes_mode<kModeSweepShift, false>();
+  if (e == cudaSuccess) e = set_attributes_mode<kModeSweepWide, false>();
   // the allocation-free entry point's unfolded half-sweep (rows of one k block)
   if (e == cudaSuccess) e = set_attribute_one<1, kModeSweep, false, kFmtBF16, false, false, true>();
   return e;
@@ -1499,13 +1536,7 @@ cudaError_t launch_fused_halfsweep(tu_market* m, int side, int residual, int upd
   const int grid = grid_for_tiles(p.num_own_tiles * p.split, m->num_sms);
   *nparts_out = grid;
   const int fmt = fmt_of(m->dtype);
-  if (m->wide) {
-    // two passes: every own row's largest exponent, then the half-sweep with it subtracted
-    p.rowmax = m->rowmax;
-    cudaError_t e = launch_any<kModeRowMax>(m->kp, fmt, own.tm_own, partner.tm_partner, p, grid, m->stream, small);
-    if (e != cudaSuccess) return e;
-    return launch_any<kModeSweepShift>(m->kp, fmt, own.tm_own, partner.tm_partner, p, grid, m->stream, small);
-  }
+  if (m->wide) return launch_any<kModeSweepWide>(m->kp, fmt, own.tm_own, partner.tm_partner, p, grid, m->stream, small);
   return launch_any<kModeSweep>(m->kp, fmt, own.tm_own, partner.tm_partner, p, grid, m->stream, small);
 }
 

@@ -430,9 +430,9 @@ tu_status load_factors(tu_market* m, const void* F, const void* K, const void* G
   const double bound = (double)hn[0] * (double)hn[1] / (2.0 * m->sigma);  // FP8: norms of the quantized rows
   // One shift per half-sweep (the partner side's max ell) keeps every exponent
   // within +-bound log2(e) of the row's largest: up to 40, FP32 holds the
-  // terms and their sums. Beyond, the fused path finds each row's largest
-  // exponent first (a second pass over the pairs) and subtracts it; the dense
-  // path's materialised A-hat itself would leave the FP32 range.
+  // terms and their sums. Beyond, the fused path keeps a running maximum per
+  // row and rescales the row's sum when it grows (one pass); the dense path's
+  // materialised A-hat itself would leave the FP32 range.
   const bool wide = bound > 40.0;
   if (wide && m->path == TU_PATH_DENSE) {
     char buf[160];
@@ -735,7 +735,6 @@ void tu_market_destroy(tu_market_t m) {
   }
   dev_free(m, m->partials);
   dev_free(m, m->st);
-  dev_free(m, m->rowmax);
   dev_free(m, m->split_part);
   dev_free(m, m->split_cnt);
   dev_free(m, m->results);
@@ -826,11 +825,6 @@ tu_status tu_market_create(const tu_market_desc* desc, tu_market_t* out) {
   }
   if ((st = side_alloc(m, m->X, D.N, D.bias_x != nullptr)) != TU_OK) return bail(st);
   if ((st = side_alloc(m, m->Y, D.M, D.bias_y != nullptr)) != TU_OK) return bail(st);
-  // fused path: per-row shifts of wide markets, one buffer for the larger side
-  if (D.path == TU_PATH_FUSED &&
-      (st = dev_alloc(m, &m->rowmax, (size_t)(m->X.rows_pad > m->Y.rows_pad ? m->X.rows_pad : m->Y.rows_pad))) !=
-          TU_OK)
-    return bail(st);
   if ((st = dev_alloc(m, &m->partials, (size_t)kMaxPartials * 4)) != TU_OK) return bail(st);
   if ((st = dev_alloc(m, &m->st, (size_t)kStSlots)) != TU_OK) return bail(st);
   if ((st = dev_alloc(m, &m->results, (size_t)kResSlots)) != TU_OK) return bail(st);

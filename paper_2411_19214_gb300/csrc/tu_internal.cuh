@@ -181,8 +181,7 @@ struct tu_market {
   int* split_cnt = nullptr;        // split > 1: arrivals per (own tile, 32-row block), zeroed
   int split_cap = 0;               // the split the buffers were sized for
   bool translate = true;           // tu_market_set_translation: translation step before every half-sweep
-  bool wide = false;               // factor range beyond one shift per half-sweep: per-row shifts (two passes)
-  float* rowmax = nullptr;         // fused path: per own row, the largest exponent (log2), max(N, M) padded
+  bool wide = false;               // factor range beyond one shift per half-sweep: per-row running maxima
   bool poisoned = false;
   std::string last_error;
   // benchmark timing (tu_profile_enable / tu_profile_read)

@@ -2,10 +2,10 @@
 
 With max|a_x| max|b_y| / (2 sigma) above 40 (strong preferences, small
 sigma), one shift per half-sweep would leave FP32 exponents out of range; the
-fused path then takes two passes per half-sweep, the first finding every own
-row's largest exponent c phi_hat + g, the second subtracting it before ex2
-(tu_market_create). These markets are checked against the oracle on the same
-rounded factors.
+fused path then keeps a running maximum of every own row's exponents
+c phi_hat + g and rescales the row's sum by an exact power of two whenever it
+grows, so that no term exceeds 2^0 (tu_market_create). These markets are
+checked against the oracle on the same rounded factors.
 
 Tolerance (derived): the tensor cores accumulate phi = <a, b> of exact BF16
 products in FP32; over the 2d = 128 terms the rounding is about
