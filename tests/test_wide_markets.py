@@ -67,6 +67,38 @@ def test_wide_market_sweeps_match_oracle(gpu_lib):
         mkt.close()
 
 
+@pytest.mark.parametrize("order", ["ascending", "descending"])
+def test_running_maximum_across_column_orders(gpu_lib, order):
+    """The running maximum under its two extremes. With the partner side sorted
+    by bias ascending, the exponents of a row tend to grow along its
+    columns, so its shift rises in chunk after chunk and everything summed
+    before is rescaled again and again; sorted descending, the first chunk
+    holds the largest terms and the shift hardly moves. The permutation
+    leaves the market's fixed point unchanged (Eq. iteration is equivariant
+    under relabelling the partners), so both orders must match the oracle
+    on the permuted market, and each other."""
+    import dataclasses
+
+    tu = gpu_lib
+    base = _mk(N=300, M=1000, d=64, seed=37)
+    perm = np.argsort(base.bias_y, kind="stable")
+    if order == "descending":
+        perm = perm[::-1].copy()
+    mk = dataclasses.replace(base, G=base.G[perm], L=base.L[perm], bias_y=base.bias_y[perm], m=base.m[perm])
+    assert _bound(mk) > 100.0
+    atol = _atol(mk)
+    mkt = tu.from_synth(mk)
+    try:
+        mkt.sweep(3)
+        lu, lv = mkt.potentials64()
+        ou, ov = oracle_sweeps(mk, 3)
+        np.testing.assert_allclose(lu, ou, rtol=0, atol=atol)
+        np.testing.assert_allclose(lv, ov, rtol=0, atol=atol)
+        print(f"{order}: max |log potential error| {max(np.abs(lu - ou).max(), np.abs(lv - ov).max()):.2e}")
+    finally:
+        mkt.close()
+
+
 def test_wide_market_solve_lists_and_mu(gpu_lib):
     """Solved to max(1e-6, 2 B 2^-24), the attainable residual: a row's
     dominant terms pair an exponent c phi of hundreds with a partner potential
@@ -134,8 +166,8 @@ def test_wide_markets_refused_where_one_shift_is_needed(gpu_lib):
 
 @pytest.mark.parametrize("per", ["row", "side"])
 def test_wide_fp8_market_sweeps_match_oracle(gpu_lib, per):
-    """The two-pass wide path with e4m3 factors (per-row scales multiply the
-    accumulator entries in both passes; per-side scales fold into c),
+    """The wide path with e4m3 factors (per-row scales multiply the
+    accumulator entries before the running maximum; per-side scales fold into c),
     against the oracle on the same quantized factors."""
     from synth import fp8_quantized
     tu = gpu_lib
