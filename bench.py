@@ -42,11 +42,13 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # workloads
 # ---------------------------------------------------------------------------
 
-def make_workload(name: str, rank: int, shape=None, fp8=None):
+def make_workload(name: str, rank: int, shape=None, fp8=None, sigma=None):
     from synth import dense_job_market, fused_market
     kw = {} if shape is None else {"N": shape[0], "M": shape[1]}
     if shape is not None and len(shape) > 2 and name == "fused":
         kw["d"] = shape[2]  # (profiling cases of other row lengths)
+    if sigma is not None and name == "fused":
+        kw["sigma"] = sigma  # (profiling cases of other exponent ranges, e.g. wide markets)
     if name == "fused" and fp8:
         # the same market with unrounded FP32 factors, quantized to e4m3 by the library
         mk = fused_market(seed=1002 + 97 * rank, dtype="fp32", **kw)
@@ -58,8 +60,8 @@ def make_workload(name: str, rank: int, shape=None, fp8=None):
                "factors": f"e4m3, {scales}",
                "l2": "inputs larger than L2: each half-sweep streams the 128 MB partner factor matrix "
                      "(L2 is 129 MB); no flush between steps"}
-        if shape is not None:
-            cfg["workload"] = f"fused FP8 IPFP, reduced shape N={mk.N}, M={mk.M}, d={mk.d}, same recipe"
+        if shape is not None or sigma is not None:
+            cfg["workload"] = f"fused FP8 IPFP, N={mk.N}, M={mk.M}, d={mk.d}, sigma={mk.sigma}, otherwise the same recipe"
         return mk, cfg, 65536
     if name == "fused":
         mk = fused_market(seed=1002 + 97 * rank, **kw)
@@ -69,8 +71,9 @@ def make_workload(name: str, rank: int, shape=None, fp8=None):
                "N": mk.N, "M": mk.M, "d": mk.d, "sigma": mk.sigma, "partition": 65536, "path": "fused",
                "l2": "inputs larger than L2: each half-sweep streams the 256 MB partner factor matrix "
                      "(L2 is 129 MB); no flush between steps"}
-        if shape is not None:
-            cfg["workload"] = f"fused mini-batch IPFP (Alg. 2), reduced shape N={mk.N}, M={mk.M}, d={mk.d}, same recipe"
+        if shape is not None or sigma is not None:
+            cfg["workload"] = (f"fused mini-batch IPFP (Alg. 2), N={mk.N}, M={mk.M}, d={mk.d}, sigma={mk.sigma}, "
+                               "otherwise the same recipe")
         return mk, cfg, 65536
     if name == "dense":
         mk = dense_job_market(seed=1001 + 97 * rank, **kw)
@@ -282,7 +285,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    mk, cfg, _ = make_workload(args.workload, 0, args.shape)
+    mk, cfg, _ = make_workload(args.workload, 0, args.shape, sigma=args.sigma)
     pool = OraclePool(mk)
     try:
         rpc = pool.calibrate(8.0)
@@ -928,6 +931,7 @@ def sub_args(args, workload: str, steps=None):
     a.fp8 = None
     a.partner_blocks = 0
     a.shape = None
+    a.sigma = None
     if steps is not None:
         a.steps = steps
     return a
@@ -961,7 +965,7 @@ def run_ours(args):
             dist.barrier()
 
     tu.load()
-    mk, cfg, partition = make_workload(args.workload, rank, args.shape, fp8=args.fp8)
+    mk, cfg, partition = make_workload(args.workload, rank, args.shape, fp8=args.fp8, sigma=args.sigma)
     # the CPU baseline pool is spawned before the first CUDA work of this process
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -1095,7 +1099,8 @@ def run_ours(args):
         roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak,
                     "traffic": (measured_traffic(f"fused fp8 {args.fp8} 1Mx1M d64" if args.fp8
-                                                 else "fused 1Mx1M d64") if args.shape is None else None),
+                                                 else "fused 1Mx1M d64")
+                                if args.shape is None and args.sigma is None else None),
                     "kernel": "k_fused_halfsweep (tcgen05 %s MMA + ex2 row reduction)" % ("e4m3" if args.fp8
                                                                                          else "BF16"),
                     "per_launch": f"{flops:.4g} flop (2*N*M*2d) in {avg_pass_s * 1e3:.2f} ms average over "
@@ -1162,6 +1167,7 @@ def run_ours(args):
     if solve is not None:
         line["solve"] = solve
     if cfg["path"] == "fused" and not args.no_extras and rank == 0 and world == 1 and args.shape is None \
+            and args.sigma is None \
             and not args.fp8:
         line["quantisation_error"] = quantisation_error(dev)
         line["expected_matches"] = expected_matches_block()
@@ -1196,6 +1202,9 @@ def main():
                     help="skip the plain-FP32 comparison and the ranked-list timing")
     ap.add_argument("--shape", default=None,
                     help="N,M[,d] override of the workload's sizes (same recipe; for small profiling cases)")
+    ap.add_argument("--sigma", type=float, default=None,
+                    help="sigma override of the fused workload (same recipe; e.g. 0.01 makes its exponent range "
+                         "wide: the running-maximum half-sweep)")
     args = ap.parse_args()
     if args.shape:
         args.shape = tuple(int(v) for v in args.shape.split(","))

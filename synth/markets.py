@@ -239,11 +239,12 @@ def dense_job_market(N: int = 20000, M: int = 10000, d: int = 32, seed: int = 10
 
 
 def fused_market(N: int = 1_000_000, M: int = 1_000_000, d: int = 64, seed: int = 1002,
-                 dtype: str = "bf16") -> Market:
+                 dtype: str = "bf16", sigma: float = 0.5) -> Market:
     """Large balanced market for the on-the-fly path: bf16 factors N(0, 1/d),
-    lognormal popularity biases on both sides, unit capacities, sigma = 0.5."""
-    return make_market(N, M, d, sigma=0.5, seed=seed, bias_x=True, bias_y=True,
-                       dtype=dtype, recipe=f"fused N={N} M={M} d={d}")
+    lognormal popularity biases on both sides, unit capacities, sigma = 0.5
+    (another sigma for profiling cases of other exponent ranges)."""
+    return make_market(N, M, d, sigma=sigma, seed=seed, bias_x=True, bias_y=True,
+                       dtype=dtype, recipe=f"fused N={N} M={M} d={d}" + ("" if sigma == 0.5 else f" sigma={sigma}"))
 
 
 def paper_shaped_market(N: int, D: int = 50, seed: int = 1005, dtype: str = "bf16") -> Market:
