@@ -477,7 +477,10 @@ typedef struct tu_batch* tu_batch_t;
  * (their buffers, tensor maps, sigma, relaxation and translation settings at
  * creation); destroy the batch before any of them. Wide markets (see
  * tu_market_create) and markets with d > 64 (BF16 with 2d > 128) cannot join
- * a batch (TU_ERR_UNSUPPORTED).
+ * a batch (TU_ERR_UNSUPPORTED). A member's factors may be replaced
+ * (tu_market_update_factors) between batch calls: the batch follows its new
+ * scales (e4m3 with one scale per side), and tu_batch_sweep / tu_batch_solve
+ * return TU_ERR_UNSUPPORTED while a member's factors are wide.
  * Batch work is ordered on `stream` (a cudaStream_t, or NULL for the legacy
  * default stream); every batch call first waits for work already enqueued on
  * the members' own streams, and the caller orders later member calls after

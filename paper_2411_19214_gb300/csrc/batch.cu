@@ -11,6 +11,7 @@
 // differs (per own tile and warp instead of per CTA).
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <map>
 #include <new>
@@ -63,6 +64,7 @@ struct tu_batch {
   cudaStream_t stream = nullptr;
   std::vector<tu_market*> markets;
   std::vector<double> relax_cfg;    // each market's relaxation setting at creation
+  std::vector<float> c_host;        // each market's exponent multiplier as its descriptors hold it
   BatchDesc* desc_dev[2] = {nullptr, nullptr};  // [side][market]
   std::vector<int> own_tiles[2];    // per market
   std::vector<int> partner_tiles[2];
@@ -286,13 +288,31 @@ tu_status check_live(tu_batch* b) {
 
 // Work already enqueued on the members' streams completes before batch work
 // (factors replaced since land in place: the descriptors hold the members'
-// buffers, and the exponent multiplier depends on sigma only).
+// buffers; refresh_members follows what else the new factors change).
 tu_status wait_members(tu_batch* b) {
   std::vector<cudaStream_t> seen;
   for (tu_market* m : b->markets) {
     if (m->stream == b->stream || std::find(seen.begin(), seen.end(), m->stream) != seen.end()) continue;
     seen.push_back(m->stream);
     TB_CK(b, cudaStreamSynchronize(m->stream));
+  }
+  return TU_OK;
+}
+
+// Members whose factors were replaced since the batch was made: the exponent
+// multiplier of e4m3 markets with one scale per side moves with the sides'
+// scales, so it is rewritten into both sides' descriptors (in stream order,
+// before the launches that read it); a member whose new factors need the
+// wide half-sweep (tu_market_create) is refused, as at creation.
+tu_status refresh_members(tu_batch* b) {
+  for (int i = 0; i < b->count; ++i) {
+    const tu_market* m = b->markets[i];
+    if (m->wide) return bfail(b, TU_ERR_UNSUPPORTED, "a member's replaced factors need the wide half-sweep");
+    if (m->cmul == b->c_host[i]) continue;
+    b->c_host[i] = m->cmul;
+    for (int side = 0; side < 2; ++side)
+      TB_CK(b, cudaMemcpyAsync(reinterpret_cast<char*>(b->desc_dev[side] + i) + offsetof(BatchDesc, c),
+                               &b->c_host[i], sizeof(float), cudaMemcpyHostToDevice, b->stream));
   }
   return TU_OK;
 }
@@ -561,6 +581,7 @@ tu_status tu_batch_create(const tu_market_t* markets, int count, void* stream, t
   b->dtype = ms[0]->dtype;
   b->stream = static_cast<cudaStream_t>(stream);
   b->markets = ms;
+  b->c_host.assign(count, 0.0f);
   if (cudaSetDevice(b->device) != cudaSuccess) return bail(TU_ERR_CUDA);
   // descriptors: side 0 updates X against Y, side 1 updates Y against X
   std::vector<BatchDesc> desc(count);
@@ -601,6 +622,7 @@ tu_status tu_batch_create(const tu_market_t* markets, int count, void* stream, t
       d.num_partner_tiles = (int)((par.rows + kFusedPartnerRows - 1) / kFusedPartnerRows);
       d.slot0 = (int)slot;
       d.c = m->cmul;
+      if (side == 0) b->c_host[i] = m->cmul;
       d.fs_own = own.fs;
       d.fs_par = par.fs;
       d.gfold = par.fold;
@@ -665,6 +687,7 @@ tu_status tu_batch_sweep(tu_batch_t b, int nsweeps, double* residual_out) {
   TB_TRY(check_live(b));
   if (nsweeps < 0) return bfail(b, TU_ERR_INVALID_ARG, "nsweeps < 0");
   TB_TRY(wait_members(b));
+  TB_TRY(refresh_members(b));
   std::vector<int> all(b->count);
   for (int i = 0; i < b->count; ++i) all[i] = i;
   TB_TRY(sched_set(b, b->sched[0], all));
@@ -686,6 +709,7 @@ tu_status tu_batch_solve(tu_batch_t b, double tol, int max_iter, int warm_start,
   TB_TRY(check_live(b));
   if (!(tol >= 0.0) || max_iter < 0) return bfail(b, TU_ERR_INVALID_ARG, "tol < 0 or max_iter < 0");
   TB_TRY(wait_members(b));
+  TB_TRY(refresh_members(b));
   const int count = b->count;
   std::vector<int> all(count);
   for (int i = 0; i < count; ++i) all[i] = i;

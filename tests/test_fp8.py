@@ -127,6 +127,59 @@ def test_fp8_batch_bit_identical_to_solo(gpu_lib, mode):
             m.close()
 
 
+def test_batch_follows_replaced_factors(gpu_lib):
+    """A batch holds its members' descriptors, built at creation. Replacing a
+    member's factors moves an e4m3 market's side scales and with them the
+    exponent multiplier c = log2(e) / (2 sigma) 2^(k_X + k_Y), which the
+    batch must follow: after the same replacement, batched sweeps stay bit
+    for bit those of the market alone. Factors that become wide are refused
+    at the next batch call (TU_ERR_UNSUPPORTED), and accepted again once
+    replaced by narrow ones."""
+    tu = gpu_lib
+    mks = [_mk(400, 300, 64, seed=70), _mk(300, 500, 48, seed=71)]
+    solo = [tu.from_synth(mk, fp8="side") for mk in mks]
+    grouped = [tu.from_synth(mk, fp8="side") for mk in mks]
+    batch = tu.Batch(grouped)
+
+    def cuda(a):
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+    def same():
+        for a, b in zip(solo, grouped):
+            (au, av), (bu, bv) = a.potentials(), b.potentials()
+            assert torch.equal(au, bu) and torch.equal(av, bv)
+
+    try:
+        batch.sweep(2)
+        torch.cuda.synchronize()
+        for m in solo:
+            m.sweep(2)
+        same()
+        # 8 x the X factors of market 0: its X scale exponent moves by 3
+        mk = mks[0]
+        new = (cuda(8.0 * mk.F), cuda(8.0 * mk.K), cuda(mk.G), cuda(mk.L))
+        for m in (solo[0], grouped[0]):
+            m.update_factors(*new)
+        batch.sweep(2)
+        torch.cuda.synchronize()
+        for m in solo:
+            m.sweep(2)
+        same()
+        # 40 x: beyond one shift per half-sweep
+        wide = (cuda(40.0 * mk.F), cuda(40.0 * mk.K), cuda(40.0 * mk.G), cuda(40.0 * mk.L))
+        grouped[0].update_factors(*wide)
+        with pytest.raises(tu.TuError) as e:
+            batch.sweep(1)
+        assert e.value.status == tu.TU_ERR_UNSUPPORTED
+        grouped[0].update_factors(*new)
+        batch.sweep(1)
+        torch.cuda.synchronize()
+    finally:
+        batch.close()
+        for m in solo + grouped:
+            m.close()
+
+
 def test_fp8_invalid_combinations(gpu_lib):
     tu = gpu_lib
     mk = _mk(100, 120, 32, seed=3)
