@@ -559,9 +559,20 @@ tu_status read_results(tu_market* m) {
   return TU_OK;
 }
 
+// The partner split's arrival counters: 8 per own tile of 128 rows or more,
+// for the larger side.
+int64_t split_counter_count(const tu_market* m) {
+  const int64_t rows = m->X.rows_pad > m->Y.rows_pad ? m->X.rows_pad : m->Y.rows_pad;
+  return (rows / (kFusedOwnRows / 2) + 1) * (kFusedOwnRows / 32);
+}
+
 tu_status clear_results(tu_market* m) {
   TU_CK(m, cudaMemsetAsync(m->results, 0, kResSlots * sizeof(double), m->stream));
   TU_CK(m, cudaMemsetAsync(m->err_dev, 0, sizeof(int), m->stream));
+  // every completed split launch leaves its counters at zero, but one that a
+  // timed-out wait cut short may not: zeroed again before the next work
+  if (m->split_cnt != nullptr)
+    TU_CK(m, cudaMemsetAsync(m->split_cnt, 0, (size_t)split_counter_count(m) * sizeof(int), m->stream));
   return TU_OK;
 }
 
@@ -998,7 +1009,7 @@ tu_status ensure_split_buffers(tu_market* m, int split) {
   dev_free(m, m->split_cnt);
   m->split_cap = 0;
   const int64_t rows = m->X.rows_pad > m->Y.rows_pad ? m->X.rows_pad : m->Y.rows_pad;
-  const int64_t blocks = (rows / (kFusedOwnRows / 2) + 1) * (kFusedOwnRows / 32);
+  const int64_t blocks = split_counter_count(m);
   TU_TRY(dev_alloc(m, &m->split_part, (size_t)split * rows));
   TU_TRY(dev_alloc(m, &m->split_cnt, (size_t)blocks));
   TU_CK(m, cudaMemsetAsync(m->split_cnt, 0, (size_t)blocks * sizeof(int), m->stream));
