@@ -404,7 +404,11 @@ tu_status tu_market_relax_update(tu_market_t mkt, double tol);
 tu_status tu_market_query(tu_market_t mkt, int* idle, double* residual, double* match_count, int64_t* sweeps);
 
 /* Device memory a market of this shape holds (bytes), for admission control:
- * the packed factors, the per-user state and the dense matrices if any. */
+ * the packed factors, the per-user state and the dense matrices if any, for
+ * BF16 or FP32 factors in the default launch shape. A partner split
+ * (tu_market_set_split, or a tuned shape a new market takes from the
+ * autotuner's cache) adds split x max(N, M) x 16 bytes; e4m3 markets hold
+ * 1-byte factors and 4 to 36 more bytes per user (scales, folded g). */
 int64_t tu_market_footprint(int64_t N, int64_t M, int64_t d, int path);
 
 /* Kernel timing for benchmarks (no counterpart in the paper). While enabled,
