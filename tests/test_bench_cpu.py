@@ -47,6 +47,15 @@ def test_reference_arm_default_workload():
     assert d["gpair_evals_per_s"] == pytest.approx(d["value"] * 2e12 / 1e9, rel=1e-9)
 
 
+def test_reference_arm_times_the_sigma_override():
+    """--sigma changes the fused workload's exponent range (0.01 makes it wide,
+    the running-maximum half-sweep); the reference arm times that same market."""
+    (d,) = _last_json(_bench("--impl", "reference", "--sigma", "0.01", "--steps", "1", "--warmup", "3"))
+    _check_reference_line(d, "sweeps/s")
+    assert d["config"]["sigma"] == 0.01 and "sigma=0.01" in d["config"]["workload"]
+    assert d["config"]["N"] == 1_000_000 and d["config"]["d"] == 64
+
+
 def test_reference_arm_batched_workload():
     (d,) = _last_json(_bench("--impl", "reference", "--workload", "batched", "--steps", "1", "--warmup", "3"))
     _check_reference_line(d, "Gpair-evals/s")
