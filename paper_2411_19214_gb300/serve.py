@@ -54,10 +54,10 @@ from typing import Dict, List, Optional
 
 import numpy as np
 
-from . import (TuError, tu_batch_create, tu_batch_destroy, tu_batch_solve, tu_get_potentials, tu_ipfp_sweep,
-               tu_market_create, tu_market_destroy, tu_market_footprint, tu_market_query, tu_market_relax_update,
-               tu_market_set_relaxation, tu_market_set_small_tiles, tu_market_set_translation,
-               tu_market_update_factors, tu_market_use_graphs, tu_topk_partners)
+from . import (TU_ERR_UNSUPPORTED, TuError, tu_batch_create, tu_batch_destroy, tu_batch_solve, tu_get_potentials,
+               tu_ipfp_solve, tu_ipfp_sweep, tu_market_create, tu_market_destroy, tu_market_footprint,
+               tu_market_query, tu_market_relax_update, tu_market_set_relaxation, tu_market_set_small_tiles,
+               tu_market_set_translation, tu_market_update_factors, tu_market_use_graphs, tu_topk_partners)
 
 # the fused path's factor dimension limit (2d padded to at most 256: four 128-byte k blocks)
 MAX_D = 128
@@ -290,14 +290,19 @@ class Server:
         except TuError:
             self.used -= arg
             raise
-        # a request runs only a few blocks of sweeps: too few to amortise a graph capture
-        tu_market_use_graphs(h, False)
-        # many markets share the GPU: 256-row own tiles keep the per-SM throughput
-        tu_market_set_small_tiles(h, False)
-        if not self.translate:
-            tu_market_set_translation(h, False)  # Eq. iteration exactly
-        if self.relax:
-            tu_market_set_relaxation(h, 0.0)
+        try:
+            # a request runs only a few blocks of sweeps: too few to amortise a graph capture
+            tu_market_use_graphs(h, False)
+            # many markets share the GPU: 256-row own tiles keep the per-SM throughput
+            tu_market_set_small_tiles(h, False)
+            if not self.translate:
+                tu_market_set_translation(h, False)  # Eq. iteration exactly
+            if self.relax:
+                tu_market_set_relaxation(h, 0.0)
+        except TuError:
+            tu_market_destroy(h)
+            self.used -= arg
+            raise
         return _Slot(handle=h, stream=stream, shape=req.shape, bytes=arg, req=req, admitted=now)
 
     def _reply(self, slot: _Slot, residual: float, match: float, now_fn):
@@ -543,7 +548,10 @@ class WindowServer:
     Admission by HBM footprint with LRU eviction of idle resident markets,
     and validation, as in Server. The host thread blocks in the batched
     solve, so requests that arrive meanwhile wait for the next window. d above
-    the batched launch's limit (64) is answered ``invalid``."""
+    the batched launch's limit (64) is answered ``invalid``; a group that the
+    batched launch refuses (a market with a wide exponent range) is solved
+    market by market (``tu_ipfp_solve``), so that one such request does not
+    fail the others."""
 
     def __init__(self, hbm_budget_bytes: int, tol: float = 1e-6, max_sweeps: int = 200, k: int = 10,
                  window_s: float = 0.01, max_batch: int = 64, relax: bool = True, translate: bool = True):
@@ -559,7 +567,8 @@ class WindowServer:
         self.used = 0
         self.resident: "collections.OrderedDict[str, tuple]" = collections.OrderedDict()  # key -> (handle, shape, bytes)
         self.stream = torch.cuda.Stream()
-        self.stats = dict(admitted=0, evicted=0, warm=0, groups=0, largest_group=0, invalid=0, errors=0)
+        self.stats = dict(admitted=0, evicted=0, warm=0, groups=0, largest_group=0, invalid=0, errors=0,
+                          solved_alone=0)
 
     def _evict_one(self) -> bool:
         if not self.resident:
@@ -598,12 +607,32 @@ class WindowServer:
                                  bias_x=req.bias_x, bias_y=req.bias_y, path="fused", stream=self.stream)
         except TuError as e:
             return f"error: {e}"
+        try:
+            if not self.translate:
+                tu_market_set_translation(h, False)
+            if self.relax:
+                tu_market_set_relaxation(h, 0.0)
+        except TuError as e:
+            tu_market_destroy(h)
+            return f"error: {e}"
         self.used += need
-        if not self.translate:
-            tu_market_set_translation(h, False)
-        if self.relax:
-            tu_market_set_relaxation(h, 0.0)
         return h, need, False
+
+    def _solve_alone(self, made, now_fn, results) -> list:
+        """The markets of a group one by one (tu_ipfp_solve); None in place of
+        a market whose solve failed, which is answered and released here."""
+        infos = []
+        for req, h, nbytes, warm, adm in made:
+            self.stats["solved_alone"] += 1
+            try:
+                infos.append(tu_ipfp_solve(h, self.tol, self.max_sweeps, warm_start=True))
+            except TuError as e:
+                tu_market_destroy(h)
+                self.used -= nbytes
+                self.stats["errors"] += 1
+                results[req.rid] = Server._failed(req, "error", str(e), now_fn(), adm, 0, warm)
+                infos.append(None)
+        return infos
 
     def _solve_group(self, group, now_fn, results) -> list:
         """Solve one group; returns the requests that found no room yet."""
@@ -627,11 +656,18 @@ class WindowServer:
         self.stats["groups"] += 1
         self.stats["largest_group"] = max(self.stats["largest_group"], len(made))
         try:
-            b = tu_batch_create([x[1] for x in made], stream=self.stream)
             try:
-                _, infos = tu_batch_solve(b, self.tol, self.max_sweeps, len(made), warm_start=True)
-            finally:
-                tu_batch_destroy(b)
+                b = tu_batch_create([x[1] for x in made], stream=self.stream)
+                try:
+                    _, infos = tu_batch_solve(b, self.tol, self.max_sweeps, len(made), warm_start=True)
+                finally:
+                    tu_batch_destroy(b)
+            except TuError as e:
+                if e.status != TU_ERR_UNSUPPORTED:
+                    raise
+                # a market the batched launch cannot take (a wide exponent
+                # range): every market of the group is solved on its own
+                infos = self._solve_alone(made, now_fn, results)
         except TuError as e:
             for req, h, nbytes, warm, adm in made:
                 tu_market_destroy(h)
@@ -640,6 +676,8 @@ class WindowServer:
                 results[req.rid] = Server._failed(req, "error", str(e), now_fn(), adm, 0, warm)
             return deferred
         for (req, h, nbytes, warm, adm), info in zip(made, infos):
+            if info is None:  # failed alone: already answered and released
+                continue
             N, M, _ = req.shape
             k = min(self.k, M)
             idx = np.empty((N, k), np.int32)

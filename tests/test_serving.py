@@ -178,3 +178,28 @@ def test_window_server_micro_batches(gpu_lib):
     assert win.stats["warm"] == len(specs)
     assert all(r.status == "ok" and r.warm for r in res2)
     assert sum(r.sweeps for r in res2) < sum(r.sweeps for r in res[:len(specs)]) / 2
+
+
+def test_window_server_wide_request_does_not_fail_its_group(gpu_lib):
+    """A market with a wide exponent range cannot join a batch: the group it
+    falls into is solved market by market instead, so its neighbours get the
+    same replies as from the stream-per-market server, and it gets its own
+    (converged, or capped at the attainable residual of wide markets)."""
+    from paper_2411_19214_gb300 import serve
+    narrow = _requests(serve, [(600, 800, 32), (900, 500, 24)], seed=90)
+    mk = make_market(300, 400, 32, sigma=0.01, seed=92, bias_x=True, bias_y=True, n_kind="uniform1to3",
+                     m_kind="uniform1to3", dtype="bf16")
+    wide = serve.SolveRequest(rid=2, arrival=0.0, F=mk.F, K=mk.K, G=mk.G, L=mk.L, n=mk.n, m=mk.m, sigma=mk.sigma,
+                              bias_x=mk.bias_x, bias_y=mk.bias_y)
+    base = serve.Server(hbm_budget_bytes=8 << 30, tol=1e-6, max_sweeps=400, k=10)
+    ref = base.run(_requests(serve, [(600, 800, 32), (900, 500, 24)], seed=90), realtime=False)
+    base.close()
+    win = serve.WindowServer(hbm_budget_bytes=8 << 30, tol=1e-6, max_sweeps=400, k=10, max_batch=4)
+    res = win.run(narrow + [wide], realtime=False)
+    win.close()
+    assert win.stats["groups"] == 1 and win.stats["solved_alone"] == 3
+    for a, b in zip(res[:2], ref):
+        assert a.status == "ok" and a.converged and a.residual <= 1e-6
+        assert a.match_count == pytest.approx(b.match_count, rel=1e-5)
+        assert np.mean(a.topk_idx == b.topk_idx) > 0.99
+    assert res[2].status in ("ok", "not_converged") and res[2].topk_idx.shape == (300, 10)
