@@ -131,3 +131,30 @@ def test_window_server_single_solve_failure_stays_with_its_request(monkeypatch):
     # the failed market is released; the others stay resident under their keys
     assert lib.destroyed == [101] and set(win.resident) == {"k0", "k2"}
     assert win.used == 2 * 1000
+
+
+def test_server_releases_a_market_whose_configuration_fails(monkeypatch):
+    """A library error in a call that configures a freshly created market
+    (here: switching its graphs off) destroys the market and returns its
+    bytes to the budget before the error reaches the request."""
+    import torch
+
+    from paper_2411_19214_gb300 import TU_ERR_CUDA, serve
+    made, destroyed = [], []
+    monkeypatch.setattr(torch.cuda, "Stream", lambda *a, **k: None)
+    monkeypatch.setattr(serve, "tu_market_create", lambda *a, **k: made.append(7) or 7)
+    monkeypatch.setattr(serve, "tu_market_destroy", destroyed.append)
+
+    def fail(h, enable):
+        raise serve.TuError(TU_ERR_CUDA, "tu_market_use_graphs")
+    monkeypatch.setattr(serve, "tu_market_use_graphs", fail)
+    srv = serve.Server(hbm_budget_bytes=1 << 20, tol=1e-6, max_sweeps=50, k=5)
+    try:
+        srv.used = 1000  # as _admit leaves it for a cold request of 1000 bytes
+        req = _req(serve)
+        arrays = dict(F=req.F, K=req.K, G=req.G, L=req.L, bias_x=req.bias_x, bias_y=req.bias_y)
+        with pytest.raises(serve.TuError):
+            srv._activate("cold", 1000, arrays, req, 0.0)
+        assert made == [7] and destroyed == [7] and srv.used == 0
+    finally:
+        srv.pool.shutdown(wait=True)
