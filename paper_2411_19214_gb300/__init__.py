@@ -18,14 +18,14 @@ from typing import Optional
 
 import numpy as np
 
-from . import build as _build
 
 TU_OK, TU_ERR_INVALID_ARG, TU_ERR_OOM, TU_ERR_CUDA, TU_ERR_NOT_CONVERGED, TU_ERR_NONFINITE, TU_ERR_TIMEOUT, \
     TU_ERR_UNSUPPORTED = range(8)
 TU_DTYPE_BF16, TU_DTYPE_FP32, TU_DTYPE_FP8E4M3, TU_DTYPE_FP8E4M3_SIDE = 0, 1, 2, 3
 TU_PATH_FUSED, TU_PATH_DENSE = 0, 1
 
-LIB_PATH = _build.LIB
+# where build.py puts the library (kept in step with build.LIB)
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libtu_ipfp.so")
 _lib = None
 
 

@@ -170,3 +170,10 @@ def test_binding_fp8_argument(lib):
     with pytest.raises(TypeError):
         tu.tu_market_create(F.astype(np.uint16), F.astype(np.uint16), F.astype(np.uint16), F.astype(np.uint16),
                             np.ones(4), np.ones(4), 1.0, fp8=True)
+
+
+def test_binding_loads_the_library_build_writes():
+    """The binding's library path is where build.py puts the library."""
+    import paper_2411_19214_gb300 as tu
+    from paper_2411_19214_gb300 import build
+    assert os.path.realpath(tu.LIB_PATH) == os.path.realpath(build.LIB)
