@@ -84,8 +84,10 @@ typedef struct {
                             TU_DTYPE_FP8E4M3_SIDE: the same from FP32 factors with one power-of-two
                             scale per side (k the smallest integer with max |entry| of the side <=
                             448 * 2^k), folded into the exponent multiplier: the faster FP8 mode
-                            (the per-row scales cost one multiply per pair), for sides whose rows
-                            have similar norms (small rows lose precision to e4m3 subnormals). */
+                            (the per-row scales cost one multiply and one shared load per pair;
+                            with one scale per side and d <= 64 the partner potentials also ride
+                            in the MMA), for sides whose rows have similar norms (small rows lose
+                            precision to e4m3 subnormals). */
   int32_t path;          /* TU_PATH_FUSED or TU_PATH_DENSE */
   const void* F;         /* N x d row-major, host or device; copied (the market owns its copy) */
   const void* K;         /* N x d row-major, host or device; copied */
@@ -114,8 +116,8 @@ typedef struct {
  * half-sweep keeps every FP32 term in range; beyond ("wide" markets, strong
  * preferences or small sigma), the fused path keeps a running maximum of
  * every row's exponents and rescales the row's sum by an exact power of two
- * whenever it grows (one pass over the pairs, about 1.3x the time of a
- * narrow half-sweep), and the dense path refuses the market
+ * whenever it grows (one pass over the pairs, 1.2 to 1.3 times the time of
+ * a narrow half-sweep), and the dense path refuses the market
  * (TU_ERR_UNSUPPORTED: its materialised FP32 A-hat would overflow). In wide
  * markets the FP32 accumulation of phi carries an absolute error of about
  * bound x 2^-24 x sqrt(2d) per exponent, above the 1e-7 of narrow ones, and
